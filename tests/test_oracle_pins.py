@@ -1,0 +1,289 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms, brute-force Ewald summation, a dense
+pseudo-inverse, finite differences and conservation laws.  None needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import p3maze_oracle as O
+from paper_2606_31379_b300 import synth as S
+from tests.golden_io import read_golden
+
+
+# ---------------------------------------------------------------- parameters
+def test_sigma_alpha_pair_printed_in_paper():
+    g = read_golden("screening_width.txt")
+    assert O.sigma_of_alpha(g["beta"]) == pytest.approx(g["sigma"], abs=5e-4)
+
+
+def test_spcfw_table_matches_table_s1():
+    g = read_golden("spcfw_table_s1.txt")
+    p = S.spcfw_params()
+    for k in ("eps_oo", "sigma_oo", "q_o", "q_h", "r0", "kb", "ka"):
+        assert p[k] == g[k]
+    assert math.degrees(p["theta0"]) == pytest.approx(g["theta0_deg"], abs=1e-12)
+
+
+def test_smoothing_schedule_values():
+    # alpha = 0.30 -> sigma^2 = 1/(2 alpha^2) = 5.5556; L = 25.2, N = 32 -> h = 0.7875
+    K, c = O.smoothing_schedule(O.sigma_of_alpha(0.30), 25.2 / 32)
+    assert K == 25 and 0.0 < c <= 1.0 / 6.0
+    # total added per-axis variance equals sigma^2 - 4 h^2/6
+    h = 25.2 / 32
+    assert 2 * K * c * h * h == pytest.approx(1 / (2 * 0.09) - 4 * h * h / 6, rel=1e-14)
+    assert O.smoothing_schedule(0.1, 1.0) == (0, 0.0)
+
+
+# ---------------------------------------------------------------- B-splines
+def _cardinal_bspline(x, order):
+    """Cox-de Boor recursion for the cardinal B-spline M_order on [0, order)."""
+    if order == 1:
+        return np.where((x >= 0) & (x < 1), 1.0, 0.0)
+    return (x * _cardinal_bspline(x, order - 1)
+            + (order - x) * _cardinal_bspline(x - 1, order - 1)) / (order - 1)
+
+
+def test_bspline_weights_match_recursion_and_moments():
+    t = np.random.default_rng(0).uniform(0, 1, 1000)
+    w = O.bspline4_weights(t)
+    for k in range(4):
+        # node floor(u)-1+k sits at distance t+1-k below u; M_4 centred at 2
+        np.testing.assert_allclose(w[:, k], _cardinal_bspline(t + 3 - k, 4), atol=1e-15)
+    offs = np.arange(4)[None, :] - 1 - t[:, None]
+    np.testing.assert_allclose(w.sum(1), 1.0, atol=1e-15)
+    np.testing.assert_allclose((w * offs).sum(1), 0.0, atol=1e-15)
+    np.testing.assert_allclose((w * offs ** 2).sum(1), 1.0 / 3.0, atol=1e-14)
+
+
+def test_assignment_moments_single_charge():
+    n, box = 16, 16.0
+    pos = np.array([[7.3, 8.91, 6.02]])
+    q = O.assign_charges(pos, np.array([0.7]), box, n)
+    assert q.sum() == pytest.approx(0.7, abs=1e-15)
+    idx = np.arange(n, dtype=float)
+    for ax in range(3):
+        marg = q.sum(axis=tuple(a for a in range(3) if a != ax))
+        m1 = (marg * idx).sum() / 0.7
+        assert m1 == pytest.approx(pos[0, ax], abs=1e-13)
+        assert ((marg * (idx - m1) ** 2).sum() / 0.7) == pytest.approx(1.0 / 3.0, abs=1e-13)
+
+
+# ---------------------------------------------------------------- smoothing
+def test_smoothing_conserves_charge_and_adds_closed_form_variance():
+    # box wide enough (> 20 sigma) that the periodic tails do not overlap
+    n, box = 64, 50.4
+    h = box / n
+    sigma = O.sigma_of_alpha(0.30)
+    K, c = O.smoothing_schedule(sigma, h)
+    pos = np.array([[24.1, 23.7, 26.05]])
+    q = O.assign_charges(pos, np.array([1.0]), box, n)
+    qs = O.smooth(q, K, c)
+    assert qs.sum() == pytest.approx(1.0, abs=1e-13)
+    assert qs.min() >= 0.0                     # c <= 1/6: positivity preserved
+    x = np.arange(n) * h
+    for ax in range(3):
+        marg = qs.sum(axis=tuple(a for a in range(3) if a != ax))
+        m1 = (marg * x).sum()
+        var = (marg * (x - m1) ** 2).sum()
+        assert m1 == pytest.approx(pos[0, ax], abs=1e-9)
+        # assignment h^2/3 plus diffusion sigma^2 - 4h^2/6  =  sigma^2 - h^2/3
+        assert var == pytest.approx(sigma * sigma - h * h / 3.0, rel=1e-9)
+    np.testing.assert_array_equal(O.smooth(q, 0, 0.1), q)
+
+
+# ---------------------------------------------------------------- Laplacian / solve
+def test_laplacian_acts_on_fourier_modes_with_closed_form_eigenvalue():
+    n = 12
+    g = np.indices((n, n, n))
+    for k in [(1, 0, 0), (2, 3, 5), (6, 6, 6), (0, 0, 0)]:
+        mode = np.cos(2 * np.pi * (k[0] * g[0] + k[1] * g[1] + k[2] * g[2]) / n)
+        lam = sum(2 * math.cos(2 * math.pi * ki / n) - 2 for ki in k)
+        np.testing.assert_allclose(O.laplacian7(mode), lam * mode, atol=1e-12)
+
+
+def _dense_M(n):
+    size = n ** 3
+    M = np.zeros((size, size))
+    lin = lambda x, y, z: ((x % n) * n + (y % n)) * n + (z % n)
+    for x in range(n):
+        for y in range(n):
+            for z in range(n):
+                i = lin(x, y, z)
+                M[i, i] -= 6
+                for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    M[i, lin(x + dx, y + dy, z + dz)] += 1
+    return M
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_fft_solve_matches_dense_pseudo_inverse(n):
+    rng = np.random.default_rng(n)
+    qs = rng.standard_normal((n, n, n))
+    qs -= qs.mean()
+    h = 0.8
+    phi = O.solve_constraint_fft(qs, h)
+    ref = -(4 * np.pi / h) * (np.linalg.pinv(_dense_M(n)) @ qs.reshape(-1))
+    np.testing.assert_allclose(phi.reshape(-1), ref, atol=1e-11 * np.abs(ref).max())
+    # and it satisfies the constraint of Eq. 13 with the stencil operator
+    np.testing.assert_allclose(h / (4 * np.pi) * O.laplacian7(phi) + qs, 0.0, atol=1e-13)
+    assert abs(phi.mean()) < 1e-13
+
+
+# ---------------------------------------------------------------- Madelung / Ewald
+def test_ewald_reproduces_madelung_constant():
+    M = read_golden("madelung_nacl.txt")["madelung"]
+    cr = S.rocksalt_crystal(5.64, 1)
+    e, F = O.ewald(cr.pos, cr.charge, cr.box, 1.0, ke=1.0)
+    assert -e * (5.64 / 2) / (cr.n / 2) == pytest.approx(M, abs=1e-6)
+    assert np.abs(F).max() < 1e-10
+
+
+def test_p3maze_energy_converges_to_madelung_as_h_squared():
+    """Narrow screening (sigma = 0.7 A) so the mesh part carries a large share
+    of the crystal's energy; real-space cutoff where erfc < 1e-12."""
+    M = read_golden("madelung_nacl.txt")["madelung"]
+    cr = S.rocksalt_crystal(5.64, 1)
+    alpha = 1.0 / (math.sqrt(2) * 0.7)
+    errs = []
+    for n in (16, 32, 64):
+        out = O.forces_and_energies(cr, alpha, 5.5, n, ke=1.0)
+        m = -out["v_coul"] * (5.64 / 2) / (cr.n / 2)
+        errs.append(abs(m - M) / M)
+        assert out["v_lr"] > 0.5 * abs(out["v_coul"])       # the mesh term matters here
+    assert errs[2] < 1.2e-3
+    assert errs[0] / errs[1] > 2.5 and errs[1] / errs[2] > 3.0
+    # Eq. 14 taken literally (1/2 phi^T q^s) double counts the smear: rejected
+    lit = O.forces_and_energies(cr, alpha, 5.5, 32, ke=1.0, lr_energy="smoothed")
+    assert abs(-lit["v_coul"] * (5.64 / 2) / (cr.n / 2) - M) / M > 0.1
+
+
+def test_p3maze_forces_converge_to_brute_force_ewald():
+    sysr = S.random_neutral(8, 12.0, seed=11, dmin=1.5)
+    alpha = 0.5
+    e_ref, F_ref = O.ewald(sysr.pos, sysr.charge, sysr.box, alpha, ke=1.0)
+    # the Ewald reference does not depend on its splitting parameter
+    e2, F2 = O.ewald(sysr.pos, sysr.charge, sysr.box, 0.8, ke=1.0)
+    assert e2 == pytest.approx(e_ref, rel=1e-12)
+    ferr, eerr = [], []
+    for n in (16, 32, 64):
+        out = O.forces_and_energies(sysr, alpha, 10.5, n, ke=1.0)
+        ferr.append(np.sqrt(((out["F"] - F_ref) ** 2).sum() / (F_ref ** 2).sum()))
+        eerr.append(abs(out["v_coul"] - e_ref) / abs(e_ref))
+        # Newton III for both parts (momentum conservation, Sec. 2)
+        assert np.abs(out["F_sr"].sum(0)).max() < 1e-14
+        assert np.abs(out["F_lr"].sum(0)).max() < 1e-14
+    assert ferr[2] < 2e-3 and eerr[2] < 1e-3
+    assert ferr[0] / ferr[1] > 3.0 and ferr[1] / ferr[2] > 3.0
+
+
+# ---------------------------------------------------------------- short range
+def _fd_check(system, energy_fn, force, h=1e-5, rtol=1e-7, atol=1e-9):
+    rng = np.random.default_rng(5)
+    for i in rng.choice(system.n, 4, replace=False):
+        for d in range(3):
+            p0 = system.pos[i, d]
+            system.pos[i, d] = p0 + h
+            ep = energy_fn(system)
+            system.pos[i, d] = p0 - h
+            em = energy_fn(system)
+            system.pos[i, d] = p0
+            fd = -(ep - em) / (2 * h)
+            assert fd == pytest.approx(force[i, d], rel=rtol, abs=atol)
+
+
+def test_sr_forces_are_minus_gradient_of_sr_energy():
+    s = S.nacl_melt(24, 11.0, seed=3, dmin=2.0)
+    sigma = O.sigma_of_alpha(0.30)
+    rc = 9.0                                  # > L/2: several images contribute
+
+    def energy(sys_):
+        _, ec, ev = O.sr_forces(sys_, sigma, rc)
+        return ec.sum() + ev.sum()
+
+    F, _, _ = O.sr_forces(s, sigma, rc)
+    assert np.abs(F.sum(0)).max() < 1e-9 * np.abs(F).max()
+    _fd_check(s, energy, F)
+
+
+def test_spcfw_intramolecular_forces_are_minus_gradient():
+    w = S.spcfw_water(8, 9.0, seed=2)
+    sigma = O.sigma_of_alpha(0.30)
+
+    def energy(sys_):
+        _, eb, ea, ex = O.intramolecular_terms(sys_, sigma)
+        return eb + ea + ex
+
+    F, _, _, _ = O.intramolecular_terms(w, sigma)
+    assert np.abs(F.sum(0)).max() < 1e-9 * np.abs(F).max()
+    _fd_check(w, energy, F, rtol=1e-6)
+
+
+def test_spcfw_exclusion_cancels_intramolecular_coulomb():
+    """One water molecule alone in a large box, with no screening cutoff issue:
+    the mesh pair kernel erf(r/sqrt2 sigma)/r minus the exclusion must leave no
+    intramolecular Coulomb, so V_SR(intra) = 0 and V_excl = -sum QQ erf/r."""
+    w = S.spcfw_water(1, 30.0, seed=0)
+    sigma = 1.0
+    _, _, _, ex = O.intramolecular_terms(w, sigma, ke=1.0)
+    p, q = w.pos, w.charge
+    ref = 0.0
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        r = np.linalg.norm(p[i] - p[j])
+        ref -= q[i] * q[j] * math.erf(r / (math.sqrt(2) * sigma)) / r
+    assert ex == pytest.approx(ref, rel=1e-14)
+    F, ec, ev = O.sr_forces(w, sigma, 9.0, ke=1.0)
+    assert np.abs(F).max() == 0.0 and ec.sum() == 0.0
+
+
+# ---------------------------------------------------------------- cell list
+def test_cell_list_covers_every_pair_within_cutoff():
+    s = S.nacl_melt(400, 25.2, seed=1)
+    rc = 9.0
+    nc, cell, start, order = O.cell_list(s.pos, s.box, rc)
+    assert nc == 5 and s.box / nc >= rc / 2
+    # order sorted by (cell, index) and start offsets consistent
+    assert np.all(np.diff(cell[order].astype(np.int64) * s.n + order) > 0)
+    for c in range(nc ** 3):
+        members = order[start[c]:start[c + 1]]
+        assert np.all(cell[members] == c)
+    # every pair within R_c sits in cells at most 2 apart along each axis (mod nc)
+    c3 = np.stack([cell % nc, (cell // nc) % nc, cell // (nc * nc)], 1)
+    d = s.pos[:, None, :] - s.pos[None, :, :]
+    d -= s.box * np.round(d / s.box)
+    close = (d ** 2).sum(-1) < rc * rc
+    i, j = np.nonzero(close)
+    dc = np.abs(c3[i] - c3[j])
+    dc = np.minimum(dc, nc - dc)
+    assert dc.max() <= 2
+
+
+# ---------------------------------------------------------------- integrator
+def test_velocity_verlet_is_second_order():
+    """Energy error of velocity Verlet shrinks as dt^2 (SI Sec. 1).  Screened
+    Coulomb only, cutoff where erfc(alpha r) < 1e-15 so the force is the exact
+    gradient of the energy."""
+    def run(dt):
+        s = S.random_neutral(6, 10.0, seed=4, dmin=2.5)
+        sigma, rc = O.sigma_of_alpha(1.0), 6.0
+
+        def ff(sys_):
+            F, ec, _ = O.sr_forces(sys_, sigma, rc, vdw=False)
+            return {"F": F, "v_pot": ec.sum()}
+
+        out = ff(s)
+        e0 = out["v_pot"] + O.kinetic_energy(s.vel, s.mass)
+        F = out["F"]
+        err = 0.0
+        for _ in range(int(round(40 / dt))):
+            out = O.velocity_verlet_step(s, F, dt, ff)
+            F = out["F"]
+            err = max(err, abs(out["v_pot"] + O.kinetic_energy(s.vel, s.mass) - e0))
+        assert np.all((s.pos >= 0) & (s.pos < s.box))
+        return err
+
+    e1, e2 = run(2.0), run(1.0)
+    assert 3.0 < e1 / e2 < 5.0
