@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of one P3MaZe molecular-dynamics step on a B300.
+
+Workload (seeded, synthetic): molten NaCl, 32768 ions (16384 Na+, 16384 Cl-)
+in a cubic box L = 100.9 A, uniform random positions with minimum pair
+distance 2 A, Maxwell-Boltzmann velocities at 1200 K, Tosi-Fumi
+Born-Mayer-Huggins short-range term, Ewald alpha 0.30 1/A, r_cut 9 A, 128^3
+mesh, cubic B-spline assignment, constraint tolerance 1e-6, dt 1 fs.
+
+One step = one velocity-Verlet MD step through the whole path: kick/drift,
+cell list, charge assignment, 25 diffusion smoothing steps, Mass-Zero
+prediction and multigrid correction solve to tol, field update, erfc +
+Born-Mayer pair forces, force interpolation, kick.  Inputs are resident on
+the device when the timed region starts; L2 is flushed (256 MiB written)
+before every timed step, outside the step's events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "nacl_32k"
+METRIC = "ns/day, molten NaCl 32768 ions, 128^3 mesh (full MD step with Mass-Zero long-range solve)"
+DATA = "synthetic: seeded molten-NaCl configuration (uniform random, d_min 2 A, 1200 K Maxwell-Boltzmann)"
+
+
+def ns_per_day(sec_per_step: float, dt_fs: float) -> float:
+    return 86400.0 / sec_per_step * dt_fs * 1e-6
+
+
+def workload_config(prm, precision):
+    return {
+        "workload": "molten NaCl, 32768 ions, L=100.9 A, 128^3 mesh, alpha 0.30/A, r_cut 9 A, "
+                    "order-4 B-spline, tol 1e-6, dt 1 fs, NVE",
+        "n_particles": 32768, "mesh": prm["mesh"], "tol": prm["tol"], "dt_fs": prm["dt"],
+        "precision": precision, "l2": "flushed (256 MiB write) before every timed step",
+        "parallelism": "replicas (one independent system per GPU, no collective)",
+    }
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str | None):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu is not None:
+                cmd += ["-i", self.gpu]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- roofline
+def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int) -> tuple[float, int]:
+    """Compulsory bytes of one launch of the stage's main kernel and the
+    launches per step.  b = bytes of a bulk mesh value, P = mesh points."""
+    if stage == "smooth":        # one diffusion step: read P values, write P values
+        return 2.0 * P * b, K
+    if stage == "spread":        # write q once, read 32 B per particle
+        return P * b + 32.0 * npart, 1
+    if stage == "predict":       # read phi^k, phi^{k-1}, q^s, 3 y histories; write sigma_p, y0
+        return P * (8 + 8 + b + 24 + 16), 1
+    if stage == "update":        # read phi^k, phi^{k-1}, y; write phi^{k+1}
+        return P * 32.0, 1
+    if stage == "gather":        # read phi once, 32 B per particle in, 3 x 24 B out
+        return P * 8.0 + 104.0 * npart, 1
+    return float("nan"), 1
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_step_seconds(system, prm, n_sample: int) -> tuple[float, str]:
+    """One oracle force evaluation (full mesh part + short-range part of
+    n_sample particles scaled to all) on one host core; returns the estimated
+    seconds of a full step and a description of the sample."""
+    from threadpoolctl import threadpool_limits
+    from oracle import p3maze_oracle as O
+
+    rng = np.random.default_rng(0)
+    sample = rng.choice(system.n, n_sample, replace=False)
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        mf = O.mesh_fields(system, prm["alpha"], prm["mesh"])
+        O.interpolate_lr_forces(system.pos, system.charge, system.box, prm["mesh"], mf["phi"])
+        t1 = time.perf_counter()
+        O.sr_forces(system, mf["sigma"], prm["r_cut"], subset=sample)
+        t2 = time.perf_counter()
+    est = (t1 - t0) + (t2 - t1) * system.n / n_sample
+    desc = (f"full mesh pipeline on {prm['mesh']}^3 (assignment, {mf['K']} smoothing steps, FFT solve, "
+            f"interpolation) + short-range forces of {n_sample} of {system.n} ions scaled by "
+            f"{system.n / n_sample:g}; 1 thread")
+    return est, desc
+
+
+def cpu_baseline(system, prm, budget_s: float = 12.0) -> dict:
+    times, desc = [], ""
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s or not times:
+        est, desc = oracle_step_seconds(system, prm, 64)
+        times.append(est)
+        if len(times) >= 5:
+            break
+    sec = statistics.median(times)
+    return {"value": ns_per_day(sec, prm["dt"]), "unit": "ns/day", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} estimated steps: {desc}", "sec_per_step": sec}
+
+
+def run_reference(args) -> int:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2606_31379_b300 import synth as S
+    system, prm = S.make_workload(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle_step_seconds(system, prm, 64)
+    times, desc = [], ""
+    for _ in range(args.steps):
+        est, desc = oracle_step_seconds(system, prm, 64)
+        times.append(est)
+    sec = sum(times) / len(times)
+    value = ns_per_day(sec, prm["dt"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA,
+        "config": workload_config(prm, "fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": "ns/day", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {desc}"},
+        "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def time_context(ctx, torch, stream, steps: int, flush):
+    """K timed steps; returns per-step ms list (CUDA events on ctx's stream)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            ctx.step(1)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ours(args) -> int:
+    import torch
+    import torch.distributed as dist
+    from paper_2606_31379_b300 import p3maze as P
+    from paper_2606_31379_b300 import synth as S
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    system, prm = S.make_workload(WORKLOAD)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def make(precision):
+        return P.Context.from_system(system, alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"],
+                                     tol=prm["tol"], dt=prm["dt"], precision=precision,
+                                     stream=stream.cuda_stream)
+
+    ctx = make(args.precision)
+    ctx.step(args.warmup)
+    torch.cuda.synchronize()
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
+    ctx.set_timing(True)
+    it0 = ctx.stats()["total_iters"]
+    barrier()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    with ClockSampler(gpu_id) as clk:
+        ms = time_context(ctx, torch, stream, args.steps, flush)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    barrier()
+    tm = ctx.timing()
+    iters = (ctx.stats()["total_iters"] - it0) / args.steps
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * ns_per_day(ms_per_step * 1e-3, prm["dt"])
+
+    # end to end through the C ABI with pinned host buffers: upload r, v;
+    # one step; download r, v.
+    pos_h = torch.empty((system.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    vel_h = torch.empty((system.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    ctx.positions(out=pos_h)
+    ctx.velocities(out=vel_h)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(pos_h, vel_h)
+        ctx.step(1)
+        ctx.positions(out=pos_h)
+        ctx.velocities(out=vel_h)
+    torch.cuda.synchronize()
+    e2e_sec = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * ns_per_day(e2e_sec, prm["dt"]), "unit": "ns/day",
+           "h2d_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes),
+           "d2h_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes), "steps": e2e_steps}
+    K_smooth = ctx.stats()["smooth_steps"]
+    ctx.close()
+
+    # the plain FP64 path beside it
+    variants = {}
+    if args.precision != "fp64" and not args.no_variants:
+        c64 = make("fp64")
+        c64.step(args.warmup)
+        c64.set_timing(True)
+        it0 = c64.stats()["total_iters"]
+        ms64 = time_context(c64, torch, stream, args.steps, flush)
+        t64 = c64.timing()
+        variants["fp64"] = {
+            "value": world * ns_per_day(sum(ms64) / args.steps * 1e-3, prm["dt"]),
+            "ms_per_step": sum(ms64) / args.steps,
+            "mg_iters_per_step": (c64.stats()["total_iters"] - it0) / args.steps,
+            "stage_us": {k: 1e3 * v / args.steps for k, v in t64["ms"].items()},
+        }
+        c64.close()
+
+    if rank != 0:
+        return 0
+    stage_us = {k: 1e3 * v / args.steps for k, v in tm["ms"].items()}
+    lr_stages = ("spread", "smooth", "predict", "solve", "update", "gather")
+    b = 4 if args.precision == "mixed" else 8
+    P3 = prm["mesh"] ** 3
+    # dominant mesh stage by time
+    mesh_stages = ("smooth", "spread", "predict", "update", "gather")
+    dom = max(mesh_stages, key=lambda k: stage_us[k])
+    peaks = measured_peaks()
+    bytes_per_launch, launches_per_step = algorithmic_bytes(dom, b, P3, system.n, K_smooth)
+    launch_us = stage_us[dom] / launches_per_step
+    achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
+                "launch_us": launch_us}
+    line = {
+        "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": DATA,
+        "config": workload_config(prm, args.precision),
+        "lr_step_us": sum(stage_us[k] for k in lr_stages),
+        "stage_us": stage_us, "mg_iters_per_step": iters,
+        "gpu_launches": int(tm["total_launches"]),
+        "gpu_launches_per_step": tm["total_launches"] / args.steps,
+        "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(system, prm)
+    print(json.dumps(line))
+    return 0
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

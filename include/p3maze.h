@@ -1,0 +1,236 @@
+/*
+ * p3maze.h -- C ABI of the P3MaZe long-range electrostatics library (one GPU).
+ *
+ * P3MaZe (Mass-Zero particle-particle particle-mesh electrostatics) splits the
+ * periodic Coulomb energy into a short-range erfc pair sum, a smooth long-range
+ * mesh part and a Gaussian self term (Eqs. 3-6).  The long-range mesh potential
+ * phi is a zero-inertia auxiliary field: each MD step predicts it by Verlet
+ * (phi_p = 2 phi^k - phi^{k-1}) and enforces the discrete Poisson equation
+ * (h/4pi) M phi + q^s = 0 (Eq. 13) as a holonomic constraint by solving the
+ * correction problem M y = sigma_p (Eqs. 16-17) with multigrid V-cycles until
+ * max|M y - sigma_p| <= tol (Eq. 20), then phi^{k+1} = phi_p - (4pi/h) y
+ * (supporting information Sec. 1, "Numerical integration").
+ *
+ * One step of the library, all on the device:
+ *   kick/drift/wrap (velocity Verlet) -> cell list -> cubic B-spline charge
+ *   assignment q -> K diffusion steps q^s = (I + cM)^K q -> predicted residual
+ *   sigma_p and multiplier guess y0 -> multigrid correction solve -> field
+ *   update -> erfc + Born-Mayer / Lennard-Jones pair forces -> force
+ *   interpolation F = -Q W . D phi (Eq. 21) -> (SPC/Fw bonded terms) -> kick.
+ *
+ * Units: A, fs, g/mol, e, kcal/mol.  Positions are wrapped into [0, L).
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (P3MAZE_OK) or a negative P3MAZE_ERR_* code; the message is
+ *     available from p3maze_last_error(ctx) (or p3maze_last_error(NULL) when
+ *     no context was created).
+ *   - Host pointers are read (or written) during the call only; the caller
+ *     keeps ownership.  The context owns all device memory it allocates.
+ *   - A context is bound to the CUDA stream given at init and to the device
+ *     current at init.  It is not thread safe; use one context per thread.
+ */
+#ifndef P3MAZE_H
+#define P3MAZE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define P3MAZE_OK                  0
+#define P3MAZE_ERR_INVALID        -1  /* bad argument or parameter                      */
+#define P3MAZE_ERR_OOM            -2  /* device allocation failed                       */
+#define P3MAZE_ERR_CUDA           -3  /* a CUDA call failed (message has the CUDA text) */
+#define P3MAZE_ERR_NOT_CONVERGED  -4  /* multigrid reached max_mg_iters above tol       */
+#define P3MAZE_ERR_NONFINITE      -5  /* NaN/Inf in the constraint residual             */
+
+/* ---- enumerations ------------------------------------------------------------ */
+#define P3MAZE_FP64   0   /* every mesh and particle array in FP64                        */
+#define P3MAZE_MIXED  1   /* FP32 assignment, smoothing, multigrid hierarchy and pair math;
+                             FP64 positions, fields phi and y, constraint residual, coarse
+                             solve, neutrality sum and all energy/force accumulation      */
+
+#define P3MAZE_SR_NONE 0  /* Coulomb only                                               */
+#define P3MAZE_SR_BMH  1  /* Born-Huggins-Mayer: A exp((s-r)/rho) - C/r^6 - D/r^8         */
+#define P3MAZE_SR_LJ   2  /* Lennard-Jones: 4 eps ((s/r)^12 - (s/r)^6), pairs with eps=0 skipped */
+
+#define P3MAZE_MAX_TYPES 4
+
+/* Mesh arrays readable with p3maze_get_mesh (N^3 doubles, x fastest:
+ * index (iz*N + iy)*N + ix). */
+#define P3MAZE_MESH_Q      0  /* assigned charge q = A(r)Q at the current positions        */
+#define P3MAZE_MESH_QS     1  /* smoothed charge q^s with its mean removed                 */
+#define P3MAZE_MESH_PHI    2  /* constrained mesh potential phi^k (e/A)                    */
+#define P3MAZE_MESH_Y      3  /* converged correction y* of the last solve                 */
+#define P3MAZE_MESH_SIGMA  4  /* predicted constraint residual sigma_p of the last solve  */
+
+/* Force parts readable with p3maze_get_forces (n*3 doubles, particle-major). */
+#define P3MAZE_F_TOTAL 0
+#define P3MAZE_F_SR    1  /* erfc Coulomb + non-Coulomb pair terms (Eq. 19 + V-bar)        */
+#define P3MAZE_F_LR    2  /* mesh force -Q W . D phi (Eq. 21)                              */
+#define P3MAZE_F_BOND  3  /* SPC/Fw bonds, angles and intramolecular exclusion             */
+
+/* ---- parameter structs ------------------------------------------------------- */
+typedef struct {
+    int32_t kind;                       /* P3MAZE_SR_*                                    */
+    int32_t n_types;                    /* 1..P3MAZE_MAX_TYPES                            */
+    /* Row-major [n_types][n_types] symmetric tables.
+     * BMH: p[0]=A (kcal/mol), p[1]=rho (A), p[2]=s (A), p[3]=C (kcal/mol A^6),
+     *      p[4]=D (kcal/mol A^8).   LJ: p[0]=eps (kcal/mol), p[1]=sigma (A).        */
+    double p[5][P3MAZE_MAX_TYPES * P3MAZE_MAX_TYPES];
+} p3maze_sr_table;
+
+typedef struct {
+    /* Rigid-topology water-like molecules (SPC/Fw, Table S1): each molecule is a
+     * triple (h1, o, h2) of particle indices, every particle in at most one
+     * triple.  Bonds o-h1, o-h2: (kb/2)(r-r0)^2; angle h1-o-h2: (ka/2)(t-t0)^2.
+     * The three intramolecular pairs are left out of the short-range Coulomb sum
+     * and their mesh part ke Q Q erf(r/(sqrt2 sigma))/r is subtracted.            */
+    int32_t n_molecules;
+    const int32_t *triples;             /* host, [n_molecules][3]                        */
+    double kb, r0, ka, theta0;          /* kcal/mol/A^2, A, kcal/mol/rad^2, rad          */
+} p3maze_topology;
+
+typedef struct {
+    double box[3];          /* cubic: |box[i]-box[0]| <= 1e-12 box[0], else INVALID       */
+    int32_t n_particles;    /* >= 1                                                        */
+    const double *charges;  /* host [n] e; total charge |sum Q| <= 1e-9 sum|Q| else INVALID */
+    const double *masses;   /* host [n] g/mol, > 0                                         */
+    const int32_t *types;   /* host [n] species index < sr->n_types (may be NULL if no sr) */
+    double alpha;           /* Ewald splitting, 1/A; sigma = 1/(sqrt(2) alpha) (Eq. 5)     */
+    double r_cut;           /* real-space cutoff, A; need r_cut <= L                        */
+    int32_t mesh;           /* N points per axis, N = m 2^l with 2 <= m <= 8 and N >= 4     */
+    int32_t order;          /* assignment order; 4 (cubic B-spline) is the only one         */
+    double tol;             /* max-norm tolerance of M y - sigma_p, e per mesh point (> 0)  */
+    double dt;              /* time step, fs                                                */
+    int32_t predictor;      /* multiplier guess y0: 1 -> y^k, 2 -> 2y^k - y^{k-1},
+                               3 -> 3y^k - 3y^{k-1} + y^{k-2} (Sec. 3.3); 0 -> 3           */
+    int32_t precision;      /* P3MAZE_FP64 or P3MAZE_MIXED                                  */
+    int32_t max_mg_iters;   /* V-cycle cap per step; 0 -> 50                                */
+    int32_t pre_sweeps;     /* red-black Gauss-Seidel sweeps before restriction; 0 -> 2    */
+    int32_t post_sweeps;    /* sweeps after prolongation; 0 -> 2                            */
+    double coulomb_k;       /* kcal A/(mol e^2); 0 -> 332.0637                              */
+    const p3maze_sr_table *sr;      /* may be NULL: Coulomb only                           */
+    const p3maze_topology *topology;/* may be NULL                                         */
+} p3maze_params;
+
+typedef struct {
+    double v_sr;        /* erfc pair energy (Eq. 5)                                        */
+    double v_lr;        /* 1/2 phi^T q with q the assigned (unsmoothed) charge             */
+    double v_self;      /* -(1/(sqrt(2 pi) sigma)) sum Q^2 (Eq. 6)                          */
+    double v_excl;      /* minus the mesh part of intramolecular pairs                     */
+    double v_vdw;       /* non-Coulomb pair energy                                         */
+    double v_bond;      /* bonds + angles                                                  */
+    double kinetic;
+    double total;
+} p3maze_energies;
+
+typedef struct {
+    int32_t last_iters;         /* V-cycles of the last constraint solve                  */
+    double last_residual;       /* max|M y - sigma_p| after it                            */
+    int64_t steps;              /* MD steps taken since init                               */
+    int64_t total_iters;        /* V-cycles summed over those steps                        */
+    int32_t init_iters;         /* V-cycles of the initial full solve                      */
+    int32_t smooth_steps;       /* K                                                       */
+    double smooth_coeff;        /* c                                                       */
+    int32_t mg_levels;          /* multigrid levels including the coarsest                 */
+    int32_t coarse_n;           /* points per axis of the coarsest level                  */
+    int32_t cells_per_axis;     /* cell-list grid                                          */
+    double sigma;               /* Gaussian width, A                                       */
+} p3maze_stats;
+
+/* Pipeline stages timed by p3maze_set_timing / p3maze_get_timing. */
+#define P3MAZE_ST_INTEGRATE 0  /* kick + drift + wrap, final kick                          */
+#define P3MAZE_ST_CELLS     1  /* cell list and cell-ordered copies                        */
+#define P3MAZE_ST_SPREAD    2  /* B-spline charge assignment                               */
+#define P3MAZE_ST_SMOOTH    3  /* K diffusion steps                                        */
+#define P3MAZE_ST_PREDICT   4  /* neutrality sum, sigma_p and y0                           */
+#define P3MAZE_ST_SOLVE     5  /* residual tests and V-cycles (includes the host waits of
+                                  the convergence test)                                    */
+#define P3MAZE_ST_UPDATE    6  /* phi update                                               */
+#define P3MAZE_ST_PAIR      7  /* short-range pair forces                                  */
+#define P3MAZE_ST_GATHER    8  /* force interpolation and bonded terms                     */
+#define P3MAZE_NSTAGES      9
+
+typedef struct {
+    double ms[P3MAZE_NSTAGES];        /* summed device time per stage (timing enabled)   */
+    int64_t launches[P3MAZE_NSTAGES]; /* kernels launched per stage (always counted)     */
+    int64_t timed_steps;              /* steps covered by ms                             */
+    int64_t total_launches;           /* all kernels launched since init or reset        */
+} p3maze_timing;
+
+typedef struct p3maze_ctx p3maze_ctx;
+
+/* ---- lifecycle ------------------------------------------------------------- */
+
+/* Validate parameters, allocate device state on the current device, upload
+ * pos/vel (host [n][3] A and A/fs; vel may be NULL for zero), wrap positions
+ * into the box, and initialise the field by a full constraint solve from
+ * phi = 0 (phi^{-1} = phi^0, empty multiplier history), then compute F^0.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID (parameters), OOM, CUDA, NOT_CONVERGED (initial solve).      */
+int p3maze_init(const p3maze_params *params, const double *pos, const double *vel,
+                void *cuda_stream, p3maze_ctx **out);
+
+/* Advance nsteps velocity-Verlet steps (Sec. 2; supporting information Sec. 1).
+ * Synchronises with the stream once per multigrid iteration to test
+ * convergence.  On NOT_CONVERGED or NONFINITE the step that failed is left
+ * applied and the error returned; the context can be re-initialised with
+ * p3maze_reinit.                                                                 */
+int p3maze_step(p3maze_ctx *ctx, int32_t nsteps);
+
+/* Full constraint solve from phi = 0 at the current positions and new forces:
+ * the same initialisation as p3maze_init (after an external state change).   */
+int p3maze_reinit(p3maze_ctx *ctx);
+
+/* Free everything the context owns.  NULL is ignored.                          */
+void p3maze_destroy(p3maze_ctx *ctx);
+
+/* ---- observables (synchronise the context's stream) ------------------------- */
+
+/* Energy terms of Eq. 4 at the current state (kcal/mol).                        */
+int p3maze_energy(p3maze_ctx *ctx, p3maze_energies *out);
+
+/* Statistics of the solver.                                                   */
+int p3maze_get_stats(p3maze_ctx *ctx, p3maze_stats *out);
+
+/* Copy particle arrays to host [n][3] (original particle order).              */
+int p3maze_get_positions(p3maze_ctx *ctx, double *out);
+int p3maze_get_velocities(p3maze_ctx *ctx, double *out);
+/* which = P3MAZE_F_*                                                           */
+int p3maze_get_forces(p3maze_ctx *ctx, int32_t which, double *out);
+
+/* Copy positions and velocities in from host [n][3] as the continuing state:
+ * forces and field histories are kept (use after a host round trip of the
+ * same state, or call p3maze_reinit after an arbitrary change).  Positions
+ * are wrapped into the box.                                                    */
+int p3maze_set_state(p3maze_ctx *ctx, const double *pos, const double *vel);
+
+/* Copy a mesh array (P3MAZE_MESH_*) to host, N^3 doubles.                      */
+int p3maze_get_mesh(p3maze_ctx *ctx, int32_t which, double *out);
+
+/* The cell list of the last force evaluation: cell index of every particle
+ * ((cz*nc + cy)*nc + cx, x fastest, c = min(floor(r nc/L), nc-1)), start
+ * offsets [nc^3 + 1] and the particle order sorted by (cell, index).  Any
+ * pointer may be NULL.  nc = floor(L / (r_cut/2)).                            */
+int p3maze_get_cells(p3maze_ctx *ctx, int32_t *cell_of, int32_t *cell_start, int32_t *order);
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing of p3maze_step and
+ * reset the timing and launch counters.  Timing adds two event records per
+ * stage per step on the context's stream.                                     */
+int p3maze_set_timing(p3maze_ctx *ctx, int32_t enable);
+
+/* Per-stage device time and kernel-launch counts since the last reset.       */
+int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
+
+/* Message of the last failing call on ctx (or of the last failing init when
+ * ctx is NULL).  Never NULL.                                                   */
+const char *p3maze_last_error(const p3maze_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P3MAZE_H */

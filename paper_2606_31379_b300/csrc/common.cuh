@@ -1,0 +1,86 @@
+// Shared device helpers and constants of the P3MaZe CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define P3_THREADS 256
+
+// Unit conversion: (kcal/mol/A) / (g/mol) -> A/fs^2.
+#define P3_ACCEL 4.184e-4
+// Default Coulomb constant, kcal A / (mol e^2).
+#define P3_COULOMB_K 332.0637
+
+namespace p3 {
+
+// Cell-ordered particle record (x, y, z, Q): one 32-byte aligned load.
+struct __align__(32) PQ {
+    double x, y, z, w;
+};
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
+
+// Periodic wrap of an index known to lie in [-n, 2n).
+__device__ __forceinline__ int wrap_idx(int i, int n) {
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Cubic (order-4) B-spline weights of the nodes floor(u)-1 .. floor(u)+2 for a
+// fractional offset t = u - floor(u) (charge assignment, Sec. 2).
+__device__ __forceinline__ void bspline4(double t, double w[4]) {
+    const double s = 1.0 - t;
+    const double t2 = t * t, t3 = t2 * t;
+    w[0] = s * s * s * (1.0 / 6.0);
+    w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) * (1.0 / 6.0);
+    w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) * (1.0 / 6.0);
+    w[3] = t3 * (1.0 / 6.0);
+}
+
+// Base node (floor(u) - 1, wrapped into [0, n)) and weights along one axis.
+__device__ __forceinline__ int bspline_axis(double x, double inv_h, int n, double w[4]) {
+    const double u = x * inv_h;
+    const double f = floor(u);
+    bspline4(u - f, w);
+    int b = (int)f - 1;
+    return b < 0 ? b + n : (b >= n ? b - n : b);
+}
+
+// Block-wide sum of a double (all threads get the result).
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) sh[0] = v;
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) sh[0] = v;
+    __syncthreads();
+    v = sh[0];
+    __syncthreads();
+    return v;
+}
+
+}  // namespace p3

@@ -1,0 +1,856 @@
+// C ABI of the P3MaZe CUDA library: context set-up, the per-step pipeline
+// and the observables.  See include/p3maze.h for the contract of each call.
+#include "p3maze.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mesh.cuh"
+#include "particles.cuh"
+
+using namespace p3;
+
+namespace {
+
+thread_local std::string g_init_error = "no error";
+
+constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
+
+// Device scalar slots.
+enum { S_QSUM = 0, S_ESR, S_EVDW, S_VLR, S_MV2, S_EBOND, S_EXCL, S_NSCAL };
+
+struct Level {
+    int n = 0;
+    int64_t pts = 0;
+    void* e = nullptr;
+    void* b = nullptr;
+    void* r = nullptr;
+};
+
+inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
+
+}  // namespace
+
+struct p3maze_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // parameters
+    int np = 0, N = 0, nc = 0, ncell = 0, prec = 0, pred = 3, itmax = 50, nu1 = 2, nu2 = 2, K = 0;
+    int nmol = 0, nlev = 0;
+    int64_t P = 0;
+    double L = 0, h = 0, inv_h = 0, alpha = 0, sigma = 0, rc = 0, c = 0, tol = 0, dt = 0, ke = 0;
+    double inv_cell = 0, v_self = 0;
+    SRTable tab{};
+    double kb = 0, r0 = 0, ka = 0, th0 = 0;
+    // particle arrays (original order)
+    double *r = nullptr, *v = nullptr, *F = nullptr, *Fsr = nullptr, *Flr = nullptr, *Fb = nullptr;
+    double *hdt_acc = nullptr, *mass = nullptr, *Q = nullptr;
+    int *type = nullptr, *mol = nullptr, *tri = nullptr;
+    // cell list and cell-ordered copies
+    int *cell = nullptr, *count = nullptr, *start = nullptr, *fill = nullptr, *order = nullptr;
+    int *ts = nullptr, *ms = nullptr, *cs = nullptr;
+    PQ* xq = nullptr;
+    double *Fs = nullptr, *ecs = nullptr, *evs = nullptr, *eb = nullptr, *ex = nullptr;
+    // mesh
+    void *q = nullptr, *qs = nullptr;
+    double* phi[2] = {nullptr, nullptr};
+    int icur = 0;                      // phi[icur] = phi^k, phi[1-icur] = phi^{k-1}
+    double* yh[4] = {nullptr, nullptr, nullptr, nullptr};  // [0] work, [1..3] y^k, y^{k-1}, y^{k-2}
+    int nhist = 0;
+    double* sig = nullptr;
+    std::vector<Level> lev;
+    double* gcoarse = nullptr;
+    // reductions
+    double* partial = nullptr;
+    double* dscal = nullptr;
+    unsigned long long* dres = nullptr;
+    double* hscal = nullptr;
+    unsigned long long* hres = nullptr;
+    p3maze_stats st{};
+    // timing and launch accounting
+    bool timing = false;
+    cudaEvent_t ev[P3MAZE_NSTAGES][2] = {};
+    bool pending[P3MAZE_NSTAGES] = {};
+    double stage_ms[P3MAZE_NSTAGES] = {};
+    int64_t launches[P3MAZE_NSTAGES] = {};
+    int64_t timed_steps = 0;
+    std::vector<void*> allocs;
+    std::string err = "no error";
+};
+
+namespace {
+
+int fail(p3maze_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, P3MAZE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                                 \
+    do {                                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                                  \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, P3MAZE_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename P>
+int dalloc(p3maze_ctx* ctx, P** p, size_t bytes) {
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, P3MAZE_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                                             cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(d);
+    *p = (P*)d;
+    return P3MAZE_OK;
+}
+
+#define ALLOC(ptr, bytes)                                  \
+    do {                                                   \
+        int rc_ = dalloc(ctx, &(ptr), (size_t)(bytes));    \
+        if (rc_) return rc_;                               \
+    } while (0)
+
+// Count `k` kernel launches of stage `st`.
+inline void count(p3maze_ctx* ctx, int st, int k = 1) { ctx->launches[st] += k; }
+
+void stage_begin(p3maze_ctx* ctx, int st) {
+    if (ctx->timing) cudaEventRecord(ctx->ev[st][0], ctx->stream);
+}
+
+void stage_end(p3maze_ctx* ctx, int st) {
+    if (ctx->timing) {
+        cudaEventRecord(ctx->ev[st][1], ctx->stream);
+        ctx->pending[st] = true;
+    }
+}
+
+// Fold the elapsed time of every stage recorded this step into the totals.
+int collect_timing(p3maze_ctx* ctx) {
+    if (!ctx->timing) return P3MAZE_OK;
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+        if (!ctx->pending[st]) continue;
+        CK(cudaEventSynchronize(ctx->ev[st][1]));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ctx->ev[st][0], ctx->ev[st][1]));
+        ctx->stage_ms[st] += t;
+        ctx->pending[st] = false;
+    }
+    ctx->timed_steps += 1;
+    return P3MAZE_OK;
+}
+
+// Pseudo-inverse kernel of the periodic 7-point operator on an n^3 mesh:
+// g(d) = n^-3 sum_{k != 0} cos(2 pi k.d / n) / lambda(k),
+// lambda(k) = -4 sum_axes sin^2(pi k_axis / n).
+std::vector<double> coarse_green(int n) {
+    const int m = n * n * n;
+    std::vector<double> s2(n), g(m, 0.0);
+    for (int k = 0; k < n; ++k) {
+        const double s = std::sin(kPi * k / n);
+        s2[k] = s * s;
+    }
+    for (int dz = 0; dz < n; ++dz)
+        for (int dy = 0; dy < n; ++dy)
+            for (int dx = 0; dx < n; ++dx) {
+                double acc = 0.0;
+                for (int kz = 0; kz < n; ++kz)
+                    for (int ky = 0; ky < n; ++ky)
+                        for (int kx = 0; kx < n; ++kx) {
+                            if (!kx && !ky && !kz) continue;
+                            const double lam = -4.0 * (s2[kx] + s2[ky] + s2[kz]);
+                            acc += std::cos(2.0 * kPi * (double)(kx * dx + ky * dy + kz * dz) / n) / lam;
+                        }
+                g[(dz * n + dy) * n + dx] = acc / m;
+            }
+    return g;
+}
+
+// ------------------------------------------------------------------ pipeline
+int build_cells(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    stage_begin(ctx, P3MAZE_ST_CELLS);
+    CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * ctx->ncell, s));
+    k_cell_count<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->cell, ctx->count);
+    k_scan_cells<<<1, 1024, 0, s>>>(ctx->ncell, ctx->count, ctx->start, ctx->fill);
+    k_cell_scatter<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->cell, ctx->start, ctx->fill, ctx->order);
+    k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
+    k_gather_sorted<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->order, ctx->r, ctx->Q, ctx->type, ctx->mol,
+                                                         ctx->cell, ctx->xq, ctx->ts, ctx->ms, ctx->cs);
+    CKL();
+    count(ctx, P3MAZE_ST_CELLS, 5);
+    stage_end(ctx, P3MAZE_ST_CELLS);
+    return P3MAZE_OK;
+}
+
+template <typename T>
+int spread_smooth(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    stage_begin(ctx, P3MAZE_ST_SPREAD);
+    CK(cudaMemsetAsync(ctx->q, 0, sizeof(T) * ctx->P, s));
+    k_spread<T><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->N, ctx->inv_h, (T*)ctx->q);
+    count(ctx, P3MAZE_ST_SPREAD);
+    stage_end(ctx, P3MAZE_ST_SPREAD);
+    stage_begin(ctx, P3MAZE_ST_SMOOTH);
+    if (ctx->K == 0) {
+        CK(cudaMemcpyAsync(ctx->qs, ctx->q, sizeof(T) * ctx->P, cudaMemcpyDeviceToDevice, s));
+    } else {
+        T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
+        const T* src = (const T*)ctx->q;
+        for (int k = 0; k < ctx->K; ++k) {
+            T* dst = (k == ctx->K - 1) ? (T*)ctx->qs : tmp[k & 1];
+            k_diffuse<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->N, src, dst, (T)ctx->c);
+            src = dst;
+        }
+        count(ctx, P3MAZE_ST_SMOOTH, ctx->K);
+    }
+    CKL();
+    stage_end(ctx, P3MAZE_ST_SMOOTH);
+    return P3MAZE_OK;
+}
+
+template <typename T>
+int vcycle(p3maze_ctx* ctx, int l) {
+    cudaStream_t s = ctx->stream;
+    Level& L = ctx->lev[l];
+    T* e = (T*)L.e;
+    T* b = (T*)L.b;
+    if (l == ctx->nlev - 1) {
+        k_coarse_solve<T><<<1, 512, 0, s>>>(L.n, ctx->gcoarse, b, e);
+        count(ctx, P3MAZE_ST_SOLVE);
+        CKL();
+        return P3MAZE_OK;
+    }
+    Level& C = ctx->lev[l + 1];
+    const unsigned gh = nblk(L.pts / 2);
+    CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
+    for (int it = 0; it < ctx->nu1; ++it) {
+        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 0);
+        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 1);
+    }
+    k_resid<T><<<nblk(L.pts), P3_THREADS, 0, s>>>(L.n, e, b, (T*)L.r);
+    k_restrict<T><<<nblk(C.pts), P3_THREADS, 0, s>>>(C.n, (const T*)L.r, (T*)C.b);
+    count(ctx, P3MAZE_ST_SOLVE, 2 * ctx->nu1 + 2);
+    CKL();
+    int rc = vcycle<T>(ctx, l + 1);
+    if (rc) return rc;
+    k_prolong_add<T><<<nblk(L.pts), P3_THREADS, 0, s>>>(L.n, (const T*)C.e, e);
+    for (int it = 0; it < ctx->nu2; ++it) {
+        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 1);
+        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 0);
+    }
+    count(ctx, P3MAZE_ST_SOLVE, 1 + 2 * ctx->nu2);
+    CKL();
+    return P3MAZE_OK;
+}
+
+// Verlet prediction, constraint residual, multigrid correction to tol and the
+// field update (Eqs. 16-17, 20; supporting information Sec. 1).
+template <typename T>
+int solve_field(p3maze_ctx* ctx, int pred_order, int* iters) {
+    cudaStream_t s = ctx->stream;
+    const double hc = ctx->h / (4.0 * kPi);
+    double* phik = ctx->phi[ctx->icur];
+    double* phikm1 = ctx->phi[1 - ctx->icur];
+    stage_begin(ctx, P3MAZE_ST_PREDICT);
+    k_sum_partial<T><<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->P, (const T*)ctx->qs, ctx->partial);
+    k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_QSUM);
+    k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->N, phik, phikm1, (const T*)ctx->qs, ctx->dscal + S_QSUM,
+                                                     1.0 / (double)ctx->P, hc, ctx->yh[1], ctx->yh[2], ctx->yh[3],
+                                                     pred_order, ctx->sig, ctx->yh[0]);
+    CKL();
+    count(ctx, P3MAZE_ST_PREDICT, 3);
+    stage_end(ctx, P3MAZE_ST_PREDICT);
+    stage_begin(ctx, P3MAZE_ST_SOLVE);
+    int it = 0;
+    double res = 0.0;
+    for (;;) {
+        CK(cudaMemsetAsync(ctx->dres, 0, sizeof(unsigned long long), s));
+        k_resid_fine<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->dres);
+        count(ctx, P3MAZE_ST_SOLVE);
+        CKL();
+        CK(cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        unsigned long long bits = *ctx->hres;
+        std::memcpy(&res, &bits, sizeof(double));
+        ctx->st.last_residual = res;
+        ctx->st.last_iters = it;
+        *iters = it;
+        if (!(res <= 1e308))
+            return fail(ctx, P3MAZE_ERR_NONFINITE, "non-finite constraint residual");
+        if (res <= ctx->tol) break;
+        if (it >= ctx->itmax) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "multigrid did not reach tol %.3g in %d V-cycles (residual %.3g)",
+                          ctx->tol, it, res);
+            return fail(ctx, P3MAZE_ERR_NOT_CONVERGED, buf);
+        }
+        int rc = vcycle<T>(ctx, 0);
+        if (rc) return rc;
+        k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->yh[0], (const T*)ctx->lev[0].e);
+        count(ctx, P3MAZE_ST_SOLVE);
+        CKL();
+        ++it;
+    }
+    stage_end(ctx, P3MAZE_ST_SOLVE);
+    stage_begin(ctx, P3MAZE_ST_UPDATE);
+    k_update<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, phik, phikm1, ctx->yh[0], 4.0 * kPi / ctx->h);
+    count(ctx, P3MAZE_ST_UPDATE);
+    stage_end(ctx, P3MAZE_ST_UPDATE);
+    CKL();
+    ctx->icur = 1 - ctx->icur;
+    return P3MAZE_OK;
+}
+
+int forces(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    const double rc2 = ctx->rc * ctx->rc;
+    const double halfL2 = 0.25 * ctx->L * ctx->L;
+    const bool mixed = ctx->prec == P3MAZE_MIXED;
+    stage_begin(ctx, P3MAZE_ST_PAIR);
+#define PAIR(KIND, MIX)                                                                              \
+    k_pair<KIND, MIX><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->ts, ctx->ms, ctx->cs, \
+        ctx->start, ctx->nc, ctx->L, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab, ctx->Fs, ctx->ecs, ctx->evs)
+    switch (ctx->tab.kind * 2 + (mixed ? 1 : 0)) {
+        case 0: PAIR(0, false); break;
+        case 1: PAIR(0, true); break;
+        case 2: PAIR(1, false); break;
+        case 3: PAIR(1, true); break;
+        case 4: PAIR(2, false); break;
+        default: PAIR(2, true); break;
+    }
+#undef PAIR
+    count(ctx, P3MAZE_ST_PAIR);
+    stage_end(ctx, P3MAZE_ST_PAIR);
+    stage_begin(ctx, P3MAZE_ST_GATHER);
+    k_gather<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h, ctx->ke,
+                                                  ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
+    if (ctx->nmol)
+        k_water<<<nblk(ctx->nmol), P3_THREADS, 0, s>>>(ctx->nmol, ctx->tri, ctx->r, ctx->Q, ctx->L, ctx->alpha, ctx->ke,
+                                                      ctx->kb, ctx->r0, ctx->ka, ctx->th0, ctx->F, ctx->Fb, ctx->eb,
+                                                      ctx->ex);
+    count(ctx, P3MAZE_ST_GATHER, ctx->nmol ? 2 : 1);
+    stage_end(ctx, P3MAZE_ST_GATHER);
+    CKL();
+    return P3MAZE_OK;
+}
+
+template <typename T>
+int mesh_pipeline(p3maze_ctx* ctx, int pred_order, int* iters) {
+    int rc = spread_smooth<T>(ctx);
+    if (rc) return rc;
+    return solve_field<T>(ctx, pred_order, iters);
+}
+
+int field_and_forces(p3maze_ctx* ctx, int pred_order, int* iters) {
+    int rc = build_cells(ctx);
+    if (rc) return rc;
+    rc = ctx->prec == P3MAZE_MIXED ? mesh_pipeline<float>(ctx, pred_order, iters)
+                                   : mesh_pipeline<double>(ctx, pred_order, iters);
+    if (rc) return rc;
+    return forces(ctx);
+}
+
+// Full solve from phi = 0 at the current positions (phi^{-1} = phi^0, empty
+// multiplier history) and the forces there.
+int initialise_field(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    const size_t mb = sizeof(double) * ctx->P;
+    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(ctx->phi[k], 0, mb, s));
+    for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(ctx->yh[k], 0, mb, s));
+    ctx->nhist = 0;
+    int it = 0;
+    int rc = field_and_forces(ctx, 0, &it);
+    ctx->st.init_iters = it;
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->phi[1 - ctx->icur], ctx->phi[ctx->icur], mb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(ctx->yh[0], 0, mb, s));
+    return P3MAZE_OK;
+}
+
+int step_once(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    stage_begin(ctx, P3MAZE_ST_INTEGRATE);
+    k_kick_drift<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->F, ctx->hdt_acc, ctx->dt, ctx->L);
+    count(ctx, P3MAZE_ST_INTEGRATE);
+    CKL();
+    int it = 0;
+    const int order = std::min(ctx->pred, ctx->nhist);
+    int rc = field_and_forces(ctx, order, &it);
+    if (rc) return rc;
+    // the converged correction becomes y^{k+1}; the oldest history buffer is reused
+    double* oldest = ctx->yh[3];
+    ctx->yh[3] = ctx->yh[2];
+    ctx->yh[2] = ctx->yh[1];
+    ctx->yh[1] = ctx->yh[0];
+    ctx->yh[0] = oldest;
+    ctx->nhist = std::min(ctx->nhist + 1, 3);
+    k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
+    count(ctx, P3MAZE_ST_INTEGRATE);
+    stage_end(ctx, P3MAZE_ST_INTEGRATE);
+    CKL();
+    ctx->st.steps += 1;
+    ctx->st.total_iters += it;
+    return collect_timing(ctx);
+}
+
+int validate_mesh(int N, int* nlev, int* ncoarse) {
+    if (N < 4) return 0;
+    int n = N, l = 1;
+    while (n > 4 && (n % 2) == 0) {
+        n /= 2;
+        ++l;
+    }
+    if (n > 8) return 0;
+    *nlev = l;
+    *ncoarse = n;
+    return 1;
+}
+
+void release(p3maze_ctx* ctx) {
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st)
+        for (int k = 0; k < 2; ++k)
+            if (ctx->ev[st][k]) cudaEventDestroy(ctx->ev[st][k]);
+    for (void* p : ctx->allocs) cudaFree(p);
+    ctx->allocs.clear();
+    if (ctx->hscal) cudaFreeHost(ctx->hscal);
+    if (ctx->hres) cudaFreeHost(ctx->hres);
+    ctx->hscal = nullptr;
+    ctx->hres = nullptr;
+}
+
+int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const double* vel) {
+    const int n = p->n_particles;
+    const bool mixed = p->precision == P3MAZE_MIXED;
+    const size_t tb = mixed ? sizeof(float) : sizeof(double);
+    CK(cudaGetDevice(&ctx->device));
+    // particle arrays
+    ALLOC(ctx->r, 24 * (size_t)n);
+    ALLOC(ctx->v, 24 * (size_t)n);
+    ALLOC(ctx->F, 24 * (size_t)n);
+    ALLOC(ctx->Fsr, 24 * (size_t)n);
+    ALLOC(ctx->Flr, 24 * (size_t)n);
+    ALLOC(ctx->Fb, 24 * (size_t)n);
+    ALLOC(ctx->hdt_acc, 8 * (size_t)n);
+    ALLOC(ctx->mass, 8 * (size_t)n);
+    ALLOC(ctx->Q, 8 * (size_t)n);
+    ALLOC(ctx->cell, 4 * (size_t)n);
+    ALLOC(ctx->order, 4 * (size_t)n);
+    ALLOC(ctx->ts, 4 * (size_t)n);
+    ALLOC(ctx->ms, 4 * (size_t)n);
+    ALLOC(ctx->cs, 4 * (size_t)n);
+    ALLOC(ctx->xq, sizeof(PQ) * (size_t)n);
+    ALLOC(ctx->Fs, 24 * (size_t)n);
+    ALLOC(ctx->ecs, 8 * (size_t)n);
+    ALLOC(ctx->evs, 8 * (size_t)n);
+    ALLOC(ctx->count, 4 * (size_t)ctx->ncell);
+    ALLOC(ctx->fill, 4 * (size_t)ctx->ncell);
+    ALLOC(ctx->start, 4 * ((size_t)ctx->ncell + 1));
+    if (p->types) ALLOC(ctx->type, 4 * (size_t)n);
+    // mesh arrays
+    const int64_t P = ctx->P;
+    ALLOC(ctx->q, tb * P);
+    ALLOC(ctx->qs, tb * P);
+    for (int k = 0; k < 2; ++k) ALLOC(ctx->phi[k], 8 * P);
+    for (int k = 0; k < 4; ++k) ALLOC(ctx->yh[k], 8 * P);
+    ALLOC(ctx->sig, 8 * P);
+    ctx->lev.resize(ctx->nlev);
+    int nn = ctx->N;
+    for (int l = 0; l < ctx->nlev; ++l) {
+        Level& L = ctx->lev[l];
+        L.n = nn;
+        L.pts = (int64_t)nn * nn * nn;
+        ALLOC(L.e, tb * L.pts);
+        ALLOC(L.b, tb * L.pts);
+        if (l < ctx->nlev - 1 || l == 0) ALLOC(L.r, tb * L.pts);
+        nn /= 2;
+    }
+    std::vector<double> g = coarse_green(ctx->lev.back().n);
+    ALLOC(ctx->gcoarse, 8 * g.size());
+    ALLOC(ctx->partial, 8 * 1024);
+    ALLOC(ctx->dscal, 8 * S_NSCAL);
+    ALLOC(ctx->dres, 8);
+    {
+        cudaError_t e1 = cudaMallocHost((void**)&ctx->hscal, 8 * S_NSCAL);
+        cudaError_t e2 = cudaMallocHost((void**)&ctx->hres, 8);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ctx, P3MAZE_ERR_OOM, "cudaMallocHost failed");
+    }
+    cudaStream_t s = ctx->stream;
+    // host-side derived arrays
+    std::vector<double> hacc(n);
+    for (int i = 0; i < n; ++i) hacc[i] = 0.5 * ctx->dt * P3_ACCEL / p->masses[i];
+    CK(cudaMemcpyAsync(ctx->gcoarse, g.data(), 8 * g.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->hdt_acc, hacc.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->mass, p->masses, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->Q, p->charges, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    if (p->types) CK(cudaMemcpyAsync(ctx->type, p->types, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->r, pos, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
+    if (vel) CK(cudaMemcpyAsync(ctx->v, vel, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
+    else CK(cudaMemsetAsync(ctx->v, 0, 24 * (size_t)n, s));
+    CK(cudaMemsetAsync(ctx->Fb, 0, 24 * (size_t)n, s));
+    CK(cudaMemsetAsync(ctx->dscal, 0, 8 * S_NSCAL, s));
+    if (ctx->nmol) {
+        const p3maze_topology* tp = p->topology;
+        std::vector<int> mol(n, -1);
+        for (int m = 0; m < ctx->nmol; ++m)
+            for (int a = 0; a < 3; ++a) mol[tp->triples[3 * m + a]] = m;
+        ALLOC(ctx->mol, 4 * (size_t)n);
+        ALLOC(ctx->tri, 12 * (size_t)ctx->nmol);
+        ALLOC(ctx->eb, 8 * (size_t)ctx->nmol);
+        ALLOC(ctx->ex, 8 * (size_t)ctx->nmol);
+        CK(cudaMemcpyAsync(ctx->mol, mol.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->tri, tp->triples, 12 * (size_t)ctx->nmol, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // host vectors go out of scope
+    }
+    k_wrap<<<nblk(3 * (int64_t)n), P3_THREADS, 0, s>>>(n, ctx->r, ctx->L);
+    CKL();
+    CK(cudaStreamSynchronize(s));
+    return P3MAZE_OK;
+}
+
+int sync_scalars(p3maze_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->hscal, ctx->dscal, 8 * S_NSCAL, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return P3MAZE_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, void* cuda_stream,
+                p3maze_ctx** out) {
+    if (!out) return fail(nullptr, P3MAZE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!p || !pos) return fail(nullptr, P3MAZE_ERR_INVALID, "params or pos is NULL");
+    const int n = p->n_particles;
+    if (n < 1) return fail(nullptr, P3MAZE_ERR_INVALID, "n_particles must be >= 1");
+    if (!p->charges || !p->masses) return fail(nullptr, P3MAZE_ERR_INVALID, "charges and masses are required");
+    const double L = p->box[0];
+    if (!(L > 0.0) || std::fabs(p->box[1] - L) > 1e-12 * L || std::fabs(p->box[2] - L) > 1e-12 * L)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "box must be cubic and positive");
+    if (!(p->alpha > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "alpha must be > 0");
+    if (!(p->r_cut > 0.0) || p->r_cut > L) return fail(nullptr, P3MAZE_ERR_INVALID, "need 0 < r_cut <= L");
+    if (p->order != 4) return fail(nullptr, P3MAZE_ERR_INVALID, "only order 4 (cubic B-spline) is supported");
+    if (!(p->tol > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "tol must be > 0");
+    if (!(p->dt >= 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "dt must be >= 0");
+    if (p->predictor < 0 || p->predictor > 3) return fail(nullptr, P3MAZE_ERR_INVALID, "predictor must be 0..3");
+    if (p->precision != P3MAZE_FP64 && p->precision != P3MAZE_MIXED)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "precision must be P3MAZE_FP64 or P3MAZE_MIXED");
+    if (p->max_mg_iters < 0 || p->pre_sweeps < 0 || p->post_sweeps < 0)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "iteration counts must be >= 0");
+    int nlev = 0, ncoarse = 0;
+    if (!validate_mesh(p->mesh, &nlev, &ncoarse))
+        return fail(nullptr, P3MAZE_ERR_INVALID, "mesh must be N >= 4 with N = m 2^l, m <= 8");
+    double qsum = 0.0, qabs = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(p->masses[i] > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "masses must be > 0");
+        if (!std::isfinite(p->charges[i])) return fail(nullptr, P3MAZE_ERR_INVALID, "non-finite charge");
+        qsum += p->charges[i];
+        qabs += std::fabs(p->charges[i]);
+    }
+    if (std::fabs(qsum) > 1e-9 * std::max(qabs, 1e-300))
+        return fail(nullptr, P3MAZE_ERR_INVALID, "system is not neutral (|sum Q| > 1e-9 sum |Q|)");
+    for (int i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
+            return fail(nullptr, P3MAZE_ERR_INVALID, "non-finite position or velocity");
+    SRTable tab{};
+    if (p->sr && p->sr->kind != P3MAZE_SR_NONE) {
+        const p3maze_sr_table* t = p->sr;
+        if (t->kind != P3MAZE_SR_BMH && t->kind != P3MAZE_SR_LJ)
+            return fail(nullptr, P3MAZE_ERR_INVALID, "unknown short-range kind");
+        if (t->n_types < 1 || t->n_types > P3MAZE_MAX_TYPES)
+            return fail(nullptr, P3MAZE_ERR_INVALID, "n_types out of range");
+        if (!p->types) return fail(nullptr, P3MAZE_ERR_INVALID, "types are required with a short-range table");
+        for (int i = 0; i < n; ++i)
+            if (p->types[i] < 0 || p->types[i] >= t->n_types)
+                return fail(nullptr, P3MAZE_ERR_INVALID, "particle type out of range");
+        tab.kind = t->kind;
+        tab.nt = t->n_types;
+        for (int a = 0; a < 5; ++a)
+            for (int k = 0; k < t->n_types * t->n_types; ++k) tab.p[a][k] = t->p[a][k];
+        if (t->kind == P3MAZE_SR_BMH)
+            for (int k = 0; k < t->n_types * t->n_types; ++k)
+                if (!(tab.p[1][k] > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "BMH rho must be > 0");
+    } else {
+        tab.kind = 0;
+        tab.nt = 1;
+    }
+    int nmol = 0;
+    if (p->topology && p->topology->n_molecules > 0) {
+        const p3maze_topology* tp = p->topology;
+        if (!tp->triples) return fail(nullptr, P3MAZE_ERR_INVALID, "topology triples missing");
+        std::vector<char> seen(n, 0);
+        for (int m = 0; m < tp->n_molecules; ++m)
+            for (int a = 0; a < 3; ++a) {
+                const int id = tp->triples[3 * m + a];
+                if (id < 0 || id >= n || seen[id])
+                    return fail(nullptr, P3MAZE_ERR_INVALID, "topology triples must be disjoint valid indices");
+                seen[id] = 1;
+            }
+        nmol = tp->n_molecules;
+    }
+    const double h = L / p->mesh;
+    const double sigma = 1.0 / (std::sqrt(2.0) * p->alpha);
+    // diffusion smoothing: per-axis variance sigma^2 - 4 h^2/6 in K steps of 2 c h^2
+    const double kappa = (sigma * sigma - 4.0 * h * h / 6.0) / (2.0 * h * h);
+    if (!(kappa > 0.0))
+        return fail(nullptr, P3MAZE_ERR_INVALID, "mesh too coarse for alpha: need sigma^2 > 2 h^2/3");
+
+    p3maze_ctx* ctx = new (std::nothrow) p3maze_ctx();
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_OOM, "host allocation failed");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->np = n;
+    ctx->N = p->mesh;
+    ctx->P = (int64_t)p->mesh * p->mesh * p->mesh;
+    ctx->L = L;
+    ctx->h = h;
+    ctx->inv_h = p->mesh / L;
+    ctx->alpha = p->alpha;
+    ctx->sigma = sigma;
+    ctx->rc = p->r_cut;
+    ctx->K = (int)std::ceil(6.0 * kappa);
+    ctx->c = kappa / ctx->K;
+    ctx->tol = p->tol;
+    ctx->dt = p->dt;
+    ctx->pred = p->predictor == 0 ? 3 : p->predictor;
+    ctx->prec = p->precision;
+    ctx->itmax = p->max_mg_iters ? p->max_mg_iters : 50;
+    ctx->nu1 = p->pre_sweeps ? p->pre_sweeps : 2;
+    ctx->nu2 = p->post_sweeps ? p->post_sweeps : 2;
+    ctx->ke = p->coulomb_k != 0.0 ? p->coulomb_k : P3_COULOMB_K;
+    ctx->nc = std::max(1, (int)std::floor(L / (0.5 * p->r_cut)));
+    ctx->ncell = ctx->nc * ctx->nc * ctx->nc;
+    ctx->inv_cell = ctx->nc / L;
+    ctx->nlev = nlev;
+    ctx->tab = tab;
+    ctx->nmol = nmol;
+    if (nmol) {
+        ctx->kb = p->topology->kb;
+        ctx->r0 = p->topology->r0;
+        ctx->ka = p->topology->ka;
+        ctx->th0 = p->topology->theta0;
+    }
+    double q2 = 0.0;
+    for (int i = 0; i < n; ++i) q2 += p->charges[i] * p->charges[i];
+    ctx->v_self = -ctx->ke * q2 / (std::sqrt(2.0 * kPi) * sigma);
+    ctx->st.smooth_steps = ctx->K;
+    ctx->st.smooth_coeff = ctx->c;
+    ctx->st.mg_levels = nlev;
+    ctx->st.coarse_n = ncoarse;
+    ctx->st.cells_per_axis = ctx->nc;
+    ctx->st.sigma = sigma;
+
+    int rc = setup(ctx, p, pos, vel);
+    if (!rc) rc = initialise_field(ctx);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = fail(ctx, P3MAZE_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
+    }
+    if (rc) {
+        g_init_error = ctx->err;
+        release(ctx);
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return P3MAZE_OK;
+}
+
+int p3maze_step(p3maze_ctx* ctx, int32_t nsteps) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, P3MAZE_ERR_INVALID, "nsteps must be >= 0");
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = step_once(ctx);
+        if (rc) return rc;
+    }
+    return P3MAZE_OK;
+}
+
+int p3maze_reinit(p3maze_ctx* ctx) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    int rc = initialise_field(ctx);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return P3MAZE_OK;
+}
+
+void p3maze_destroy(p3maze_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    release(ctx);
+    delete ctx;
+}
+
+int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    cudaStream_t s = ctx->stream;
+    const int nb = kReduceBlocks;
+    k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->ecs, ctx->partial);
+    k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_ESR);
+    k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->evs, ctx->partial);
+    k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_EVDW);
+    if (ctx->prec == P3MAZE_MIXED)
+        k_dot_partial<float><<<nb, P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ctx->icur], (const float*)ctx->q, ctx->partial);
+    else
+        k_dot_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ctx->icur], (const double*)ctx->q, ctx->partial);
+    k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_VLR);
+    k_mv2_partial<<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->mass, ctx->partial);
+    k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_MV2);
+    if (ctx->nmol) {
+        k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->nmol, ctx->eb, ctx->partial);
+        k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_EBOND);
+        k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->nmol, ctx->ex, ctx->partial);
+        k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_EXCL);
+    }
+    CKL();
+    int rc = sync_scalars(ctx);
+    if (rc) return rc;
+    const double* h = ctx->hscal;
+    out->v_sr = h[S_ESR];
+    out->v_vdw = h[S_EVDW];
+    out->v_lr = 0.5 * ctx->ke * h[S_VLR];
+    out->v_self = ctx->v_self;
+    out->v_bond = ctx->nmol ? h[S_EBOND] : 0.0;
+    out->v_excl = ctx->nmol ? h[S_EXCL] : 0.0;
+    out->kinetic = 0.5 * h[S_MV2] / P3_ACCEL;
+    out->total = out->v_sr + out->v_lr + out->v_self + out->v_excl + out->v_vdw + out->v_bond + out->kinetic;
+    return P3MAZE_OK;
+}
+
+int p3maze_get_stats(p3maze_ctx* ctx, p3maze_stats* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    *out = ctx->st;
+    return P3MAZE_OK;
+}
+
+static int copy_out(p3maze_ctx* ctx, const void* dsrc, void* hdst, size_t bytes) {
+    CK(cudaMemcpyAsync(hdst, dsrc, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return P3MAZE_OK;
+}
+
+int p3maze_get_positions(p3maze_ctx* ctx, double* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    return copy_out(ctx, ctx->r, out, 24 * (size_t)ctx->np);
+}
+
+int p3maze_get_velocities(p3maze_ctx* ctx, double* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    return copy_out(ctx, ctx->v, out, 24 * (size_t)ctx->np);
+}
+
+int p3maze_get_forces(p3maze_ctx* ctx, int32_t which, double* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    const double* src = which == P3MAZE_F_TOTAL ? ctx->F
+                      : which == P3MAZE_F_SR    ? ctx->Fsr
+                      : which == P3MAZE_F_LR    ? ctx->Flr
+                      : which == P3MAZE_F_BOND  ? ctx->Fb
+                                                : nullptr;
+    if (!src) return fail(ctx, P3MAZE_ERR_INVALID, "unknown force part");
+    return copy_out(ctx, src, out, 24 * (size_t)ctx->np);
+}
+
+int p3maze_set_state(p3maze_ctx* ctx, const double* pos, const double* vel) {
+    if (!ctx || !pos || !vel) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->r, pos, 24 * (size_t)ctx->np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->v, vel, 24 * (size_t)ctx->np, cudaMemcpyHostToDevice, s));
+    k_wrap<<<nblk(3 * (int64_t)ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->L);
+    CKL();
+    return P3MAZE_OK;
+}
+
+int p3maze_get_mesh(p3maze_ctx* ctx, int32_t which, double* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    const int64_t P = ctx->P;
+    const bool mixed = ctx->prec == P3MAZE_MIXED;
+    if (which == P3MAZE_MESH_Q || which == P3MAZE_MESH_QS) {
+        const void* src = which == P3MAZE_MESH_Q ? ctx->q : ctx->qs;
+        if (mixed) {
+            std::vector<float> tmp(P);
+            int rc = copy_out(ctx, src, tmp.data(), 4 * (size_t)P);
+            if (rc) return rc;
+            for (int64_t i = 0; i < P; ++i) out[i] = tmp[i];
+        } else {
+            int rc = copy_out(ctx, src, out, 8 * (size_t)P);
+            if (rc) return rc;
+        }
+        if (which == P3MAZE_MESH_QS) {
+            double qsum = 0.0;
+            int rc = copy_out(ctx, ctx->dscal + S_QSUM, &qsum, 8);
+            if (rc) return rc;
+            const double mean = qsum / (double)P;
+            for (int64_t i = 0; i < P; ++i) out[i] -= mean;
+        }
+        return P3MAZE_OK;
+    }
+    const double* src = which == P3MAZE_MESH_PHI   ? ctx->phi[ctx->icur]
+                      : which == P3MAZE_MESH_Y     ? (ctx->st.steps > 0 ? ctx->yh[1] : nullptr)
+                      : which == P3MAZE_MESH_SIGMA ? ctx->sig
+                                                   : nullptr;
+    if (which == P3MAZE_MESH_Y && ctx->st.steps == 0)
+        return fail(ctx, P3MAZE_ERR_INVALID, "no correction has been solved yet (take a step first)");
+    if (!src) return fail(ctx, P3MAZE_ERR_INVALID, "unknown mesh array");
+    return copy_out(ctx, src, out, 8 * (size_t)P);
+}
+
+int p3maze_get_cells(p3maze_ctx* ctx, int32_t* cell_of, int32_t* cell_start, int32_t* order) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    int rc = 0;
+    if (cell_of && (rc = copy_out(ctx, ctx->cell, cell_of, 4 * (size_t)ctx->np))) return rc;
+    if (cell_start && (rc = copy_out(ctx, ctx->start, cell_start, 4 * ((size_t)ctx->ncell + 1)))) return rc;
+    if (order && (rc = copy_out(ctx, ctx->order, order, 4 * (size_t)ctx->np))) return rc;
+    return P3MAZE_OK;
+}
+
+int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    if (enable && !ctx->ev[0][0])
+        for (int st = 0; st < P3MAZE_NSTAGES; ++st)
+            for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ctx->ev[st][k]));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->timing = enable != 0;
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+        ctx->stage_ms[st] = 0.0;
+        ctx->launches[st] = 0;
+        ctx->pending[st] = false;
+    }
+    ctx->timed_steps = 0;
+    return P3MAZE_OK;
+}
+
+int p3maze_get_timing(p3maze_ctx* ctx, p3maze_timing* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    int64_t tot = 0;
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+        out->ms[st] = ctx->stage_ms[st];
+        out->launches[st] = ctx->launches[st];
+        tot += ctx->launches[st];
+    }
+    out->timed_steps = ctx->timed_steps;
+    out->total_launches = tot;
+    return P3MAZE_OK;
+}
+
+const char* p3maze_last_error(const p3maze_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle on the same seeded inputs, at the GPU's own positions.
+
+Tolerances (written here, derived in the design notes):
+  * integer work (cell index, cell starts, cell order): bit-exact;
+  * assigned and smoothed charge: 1e-12 of max|q| in FP64, 1e-6 in mixed;
+  * constrained potential: the oracle's constraint residual of the GPU phi,
+    max|(h/4pi) M phi + q^s|, at most tol (plus rounding);
+  * forces: 1e-5 relative RMS in FP64 and 1e-4 in mixed mode (solved to a
+    tolerance well below the force error it would cause).
+"""
+import numpy as np
+import pytest
+
+from oracle import p3maze_oracle as O
+from paper_2606_31379_b300 import synth as S
+from tests.parity_helpers import (at_positions, constraint_residual, oracle_full, oracle_sampled,
+                                  rel_rms)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2606_31379_b300 import p3maze
+    return p3maze
+
+
+def _ctx(P, system, **kw):
+    args = dict(alpha=0.30, r_cut=9.0, mesh=32, tol=1e-9, dt=1.0)
+    args.update(kw)
+    return P.Context.from_system(system, **args)
+
+
+# ------------------------------------------------------------------ NaCl 512
+@pytest.fixture(scope="module")
+def nacl512():
+    return S.nacl_melt(512, 25.2, seed=1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_init_mesh_and_cells_match_oracle(P, nacl512, precision):
+    s = nacl512
+    with _ctx(P, s, precision=precision) as ctx:
+        pos = ctx.positions()
+        np.testing.assert_array_equal(pos, O.wrap(s.pos, s.box))
+        nc, cell, start, order = ctx.cells()
+        onc, ocell, ostart, oorder = O.cell_list(pos, s.box, 9.0)
+        assert nc == onc
+        np.testing.assert_array_equal(cell, ocell)
+        np.testing.assert_array_equal(start, ostart)
+        np.testing.assert_array_equal(order, oorder)
+        st = ctx.stats()
+        K, c = O.smoothing_schedule(O.sigma_of_alpha(0.30), s.box / 32)
+        assert st["smooth_steps"] == K and st["smooth_coeff"] == pytest.approx(c, rel=1e-15)
+        q = O.assign_charges(pos, s.charge, s.box, 32)
+        qs = O.smooth(q, K, c)
+        qs -= qs.mean()
+        tolq = 1e-12 if precision == "fp64" else 1e-6
+        assert np.abs(ctx.mesh("q") - q).max() <= tolq * np.abs(q).max()
+        assert np.abs(ctx.mesh("qs") - qs).max() <= tolq * np.abs(qs).max()
+
+
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_init_forces_and_energies_match_oracle(P, nacl512, precision, ftol):
+    s = nacl512
+    with _ctx(P, s, precision=precision, tol=1e-10) as ctx:
+        pos = ctx.positions()
+        ref = oracle_full(s, pos, 0.30, 9.0, 32)
+        F = ctx.forces()
+        assert rel_rms(F, ref["F"]) < ftol
+        assert rel_rms(ctx.forces("lr"), ref["F_lr"]) < ftol
+        assert rel_rms(ctx.forces("sr"), ref["F_sr"]) < ftol
+        np.testing.assert_allclose(ctx.forces("sr") + ctx.forces("lr"), F, rtol=0, atol=1e-9 * np.abs(F).max())
+        e = ctx.energy()
+        etol = 1e-9 if precision == "fp64" else 1e-5
+        for k in ("v_sr", "v_lr", "v_self", "v_vdw"):
+            assert e[k] == pytest.approx(ref[k], rel=etol, abs=1e-9), k
+        phi = ctx.mesh("phi")
+        phi_ref = ref["fields"]["phi"]
+        assert np.abs((phi - phi.mean()) - phi_ref).max() < 1e-5 * np.abs(phi_ref).max()
+
+
+def test_constraint_satisfied_to_tolerance_at_config_tol(P, nacl512):
+    """At the production tolerance 1e-6 the GPU potential satisfies the
+    discrete Poisson constraint (Eq. 13) to tol, checked with the oracle's
+    stencil and smoothed charge."""
+    s = nacl512
+    with _ctx(P, s, tol=1e-6) as ctx:
+        pos = ctx.positions()
+        mf = O.mesh_fields(at_positions(s, pos), 0.30, 32)
+        res = constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"])
+        assert res <= 1e-6 * (1 + 1e-6)
+        assert ctx.stats()["last_residual"] <= 1e-6
+        ctx.step(3)
+        mf = O.mesh_fields(at_positions(s, ctx.positions()), 0.30, 32)
+        assert constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"]) <= 1e-6 * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_steps_follow_velocity_verlet_and_oracle_forces(P, nacl512, precision, ftol):
+    s = nacl512
+    acc = O.ACCEL / s.mass[:, None]
+    with _ctx(P, s, precision=precision, tol=1e-10) as ctx:
+        for k in range(4):
+            r0, v0, F0 = ctx.positions(), ctx.velocities(), ctx.forces()
+            ctx.step(1)
+            r1, v1, F1 = ctx.positions(), ctx.velocities(), ctx.forces()
+            vh = v0 + 0.5 * 1.0 * F0 * acc
+            np.testing.assert_allclose(r1, O.wrap(r0 + 1.0 * vh, s.box), rtol=0, atol=1e-11)
+            np.testing.assert_allclose(v1, vh + 0.5 * F1 * acc, rtol=1e-12, atol=1e-15)
+            ref = oracle_full(s, r1, 0.30, 9.0, 32)
+            assert rel_rms(F1, ref["F"]) < ftol
+            nc, cell, start, order = ctx.cells()
+            _, ocell, ostart, oorder = O.cell_list(r1, s.box, 9.0)
+            np.testing.assert_array_equal(order, oorder)
+        st = ctx.stats()
+        assert st["steps"] == 4 and st["total_iters"] >= 1
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("n, box, mesh, rc, seed", [
+    (2, 10.0, 16, 9.0, 1),      # two ions, L < 2 r_cut: several images, 2 cells per axis
+    (16, 12.0, 24, 9.0, 2),     # mesh 24 = 3 * 8: coarsest level 3^3
+    (40, 14.0, 20, 7.0, 3),     # mesh 20 = 5 * 4: coarsest 5^3
+    (24, 11.0, 5, 5.0, 4),      # single-level mesh: direct coarse solve only
+    (64, 19.0, 12, 9.5, 5),     # mesh 12 -> 6 -> 3
+])
+def test_ragged_and_degenerate_shapes(P, n, box, mesh, rc, seed):
+    s = S.nacl_melt(n, box, seed=seed, dmin=1.8)
+    alpha = 0.30 if mesh >= 12 else 0.2
+    with _ctx(P, s, mesh=mesh, r_cut=rc, alpha=alpha, tol=1e-11) as ctx:
+        pos = ctx.positions()
+        ref = oracle_full(s, pos, alpha, rc, mesh)
+        assert rel_rms(ctx.forces(), ref["F"]) < 1e-5
+        _, cell, start, order = ctx.cells()
+        _, ocell, ostart, oorder = O.cell_list(pos, s.box, rc)
+        np.testing.assert_array_equal(order, oorder)
+        np.testing.assert_array_equal(start, ostart)
+        ctx.step(2)
+        ref = oracle_full(s, ctx.positions(), alpha, rc, mesh)
+        assert rel_rms(ctx.forces(), ref["F"]) < 1e-5
+
+
+@pytest.mark.parametrize("predictor", [1, 2, 3])
+def test_predictors_reach_same_field(P, nacl512, predictor):
+    s = nacl512
+    with _ctx(P, s, predictor=predictor, tol=1e-10) as ctx:
+        ctx.step(4)
+        ref = oracle_full(s, ctx.positions(), 0.30, 9.0, 32)
+        assert rel_rms(ctx.forces(), ref["F"]) < 1e-5
+
+
+def test_non_convergence_is_reported(P, nacl512):
+    with pytest.raises(P.P3MaZeError) as ei:
+        _ctx(P, nacl512, tol=1e-14, max_mg_iters=1)
+    assert ei.value.code == P.ERR_NOT_CONVERGED
+    assert "did not reach" in str(ei.value)
+
+
+def test_momentum_conservation_on_gpu(P, nacl512):
+    with _ctx(P, nacl512, tol=1e-11) as ctx:
+        F = ctx.forces()
+        assert np.abs(ctx.forces("sr").sum(0)).max() < 1e-10 * np.abs(F).max()
+        assert np.abs(ctx.forces("lr").sum(0)).max() < 1e-7 * np.abs(ctx.forces("lr")).max()
+
+
+# ------------------------------------------------------------------ SPC/Fw
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_spcfw_small_matches_oracle(P, precision, ftol):
+    w = S.spcfw_water(64, 12.42, seed=3)
+    with _ctx(P, w, mesh=16, r_cut=6.0, tol=1e-10, dt=0.5, precision=precision) as ctx:
+        pos = ctx.positions()
+        ref = oracle_full(w, pos, 0.30, 6.0, 16)
+        assert rel_rms(ctx.forces(), ref["F"]) < ftol
+        e = ctx.energy()
+        etol = 1e-9 if precision == "fp64" else 1e-5
+        for k in ("v_sr", "v_lr", "v_vdw", "v_bond", "v_excl"):
+            ref_k = ref[k] if k != "v_bond" else ref["v_bond"] + ref["v_angle"]
+            assert e[k] == pytest.approx(ref_k, rel=etol, abs=1e-8), k
+        ctx.step(2)
+        ref = oracle_full(w, ctx.positions(), 0.30, 6.0, 16)
+        assert rel_rms(ctx.forces(), ref["F"]) < ftol
+
+
+# ------------------------------------------------------------------ full size
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_nacl_32k_128_sampled_parity(P, precision, ftol):
+    """Molten NaCl, 32768 ions, 128^3 mesh, in the launch configuration the
+    benchmark times: full-mesh check of q^s and phi, and total forces on a
+    sample of particles summed one by one by the oracle."""
+    s, prm = S.make_workload("nacl_32k")
+    with P.Context.from_system(s, alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"],
+                               tol=1e-9, dt=prm["dt"], precision=precision) as ctx:
+        ctx.step(1)
+        pos = ctx.positions()
+        sample = np.random.default_rng(0).choice(s.n, 48, replace=False)
+        F_ref, mf, F_lr = oracle_sampled(s, pos, prm["alpha"], prm["r_cut"], prm["mesh"], sample)
+        qs = ctx.mesh("qs")
+        tolq = 1e-12 if precision == "fp64" else 1e-6
+        assert np.abs(qs - mf["qs"]).max() <= tolq * np.abs(mf["qs"]).max()
+        assert rel_rms(ctx.forces("lr"), F_lr) < ftol
+        assert rel_rms(ctx.forces()[sample], F_ref) < ftol
+    with P.Context.from_system(s, alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"],
+                               tol=prm["tol"], dt=prm["dt"], precision=precision) as ctx:
+        ctx.step(2)
+        mf = O.mesh_fields(at_positions(s, ctx.positions()), prm["alpha"], prm["mesh"])
+        # mixed mode: the FP32 q^s differs from the oracle's by ~1e-7 relative
+        margin = 1e-6 * prm["tol"] if precision == "fp64" else 1e-8
+        assert constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"]) <= prm["tol"] + margin
