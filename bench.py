@@ -142,7 +142,13 @@ def oracle_step_seconds(system, prm, n_sample: int) -> tuple[float, str]:
     """One oracle force evaluation (full mesh part + short-range part of
     n_sample particles scaled to all) on one host core; returns the estimated
     seconds of a full step and a description of the sample."""
-    from threadpoolctl import threadpool_limits
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:          # numpy's FFT and array ops run on one thread anyway
+        import contextlib
+
+        def threadpool_limits(_n):
+            return contextlib.nullcontext()
     from oracle import p3maze_oracle as O
 
     rng = np.random.default_rng(0)

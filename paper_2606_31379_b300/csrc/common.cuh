@@ -46,19 +46,25 @@ __device__ __forceinline__ int bspline_axis(double x, double inv_h, int n, doubl
     return b < 0 ? b + n : (b >= n ? b - n : b);
 }
 
-// Block-wide sum of a double (all threads get the result).
+__device__ __forceinline__ int linear_tid() {
+    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+
+__device__ __forceinline__ int block_threads() { return blockDim.x * blockDim.y * blockDim.z; }
+
+// Block-wide sum of a double (all threads get the result).  Any block shape.
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tid = linear_tid(), lane = tid & 31, wid = tid >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = v;
     __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    const int nw = (block_threads() + 31) >> 5;
+    v = (tid < nw) ? sh[tid] : 0.0;
     if (wid == 0)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) sh[0] = v;
+    if (tid == 0) sh[0] = v;
     __syncthreads();
     v = sh[0];
     __syncthreads();
@@ -68,15 +74,15 @@ __device__ __forceinline__ double block_sum(double v) {
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int tid = linear_tid(), lane = tid & 31, wid = tid >> 5;
     __syncthreads();
     if (lane == 0) sh[wid] = v;
     __syncthreads();
-    const int nw = (blockDim.x + 31) >> 5;
-    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    const int nw = (block_threads() + 31) >> 5;
+    v = (tid < nw) ? sh[tid] : 0.0;
     if (wid == 0)
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) sh[0] = v;
+    if (tid == 0) sh[0] = v;
     __syncthreads();
     v = sh[0];
     __syncthreads();

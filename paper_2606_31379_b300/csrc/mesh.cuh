@@ -19,13 +19,6 @@ __device__ __forceinline__ T nb6(const T* __restrict__ f, int x, int y, int z, i
            f[(zm * n + y) * n + x] + f[(zp * n + y) * n + x];
 }
 
-__device__ __forceinline__ void unflatten(int64_t i, int n, int& x, int& y, int& z) {
-    x = (int)(i % n);
-    const int64_t r = i / n;
-    y = (int)(r % n);
-    z = (int)(r / n);
-}
-
 // ---------------------------------------------------------------- assignment
 // q_n += Q_a W(u_a - n): cubic B-spline charge assignment (Sec. 2), one thread
 // per particle in cell order, 64 atomic adds.
@@ -53,16 +46,29 @@ k_spread(int np, const PQ* __restrict__ xq, int n, double inv_h, T* __restrict__
     }
 }
 
+// ---------------------------------------------------------------- 3D launch
+// Stencil kernels run on a (32, 8) thread block over an (x, y) tile with
+// blockIdx.z = z, so no index division is needed.  XDIV = 2 packs two x
+// points per thread slot (red-black half sweeps).
+#define P3_BX 32
+#define P3_BY 8
+
+__device__ __forceinline__ bool xyz3(int n, int& x, int& y, int& z) {
+    x = blockIdx.x * P3_BX + threadIdx.x;
+    y = blockIdx.y * P3_BY + threadIdx.y;
+    z = blockIdx.z;
+    return x < n && y < n;
+}
+
 // ---------------------------------------------------------------- smoothing
 // One explicit diffusion step out = in + c M in (reading of Sec. 2's
 // diffusion-based smoothing).
 template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
+__global__ void __launch_bounds__(P3_BX * P3_BY)
 k_diffuse(int n, const T* __restrict__ in, T* __restrict__ out, T c) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * n * n) return;
     int x, y, z;
-    unflatten(i, n, x, y, z);
+    if (!xyz3(n, x, y, z)) return;
+    const int i = (z * n + y) * n + x;
     const T v = in[i];
     out[i] = v + c * (nb6(in, x, y, z, n) - (T)6 * v);
 }
@@ -106,24 +112,23 @@ __global__ void k_sum_final(int nb, const double* __restrict__ partial, double* 
 }
 
 // ---------------------------------------------------------------- Mass-Zero
-// Predicted constraint residual (Eq. 17) with the gauge fix:
-//   sigma_p = (h/4pi) M (2 phi^k - phi^{k-1}) + q^s - mean(q^s)
+// psi = (h/4pi) M phi is carried from step to step (it follows from the final
+// FP64 residual: (h/4pi) M phi^{k+1} = sigma_p - M y* - q^s), so the
+// prediction needs no stencil:
+//   sigma_p = (h/4pi) M (2 phi^k - phi^{k-1}) + q^s - mean      (Eq. 17)
+//           = 2 psi^k - psi^{k-1} + q^s - mean(q^s)
 // and the multiplier guess y0 (Sec. 3.3): order 0 -> 0, 1 -> y^k,
 // 2 -> 2y^k - y^{k-1}, 3 -> 3y^k - 3y^{k-1} + y^{k-2}.
 template <typename T>
 __global__ void __launch_bounds__(P3_THREADS)
-k_predict(int n, const double* __restrict__ phik, const double* __restrict__ phikm1,
-          const T* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, double hc,
+k_predict(int64_t m, const double* __restrict__ psik, const double* __restrict__ psikm1,
+          const T* __restrict__ qs, const double* __restrict__ qsum, double inv_pts,
           const double* __restrict__ y1, const double* __restrict__ y2, const double* __restrict__ y3,
           int order, double* __restrict__ sig, double* __restrict__ y0) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * n * n) return;
-    int x, y, z;
-    unflatten(i, n, x, y, z);
-    const double mk = nb6(phik, x, y, z, n) - 6.0 * phik[i];
-    const double mkm1 = nb6(phikm1, x, y, z, n) - 6.0 * phikm1[i];
+    if (i >= m) return;
     const double mean = qsum[0] * inv_pts;
-    sig[i] = hc * (2.0 * mk - mkm1) + ((double)qs[i] - mean);
+    sig[i] = 2.0 * psik[i] - psikm1[i] + ((double)qs[i] - mean);
     double g = 0.0;
     if (order == 1) g = y1[i];
     else if (order == 2) g = 2.0 * y1[i] - y2[i];
@@ -131,26 +136,28 @@ k_predict(int n, const double* __restrict__ phik, const double* __restrict__ phi
     y0[i] = g;
 }
 
-// Fine-level FP64 residual r = sigma_p - M y, stored in the bulk type for the
-// correction V-cycle, and max_n |r_n| (Eq. 20) folded into *rmax with an
-// atomic max on the bit pattern (non-negative doubles order like integers).
-// A NaN or Inf residual is recorded as +Inf.
+// Fine-level FP64 residual r = sigma_p - M y (Eq. 20's argument): kept in
+// FP64 (rfin, for the psi update) and in the bulk type (input of the
+// correction V-cycle), with max_n |r_n| folded into *rmax by an atomic max on
+// the bit pattern (non-negative doubles order like integers).  NaN or Inf is
+// recorded as +Inf.
 template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
+__global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_fine(int n, const double* __restrict__ yv, const double* __restrict__ sig, T* __restrict__ r,
-             unsigned long long* __restrict__ rmax) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+             double* __restrict__ rfin, unsigned long long* __restrict__ rmax) {
+    int x, y, z;
     double a = 0.0;
-    if (i < (int64_t)n * n * n) {
-        int x, y, z;
-        unflatten(i, n, x, y, z);
+    if (xyz3(n, x, y, z)) {
+        const int i = (z * n + y) * n + x;
         const double res = sig[i] - (nb6(yv, x, y, z, n) - 6.0 * yv[i]);
         r[i] = (T)res;
+        rfin[i] = res;
         a = fabs(res);
         if (!(a <= 1.0e308)) a = __longlong_as_double(0x7ff0000000000000LL);
     }
     a = block_max(a);
-    if (threadIdx.x == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(a));
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        atomicMax(rmax, (unsigned long long)__double_as_longlong(a));
 }
 
 // y += e (FP64 accumulation of the correction).
@@ -160,52 +167,92 @@ __global__ void k_add_correction(int64_t m, double* __restrict__ yv, const T* __
     if (i < m) yv[i] += (double)e[i];
 }
 
-// Field update (supporting information Sec. 1):
-// phi^{k+1} = 2 phi^k - phi^{k-1} - (4pi/h) y*, written over phi^{k-1}.
+// Field update (supporting information Sec. 1), written over the k-1 slots:
+//   phi^{k+1} = 2 phi^k - phi^{k-1} - (4pi/h) y*
+//   psi^{k+1} = (h/4pi) M phi^{k+1} = r_final - (q^s - mean)
+template <typename T>
 __global__ void k_update(int64_t m, const double* __restrict__ phik, double* __restrict__ phikm1,
-                         const double* __restrict__ yv, double coef) {
+                         double* __restrict__ psikm1, const double* __restrict__ yv,
+                         const double* __restrict__ rfin, const T* __restrict__ qs,
+                         const double* __restrict__ qsum, double inv_pts, double coef) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) phikm1[i] = 2.0 * phik[i] - phikm1[i] - coef * yv[i];
+    if (i >= m) return;
+    phikm1[i] = 2.0 * phik[i] - phikm1[i] - coef * yv[i];
+    psikm1[i] = rfin[i] - ((double)qs[i] - qsum[0] * inv_pts);
+}
+
+// Convergence control of the correction solve (Eq. 20), one thread:
+// reads max|r| of the residual just computed, resets the accumulator, and
+// decides whether another V-cycle runs (res > tol, finite, fewer than itmax
+// cycles so far).  Records the outcome in MGState; a failure code is sticky.
+// With use_handle the decision also drives the graph's while node.
+struct MGState {
+    int it;                 // V-cycles run in the current solve
+    int cont;               // 1: run another V-cycle
+    int status;             // first failure: 0, -4 not converged, -5 non-finite
+    int last_iters;
+    double last_res;
+    long long total_iters;  // summed over finished solves
+    long long solves;
+};
+
+__global__ void k_mg_check(unsigned long long* __restrict__ rmax, double tol, int itmax,
+                           MGState* __restrict__ st, cudaGraphConditionalHandle handle, int use_handle) {
+    if (threadIdx.x != 0) return;
+    const unsigned long long bits = *rmax;
+    *rmax = 0ull;
+    const double res = __longlong_as_double((long long)bits);
+    int cont = 0;
+    if (!(res <= 1.0e308)) {
+        if (st->status == 0) st->status = -5;
+    } else if (res > tol) {
+        if (st->it < itmax) cont = 1;
+        else if (st->status == 0) st->status = -4;
+    }
+    if (cont) {
+        st->it += 1;
+    } else {
+        st->last_iters = st->it;
+        st->last_res = res;
+        st->total_iters += st->it;
+        st->solves += 1;
+        st->it = 0;
+    }
+    st->cont = cont;
+    if (use_handle) cudaGraphSetConditional(handle, cont);
 }
 
 // ---------------------------------------------------------------- multigrid
 // Red-black Gauss-Seidel half sweep on M e = b: points with (x+y+z)%2 == color
-// get e = (sum of neighbours - b)/6.  One thread per point of the colour.
+// get e = (sum of neighbours - b)/6.  Thread slot (tx, y, z) handles
+// x = 2 tx + parity.  first = 1: the sweep starts from e = 0, so red points
+// get -b/6 and black points are cleared (replaces a memset and a sweep).
 template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
-k_rbgs(int n, T* __restrict__ e, const T* __restrict__ b, int color) {
-    const int half = n >> 1;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)half * n * n) return;
-    const int xi = (int)(t % half);
-    const int64_t rr = t / half;
-    const int y = (int)(rr % n), z = (int)(rr / n);
-    const int x = 2 * xi + ((y + z + color) & 1);
-    const int64_t i = ((int64_t)z * n + y) * n + x;
-    e[i] = (nb6(e, x, y, z, n) - b[i]) * (T)(1.0 / 6.0);
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_rbgs(int n, T* __restrict__ e, const T* __restrict__ b, int color, int first) {
+    const int tx = blockIdx.x * P3_BX + threadIdx.x;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int z = blockIdx.z;
+    const int x = 2 * tx + ((y + z + color) & 1);
+    if (x >= n || y >= n) return;
+    const int i = (z * n + y) * n + x;
+    if (first) {
+        e[i] = -b[i] * (T)(1.0 / 6.0);
+        const int xo = x ^ 1;  // the other colour in this pair of x (n even)
+        e[i - x + xo] = (T)0;
+    } else {
+        e[i] = (nb6(e, x, y, z, n) - b[i]) * (T)(1.0 / 6.0);
+    }
 }
 
-// r = b - M e on one level.
+// Residual and full-weighting restriction fused: b_c[I] = 4 sum_d w(d)
+// (b_f - M e_f)[2I + d], w = prod of (1/4, 1/2, 1/4); the factor 4 is the
+// rediscretisation of the dimensionless M on a mesh of twice the spacing.
 template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
-k_resid(int n, const T* __restrict__ e, const T* __restrict__ b, T* __restrict__ r) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * n * n) return;
-    int x, y, z;
-    unflatten(i, n, x, y, z);
-    r[i] = b[i] - (nb6(e, x, y, z, n) - (T)6 * e[i]);
-}
-
-// Full-weighting restriction to the coarse level (nc = n_fine/2) and the
-// rediscretisation factor 4 (the coarse spacing is twice the fine one):
-// b_c[I] = 4 sum_{d in {-1,0,1}^3} w(d) r_f[2I + d], w = prod (1/2 or 1/4).
-template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
-k_restrict(int nc, const T* __restrict__ rf, T* __restrict__ bc) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)nc * nc * nc) return;
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_resid_restrict(int nc, const T* __restrict__ e, const T* __restrict__ b, T* __restrict__ bc) {
     int X, Y, Z;
-    unflatten(i, nc, X, Y, Z);
+    if (!xyz3(nc, X, Y, Z)) return;
     const int n = 2 * nc;
     const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
     T acc = 0;
@@ -216,63 +263,166 @@ k_restrict(int nc, const T* __restrict__ rf, T* __restrict__ bc) {
         for (int dy = -1; dy <= 1; ++dy) {
             const int y = wrap_idx(2 * Y + dy, n);
             const T wyz = w1[dy + 1] * w1[dz + 1];
-            const T* row = rf + ((int64_t)z * n + y) * n;
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) acc += wyz * w1[dx + 1] * row[wrap_idx(2 * X + dx, n)];
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = wrap_idx(2 * X + dx, n);
+                const int i = (z * n + y) * n + x;
+                acc += wyz * w1[dx + 1] * (b[i] - (nb6(e, x, y, z, n) - (T)6 * e[i]));
+            }
         }
     }
-    bc[i] = (T)4 * acc;
+    bc[(Z * nc + Y) * nc + X] = (T)4 * acc;
 }
 
 // Trilinear prolongation and correction on the fine level: e_f += P e_c.
 template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
-k_prolong_add(int n, const T* __restrict__ ec, T* __restrict__ ef) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * n * n) return;
-    int x, y, z;
-    unflatten(i, n, x, y, z);
-    const int nc = n >> 1;
-    int ix[2], iy[2], iz[2];
-    T wx[2], wy[2], wz[2];
-    ix[0] = x >> 1; ix[1] = (x & 1) ? ((x >> 1) + 1 == nc ? 0 : (x >> 1) + 1) : ix[0];
-    wx[0] = (x & 1) ? (T)0.5 : (T)1; wx[1] = (x & 1) ? (T)0.5 : (T)0;
-    iy[0] = y >> 1; iy[1] = (y & 1) ? ((y >> 1) + 1 == nc ? 0 : (y >> 1) + 1) : iy[0];
-    wy[0] = (y & 1) ? (T)0.5 : (T)1; wy[1] = (y & 1) ? (T)0.5 : (T)0;
-    iz[0] = z >> 1; iz[1] = (z & 1) ? ((z >> 1) + 1 == nc ? 0 : (z >> 1) + 1) : iz[0];
-    wz[0] = (z & 1) ? (T)0.5 : (T)1; wz[1] = (z & 1) ? (T)0.5 : (T)0;
-    T acc = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-                acc += wx[a] * wy[b] * wz[c] * ec[((int64_t)iz[c] * nc + iy[b]) * nc + ix[a]];
-    ef[i] += acc;
+__device__ __forceinline__ T prolong_at(const T* __restrict__ ec, int nc, int x, int y, int z) {
+    const int x0 = x >> 1, y0 = y >> 1, z0 = z >> 1;
+    const int x1 = (x & 1) ? (x0 + 1 == nc ? 0 : x0 + 1) : x0;
+    const int y1 = (y & 1) ? (y0 + 1 == nc ? 0 : y0 + 1) : y0;
+    const int z1 = (z & 1) ? (z0 + 1 == nc ? 0 : z0 + 1) : z0;
+    const T ax = (x & 1) ? (T)0.5 : (T)1, bx = (x & 1) ? (T)0.5 : (T)0;
+    const T ay = (y & 1) ? (T)0.5 : (T)1, by = (y & 1) ? (T)0.5 : (T)0;
+    const T az = (z & 1) ? (T)0.5 : (T)1, bz = (z & 1) ? (T)0.5 : (T)0;
+    const T* p00 = ec + (z0 * nc + y0) * nc;
+    const T* p01 = ec + (z0 * nc + y1) * nc;
+    const T* p10 = ec + (z1 * nc + y0) * nc;
+    const T* p11 = ec + (z1 * nc + y1) * nc;
+    return az * (ay * (ax * p00[x0] + bx * p00[x1]) + by * (ax * p01[x0] + bx * p01[x1])) +
+           bz * (ay * (ax * p10[x0] + bx * p10[x1]) + by * (ax * p11[x0] + bx * p11[x1]));
 }
 
-// Coarsest level: e = M^+ b in FP64 with the translation-invariant
-// pseudo-inverse kernel g (e_i = sum_j g[(i - j) mod n] b_j).  One block.
 template <typename T>
-__global__ void k_coarse_solve(int n, const double* __restrict__ g, const T* __restrict__ b, T* __restrict__ e) {
-    __shared__ double sb[512];
-    const int m = n * n * n;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) sb[j] = (double)b[j];
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const int x = i % n, y = (i / n) % n, z = i / (n * n);
-        double acc = 0.0;
-        for (int j = 0; j < m; ++j) {
-            const int jx = j % n, jy = (j / n) % n, jz = j / (n * n);
-            int dx = x - jx, dy = y - jy, dz = z - jz;
-            dx += dx < 0 ? n : 0;
-            dy += dy < 0 ? n : 0;
-            dz += dz < 0 ? n : 0;
-            acc += g[(dz * n + dy) * n + dx] * sb[j];
-        }
-        e[i] = (T)acc;
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_prolong_add(int n, const T* __restrict__ ec, T* __restrict__ ef) {
+    int x, y, z;
+    if (!xyz3(n, x, y, z)) return;
+    ef[(z * n + y) * n + x] += prolong_at(ec, n >> 1, x, y, z);
+}
+
+// ---------------------------------------------------------------- small levels
+// The levels of at most 16^3 points run inside one block of 1024 threads with
+// every array in shared memory: red-black Gauss-Seidel, fused residual and
+// restriction, the exact FP64 pseudo-inverse solve on the coarsest level and
+// trilinear prolongation.  Input b (level l0, global), output e (global).
+template <typename T>
+__device__ void blk_rbgs(int n, T* e, const T* b, int color) {
+    const int half = n >> 1, m = half * n * n;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int tx = t % half, yz = t / half, y = yz % n, z = yz / n;
+        const int x = 2 * tx + ((y + z + color) & 1);
+        e[(z * n + y) * n + x] = (nb6(e, x, y, z, n) - b[(z * n + y) * n + x]) * (T)(1.0 / 6.0);
     }
+}
+
+template <typename T>
+__device__ void blk_resid_restrict(int nc, const T* e, const T* b, T* bc) {
+    const int n = 2 * nc, m = nc * nc * nc;
+    const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int X = t % nc, Y = (t / nc) % nc, Z = t / (nc * nc);
+        T acc = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = wrap_idx(2 * Z + dz, n);
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = wrap_idx(2 * Y + dy, n);
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = wrap_idx(2 * X + dx, n);
+                    const int i = (z * n + y) * n + x;
+                    acc += w1[dx + 1] * w1[dy + 1] * w1[dz + 1] * (b[i] - (nb6(e, x, y, z, n) - (T)6 * e[i]));
+                }
+            }
+        }
+        bc[t] = (T)4 * acc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_vcycle_block(int n0, int nlev, const T* __restrict__ b_in, T* __restrict__ e_out,
+               const double* __restrict__ g, int nu1, int nu2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // layout: per level l: e_l, b_l (T, n_l^3); then the coarsest b in double
+    T* e[6];
+    T* b[6];
+    int nl[6];
+    size_t off = 0;
+    for (int l = 0, n = n0; l < nlev; ++l, n >>= 1) {
+        nl[l] = n;
+        const size_t m = (size_t)n * n * n;
+        e[l] = reinterpret_cast<T*>(smem_raw + off);
+        off += m * sizeof(T);
+        b[l] = reinterpret_cast<T*>(smem_raw + off);
+        off += m * sizeof(T);
+    }
+    off = (off + 15) / 16 * 16;
+    double* bd = reinterpret_cast<double*>(smem_raw + off);
+    const int m0 = n0 * n0 * n0;
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) b[0][i] = b_in[i];
+    __syncthreads();
+    // descend
+    for (int l = 0; l < nlev - 1; ++l) {
+        const int n = nl[l], m = n * n * n;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) e[l][i] = (T)0;
+        __syncthreads();
+        for (int s = 0; s < nu1; ++s) {
+            blk_rbgs(n, e[l], b[l], 0);
+            __syncthreads();
+            blk_rbgs(n, e[l], b[l], 1);
+            __syncthreads();
+        }
+        blk_resid_restrict(nl[l + 1], e[l], b[l], b[l + 1]);
+        __syncthreads();
+    }
+    // coarsest: exact pseudo-inverse in FP64
+    {
+        const int n = nl[nlev - 1], m = n * n * n;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) bd[j] = (double)b[nlev - 1][j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const int x = i % n, y = (i / n) % n, z = i / (n * n);
+            double acc = 0.0;
+            for (int j = 0; j < m; ++j) {
+                const int jx = j % n, jy = (j / n) % n, jz = j / (n * n);
+                int dx = x - jx, dy = y - jy, dz = z - jz;
+                dx += dx < 0 ? n : 0;
+                dy += dy < 0 ? n : 0;
+                dz += dz < 0 ? n : 0;
+                acc += g[(dz * n + dy) * n + dx] * bd[j];
+            }
+            e[nlev - 1][i] = (T)acc;
+        }
+        __syncthreads();
+    }
+    // ascend
+    for (int l = nlev - 2; l >= 0; --l) {
+        const int n = nl[l], m = n * n * n;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const int x = i % n, y = (i / n) % n, z = i / (n * n);
+            e[l][i] += prolong_at(e[l + 1], n >> 1, x, y, z);
+        }
+        __syncthreads();
+        for (int s = 0; s < nu2; ++s) {
+            blk_rbgs(n, e[l], b[l], 1);
+            __syncthreads();
+            blk_rbgs(n, e[l], b[l], 0);
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < m0; i += blockDim.x) e_out[i] = e[0][i];
+}
+
+// Shared memory of k_vcycle_block for levels n0, n0/2, ... (nlev of them).
+inline size_t vcycle_block_smem(int n0, int nlev, size_t tb) {
+    size_t bytes = 0;
+    int n = n0, nc = n0;
+    for (int l = 0; l < nlev; ++l) {
+        bytes += 2 * tb * (size_t)n * n * n;
+        nc = n;
+        n >>= 1;
+    }
+    bytes = (bytes + 15) / 16 * 16;
+    return bytes + 8 * (size_t)nc * nc * nc;
 }
 
 // ---------------------------------------------------------------- interpolation

@@ -21,6 +21,8 @@ namespace {
 thread_local std::string g_init_error = "no error";
 
 constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
+constexpr int kBlockLevelMax = 16;  // levels with n <= 16 run in one block (shared memory)
+constexpr int kMaxGraphs = 4;       // pointer phases of the phi (2) and y (4) rings
 
 // Device scalar slots.
 enum { S_QSUM = 0, S_ESR, S_EVDW, S_VLR, S_MV2, S_EBOND, S_EXCL, S_NSCAL };
@@ -33,19 +35,35 @@ struct Level {
     void* r = nullptr;
 };
 
+// One captured MD step for a given pointer phase of the field rings.
+struct StepGraph {
+    bool valid = false;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    int icur = 0;
+    double* yh[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t launches[P3MAZE_NSTAGES] = {};
+    bool timed[P3MAZE_NSTAGES] = {};
+};
+
 inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
+inline dim3 g3(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
+inline dim3 g3h(int n) { return dim3((n / 2 + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
+const dim3 kB3(P3_BX, P3_BY, 1);
 
 }  // namespace
 
 struct p3maze_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t body_stream = nullptr;  // capture of the while-node body
     // parameters
     int np = 0, N = 0, nc = 0, ncell = 0, prec = 0, pred = 3, itmax = 50, nu1 = 2, nu2 = 2, K = 0;
     int nmol = 0, nlev = 0;
     int64_t P = 0;
     double L = 0, h = 0, inv_h = 0, alpha = 0, sigma = 0, rc = 0, c = 0, tol = 0, dt = 0, ke = 0;
-    double inv_cell = 0, v_self = 0;
+    double inv_cell = 0, lcell = 0, v_self = 0;
     SRTable tab{};
     double kb = 0, r0 = 0, ka = 0, th0 = 0;
     // particle arrays (original order)
@@ -56,23 +74,37 @@ struct p3maze_ctx {
     int *cell = nullptr, *count = nullptr, *start = nullptr, *fill = nullptr, *order = nullptr;
     int *ts = nullptr, *ms = nullptr, *cs = nullptr;
     PQ* xq = nullptr;
+    PQ* xl64 = nullptr;
+    float4* xl32 = nullptr;
     double *Fs = nullptr, *ecs = nullptr, *evs = nullptr, *eb = nullptr, *ex = nullptr;
     // mesh
     void *q = nullptr, *qs = nullptr;
     double* phi[2] = {nullptr, nullptr};
-    int icur = 0;                      // phi[icur] = phi^k, phi[1-icur] = phi^{k-1}
+    double* psi[2] = {nullptr, nullptr};  // (h/4pi) M phi, same ring as phi
+    int icur = 0;                         // [icur] = step k, [1-icur] = step k-1
     double* yh[4] = {nullptr, nullptr, nullptr, nullptr};  // [0] work, [1..3] y^k, y^{k-1}, y^{k-2}
     int nhist = 0;
     double* sig = nullptr;
+    double* rfin = nullptr;
     std::vector<Level> lev;
     double* gcoarse = nullptr;
-    // reductions
+    size_t blk_smem = 0;
+    // reductions and solver state
     double* partial = nullptr;
     double* dscal = nullptr;
     unsigned long long* dres = nullptr;
+    MGState* dmg = nullptr;
     double* hscal = nullptr;
-    unsigned long long* hres = nullptr;
+    MGState* hmg = nullptr;
     p3maze_stats st{};
+    // graphs
+    bool use_graphs = true;
+    bool capturing = false;
+    bool in_body = false;
+    StepGraph graphs[kMaxGraphs];
+    int64_t body_launches = 0;       // kernels per V-cycle iteration of the while body
+    int64_t eager_iters = 0;         // V-cycles launched outside graphs since the last reset
+    int64_t graph_iters_seen = 0;    // graph V-cycles already folded into the launch count
     // timing and launch accounting
     bool timing = false;
     cudaEvent_t ev[P3MAZE_NSTAGES][2] = {};
@@ -126,16 +158,27 @@ int dalloc(p3maze_ctx* ctx, P** p, size_t bytes) {
         if (rc_) return rc_;                               \
     } while (0)
 
-// Count `k` kernel launches of stage `st`.
-inline void count(p3maze_ctx* ctx, int st, int k = 1) { ctx->launches[st] += k; }
+// Count `k` kernel launches of stage `st` (into the while-body tally while
+// capturing the body).
+inline void count(p3maze_ctx* ctx, int st, int k = 1) {
+    if (ctx->in_body) ctx->body_launches += k;
+    else ctx->launches[st] += k;
+}
+
+// Stage events; while capturing they must be external records so that the
+// graph gets event-record nodes (a plain record only orders the capture).
+void record(p3maze_ctx* ctx, cudaEvent_t ev) {
+    if (ctx->capturing) cudaEventRecordWithFlags(ev, ctx->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ev, ctx->stream);
+}
 
 void stage_begin(p3maze_ctx* ctx, int st) {
-    if (ctx->timing) cudaEventRecord(ctx->ev[st][0], ctx->stream);
+    if (ctx->timing) record(ctx, ctx->ev[st][0]);
 }
 
 void stage_end(p3maze_ctx* ctx, int st) {
     if (ctx->timing) {
-        cudaEventRecord(ctx->ev[st][1], ctx->stream);
+        record(ctx, ctx->ev[st][1]);
         ctx->pending[st] = true;
     }
 }
@@ -191,7 +234,8 @@ int build_cells(p3maze_ctx* ctx) {
     k_cell_scatter<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->cell, ctx->start, ctx->fill, ctx->order);
     k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
     k_gather_sorted<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->order, ctx->r, ctx->Q, ctx->type, ctx->mol,
-                                                         ctx->cell, ctx->xq, ctx->ts, ctx->ms, ctx->cs);
+                                                         ctx->cell, ctx->nc, ctx->lcell, ctx->xq, ctx->xl64,
+                                                         ctx->xl32, ctx->ts, ctx->ms, ctx->cs);
     CKL();
     count(ctx, P3MAZE_ST_CELLS, 5);
     stage_end(ctx, P3MAZE_ST_CELLS);
@@ -214,7 +258,7 @@ int spread_smooth(p3maze_ctx* ctx) {
         const T* src = (const T*)ctx->q;
         for (int k = 0; k < ctx->K; ++k) {
             T* dst = (k == ctx->K - 1) ? (T*)ctx->qs : tmp[k & 1];
-            k_diffuse<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->N, src, dst, (T)ctx->c);
+            k_diffuse<T><<<g3(ctx->N), kB3, 0, s>>>(ctx->N, src, dst, (T)ctx->c);
             src = dst;
         }
         count(ctx, P3MAZE_ST_SMOOTH, ctx->K);
@@ -224,96 +268,149 @@ int spread_smooth(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
+// One V-cycle on M e_l = b_l (A6): levels with more than 16^3 points by grid
+// kernels (red-black Gauss-Seidel, fused residual + restriction, trilinear
+// prolongation), the rest inside one shared-memory block.
 template <typename T>
 int vcycle(p3maze_ctx* ctx, int l) {
     cudaStream_t s = ctx->stream;
     Level& L = ctx->lev[l];
     T* e = (T*)L.e;
     T* b = (T*)L.b;
-    if (l == ctx->nlev - 1) {
-        k_coarse_solve<T><<<1, 512, 0, s>>>(L.n, ctx->gcoarse, b, e);
+    if (L.n <= kBlockLevelMax || l == ctx->nlev - 1) {
+        k_vcycle_block<T><<<1, 1024, ctx->blk_smem, s>>>(L.n, ctx->nlev - l, b, e, ctx->gcoarse, ctx->nu1, ctx->nu2);
         count(ctx, P3MAZE_ST_SOLVE);
         CKL();
         return P3MAZE_OK;
     }
     Level& C = ctx->lev[l + 1];
-    const unsigned gh = nblk(L.pts / 2);
-    CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
+    if (ctx->nu1 == 0) CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
     for (int it = 0; it < ctx->nu1; ++it) {
-        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 0);
-        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 1);
+        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 0, it == 0 ? 1 : 0);
+        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 1, 0);
     }
-    k_resid<T><<<nblk(L.pts), P3_THREADS, 0, s>>>(L.n, e, b, (T*)L.r);
-    k_restrict<T><<<nblk(C.pts), P3_THREADS, 0, s>>>(C.n, (const T*)L.r, (T*)C.b);
-    count(ctx, P3MAZE_ST_SOLVE, 2 * ctx->nu1 + 2);
+    k_resid_restrict<T><<<g3(C.n), kB3, 0, s>>>(C.n, e, b, (T*)C.b);
+    count(ctx, P3MAZE_ST_SOLVE, 2 * ctx->nu1 + 1);
     CKL();
     int rc = vcycle<T>(ctx, l + 1);
     if (rc) return rc;
-    k_prolong_add<T><<<nblk(L.pts), P3_THREADS, 0, s>>>(L.n, (const T*)C.e, e);
+    k_prolong_add<T><<<g3(L.n), kB3, 0, s>>>(L.n, (const T*)C.e, e);
     for (int it = 0; it < ctx->nu2; ++it) {
-        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 1);
-        k_rbgs<T><<<gh, P3_THREADS, 0, s>>>(L.n, e, b, 0);
+        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 1, 0);
+        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 0, 0);
     }
     count(ctx, P3MAZE_ST_SOLVE, 1 + 2 * ctx->nu2);
     CKL();
     return P3MAZE_OK;
 }
 
-// Verlet prediction, constraint residual, multigrid correction to tol and the
-// field update (Eqs. 16-17, 20; supporting information Sec. 1).
 template <typename T>
-int solve_field(p3maze_ctx* ctx, int pred_order, int* iters) {
+void launch_resid_check(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
     cudaStream_t s = ctx->stream;
-    const double hc = ctx->h / (4.0 * kPi);
-    double* phik = ctx->phi[ctx->icur];
-    double* phikm1 = ctx->phi[1 - ctx->icur];
+    k_resid_fine<T><<<g3(ctx->N), kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin,
+                                                ctx->dres);
+    k_mg_check<<<1, 32, 0, s>>>(ctx->dres, ctx->tol, ctx->itmax, ctx->dmg, h, use_handle);
+    count(ctx, P3MAZE_ST_SOLVE, 2);
+}
+
+template <typename T>
+int launch_iteration(p3maze_ctx* ctx) {
+    int rc = vcycle<T>(ctx, 0);
+    if (rc) return rc;
+    k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0], (const T*)ctx->lev[0].e);
+    count(ctx, P3MAZE_ST_SOLVE);
+    return P3MAZE_OK;
+}
+
+// Correction solve to tol (Eqs. 16, 20).  Eagerly: the host reads the check
+// kernel's decision after every residual.  While capturing a graph: a while
+// node whose body is [V-cycle, y += e, residual, check] and whose condition
+// the check kernel sets, so a step needs no host round trip.
+template <typename T>
+int solve_loop(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    if (!ctx->capturing) {
+        for (;;) {
+            launch_resid_check<T>(ctx, 0, 0);
+            CKL();
+            CK(cudaMemcpyAsync(ctx->hmg, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (ctx->hmg->status) break;
+            if (!ctx->hmg->cont) break;
+            int rc = launch_iteration<T>(ctx);
+            if (rc) return rc;
+            ctx->eager_iters += 1;
+            CKL();
+        }
+        return P3MAZE_OK;
+    }
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    launch_resid_check<T>(ctx, h, 1);
+    CKL();
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // populate the body on the second stream
+    CK(cudaStreamBeginCaptureToGraph(ctx->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->body_stream;
+    ctx->in_body = true;
+    ctx->body_launches = 0;
+    int brc = launch_iteration<T>(ctx);
+    launch_resid_check<T>(ctx, h, 1);
+    ctx->in_body = false;
+    ctx->stream = s;
+    if (brc) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(ctx->body_stream, &junk);
+        return brc;
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaGraph_t out = nullptr;
+    CK(cudaStreamEndCapture(ctx->body_stream, &out));
+    if (le != cudaSuccess) return fail(ctx, P3MAZE_ERR_CUDA, std::string("body launch: ") + cudaGetErrorString(le));
+    return P3MAZE_OK;
+}
+
+// Verlet prediction, constraint residual, correction solve and field update
+// (Eqs. 16-17, 20; supporting information Sec. 1).
+template <typename T>
+int solve_field(p3maze_ctx* ctx, int pred_order) {
+    cudaStream_t s = ctx->stream;
+    const int ik = ctx->icur, ikm1 = 1 - ctx->icur;
     stage_begin(ctx, P3MAZE_ST_PREDICT);
     k_sum_partial<T><<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->P, (const T*)ctx->qs, ctx->partial);
     k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_QSUM);
-    k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->N, phik, phikm1, (const T*)ctx->qs, ctx->dscal + S_QSUM,
-                                                     1.0 / (double)ctx->P, hc, ctx->yh[1], ctx->yh[2], ctx->yh[3],
-                                                     pred_order, ctx->sig, ctx->yh[0]);
+    k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->psi[ik], ctx->psi[ikm1], (const T*)ctx->qs,
+                                                     ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, ctx->yh[1],
+                                                     ctx->yh[2], ctx->yh[3], pred_order, ctx->sig, ctx->yh[0]);
     CKL();
     count(ctx, P3MAZE_ST_PREDICT, 3);
     stage_end(ctx, P3MAZE_ST_PREDICT);
     stage_begin(ctx, P3MAZE_ST_SOLVE);
-    int it = 0;
-    double res = 0.0;
-    for (;;) {
-        CK(cudaMemsetAsync(ctx->dres, 0, sizeof(unsigned long long), s));
-        k_resid_fine<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->dres);
-        count(ctx, P3MAZE_ST_SOLVE);
-        CKL();
-        CK(cudaMemcpyAsync(ctx->hres, ctx->dres, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        unsigned long long bits = *ctx->hres;
-        std::memcpy(&res, &bits, sizeof(double));
-        ctx->st.last_residual = res;
-        ctx->st.last_iters = it;
-        *iters = it;
-        if (!(res <= 1e308))
-            return fail(ctx, P3MAZE_ERR_NONFINITE, "non-finite constraint residual");
-        if (res <= ctx->tol) break;
-        if (it >= ctx->itmax) {
-            char buf[160];
-            std::snprintf(buf, sizeof buf, "multigrid did not reach tol %.3g in %d V-cycles (residual %.3g)",
-                          ctx->tol, it, res);
-            return fail(ctx, P3MAZE_ERR_NOT_CONVERGED, buf);
-        }
-        int rc = vcycle<T>(ctx, 0);
-        if (rc) return rc;
-        k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->yh[0], (const T*)ctx->lev[0].e);
-        count(ctx, P3MAZE_ST_SOLVE);
-        CKL();
-        ++it;
-    }
+    int rc = solve_loop<T>(ctx);
+    if (rc) return rc;
     stage_end(ctx, P3MAZE_ST_SOLVE);
     stage_begin(ctx, P3MAZE_ST_UPDATE);
-    k_update<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, phik, phikm1, ctx->yh[0], 4.0 * kPi / ctx->h);
+    k_update<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1], ctx->yh[0],
+                                                    ctx->rfin, (const T*)ctx->qs, ctx->dscal + S_QSUM,
+                                                    1.0 / (double)ctx->P, 4.0 * kPi / ctx->h);
     count(ctx, P3MAZE_ST_UPDATE);
     stage_end(ctx, P3MAZE_ST_UPDATE);
     CKL();
-    ctx->icur = 1 - ctx->icur;
+    ctx->icur = ikm1;
     return P3MAZE_OK;
 }
 
@@ -323,47 +420,78 @@ int forces(p3maze_ctx* ctx) {
     const double halfL2 = 0.25 * ctx->L * ctx->L;
     const bool mixed = ctx->prec == P3MAZE_MIXED;
     stage_begin(ctx, P3MAZE_ST_PAIR);
-#define PAIR(KIND, MIX)                                                                              \
-    k_pair<KIND, MIX><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->ts, ctx->ms, ctx->cs, \
-        ctx->start, ctx->nc, ctx->L, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab, ctx->Fs, ctx->ecs, ctx->evs)
-    switch (ctx->tab.kind * 2 + (mixed ? 1 : 0)) {
-        case 0: PAIR(0, false); break;
-        case 1: PAIR(0, true); break;
-        case 2: PAIR(1, false); break;
-        case 3: PAIR(1, true); break;
-        case 4: PAIR(2, false); break;
-        default: PAIR(2, true); break;
-    }
+    const unsigned pb = nblk(32 * (int64_t)ctx->np);
+#define PAIR(KIND)                                                                                      \
+    do {                                                                                                \
+        if (mixed)                                                                                      \
+            k_pair<KIND, float, float4><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts, ctx->ms, \
+                ctx->cs, ctx->start, ctx->nc, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,   \
+                ctx->Fs, ctx->ecs, ctx->evs);                                                           \
+        else                                                                                            \
+            k_pair<KIND, double, PQ><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts, ctx->ms,    \
+                ctx->cs, ctx->start, ctx->nc, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,   \
+                ctx->Fs, ctx->ecs, ctx->evs);                                                           \
+    } while (0)
+    if (ctx->tab.kind == 1) PAIR(1);
+    else if (ctx->tab.kind == 2) PAIR(2);
+    else PAIR(0);
 #undef PAIR
     count(ctx, P3MAZE_ST_PAIR);
     stage_end(ctx, P3MAZE_ST_PAIR);
     stage_begin(ctx, P3MAZE_ST_GATHER);
     k_gather<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h, ctx->ke,
                                                   ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
-    if (ctx->nmol)
+    count(ctx, P3MAZE_ST_GATHER);
+    if (ctx->nmol) {
         k_water<<<nblk(ctx->nmol), P3_THREADS, 0, s>>>(ctx->nmol, ctx->tri, ctx->r, ctx->Q, ctx->L, ctx->alpha, ctx->ke,
                                                       ctx->kb, ctx->r0, ctx->ka, ctx->th0, ctx->F, ctx->Fb, ctx->eb,
                                                       ctx->ex);
-    count(ctx, P3MAZE_ST_GATHER, ctx->nmol ? 2 : 1);
-    stage_end(ctx, P3MAZE_ST_GATHER);
+        count(ctx, P3MAZE_ST_GATHER);
+    }
     CKL();
     return P3MAZE_OK;
 }
 
 template <typename T>
-int mesh_pipeline(p3maze_ctx* ctx, int pred_order, int* iters) {
+int mesh_pipeline(p3maze_ctx* ctx, int pred_order) {
     int rc = spread_smooth<T>(ctx);
     if (rc) return rc;
-    return solve_field<T>(ctx, pred_order, iters);
+    return solve_field<T>(ctx, pred_order);
 }
 
-int field_and_forces(p3maze_ctx* ctx, int pred_order, int* iters) {
+// Cell list, mesh pipeline and forces at the current positions.  The gather
+// stage stays open: the caller closes it (after the final half kick).
+int field_and_forces(p3maze_ctx* ctx, int pred_order) {
     int rc = build_cells(ctx);
     if (rc) return rc;
-    rc = ctx->prec == P3MAZE_MIXED ? mesh_pipeline<float>(ctx, pred_order, iters)
-                                   : mesh_pipeline<double>(ctx, pred_order, iters);
+    rc = ctx->prec == P3MAZE_MIXED ? mesh_pipeline<float>(ctx, pred_order)
+                                   : mesh_pipeline<double>(ctx, pred_order);
     if (rc) return rc;
     return forces(ctx);
+}
+
+// Copy the solver state to the host and turn a recorded failure into an error.
+int read_solver_state(p3maze_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->hmg, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const MGState& m = *ctx->hmg;
+    ctx->st.last_iters = m.last_iters;
+    ctx->st.last_residual = m.last_res;
+    ctx->st.total_iters = m.total_iters;
+    // V-cycles run inside graphs: add their body launches to the tally
+    const int64_t graph_iters = m.total_iters - ctx->eager_iters;
+    if (graph_iters > ctx->graph_iters_seen) {
+        ctx->launches[P3MAZE_ST_SOLVE] += (graph_iters - ctx->graph_iters_seen) * ctx->body_launches;
+        ctx->graph_iters_seen = graph_iters;
+    }
+    if (m.status == P3MAZE_ERR_NONFINITE) return fail(ctx, P3MAZE_ERR_NONFINITE, "non-finite constraint residual");
+    if (m.status == P3MAZE_ERR_NOT_CONVERGED) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "multigrid did not reach tol %.3g in %d V-cycles (residual %.3g)", ctx->tol,
+                      ctx->itmax, m.last_res);
+        return fail(ctx, P3MAZE_ERR_NOT_CONVERGED, buf);
+    }
+    return P3MAZE_OK;
 }
 
 // Full solve from phi = 0 at the current positions (phi^{-1} = phi^0, empty
@@ -371,41 +499,157 @@ int field_and_forces(p3maze_ctx* ctx, int pred_order, int* iters) {
 int initialise_field(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     const size_t mb = sizeof(double) * ctx->P;
-    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(ctx->phi[k], 0, mb, s));
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaMemsetAsync(ctx->phi[k], 0, mb, s));
+        CK(cudaMemsetAsync(ctx->psi[k], 0, mb, s));
+    }
     for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(ctx->yh[k], 0, mb, s));
+    CK(cudaMemsetAsync(ctx->dmg, 0, sizeof(MGState), s));
+    CK(cudaMemsetAsync(ctx->dres, 0, sizeof(unsigned long long), s));
     ctx->nhist = 0;
-    int it = 0;
-    int rc = field_and_forces(ctx, 0, &it);
-    ctx->st.init_iters = it;
+    const bool was_timing = ctx->timing;
+    ctx->timing = false;
+    int rc = field_and_forces(ctx, 0);
+    ctx->timing = was_timing;
+    if (rc) return rc;
+    rc = read_solver_state(ctx);
+    ctx->st.init_iters = ctx->hmg->last_iters;
     if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->phi[1 - ctx->icur], ctx->phi[ctx->icur], mb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(ctx->psi[1 - ctx->icur], ctx->psi[ctx->icur], mb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(ctx->yh[0], 0, mb, s));
+    // the initial solve is not part of the step statistics
+    CK(cudaMemsetAsync(ctx->dmg, 0, sizeof(MGState), s));
+    CK(cudaStreamSynchronize(s));
+    ctx->eager_iters = 0;
+    ctx->graph_iters_seen = 0;
+    ctx->st.total_iters = 0;
     return P3MAZE_OK;
 }
 
-int step_once(p3maze_ctx* ctx) {
+// The launches of one MD step (eager, or recorded into a graph): kick/drift,
+// field and forces, closing kick.
+int step_body(p3maze_ctx* ctx, int order) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_INTEGRATE);
     k_kick_drift<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->F, ctx->hdt_acc, ctx->dt, ctx->L);
     count(ctx, P3MAZE_ST_INTEGRATE);
+    stage_end(ctx, P3MAZE_ST_INTEGRATE);
     CKL();
-    int it = 0;
-    const int order = std::min(ctx->pred, ctx->nhist);
-    int rc = field_and_forces(ctx, order, &it);
+    int rc = field_and_forces(ctx, order);
     if (rc) return rc;
+    k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
+    count(ctx, P3MAZE_ST_GATHER);
+    stage_end(ctx, P3MAZE_ST_GATHER);
+    CKL();
     // the converged correction becomes y^{k+1}; the oldest history buffer is reused
     double* oldest = ctx->yh[3];
     ctx->yh[3] = ctx->yh[2];
     ctx->yh[2] = ctx->yh[1];
     ctx->yh[1] = ctx->yh[0];
     ctx->yh[0] = oldest;
+    return P3MAZE_OK;
+}
+
+void destroy_graphs(p3maze_ctx* ctx) {
+    for (StepGraph& G : ctx->graphs) {
+        if (G.x) cudaGraphExecDestroy(G.x);
+        if (G.g) cudaGraphDestroy(G.g);
+        G = StepGraph();
+    }
+}
+
+// Record one steady-state step (full predictor history) for the current
+// pointer phase.  The pointer state is restored afterwards.
+int capture_graph(p3maze_ctx* ctx, StepGraph& G) {
+    cudaStream_t s = ctx->stream;
+    int64_t saved[P3MAZE_NSTAGES];
+    bool saved_pending[P3MAZE_NSTAGES];
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+        saved[st] = ctx->launches[st];
+        saved_pending[st] = ctx->pending[st];
+        ctx->launches[st] = 0;
+        ctx->pending[st] = false;
+    }
+    const int icur = ctx->icur;
+    double* yh[4];
+    std::memcpy(yh, ctx->yh, sizeof yh);
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    int rc = step_body(ctx, ctx->pred);
+    ctx->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    ctx->icur = icur;
+    std::memcpy(ctx->yh, yh, sizeof yh);
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+        G.launches[st] = ctx->launches[st];
+        G.timed[st] = ctx->pending[st];
+        ctx->launches[st] = saved[st];
+        ctx->pending[st] = saved_pending[st];
+    }
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, P3MAZE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&G.x, g, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(ctx, P3MAZE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    }
+    G.g = g;
+    G.icur = icur;
+    std::memcpy(G.yh, yh, sizeof yh);
+    G.valid = true;
+    return P3MAZE_OK;
+}
+
+int step_graph(p3maze_ctx* ctx) {
+    StepGraph* G = nullptr;
+    for (StepGraph& sg : ctx->graphs)
+        if (sg.valid && sg.icur == ctx->icur && std::memcmp(sg.yh, ctx->yh, sizeof sg.yh) == 0) G = &sg;
+    if (!G) {
+        for (StepGraph& sg : ctx->graphs)
+            if (!sg.valid) {
+                G = &sg;
+                break;
+            }
+        if (!G) {
+            destroy_graphs(ctx);
+            G = &ctx->graphs[0];
+        }
+        int rc = capture_graph(ctx, *G);
+        if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(G->x, ctx->stream));
+    for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+        ctx->launches[st] += G->launches[st];
+        if (G->timed[st]) ctx->pending[st] = true;
+    }
+    // pointer rotation identical to step_body
+    ctx->icur = 1 - ctx->icur;
+    double* oldest = ctx->yh[3];
+    ctx->yh[3] = ctx->yh[2];
+    ctx->yh[2] = ctx->yh[1];
+    ctx->yh[1] = ctx->yh[0];
+    ctx->yh[0] = oldest;
+    return P3MAZE_OK;
+}
+
+int step_once(p3maze_ctx* ctx) {
+    int rc;
+    if (ctx->use_graphs && ctx->nhist >= ctx->pred) {
+        rc = step_graph(ctx);
+    } else {
+        rc = step_body(ctx, std::min(ctx->pred, ctx->nhist));
+    }
+    if (rc) return rc;
     ctx->nhist = std::min(ctx->nhist + 1, 3);
-    k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
-    count(ctx, P3MAZE_ST_INTEGRATE);
-    stage_end(ctx, P3MAZE_ST_INTEGRATE);
-    CKL();
     ctx->st.steps += 1;
-    ctx->st.total_iters += it;
     return collect_timing(ctx);
 }
 
@@ -423,15 +667,20 @@ int validate_mesh(int N, int* nlev, int* ncoarse) {
 }
 
 void release(p3maze_ctx* ctx) {
+    destroy_graphs(ctx);
     for (int st = 0; st < P3MAZE_NSTAGES; ++st)
         for (int k = 0; k < 2; ++k)
             if (ctx->ev[st][k]) cudaEventDestroy(ctx->ev[st][k]);
     for (void* p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
     if (ctx->hscal) cudaFreeHost(ctx->hscal);
-    if (ctx->hres) cudaFreeHost(ctx->hres);
+    if (ctx->hmg) cudaFreeHost(ctx->hmg);
     ctx->hscal = nullptr;
-    ctx->hres = nullptr;
+    ctx->hmg = nullptr;
+    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    ctx->body_stream = nullptr;
+    ctx->stream = nullptr;
 }
 
 int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const double* vel) {
@@ -439,6 +688,13 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     const bool mixed = p->precision == P3MAZE_MIXED;
     const size_t tb = mixed ? sizeof(float) : sizeof(double);
     CK(cudaGetDevice(&ctx->device));
+    if (!ctx->stream) {
+        // graphs cannot be captured on the legacy default stream; a blocking
+        // stream keeps the legacy stream's ordering with other work
+        CK(cudaStreamCreate(&ctx->stream));
+        ctx->own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking));
     // particle arrays
     ALLOC(ctx->r, 24 * (size_t)n);
     ALLOC(ctx->v, 24 * (size_t)n);
@@ -455,6 +711,8 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     ALLOC(ctx->ms, 4 * (size_t)n);
     ALLOC(ctx->cs, 4 * (size_t)n);
     ALLOC(ctx->xq, sizeof(PQ) * (size_t)n);
+    ALLOC(ctx->xl64, sizeof(PQ) * (size_t)n);
+    ALLOC(ctx->xl32, sizeof(float4) * (size_t)n);
     ALLOC(ctx->Fs, 24 * (size_t)n);
     ALLOC(ctx->ecs, 8 * (size_t)n);
     ALLOC(ctx->evs, 8 * (size_t)n);
@@ -466,7 +724,11 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     const int64_t P = ctx->P;
     ALLOC(ctx->q, tb * P);
     ALLOC(ctx->qs, tb * P);
-    for (int k = 0; k < 2; ++k) ALLOC(ctx->phi[k], 8 * P);
+    for (int k = 0; k < 2; ++k) {
+        ALLOC(ctx->phi[k], 8 * P);
+        ALLOC(ctx->psi[k], 8 * P);
+    }
+    ALLOC(ctx->rfin, 8 * P);
     for (int k = 0; k < 4; ++k) ALLOC(ctx->yh[k], 8 * P);
     ALLOC(ctx->sig, 8 * P);
     ctx->lev.resize(ctx->nlev);
@@ -477,17 +739,30 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         L.pts = (int64_t)nn * nn * nn;
         ALLOC(L.e, tb * L.pts);
         ALLOC(L.b, tb * L.pts);
-        if (l < ctx->nlev - 1 || l == 0) ALLOC(L.r, tb * L.pts);
+        if (l == 0) ALLOC(L.r, tb * L.pts);  // smoothing ping-pong buffer
         nn /= 2;
+    }
+    // the shared-memory V-cycle starts at the first level with n <= 16
+    {
+        int l0 = 0;
+        while (l0 < ctx->nlev - 1 && ctx->lev[l0].n > kBlockLevelMax) ++l0;
+        ctx->blk_smem = vcycle_block_smem(ctx->lev[l0].n, ctx->nlev - l0, tb);
+        cudaError_t ea = mixed ? cudaFuncSetAttribute(k_vcycle_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)ctx->blk_smem)
+                               : cudaFuncSetAttribute(k_vcycle_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)ctx->blk_smem);
+        if (ea != cudaSuccess)
+            return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory for the block V-cycle: ") + cudaGetErrorString(ea));
     }
     std::vector<double> g = coarse_green(ctx->lev.back().n);
     ALLOC(ctx->gcoarse, 8 * g.size());
     ALLOC(ctx->partial, 8 * 1024);
     ALLOC(ctx->dscal, 8 * S_NSCAL);
     ALLOC(ctx->dres, 8);
+    ALLOC(ctx->dmg, sizeof(MGState));
     {
         cudaError_t e1 = cudaMallocHost((void**)&ctx->hscal, 8 * S_NSCAL);
-        cudaError_t e2 = cudaMallocHost((void**)&ctx->hres, 8);
+        cudaError_t e2 = cudaMallocHost((void**)&ctx->hmg, sizeof(MGState));
         if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ctx, P3MAZE_ERR_OOM, "cudaMallocHost failed");
     }
     cudaStream_t s = ctx->stream;
@@ -638,6 +913,7 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->nc = std::max(1, (int)std::floor(L / (0.5 * p->r_cut)));
     ctx->ncell = ctx->nc * ctx->nc * ctx->nc;
     ctx->inv_cell = ctx->nc / L;
+    ctx->lcell = L / ctx->nc;
     ctx->nlev = nlev;
     ctx->tab = tab;
     ctx->nmol = nmol;
@@ -680,7 +956,7 @@ int p3maze_step(p3maze_ctx* ctx, int32_t nsteps) {
         int rc = step_once(ctx);
         if (rc) return rc;
     }
-    return P3MAZE_OK;
+    return read_solver_state(ctx);
 }
 
 int p3maze_reinit(p3maze_ctx* ctx) {
@@ -736,6 +1012,7 @@ int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
 
 int p3maze_get_stats(p3maze_ctx* ctx, p3maze_stats* out) {
     if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    read_solver_state(ctx);
     *out = ctx->st;
     return P3MAZE_OK;
 }
@@ -826,6 +1103,7 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
         for (int st = 0; st < P3MAZE_NSTAGES; ++st)
             for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ctx->ev[st][k]));
     CK(cudaStreamSynchronize(ctx->stream));
+    if ((enable != 0) != ctx->timing) destroy_graphs(ctx);  // event-record nodes differ
     ctx->timing = enable != 0;
     for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
         ctx->stage_ms[st] = 0.0;

@@ -121,19 +121,26 @@ __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __restric
     }
 }
 
-// Gather particle data into cell order: xq = (x, y, z, Q).
+// Gather particle data into cell order: xq = (x, y, z, Q) and the
+// cell-local coordinates x - c l (FP64 and FP32 copies) used by the pair kernel.
 __global__ void k_gather_sorted(int n, const int* __restrict__ order, const double* __restrict__ r,
                                 const double* __restrict__ Q, const int* __restrict__ type,
-                                const int* __restrict__ mol, const int* __restrict__ cell,
-                                PQ* __restrict__ xq, int* __restrict__ ts, int* __restrict__ ms,
+                                const int* __restrict__ mol, const int* __restrict__ cell, int nc,
+                                double lcell, PQ* __restrict__ xq, PQ* __restrict__ xl64,
+                                float4* __restrict__ xl32, int* __restrict__ ts, int* __restrict__ ms,
                                 int* __restrict__ cs) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int i = order[s];
-    xq[s] = PQ{r[3 * i], r[3 * i + 1], r[3 * i + 2], Q[i]};
+    const int c = cell[i];
+    const double x = r[3 * i], y = r[3 * i + 1], z = r[3 * i + 2], q = Q[i];
+    xq[s] = PQ{x, y, z, q};
+    const double lx = x - (c % nc) * lcell, ly = y - ((c / nc) % nc) * lcell, lz = z - (c / (nc * nc)) * lcell;
+    xl64[s] = PQ{lx, ly, lz, q};
+    xl32[s] = make_float4((float)lx, (float)ly, (float)lz, (float)q);
     ts[s] = type ? type[i] : 0;
     ms[s] = mol ? mol[i] : -1;
-    cs[s] = cell[i];
+    cs[s] = c;
 }
 
 // ---------------------------------------------------------------- pair forces
@@ -143,127 +150,115 @@ struct SRTable {
     double p[5][16];
 };
 
+// Per-pair screened Coulomb (Eq. 19 with alpha = 1/(sqrt2 sigma); energy
+// Eq. 5) and the non-Coulomb term.  Returns F/r scaled by ke for the Coulomb
+// part; energies are accumulated unscaled.
+template <int KIND, typename R>
+__device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const SRTable& tab, int k, R& ec, R& ev,
+                                        R& fvdw) {
+    const R ir = (R)1 / sqrt(r2);
+    const R rr = r2 * ir;
+    const R ar = alpha * rr;
+    const R erfcv = erfc(ar);
+    const R ex = exp(-ar * ar);
+    const R ir2 = ir * ir;
+    ec = qq * erfcv * ir;
+    ev = (R)0;
+    fvdw = (R)0;
+    if (KIND == 1) {
+        const R A = (R)tab.p[0][k], rho = (R)tab.p[1][k], sg = (R)tab.p[2][k];
+        const R C = (R)tab.p[3][k], D = (R)tab.p[4][k];
+        const R eb = A * exp((sg - rr) / rho);
+        const R ir6 = ir2 * ir2 * ir2, ir8 = ir6 * ir2;
+        ev = eb - C * ir6 - D * ir8;
+        fvdw = (eb / rho - (R)6 * C * ir6 * ir - (R)8 * D * ir8 * ir) * ir;
+    } else if (KIND == 2) {
+        const R eps = (R)tab.p[0][k];
+        if (eps != (R)0) {
+            const R sg = (R)tab.p[1][k];
+            const R sr2 = sg * sg * ir2;
+            const R sr6 = sr2 * sr2 * sr2;
+            ev = (R)4 * eps * (sr6 * sr6 - sr6);
+            fvdw = (R)24 * eps * ((R)2 * sr6 * sr6 - sr6) * ir2;
+        }
+    }
+    return qq * (erfcv * ir + (R)kTwoOverSqrtPi * alpha * ex) * ir2;
+}
+
 // Short-range forces on particle s (cell order) from every particle image
-// within r_cut, found in the 5x5x5 block of cells of edge >= r_cut/2 around
-// it: the erfc-screened Coulomb force of Eq. 19 (written with alpha =
-// 1/(sqrt2 sigma)) plus the Born-Mayer or Lennard-Jones term.  Pairs within
-// one molecule at separation below L/2 (the nearest image) are excluded.
-// Writes per-particle force and half of its pair energies; no atomics.
-// MIXED evaluates the pair functions in FP32 from an FP64 separation and
-// accumulates in FP64.
-template <int KIND, bool MIXED>
+// within r_cut, found in the 5x5x5 block of cells of edge l >= r_cut/2 around
+// it: Eq. 19 plus the Born-Mayer or Lennard-Jones term.  One warp per
+// particle, each lane walking a share of the 125 neighbour cells; a
+// particle's neighbour j in unwrapped cell c_i + d sits at the image
+// (c_i + d) l + x_j,loc, so the separation is x_i,loc - x_j,loc - d l with no
+// periodic shift.  Pairs within one molecule closer than L/2 (the nearest
+// image) are excluded.  Writes the force and half of the pair energies of s;
+// no atomics.  R is the arithmetic type (double, or float in mixed mode with
+// FP32 cell-local coordinates and FP64 accumulation across lanes).
+template <int KIND, typename R, typename LQ>
 __global__ void __launch_bounds__(P3_THREADS)
-k_pair(int n, const PQ* __restrict__ xq, const int* __restrict__ ts, const int* __restrict__ ms,
-       const int* __restrict__ cs, const int* __restrict__ start, int nc, double L, double rc2,
+k_pair(int n, const LQ* __restrict__ xl, const int* __restrict__ ts, const int* __restrict__ ms,
+       const int* __restrict__ cs, const int* __restrict__ start, int nc, double lcell, double rc2,
        double halfL2, double alpha, double ke, SRTable tab, double* __restrict__ Fs,
        double* __restrict__ ecs, double* __restrict__ evs) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (s >= n) return;
-    const PQ pi = xq[s];
+    const LQ pi = xl[s];
     const int ti = ts[s];
     const int mi = ms[s];
     const int ci = cs[s];
     const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
-    double fx = 0.0, fy = 0.0, fz = 0.0, ec = 0.0, ev = 0.0;
-    for (int dz = -2; dz <= 2; ++dz) {
-        int zz = cz + dz, kz = 0;
-        while (zz < 0) { zz += nc; --kz; }
-        while (zz >= nc) { zz -= nc; ++kz; }
-        for (int dy = -2; dy <= 2; ++dy) {
-            int yy = cy + dy, ky = 0;
-            while (yy < 0) { yy += nc; --ky; }
-            while (yy >= nc) { yy -= nc; ++ky; }
-            for (int dx = -2; dx <= 2; ++dx) {
-                int xx = cx + dx, kx = 0;
-                while (xx < 0) { xx += nc; --kx; }
-                while (xx >= nc) { xx -= nc; ++kx; }
-                const bool home = (kx | ky | kz) == 0;
-                const double sx = kx * L, sy = ky * L, sz = kz * L;
-                const int c = (zz * nc + yy) * nc + xx;
-                const int e = start[c + 1];
-                for (int t = start[c]; t < e; ++t) {
-                    if (home && t == s) continue;
-                    const PQ pj = xq[t];
-                    const double ddx = pi.x - (pj.x + sx);
-                    const double ddy = pi.y - (pj.y + sy);
-                    const double ddz = pi.z - (pj.z + sz);
-                    const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 >= rc2) continue;
-                    if (mi >= 0 && ms[t] == mi && r2 < halfL2) continue;
-                    const double qq = pi.w * pj.w;
-                    double fr, e_c, e_v = 0.0, f_v = 0.0;
-                    if (MIXED) {
-                        const float r2f = (float)r2;
-                        const float ir = rsqrtf(r2f);
-                        const float rr = r2f * ir;
-                        const float ar = (float)alpha * rr;
-                        const float erfcv = erfcf(ar);
-                        const float ex = expf(-ar * ar);
-                        const float ir2 = ir * ir;
-                        e_c = (double)((float)qq * erfcv * ir);
-                        fr = (double)((float)qq * (erfcv * ir + (float)(kTwoOverSqrtPi * alpha) * ex) * ir2);
-                        if (KIND == 1) {
-                            const int k = ti * tab.nt + ts[t];
-                            const float A = (float)tab.p[0][k], rho = (float)tab.p[1][k], sg = (float)tab.p[2][k];
-                            const float C = (float)tab.p[3][k], D = (float)tab.p[4][k];
-                            const float eb = A * expf((sg - rr) / rho);
-                            const float ir6 = ir2 * ir2 * ir2, ir8 = ir6 * ir2;
-                            e_v = (double)(eb - C * ir6 - D * ir8);
-                            f_v = (double)((eb / rho - 6.0f * C * ir6 * ir - 8.0f * D * ir8 * ir) * ir);
-                        } else if (KIND == 2) {
-                            const int k = ti * tab.nt + ts[t];
-                            const float eps = (float)tab.p[0][k];
-                            if (eps != 0.0f) {
-                                const float sg = (float)tab.p[1][k];
-                                const float sr2 = sg * sg * ir2;
-                                const float sr6 = sr2 * sr2 * sr2;
-                                e_v = (double)(4.0f * eps * (sr6 * sr6 - sr6));
-                                f_v = (double)(24.0f * eps * (2.0f * sr6 * sr6 - sr6) * ir2);
-                            }
-                        }
-                    } else {
-                        const double rr = sqrt(r2);
-                        const double ir = 1.0 / rr;
-                        const double ar = alpha * rr;
-                        const double erfcv = erfc(ar);
-                        const double ex = exp(-ar * ar);
-                        const double ir2 = ir * ir;
-                        e_c = qq * erfcv * ir;
-                        fr = qq * (erfcv * ir + kTwoOverSqrtPi * alpha * ex) * ir2;
-                        if (KIND == 1) {
-                            const int k = ti * tab.nt + ts[t];
-                            const double rho = tab.p[1][k];
-                            const double eb = tab.p[0][k] * exp((tab.p[2][k] - rr) / rho);
-                            const double ir6 = ir2 * ir2 * ir2, ir8 = ir6 * ir2;
-                            e_v = eb - tab.p[3][k] * ir6 - tab.p[4][k] * ir8;
-                            f_v = (eb / rho - 6.0 * tab.p[3][k] * ir6 * ir - 8.0 * tab.p[4][k] * ir8 * ir) * ir;
-                        } else if (KIND == 2) {
-                            const int k = ti * tab.nt + ts[t];
-                            const double eps = tab.p[0][k];
-                            if (eps != 0.0) {
-                                const double sg = tab.p[1][k];
-                                const double sr2 = sg * sg * ir2;
-                                const double sr6 = sr2 * sr2 * sr2;
-                                e_v = 4.0 * eps * (sr6 * sr6 - sr6);
-                                f_v = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) * ir2;
-                            }
-                        }
-                    }
-                    const double f = ke * fr + f_v;
-                    fx += f * ddx;
-                    fy += f * ddy;
-                    fz += f * ddz;
-                    ec += e_c;
-                    ev += e_v;
-                }
-            }
+    const R lc = (R)lcell, r2c = (R)rc2, hl2 = (R)halfL2, al = (R)alpha;
+    R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
+    for (int o = lane; o < 125; o += 32) {
+        const int dx = o % 5 - 2, dy = (o / 5) % 5 - 2, dz = o / 25 - 2;
+        int xx = cx + dx, yy = cy + dy, zz = cz + dz;
+        while (xx < 0) xx += nc;
+        while (xx >= nc) xx -= nc;
+        while (yy < 0) yy += nc;
+        while (yy >= nc) yy -= nc;
+        while (zz < 0) zz += nc;
+        while (zz >= nc) zz -= nc;
+        const bool home = dx == 0 && dy == 0 && dz == 0;
+        const R ox = (R)dx * lc, oy = (R)dy * lc, oz = (R)dz * lc;
+        const int c = (zz * nc + yy) * nc + xx;
+        const int e = start[c + 1];
+        for (int t = start[c]; t < e; ++t) {
+            if (home && t == s) continue;
+            const LQ pj = xl[t];
+            const R ddx = (R)pi.x - (R)pj.x - ox;
+            const R ddy = (R)pi.y - (R)pj.y - oy;
+            const R ddz = (R)pi.z - (R)pj.z - oz;
+            const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (r2 >= r2c) continue;
+            if (mi >= 0 && ms[t] == mi && r2 < hl2) continue;
+            R e_c, e_v, f_v;
+            const R fr = pair_terms<KIND, R>(r2, (R)pi.w * (R)pj.w, al, tab, ti * tab.nt + ts[t], e_c, e_v, f_v);
+            const R f = (R)ke * fr + f_v;
+            fx += f * ddx;
+            fy += f * ddy;
+            fz += f * ddz;
+            ec += e_c;
+            ev += e_v;
         }
     }
-    Fs[3 * s + 0] = fx;
-    Fs[3 * s + 1] = fy;
-    Fs[3 * s + 2] = fz;
-    ecs[s] = 0.5 * ke * ec;
-    evs[s] = 0.5 * ev;
+    double dfx = fx, dfy = fy, dfz = fz, dec = ec, dev = ev;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        dfx += __shfl_xor_sync(0xffffffffu, dfx, w);
+        dfy += __shfl_xor_sync(0xffffffffu, dfy, w);
+        dfz += __shfl_xor_sync(0xffffffffu, dfz, w);
+        dec += __shfl_xor_sync(0xffffffffu, dec, w);
+        dev += __shfl_xor_sync(0xffffffffu, dev, w);
+    }
+    if (lane == 0) {
+        Fs[3 * s + 0] = dfx;
+        Fs[3 * s + 1] = dfy;
+        Fs[3 * s + 2] = dfz;
+        ecs[s] = 0.5 * ke * dec;
+        evs[s] = 0.5 * dev;
+    }
 }
 
 // SPC/Fw intramolecular terms, one thread per (h1, o, h2) molecule: harmonic
