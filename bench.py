@@ -248,6 +248,8 @@ def run_ours(args) -> int:
                                      stream=stream.cuda_stream)
 
     ctx = make(args.precision)
+    if args.no_graphs:
+        ctx.set_graphs(False)
     ctx.step(args.warmup)
     torch.cuda.synchronize()
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
@@ -331,7 +333,7 @@ def run_ours(args) -> int:
         "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": DATA,
-        "config": workload_config(prm, args.precision),
+        "config": dict(workload_config(prm, args.precision), graphs=not args.no_graphs),
         "lr_step_us": sum(stage_us[k] for k in lr_stages),
         "stage_us": stage_us, "mg_iters_per_step": iters,
         "gpu_launches": int(tm["total_launches"]),
@@ -353,6 +355,8 @@ def main() -> int:
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel eagerly (profiling: ncu does not list kernels of graph while nodes)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -226,6 +226,13 @@ int p3maze_set_timing(p3maze_ctx *ctx, int32_t enable);
 /* Per-stage device time and kernel-launch counts since the last reset.       */
 int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
 
+/* Steady-state steps (full multiplier history) replay captured CUDA graphs by
+ * default (enable = 1): one graph launch per step with the multigrid loop as
+ * a device-side while node.  enable = 0 issues every kernel individually (same
+ * kernels and launch shapes), e.g. for profilers that do not list kernels of
+ * conditional graph nodes.                                                    */
+int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
+
 /* Message of the last failing call on ctx (or of the last failing init when
  * ctx is NULL).  Never NULL.                                                   */
 const char *p3maze_last_error(const p3maze_ctx *ctx);

@@ -39,7 +39,11 @@ __device__ __forceinline__ void bspline4(double t, double w[4]) {
 
 // Base node (floor(u) - 1, wrapped into [0, n)) and weights along one axis.
 __device__ __forceinline__ int bspline_axis(double x, double inv_h, int n, double w[4]) {
-    const double u = x * inv_h;
+    double u = x * inv_h;
+    // positions are wrapped into [0, L); a non-finite one maps to node 0 so
+    // every access stays in bounds (the NaN charge weight then surfaces as a
+    // non-finite constraint residual)
+    if (!(u >= 0.0 && u <= (double)n)) u = 0.0;
     const double f = floor(u);
     bspline4(u - f, w);
     int b = (int)f - 1;

@@ -62,15 +62,44 @@ __device__ __forceinline__ bool xyz3(int n, int& x, int& y, int& z) {
 
 // ---------------------------------------------------------------- smoothing
 // One explicit diffusion step out = in + c M in (reading of Sec. 2's
-// diffusion-based smoothing).
-template <typename T>
+// diffusion-based smoothing).  Each thread marches ZC planes along z keeping
+// the z neighbours in registers; x and y neighbours come through L1.  With
+// SUM (the last step) the block also writes the FP64 sum of
+// its outputs, from which the neutrality mean is formed.
+#define P3_ZC 16
+
+template <typename T, bool SUM>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
-k_diffuse(int n, const T* __restrict__ in, T* __restrict__ out, T c) {
-    int x, y, z;
-    if (!xyz3(n, x, y, z)) return;
-    const int i = (z * n + y) * n + x;
-    const T v = in[i];
-    out[i] = v + c * (nb6(in, x, y, z, n) - (T)6 * v);
+k_diffuse(int n, const T* __restrict__ in, T* __restrict__ out, T c, double* __restrict__ partial) {
+    const int x = blockIdx.x * P3_BX + threadIdx.x;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int z0 = blockIdx.z * P3_ZC;
+    const int z1 = min(z0 + P3_ZC, n);
+    double acc = 0.0;
+    if (x < n && y < n) {
+        const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        const int plane = n * n;
+        const int col = y * n + x;
+        T vm = in[(z0 == 0 ? n - 1 : z0 - 1) * plane + col];
+        T vc = in[z0 * plane + col];
+        for (int z = z0; z < z1; ++z) {
+            const int zp = z == n - 1 ? 0 : z + 1;
+            const T vp = in[zp * plane + col];
+            const int base = z * plane;
+            const T sxy = in[base + y * n + xm] + in[base + y * n + xp] + in[base + ym * n + x] + in[base + yp * n + x];
+            const T v = vc + c * (sxy + vm + vp - (T)6 * vc);
+            out[base + col] = v;
+            if (SUM) acc += (double)v;
+            vm = vc;
+            vc = vp;
+        }
+    }
+    if (SUM) {
+        acc = block_sum(acc);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+    }
 }
 
 // ---------------------------------------------------------------- reductions
@@ -138,26 +167,31 @@ k_predict(int64_t m, const double* __restrict__ psik, const double* __restrict__
 
 // Fine-level FP64 residual r = sigma_p - M y (Eq. 20's argument): kept in
 // FP64 (rfin, for the psi update) and in the bulk type (input of the
-// correction V-cycle), with max_n |r_n| folded into *rmax by an atomic max on
-// the bit pattern (non-negative doubles order like integers).  NaN or Inf is
-// recorded as +Inf.
+// correction V-cycle).  Each block walks z planes blockIdx.z, +gridDim.z, ...
+// and writes max |r| over its points to bmax (NaN or Inf recorded as +Inf);
+// the check kernel reduces those block maxima.
 template <typename T>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_fine(int n, const double* __restrict__ yv, const double* __restrict__ sig, T* __restrict__ r,
-             double* __restrict__ rfin, unsigned long long* __restrict__ rmax) {
-    int x, y, z;
-    double a = 0.0;
-    if (xyz3(n, x, y, z)) {
-        const int i = (z * n + y) * n + x;
-        const double res = sig[i] - (nb6(yv, x, y, z, n) - 6.0 * yv[i]);
-        r[i] = (T)res;
-        rfin[i] = res;
-        a = fabs(res);
-        if (!(a <= 1.0e308)) a = __longlong_as_double(0x7ff0000000000000LL);
+             double* __restrict__ rfin, double* __restrict__ bmax) {
+    const int x = blockIdx.x * P3_BX + threadIdx.x;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    float a = 0.0f;
+    if (x < n && y < n) {
+        for (int z = blockIdx.z; z < n; z += gridDim.z) {
+            const int i = (z * n + y) * n + x;
+            const double res = sig[i] - (nb6(yv, x, y, z, n) - 6.0 * yv[i]);
+            r[i] = (T)res;
+            rfin[i] = res;
+            // the max-norm is taken on the FP32-rounded |r| (relative error
+            // 6e-8, far inside any tolerance); NaN becomes +Inf
+            const float v = fabsf((float)res);
+            a = (v == v) ? fmaxf(a, v) : __int_as_float(0x7f800000);
+        }
     }
-    a = block_max(a);
+    const double am = block_max((double)a);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        atomicMax(rmax, (unsigned long long)__double_as_longlong(a));
+        bmax[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = am;
 }
 
 // y += e (FP64 accumulation of the correction).
@@ -174,16 +208,20 @@ template <typename T>
 __global__ void k_update(int64_t m, const double* __restrict__ phik, double* __restrict__ phikm1,
                          double* __restrict__ psikm1, const double* __restrict__ yv,
                          const double* __restrict__ rfin, const T* __restrict__ qs,
-                         const double* __restrict__ qsum, double inv_pts, double coef) {
+                         const double* __restrict__ qsum, double inv_pts, double coef, float* __restrict__ phi32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    phikm1[i] = 2.0 * phik[i] - phikm1[i] - coef * yv[i];
+    const double p = 2.0 * phik[i] - phikm1[i] - coef * yv[i];
+    phikm1[i] = p;
     psikm1[i] = rfin[i] - ((double)qs[i] - qsum[0] * inv_pts);
+    // FP32 copy for the mixed-precision interpolation, relative to one node
+    // value of phi^k so the constant mode of phi (a gauge freedom) never eats
+    // FP32 digits; the central differences are unchanged by it
+    if (phi32 != nullptr) phi32[i] = (float)(p - phik[0]);
 }
 
-// Convergence control of the correction solve (Eq. 20), one thread:
-// reads max|r| of the residual just computed, resets the accumulator, and
-// decides whether another V-cycle runs (res > tol, finite, fewer than itmax
+// Convergence control of the correction solve (Eq. 20), one block: reduces
+// the block maxima of the residual just computed to max|r| and decides whether another V-cycle runs (res > tol, finite, fewer than itmax
 // cycles so far).  Records the outcome in MGState; a failure code is sticky.
 // With use_handle the decision also drives the graph's while node.
 struct MGState {
@@ -196,12 +234,13 @@ struct MGState {
     long long solves;
 };
 
-__global__ void k_mg_check(unsigned long long* __restrict__ rmax, double tol, int itmax,
-                           MGState* __restrict__ st, cudaGraphConditionalHandle handle, int use_handle) {
+__global__ void __launch_bounds__(1024)
+k_mg_check(const double* __restrict__ bmax, int nb, double tol, int itmax, MGState* __restrict__ st,
+           cudaGraphConditionalHandle handle, int use_handle) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a = fmax(a, bmax[i]);
+    const double res = block_max(a);
     if (threadIdx.x != 0) return;
-    const unsigned long long bits = *rmax;
-    *rmax = 0ull;
-    const double res = __longlong_as_double((long long)bits);
     int cont = 0;
     if (!(res <= 1.0e308)) {
         if (st->status == 0) st->status = -5;
@@ -305,22 +344,51 @@ k_prolong_add(int n, const T* __restrict__ ec, T* __restrict__ ef) {
 // every array in shared memory: red-black Gauss-Seidel, fused residual and
 // restriction, the exact FP64 pseudo-inverse solve on the coarsest level and
 // trilinear prolongation.  Input b (level l0, global), output e (global).
-template <typename T>
-__device__ void blk_rbgs(int n, T* e, const T* b, int color) {
-    const int half = n >> 1, m = half * n * n;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const int tx = t % half, yz = t / half, y = yz % n, z = yz / n;
-        const int x = 2 * tx + ((y + z + color) & 1);
-        e[(z * n + y) * n + x] = (nb6(e, x, y, z, n) - b[(z * n + y) * n + x]) * (T)(1.0 / 6.0);
+struct BlkLevel {
+    int n, lg;  // lg = log2(n) for powers of two, else -1
+};
+
+__device__ __forceinline__ void dec3(int p, const BlkLevel& L, int& x, int& y, int& z) {
+    if (L.lg >= 0) {
+        x = p & (L.n - 1);
+        y = (p >> L.lg) & (L.n - 1);
+        z = p >> (2 * L.lg);
+    } else {
+        x = p % L.n;
+        const int q = p / L.n;
+        y = q % L.n;
+        z = q / L.n;
     }
 }
 
 template <typename T>
-__device__ void blk_resid_restrict(int nc, const T* e, const T* b, T* bc) {
-    const int n = 2 * nc, m = nc * nc * nc;
+__device__ void blk_rbgs(const BlkLevel& L, T* e, const T* b, int color) {
+    const int n = L.n, half = n >> 1, m = half * n * n;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        int tx, y, z;
+        if (L.lg >= 0) {
+            tx = t & (half - 1);
+            y = (t >> (L.lg - 1)) & (n - 1);
+            z = t >> (2 * L.lg - 1);
+        } else {
+            tx = t % half;
+            const int q = t / half;
+            y = q % n;
+            z = q / n;
+        }
+        const int x = 2 * tx + ((y + z + color) & 1);
+        const int i = (z * n + y) * n + x;
+        e[i] = (nb6(e, x, y, z, n) - b[i]) * (T)(1.0 / 6.0);
+    }
+}
+
+template <typename T>
+__device__ void blk_resid_restrict(const BlkLevel& C, const T* e, const T* b, T* bc) {
+    const int nc = C.n, n = 2 * nc, m = nc * nc * nc;
     const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        const int X = t % nc, Y = (t / nc) % nc, Z = t / (nc * nc);
+        int X, Y, Z;
+        dec3(t, C, X, Y, Z);
         T acc = 0;
         for (int dz = -1; dz <= 1; ++dz) {
             const int z = wrap_idx(2 * Z + dz, n);
@@ -342,13 +410,15 @@ __global__ void __launch_bounds__(1024)
 k_vcycle_block(int n0, int nlev, const T* __restrict__ b_in, T* __restrict__ e_out,
                const double* __restrict__ g, int nu1, int nu2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // layout: per level l: e_l, b_l (T, n_l^3); then the coarsest b in double
+    // layout: per level l: e_l, b_l (T, n_l^3); then, 16-byte aligned, the
+    // coarsest right-hand side and the pseudo-inverse kernel in FP64
     T* e[6];
     T* b[6];
-    int nl[6];
+    BlkLevel lv[6];
     size_t off = 0;
     for (int l = 0, n = n0; l < nlev; ++l, n >>= 1) {
-        nl[l] = n;
+        lv[l].n = n;
+        lv[l].lg = (n & (n - 1)) == 0 ? __ffs(n) - 1 : -1;
         const size_t m = (size_t)n * n * n;
         e[l] = reinterpret_cast<T*>(smem_raw + off);
         off += m * sizeof(T);
@@ -356,56 +426,62 @@ k_vcycle_block(int n0, int nlev, const T* __restrict__ b_in, T* __restrict__ e_o
         off += m * sizeof(T);
     }
     off = (off + 15) / 16 * 16;
+    const int nc = lv[nlev - 1].n, mc = nc * nc * nc;
     double* bd = reinterpret_cast<double*>(smem_raw + off);
+    double* gs = bd + mc;
+    for (int i = threadIdx.x; i < mc; i += blockDim.x) gs[i] = g[i];
     const int m0 = n0 * n0 * n0;
     for (int i = threadIdx.x; i < m0; i += blockDim.x) b[0][i] = b_in[i];
     __syncthreads();
     // descend
     for (int l = 0; l < nlev - 1; ++l) {
-        const int n = nl[l], m = n * n * n;
+        const int m = lv[l].n * lv[l].n * lv[l].n;
         for (int i = threadIdx.x; i < m; i += blockDim.x) e[l][i] = (T)0;
         __syncthreads();
         for (int s = 0; s < nu1; ++s) {
-            blk_rbgs(n, e[l], b[l], 0);
+            blk_rbgs(lv[l], e[l], b[l], 0);
             __syncthreads();
-            blk_rbgs(n, e[l], b[l], 1);
+            blk_rbgs(lv[l], e[l], b[l], 1);
             __syncthreads();
         }
-        blk_resid_restrict(nl[l + 1], e[l], b[l], b[l + 1]);
+        blk_resid_restrict(lv[l + 1], e[l], b[l], b[l + 1]);
         __syncthreads();
     }
-    // coarsest: exact pseudo-inverse in FP64
-    {
-        const int n = nl[nlev - 1], m = n * n * n;
-        for (int j = threadIdx.x; j < m; j += blockDim.x) bd[j] = (double)b[nlev - 1][j];
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const int x = i % n, y = (i / n) % n, z = i / (n * n);
-            double acc = 0.0;
-            for (int j = 0; j < m; ++j) {
-                const int jx = j % n, jy = (j / n) % n, jz = j / (n * n);
-                int dx = x - jx, dy = y - jy, dz = z - jz;
-                dx += dx < 0 ? n : 0;
-                dy += dy < 0 ? n : 0;
-                dz += dz < 0 ? n : 0;
-                acc += g[(dz * n + dy) * n + dx] * bd[j];
+    // coarsest: exact pseudo-inverse in FP64, e_i = sum_j g[(i - j) mod n] b_j
+    for (int j = threadIdx.x; j < mc; j += blockDim.x) bd[j] = (double)b[nlev - 1][j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < mc; i += blockDim.x) {
+        int x, y, z;
+        dec3(i, lv[nlev - 1], x, y, z);
+        double acc = 0.0;
+        int j = 0;
+        for (int jz = 0; jz < nc; ++jz) {
+            const int dz = z >= jz ? z - jz : z - jz + nc;
+            for (int jy = 0; jy < nc; ++jy) {
+                const int dy = y >= jy ? y - jy : y - jy + nc;
+                const double* grow = gs + (dz * nc + dy) * nc;
+                for (int jx = 0; jx < nc; ++jx, ++j) {
+                    const int dx = x >= jx ? x - jx : x - jx + nc;
+                    acc += grow[dx] * bd[j];
+                }
             }
-            e[nlev - 1][i] = (T)acc;
         }
-        __syncthreads();
+        e[nlev - 1][i] = (T)acc;
     }
+    __syncthreads();
     // ascend
     for (int l = nlev - 2; l >= 0; --l) {
-        const int n = nl[l], m = n * n * n;
+        const int n = lv[l].n, m = n * n * n;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const int x = i % n, y = (i / n) % n, z = i / (n * n);
+            int x, y, z;
+            dec3(i, lv[l], x, y, z);
             e[l][i] += prolong_at(e[l + 1], n >> 1, x, y, z);
         }
         __syncthreads();
         for (int s = 0; s < nu2; ++s) {
-            blk_rbgs(n, e[l], b[l], 1);
+            blk_rbgs(lv[l], e[l], b[l], 1);
             __syncthreads();
-            blk_rbgs(n, e[l], b[l], 0);
+            blk_rbgs(lv[l], e[l], b[l], 0);
             __syncthreads();
         }
     }
@@ -422,46 +498,66 @@ inline size_t vcycle_block_smem(int n0, int nlev, size_t tb) {
         n >>= 1;
     }
     bytes = (bytes + 15) / 16 * 16;
-    return bytes + 8 * (size_t)nc * nc * nc;
+    return bytes + 2 * 8 * (size_t)nc * nc * nc;
 }
 
 // ---------------------------------------------------------------- interpolation
 // F_a = -ke Q_a sum_n W(r_a - r_n) (D phi)_n with central differences
 // (Eq. 21), one thread per particle in cell order; writes the total force
-// (adding the short-range part) and the two parts in original order.
+// (adding the short-range part) and the two parts in original order.  R is
+// the arithmetic type of the weights, differences and the 64-term sums (FP64,
+// or FP32 from an FP32 copy of phi in mixed mode); the result is FP64.
+template <typename R>
 __global__ void __launch_bounds__(P3_THREADS)
 k_gather(int np, const PQ* __restrict__ xq, const int* __restrict__ order, int n, double inv_h,
-         double ke, const double* __restrict__ phi, const double* __restrict__ Fsr_s,
+         double ke, const R* __restrict__ phi, const double* __restrict__ Fsr_s,
          double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
     const PQ p = xq[s];
-    double wx[4], wy[4], wz[4];
-    const int bx = bspline_axis(p.x, inv_h, n, wx);
-    const int by = bspline_axis(p.y, inv_h, n, wy);
-    const int bz = bspline_axis(p.z, inv_h, n, wz);
-    double gx = 0.0, gy = 0.0, gz = 0.0;
+    double wxd[4], wyd[4], wzd[4];
+    const int bx = bspline_axis(p.x, inv_h, n, wxd);
+    const int by = bspline_axis(p.y, inv_h, n, wyd);
+    const int bz = bspline_axis(p.z, inv_h, n, wzd);
+    R wx[4], wy[4], wz[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        wx[k] = (R)wxd[k];
+        wy[k] = (R)wyd[k];
+        wz[k] = (R)wzd[k];
+    }
+    int ix[4], ixm[4], ixp[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        ix[a] = wrap_idx(bx + a, n);
+        ixm[a] = ix[a] == 0 ? n - 1 : ix[a] - 1;
+        ixp[a] = ix[a] == n - 1 ? 0 : ix[a] + 1;
+    }
+    R gx = 0, gy = 0, gz = 0;
     for (int c = 0; c < 4; ++c) {
         const int iz = wrap_idx(bz + c, n);
         const int izm = iz == 0 ? n - 1 : iz - 1, izp = iz == n - 1 ? 0 : iz + 1;
         for (int b = 0; b < 4; ++b) {
             const int iy = wrap_idx(by + b, n);
             const int iym = iy == 0 ? n - 1 : iy - 1, iyp = iy == n - 1 ? 0 : iy + 1;
-            const double wyz = wy[b] * wz[c];
+            const R wyz = wy[b] * wz[c];
+            const R* row = phi + ((int64_t)iz * n + iy) * n;
+            const R* rym = phi + ((int64_t)iz * n + iym) * n;
+            const R* ryp = phi + ((int64_t)iz * n + iyp) * n;
+            const R* rzm = phi + ((int64_t)izm * n + iy) * n;
+            const R* rzp = phi + ((int64_t)izp * n + iy) * n;
+#pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const int ix = wrap_idx(bx + a, n);
-                const int ixm = ix == 0 ? n - 1 : ix - 1, ixp = ix == n - 1 ? 0 : ix + 1;
-                const double w = wyz * wx[a];
-                const int64_t row = ((int64_t)iz * n + iy) * n;
-                gx += w * (phi[row + ixp] - phi[row + ixm]);
-                gy += w * (phi[((int64_t)iz * n + iyp) * n + ix] - phi[((int64_t)iz * n + iym) * n + ix]);
-                gz += w * (phi[((int64_t)izp * n + iy) * n + ix] - phi[((int64_t)izm * n + iy) * n + ix]);
+                const R w = wyz * wx[a];
+                gx += w * (row[ixp[a]] - row[ixm[a]]);
+                gy += w * (ryp[ix[a]] - rym[ix[a]]);
+                gz += w * (rzp[ix[a]] - rzm[ix[a]]);
             }
         }
     }
     const double scale = -ke * p.w * 0.5 * inv_h;
     const int i = order[s];
-    const double f[3] = {scale * gx, scale * gy, scale * gz};
+    const double f[3] = {scale * (double)gx, scale * (double)gy, scale * (double)gz};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double sr = Fsr_s[3 * s + d];

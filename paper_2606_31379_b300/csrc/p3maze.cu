@@ -49,6 +49,11 @@ struct StepGraph {
 inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
 inline dim3 g3(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
 inline dim3 g3h(int n) { return dim3((n / 2 + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
+// z-marching stencils: ZC planes per thread.
+inline dim3 gz(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, (n + P3_ZC - 1) / P3_ZC); }
+inline unsigned gz_blocks(int n) { const dim3 g = gz(n); return g.x * g.y * g.z; }
+// Fine residual: each block walks every 16th z plane (about a thousand blocks at 128^3).
+inline dim3 resid_grid(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, std::min(n, 16)); }
 const dim3 kB3(P3_BX, P3_BY, 1);
 
 }  // namespace
@@ -86,13 +91,14 @@ struct p3maze_ctx {
     int nhist = 0;
     double* sig = nullptr;
     double* rfin = nullptr;
+    float* phi32 = nullptr;               // mixed mode: FP32 copy of phi^k for the interpolation
     std::vector<Level> lev;
     double* gcoarse = nullptr;
     size_t blk_smem = 0;
     // reductions and solver state
     double* partial = nullptr;
     double* dscal = nullptr;
-    unsigned long long* dres = nullptr;
+    double* bmax = nullptr;          // block maxima of the fine residual
     MGState* dmg = nullptr;
     double* hscal = nullptr;
     MGState* hmg = nullptr;
@@ -253,15 +259,22 @@ int spread_smooth(p3maze_ctx* ctx) {
     stage_begin(ctx, P3MAZE_ST_SMOOTH);
     if (ctx->K == 0) {
         CK(cudaMemcpyAsync(ctx->qs, ctx->q, sizeof(T) * ctx->P, cudaMemcpyDeviceToDevice, s));
+        k_sum_partial<T><<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->P, (const T*)ctx->qs, ctx->partial);
+        k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_QSUM);
+        count(ctx, P3MAZE_ST_SMOOTH, 2);
     } else {
         T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
         const T* src = (const T*)ctx->q;
         for (int k = 0; k < ctx->K; ++k) {
-            T* dst = (k == ctx->K - 1) ? (T*)ctx->qs : tmp[k & 1];
-            k_diffuse<T><<<g3(ctx->N), kB3, 0, s>>>(ctx->N, src, dst, (T)ctx->c);
+            const bool last = k == ctx->K - 1;
+            T* dst = last ? (T*)ctx->qs : tmp[k & 1];
+            if (last) k_diffuse<T, true><<<gz(ctx->N), kB3, 0, s>>>(ctx->N, src, dst, (T)ctx->c, ctx->partial);
+            else k_diffuse<T, false><<<gz(ctx->N), kB3, 0, s>>>(ctx->N, src, dst, (T)ctx->c, nullptr);
             src = dst;
         }
-        count(ctx, P3MAZE_ST_SMOOTH, ctx->K);
+        // neutrality: the last step's block sums (FP64) give mean(q^s)
+        k_sum_final<<<1, 1024, 0, s>>>((int)gz_blocks(ctx->N), ctx->partial, ctx->dscal + S_QSUM);
+        count(ctx, P3MAZE_ST_SMOOTH, ctx->K + 1);
     }
     CKL();
     stage_end(ctx, P3MAZE_ST_SMOOTH);
@@ -307,9 +320,10 @@ int vcycle(p3maze_ctx* ctx, int l) {
 template <typename T>
 void launch_resid_check(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
     cudaStream_t s = ctx->stream;
-    k_resid_fine<T><<<g3(ctx->N), kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin,
-                                                ctx->dres);
-    k_mg_check<<<1, 32, 0, s>>>(ctx->dres, ctx->tol, ctx->itmax, ctx->dmg, h, use_handle);
+    const dim3 gr = resid_grid(ctx->N);
+    k_resid_fine<T><<<gr, kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin, ctx->bmax);
+    k_mg_check<<<1, 1024, 0, s>>>(ctx->bmax, (int)(gr.x * gr.y * gr.z), ctx->tol, ctx->itmax, ctx->dmg, h,
+                                  use_handle);
     count(ctx, P3MAZE_ST_SOLVE, 2);
 }
 
@@ -391,13 +405,11 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     cudaStream_t s = ctx->stream;
     const int ik = ctx->icur, ikm1 = 1 - ctx->icur;
     stage_begin(ctx, P3MAZE_ST_PREDICT);
-    k_sum_partial<T><<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->P, (const T*)ctx->qs, ctx->partial);
-    k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_QSUM);
     k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->psi[ik], ctx->psi[ikm1], (const T*)ctx->qs,
                                                      ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, ctx->yh[1],
                                                      ctx->yh[2], ctx->yh[3], pred_order, ctx->sig, ctx->yh[0]);
     CKL();
-    count(ctx, P3MAZE_ST_PREDICT, 3);
+    count(ctx, P3MAZE_ST_PREDICT, 1);
     stage_end(ctx, P3MAZE_ST_PREDICT);
     stage_begin(ctx, P3MAZE_ST_SOLVE);
     int rc = solve_loop<T>(ctx);
@@ -406,7 +418,7 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     stage_begin(ctx, P3MAZE_ST_UPDATE);
     k_update<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1], ctx->yh[0],
                                                     ctx->rfin, (const T*)ctx->qs, ctx->dscal + S_QSUM,
-                                                    1.0 / (double)ctx->P, 4.0 * kPi / ctx->h);
+                                                    1.0 / (double)ctx->P, 4.0 * kPi / ctx->h, ctx->phi32);
     count(ctx, P3MAZE_ST_UPDATE);
     stage_end(ctx, P3MAZE_ST_UPDATE);
     CKL();
@@ -420,16 +432,17 @@ int forces(p3maze_ctx* ctx) {
     const double halfL2 = 0.25 * ctx->L * ctx->L;
     const bool mixed = ctx->prec == P3MAZE_MIXED;
     stage_begin(ctx, P3MAZE_ST_PAIR);
-    const unsigned pb = nblk(32 * (int64_t)ctx->np);
+    const int nbox = (ctx->nc + 1) / 2;
+    const unsigned pb = (unsigned)nbox * nbox * nbox;
 #define PAIR(KIND)                                                                                      \
     do {                                                                                                \
         if (mixed)                                                                                      \
-            k_pair<KIND, float, float4><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts, ctx->ms, \
-                ctx->cs, ctx->start, ctx->nc, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,   \
+            k_pair<KIND, float, 1024><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts, ctx->ms,   \
+                ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,      \
                 ctx->Fs, ctx->ecs, ctx->evs);                                                           \
         else                                                                                            \
-            k_pair<KIND, double, PQ><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts, ctx->ms,    \
-                ctx->cs, ctx->start, ctx->nc, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,   \
+            k_pair<KIND, double, 512><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts, ctx->ms,   \
+                ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,      \
                 ctx->Fs, ctx->ecs, ctx->evs);                                                           \
     } while (0)
     if (ctx->tab.kind == 1) PAIR(1);
@@ -439,8 +452,13 @@ int forces(p3maze_ctx* ctx) {
     count(ctx, P3MAZE_ST_PAIR);
     stage_end(ctx, P3MAZE_ST_PAIR);
     stage_begin(ctx, P3MAZE_ST_GATHER);
-    k_gather<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h, ctx->ke,
-                                                  ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
+    if (mixed)
+        k_gather<float><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h, ctx->ke,
+                                                             ctx->phi32, ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
+    else
+        k_gather<double><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h,
+                                                              ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr,
+                                                              ctx->Fsr);
     count(ctx, P3MAZE_ST_GATHER);
     if (ctx->nmol) {
         k_water<<<nblk(ctx->nmol), P3_THREADS, 0, s>>>(ctx->nmol, ctx->tri, ctx->r, ctx->Q, ctx->L, ctx->alpha, ctx->ke,
@@ -505,7 +523,6 @@ int initialise_field(p3maze_ctx* ctx) {
     }
     for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(ctx->yh[k], 0, mb, s));
     CK(cudaMemsetAsync(ctx->dmg, 0, sizeof(MGState), s));
-    CK(cudaMemsetAsync(ctx->dres, 0, sizeof(unsigned long long), s));
     ctx->nhist = 0;
     const bool was_timing = ctx->timing;
     ctx->timing = false;
@@ -656,7 +673,7 @@ int step_once(p3maze_ctx* ctx) {
 int validate_mesh(int N, int* nlev, int* ncoarse) {
     if (N < 4) return 0;
     int n = N, l = 1;
-    while (n > 4 && (n % 2) == 0) {
+    while (n > 2 && (n % 2) == 0) {
         n /= 2;
         ++l;
     }
@@ -729,6 +746,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         ALLOC(ctx->psi[k], 8 * P);
     }
     ALLOC(ctx->rfin, 8 * P);
+    if (mixed) ALLOC(ctx->phi32, 4 * P);
     for (int k = 0; k < 4; ++k) ALLOC(ctx->yh[k], 8 * P);
     ALLOC(ctx->sig, 8 * P);
     ctx->lev.resize(ctx->nlev);
@@ -756,9 +774,12 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     }
     std::vector<double> g = coarse_green(ctx->lev.back().n);
     ALLOC(ctx->gcoarse, 8 * g.size());
-    ALLOC(ctx->partial, 8 * 1024);
+    ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(1024, gz_blocks(ctx->N)));
     ALLOC(ctx->dscal, 8 * S_NSCAL);
-    ALLOC(ctx->dres, 8);
+    {
+        const dim3 gr = resid_grid(ctx->N);
+        ALLOC(ctx->bmax, 8 * (size_t)gr.x * gr.y * gr.z);
+    }
     ALLOC(ctx->dmg, sizeof(MGState));
     {
         cudaError_t e1 = cudaMallocHost((void**)&ctx->hscal, 8 * S_NSCAL);
@@ -1046,6 +1067,9 @@ int p3maze_get_forces(p3maze_ctx* ctx, int32_t which, double* out) {
 
 int p3maze_set_state(p3maze_ctx* ctx, const double* pos, const double* vel) {
     if (!ctx || !pos || !vel) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    for (int64_t i = 0; i < 3 * (int64_t)ctx->np; ++i)
+        if (!std::isfinite(pos[i]) || !std::isfinite(vel[i]))
+            return fail(ctx, P3MAZE_ERR_INVALID, "non-finite position or velocity");
     cudaStream_t s = ctx->stream;
     CK(cudaMemcpyAsync(ctx->r, pos, 24 * (size_t)ctx->np, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->v, vel, 24 * (size_t)ctx->np, cudaMemcpyHostToDevice, s));
@@ -1111,6 +1135,14 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
         ctx->pending[st] = false;
     }
     ctx->timed_steps = 0;
+    return P3MAZE_OK;
+}
+
+int p3maze_set_graphs(p3maze_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!enable) destroy_graphs(ctx);
+    ctx->use_graphs = enable != 0;
     return P3MAZE_OK;
 }
 

@@ -52,9 +52,11 @@ __global__ void k_cell_count(int n, const double* __restrict__ r, double inv_cel
                              int* __restrict__ cell, int* __restrict__ count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int cx = min((int)floor(r[3 * i + 0] * inv_cell), nc - 1);
-    const int cy = min((int)floor(r[3 * i + 1] * inv_cell), nc - 1);
-    const int cz = min((int)floor(r[3 * i + 2] * inv_cell), nc - 1);
+    // clamped on both sides so that a non-finite position cannot index out of
+    // bounds (wrapped positions always give 0 <= c < nc)
+    const int cx = min(max((int)floor(r[3 * i + 0] * inv_cell), 0), nc - 1);
+    const int cy = min(max((int)floor(r[3 * i + 1] * inv_cell), 0), nc - 1);
+    const int cz = min(max((int)floor(r[3 * i + 2] * inv_cell), 0), nc - 1);
     const int c = (cz * nc + cy) * nc + cx;
     cell[i] = c;
     atomicAdd(&count[c], 1);
@@ -150,114 +152,249 @@ struct SRTable {
     double p[5][16];
 };
 
+// Math in the pair kernel's arithmetic type, with the FP32 versions named
+// explicitly (no silent promotion to the FP64 pipe).
+__device__ __forceinline__ float m_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double m_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float m_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return rsqrt(x); }
+
+// Pair parameters of one species pair in the arithmetic type: BMH A, 1/rho,
+// s, C, D or LJ eps, sigma^2.
+template <typename R>
+struct PairPar {
+    R a, b, c, d, e;
+};
+
 // Per-pair screened Coulomb (Eq. 19 with alpha = 1/(sqrt2 sigma); energy
-// Eq. 5) and the non-Coulomb term.  Returns F/r scaled by ke for the Coulomb
-// part; energies are accumulated unscaled.
+// Eq. 5) and the non-Coulomb term.  Returns the Coulomb F/r without ke;
+// energies are returned unscaled.
 template <int KIND, typename R>
-__device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const SRTable& tab, int k, R& ec, R& ev,
-                                        R& fvdw) {
-    const R ir = (R)1 / sqrt(r2);
+__device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& pp, R& ec, R& ev, R& fvdw) {
+    const R ir = m_rsqrt(r2);
     const R rr = r2 * ir;
     const R ar = alpha * rr;
-    const R erfcv = erfc(ar);
-    const R ex = exp(-ar * ar);
+    const R erfcv = m_erfc(ar);
+    const R ex = m_exp(-ar * ar);
     const R ir2 = ir * ir;
     ec = qq * erfcv * ir;
     ev = (R)0;
     fvdw = (R)0;
     if (KIND == 1) {
-        const R A = (R)tab.p[0][k], rho = (R)tab.p[1][k], sg = (R)tab.p[2][k];
-        const R C = (R)tab.p[3][k], D = (R)tab.p[4][k];
-        const R eb = A * exp((sg - rr) / rho);
+        const R eb = pp.a * m_exp((pp.c - rr) * pp.b);
         const R ir6 = ir2 * ir2 * ir2, ir8 = ir6 * ir2;
-        ev = eb - C * ir6 - D * ir8;
-        fvdw = (eb / rho - (R)6 * C * ir6 * ir - (R)8 * D * ir8 * ir) * ir;
+        ev = eb - pp.d * ir6 - pp.e * ir8;
+        fvdw = (eb * pp.b - (R)6 * pp.d * ir6 * ir - (R)8 * pp.e * ir8 * ir) * ir;
     } else if (KIND == 2) {
-        const R eps = (R)tab.p[0][k];
-        if (eps != (R)0) {
-            const R sg = (R)tab.p[1][k];
-            const R sr2 = sg * sg * ir2;
+        if (pp.a != (R)0) {
+            const R sr2 = pp.b * ir2;
             const R sr6 = sr2 * sr2 * sr2;
-            ev = (R)4 * eps * (sr6 * sr6 - sr6);
-            fvdw = (R)24 * eps * ((R)2 * sr6 * sr6 - sr6) * ir2;
+            ev = (R)4 * pp.a * (sr6 * sr6 - sr6);
+            fvdw = (R)24 * pp.a * ((R)2 * sr6 * sr6 - sr6) * ir2;
         }
     }
     return qq * (erfcv * ir + (R)kTwoOverSqrtPi * alpha * ex) * ir2;
 }
 
-// Short-range forces on particle s (cell order) from every particle image
-// within r_cut, found in the 5x5x5 block of cells of edge l >= r_cut/2 around
-// it: Eq. 19 plus the Born-Mayer or Lennard-Jones term.  One warp per
-// particle, each lane walking a share of the 125 neighbour cells; a
-// particle's neighbour j in unwrapped cell c_i + d sits at the image
-// (c_i + d) l + x_j,loc, so the separation is x_i,loc - x_j,loc - d l with no
-// periodic shift.  Pairs within one molecule closer than L/2 (the nearest
-// image) are excluded.  Writes the force and half of the pair energies of s;
-// no atomics.  R is the arithmetic type (double, or float in mixed mode with
-// FP32 cell-local coordinates and FP64 accumulation across lanes).
-template <int KIND, typename R, typename LQ>
+// Short-range forces (Eq. 19 plus the Born-Mayer or Lennard-Jones term) on
+// the particles of a "home box" of 2x2x2 cells (edge l >= r_cut/2), one block
+// per box.  The block stages every particle image of the surrounding region
+// (home cells +-2 cells, up to 6x6x6 cells, periodic images explicit) in
+// shared memory with coordinates in the box frame, x_loc + (u - u0) l for a
+// particle of unwrapped cell u, so separations need no periodic shift and, in
+// mixed mode, no FP64.  Groups of G lanes share a home particle, each lane
+// scanning every G-th staged candidate; the group reduces in FP64.  Pairs
+// within one molecule closer than L/2 (the nearest image) are excluded.
+// Writes the force and half of the pair energies of each particle; no
+// atomics.  Regions larger than the staging buffer are processed in chunks.
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = PQ; };
+
+template <int KIND, typename R, int CAP>
 __global__ void __launch_bounds__(P3_THREADS)
-k_pair(int n, const LQ* __restrict__ xl, const int* __restrict__ ts, const int* __restrict__ ms,
-       const int* __restrict__ cs, const int* __restrict__ start, int nc, double lcell, double rc2,
+k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restrict__ ts,
+       const int* __restrict__ ms, const int* __restrict__ start, int nc, int nbox, double lcell, double rc2,
        double halfL2, double alpha, double ke, SRTable tab, double* __restrict__ Fs,
        double* __restrict__ ecs, double* __restrict__ evs) {
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (s >= n) return;
-    const LQ pi = xl[s];
-    const int ti = ts[s];
-    const int mi = ms[s];
-    const int ci = cs[s];
-    const int cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
-    const R lc = (R)lcell, r2c = (R)rc2, hl2 = (R)halfL2, al = (R)alpha;
-    R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
-    for (int o = lane; o < 125; o += 32) {
-        const int dx = o % 5 - 2, dy = (o / 5) % 5 - 2, dz = o / 25 - 2;
-        int xx = cx + dx, yy = cy + dy, zz = cz + dz;
-        while (xx < 0) xx += nc;
-        while (xx >= nc) xx -= nc;
-        while (yy < 0) yy += nc;
-        while (yy >= nc) yy -= nc;
-        while (zz < 0) zz += nc;
-        while (zz >= nc) zz -= nc;
-        const bool home = dx == 0 && dy == 0 && dz == 0;
-        const R ox = (R)dx * lc, oy = (R)dy * lc, oz = (R)dz * lc;
-        const int c = (zz * nc + yy) * nc + xx;
-        const int e = start[c + 1];
-        for (int t = start[c]; t < e; ++t) {
-            if (home && t == s) continue;
-            const LQ pj = xl[t];
-            const R ddx = (R)pi.x - (R)pj.x - ox;
-            const R ddy = (R)pi.y - (R)pj.y - oy;
-            const R ddz = (R)pi.z - (R)pj.z - oz;
-            const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 >= r2c) continue;
-            if (mi >= 0 && ms[t] == mi && r2 < hl2) continue;
-            R e_c, e_v, f_v;
-            const R fr = pair_terms<KIND, R>(r2, (R)pi.w * (R)pj.w, al, tab, ti * tab.nt + ts[t], e_c, e_v, f_v);
-            const R f = (R)ke * fr + f_v;
-            fx += f * ddx;
-            fy += f * ddy;
-            fz += f * ddz;
-            ec += e_c;
-            ev += e_v;
+    using V = typename Vec4<R>::type;
+    constexpr int HCAP = 256;
+    __shared__ V sp[CAP];
+    __shared__ int sidx[CAP], styp[CAP], smol[CAP];
+    __shared__ int rstart[216], roff[217];
+    __shared__ signed char rsh[216];          // 1 if the region cell is a shifted image
+    __shared__ V hpos[HCAP];
+    __shared__ unsigned hidx[HCAP];  // sorted index | home-cell offset bits 29..31
+    __shared__ int s_nh, s_total;
+    __shared__ PairPar<R> spar[16];
+    const int tid = threadIdx.x;
+    if (tid < tab.nt * tab.nt) {
+        PairPar<R> pp;
+        if (KIND == 1) {
+            pp.a = (R)tab.p[0][tid];
+            pp.b = (R)(1.0 / tab.p[1][tid]);
+            pp.c = (R)tab.p[2][tid];
+            pp.d = (R)tab.p[3][tid];
+            pp.e = (R)tab.p[4][tid];
+        } else {
+            pp.a = (R)tab.p[0][tid];
+            pp.b = (R)(tab.p[1][tid] * tab.p[1][tid]);
+            pp.c = pp.d = pp.e = (R)0;
         }
+        spar[tid] = pp;
     }
-    double dfx = fx, dfy = fy, dfz = fz, dec = ec, dev = ev;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-        dfx += __shfl_xor_sync(0xffffffffu, dfx, w);
-        dfy += __shfl_xor_sync(0xffffffffu, dfy, w);
-        dfz += __shfl_xor_sync(0xffffffffu, dfz, w);
-        dec += __shfl_xor_sync(0xffffffffu, dec, w);
-        dev += __shfl_xor_sync(0xffffffffu, dev, w);
+    const int b = blockIdx.x;
+    const int bx = b % nbox, by = (b / nbox) % nbox, bz = b / (nbox * nbox);
+    const int h0[3] = {2 * bx, 2 * by, 2 * bz};
+    int hw[3];
+    for (int d = 0; d < 3; ++d) hw[d] = min(2, nc - h0[d]);
+    const int wx = hw[0] + 4, wy = hw[1] + 4, wz = hw[2] + 4;
+    const int nreg = wx * wy * wz;
+    const R lc = (R)lcell;
+    // region cells: unwrapped u = h0 - 2 + r
+    if (tid < nreg) {
+        const int rx = tid % wx, ry = (tid / wx) % wy, rz = tid / (wx * wy);
+        int u[3] = {h0[0] - 2 + rx, h0[1] - 2 + ry, h0[2] - 2 + rz};
+        int c3[3];
+        bool shifted = false;
+        for (int d = 0; d < 3; ++d) {
+            int c = u[d] % nc;
+            if (c < 0) c += nc;
+            c3[d] = c;
+            shifted |= (c != u[d]);
+        }
+        const int c = (c3[2] * nc + c3[1]) * nc + c3[0];
+        rstart[tid] = start[c];
+        roff[tid + 1] = start[c + 1] - start[c];
+        rsh[tid] = shifted ? 1 : 0;
     }
-    if (lane == 0) {
-        Fs[3 * s + 0] = dfx;
-        Fs[3 * s + 1] = dfy;
-        Fs[3 * s + 2] = dfz;
-        ecs[s] = 0.5 * ke * dec;
-        evs[s] = 0.5 * dev;
+    __syncthreads();
+    if (tid == 0) {
+        roff[0] = 0;
+        for (int r = 0; r < nreg; ++r) roff[r + 1] += roff[r];
+        s_total = roff[nreg];
+        // home particles: region cells with r in [2, 2 + hw) on every axis
+        int nh = 0;
+        for (int rz = 2; rz < 2 + hw[2]; ++rz)
+            for (int ry = 2; ry < 2 + hw[1]; ++ry)
+                for (int rx = 2; rx < 2 + hw[0]; ++rx) {
+                    const int r = (rz * wy + ry) * wx + rx;
+                    for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t) {
+                        if (nh < HCAP) hidx[nh] = (unsigned)t | ((unsigned)(rx - 2) << 29) | ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
+                        ++nh;
+                    }
+                }
+        s_nh = nh;
+    }
+    __syncthreads();
+    const int nh_all = s_nh, total = s_total;
+    // lanes per home particle: a power of two with nh * G <= threads (G <= 32)
+    int G = 32;
+    while (G > 1 && G * min(nh_all, HCAP) > (int)blockDim.x) G >>= 1;
+    const int slots = blockDim.x / G;
+    const int lg = tid & (G - 1);
+    for (int hbase = 0; hbase < nh_all; hbase += HCAP) {
+        const int nh = min(HCAP, nh_all - hbase);
+        if (hbase > 0) {
+            // rebuild the home list for this pass
+            __syncthreads();
+            if (tid == 0) {
+                int k = 0;
+                for (int rz = 2; rz < 2 + hw[2]; ++rz)
+                    for (int ry = 2; ry < 2 + hw[1]; ++ry)
+                        for (int rx = 2; rx < 2 + hw[0]; ++rx) {
+                            const int r = (rz * wy + ry) * wx + rx;
+                            for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t, ++k)
+                                if (k >= hbase && k < hbase + HCAP)
+                                    hidx[k - hbase] = (unsigned)t | ((unsigned)(rx - 2) << 29) | ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
+                        }
+            }
+            __syncthreads();
+        }
+        for (int k = tid; k < nh; k += blockDim.x) {
+            const unsigned code = hidx[k];
+            const int t = (int)(code & 0x1fffffffu);
+            const V p = xl[t];
+            V q = p;
+            q.x = (R)p.x + (R)((code >> 29) & 1) * lc;
+            q.y = (R)p.y + (R)((code >> 30) & 1) * lc;
+            q.z = (R)p.z + (R)((code >> 31) & 1) * lc;
+            hpos[k] = q;
+        }
+        __syncthreads();
+        for (int h = tid / G; h < ((nh + slots - 1) / slots) * slots; h += slots) {
+            const bool live = h < nh;
+            const int hs = live ? (int)(hidx[h] & 0x1fffffffu) : 0;
+            const V pi = live ? hpos[h] : hpos[0];
+            const int ti = live ? ts[hs] : 0;
+            const int mi = live ? ms[hs] : -1;
+            R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
+            const R rc2r = (R)rc2, hl2r = (R)halfL2, alr = (R)alpha, ker = (R)ke;
+            for (int c0 = 0; c0 < total; c0 += CAP) {
+                const int cn = min(CAP, total - c0);
+                __syncthreads();
+                for (int k = tid; k < cn; k += blockDim.x) {
+                    const int gk = c0 + k;
+                    int lo = 0, hi = nreg - 1;  // region cell holding candidate gk
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (roff[mid] <= gk) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int r = lo;
+                    const int t = rstart[r] + (gk - roff[r]);
+                    const int rx = r % wx, ry = (r / wx) % wy, rz = r / (wx * wy);
+                    const V p = xl[t];
+                    V q = p;
+                    q.x = (R)p.x + (R)(rx - 2) * lc;
+                    q.y = (R)p.y + (R)(ry - 2) * lc;
+                    q.z = (R)p.z + (R)(rz - 2) * lc;
+                    sp[k] = q;
+                    sidx[k] = rsh[r] ? -1 : t;
+                    styp[k] = ts[t];
+                    smol[k] = ms[t];
+                }
+                __syncthreads();
+                if (live) {
+                    for (int k = lg; k < cn; k += G) {
+                        if (sidx[k] == hs) continue;
+                        const V pj = sp[k];
+                        const R ddx = (R)pi.x - (R)pj.x;
+                        const R ddy = (R)pi.y - (R)pj.y;
+                        const R ddz = (R)pi.z - (R)pj.z;
+                        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (r2 >= rc2r) continue;
+                        if (mi >= 0 && smol[k] == mi && r2 < hl2r) continue;
+                        R e_c, e_v, f_v;
+                        const R fr = pair_terms<KIND, R>(r2, (R)pi.w * (R)pj.w, alr, spar[ti * tab.nt + styp[k]],
+                                                         e_c, e_v, f_v);
+                        const R f = ker * fr + f_v;
+                        fx += f * ddx;
+                        fy += f * ddy;
+                        fz += f * ddz;
+                        ec += e_c;
+                        ev += e_v;
+                    }
+                }
+            }
+            double dfx = fx, dfy = fy, dfz = fz, dec = ec, dev = ev;
+            for (int w = G >> 1; w > 0; w >>= 1) {
+                dfx += __shfl_xor_sync(0xffffffffu, dfx, w);
+                dfy += __shfl_xor_sync(0xffffffffu, dfy, w);
+                dfz += __shfl_xor_sync(0xffffffffu, dfz, w);
+                dec += __shfl_xor_sync(0xffffffffu, dec, w);
+                dev += __shfl_xor_sync(0xffffffffu, dev, w);
+            }
+            if (live && lg == 0) {
+                Fs[3 * hs + 0] = dfx;
+                Fs[3 * hs + 1] = dfy;
+                Fs[3 * hs + 2] = dfz;
+                ecs[hs] = 0.5 * ke * dec;
+                evs[hs] = 0.5 * dev;
+            }
+        }
     }
 }
 

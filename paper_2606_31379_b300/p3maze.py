@@ -83,6 +83,7 @@ _sig = {
     "p3maze_get_cells": (C.c_int, [_ctx, _ip, _ip, _ip]),
     "p3maze_set_timing": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_get_timing": (C.c_int, [_ctx, C.POINTER(Timing)]),
+    "p3maze_set_graphs": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_last_error": (C.c_char_p, [_ctx]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -265,6 +266,10 @@ class Context:
     def set_timing(self, enable: bool = True):
         """Enable per-stage CUDA-event timing and reset the counters."""
         self._check(lib.p3maze_set_timing(self._h, 1 if enable else 0))
+
+    def set_graphs(self, enable: bool = True):
+        """Replay steady-state steps as CUDA graphs (default) or launch eagerly."""
+        self._check(lib.p3maze_set_graphs(self._h, 1 if enable else 0))
 
     def timing(self) -> dict:
         t = Timing()
