@@ -233,6 +233,33 @@ int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
  * conditional graph nodes.                                                    */
 int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
 
+/* Diffusion smoothing of a caller-owned mesh that allocates nothing.
+ * The paper has no counterpart: this call exists for callers that cannot
+ * allocate device memory when they need the smoothing -- code recording a
+ * CUDA stream capture (allocation is not allowed there), code running under a
+ * fixed device-memory budget owned by a host framework, or callers that must
+ * not grow their footprint after start-up.
+ *   q     device, [mesh^3] FP64 input (x fastest), read only
+ *   qs    device, [mesh^3] FP64 output: (I + coeff M)^steps q with its mean
+ *         removed -- the same q^s the context computes (P3MAZE_MESH_QS) for
+ *         steps = K, coeff = c of p3maze_get_stats; must not alias q
+ *   mesh  4..64 points per axis; larger meshes are rejected (INVALID)
+ *   steps >= 0; coeff in (0, 1/6] when steps > 0
+ *   cuda_stream  cudaStream_t the work is queued on (NULL = legacy stream)
+ * Scratch: one file-scope device array of 2 MiB + 32 KiB (a 64^3 FP64
+ * ping-pong mesh and the block sums of the mean), present on every GPU that
+ * loads this library until the process exits.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device
+ * share the array and keep nothing from earlier calls: calls that overlap on
+ * the GPU (different streams, or host threads queueing concurrently) race on
+ * it and must be ordered by the caller.  Returns 0 or INVALID/CUDA; the
+ * message is p3maze_last_error(NULL).  Asynchronous: outputs are ready when
+ * the stream reaches this point.                                              */
+int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t steps, double coeff,
+                          void *cuda_stream);
+
 /* Message of the last failing call on ctx (or of the last failing init when
  * ctx is NULL).  Never NULL.                                                   */
 const char *p3maze_last_error(const p3maze_ctx *ctx);

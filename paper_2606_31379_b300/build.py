@@ -12,7 +12,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libp3maze.so")
-SOURCES = ["p3maze.cu"]
+SOURCES = ["p3maze.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "mesh.cuh", "particles.cuh"]
 
 NVCC_FLAGS = [

@@ -123,7 +123,7 @@ __global__ void k_dot_partial(int64_t m, const double* __restrict__ a, const T* 
 }
 
 // Kinetic-energy partials: sum m v^2 over particles.
-__global__ void k_mv2_partial(int np, const double* __restrict__ v, const double* __restrict__ m,
+static __global__ void k_mv2_partial(int np, const double* __restrict__ v, const double* __restrict__ m,
                               double* __restrict__ partial) {
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
@@ -133,7 +133,7 @@ __global__ void k_mv2_partial(int np, const double* __restrict__ v, const double
 }
 
 // Sum of nb partials (in a fixed order) into out[0].
-__global__ void k_sum_final(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+static __global__ void k_sum_final(int nb, const double* __restrict__ partial, double* __restrict__ out) {
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
     acc = block_sum(acc);
@@ -234,7 +234,7 @@ struct MGState {
     long long solves;
 };
 
-__global__ void __launch_bounds__(1024)
+static __global__ void __launch_bounds__(1024)
 k_mg_check(const double* __restrict__ bmax, int nb, double tol, int itmax, MGState* __restrict__ st,
            cudaGraphConditionalHandle handle, int use_handle) {
     double a = 0.0;

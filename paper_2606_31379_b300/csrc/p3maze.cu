@@ -58,6 +58,9 @@ const dim3 kB3(P3_BX, P3_BY, 1);
 
 }  // namespace
 
+// Library-internal: set the message of p3maze_last_error(NULL).
+__attribute__((visibility("hidden"))) void p3_set_global_error(const char* msg) { g_init_error = msg; }
+
 struct p3maze_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -8,7 +8,7 @@ namespace p3 {
 
 // Velocity-Verlet half kick (Sec. 2; supporting information Sec. 1):
 // v += (dt/2) F / m.  hdt_acc[i] = 0.5 dt ACCEL / m_i.
-__global__ void k_kick(int n, double* __restrict__ v, const double* __restrict__ F,
+static __global__ void k_kick(int n, double* __restrict__ v, const double* __restrict__ F,
                        const double* __restrict__ hdt_acc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -25,7 +25,7 @@ __device__ __forceinline__ double wrap_pos(double x, double L) {
 }
 
 // Half kick, drift r += dt v, and wrap into [0, L).
-__global__ void k_kick_drift(int n, double* __restrict__ r, double* __restrict__ v,
+static __global__ void k_kick_drift(int n, double* __restrict__ r, double* __restrict__ v,
                              const double* __restrict__ F, const double* __restrict__ hdt_acc,
                              double dt, double L) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -39,7 +39,7 @@ __global__ void k_kick_drift(int n, double* __restrict__ r, double* __restrict__
     }
 }
 
-__global__ void k_wrap(int n, double* __restrict__ r, double L) {
+static __global__ void k_wrap(int n, double* __restrict__ r, double L) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * n) return;
     r[i] = wrap_pos(r[i], L);
@@ -48,7 +48,7 @@ __global__ void k_wrap(int n, double* __restrict__ r, double L) {
 // ---------------------------------------------------------------- cell list
 // Cell of each particle, c = min(floor(r * nc/L), nc-1) per axis, x fastest,
 // and per-cell counts.
-__global__ void k_cell_count(int n, const double* __restrict__ r, double inv_cell, int nc,
+static __global__ void k_cell_count(int n, const double* __restrict__ r, double inv_cell, int nc,
                              int* __restrict__ cell, int* __restrict__ count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -64,7 +64,7 @@ __global__ void k_cell_count(int n, const double* __restrict__ r, double inv_cel
 
 // Exclusive scan of m counts into start[0..m] with one block of 1024 threads;
 // also clears the per-cell fill counters.
-__global__ void __launch_bounds__(1024) k_scan_cells(int m, const int* __restrict__ count,
+static __global__ void __launch_bounds__(1024) k_scan_cells(int m, const int* __restrict__ count,
                                                      int* __restrict__ start, int* __restrict__ fill) {
     __shared__ int warp_tot[32];
     const int tid = threadIdx.x;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(1024) k_scan_cells(int m, const int* __restric
     if (tid == blockDim.x - 1) start[m] = warp_tot[31];
 }
 
-__global__ void k_cell_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
+static __global__ void k_cell_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
                                int* __restrict__ fill, int* __restrict__ order) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -108,7 +108,7 @@ __global__ void k_cell_scatter(int n, const int* __restrict__ cell, const int* _
 }
 
 // Sort each cell's members by particle index so the order is deterministic.
-__global__ void k_cell_sort(int m, const int* __restrict__ start, int* __restrict__ order) {
+static __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __restrict__ order) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
     const int b = start[c], e = start[c + 1];
@@ -125,7 +125,7 @@ __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __restric
 
 // Gather particle data into cell order: xq = (x, y, z, Q) and the
 // cell-local coordinates x - c l (FP64 and FP32 copies) used by the pair kernel.
-__global__ void k_gather_sorted(int n, const int* __restrict__ order, const double* __restrict__ r,
+static __global__ void k_gather_sorted(int n, const int* __restrict__ order, const double* __restrict__ r,
                                 const double* __restrict__ Q, const int* __restrict__ type,
                                 const int* __restrict__ mol, const int* __restrict__ cell, int nc,
                                 double lcell, PQ* __restrict__ xq, PQ* __restrict__ xl64,
@@ -402,7 +402,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
 // bonds and angle (Table S1) and the subtraction of the mesh part
 // ke QQ erf(r/(sqrt2 sigma))/r of the three intramolecular pairs.  Adds into
 // F (original order) and writes the bonded force and energies.
-__global__ void k_water(int nmol, const int* __restrict__ tri, const double* __restrict__ r,
+static __global__ void k_water(int nmol, const int* __restrict__ tri, const double* __restrict__ r,
                         const double* __restrict__ Q, double L, double alpha, double ke, double kb,
                         double r0, double ka, double th0, double* __restrict__ F,
                         double* __restrict__ Fb, double* __restrict__ eb, double* __restrict__ ex) {

@@ -84,6 +84,7 @@ _sig = {
     "p3maze_set_timing": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_get_timing": (C.c_int, [_ctx, C.POINTER(Timing)]),
     "p3maze_set_graphs": (C.c_int, [_ctx, C.c_int32]),
+    "p3maze_smooth_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p]),
     "p3maze_last_error": (C.c_char_p, [_ctx]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -96,6 +97,14 @@ class P3MaZeError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"p3maze error {code}: {msg}")
         self.code = code
+
+
+def smooth_noalloc(q_ptr: int, qs_ptr: int, mesh: int, steps: int, coeff: float, stream: int | None = None):
+    """p3maze_smooth_noalloc on device pointers (no device allocation)."""
+    rc = lib.p3maze_smooth_noalloc(C.c_void_p(q_ptr), C.c_void_p(qs_ptr), int(mesh), int(steps), float(coeff),
+                                   C.c_void_p(stream or 0))
+    if rc:
+        raise P3MaZeError(rc, lib.p3maze_last_error(None).decode())
 
 
 def _f64(a, shape=None) -> np.ndarray:
