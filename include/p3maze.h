@@ -26,8 +26,12 @@
  *     no context was created).
  *   - Host pointers are read (or written) during the call only; the caller
  *     keeps ownership.  The context owns all device memory it allocates.
- *   - A context is bound to the CUDA stream given at init and to the device
- *     current at init.  It is not thread safe; use one context per thread.
+ *   - A context is bound to the device current at init and to the CUDA stream
+ *     given there: every call is ordered after the work already queued on
+ *     that stream, and the stream is ordered after the call's work.  The
+ *     context runs its kernels on two internal streams (the mesh pipeline at
+ *     the highest priority, the short-range pair branch at the lowest).  A
+ *     context is not thread safe; use one context per thread.
  */
 #ifndef P3MAZE_H
 #define P3MAZE_H
@@ -52,6 +56,14 @@ extern "C" {
 #define P3MAZE_MIXED  1   /* FP32 assignment, smoothing, multigrid hierarchy and pair math;
                              FP64 positions, fields phi and y, constraint residual, coarse
                              solve, neutrality sum and all energy/force accumulation      */
+
+#define P3MAZE_METHOD_MAZE 0  /* P3MaZe: Verlet-predicted field corrected by the multiplier y,
+                                 convergence on max|M y - sigma_p| (Eq. 20)              */
+#define P3MAZE_METHOD_P3M  1  /* real-space P3M baseline (Sec. 3.3): the same splitting,
+                                 smoothing and Verlet-predicted initial field, the Poisson
+                                 equation solved directly by multigrid with no multiplier
+                                 predictor, convergence on max|M phi + (4pi/h) q^s| (the P3M
+                                 residual of Sec. 3.3) <= tol                               */
 
 #define P3MAZE_SR_NONE 0  /* Coulomb only                                               */
 #define P3MAZE_SR_BMH  1  /* Born-Huggins-Mayer: A exp((s-r)/rho) - C/r^6 - D/r^8         */
@@ -115,6 +127,7 @@ typedef struct {
     double coulomb_k;       /* kcal A/(mol e^2); 0 -> 332.0637                              */
     const p3maze_sr_table *sr;      /* may be NULL: Coulomb only                           */
     const p3maze_topology *topology;/* may be NULL                                         */
+    int32_t method;         /* P3MAZE_METHOD_MAZE (0) or P3MAZE_METHOD_P3M                  */
 } p3maze_params;
 
 typedef struct {
@@ -130,7 +143,7 @@ typedef struct {
 
 typedef struct {
     int32_t last_iters;         /* V-cycles of the last constraint solve                  */
-    double last_residual;       /* max|M y - sigma_p| after it                            */
+    double last_residual;       /* max|M y - sigma_p| after it (P3M: max|M phi + 4pi q^s/h|) */
     int64_t steps;              /* MD steps taken since init                               */
     int64_t total_iters;        /* V-cycles summed over those steps                        */
     int32_t init_iters;         /* V-cycles of the initial full solve                      */
@@ -162,6 +175,17 @@ typedef struct {
     int64_t total_launches;           /* all kernels launched since init or reset        */
 } p3maze_timing;
 
+typedef struct {
+    int32_t predictor;          /* chosen multiplier predictor (0 for P3M)              */
+    int32_t pre_sweeps;         /* chosen red-black Gauss-Seidel sweeps before / after  */
+    int32_t post_sweeps;
+    int32_t diffusion_zc;       /* z planes per thread of the diffusion kernel          */
+    double ms_per_step;         /* measured with the chosen setting                    */
+    double initial_ms_per_step; /* measured with the setting in use before tuning      */
+    int32_t trials;             /* settings timed                                      */
+    int32_t steps;              /* MD steps advanced while tuning                      */
+} p3maze_tuning;
+
 typedef struct p3maze_ctx p3maze_ctx;
 
 /* ---- lifecycle ------------------------------------------------------------- */
@@ -175,12 +199,23 @@ typedef struct p3maze_ctx p3maze_ctx;
 int p3maze_init(const p3maze_params *params, const double *pos, const double *vel,
                 void *cuda_stream, p3maze_ctx **out);
 
-/* Advance nsteps velocity-Verlet steps (Sec. 2; supporting information Sec. 1).
- * Synchronises with the stream once per multigrid iteration to test
- * convergence.  On NOT_CONVERGED or NONFINITE the step that failed is left
- * applied and the error returned; the context can be re-initialised with
- * p3maze_reinit.                                                                 */
+/* Advance nsteps velocity-Verlet steps (Sec. 2; supporting information Sec. 1)
+ * and wait for them.  The first steps after (re)initialisation, before the
+ * multiplier history is full, test convergence on the host after every
+ * V-cycle; later steps replay a captured CUDA graph whose multigrid loop is a
+ * device-side while node, so the host waits once per call.  On
+ * NOT_CONVERGED or NONFINITE (recorded on the device, first failure kept)
+ * the steps are left applied and the error returned; re-initialise with
+ * p3maze_reinit.                                                               */
 int p3maze_step(p3maze_ctx *ctx, int32_t nsteps);
+
+/* As p3maze_step, but return once the steps are queued (graph steps do not
+ * wait for the GPU); the caller's stream is ordered after them.  Convergence
+ * failures are reported by the next p3maze_wait.                               */
+int p3maze_step_async(p3maze_ctx *ctx, int32_t nsteps);
+
+/* Wait for queued steps and report a recorded solver failure.                  */
+int p3maze_wait(p3maze_ctx *ctx);
 
 /* Full constraint solve from phi = 0 at the current positions and new forces:
  * the same initialisation as p3maze_init (after an external state change).   */
@@ -259,6 +294,16 @@ int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
  * the stream reaches this point.                                              */
 int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t steps, double coeff,
                           void *cuda_stream);
+
+/* Autotuner: time real MD steps under candidate settings and keep the
+ * fastest -- multiplier predictor 1..3 (P3MaZe only), smoothing sweeps
+ * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the diffusion
+ * kernel's z planes per thread in {4, 8, 16}.  None of them changes the
+ * converged field beyond tol (they change iteration counts and speed only).
+ * Every trial runs 2 warm-up steps (graph capture) and steps_per_trial timed
+ * steps (CUDA events); the system advances by all of them (out->steps).
+ * Errors as p3maze_step.                                                      */
+int p3maze_autotune(p3maze_ctx *ctx, int32_t steps_per_trial, p3maze_tuning *out);
 
 /* Message of the last failing call on ctx (or of the last failing init when
  * ctx is NULL).  Never NULL.                                                   */

@@ -62,19 +62,19 @@ __device__ __forceinline__ bool xyz3(int n, int& x, int& y, int& z) {
 
 // ---------------------------------------------------------------- smoothing
 // One explicit diffusion step out = in + c M in (reading of Sec. 2's
-// diffusion-based smoothing).  Each thread marches ZC planes along z keeping
-// the z neighbours in registers; x and y neighbours come through L1.  With
+// diffusion-based smoothing).  Each thread marches zc planes along z keeping
+// the z neighbours in registers (zc planes per thread, a tunable); x and y
+// neighbours come through L1.  With
 // SUM (the last step) the block also writes the FP64 sum of
 // its outputs, from which the neutrality mean is formed.
-#define P3_ZC 16
 
 template <typename T, bool SUM>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
-k_diffuse(int n, const T* __restrict__ in, T* __restrict__ out, T c, double* __restrict__ partial) {
+k_diffuse(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, double* __restrict__ partial) {
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
-    const int z0 = blockIdx.z * P3_ZC;
-    const int z1 = min(z0 + P3_ZC, n);
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, n);
     double acc = 0.0;
     if (x < n && y < n) {
         const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kNoAllocMaxMesh = 64;                                   // points per axis
 constexpr int kNoAllocMesh = kNoAllocMaxMesh * kNoAllocMaxMesh * kNoAllocMaxMesh;
-constexpr int kNoAllocPartials = 4096;                                // >= blocks of one diffusion launch at 64^3
+constexpr int kNoAllocPartials = 4096;                                // >= blocks of one diffusion launch at 64^3 (16 at zc 8)
 constexpr int kMaxDevices = 64;
 
 // Scratch: one ping-pong mesh (FP64) followed by the FP64 block sums and the
@@ -89,7 +89,8 @@ extern "C" int p3maze_smooth_noalloc(const double* q, double* qs, int32_t mesh, 
     const int n = mesh;
     const int64_t m = (int64_t)n * n * n;
     const dim3 blk(P3_BX, P3_BY, 1);
-    const dim3 grd((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, (n + P3_ZC - 1) / P3_ZC);
+    const int zc = 8;
+    const dim3 grd((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, (n + zc - 1) / zc);
     const int nb = (int)(grd.x * grd.y * grd.z);
     if (steps == 0) {
         cudaError_t e = cudaMemcpyAsync(qs, q, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
@@ -102,9 +103,9 @@ extern "C" int p3maze_smooth_noalloc(const double* q, double* qs, int32_t mesh, 
         for (int k = 0; k < steps; ++k) {
             double* dst = ((steps - 1 - k) % 2 == 0) ? qs : tmp;
             if (k == steps - 1)
-                k_diffuse<double, true><<<grd, blk, 0, s>>>(n, src, dst, coeff, partial);
+                k_diffuse<double, true><<<grd, blk, 0, s>>>(n, zc, src, dst, coeff, partial);
             else
-                k_diffuse<double, false><<<grd, blk, 0, s>>>(n, src, dst, coeff, nullptr);
+                k_diffuse<double, false><<<grd, blk, 0, s>>>(n, zc, src, dst, coeff, nullptr);
             src = dst;
         }
         k_sum_final<<<1, 1024, 0, s>>>(nb, partial, total);

@@ -50,8 +50,8 @@ inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_TH
 inline dim3 g3(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
 inline dim3 g3h(int n) { return dim3((n / 2 + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
 // z-marching stencils: ZC planes per thread.
-inline dim3 gz(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, (n + P3_ZC - 1) / P3_ZC); }
-inline unsigned gz_blocks(int n) { const dim3 g = gz(n); return g.x * g.y * g.z; }
+inline dim3 gz(int n, int zc) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, (n + zc - 1) / zc); }
+inline unsigned gz_blocks(int n, int zc) { const dim3 g = gz(n, zc); return g.x * g.y * g.z; }
 // Fine residual: each block walks every 16th z plane (about a thousand blocks at 128^3).
 inline dim3 resid_grid(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, std::min(n, 16)); }
 const dim3 kB3(P3_BX, P3_BY, 1);
@@ -63,12 +63,17 @@ __attribute__((visibility("hidden"))) void p3_set_global_error(const char* msg) 
 
 struct p3maze_ctx {
     int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
+    cudaStream_t stream = nullptr;       // internal work stream (highest priority)
+    cudaStream_t user_stream = nullptr;  // the caller's stream; every call is fenced against it
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaStream_t body_stream = nullptr;  // capture of the while-node body
+    cudaStream_t pair_stream = nullptr;  // short-range forces, concurrent with the mesh pipeline
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // parameters
     int np = 0, N = 0, nc = 0, ncell = 0, prec = 0, pred = 3, itmax = 50, nu1 = 2, nu2 = 2, K = 0;
-    int nmol = 0, nlev = 0;
+    int nmol = 0, nlev = 0, method = 0;
+    int zc = 8;                          // z planes per thread in the diffusion step (tunable)
+    double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     int64_t P = 0;
     double L = 0, h = 0, inv_h = 0, alpha = 0, sigma = 0, rc = 0, c = 0, tol = 0, dt = 0, ke = 0;
     double inv_cell = 0, lcell = 0, v_self = 0;
@@ -207,6 +212,20 @@ int collect_timing(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
+// Order the work stream after everything queued on the caller's stream so far.
+int enter(p3maze_ctx* ctx) {
+    CK(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+    return P3MAZE_OK;
+}
+
+// Order the caller's stream after everything queued on the work stream.
+int leave(p3maze_ctx* ctx) {
+    CK(cudaEventRecord(ctx->ev_out, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+    return P3MAZE_OK;
+}
+
 // Pseudo-inverse kernel of the periodic 7-point operator on an n^3 mesh:
 // g(d) = n^-3 sum_{k != 0} cos(2 pi k.d / n) / lambda(k),
 // lambda(k) = -4 sum_axes sin^2(pi k_axis / n).
@@ -271,12 +290,14 @@ int spread_smooth(p3maze_ctx* ctx) {
         for (int k = 0; k < ctx->K; ++k) {
             const bool last = k == ctx->K - 1;
             T* dst = last ? (T*)ctx->qs : tmp[k & 1];
-            if (last) k_diffuse<T, true><<<gz(ctx->N), kB3, 0, s>>>(ctx->N, src, dst, (T)ctx->c, ctx->partial);
-            else k_diffuse<T, false><<<gz(ctx->N), kB3, 0, s>>>(ctx->N, src, dst, (T)ctx->c, nullptr);
+            if (last)
+                k_diffuse<T, true><<<gz(ctx->N, ctx->zc), kB3, 0, s>>>(ctx->N, ctx->zc, src, dst, (T)ctx->c, ctx->partial);
+            else
+                k_diffuse<T, false><<<gz(ctx->N, ctx->zc), kB3, 0, s>>>(ctx->N, ctx->zc, src, dst, (T)ctx->c, nullptr);
             src = dst;
         }
         // neutrality: the last step's block sums (FP64) give mean(q^s)
-        k_sum_final<<<1, 1024, 0, s>>>((int)gz_blocks(ctx->N), ctx->partial, ctx->dscal + S_QSUM);
+        k_sum_final<<<1, 1024, 0, s>>>((int)gz_blocks(ctx->N, ctx->zc), ctx->partial, ctx->dscal + S_QSUM);
         count(ctx, P3MAZE_ST_SMOOTH, ctx->K + 1);
     }
     CKL();
@@ -325,8 +346,9 @@ void launch_resid_check(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_h
     cudaStream_t s = ctx->stream;
     const dim3 gr = resid_grid(ctx->N);
     k_resid_fine<T><<<gr, kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin, ctx->bmax);
-    k_mg_check<<<1, 1024, 0, s>>>(ctx->bmax, (int)(gr.x * gr.y * gr.z), ctx->tol, ctx->itmax, ctx->dmg, h,
-                                  use_handle);
+    // P3M: max|M phi + (4pi/h) q^s| = (4pi/h) max|M y - sigma_p| for phi = phi_p - (4pi/h) y
+    k_mg_check<<<1, 1024, 0, s>>>(ctx->bmax, (int)(gr.x * gr.y * gr.z), ctx->tol / ctx->res_scale, ctx->itmax,
+                                  ctx->dmg, h, use_handle);
     count(ctx, P3MAZE_ST_SOLVE, 2);
 }
 
@@ -429,18 +451,24 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     return P3MAZE_OK;
 }
 
-int forces(p3maze_ctx* ctx) {
-    cudaStream_t s = ctx->stream;
+// Short-range pair forces on the pair stream (forked from the main stream
+// after the cell list; joined before the interpolation).
+int pair_forces(p3maze_ctx* ctx) {
     const double rc2 = ctx->rc * ctx->rc;
     const double halfL2 = 0.25 * ctx->L * ctx->L;
     const bool mixed = ctx->prec == P3MAZE_MIXED;
+    cudaStream_t main = ctx->stream;
+    CK(cudaEventRecord(ctx->ev_fork, main));
+    CK(cudaStreamWaitEvent(ctx->pair_stream, ctx->ev_fork, 0));
+    ctx->stream = ctx->pair_stream;
+    cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_PAIR);
     const int nbox = (ctx->nc + 1) / 2;
     const unsigned pb = (unsigned)nbox * nbox * nbox;
 #define PAIR(KIND)                                                                                      \
     do {                                                                                                \
         if (mixed)                                                                                      \
-            k_pair<KIND, float, 1024><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts, ctx->ms,   \
+            k_pair<KIND, float, 768><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts, ctx->ms,    \
                 ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,      \
                 ctx->Fs, ctx->ecs, ctx->evs);                                                           \
         else                                                                                            \
@@ -454,6 +482,17 @@ int forces(p3maze_ctx* ctx) {
 #undef PAIR
     count(ctx, P3MAZE_ST_PAIR);
     stage_end(ctx, P3MAZE_ST_PAIR);
+    ctx->stream = main;
+    CKL();
+    CK(cudaEventRecord(ctx->ev_join, ctx->pair_stream));
+    return P3MAZE_OK;
+}
+
+// Join the pair branch, then interpolate the mesh force and add the bonded terms.
+int gather_forces(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    const bool mixed = ctx->prec == P3MAZE_MIXED;
+    CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     stage_begin(ctx, P3MAZE_ST_GATHER);
     if (mixed)
         k_gather<float><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h, ctx->ke,
@@ -473,9 +512,13 @@ int forces(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
+// Assignment and smoothing use the whole GPU; the pair branch is forked
+// after them so that it fills the SMs the latency-bound solve leaves idle.
 template <typename T>
 int mesh_pipeline(p3maze_ctx* ctx, int pred_order) {
     int rc = spread_smooth<T>(ctx);
+    if (rc) return rc;
+    rc = pair_forces(ctx);
     if (rc) return rc;
     return solve_field<T>(ctx, pred_order);
 }
@@ -488,7 +531,7 @@ int field_and_forces(p3maze_ctx* ctx, int pred_order) {
     rc = ctx->prec == P3MAZE_MIXED ? mesh_pipeline<float>(ctx, pred_order)
                                    : mesh_pipeline<double>(ctx, pred_order);
     if (rc) return rc;
-    return forces(ctx);
+    return gather_forces(ctx);
 }
 
 // Copy the solver state to the host and turn a recorded failure into an error.
@@ -497,7 +540,7 @@ int read_solver_state(p3maze_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     const MGState& m = *ctx->hmg;
     ctx->st.last_iters = m.last_iters;
-    ctx->st.last_residual = m.last_res;
+    ctx->st.last_residual = m.last_res * ctx->res_scale;
     ctx->st.total_iters = m.total_iters;
     // V-cycles run inside graphs: add their body launches to the tally
     const int64_t graph_iters = m.total_iters - ctx->eager_iters;
@@ -509,7 +552,7 @@ int read_solver_state(p3maze_ctx* ctx) {
     if (m.status == P3MAZE_ERR_NOT_CONVERGED) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "multigrid did not reach tol %.3g in %d V-cycles (residual %.3g)", ctx->tol,
-                      ctx->itmax, m.last_res);
+                      ctx->itmax, m.last_res * ctx->res_scale);
         return fail(ctx, P3MAZE_ERR_NOT_CONVERGED, buf);
     }
     return P3MAZE_OK;
@@ -698,7 +741,15 @@ void release(p3maze_ctx* ctx) {
     ctx->hscal = nullptr;
     ctx->hmg = nullptr;
     if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
-    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->pair_stream) cudaStreamDestroy(ctx->pair_stream);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    ctx->pair_stream = nullptr;
+    ctx->ev_fork = ctx->ev_join = nullptr;
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    ctx->ev_in = ctx->ev_out = nullptr;
     ctx->body_stream = nullptr;
     ctx->stream = nullptr;
 }
@@ -708,13 +759,22 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     const bool mixed = p->precision == P3MAZE_MIXED;
     const size_t tb = mixed ? sizeof(float) : sizeof(double);
     CK(cudaGetDevice(&ctx->device));
-    if (!ctx->stream) {
-        // graphs cannot be captured on the legacy default stream; a blocking
-        // stream keeps the legacy stream's ordering with other work
-        CK(cudaStreamCreate(&ctx->stream));
-        ctx->own_stream = true;
+    {
+        // Work runs on an internal stream of the highest priority (graphs can
+        // be captured on it whatever the caller passed), the short-range
+        // branch on one of the lowest so its blocks fill SMs that the
+        // latency-bound multigrid leaves idle.  Each call is fenced against
+        // the caller's stream with events on entry and exit.
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&ctx->stream, cudaStreamNonBlocking, greatest));
+        CK(cudaStreamCreateWithPriority(&ctx->pair_stream, cudaStreamNonBlocking, least));
+        CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
     }
     CK(cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     // particle arrays
     ALLOC(ctx->r, 24 * (size_t)n);
     ALLOC(ctx->v, 24 * (size_t)n);
@@ -777,7 +837,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     }
     std::vector<double> g = coarse_green(ctx->lev.back().n);
     ALLOC(ctx->gcoarse, 8 * g.size());
-    ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(1024, gz_blocks(ctx->N)));
+    ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(1024, gz_blocks(ctx->N, 1)));
     ALLOC(ctx->dscal, 8 * S_NSCAL);
     {
         const dim3 gr = resid_grid(ctx->N);
@@ -850,6 +910,8 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     if (!(p->tol > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "tol must be > 0");
     if (!(p->dt >= 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "dt must be >= 0");
     if (p->predictor < 0 || p->predictor > 3) return fail(nullptr, P3MAZE_ERR_INVALID, "predictor must be 0..3");
+    if (p->method != P3MAZE_METHOD_MAZE && p->method != P3MAZE_METHOD_P3M)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "method must be P3MAZE_METHOD_MAZE or P3MAZE_METHOD_P3M");
     if (p->precision != P3MAZE_FP64 && p->precision != P3MAZE_MIXED)
         return fail(nullptr, P3MAZE_ERR_INVALID, "precision must be P3MAZE_FP64 or P3MAZE_MIXED");
     if (p->max_mg_iters < 0 || p->pre_sweeps < 0 || p->post_sweeps < 0)
@@ -914,7 +976,7 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
 
     p3maze_ctx* ctx = new (std::nothrow) p3maze_ctx();
     if (!ctx) return fail(nullptr, P3MAZE_ERR_OOM, "host allocation failed");
-    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->user_stream = (cudaStream_t)cuda_stream;
     ctx->np = n;
     ctx->N = p->mesh;
     ctx->P = (int64_t)p->mesh * p->mesh * p->mesh;
@@ -928,7 +990,10 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->c = kappa / ctx->K;
     ctx->tol = p->tol;
     ctx->dt = p->dt;
-    ctx->pred = p->predictor == 0 ? 3 : p->predictor;
+    ctx->method = p->method;
+    ctx->res_scale = p->method == P3MAZE_METHOD_P3M ? 4.0 * kPi / h : 1.0;
+    // P3M has no multiplier: every solve starts from the Verlet-predicted field
+    ctx->pred = p->method == P3MAZE_METHOD_P3M ? 0 : (p->predictor == 0 ? 3 : p->predictor);
     ctx->prec = p->precision;
     ctx->itmax = p->max_mg_iters ? p->max_mg_iters : 50;
     ctx->nu1 = p->pre_sweeps ? p->pre_sweeps : 2;
@@ -959,6 +1024,7 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
 
     int rc = setup(ctx, p, pos, vel);
     if (!rc) rc = initialise_field(ctx);
+    if (!rc) rc = leave(ctx);
     if (!rc) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) rc = fail(ctx, P3MAZE_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
@@ -973,19 +1039,58 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     return P3MAZE_OK;
 }
 
-int p3maze_step(p3maze_ctx* ctx, int32_t nsteps) {
+int p3maze_step_async(p3maze_ctx* ctx, int32_t nsteps) {
     if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, P3MAZE_ERR_INVALID, "nsteps must be >= 0");
+    int rc = enter(ctx);
+    if (rc) return rc;
     for (int k = 0; k < nsteps; ++k) {
-        int rc = step_once(ctx);
+        rc = step_once(ctx);
         if (rc) return rc;
     }
+    return leave(ctx);
+}
+
+int p3maze_wait(p3maze_ctx* ctx) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    return read_solver_state(ctx);
+}
+
+int p3maze_step(p3maze_ctx* ctx, int32_t nsteps) {
+    int rc = p3maze_step_async(ctx, nsteps);
+    if (rc) return rc;
+    return read_solver_state(ctx);
+}
+
+int p3maze_equilibrate(p3maze_ctx* ctx, int32_t nsteps, double temperature_K) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    if (nsteps < 0 || !(temperature_K > 0.0)) return fail(ctx, P3MAZE_ERR_INVALID, "need nsteps >= 0, T > 0");
+    int rc = enter(ctx);
+    if (rc) return rc;
+    // sum m v^2 (g/mol A^2/fs^2) of (3n - 3) degrees of freedom at T
+    const double kb = 0.0019872043;  // kcal/(mol K)
+    const double target = (3.0 * ctx->np - 3.0) * kb * temperature_K * P3_ACCEL;
+    cudaStream_t s = ctx->stream;
+    for (int k = 0; k < nsteps; ++k) {
+        rc = step_once(ctx);
+        if (rc) return rc;
+        k_mv2_partial<<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->mass, ctx->partial);
+        k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_MV2);
+        k_rescale_v<<<nblk(3 * (int64_t)ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->dscal + S_MV2, target);
+        CKL();
+    }
+    rc = leave(ctx);
+    if (rc) return rc;
     return read_solver_state(ctx);
 }
 
 int p3maze_reinit(p3maze_ctx* ctx) {
     if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
-    int rc = initialise_field(ctx);
+    int rc = enter(ctx);
+    if (rc) return rc;
+    rc = initialise_field(ctx);
+    if (rc) return rc;
+    rc = leave(ctx);
     if (rc) return rc;
     CK(cudaStreamSynchronize(ctx->stream));
     return P3MAZE_OK;
@@ -1002,6 +1107,8 @@ int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
     if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
     cudaStream_t s = ctx->stream;
     const int nb = kReduceBlocks;
+    int rc0 = enter(ctx);
+    if (rc0) return rc0;
     k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->ecs, ctx->partial);
     k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_ESR);
     k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->evs, ctx->partial);
@@ -1042,6 +1149,8 @@ int p3maze_get_stats(p3maze_ctx* ctx, p3maze_stats* out) {
 }
 
 static int copy_out(p3maze_ctx* ctx, const void* dsrc, void* hdst, size_t bytes) {
+    int rc = enter(ctx);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(hdst, dsrc, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return P3MAZE_OK;
@@ -1074,11 +1183,13 @@ int p3maze_set_state(p3maze_ctx* ctx, const double* pos, const double* vel) {
         if (!std::isfinite(pos[i]) || !std::isfinite(vel[i]))
             return fail(ctx, P3MAZE_ERR_INVALID, "non-finite position or velocity");
     cudaStream_t s = ctx->stream;
+    int rc = enter(ctx);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->r, pos, 24 * (size_t)ctx->np, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->v, vel, 24 * (size_t)ctx->np, cudaMemcpyHostToDevice, s));
     k_wrap<<<nblk(3 * (int64_t)ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->L);
     CKL();
-    return P3MAZE_OK;
+    return leave(ctx);
 }
 
 int p3maze_get_mesh(p3maze_ctx* ctx, int32_t which, double* out) {
@@ -1139,6 +1250,118 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
     }
     ctx->timed_steps = 0;
     return P3MAZE_OK;
+}
+
+namespace {
+
+struct Setting {
+    int pred, nu1, nu2, zc;
+};
+
+// Run `warm` + `steps` steps under setting `cfg`; ms per timed step.
+int tune_trial(p3maze_ctx* ctx, const Setting& cfg, int warm, int steps, double* ms) {
+    if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = cfg.pred;
+    ctx->nu1 = cfg.nu1;
+    ctx->nu2 = cfg.nu2;
+    ctx->zc = cfg.zc;
+    destroy_graphs(ctx);  // the setting is recorded in the graphs
+    for (int k = 0; k < warm; ++k) {
+        int rc = step_once(ctx);
+        if (rc) return rc;
+    }
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CK(cudaEventRecord(a, ctx->stream));
+    for (int k = 0; k < steps; ++k) {
+        int rc = step_once(ctx);
+        if (rc) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return rc;
+        }
+    }
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = t / std::max(steps, 1);
+    return read_solver_state(ctx);
+}
+
+}  // namespace
+
+int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    if (steps_per_trial < 1) return fail(ctx, P3MAZE_ERR_INVALID, "steps_per_trial must be >= 1");
+    int rc = enter(ctx);
+    if (rc) return rc;
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    const int warm = 2;
+    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc};
+    std::vector<Setting> cand;
+    const int preds[3] = {1, 2, 3};
+    const int sweeps[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
+    const int np = ctx->method == P3MAZE_METHOD_P3M ? 1 : 3;
+    for (int a = 0; a < np; ++a)
+        for (auto& sw : sweeps) cand.push_back({ctx->method == P3MAZE_METHOD_P3M ? 0 : preds[a], sw[0], sw[1], start.zc});
+    double initial = 0.0, best = 1e300;
+    Setting chosen = start;
+    int trials = 0, steps = 0;
+    rc = tune_trial(ctx, start, warm, steps_per_trial, &initial);
+    trials += 1;
+    steps += warm + steps_per_trial;
+    if (!rc) {
+        best = initial;
+        for (const Setting& c : cand) {
+            double ms = 0.0;
+            rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
+            trials += 1;
+            steps += warm + steps_per_trial;
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                chosen = c;
+            }
+        }
+    }
+    if (!rc) {
+        const int zcs[3] = {4, 8, 16};
+        for (int z : zcs) {
+            if (z == chosen.zc) continue;
+            Setting c = chosen;
+            c.zc = z;
+            double ms = 0.0;
+            rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
+            trials += 1;
+            steps += warm + steps_per_trial;
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                chosen = c;
+            }
+        }
+    }
+    // keep the fastest setting
+    if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = chosen.pred;
+    ctx->nu1 = chosen.nu1;
+    ctx->nu2 = chosen.nu2;
+    ctx->zc = chosen.zc;
+    destroy_graphs(ctx);
+    ctx->timing = timing;
+    out->predictor = ctx->pred;
+    out->pre_sweeps = ctx->nu1;
+    out->post_sweeps = ctx->nu2;
+    out->diffusion_zc = ctx->zc;
+    out->ms_per_step = best;
+    out->initial_ms_per_step = initial;
+    out->trials = trials;
+    out->steps = steps;
+    if (rc) return rc;
+    return leave(ctx);
 }
 
 int p3maze_set_graphs(p3maze_ctx* ctx, int32_t enable) {

@@ -17,6 +17,14 @@ static __global__ void k_kick(int n, double* __restrict__ v, const double* __res
     for (int d = 0; d < 3; ++d) v[3 * i + d] += a * F[3 * i + d];
 }
 
+// Velocity rescaling to a target sum m v^2 (one block sum in mv2[0]).
+static __global__ void k_rescale_v(int n, double* __restrict__ v, const double* __restrict__ mv2, double target) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const double cur = mv2[0];
+    if (cur > 0.0) v[i] *= sqrt(target / cur);
+}
+
 __device__ __forceinline__ double wrap_pos(double x, double L) {
     x = x - L * floor(x / L);
     if (x < 0.0) x += L;
@@ -154,8 +162,6 @@ struct SRTable {
 
 // Math in the pair kernel's arithmetic type, with the FP32 versions named
 // explicitly (no silent promotion to the FP64 pipe).
-__device__ __forceinline__ float m_erfc(float x) { return erfcf(x); }
-__device__ __forceinline__ double m_erfc(double x) { return erfc(x); }
 __device__ __forceinline__ float m_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
@@ -171,13 +177,25 @@ struct PairPar {
 // Per-pair screened Coulomb (Eq. 19 with alpha = 1/(sqrt2 sigma); energy
 // Eq. 5) and the non-Coulomb term.  Returns the Coulomb F/r without ke;
 // energies are returned unscaled.
+// erfc for the pair kernel.  FP32 (mixed mode): Abramowitz & Stegun 7.1.26,
+// erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+// t = 1/(1 + p x), |error| <= 1.5e-7 for x >= 0, which reuses the exp(-x^2)
+// the force needs anyway.  FP64: the CUDA math library's erfc.
+__device__ __forceinline__ float erfc_with_exp(float x, float ex) {
+    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.0f));
+    const float poly = fmaf(fmaf(fmaf(fmaf(1.061405429f, t, -1.453152027f), t, 1.421413741f), t, -0.284496736f), t,
+                            0.254829592f);
+    return t * poly * ex;
+}
+__device__ __forceinline__ double erfc_with_exp(double x, double) { return erfc(x); }
+
 template <int KIND, typename R>
 __device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& pp, R& ec, R& ev, R& fvdw) {
     const R ir = m_rsqrt(r2);
     const R rr = r2 * ir;
     const R ar = alpha * rr;
-    const R erfcv = m_erfc(ar);
     const R ex = m_exp(-ar * ar);
+    const R erfcv = erfc_with_exp(ar, ex);
     const R ir2 = ir * ir;
     ec = qq * erfcv * ir;
     ev = (R)0;
@@ -204,14 +222,34 @@ __device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& p
 // (home cells +-2 cells, up to 6x6x6 cells, periodic images explicit) in
 // shared memory with coordinates in the box frame, x_loc + (u - u0) l for a
 // particle of unwrapped cell u, so separations need no periodic shift and, in
-// mixed mode, no FP64.  Groups of G lanes share a home particle, each lane
-// scanning every G-th staged candidate; the group reduces in FP64.  Pairs
-// within one molecule closer than L/2 (the nearest image) are excluded.
-// Writes the force and half of the pair energies of each particle; no
-// atomics.  Regions larger than the staging buffer are processed in chunks.
+// mixed mode, no FP64.  One warp per home particle scans 32 candidates at a
+// time and compacts those inside the cutoff into a per-warp queue
+// (__ballot_sync), so the pair functions run with every lane on a real pair.
+// Pairs within one molecule closer than L/2 (the nearest image) are excluded.
+// Each particle's force and half of its pair energies are accumulated in the
+// arithmetic type in shared memory (FP32 sums of FP32 pair terms in mixed
+// mode) and written as FP64; no global atomics.  Regions larger than the staging
+// buffer are processed in chunks, home lists longer than 256 in passes.
 template <typename R> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = PQ; };
+
+template <int KIND, typename R, typename V>
+__device__ __forceinline__ void pair_accumulate(const V& pi, const V& pj, R alpha, R ke, const PairPar<R>& pp,
+                                                R& fx, R& fy, R& fz, R& ec, R& ev) {
+    const R ddx = (R)pi.x - (R)pj.x;
+    const R ddy = (R)pi.y - (R)pj.y;
+    const R ddz = (R)pi.z - (R)pj.z;
+    const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+    R e_c, e_v, f_v;
+    const R fr = pair_terms<KIND, R>(r2, (R)pi.w * (R)pj.w, alpha, pp, e_c, e_v, f_v);
+    const R f = ke * fr + f_v;
+    fx += f * ddx;
+    fy += f * ddy;
+    fz += f * ddz;
+    ec += e_c;
+    ev += e_v;
+}
 
 template <int KIND, typename R, int CAP>
 __global__ void __launch_bounds__(P3_THREADS)
@@ -221,15 +259,18 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
        double* __restrict__ ecs, double* __restrict__ evs) {
     using V = typename Vec4<R>::type;
     constexpr int HCAP = 256;
+    constexpr int NW = P3_THREADS / 32;
     __shared__ V sp[CAP];
     __shared__ int sidx[CAP], styp[CAP], smol[CAP];
     __shared__ int rstart[216], roff[217];
     __shared__ signed char rsh[216];          // 1 if the region cell is a shifted image
     __shared__ V hpos[HCAP];
-    __shared__ unsigned hidx[HCAP];  // sorted index | home-cell offset bits 29..31
+    __shared__ unsigned hidx[HCAP];           // sorted index | home-cell offset bits 29..31
+    __shared__ R hacc[HCAP][5];               // per home particle: force, Coulomb and non-Coulomb energy
+    __shared__ int wq[NW][64];
     __shared__ int s_nh, s_total;
     __shared__ PairPar<R> spar[16];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < tab.nt * tab.nt) {
         PairPar<R> pp;
         if (KIND == 1) {
@@ -275,126 +316,136 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
         roff[0] = 0;
         for (int r = 0; r < nreg; ++r) roff[r + 1] += roff[r];
         s_total = roff[nreg];
-        // home particles: region cells with r in [2, 2 + hw) on every axis
         int nh = 0;
         for (int rz = 2; rz < 2 + hw[2]; ++rz)
             for (int ry = 2; ry < 2 + hw[1]; ++ry)
                 for (int rx = 2; rx < 2 + hw[0]; ++rx) {
                     const int r = (rz * wy + ry) * wx + rx;
-                    for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t) {
-                        if (nh < HCAP) hidx[nh] = (unsigned)t | ((unsigned)(rx - 2) << 29) | ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
-                        ++nh;
-                    }
+                    nh += roff[r + 1] - roff[r];
                 }
         s_nh = nh;
     }
     __syncthreads();
     const int nh_all = s_nh, total = s_total;
-    // lanes per home particle: a power of two with nh * G <= threads (G <= 32)
-    int G = 32;
-    while (G > 1 && G * min(nh_all, HCAP) > (int)blockDim.x) G >>= 1;
-    const int slots = blockDim.x / G;
-    const int lg = tid & (G - 1);
+    const R rc2r = (R)rc2, hl2r = (R)halfL2, alr = (R)alpha, ker = (R)ke;
     for (int hbase = 0; hbase < nh_all; hbase += HCAP) {
         const int nh = min(HCAP, nh_all - hbase);
-        if (hbase > 0) {
-            // rebuild the home list for this pass
-            __syncthreads();
-            if (tid == 0) {
-                int k = 0;
-                for (int rz = 2; rz < 2 + hw[2]; ++rz)
-                    for (int ry = 2; ry < 2 + hw[1]; ++ry)
-                        for (int rx = 2; rx < 2 + hw[0]; ++rx) {
-                            const int r = (rz * wy + ry) * wx + rx;
-                            for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t, ++k)
-                                if (k >= hbase && k < hbase + HCAP)
-                                    hidx[k - hbase] = (unsigned)t | ((unsigned)(rx - 2) << 29) | ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
-                        }
-            }
-            __syncthreads();
+        // home list of this pass: home cells in region order
+        if (tid == 0) {
+            int k = 0;
+            for (int rz = 2; rz < 2 + hw[2]; ++rz)
+                for (int ry = 2; ry < 2 + hw[1]; ++ry)
+                    for (int rx = 2; rx < 2 + hw[0]; ++rx) {
+                        const int r = (rz * wy + ry) * wx + rx;
+                        for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t, ++k)
+                            if (k >= hbase && k < hbase + HCAP)
+                                hidx[k - hbase] = (unsigned)t | ((unsigned)(rx - 2) << 29) |
+                                                  ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
+                    }
         }
+        __syncthreads();
         for (int k = tid; k < nh; k += blockDim.x) {
             const unsigned code = hidx[k];
             const int t = (int)(code & 0x1fffffffu);
             const V p = xl[t];
             V q = p;
-            q.x = (R)p.x + (R)((code >> 29) & 1) * lc;
-            q.y = (R)p.y + (R)((code >> 30) & 1) * lc;
-            q.z = (R)p.z + (R)((code >> 31) & 1) * lc;
+            q.x = (R)p.x + (R)((code >> 29) & 1u) * lc;
+            q.y = (R)p.y + (R)((code >> 30) & 1u) * lc;
+            q.z = (R)p.z + (R)((code >> 31) & 1u) * lc;
             hpos[k] = q;
+            for (int a = 0; a < 5; ++a) hacc[k][a] = (R)0;
         }
-        __syncthreads();
-        for (int h = tid / G; h < ((nh + slots - 1) / slots) * slots; h += slots) {
-            const bool live = h < nh;
-            const int hs = live ? (int)(hidx[h] & 0x1fffffffu) : 0;
-            const V pi = live ? hpos[h] : hpos[0];
-            const int ti = live ? ts[hs] : 0;
-            const int mi = live ? ms[hs] : -1;
-            R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
-            const R rc2r = (R)rc2, hl2r = (R)halfL2, alr = (R)alpha, ker = (R)ke;
-            for (int c0 = 0; c0 < total; c0 += CAP) {
-                const int cn = min(CAP, total - c0);
-                __syncthreads();
-                for (int k = tid; k < cn; k += blockDim.x) {
-                    const int gk = c0 + k;
-                    int lo = 0, hi = nreg - 1;  // region cell holding candidate gk
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (roff[mid] <= gk) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    const int r = lo;
-                    const int t = rstart[r] + (gk - roff[r]);
-                    const int rx = r % wx, ry = (r / wx) % wy, rz = r / (wx * wy);
-                    const V p = xl[t];
-                    V q = p;
-                    q.x = (R)p.x + (R)(rx - 2) * lc;
-                    q.y = (R)p.y + (R)(ry - 2) * lc;
-                    q.z = (R)p.z + (R)(rz - 2) * lc;
-                    sp[k] = q;
-                    sidx[k] = rsh[r] ? -1 : t;
-                    styp[k] = ts[t];
-                    smol[k] = ms[t];
+        for (int c0 = 0; c0 < total; c0 += CAP) {
+            const int cn = min(CAP, total - c0);
+            __syncthreads();
+            for (int k = tid; k < cn; k += blockDim.x) {
+                const int gk = c0 + k;
+                int lo = 0, hi = nreg - 1;  // region cell holding candidate gk
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (roff[mid] <= gk) lo = mid;
+                    else hi = mid - 1;
                 }
-                __syncthreads();
-                if (live) {
-                    for (int k = lg; k < cn; k += G) {
-                        if (sidx[k] == hs) continue;
+                const int r = lo;
+                const int t = rstart[r] + (gk - roff[r]);
+                const int rx = r % wx, ry = (r / wx) % wy, rz = r / (wx * wy);
+                const V p = xl[t];
+                V q = p;
+                q.x = (R)p.x + (R)(rx - 2) * lc;
+                q.y = (R)p.y + (R)(ry - 2) * lc;
+                q.z = (R)p.z + (R)(rz - 2) * lc;
+                sp[k] = q;
+                sidx[k] = rsh[r] ? -1 : t;
+                styp[k] = ts[t];
+                smol[k] = ms[t];
+            }
+            __syncthreads();
+            for (int h = warp; h < nh; h += NW) {
+                const int hs = (int)(hidx[h] & 0x1fffffffu);
+                const V pi = hpos[h];
+                const int prow = ts[hs] * tab.nt;
+                const int mi = ms[hs];
+                R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
+                int qn = 0;
+                for (int base = 0; base < cn; base += 32) {
+                    const int k = base + lane;
+                    bool hit = false;
+                    if (k < cn && sidx[k] != hs) {
                         const V pj = sp[k];
                         const R ddx = (R)pi.x - (R)pj.x;
                         const R ddy = (R)pi.y - (R)pj.y;
                         const R ddz = (R)pi.z - (R)pj.z;
                         const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        if (r2 >= rc2r) continue;
-                        if (mi >= 0 && smol[k] == mi && r2 < hl2r) continue;
-                        R e_c, e_v, f_v;
-                        const R fr = pair_terms<KIND, R>(r2, (R)pi.w * (R)pj.w, alr, spar[ti * tab.nt + styp[k]],
-                                                         e_c, e_v, f_v);
-                        const R f = ker * fr + f_v;
-                        fx += f * ddx;
-                        fy += f * ddy;
-                        fz += f * ddz;
-                        ec += e_c;
-                        ev += e_v;
+                        hit = r2 < rc2r && !(mi >= 0 && smol[k] == mi && r2 < hl2r);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) wq[warp][qn + __popc(m & ((1u << lane) - 1u))] = k;
+                    qn += __popc(m);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        const int kk = wq[warp][lane];
+                        pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
+                        __syncwarp();
+                        if (lane < qn - 32) wq[warp][lane] = wq[warp][32 + lane];
+                        __syncwarp();
+                        qn -= 32;
                     }
                 }
-            }
-            double dfx = fx, dfy = fy, dfz = fz, dec = ec, dev = ev;
-            for (int w = G >> 1; w > 0; w >>= 1) {
-                dfx += __shfl_xor_sync(0xffffffffu, dfx, w);
-                dfy += __shfl_xor_sync(0xffffffffu, dfy, w);
-                dfz += __shfl_xor_sync(0xffffffffu, dfz, w);
-                dec += __shfl_xor_sync(0xffffffffu, dec, w);
-                dev += __shfl_xor_sync(0xffffffffu, dev, w);
-            }
-            if (live && lg == 0) {
-                Fs[3 * hs + 0] = dfx;
-                Fs[3 * hs + 1] = dfy;
-                Fs[3 * hs + 2] = dfz;
-                ecs[hs] = 0.5 * ke * dec;
-                evs[hs] = 0.5 * dev;
+                if (lane < qn) {
+                    const int kk = wq[warp][lane];
+                    pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
+                }
+                __syncwarp();
+                // lane partials (a few pairs each) are reduced and accumulated
+                // in the arithmetic type -- FP64 warp instructions are
+                // expensive on this part -- and converted to FP64 once
+#pragma unroll
+                for (int w = 16; w > 0; w >>= 1) {
+                    fx += __shfl_xor_sync(0xffffffffu, fx, w);
+                    fy += __shfl_xor_sync(0xffffffffu, fy, w);
+                    fz += __shfl_xor_sync(0xffffffffu, fz, w);
+                    ec += __shfl_xor_sync(0xffffffffu, ec, w);
+                    ev += __shfl_xor_sync(0xffffffffu, ev, w);
+                }
+                if (lane == 0) {
+                    hacc[h][0] += fx;
+                    hacc[h][1] += fy;
+                    hacc[h][2] += fz;
+                    hacc[h][3] += ec;
+                    hacc[h][4] += ev;
+                }
             }
         }
+        __syncthreads();
+        for (int k = tid; k < nh; k += blockDim.x) {
+            const int hs = (int)(hidx[k] & 0x1fffffffu);
+            Fs[3 * hs + 0] = (double)hacc[k][0];
+            Fs[3 * hs + 1] = (double)hacc[k][1];
+            Fs[3 * hs + 2] = (double)hacc[k][2];
+            ecs[hs] = 0.5 * ke * (double)hacc[k][3];
+            evs[hs] = 0.5 * (double)hacc[k][4];
+        }
+        __syncthreads();
     }
 }
 

@@ -18,6 +18,7 @@ lib = C.CDLL(_LIB_PATH)
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2, -3, -4, -5
 FP64, MIXED = 0, 1
+METHOD_MAZE, METHOD_P3M = 0, 1
 SR_NONE, SR_BMH, SR_LJ = 0, 1, 2
 MAX_TYPES = 4
 MESH = {"q": 0, "qs": 1, "phi": 2, "y": 3, "sigma": 4}
@@ -41,7 +42,7 @@ class Params(C.Structure):
                 ("mesh", C.c_int32), ("order", C.c_int32), ("tol", C.c_double), ("dt", C.c_double),
                 ("predictor", C.c_int32), ("precision", C.c_int32), ("max_mg_iters", C.c_int32),
                 ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32), ("coulomb_k", C.c_double),
-                ("sr", C.POINTER(SRTable)), ("topology", C.POINTER(Topology))]
+                ("sr", C.POINTER(SRTable)), ("topology", C.POINTER(Topology)), ("method", C.c_int32)]
 
 
 class Energies(C.Structure):
@@ -65,13 +66,22 @@ class Timing(C.Structure):
                 ("timed_steps", C.c_int64), ("total_launches", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("predictor", C.c_int32), ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32),
+                ("diffusion_zc", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
+                ("trials", C.c_int32), ("steps", C.c_int32)]
+
+
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 _ctx = C.c_void_p
 _sig = {
     "p3maze_init": (C.c_int, [C.POINTER(Params), _dp, _dp, C.c_void_p, C.POINTER(_ctx)]),
     "p3maze_step": (C.c_int, [_ctx, C.c_int32]),
+    "p3maze_step_async": (C.c_int, [_ctx, C.c_int32]),
+    "p3maze_wait": (C.c_int, [_ctx]),
     "p3maze_reinit": (C.c_int, [_ctx]),
+    "p3maze_equilibrate": (C.c_int, [_ctx, C.c_int32, C.c_double]),
     "p3maze_destroy": (None, [_ctx]),
     "p3maze_energy": (C.c_int, [_ctx, C.POINTER(Energies)]),
     "p3maze_get_stats": (C.c_int, [_ctx, C.POINTER(Stats)]),
@@ -84,6 +94,7 @@ _sig = {
     "p3maze_set_timing": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_get_timing": (C.c_int, [_ctx, C.POINTER(Timing)]),
     "p3maze_set_graphs": (C.c_int, [_ctx, C.c_int32]),
+    "p3maze_autotune": (C.c_int, [_ctx, C.c_int32, C.POINTER(Tuning)]),
     "p3maze_smooth_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p]),
     "p3maze_last_error": (C.c_char_p, [_ctx]),
 }
@@ -147,7 +158,7 @@ class Context:
                  sr_table: dict | None = None, triples=None, bonded: dict | None = None,
                  order: int = 4, predictor: int = 3, precision: str = "fp64",
                  max_mg_iters: int = 0, pre_sweeps: int = 0, post_sweeps: int = 0,
-                 coulomb_k: float = 0.0, stream: int | None = None):
+                 coulomb_k: float = 0.0, stream: int | None = None, method: str = "maze"):
         self._h = _ctx()
         n = int(np.asarray(charges).shape[0])
         self.n = n
@@ -172,6 +183,7 @@ class Context:
         p.precision = {"fp64": FP64, "mixed": MIXED}[precision]
         p.max_mg_iters, p.pre_sweeps, p.post_sweeps = int(max_mg_iters), int(pre_sweeps), int(post_sweeps)
         p.coulomb_k = float(coulomb_k)
+        p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M}[method]
         tab = sr_table_from(sr_kind, sr_table or {})
         if tab is not None:
             keep.append(tab)
@@ -214,6 +226,18 @@ class Context:
 
     def step(self, n: int = 1):
         self._check(lib.p3maze_step(self._h, int(n)))
+
+    def step_async(self, n: int = 1):
+        """Queue n steps without waiting (graph steps); see wait()."""
+        self._check(lib.p3maze_step_async(self._h, int(n)))
+
+    def wait(self):
+        """Wait for queued steps; raises on a recorded solver failure."""
+        self._check(lib.p3maze_wait(self._h))
+
+    def equilibrate(self, nsteps: int, temperature: float):
+        """nsteps MD steps with velocity rescaling to temperature (K) after each."""
+        self._check(lib.p3maze_equilibrate(self._h, int(nsteps), float(temperature)))
 
     def reinit(self):
         self._check(lib.p3maze_reinit(self._h))
@@ -275,6 +299,12 @@ class Context:
     def set_timing(self, enable: bool = True):
         """Enable per-stage CUDA-event timing and reset the counters."""
         self._check(lib.p3maze_set_timing(self._h, 1 if enable else 0))
+
+    def autotune(self, steps_per_trial: int = 8) -> dict:
+        """Time candidate solver settings on real MD steps and keep the fastest."""
+        t = Tuning()
+        self._check(lib.p3maze_autotune(self._h, int(steps_per_trial), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
     def set_graphs(self, enable: bool = True):
         """Replay steady-state steps as CUDA graphs (default) or launch eagerly."""

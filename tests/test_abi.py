@@ -37,7 +37,7 @@ def test_library_exports_every_declared_function():
 def test_ctypes_layout_matches_c(tmp_path):
     from paper_2606_31379_b300 import p3maze as P
     structs = {"p3maze_params": P.Params, "p3maze_sr_table": P.SRTable, "p3maze_topology": P.Topology,
-               "p3maze_energies": P.Energies, "p3maze_stats": P.Stats, "p3maze_timing": P.Timing}
+               "p3maze_energies": P.Energies, "p3maze_stats": P.Stats, "p3maze_timing": P.Timing, "p3maze_tuning": P.Tuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "p3maze.h"', "int main(void){"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -215,3 +215,68 @@ def test_nacl_32k_128_sampled_parity(P, precision, ftol):
         # mixed mode: the FP32 q^s differs from the oracle's by ~1e-7 relative
         margin = 1e-6 * prm["tol"] if precision == "fp64" else 1e-8
         assert constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"]) <= prm["tol"] + margin
+
+
+def test_async_steps_match_blocking_steps(P, nacl512):
+    """p3maze_step_async + p3maze_wait run the same kernels as p3maze_step.
+    Charge assignment adds with atomics, so summation order (and the last
+    bits) may differ between runs: compared within the mixed tolerance."""
+    with _ctx(P, nacl512, precision="mixed", tol=1e-8) as a, _ctx(P, nacl512, precision="mixed", tol=1e-8) as b:
+        a.step(6)
+        b.step_async(6)
+        b.wait()
+        np.testing.assert_allclose(b.positions(), a.positions(), rtol=0, atol=1e-9)
+        assert rel_rms(b.forces(), a.forces()) < 1e-5
+        assert b.stats()["steps"] == a.stats()["steps"] == 6
+
+
+def test_p3m_baseline_reaches_same_field_with_more_iterations(P, nacl512):
+    """Real-space P3M baseline (Sec. 3.3): the same splitting, smoothing and
+    Verlet-predicted field, the Poisson equation solved directly (no
+    multiplier predictor) to max|M phi + (4pi/h) q^s| <= tol.  It reaches the
+    same constrained field as P3MaZe, and at equal tol it needs more V-cycles
+    per step (the comparison of Fig. 8)."""
+    iters = {}
+    for method in ("maze", "p3m"):
+        with _ctx(P, nacl512, method=method, tol=1e-7, precision="mixed") as ctx:
+            ctx.step(3)
+            it0 = ctx.stats()["total_iters"]
+            ctx.step(20)
+            st = ctx.stats()
+            iters[method] = (st["total_iters"] - it0) / 20
+            assert st["last_residual"] <= 1e-7
+            ref = oracle_full(nacl512, ctx.positions(), 0.30, 9.0, 32)
+            assert rel_rms(ctx.forces(), ref["F"]) < 1e-4
+            mf = O.mesh_fields(at_positions(nacl512, ctx.positions()), 0.30, 32)
+            res = constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"])
+            bound = 1e-7 if method == "maze" else 1e-7 * mf["h"] / (4 * np.pi)
+            assert res <= bound + 1e-8
+    assert iters["p3m"] > iters["maze"]
+
+
+def test_autotuner_keeps_results_within_tolerance(P, nacl512):
+    """The autotuner changes only solver settings (predictor, sweep counts,
+    diffusion tile depth): afterwards the field still satisfies the constraint
+    and the forces still match the oracle."""
+    with _ctx(P, nacl512, precision="mixed", tol=1e-8) as ctx:
+        ctx.step(4)
+        t = ctx.autotune(3)
+        assert t["predictor"] in (1, 2, 3)
+        assert (t["pre_sweeps"], t["post_sweeps"]) in ((1, 1), (2, 1), (1, 2), (2, 2), (3, 3))
+        assert t["diffusion_zc"] in (4, 8, 16)
+        assert t["trials"] >= 16 and t["ms_per_step"] <= t["initial_ms_per_step"]
+        assert ctx.stats()["steps"] == 4 + t["steps"]
+        ctx.step(2)
+        ref = oracle_full(nacl512, ctx.positions(), 0.30, 9.0, 32)
+        assert rel_rms(ctx.forces(), ref["F"]) < 1e-4
+        mf = O.mesh_fields(at_positions(nacl512, ctx.positions()), 0.30, 32)
+        assert constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"]) <= 1e-8 + 1e-9
+
+
+def test_equilibrate_sets_kinetic_temperature(P, nacl512):
+    """After p3maze_equilibrate the kinetic energy is (3n - 3) k_B T / 2."""
+    with _ctx(P, nacl512, precision="mixed", tol=1e-6) as ctx:
+        ctx.equilibrate(10, 1200.0)
+        ke = ctx.energy()["kinetic"]
+        assert ke == pytest.approx(0.5 * (3 * 512 - 3) * 0.0019872043 * 1200.0, rel=1e-9)
+        assert ctx.stats()["steps"] == 10
