@@ -179,7 +179,8 @@ typedef struct {
     int32_t predictor;          /* chosen multiplier predictor (0 for P3M)              */
     int32_t pre_sweeps;         /* chosen red-black Gauss-Seidel sweeps before / after  */
     int32_t post_sweeps;
-    int32_t diffusion_zc;       /* z planes per thread of the diffusion kernel          */
+    int32_t diffusion_zc;       /* z planes per thread (block) of the diffusion kernel  */
+    int32_t diffusion_fuse;     /* diffusion steps per launch: 1, or 4 (temporal blocking) */
     double ms_per_step;         /* measured with the chosen setting                    */
     double initial_ms_per_step; /* measured with the setting in use before tuning      */
     int32_t trials;             /* settings timed                                      */
@@ -297,8 +298,9 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
 
 /* Autotuner: time real MD steps under candidate settings and keep the
  * fastest -- multiplier predictor 1..3 (P3MaZe only), smoothing sweeps
- * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)} and the diffusion
- * kernel's z planes per thread in {4, 8, 16}.  None of them changes the
+ * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)}, and the diffusion
+ * kernel's z planes per thread in {4, 8, 16, 32} with, in mixed mode, 1 or 4
+ * diffusion steps fused per launch.  None of them changes the
  * converged field beyond tol (they change iteration counts and speed only).
  * Every trial runs 2 warm-up steps (graph capture) and steps_per_trial timed
  * steps (CUDA events); the system advances by all of them (out->steps).

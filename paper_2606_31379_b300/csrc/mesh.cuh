@@ -102,6 +102,143 @@ k_diffuse(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, dou
     }
 }
 
+// One diffusion step, FP32, four x points per thread (16-byte loads), for
+// meshes with n % 4 == 0.  A warp row covers 128 consecutive x; the x-1 and
+// x+4 neighbours of a quad come from the neighbouring lanes by shuffle (the
+// row ends load them).  Each thread marches zc planes keeping z neighbours
+// in registers.  SUM as in k_diffuse.
+template <bool SUM>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_diffuse4(int n, int zc, const float* __restrict__ in, float* __restrict__ out, float c,
+           double* __restrict__ partial) {
+    const int lane = threadIdx.x;
+    const int q = blockIdx.x * P3_BX + lane;     // quad index along x
+    const int x = 4 * q;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, n);
+    const bool live = x < n && y < n;
+    const int nq = n >> 2;
+    // lanes outside the mesh read point (0, 0) so every access stays in bounds
+    const int yy = live ? y : 0, xx = live ? x : 0;
+    const int xl = xx == 0 ? n - 1 : xx - 1;        // x - 1 (periodic)
+    const int xr = xx + 4 == n ? 0 : xx + 4;        // x + 4 (periodic)
+    const int ym = yy == 0 ? n - 1 : yy - 1, yp = yy == n - 1 ? 0 : yy + 1;
+    const int plane = n * n;
+    double acc = 0.0;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    auto ld4 = [&](int z, int row) { return in4[(z * plane + row * n + xx) >> 2]; };
+    float4 vm = ld4(z0 == 0 ? n - 1 : z0 - 1, yy);
+    float4 vc = ld4(z0, yy);
+    for (int z = z0; z < z1; ++z) {
+        const int zp = z == n - 1 ? 0 : z + 1;
+        const float4 vp = ld4(zp, yy);
+        const float4 a = ld4(z, ym);
+        const float4 b = ld4(z, yp);
+        // x neighbours across quads: lane-1's .w and lane+1's .x
+        float left = __shfl_up_sync(0xffffffffu, vc.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, vc.x, 1);
+        if (lane == 0 || q - 1 >= nq) left = in[z * plane + yy * n + xl];
+        if (lane == P3_BX - 1 || q + 1 >= nq) right = in[z * plane + yy * n + xr];
+        float4 o;
+        o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
+        o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
+        o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
+        o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
+        if (live) {
+            reinterpret_cast<float4*>(out)[(z * plane + yy * n + x) >> 2] = o;
+            if (SUM) acc += ((double)o.x + (double)o.y) + ((double)o.z + (double)o.w);
+        }
+        vm = vc;
+        vc = vp;
+    }
+    if (SUM) {
+        acc = block_sum(acc);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// S explicit diffusion steps fused in one launch (2.5D temporal blocking).
+// A block owns an output tile of TX x TY columns and zc planes; its
+// (TX + 2S) x (TY + 2S) threads each hold one column of the haloed tile and
+// stream z from z0 - S to z0 + zc + S.  When input plane z_in arrives, level
+// t (t diffusion steps applied) is formed at plane z_in - t from level t - 1:
+// its z neighbours come from the thread's register window, its x and y
+// neighbours from the plane of level t - 1 published to shared memory one
+// z-step earlier (double buffered, one barrier per z-step).  Level t is valid
+// on the tile shrunk by t on each side, so the interior receives S exact
+// steps; periodic wrap is applied to every loaded index.  SUM adds the FP64
+// block sum of the outputs (neutrality mean) as in k_diffuse.
+template <typename T, int S, int TX, int TY, bool SUM>
+__global__ void __launch_bounds__((TX + 2 * S) * (TY + 2 * S))
+k_diffuse_tb(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, double* __restrict__ partial) {
+    constexpr int WX = TX + 2 * S, WY = TY + 2 * S, W = WX * WY;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* sm = reinterpret_cast<T*>(sm_raw);  // [2 parities][S levels][W]
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * WX + tx;
+    const int gx = (int)blockIdx.x * TX + tx - S;
+    const int gy = (int)blockIdx.y * TY + ty - S;
+    const int x = ((gx % n) + n) % n, y = ((gy % n) + n) % n;
+    const int col = y * n + x, plane = n * n;
+    const int z0 = blockIdx.z * zc;
+    const int zend = min(z0 + zc, n);
+    const bool writer = tx >= S && tx < S + TX && ty >= S && ty < S + TY && gx < n && gy < n;
+    T win[S][3];
+#pragma unroll
+    for (int t = 0; t < S; ++t) win[t][0] = win[t][1] = win[t][2] = (T)0;
+    double acc = 0.0;
+    const int zstart = z0 - S;
+    const int nsteps = (zend - z0) + 2 * S;
+    // input planes are fetched two z-steps ahead so their latency overlaps
+    // the current step's work and barrier
+    auto fetch = [&](int zi) -> T {
+        int zw = zi % n;
+        if (zw < 0) zw += n;
+        return in[zw * plane + col];
+    };
+    T pf0 = fetch(zstart), pf1 = fetch(zstart + 1);
+    for (int st = 0; st < nsteps; ++st) {
+        const int zin = zstart + st;
+        const int cur = st & 1, prev = cur ^ 1;
+        const T v0 = pf0;
+        pf0 = pf1;
+        if (st + 2 < nsteps) pf1 = fetch(zin + 2);
+        win[0][0] = win[0][1];
+        win[0][1] = win[0][2];
+        win[0][2] = v0;
+        sm[(cur * S + 0) * W + tid] = v0;
+#pragma unroll
+        for (int t = 1; t <= S; ++t) {
+            T vt = (T)0;
+            if (tx >= t && tx < WX - t && ty >= t && ty < WY - t) {
+                const T* pl = sm + (prev * S + (t - 1)) * W;
+                const T mid = win[t - 1][1];
+                const T sxy = pl[tid - 1] + pl[tid + 1] + pl[tid - WX] + pl[tid + WX];
+                vt = mid + c * (sxy + win[t - 1][0] + win[t - 1][2] - (T)6 * mid);
+            }
+            if (t < S) {
+                win[t][0] = win[t][1];
+                win[t][1] = win[t][2];
+                win[t][2] = vt;
+                sm[(cur * S + t) * W + tid] = vt;
+            } else {
+                const int zo = zin - S;
+                if (writer && zo >= z0 && zo < zend) {
+                    out[zo * plane + col] = vt;
+                    if (SUM) acc += (double)vt;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (SUM) {
+        acc = block_sum(acc);
+        if (tid == 0) partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- reductions
 template <typename T>
 __global__ void k_sum_partial(int64_t m, const T* __restrict__ x, double* __restrict__ partial) {

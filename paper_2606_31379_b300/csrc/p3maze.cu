@@ -73,6 +73,7 @@ struct p3maze_ctx {
     int np = 0, N = 0, nc = 0, ncell = 0, prec = 0, pred = 3, itmax = 50, nu1 = 2, nu2 = 2, K = 0;
     int nmol = 0, nlev = 0, method = 0;
     int zc = 8;                          // z planes per thread in the diffusion step (tunable)
+    int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     int64_t P = 0;
     double L = 0, h = 0, inv_h = 0, alpha = 0, sigma = 0, rc = 0, c = 0, tol = 0, dt = 0, ke = 0;
@@ -270,6 +271,33 @@ int build_cells(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
+// Temporally blocked diffusion: tile 32 x 16 columns, S steps per launch.
+constexpr int kTbX = 32, kTbY = 16;
+inline dim3 tb_grid(int n, int zc) { return dim3((n + kTbX - 1) / kTbX, (n + kTbY - 1) / kTbY, (n + zc - 1) / zc); }
+inline unsigned tb_blocks(int n, int zc) { const dim3 g = tb_grid(n, zc); return g.x * g.y * g.z; }
+
+template <typename T, int S>
+void launch_tb_s(p3maze_ctx* ctx, bool last, const T* src, T* dst) {
+    const dim3 blk(kTbX + 2 * S, kTbY + 2 * S, 1);
+    const size_t smem = 2 * S * (size_t)blk.x * blk.y * sizeof(T);
+    if (last)
+        k_diffuse_tb<T, S, kTbX, kTbY, true><<<tb_grid(ctx->N, ctx->zc), blk, smem, ctx->stream>>>(
+            ctx->N, ctx->zc, src, dst, (T)ctx->c, ctx->partial);
+    else
+        k_diffuse_tb<T, S, kTbX, kTbY, false><<<tb_grid(ctx->N, ctx->zc), blk, smem, ctx->stream>>>(
+            ctx->N, ctx->zc, src, dst, (T)ctx->c, nullptr);
+}
+
+template <typename T>
+void launch_diffuse_tb(p3maze_ctx* ctx, int S, bool last, const T* src, T* dst) {
+    switch (S) {
+        case 1: launch_tb_s<T, 1>(ctx, last, src, dst); break;
+        case 2: launch_tb_s<T, 2>(ctx, last, src, dst); break;
+        case 3: launch_tb_s<T, 3>(ctx, last, src, dst); break;
+        default: launch_tb_s<T, 4>(ctx, last, src, dst); break;
+    }
+}
+
 template <typename T>
 int spread_smooth(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
@@ -284,6 +312,54 @@ int spread_smooth(p3maze_ctx* ctx) {
         k_sum_partial<T><<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->P, (const T*)ctx->qs, ctx->partial);
         k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_QSUM);
         count(ctx, P3MAZE_ST_SMOOTH, 2);
+    } else if constexpr (sizeof(T) == 4) {
+        T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
+        const T* src = (const T*)ctx->q;
+        if (ctx->fuse > 1) {
+            // S = fuse steps per launch (temporal blocking), then the rest
+            int done = 0, launches = 0;
+            while (done < ctx->K) {
+                const int S = std::min(ctx->fuse, ctx->K - done);
+                const bool last = done + S == ctx->K;
+                T* dst = last ? (T*)ctx->qs : tmp[launches & 1];
+                launch_diffuse_tb<T>(ctx, S, last, src, dst);
+                src = dst;
+                done += S;
+                ++launches;
+            }
+            k_sum_final<<<1, 1024, 0, s>>>((int)tb_blocks(ctx->N, ctx->zc), ctx->partial, ctx->dscal + S_QSUM);
+            count(ctx, P3MAZE_ST_SMOOTH, launches + 1);
+        } else if (ctx->N % 4 == 0) {
+            // one step per launch, four points per thread
+            const dim3 g((ctx->N / 4 + P3_BX - 1) / P3_BX, (ctx->N + P3_BY - 1) / P3_BY, (ctx->N + ctx->zc - 1) / ctx->zc);
+            for (int k = 0; k < ctx->K; ++k) {
+                const bool last = k == ctx->K - 1;
+                T* dst = last ? (T*)ctx->qs : tmp[k & 1];
+                if (last)
+                    k_diffuse4<true><<<g, kB3, 0, s>>>(ctx->N, ctx->zc, (const float*)src, (float*)dst, (float)ctx->c,
+                                                       ctx->partial);
+                else
+                    k_diffuse4<false><<<g, kB3, 0, s>>>(ctx->N, ctx->zc, (const float*)src, (float*)dst, (float)ctx->c,
+                                                        nullptr);
+                src = dst;
+            }
+            k_sum_final<<<1, 1024, 0, s>>>((int)(g.x * g.y * g.z), ctx->partial, ctx->dscal + S_QSUM);
+            count(ctx, P3MAZE_ST_SMOOTH, ctx->K + 1);
+        } else {
+            for (int k = 0; k < ctx->K; ++k) {
+                const bool last = k == ctx->K - 1;
+                T* dst = last ? (T*)ctx->qs : tmp[k & 1];
+                if (last)
+                    k_diffuse<T, true><<<gz(ctx->N, ctx->zc), kB3, 0, s>>>(ctx->N, ctx->zc, src, dst, (T)ctx->c,
+                                                                          ctx->partial);
+                else
+                    k_diffuse<T, false><<<gz(ctx->N, ctx->zc), kB3, 0, s>>>(ctx->N, ctx->zc, src, dst, (T)ctx->c,
+                                                                           nullptr);
+                src = dst;
+            }
+            k_sum_final<<<1, 1024, 0, s>>>((int)gz_blocks(ctx->N, ctx->zc), ctx->partial, ctx->dscal + S_QSUM);
+            count(ctx, P3MAZE_ST_SMOOTH, ctx->K + 1);
+        }
     } else {
         T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
         const T* src = (const T*)ctx->q;
@@ -837,7 +913,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     }
     std::vector<double> g = coarse_green(ctx->lev.back().n);
     ALLOC(ctx->gcoarse, 8 * g.size());
-    ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(1024, gz_blocks(ctx->N, 1)));
+    ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(ctx->N, 1)), tb_blocks(ctx->N, 1)));
     ALLOC(ctx->dscal, 8 * S_NSCAL);
     {
         const dim3 gr = resid_grid(ctx->N);
@@ -991,6 +1067,8 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->tol = p->tol;
     ctx->dt = p->dt;
     ctx->method = p->method;
+    ctx->zc = 8;
+    ctx->fuse = 1;
     ctx->res_scale = p->method == P3MAZE_METHOD_P3M ? 4.0 * kPi / h : 1.0;
     // P3M has no multiplier: every solve starts from the Verlet-predicted field
     ctx->pred = p->method == P3MAZE_METHOD_P3M ? 0 : (p->predictor == 0 ? 3 : p->predictor);
@@ -1255,7 +1333,7 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
 namespace {
 
 struct Setting {
-    int pred, nu1, nu2, zc;
+    int pred, nu1, nu2, zc, fuse;
 };
 
 // Run `warm` + `steps` steps under setting `cfg`; ms per timed step.
@@ -1264,6 +1342,7 @@ int tune_trial(p3maze_ctx* ctx, const Setting& cfg, int warm, int steps, double*
     ctx->nu1 = cfg.nu1;
     ctx->nu2 = cfg.nu2;
     ctx->zc = cfg.zc;
+    ctx->fuse = cfg.fuse;
     destroy_graphs(ctx);  // the setting is recorded in the graphs
     for (int k = 0; k < warm; ++k) {
         int rc = step_once(ctx);
@@ -1301,13 +1380,14 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     const bool timing = ctx->timing;
     ctx->timing = false;
     const int warm = 2;
-    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc};
+    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc, ctx->fuse};
     std::vector<Setting> cand;
     const int preds[3] = {1, 2, 3};
     const int sweeps[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
     const int np = ctx->method == P3MAZE_METHOD_P3M ? 1 : 3;
     for (int a = 0; a < np; ++a)
-        for (auto& sw : sweeps) cand.push_back({ctx->method == P3MAZE_METHOD_P3M ? 0 : preds[a], sw[0], sw[1], start.zc});
+        for (auto& sw : sweeps)
+            cand.push_back({ctx->method == P3MAZE_METHOD_P3M ? 0 : preds[a], sw[0], sw[1], start.zc, start.fuse});
     double initial = 0.0, best = 1e300;
     Setting chosen = start;
     int trials = 0, steps = 0;
@@ -1329,20 +1409,27 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
         }
     }
     if (!rc) {
-        const int zcs[3] = {4, 8, 16};
-        for (int z : zcs) {
-            if (z == chosen.zc) continue;
-            Setting c = chosen;
-            c.zc = z;
-            double ms = 0.0;
-            rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
-            trials += 1;
-            steps += warm + steps_per_trial;
-            if (rc) break;
-            if (ms < best) {
-                best = ms;
-                chosen = c;
+        // diffusion kernel: steps per launch (mixed: 1 or 4) x z planes per block
+        const int fuses[2] = {1, 4};
+        const int zcs[4] = {4, 8, 16, 32};
+        for (int f : fuses) {
+            if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
+            for (int z : zcs) {
+                if (z == chosen.zc && f == chosen.fuse) continue;
+                Setting c = chosen;
+                c.zc = z;
+                c.fuse = f;
+                double ms = 0.0;
+                rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
+                trials += 1;
+                steps += warm + steps_per_trial;
+                if (rc) break;
+                if (ms < best) {
+                    best = ms;
+                    chosen = c;
+                }
             }
+            if (rc) break;
         }
     }
     // keep the fastest setting
@@ -1350,12 +1437,14 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     ctx->nu1 = chosen.nu1;
     ctx->nu2 = chosen.nu2;
     ctx->zc = chosen.zc;
+    ctx->fuse = chosen.fuse;
     destroy_graphs(ctx);
     ctx->timing = timing;
     out->predictor = ctx->pred;
     out->pre_sweeps = ctx->nu1;
     out->post_sweeps = ctx->nu2;
     out->diffusion_zc = ctx->zc;
+    out->diffusion_fuse = ctx->fuse;
     out->ms_per_step = best;
     out->initial_ms_per_step = initial;
     out->trials = trials;

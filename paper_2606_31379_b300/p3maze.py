@@ -68,7 +68,7 @@ class Timing(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("predictor", C.c_int32), ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32),
-                ("diffusion_zc", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
+                ("diffusion_zc", C.c_int32), ("diffusion_fuse", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
                 ("trials", C.c_int32), ("steps", C.c_int32)]
 
 
