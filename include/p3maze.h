@@ -153,6 +153,7 @@ typedef struct {
     int32_t coarse_n;           /* points per axis of the coarsest level                  */
     int32_t cells_per_axis;     /* cell-list grid                                          */
     double sigma;               /* Gaussian width, A                                       */
+    int64_t device_bytes;       /* device memory the context allocated                     */
 } p3maze_stats;
 
 /* Pipeline stages timed by p3maze_set_timing / p3maze_get_timing. */
@@ -221,6 +222,11 @@ int p3maze_wait(p3maze_ctx *ctx);
 /* Full constraint solve from phi = 0 at the current positions and new forces:
  * the same initialisation as p3maze_init (after an external state change).   */
 int p3maze_reinit(p3maze_ctx *ctx);
+
+/* Device memory (bytes requested from cudaMalloc) that p3maze_init would
+ * allocate for these parameters; host-only, no CUDA call.  For admission
+ * control by memory (the allocator rounds each array up, add a margin).      */
+int p3maze_device_bytes(const p3maze_params *params, size_t *out);
 
 /* Free everything the context owns.  NULL is ignored.                          */
 void p3maze_destroy(p3maze_ctx *ctx);
@@ -306,6 +312,40 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
  * steps (CUDA events); the system advances by all of them (out->steps).
  * Errors as p3maze_step.                                                      */
 int p3maze_autotune(p3maze_ctx *ctx, int32_t steps_per_trial, p3maze_tuning *out);
+
+/* ---- batches: many systems advanced by shared launches ---------------------- */
+
+/* A batch advances several contexts (independent systems of any size on the
+ * current device) together: each batch step is ONE CUDA graph launch holding
+ * one MD step of every member as a parallel branch -- each member with its
+ * own device-side multigrid loop -- so their kernels overlap on the GPU.
+ * Members keep all their state resident.  The batch records a graph per
+ * pointer phase of its members (four at most) until the membership changes.
+ * Stepping a member by itself (p3maze_step) while it is in a batch is
+ * allowed between batch steps.                                                */
+typedef struct p3maze_batch p3maze_batch;
+
+/* cuda_stream: the caller's stream; each p3maze_batch_step is ordered after
+ * the work queued on it, and the stream after the step.                        */
+int p3maze_batch_create(void *cuda_stream, p3maze_batch **out);
+
+/* Add a context (same device).  A context whose multiplier history is not yet
+ * full is first advanced by the missing steps on its own (those steps test
+ * convergence on the host).  Invalidates the recorded graphs.                  */
+int p3maze_batch_add(p3maze_batch *batch, p3maze_ctx *ctx);
+
+/* Remove a member (waits for queued batch steps).  The context stays valid.    */
+int p3maze_batch_remove(p3maze_batch *batch, p3maze_ctx *ctx);
+
+/* Queue nsteps batch steps (one graph launch each); does not wait.             */
+int p3maze_batch_step(p3maze_batch *batch, int32_t nsteps);
+
+/* Wait for queued batch steps; report the first member with a solver failure. */
+int p3maze_batch_wait(p3maze_batch *batch);
+
+int p3maze_batch_size(const p3maze_batch *batch);
+void p3maze_batch_destroy(p3maze_batch *batch);
+const char *p3maze_batch_last_error(const p3maze_batch *batch);
 
 /* Message of the last failing call on ctx (or of the last failing init when
  * ctx is NULL).  Never NULL.                                                   */

@@ -3,6 +3,7 @@
 #include "p3maze.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -128,6 +129,7 @@ struct p3maze_ctx {
     int64_t launches[P3MAZE_NSTAGES] = {};
     int64_t timed_steps = 0;
     std::vector<void*> allocs;
+    size_t dev_bytes = 0;                // device memory this context allocated
     std::string err = "no error";
 };
 
@@ -163,6 +165,7 @@ int dalloc(p3maze_ctx* ctx, P** p, size_t bytes) {
                                              cudaGetErrorString(e));
     }
     ctx->allocs.push_back(d);
+    ctx->dev_bytes += bytes ? bytes : 16;
     *p = (P*)d;
     return P3MAZE_OK;
 }
@@ -966,6 +969,54 @@ int sync_scalars(p3maze_ctx* ctx) {
 
 }  // namespace
 
+// Device bytes p3maze_init allocates for these parameters: the same list of
+// arrays as setup() (requested sizes, before the allocator's rounding).
+size_t planned_bytes(const p3maze_params* p, int nlev) {
+    auto a = [](size_t b) { return b ? b : (size_t)16; };
+    const size_t n = (size_t)p->n_particles;
+    const bool mixed = p->precision == P3MAZE_MIXED;
+    const size_t tb = mixed ? 4 : 8;
+    const int N = p->mesh;
+    const size_t P = (size_t)N * N * N;
+    const int nc = std::max(1, (int)std::floor(p->box[0] / (0.5 * p->r_cut)));
+    const size_t ncell = (size_t)nc * nc * nc;
+    size_t b = 0;
+    for (int k = 0; k < 6; ++k) b += a(24 * n);          // r v F Fsr Flr Fb
+    for (int k = 0; k < 3; ++k) b += a(8 * n);           // hdt_acc mass Q
+    for (int k = 0; k < 5; ++k) b += a(4 * n);           // cell order ts ms cs
+    b += a(32 * n) + a(32 * n) + a(16 * n);              // xq xl64 xl32
+    b += a(24 * n) + a(8 * n) + a(8 * n);                // Fs ecs evs
+    b += a(4 * ncell) + a(4 * ncell) + a(4 * (ncell + 1));
+    if (p->types) b += a(4 * n);
+    b += a(tb * P) + a(tb * P);                          // q qs
+    for (int k = 0; k < 4; ++k) b += a(8 * P);           // phi, psi
+    b += a(8 * P);                                       // rfin
+    if (mixed) b += a(4 * P);                            // phi32
+    for (int k = 0; k < 4; ++k) b += a(8 * P);           // y ring
+    b += a(8 * P);                                       // sigma
+    int nn = N, ncoarse = N;
+    for (int l = 0; l < nlev; ++l) {
+        const size_t pts = (size_t)nn * nn * nn;
+        b += a(tb * pts) + a(tb * pts);
+        if (l == 0) b += a(tb * pts);
+        ncoarse = nn;
+        nn /= 2;
+    }
+    b += a(8 * (size_t)ncoarse * ncoarse * ncoarse);     // coarse pseudo-inverse kernel
+    b += a(8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(N, 1)), tb_blocks(N, 1)));
+    b += a(8 * S_NSCAL);
+    {
+        const dim3 gr = resid_grid(N);
+        b += a(8 * (size_t)gr.x * gr.y * gr.z);
+    }
+    b += a(sizeof(MGState));
+    if (p->topology && p->topology->n_molecules > 0) {
+        const size_t m = (size_t)p->topology->n_molecules;
+        b += a(4 * n) + a(12 * m) + a(8 * m) + a(8 * m);
+    }
+    return b;
+}
+
 // =============================================================== C ABI
 extern "C" {
 
@@ -1219,9 +1270,19 @@ int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
     return P3MAZE_OK;
 }
 
+int p3maze_device_bytes(const p3maze_params* p, size_t* out) {
+    if (!p || !out) return fail(nullptr, P3MAZE_ERR_INVALID, "NULL argument");
+    int nlev = 0, ncoarse = 0;
+    if (p->n_particles < 1 || !(p->box[0] > 0.0) || !(p->r_cut > 0.0) || !validate_mesh(p->mesh, &nlev, &ncoarse))
+        return fail(nullptr, P3MAZE_ERR_INVALID, "invalid particle count, box, r_cut or mesh");
+    *out = planned_bytes(p, nlev);
+    return P3MAZE_OK;
+}
+
 int p3maze_get_stats(p3maze_ctx* ctx, p3maze_stats* out) {
     if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
     read_solver_state(ctx);
+    ctx->st.device_bytes = (int64_t)ctx->dev_bytes;
     *out = ctx->st;
     return P3MAZE_OK;
 }
@@ -1473,6 +1534,240 @@ int p3maze_get_timing(p3maze_ctx* ctx, p3maze_timing* out) {
     out->total_launches = tot;
     return P3MAZE_OK;
 }
+
+// ------------------------------------------------------------------ batches
+}  // extern "C"
+
+struct p3maze_batch {
+    cudaStream_t origin = nullptr;      // capture and launch stream
+    cudaStream_t user = nullptr;        // caller's stream (fenced on entry and exit)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+    std::vector<p3maze_ctx*> members;
+    std::vector<cudaEvent_t> ev_done;   // per member: end of its branch
+    struct Phase {
+        bool valid = false;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        std::vector<int> icur;
+        std::vector<std::array<double*, 4>> yh;
+    };
+    Phase phases[kMaxGraphs];
+    std::string err = "no error";
+};
+
+namespace {
+
+int bfail(p3maze_batch* b, int code, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+#define BCK(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return bfail(b, P3MAZE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void batch_drop_graphs(p3maze_batch* b) {
+    for (auto& ph : b->phases) {
+        if (ph.x) cudaGraphExecDestroy(ph.x);
+        if (ph.g) cudaGraphDestroy(ph.g);
+        ph = p3maze_batch::Phase();
+    }
+}
+
+bool phase_matches(const p3maze_batch::Phase& ph, const std::vector<p3maze_ctx*>& m) {
+    if (!ph.valid || ph.icur.size() != m.size()) return false;
+    for (size_t i = 0; i < m.size(); ++i) {
+        if (ph.icur[i] != m[i]->icur) return false;
+        for (int k = 0; k < 4; ++k)
+            if (ph.yh[i][k] != m[i]->yh[k]) return false;
+    }
+    return true;
+}
+
+// One graph holding one MD step of every member, each member's step a branch
+// from a common fork (with its own device-side multigrid while node).
+int batch_capture(p3maze_batch* b, p3maze_batch::Phase& ph) {
+    BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
+    int rc = e == cudaSuccess ? P3MAZE_OK : bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
+    ph.icur.clear();
+    ph.yh.clear();
+    for (size_t i = 0; i < b->members.size() && !rc; ++i) {
+        p3maze_ctx* m = b->members[i];
+        e = cudaStreamWaitEvent(m->stream, b->ev_fork, 0);
+        if (e != cudaSuccess) {
+            rc = bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
+            break;
+        }
+        const int icur = m->icur;
+        std::array<double*, 4> yh;
+        for (int k = 0; k < 4; ++k) yh[k] = m->yh[k];
+        ph.icur.push_back(icur);
+        ph.yh.push_back(yh);
+        const bool timing = m->timing;
+        int64_t saved[P3MAZE_NSTAGES];
+        for (int st = 0; st < P3MAZE_NSTAGES; ++st) saved[st] = m->launches[st];
+        m->timing = false;
+        m->capturing = true;
+        rc = step_body(m, m->pred);
+        m->capturing = false;
+        m->timing = timing;
+        for (int st = 0; st < P3MAZE_NSTAGES; ++st) m->launches[st] = saved[st];
+        m->icur = icur;
+        for (int k = 0; k < 4; ++k) m->yh[k] = yh[k];
+        if (rc) {
+            rc = bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
+            break;
+        }
+        e = cudaEventRecord(b->ev_done[i], m->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev_done[i], 0);
+        if (e != cudaSuccess) rc = bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->origin, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : bfail(b, P3MAZE_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&ph.x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return bfail(b, P3MAZE_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    }
+    ph.g = g;
+    ph.valid = true;
+    return P3MAZE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int p3maze_batch_create(void* cuda_stream, p3maze_batch** out) {
+    if (!out) return bfail(nullptr, P3MAZE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    p3maze_batch* b = new (std::nothrow) p3maze_batch();
+    if (!b) return bfail(nullptr, P3MAZE_ERR_OOM, "host allocation failed");
+    b->user = (cudaStream_t)cuda_stream;
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->origin, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("batch create: ") + cudaGetErrorString(e);
+        p3maze_batch_destroy(b);
+        return bfail(nullptr, P3MAZE_ERR_CUDA, msg);
+    }
+    *out = b;
+    return P3MAZE_OK;
+}
+
+int p3maze_batch_add(p3maze_batch* b, p3maze_ctx* ctx) {
+    if (!b || !ctx) return bfail(b, P3MAZE_ERR_INVALID, "NULL argument");
+    for (p3maze_ctx* m : b->members)
+        if (m == ctx) return bfail(b, P3MAZE_ERR_INVALID, "context is already in the batch");
+    int dev = 0;
+    BCK(cudaGetDevice(&dev));
+    if (dev != ctx->device) return bfail(b, P3MAZE_ERR_INVALID, "context belongs to another device");
+    // a member joins with a full multiplier history (its first steps test
+    // convergence on the host and cannot be recorded in the batch graph)
+    if (ctx->nhist < ctx->pred) {
+        int rc = p3maze_step(ctx, ctx->pred - ctx->nhist);
+        if (rc) return bfail(b, rc, std::string("warm-up of the new member: ") + ctx->err);
+    }
+    BCK(cudaStreamSynchronize(ctx->stream));
+    cudaEvent_t ev;
+    BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->members.push_back(ctx);
+    b->ev_done.push_back(ev);
+    batch_drop_graphs(b);
+    return P3MAZE_OK;
+}
+
+int p3maze_batch_remove(p3maze_batch* b, p3maze_ctx* ctx) {
+    if (!b || !ctx) return bfail(b, P3MAZE_ERR_INVALID, "NULL argument");
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i] == ctx) {
+            BCK(cudaStreamSynchronize(b->origin));
+            cudaEventDestroy(b->ev_done[i]);
+            b->members.erase(b->members.begin() + (long)i);
+            b->ev_done.erase(b->ev_done.begin() + (long)i);
+            batch_drop_graphs(b);
+            return P3MAZE_OK;
+        }
+    return bfail(b, P3MAZE_ERR_INVALID, "context is not in the batch");
+}
+
+int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
+    if (!b) return bfail(nullptr, P3MAZE_ERR_INVALID, "batch is NULL");
+    if (nsteps < 0) return bfail(b, P3MAZE_ERR_INVALID, "nsteps must be >= 0");
+    if (b->members.empty() || nsteps == 0) return P3MAZE_OK;
+    BCK(cudaEventRecord(b->ev_in, b->user));
+    BCK(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    for (int k = 0; k < nsteps; ++k) {
+        p3maze_batch::Phase* ph = nullptr;
+        for (auto& c : b->phases)
+            if (phase_matches(c, b->members)) ph = &c;
+        if (!ph) {
+            for (auto& c : b->phases)
+                if (!c.valid) {
+                    ph = &c;
+                    break;
+                }
+            if (!ph) {
+                batch_drop_graphs(b);
+                ph = &b->phases[0];
+            }
+            int rc = batch_capture(b, *ph);
+            if (rc) return rc;
+        }
+        BCK(cudaGraphLaunch(ph->x, b->origin));
+        for (p3maze_ctx* m : b->members) {
+            m->icur = 1 - m->icur;
+            double* oldest = m->yh[3];
+            m->yh[3] = m->yh[2];
+            m->yh[2] = m->yh[1];
+            m->yh[1] = m->yh[0];
+            m->yh[0] = oldest;
+            m->st.steps += 1;
+        }
+    }
+    BCK(cudaEventRecord(b->ev_out, b->origin));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return P3MAZE_OK;
+}
+
+int p3maze_batch_wait(p3maze_batch* b) {
+    if (!b) return bfail(nullptr, P3MAZE_ERR_INVALID, "batch is NULL");
+    BCK(cudaStreamSynchronize(b->origin));
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        int rc = read_solver_state(b->members[i]);
+        if (rc) return bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + b->members[i]->err);
+    }
+    return P3MAZE_OK;
+}
+
+int p3maze_batch_size(const p3maze_batch* b) { return b ? (int)b->members.size() : 0; }
+
+void p3maze_batch_destroy(p3maze_batch* b) {
+    if (!b) return;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    batch_drop_graphs(b);
+    for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+const char* p3maze_batch_last_error(const p3maze_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
 
 const char* p3maze_last_error(const p3maze_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_init_error.c_str();

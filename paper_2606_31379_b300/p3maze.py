@@ -54,7 +54,7 @@ class Stats(C.Structure):
     _fields_ = [("last_iters", C.c_int32), ("last_residual", C.c_double), ("steps", C.c_int64),
                 ("total_iters", C.c_int64), ("init_iters", C.c_int32), ("smooth_steps", C.c_int32),
                 ("smooth_coeff", C.c_double), ("mg_levels", C.c_int32), ("coarse_n", C.c_int32),
-                ("cells_per_axis", C.c_int32), ("sigma", C.c_double)]
+                ("cells_per_axis", C.c_int32), ("sigma", C.c_double), ("device_bytes", C.c_int64)]
 
 
 NSTAGES = 9
@@ -83,6 +83,7 @@ _sig = {
     "p3maze_reinit": (C.c_int, [_ctx]),
     "p3maze_equilibrate": (C.c_int, [_ctx, C.c_int32, C.c_double]),
     "p3maze_destroy": (None, [_ctx]),
+    "p3maze_device_bytes": (C.c_int, [C.POINTER(Params), C.POINTER(C.c_size_t)]),
     "p3maze_energy": (C.c_int, [_ctx, C.POINTER(Energies)]),
     "p3maze_get_stats": (C.c_int, [_ctx, C.POINTER(Stats)]),
     "p3maze_get_positions": (C.c_int, [_ctx, _dp]),
@@ -97,6 +98,14 @@ _sig = {
     "p3maze_autotune": (C.c_int, [_ctx, C.c_int32, C.POINTER(Tuning)]),
     "p3maze_smooth_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p]),
     "p3maze_last_error": (C.c_char_p, [_ctx]),
+    "p3maze_batch_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "p3maze_batch_add": (C.c_int, [C.c_void_p, _ctx]),
+    "p3maze_batch_remove": (C.c_int, [C.c_void_p, _ctx]),
+    "p3maze_batch_step": (C.c_int, [C.c_void_p, C.c_int32]),
+    "p3maze_batch_wait": (C.c_int, [C.c_void_p]),
+    "p3maze_batch_size": (C.c_int, [C.c_void_p]),
+    "p3maze_batch_destroy": (None, [C.c_void_p]),
+    "p3maze_batch_last_error": (C.c_char_p, [C.c_void_p]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -147,73 +156,94 @@ def sr_table_from(kind: str, table: dict) -> SRTable | None:
     return t
 
 
+def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float, mesh: int,
+                 tol: float, dt: float, vel=None, types=None, sr_kind: str = "none",
+                 sr_table: dict | None = None, triples=None, bonded: dict | None = None,
+                 order: int = 4, predictor: int = 3, precision: str = "fp64",
+                 max_mg_iters: int = 0, pre_sweeps: int = 0, post_sweeps: int = 0,
+                 coulomb_k: float = 0.0, method: str = "maze"):
+    """p3maze_params for these arguments, plus the arrays it points into
+    (keep them alive while the struct is used)."""
+    n = int(np.asarray(charges).shape[0])
+    pos = _f64(pos, (n, 3))
+    vel = None if vel is None else _f64(vel, (n, 3))
+    q = _f64(charges)
+    m = _f64(masses)
+    p = Params()
+    p.box[0] = p.box[1] = p.box[2] = float(box)
+    p.n_particles = n
+    p.charges = _ptr(q)
+    p.masses = _ptr(m)
+    keep = {"pos": pos, "vel": vel, "q": q, "m": m}
+    if types is not None:
+        t = np.ascontiguousarray(types, dtype=np.int32)
+        keep["types"] = t
+        p.types = _ptr(t, C.c_int32)
+    p.alpha, p.r_cut, p.mesh, p.order = float(alpha), float(r_cut), int(mesh), int(order)
+    p.tol, p.dt, p.predictor = float(tol), float(dt), int(predictor)
+    p.precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    p.max_mg_iters, p.pre_sweeps, p.post_sweeps = int(max_mg_iters), int(pre_sweeps), int(post_sweeps)
+    p.coulomb_k = float(coulomb_k)
+    p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M}[method]
+    tab = sr_table_from(sr_kind, sr_table or {})
+    if tab is not None:
+        keep["sr"] = tab
+        p.sr = C.pointer(tab)
+    if triples is not None and len(triples):
+        tri = np.ascontiguousarray(triples, dtype=np.int32).reshape(-1, 3)
+        topo = Topology()
+        topo.n_molecules = tri.shape[0]
+        topo.triples = _ptr(tri, C.c_int32)
+        topo.kb, topo.r0 = float(bonded["kb"]), float(bonded["r0"])
+        topo.ka, topo.theta0 = float(bonded["ka"]), float(bonded["theta0"])
+        keep["tri"], keep["topo"] = tri, topo
+        p.topology = C.pointer(topo)
+    return p, keep
+
+
+def system_kwargs(system) -> dict:
+    """Context/build_params keyword arguments of a synth.System."""
+    kw = dict(vel=system.vel, types=system.types, sr_kind=system.sr_kind, sr_table=system.sr_table)
+    if system.angles is not None and len(system.angles):
+        kw["triples"] = system.angles          # (h1, o, h2)
+        kw["bonded"] = system.bonded
+    return kw
+
+
+def device_bytes(system, **kw) -> int:
+    """Device memory p3maze_init would allocate for this system and setting
+    (host-only; p3maze_device_bytes)."""
+    p, keep = build_params(system.pos, system.charge, system.mass, system.box, **system_kwargs(system), **kw)
+    out = C.c_size_t()
+    rc = lib.p3maze_device_bytes(C.byref(p), C.byref(out))
+    if rc:
+        raise P3MaZeError(rc, lib.p3maze_last_error(None).decode())
+    return int(out.value)
+
+
 class Context:
     """One periodic system resident on the current CUDA device.
 
     Parameters follow p3maze_params; `stream` is a raw cudaStream_t handle
     (e.g. torch.cuda.Stream().cuda_stream) or None for the default stream."""
 
-    def __init__(self, pos, charges, masses, box: float, *, alpha: float, r_cut: float, mesh: int,
-                 tol: float, dt: float, vel=None, types=None, sr_kind: str = "none",
-                 sr_table: dict | None = None, triples=None, bonded: dict | None = None,
-                 order: int = 4, predictor: int = 3, precision: str = "fp64",
-                 max_mg_iters: int = 0, pre_sweeps: int = 0, post_sweeps: int = 0,
-                 coulomb_k: float = 0.0, stream: int | None = None, method: str = "maze"):
+    def __init__(self, pos, charges, masses, box: float, *, stream: int | None = None, **kw):
         self._h = _ctx()
-        n = int(np.asarray(charges).shape[0])
-        self.n = n
-        self.mesh_n = int(mesh)
+        p, keep = build_params(pos, charges, masses, box, **kw)
+        self.n = int(p.n_particles)
+        self.mesh_n = int(p.mesh)
         self.box = float(box)
-        pos = _f64(pos, (n, 3))
-        vel = None if vel is None else _f64(vel, (n, 3))
-        q = _f64(charges)
-        m = _f64(masses)
-        p = Params()
-        p.box[0] = p.box[1] = p.box[2] = float(box)
-        p.n_particles = n
-        p.charges = _ptr(q)
-        p.masses = _ptr(m)
-        keep = [pos, vel, q, m]
-        if types is not None:
-            t = np.ascontiguousarray(types, dtype=np.int32)
-            keep.append(t)
-            p.types = _ptr(t, C.c_int32)
-        p.alpha, p.r_cut, p.mesh, p.order = float(alpha), float(r_cut), int(mesh), int(order)
-        p.tol, p.dt, p.predictor = float(tol), float(dt), int(predictor)
-        p.precision = {"fp64": FP64, "mixed": MIXED}[precision]
-        p.max_mg_iters, p.pre_sweeps, p.post_sweeps = int(max_mg_iters), int(pre_sweeps), int(post_sweeps)
-        p.coulomb_k = float(coulomb_k)
-        p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M}[method]
-        tab = sr_table_from(sr_kind, sr_table or {})
-        if tab is not None:
-            keep.append(tab)
-            p.sr = C.pointer(tab)
-        if triples is not None and len(triples):
-            tri = np.ascontiguousarray(triples, dtype=np.int32).reshape(-1, 3)
-            topo = Topology()
-            topo.n_molecules = tri.shape[0]
-            topo.triples = _ptr(tri, C.c_int32)
-            topo.kb, topo.r0 = float(bonded["kb"]), float(bonded["r0"])
-            topo.ka, topo.theta0 = float(bonded["ka"]), float(bonded["theta0"])
-            keep += [tri, topo]
-            p.topology = C.pointer(topo)
-        rc = lib.p3maze_init(C.byref(p), _ptr(pos), None if vel is None else _ptr(vel),
+        vel = keep["vel"]
+        rc = lib.p3maze_init(C.byref(p), _ptr(keep["pos"]), None if vel is None else _ptr(vel),
                              C.c_void_p(stream or 0), C.byref(self._h))
         if rc:
             raise P3MaZeError(rc, lib.p3maze_last_error(None).decode())
-        self.precision = precision
+        self.precision = kw.get("precision", "fp64")
 
     @classmethod
     def from_system(cls, system, **kw) -> "Context":
         """Build from a synth.System (positions, charges, tables, topology)."""
-        triples = None
-        bonded = None
-        if system.angles is not None and len(system.angles):
-            triples = system.angles          # (h1, o, h2)
-            bonded = system.bonded
-        return cls(system.pos, system.charge, system.mass, system.box, vel=system.vel,
-                   types=system.types, sr_kind=system.sr_kind, sr_table=system.sr_table,
-                   triples=triples, bonded=bonded, **kw)
+        return cls(system.pos, system.charge, system.mass, system.box, **system_kwargs(system), **kw)
 
     # ------------------------------------------------------------------ calls
     def _check(self, rc: int):
@@ -333,3 +363,47 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Several contexts advanced together: one CUDA graph launch per batch
+    step holds one MD step of every member (p3maze_batch_*)."""
+
+    def __init__(self, stream: int | None = None):
+        self._h = C.c_void_p()
+        rc = lib.p3maze_batch_create(C.c_void_p(stream or 0), C.byref(self._h))
+        if rc:
+            raise P3MaZeError(rc, lib.p3maze_last_error(None).decode())
+        self.members: list[Context] = []
+
+    def _check(self, rc: int):
+        if rc:
+            raise P3MaZeError(rc, lib.p3maze_batch_last_error(self._h).decode())
+
+    def add(self, ctx: Context):
+        self._check(lib.p3maze_batch_add(self._h, ctx._h))
+        self.members.append(ctx)
+
+    def remove(self, ctx: Context):
+        self._check(lib.p3maze_batch_remove(self._h, ctx._h))
+        self.members.remove(ctx)
+
+    def step(self, n: int = 1):
+        self._check(lib.p3maze_batch_step(self._h, int(n)))
+
+    def wait(self):
+        self._check(lib.p3maze_batch_wait(self._h))
+
+    def __len__(self):
+        return int(lib.p3maze_batch_size(self._h))
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.p3maze_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,67 @@
+"""Batched stepping (one graph launch advances every member by one MD step)
+and the device-memory estimate used for admission."""
+import numpy as np
+import pytest
+
+from paper_2606_31379_b300 import synth as S
+from tests.parity_helpers import rel_rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2606_31379_b300 import p3maze
+    return p3maze
+
+
+def _systems():
+    return [
+        (S.nacl_melt(512, 25.2, seed=1), dict(mesh=32, r_cut=9.0, dt=1.0)),
+        (S.nacl_melt(216, 18.9, seed=8), dict(mesh=24, r_cut=9.0, dt=1.0)),
+        (S.spcfw_water(64, 12.42, seed=3), dict(mesh=16, r_cut=6.0, dt=0.5)),
+    ]
+
+
+def _ctx(P, system, precision, **kw):
+    return P.Context.from_system(system, alpha=0.30, tol=1e-9, precision=precision, **kw)
+
+
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-9), ("mixed", 1e-5)])
+def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, tol):
+    total = 12
+    alone = []
+    for system, kw in _systems():
+        with _ctx(P, system, precision, **kw) as c:
+            c.step(total)
+            alone.append((c.positions(), c.forces(), c.stats()["steps"]))
+    ctxs = [_ctx(P, system, precision, **kw) for system, kw in _systems()]
+    batch = P.Batch()
+    try:
+        for c in ctxs:
+            batch.add(c)                      # each joins after its 3 warm-up steps
+        assert len(batch) == 3
+        batch.step(total - 3)
+        batch.wait()
+        for c, (pos, F, steps) in zip(ctxs, alone):
+            assert c.stats()["steps"] == steps == total
+            np.testing.assert_allclose(c.positions(), pos, rtol=0, atol=1e-9 if precision == "fp64" else 1e-7)
+            assert rel_rms(c.forces(), F) < tol
+        # membership change: drop one, keep stepping, it can still step alone
+        batch.remove(ctxs[1])
+        batch.step(2)
+        batch.wait()
+        ctxs[1].step(1)
+        assert ctxs[0].stats()["steps"] == total + 2 and ctxs[1].stats()["steps"] == total + 1
+    finally:
+        batch.close()
+        for c in ctxs:
+            c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_bytes_estimate_matches_allocation(P, precision):
+    for system, kw in _systems():
+        est = P.device_bytes(system, alpha=0.30, tol=1e-6, precision=precision, **kw)
+        with _ctx(P, system, precision, **kw) as c:
+            assert c.stats()["device_bytes"] == est
