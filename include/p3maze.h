@@ -344,6 +344,15 @@ int p3maze_batch_step(p3maze_batch *batch, int32_t nsteps);
 int p3maze_batch_wait(p3maze_batch *batch);
 
 int p3maze_batch_size(const p3maze_batch *batch);
+
+/* P3MAZE_BATCH_SHARED_GRAPH (default): one graph launch per batch step, the
+ * graph recorded again after every membership change.  P3MAZE_BATCH_PER_MEMBER:
+ * each member replays its own cached step graph on its own stream (forked
+ * from and joined to the batch stream) -- one launch per member, no
+ * re-recording when members come and go; used by the serving loop.             */
+#define P3MAZE_BATCH_SHARED_GRAPH 0
+#define P3MAZE_BATCH_PER_MEMBER   1
+int p3maze_batch_set_mode(p3maze_batch *batch, int32_t mode);
 void p3maze_batch_destroy(p3maze_batch *batch);
 const char *p3maze_batch_last_error(const p3maze_batch *batch);
 

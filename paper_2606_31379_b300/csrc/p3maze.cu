@@ -907,10 +907,17 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         int l0 = 0;
         while (l0 < ctx->nlev - 1 && ctx->lev[l0].n > kBlockLevelMax) ++l0;
         ctx->blk_smem = vcycle_block_smem(ctx->lev[l0].n, ctx->nlev - l0, tb);
-        cudaError_t ea = mixed ? cudaFuncSetAttribute(k_vcycle_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)ctx->blk_smem)
-                               : cudaFuncSetAttribute(k_vcycle_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)ctx->blk_smem);
+        // The limit is an attribute of the kernel, shared by every context in
+        // the process: only ever raise it, never lower it below what another
+        // context's launches need.
+        cudaFuncAttributes fa{};
+        cudaError_t ea = mixed ? cudaFuncGetAttributes(&fa, k_vcycle_block<float>)
+                               : cudaFuncGetAttributes(&fa, k_vcycle_block<double>);
+        if (ea == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < ctx->blk_smem)
+            ea = mixed ? cudaFuncSetAttribute(k_vcycle_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ctx->blk_smem)
+                       : cudaFuncSetAttribute(k_vcycle_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ctx->blk_smem);
         if (ea != cudaSuccess)
             return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory for the block V-cycle: ") + cudaGetErrorString(ea));
     }
@@ -1552,6 +1559,7 @@ struct p3maze_batch {
         std::vector<std::array<double*, 4>> yh;
     };
     Phase phases[kMaxGraphs];
+    int mode = 0;                       // P3MAZE_BATCH_SHARED_GRAPH or P3MAZE_BATCH_PER_MEMBER
     std::string err = "no error";
 };
 
@@ -1710,6 +1718,24 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
     if (b->members.empty() || nsteps == 0) return P3MAZE_OK;
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    if (b->mode == P3MAZE_BATCH_PER_MEMBER) {
+        // each member replays its own cached step graph on its own stream,
+        // forked from and joined to the batch stream
+        for (int k = 0; k < nsteps; ++k) {
+            BCK(cudaEventRecord(b->ev_fork, b->origin));
+            for (size_t i = 0; i < b->members.size(); ++i) {
+                p3maze_ctx* m = b->members[i];
+                BCK(cudaStreamWaitEvent(m->stream, b->ev_fork, 0));
+                int rc = step_once(m);
+                if (rc) return bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
+                BCK(cudaEventRecord(b->ev_done[i], m->stream));
+                BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
+            }
+        }
+        BCK(cudaEventRecord(b->ev_out, b->origin));
+        BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+        return P3MAZE_OK;
+    }
     for (int k = 0; k < nsteps; ++k) {
         p3maze_batch::Phase* ph = nullptr;
         for (auto& c : b->phases)
@@ -1754,6 +1780,15 @@ int p3maze_batch_wait(p3maze_batch* b) {
 }
 
 int p3maze_batch_size(const p3maze_batch* b) { return b ? (int)b->members.size() : 0; }
+
+int p3maze_batch_set_mode(p3maze_batch* b, int32_t mode) {
+    if (!b) return bfail(nullptr, P3MAZE_ERR_INVALID, "batch is NULL");
+    if (mode != P3MAZE_BATCH_SHARED_GRAPH && mode != P3MAZE_BATCH_PER_MEMBER)
+        return bfail(b, P3MAZE_ERR_INVALID, "unknown batch mode");
+    BCK(cudaStreamSynchronize(b->origin));
+    b->mode = mode;
+    return P3MAZE_OK;
+}
 
 void p3maze_batch_destroy(p3maze_batch* b) {
     if (!b) return;

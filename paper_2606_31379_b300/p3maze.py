@@ -104,6 +104,7 @@ _sig = {
     "p3maze_batch_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "p3maze_batch_wait": (C.c_int, [C.c_void_p]),
     "p3maze_batch_size": (C.c_int, [C.c_void_p]),
+    "p3maze_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "p3maze_batch_destroy": (None, [C.c_void_p]),
     "p3maze_batch_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -369,12 +370,16 @@ class Batch:
     """Several contexts advanced together: one CUDA graph launch per batch
     step holds one MD step of every member (p3maze_batch_*)."""
 
-    def __init__(self, stream: int | None = None):
+    SHARED_GRAPH, PER_MEMBER = 0, 1
+
+    def __init__(self, stream: int | None = None, mode: str = "shared"):
         self._h = C.c_void_p()
         rc = lib.p3maze_batch_create(C.c_void_p(stream or 0), C.byref(self._h))
         if rc:
             raise P3MaZeError(rc, lib.p3maze_last_error(None).decode())
         self.members: list[Context] = []
+        if mode != "shared":
+            self._check(lib.p3maze_batch_set_mode(self._h, {"per_member": self.PER_MEMBER}[mode]))
 
     def _check(self, rc: int):
         if rc:

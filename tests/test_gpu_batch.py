@@ -27,8 +27,9 @@ def _ctx(P, system, precision, **kw):
     return P.Context.from_system(system, alpha=0.30, tol=1e-9, precision=precision, **kw)
 
 
-@pytest.mark.parametrize("precision, tol", [("fp64", 1e-9), ("mixed", 1e-5)])
-def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, tol):
+@pytest.mark.parametrize("precision, tol, mode", [("fp64", 1e-9, "shared"), ("mixed", 1e-5, "shared"),
+                                                 ("fp64", 1e-9, "per_member")])
+def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, tol, mode):
     total = 12
     alone = []
     for system, kw in _systems():
@@ -36,7 +37,7 @@ def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, tol):
             c.step(total)
             alone.append((c.positions(), c.forces(), c.stats()["steps"]))
     ctxs = [_ctx(P, system, precision, **kw) for system, kw in _systems()]
-    batch = P.Batch()
+    batch = P.Batch(mode=mode)
     try:
         for c in ctxs:
             batch.add(c)                      # each joins after its 3 warm-up steps
@@ -65,3 +66,20 @@ def test_device_bytes_estimate_matches_allocation(P, precision):
         est = P.device_bytes(system, alpha=0.30, tol=1e-6, precision=precision, **kw)
         with _ctx(P, system, precision, **kw) as c:
             assert c.stats()["device_bytes"] == est
+
+
+def test_contexts_with_different_shared_memory_needs_coexist(P):
+    """The shared-memory V-cycle kernel's limit is per process: a context with
+    a small mesh created after one with a large need must not lower it (FP64
+    28^3 needs more than 24^3)."""
+    big = S.nacl_melt(300, 21.1, seed=31)
+    small = S.nacl_melt(216, 18.9, seed=32)
+    a = P.Context.from_system(big, alpha=0.30, r_cut=9.0, mesh=28, tol=1e-8, dt=1.0, precision="fp64")
+    b = P.Context.from_system(small, alpha=0.30, r_cut=9.0, mesh=24, tol=1e-8, dt=1.0, precision="fp64")
+    try:
+        a.step(6)                      # graph steps of the 28^3 context after the 24^3 set-up
+        b.step(6)
+        assert a.stats()["steps"] == 6 and b.stats()["steps"] == 6
+    finally:
+        a.close()
+        b.close()
