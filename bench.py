@@ -56,30 +56,73 @@ def workload_config(prm, precision):
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """SM clock and throttle reasons sampled during the timed region: an NVML
+    thread polling every ~2 ms (nvidia-smi -lms 200 as a fallback)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
     def __init__(self, gpu_index: str | None):
         self.gpu = gpu_index
+        self.samples = []
+        self._stop = False
+        self._thread = None
         self.proc = None
         self.path = None
+        self.handle = None
+
+    def _nvml_handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+            return pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(int(self.gpu or 0))
+
+    def _poll(self):
+        import pynvml
+        while not self._stop:
+            try:
+                sm = pynvml.nvmlDeviceGetClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
+                smax = pynvml.nvmlDeviceGetMaxClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
+                reasons = pynvml.nvmlDeviceGetCurrentClocksEventReasons(self.handle)
+                self.samples.append((sm, smax, reasons))
+            except Exception:
+                pass
+            time.sleep(0.002)
 
     def __enter__(self):
+        import threading
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
-            if self.gpu is not None:
-                cmd += ["-i", self.gpu]
-            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.handle = self._nvml_handle()
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+            t0 = time.time()
+            while not self.samples and time.time() - t0 < 1.0:
+                time.sleep(0.001)
+            self.samples.clear()            # keep only samples taken inside the region
         except Exception:
-            self.proc = None
+            self.handle = None
+            try:
+                fd, self.path = tempfile.mkstemp(suffix=".csv")
+                os.close(fd)
+                fields = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+                cmd = ["nvidia-smi", f"--query-gpu={fields}", "--format=csv,noheader,nounits", "-lms", "200"]
+                if self.gpu is not None:
+                    cmd += ["-i", self.gpu]
+                self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            except Exception:
+                self.proc = None
         return self
 
     def __exit__(self, *a):
+        self._stop = True
+        if self._thread is not None:
+            self._thread.join(timeout=1.0)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -88,6 +131,11 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self) -> dict:
+        if self.samples:
+            sm = [s[0] for s in self.samples]
+            reasons = sorted({k for s in self.samples for k, bit in self.REASONS.items() if s[2] & bit})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(s[1] for s in self.samples),
+                    "samples": len(sm), "source": "nvml", "reasons": reasons}
         if not self.path or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm, smax, reasons = [], [], set()
@@ -108,7 +156,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "reasons": sorted(reasons)}
+                "source": "nvidia-smi", "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------- roofline
@@ -374,9 +422,79 @@ def run_ours(args) -> int:
         "gpu_launches_per_step": tm["total_launches"] / args.steps,
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
     }
+    if not args.no_serve:
+        line["served"] = served_run(stream.cuda_stream, n_req=48, steps=200, slots=16)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system, prm)
     print(json.dumps(line))
+    return 0
+
+
+def served_run(stream, n_req: int, steps: int, slots: int, rate: float = 200.0) -> dict:
+    """The served-batch workload at reduced count: Poisson arrivals, molten
+    NaCl or SPC/Fw (50/50), 216-32768 atoms log-uniform, mesh ~0.8 A, each
+    advanced `steps` steps, admitted by device memory into `slots` slots."""
+    from paper_2606_31379_b300.serve import GpuBackend, Server, poisson_requests
+    reqs = poisson_requests(n_req, rate=rate, seed=4, steps=steps)
+    be = GpuBackend(precision="mixed", stream=stream)
+    try:
+        m = Server(be, budget_bytes=60 << 30, max_slots=slots).run(reqs)
+    finally:
+        be.shutdown()
+    m["config"] = {"requests": n_req, "arrival_rate_per_s": rate, "steps_per_request": steps, "slots": slots,
+                   "sizes": "216-32768 atoms log-uniform, molten NaCl / SPC/Fw 50:50, mesh ~0.8 A",
+                   "precision": "mixed", "start": "seeded random configurations"}
+    return m
+
+
+SWEEP = [("nacl_4k", 4096, 50.45, 64), ("nacl_32k", 32768, 100.9, 128), ("nacl_262k", 262144, 201.8, 256),
+         ("nacl_1m", 1000000, 315.4, 384)]
+
+
+def run_sweep(args) -> int:
+    """Linear-scaling sweep of molten NaCl (and the SPC/Fw workload): one JSON
+    line per size with per-stage time, V-cycles per step and the smoothing
+    kernel's algorithmic bandwidth."""
+    import torch
+    from paper_2606_31379_b300 import p3maze as P
+    from paper_2606_31379_b300 import synth as S
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks = measured_peaks()
+    only = set(args.sweep_cases.split(",")) if args.sweep_cases else None
+    cases = [(name, S.nacl_melt(n, box, seed=5 + i), mesh, 1.0)
+             for i, (name, n, box, mesh) in enumerate(SWEEP)
+             if (args.sweep_max is None or n <= args.sweep_max) and (only is None or name in only)]
+    if not args.no_water and (only is None or "spcfw_30k" in only):
+        cases.append(("spcfw_30k", S.spcfw_water(30000, 96.4, seed=3), 128, 0.5))
+    for name, system, mesh, dt in cases:
+        kw = dict(alpha=S.EWALD_ALPHA, r_cut=S.R_CUT, mesh=mesh, tol=S.TOL, dt=dt, precision=args.precision,
+                  stream=stream.cuda_stream)
+        with P.Context.from_system(system, **kw) as eq:
+            eq.equilibrate(args.equilibrate, 1200.0 if system.sr_kind == "bmh" else 298.15)
+            system.pos, system.vel = eq.positions(), eq.velocities()
+        with P.Context.from_system(system, **kw) as ctx:
+            ctx.step(args.warmup)
+            tuning = ctx.autotune(4)
+            ctx.set_timing(True)
+            it0 = ctx.stats()["total_iters"]
+            ms = time_context(ctx, torch, stream, args.steps, flush)
+            tm = ctx.timing()
+            st = ctx.stats()
+        stage_us = {k: 1e3 * v / args.steps for k, v in tm["ms"].items()}
+        b = 4 if args.precision == "mixed" else 8
+        K = st["smooth_steps"]
+        smooth_gbs = 2.0 * mesh ** 3 * b * K / (stage_us["smooth"] * 1e-6) / 1e9
+        ms_step = sum(ms) / args.steps
+        print(json.dumps({
+            "workload": name, "n_particles": system.n, "mesh": mesh, "ms_per_step": ms_step,
+            "ns_per_day": ns_per_day(ms_step * 1e-3, dt), "mg_iters_per_step": (st["total_iters"] - it0) / args.steps,
+            "stage_us": stage_us, "smooth_steps": K, "smooth_algorithmic_gbs": smooth_gbs,
+            "smooth_frac_of_measured_hbm": smooth_gbs / peaks["hbm_gbs"], "tuning": tuning,
+            "device_bytes": st["device_bytes"], "precision": args.precision,
+        }), flush=True)
     return 0
 
 
@@ -390,6 +508,12 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the solver-setting autotuner")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-batch measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="linear-scaling sweep (4096 to 1e6 ions) and SPC/Fw 90000 atoms, one line per size")
+    ap.add_argument("--sweep-max", type=int, default=None)
+    ap.add_argument("--sweep-cases", type=str, default=None, help="comma-separated subset of the sweep")
+    ap.add_argument("--no-water", action="store_true")
     ap.add_argument("--equilibrate", type=int, default=400,
                     help="untimed velocity-rescaled steps at 1200 K before any measurement")
     ap.add_argument("--no-graphs", action="store_true",
@@ -399,6 +523,8 @@ def main() -> int:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 
