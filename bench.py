@@ -44,6 +44,26 @@ def ns_per_day(sec_per_step: float, dt_fs: float) -> float:
     return 86400.0 / sec_per_step * dt_fs * 1e-6
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest x over all ranks (the slowest replica sets the whole job's
+    time).  torch.distributed must be initialised when world > 1; the tensor
+    lives on ``device`` (a CUDA device for NCCL, the CPU for gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ns_per_day(ms_per_step_max: float, world: int, dt_fs: float) -> float:
+    """Whole-job throughput of ``world`` independent replicas, each of which
+    advances its own system by one step in at most ms_per_step_max."""
+    return world * ns_per_day(ms_per_step_max * 1e-3, dt_fs)
+
+
 def workload_config(prm, precision):
     return {
         "workload": "molten NaCl, 32768 ions, L=100.9 A, 128^3 mesh, alpha 0.30/A, r_cut 9 A, "
@@ -70,6 +90,7 @@ class ClockSampler:
         self.proc = None
         self.path = None
         self.handle = None
+        self.nvml_error = None
 
     def _nvml_handle(self):
         import pynvml
@@ -77,9 +98,14 @@ class ClockSampler:
         try:
             import torch
             uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
-            return pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+            return pynvml.nvmlDeviceGetHandleByUUID((uuid if uuid.startswith("GPU-") else "GPU-" + uuid).encode())
         except Exception:
-            return pynvml.nvmlDeviceGetHandleByIndex(int(self.gpu or 0))
+            pass
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        first = vis.split(",")[0].strip() if vis else ""
+        if first.startswith("GPU-"):
+            return pynvml.nvmlDeviceGetHandleByUUID(first.encode())
+        return pynvml.nvmlDeviceGetHandleByIndex(int(first) if first.isdigit() else int(self.gpu or 0))
 
     def _poll(self):
         import pynvml
@@ -103,8 +129,9 @@ class ClockSampler:
             while not self.samples and time.time() - t0 < 1.0:
                 time.sleep(0.001)
             self.samples.clear()            # keep only samples taken inside the region
-        except Exception:
+        except Exception as exc:
             self.handle = None
+            self.nvml_error = f"{type(exc).__name__}: {exc}"
             try:
                 fd, self.path = tempfile.mkstemp(suffix=".csv")
                 os.close(fd)
@@ -154,9 +181,9 @@ class ClockSampler:
                     reasons.add(nm)
         os.unlink(self.path)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "nvml_error": self.nvml_error}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "source": "nvidia-smi", "reasons": sorted(reasons)}
+                "source": "nvidia-smi", "nvml_error": self.nvml_error, "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------- roofline
@@ -176,6 +203,20 @@ def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int) -> tuple[f
     if stage == "gather":        # read phi once, 32 B per particle in, 3 x 24 B out
         return P * 8.0 + 104.0 * npart, 1
     return float("nan"), 1
+
+
+def recorded_traffic(kernel: str, workload: str, precision: str):
+    """DRAM bytes per launch from the committed ncu record, if it was taken on
+    the current kernel source (profiles/roofline_traffic.json)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)[f"{kernel}|{workload}|{precision}"]
+        with open(os.path.join(ROOT, "paper_2606_31379_b300", "csrc", "mesh.cuh"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        return float(rec["dram_bytes_per_launch"]) if sha == rec["mesh_cuh_sha256_16"] else None
+    except Exception:
+        return None
 
 
 def measured_peaks() -> dict:
@@ -325,13 +366,9 @@ def run_ours(args) -> int:
     barrier()
     tm = ctx.timing()
     iters = (ctx.stats()["total_iters"] - it0) / args.steps
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), world, device="cuda")
     ms_per_step = total_ms / args.steps
-    value = world * ns_per_day(ms_per_step * 1e-3, prm["dt"])
+    value = job_ns_per_day(ms_per_step, world, prm["dt"])
 
     # end to end through the C ABI with pinned host buffers: upload r, v;
     # one step; download r, v.
@@ -348,8 +385,8 @@ def run_ours(args) -> int:
         ctx.positions(out=pos_h)
         ctx.velocities(out=vel_h)
     torch.cuda.synchronize()
-    e2e_sec = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": world * ns_per_day(e2e_sec, prm["dt"]), "unit": "ns/day",
+    e2e_sec = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, device="cuda")
+    e2e = {"value": job_ns_per_day(1e3 * e2e_sec, world, prm["dt"]), "unit": "ns/day",
            "h2d_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes),
            "d2h_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes), "steps": e2e_steps}
     K_smooth = ctx.stats()["smooth_steps"]
@@ -378,9 +415,10 @@ def run_ours(args) -> int:
             it0 = cv.stats()["total_iters"]
             msv = time_context(cv, torch, stream, args.steps, flush)
             tv = cv.timing()
+            msv_step = max_over_ranks(sum(msv), world, device="cuda") / args.steps
             variants[name] = {
-                "value": world * ns_per_day(sum(msv) / args.steps * 1e-3, prm["dt"]),
-                "ms_per_step": sum(msv) / args.steps,
+                "value": job_ns_per_day(msv_step, world, prm["dt"]),
+                "ms_per_step": msv_step,
                 "mg_iters_per_step": (cv.stats()["total_iters"] - it0) / args.steps,
                 "stage_us": {k: 1e3 * v / args.steps for k, v in tv["ms"].items()},
                 "settings": {k: v for k, v in kw.items()},
@@ -406,7 +444,8 @@ def run_ours(args) -> int:
                      "k_diffuse4" if args.precision == "mixed" else "k_diffuse")
     roofline = {"bound": "hbm", "kernel": dom if dom != "smooth" else smooth_kernel,
                 "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": recorded_traffic(smooth_kernel if dom == "smooth" else dom, WORKLOAD, args.precision),
                 "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
                 "launch_us": launch_us}
     line = {

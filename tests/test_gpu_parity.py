@@ -280,3 +280,28 @@ def test_equilibrate_sets_kinetic_temperature(P, nacl512):
         ke = ctx.energy()["kinetic"]
         assert ke == pytest.approx(0.5 * (3 * 512 - 3) * 0.0019872043 * 1200.0, rel=1e-9)
         assert ctx.stats()["steps"] == 10
+
+
+@pytest.mark.parametrize("precision, xtol", [("fp64", 1e-6), ("mixed", 1e-2)])
+def test_time_reversibility(P, nacl512, precision, xtol):
+    """Velocity Verlet with positions-determined forces is time reversible
+    (Sec. 2: the field is fixed by the constraint at every step, so the
+    multiplier history only changes the solver's starting point).  Forward 40
+    steps, reverse the velocities, 40 more steps: the start comes back up to
+    solver tolerance and rounding, grown by the melt's chaotic divergence
+    (Lyapunov time >= 10 fs, so at most ~3e3 over 80 fs).  Bound: 1e-6 A in
+    FP64 (tol 1e-11), 1e-2 A in mixed mode (FP32 forces, ~1e-6 relative)."""
+    with _ctx(P, nacl512, precision=precision, tol=1e-11 if precision == "fp64" else 1e-7) as ctx:
+        ctx.equilibrate(50, 1200.0)
+        x0, v0 = ctx.positions(), ctx.velocities()
+        ctx.step(40)
+        x1, v1 = ctx.positions(), ctx.velocities()
+        assert np.abs(x1 - x0).max() > 0.05                   # the particles did move
+        ctx.set_state(x1, -v1)
+        ctx.step(40)
+        x2, v2 = ctx.positions(), ctx.velocities()
+    L = nacl512.box
+    d = x2 - x0
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < xtol
+    assert np.abs(v2 + v0).max() < xtol          # A/fs: an error built up over >= 1 fs
