@@ -91,32 +91,53 @@ class ClockSampler:
         self.path = None
         self.handle = None
         self.nvml_error = None
+        self.lib = None
 
     def _nvml_handle(self):
-        import pynvml
-        pynvml.nvmlInit()
+        """Open NVML through ctypes (read-only queries) and return the handle
+        of this process's CUDA device, matched by UUID."""
+        import ctypes
+
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.lib = lib
+        h = ctypes.c_void_p()
         try:
             import torch
             uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
-            return pynvml.nvmlDeviceGetHandleByUUID((uuid if uuid.startswith("GPU-") else "GPU-" + uuid).encode())
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0:
+                return h
         except Exception:
             pass
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         first = vis.split(",")[0].strip() if vis else ""
         if first.startswith("GPU-"):
-            return pynvml.nvmlDeviceGetHandleByUUID(first.encode())
-        return pynvml.nvmlDeviceGetHandleByIndex(int(first) if first.isdigit() else int(self.gpu or 0))
+            rc = lib.nvmlDeviceGetHandleByUUID(first.encode(), ctypes.byref(h))
+        else:
+            idx = int(first) if first.isdigit() else int(self.gpu or 0)
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"NVML device handle lookup failed ({rc})")
+        return h
 
     def _poll(self):
-        import pynvml
+        import ctypes
+
+        lib = self.lib
+        try:
+            get_reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            get_reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        sm, smax, reasons = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        NVML_CLOCK_SM = 1
         while not self._stop:
-            try:
-                sm = pynvml.nvmlDeviceGetClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
-                smax = pynvml.nvmlDeviceGetMaxClockInfo(self.handle, pynvml.NVML_CLOCK_SM)
-                reasons = pynvml.nvmlDeviceGetCurrentClocksEventReasons(self.handle)
-                self.samples.append((sm, smax, reasons))
-            except Exception:
-                pass
+            ok = (lib.nvmlDeviceGetClockInfo(self.handle, NVML_CLOCK_SM, ctypes.byref(sm)) == 0 and
+                  lib.nvmlDeviceGetMaxClockInfo(self.handle, NVML_CLOCK_SM, ctypes.byref(smax)) == 0 and
+                  get_reasons(self.handle, ctypes.byref(reasons)) == 0)
+            if ok:
+                self.samples.append((sm.value, smax.value, reasons.value))
             time.sleep(0.002)
 
     def __enter__(self):
@@ -370,20 +391,22 @@ def run_ours(args) -> int:
     ms_per_step = total_ms / args.steps
     value = job_ns_per_day(ms_per_step, world, prm["dt"])
 
-    # end to end through the C ABI with pinned host buffers: upload r, v;
-    # one step; download r, v.
+    # end to end through the C ABI with pinned host buffers, every step: the
+    # state (r, v) copied in from the host, one MD step, r and v copied back
+    # out, one host wait (p3maze_step_host).  Stage timing is off here, as in
+    # a production run.
+    ctx.set_timing(False)
     pos_h = torch.empty((system.n, 3), dtype=torch.float64, pin_memory=True).numpy()
     vel_h = torch.empty((system.n, 3), dtype=torch.float64, pin_memory=True).numpy()
     ctx.positions(out=pos_h)
     ctx.velocities(out=vel_h)
+    for _ in range(3):
+        ctx.step_host(pos_h, vel_h, 1, pos_h, vel_h)
     torch.cuda.synchronize()
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, args.steps)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.set_state(pos_h, vel_h)
-        ctx.step(1)
-        ctx.positions(out=pos_h)
-        ctx.velocities(out=vel_h)
+        ctx.step_host(pos_h, vel_h, 1, pos_h, vel_h)
     torch.cuda.synchronize()
     e2e_sec = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, device="cuda")
     e2e = {"value": job_ns_per_day(1e3 * e2e_sec, world, prm["dt"]), "unit": "ns/day",

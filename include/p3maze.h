@@ -219,6 +219,19 @@ int p3maze_step_async(p3maze_ctx *ctx, int32_t nsteps);
 /* Wait for queued steps and report a recorded solver failure.                  */
 int p3maze_wait(p3maze_ctx *ctx);
 
+/* One host round trip in one call, for drivers that keep the state on the
+ * host: copy pos_in/vel_in (host [n][3], A and A/fs; either may be NULL to
+ * keep the device copy) in as the continuing state (as p3maze_set_state:
+ * forces and field histories kept, positions wrapped), advance nsteps steps,
+ * copy positions/velocities out to pos_out/vel_out (either may be NULL), and
+ * wait once.  Pinned host buffers make the copies asynchronous; pageable ones
+ * work too.  pos_in may equal pos_out (and vel_in vel_out).  Inputs are
+ * checked for NaN/Inf on the device: a non-finite input returns INVALID after
+ * the call, with the steps applied to garbage (re-initialise with
+ * p3maze_set_state + p3maze_reinit).  Solver failures as p3maze_step.          */
+int p3maze_step_host(p3maze_ctx *ctx, const double *pos_in, const double *vel_in, int32_t nsteps,
+                     double *pos_out, double *vel_out);
+
 /* Full constraint solve from phi = 0 at the current positions and new forces:
  * the same initialisation as p3maze_init (after an external state change).   */
 int p3maze_reinit(p3maze_ctx *ctx);

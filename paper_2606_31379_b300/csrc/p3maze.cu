@@ -627,6 +627,8 @@ int read_solver_state(p3maze_ctx* ctx) {
         ctx->launches[P3MAZE_ST_SOLVE] += (graph_iters - ctx->graph_iters_seen) * ctx->body_launches;
         ctx->graph_iters_seen = graph_iters;
     }
+    if (m.status == P3MAZE_ERR_INVALID)
+        return fail(ctx, P3MAZE_ERR_INVALID, "non-finite position or velocity copied in from the host");
     if (m.status == P3MAZE_ERR_NONFINITE) return fail(ctx, P3MAZE_ERR_NONFINITE, "non-finite constraint residual");
     if (m.status == P3MAZE_ERR_NOT_CONVERGED) {
         char buf[160];
@@ -1194,6 +1196,32 @@ int p3maze_wait(p3maze_ctx* ctx) {
 
 int p3maze_step(p3maze_ctx* ctx, int32_t nsteps) {
     int rc = p3maze_step_async(ctx, nsteps);
+    if (rc) return rc;
+    return read_solver_state(ctx);
+}
+
+int p3maze_step_host(p3maze_ctx* ctx, const double* pos_in, const double* vel_in, int32_t nsteps, double* pos_out,
+                     double* vel_out) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, P3MAZE_ERR_INVALID, "nsteps must be >= 0");
+    cudaStream_t s = ctx->stream;
+    const size_t bytes = 24 * (size_t)ctx->np;
+    int rc = enter(ctx);
+    if (rc) return rc;
+    if (pos_in) CK(cudaMemcpyAsync(ctx->r, pos_in, bytes, cudaMemcpyHostToDevice, s));
+    if (vel_in) CK(cudaMemcpyAsync(ctx->v, vel_in, bytes, cudaMemcpyHostToDevice, s));
+    if (pos_in || vel_in) {
+        k_wrap_check<<<nblk(3 * (int64_t)ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->L,
+                                                                        &ctx->dmg->status, P3MAZE_ERR_INVALID);
+        CKL();
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        rc = step_once(ctx);
+        if (rc) return rc;
+    }
+    if (pos_out) CK(cudaMemcpyAsync(pos_out, ctx->r, bytes, cudaMemcpyDeviceToHost, s));
+    if (vel_out) CK(cudaMemcpyAsync(vel_out, ctx->v, bytes, cudaMemcpyDeviceToHost, s));
+    rc = leave(ctx);
     if (rc) return rc;
     return read_solver_state(ctx);
 }

@@ -53,6 +53,18 @@ static __global__ void k_wrap(int n, double* __restrict__ r, double L) {
     r[i] = wrap_pos(r[i], L);
 }
 
+// Wrap positions uploaded from the host and flag a non-finite position or
+// velocity: *status (the solver's first-failure word) becomes `code` unless
+// an earlier failure is recorded.
+static __global__ void k_wrap_check(int n, double* __restrict__ r, const double* __restrict__ v, double L,
+                                    int* __restrict__ status, int code) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const double x = r[i];
+    if (!isfinite(x) || !isfinite(v[i])) atomicCAS(status, 0, code);
+    r[i] = wrap_pos(x, L);
+}
+
 // ---------------------------------------------------------------- cell list
 // Cell of each particle, c = min(floor(r * nc/L), nc-1) per axis, x fastest,
 // and per-cell counts.

@@ -80,6 +80,7 @@ _sig = {
     "p3maze_step": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_step_async": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_wait": (C.c_int, [_ctx]),
+    "p3maze_step_host": (C.c_int, [_ctx, _dp, _dp, C.c_int32, _dp, _dp]),
     "p3maze_reinit": (C.c_int, [_ctx]),
     "p3maze_equilibrate": (C.c_int, [_ctx, C.c_int32, C.c_double]),
     "p3maze_destroy": (None, [_ctx]),
@@ -261,6 +262,24 @@ class Context:
     def step_async(self, n: int = 1):
         """Queue n steps without waiting (graph steps); see wait()."""
         self._check(lib.p3maze_step_async(self._h, int(n)))
+
+    def step_host(self, pos_in=None, vel_in=None, n: int = 1, pos_out=None, vel_out=None):
+        """Copy pos_in/vel_in in (None keeps the device state), advance n
+        steps, copy positions/velocities out into pos_out/vel_out (float64
+        C-contiguous [n][3] arrays, filled in place), one host wait."""
+        def arg_in(a):
+            return None if a is None else _f64(a, (self.n, 3))
+
+        def arg_out(a):
+            if a is None:
+                return None
+            if a.dtype != np.float64 or a.shape != (self.n, 3) or not a.flags.c_contiguous:
+                raise ValueError("output arrays must be float64, C-contiguous, shape (n, 3)")
+            return a
+
+        pi, vi, po, vo = arg_in(pos_in), arg_in(vel_in), arg_out(pos_out), arg_out(vel_out)
+        ptr = lambda a: None if a is None else _ptr(a)
+        self._check(lib.p3maze_step_host(self._h, ptr(pi), ptr(vi), int(n), ptr(po), ptr(vo)))
 
     def wait(self):
         """Wait for queued steps; raises on a recorded solver failure."""

@@ -305,3 +305,31 @@ def test_time_reversibility(P, nacl512, precision, xtol):
     d -= L * np.round(d / L)
     assert np.abs(d).max() < xtol
     assert np.abs(v2 + v0).max() < xtol          # A/fs: an error built up over >= 1 fs
+
+
+def test_step_host_matches_separate_calls(P, nacl512):
+    """p3maze_step_host (copy in, steps, copy out, one wait) gives the same
+    state as set_state + step + get on a twin context."""
+    with _ctx(P, nacl512, precision="fp64", tol=1e-10) as a, _ctx(P, nacl512, precision="fp64", tol=1e-10) as b:
+        a.step(3)
+        b.step(3)
+        x, v = a.positions(), a.velocities()
+        x = x + 0.01                          # a host-side change of the state
+        a.set_state(x, v)
+        a.step(2)
+        xo, vo = np.empty_like(x), np.empty_like(v)
+        b.step_host(x, v, 2, xo, vo)
+        np.testing.assert_allclose(xo, a.positions(), rtol=0, atol=1e-9)
+        np.testing.assert_allclose(vo, a.velocities(), rtol=0, atol=1e-9)
+        # NULL inputs keep the device state; NULL outputs skip the copies
+        b.step_host(None, None, 1, None, None)
+        a.step(1)
+        np.testing.assert_allclose(b.positions(), a.positions(), rtol=0, atol=1e-9)
+
+
+def test_step_host_flags_nonfinite_input(P, nacl512):
+    with _ctx(P, nacl512, precision="mixed", tol=1e-6) as ctx:
+        x, v = ctx.positions(), ctx.velocities()
+        v[7, 1] = np.nan
+        with pytest.raises(P.P3MaZeError, match="non-finite position or velocity"):
+            ctx.step_host(x, v, 1, None, None)
