@@ -93,4 +93,23 @@ __device__ __forceinline__ double block_max(double v) {
     return v;
 }
 
+// Block-wide maximum of a float (all threads get the result).  Any block shape.
+__device__ __forceinline__ float block_max_f(float v) {
+    __shared__ float shf[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int tid = linear_tid(), lane = tid & 31, wid = tid >> 5;
+    __syncthreads();
+    if (lane == 0) shf[wid] = v;
+    __syncthreads();
+    const int nw = (block_threads() + 31) >> 5;
+    v = (tid < nw) ? shf[tid] : 0.0f;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (tid == 0) shf[0] = v;
+    __syncthreads();
+    v = shf[0];
+    __syncthreads();
+    return v;
+}
+
 }  // namespace p3

@@ -159,6 +159,66 @@ k_diffuse4(int n, int zc, const float* __restrict__ in, float* __restrict__ out,
     }
 }
 
+// k_diffuse4 with the plane count ZC fixed at compile time: every load of
+// the thread's ZC planes (its column from z0-1 to z0+ZC, the y-1 and y+1 rows
+// of its planes, the row-end x neighbours) is issued before the first
+// output is formed, so one L2 round trip covers the whole column instead of
+// one per plane.  Same arithmetic, in the same order, as k_diffuse4.
+template <int ZC, bool SUM>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_diffuse4z(int n, const float* __restrict__ in, float* __restrict__ out, float c, double* __restrict__ partial) {
+    const int lane = threadIdx.x;
+    const int q = blockIdx.x * P3_BX + lane;
+    const int x = 4 * q;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int z0 = blockIdx.z * ZC;
+    const bool live = x < n && y < n;
+    const int nq = n >> 2;
+    const int yy = live ? y : 0, xx = live ? x : 0;
+    const int xl = xx == 0 ? n - 1 : xx - 1;
+    const int xr = xx + 4 == n ? 0 : xx + 4;
+    const int ym = yy == 0 ? n - 1 : yy - 1, yp = yy == n - 1 ? 0 : yy + 1;
+    const int plane = n * n;
+    const bool lend = lane == 0 || q - 1 >= nq, rend = lane == P3_BX - 1 || q + 1 >= nq;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    auto wz = [&](int z) { return z < 0 ? z + n : (z >= n ? z - n : z); };
+    float4 col[ZC + 2], am[ZC], bp[ZC];
+    float lft[ZC], rgt[ZC];
+#pragma unroll
+    for (int k = 0; k < ZC + 2; ++k) col[k] = in4[(wz(z0 - 1 + k) * plane + yy * n + xx) >> 2];
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const int z = wz(z0 + k);
+        am[k] = in4[(z * plane + ym * n + xx) >> 2];
+        bp[k] = in4[(z * plane + yp * n + xx) >> 2];
+        lft[k] = lend ? in[z * plane + yy * n + xl] : 0.0f;
+        rgt[k] = rend ? in[z * plane + yy * n + xr] : 0.0f;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const float4 vm = col[k], vc = col[k + 1], vp = col[k + 2], a = am[k], b = bp[k];
+        float left = __shfl_up_sync(0xffffffffu, vc.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, vc.x, 1);
+        if (lend) left = lft[k];
+        if (rend) right = rgt[k];
+        float4 o;
+        o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
+        o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
+        o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
+        o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
+        if (live && z0 + k < n) {
+            reinterpret_cast<float4*>(out)[((z0 + k) * plane + yy * n + x) >> 2] = o;
+            if (SUM) acc += ((double)o.x + (double)o.y) + ((double)o.z + (double)o.w);
+        }
+    }
+    if (SUM) {
+        acc = block_sum(acc);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
 // S explicit diffusion steps fused in one launch (2.5D temporal blocking).
 // A block owns an output tile of TX x TY columns and zc planes; its
 // (TX + 2S) x (TY + 2S) threads each hold one column of the haloed tile and
@@ -357,6 +417,146 @@ __global__ void k_update(int64_t m, const double* __restrict__ phik, double* __r
     if (phi32 != nullptr) phi32[i] = (float)(p - phik[0]);
 }
 
+// ---------------------------------------------------------------- fixed point
+// Mixed precision carries the constraint algebra of Eqs. 16-17 and 20 in
+// 64-bit fixed point, value x 2^40 in potential units (e/A; resolution
+// 9.1e-13, range +-8.4e6): the potential phi, Psi = M phi, the correction
+// z = (4pi/h) y, the predicted residual s = M phi_p + (4pi/h)(q^s - mean)
+// = (4pi/h) sigma_p and the residual r = s - M z.  Sums, differences and the
+// integer 7-point stencil are exact in this form, so Psi^{k+1} = M phi^{k+1}
+// holds bit for bit at every step and is carried forward instead of
+// recomputed; FP32 values enter once each (the smoothed charge, the V-cycle
+// corrections) and are accounted for exactly in both phi and Psi.  The
+// constant mode of phi (a gauge freedom) may wrap around in two's
+// complement: every use takes differences of phi values, which stay exact.
+typedef long long fix_t;
+constexpr float kFixOne = 1099511627776.0f;        // 2^40
+constexpr float kFixInv = 1.0f / 1099511627776.0f;  // 2^-40, exact
+
+// int64 -> float as hi 2^32 + lo with 32-bit conversions (round-off of one
+// or two float ulps; used for V-cycle inputs and the max-norm only).
+__device__ __forceinline__ float fix_to_float(fix_t v) {
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 4294967296.0f, (float)lo) * kFixInv;
+}
+
+// float -> nearest-or-truncated fixed point with 32-bit conversions.  Small
+// values convert directly; large ones (|f| >= 2^31, so f is a multiple of
+// 2^8) split exactly into 2^32 hi + lo.  Which integer is chosen does not
+// matter for exactness: the same integer enters phi and Psi.  Finite inputs
+// of magnitude below 2^23 only (the callers flag non-finite values).
+__device__ __forceinline__ fix_t float_to_fix(float e) {
+    const float f = e * kFixOne;
+    if (fabsf(f) < 2147483648.0f) return (fix_t)__float2int_rn(f);
+    const float hi = truncf(f * (1.0f / 4294967296.0f));
+    const float lo = fmaf(-hi, 4294967296.0f, f);  // exact: multiple of 2^8, |lo| < 2^32
+    return (fix_t)__float2int_rz(hi) * 4294967296ll + 2ll * (fix_t)__float2int_rn(0.5f * lo);
+}
+
+// (4pi/h)(q^s - mean) in fixed point, rounded the same way wherever it is
+// formed (no contraction into an FMA).
+__device__ __forceinline__ fix_t charge_term(float qs, float mean, float u) {
+    return float_to_fix(__fmul_rn(__fsub_rn(qs, mean), u));
+}
+
+// Prediction (Eq. 17) in fixed point: s = 2 Psi^k - Psi^{k-1} + (4pi/h)(q^s -
+// mean) and the correction guess z0 from the history (order 0-3, as
+// k_predict).  A non-finite q^s sets status to NONFINITE.
+static __global__ void __launch_bounds__(P3_THREADS)
+k_predict_fix(int64_t m, const fix_t* __restrict__ Psik, const fix_t* __restrict__ Psikm1,
+              const float* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, float u,
+              const fix_t* __restrict__ z1, const fix_t* __restrict__ z2, const fix_t* __restrict__ z3, int order,
+              fix_t* __restrict__ s, fix_t* __restrict__ z0, int* __restrict__ status) {
+    __shared__ float mean_s;
+    if (threadIdx.x == 0) mean_s = (float)(qsum[0] * inv_pts);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float q = qs[i];
+    if (!isfinite(q)) atomicCAS(status, 0, -5);
+    s[i] = 2 * Psik[i] - Psikm1[i] + charge_term(q, mean_s, u);
+    fix_t g = 0;
+    if (order == 1) g = z1[i];
+    else if (order == 2) g = 2 * z1[i] - z2[i];
+    else if (order == 3) g = 3 * (z1[i] - z2[i]) + z3[i];
+    z0[i] = g;
+}
+
+// Exact fine-level residual r = s - M z: kept in fixed point (rfin, for the
+// Psi update) and as float (input of the correction V-cycle); block maxima
+// of |r| (potential units) to bmax, as k_resid_fine.
+static __global__ void __launch_bounds__(P3_BX * P3_BY)
+k_resid_fix(int n, const fix_t* __restrict__ z, const fix_t* __restrict__ s, float* __restrict__ r,
+            fix_t* __restrict__ rfin, double* __restrict__ bmax) {
+    const int x = blockIdx.x * P3_BX + threadIdx.x;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    float a = 0.0f;
+    if (x < n && y < n) {
+        for (int zz = blockIdx.z; zz < n; zz += gridDim.z) {
+            const int i = (zz * n + y) * n + x;
+            const fix_t res = s[i] - (nb6(z, x, y, zz, n) - 6 * z[i]);
+            rfin[i] = res;
+            const float v = fix_to_float(res);
+            r[i] = v;
+            a = fmaxf(a, fabsf(v));
+        }
+    }
+    const float am = block_max_f(a);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        bmax[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)am;
+}
+
+// z += e, the V-cycle's float correction converted once to fixed point.  A
+// non-finite e sets status to NONFINITE.
+static __global__ void k_add_correction_fix(int64_t m, fix_t* __restrict__ z, const float* __restrict__ e,
+                                     int* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float v = e[i];
+    if (!(fabsf(v) < 8.0e6f)) {
+        atomicCAS(status, 0, -5);
+        return;
+    }
+    z[i] += float_to_fix(v);
+}
+
+// Field update in fixed point, written over the k-1 slots:
+//   phi^{k+1} = 2 phi^k - phi^{k-1} - z*
+//   Psi^{k+1} = M phi^{k+1} = r_final - (4pi/h)(q^s - mean)
+// and the FP32 copy of phi^{k+1} - phi^k[0] for the interpolation.
+static __global__ void __launch_bounds__(P3_THREADS)
+k_update_fix(int64_t m, const fix_t* __restrict__ phik, fix_t* __restrict__ phikm1, fix_t* __restrict__ Psikm1,
+             const fix_t* __restrict__ z, const fix_t* __restrict__ rfin, const float* __restrict__ qs,
+             const double* __restrict__ qsum, double inv_pts, float u, float* __restrict__ phi32) {
+    __shared__ float mean_s;
+    __shared__ fix_t ref_s;
+    if (threadIdx.x == 0) {
+        mean_s = (float)(qsum[0] * inv_pts);
+        ref_s = phik[0];
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const fix_t p = 2 * phik[i] - phikm1[i] - z[i];
+    phikm1[i] = p;
+    Psikm1[i] = rfin[i] - charge_term(qs[i], mean_s, u);
+    phi32[i] = fix_to_float(p - ref_s);
+}
+
+// Partial sums of (phi_i - phi_0) b_i with phi in fixed point (energy
+// 1/2 phi^T q; the reference value removes the gauge constant).
+template <typename T>
+__global__ void k_dot_partial_fix(int64_t m, const fix_t* __restrict__ a, const T* __restrict__ b,
+                                  double* __restrict__ partial) {
+    const fix_t ref = a[0];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)(a[i] - ref) * (double)b[i];
+    acc = block_sum(acc) * (1.0 / 1099511627776.0);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
 // Convergence control of the correction solve (Eq. 20), one block: reduces
 // the block maxima of the residual just computed to max|r| and decides whether another V-cycle runs (res > tol, finite, fewer than itmax
 // cycles so far).  Records the outcome in MGState; a failure code is sticky.
@@ -385,6 +585,7 @@ k_mg_check(const double* __restrict__ bmax, int nb, double tol, int itmax, MGSta
         if (st->it < itmax) cont = 1;
         else if (st->status == 0) st->status = -4;
     }
+    if (st->status == -5 || st->status == -1) cont = 0;  // non-finite data: no further V-cycles
     if (cont) {
         st->it += 1;
     } else {

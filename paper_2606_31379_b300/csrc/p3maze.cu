@@ -48,6 +48,10 @@ struct StepGraph {
 };
 
 inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
+
+// In mixed precision the 8-byte constraint arrays (phi, Psi, z history, s,
+// final residual) hold 64-bit fixed-point values (x 2^40, potential units).
+inline fix_t* fx(double* p) { return reinterpret_cast<fix_t*>(p); }
 inline dim3 g3(int n) { return dim3((n + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
 inline dim3 g3h(int n) { return dim3((n / 2 + P3_BX - 1) / P3_BX, (n + P3_BY - 1) / P3_BY, n); }
 // z-marching stencils: ZC planes per thread.
@@ -76,6 +80,7 @@ struct p3maze_ctx {
     int zc = 8;                          // z planes per thread in the diffusion step (tunable)
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
+    double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
     int64_t P = 0;
     double L = 0, h = 0, inv_h = 0, alpha = 0, sigma = 0, rc = 0, c = 0, tol = 0, dt = 0, ke = 0;
     double inv_cell = 0, lcell = 0, v_self = 0;
@@ -424,9 +429,14 @@ template <typename T>
 void launch_resid_check(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
     cudaStream_t s = ctx->stream;
     const dim3 gr = resid_grid(ctx->N);
-    k_resid_fine<T><<<gr, kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin, ctx->bmax);
+    if (ctx->prec == P3MAZE_MIXED)
+        k_resid_fix<<<gr, kB3, 0, s>>>(ctx->N, fx(ctx->yh[0]), fx(ctx->sig), (float*)ctx->lev[0].b, fx(ctx->rfin),
+                                       ctx->bmax);
+    else
+        k_resid_fine<T><<<gr, kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin, ctx->bmax);
     // P3M: max|M phi + (4pi/h) q^s| = (4pi/h) max|M y - sigma_p| for phi = phi_p - (4pi/h) y
-    k_mg_check<<<1, 1024, 0, s>>>(ctx->bmax, (int)(gr.x * gr.y * gr.z), ctx->tol / ctx->res_scale, ctx->itmax,
+    k_mg_check<<<1, 1024, 0, s>>>(ctx->bmax, (int)(gr.x * gr.y * gr.z), ctx->tol * ctx->res_unit / ctx->res_scale,
+                                  ctx->itmax,
                                   ctx->dmg, h, use_handle);
     count(ctx, P3MAZE_ST_SOLVE, 2);
 }
@@ -435,7 +445,13 @@ template <typename T>
 int launch_iteration(p3maze_ctx* ctx) {
     int rc = vcycle<T>(ctx, 0);
     if (rc) return rc;
-    k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0], (const T*)ctx->lev[0].e);
+    if (ctx->prec == P3MAZE_MIXED)
+        k_add_correction_fix<<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, fx(ctx->yh[0]),
+                                                                           (const float*)ctx->lev[0].e,
+                                                                           &ctx->dmg->status);
+    else
+        k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0],
+                                                                          (const T*)ctx->lev[0].e);
     count(ctx, P3MAZE_ST_SOLVE);
     return P3MAZE_OK;
 }
@@ -509,9 +525,16 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     cudaStream_t s = ctx->stream;
     const int ik = ctx->icur, ikm1 = 1 - ctx->icur;
     stage_begin(ctx, P3MAZE_ST_PREDICT);
-    k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->psi[ik], ctx->psi[ikm1], (const T*)ctx->qs,
-                                                     ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, ctx->yh[1],
-                                                     ctx->yh[2], ctx->yh[3], pred_order, ctx->sig, ctx->yh[0]);
+    if (ctx->prec == P3MAZE_MIXED)
+        k_predict_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, fx(ctx->psi[ik]), fx(ctx->psi[ikm1]),
+                                                          (const float*)ctx->qs, ctx->dscal + S_QSUM,
+                                                          1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
+                                                          fx(ctx->yh[1]), fx(ctx->yh[2]), fx(ctx->yh[3]), pred_order,
+                                                          fx(ctx->sig), fx(ctx->yh[0]), &ctx->dmg->status);
+    else
+        k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->psi[ik], ctx->psi[ikm1], (const T*)ctx->qs,
+                                                         ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, ctx->yh[1],
+                                                         ctx->yh[2], ctx->yh[3], pred_order, ctx->sig, ctx->yh[0]);
     CKL();
     count(ctx, P3MAZE_ST_PREDICT, 1);
     stage_end(ctx, P3MAZE_ST_PREDICT);
@@ -520,9 +543,17 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     if (rc) return rc;
     stage_end(ctx, P3MAZE_ST_SOLVE);
     stage_begin(ctx, P3MAZE_ST_UPDATE);
-    k_update<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1], ctx->yh[0],
-                                                    ctx->rfin, (const T*)ctx->qs, ctx->dscal + S_QSUM,
-                                                    1.0 / (double)ctx->P, 4.0 * kPi / ctx->h, ctx->phi32);
+    if (ctx->prec == P3MAZE_MIXED)
+        k_update_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, fx(ctx->phi[ik]), fx(ctx->phi[ikm1]),
+                                                         fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
+                                                         (const float*)ctx->qs, ctx->dscal + S_QSUM,
+                                                         1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
+                                                         ctx->phi32);
+    else
+        k_update<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1],
+                                                        ctx->yh[0], ctx->rfin, (const T*)ctx->qs,
+                                                        ctx->dscal + S_QSUM, 1.0 / (double)ctx->P,
+                                                        4.0 * kPi / ctx->h, ctx->phi32);
     count(ctx, P3MAZE_ST_UPDATE);
     stage_end(ctx, P3MAZE_ST_UPDATE);
     CKL();
@@ -619,7 +650,7 @@ int read_solver_state(p3maze_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     const MGState& m = *ctx->hmg;
     ctx->st.last_iters = m.last_iters;
-    ctx->st.last_residual = m.last_res * ctx->res_scale;
+    ctx->st.last_residual = m.last_res * ctx->res_scale / ctx->res_unit;
     ctx->st.total_iters = m.total_iters;
     // V-cycles run inside graphs: add their body launches to the tally
     const int64_t graph_iters = m.total_iters - ctx->eager_iters;
@@ -633,7 +664,7 @@ int read_solver_state(p3maze_ctx* ctx) {
     if (m.status == P3MAZE_ERR_NOT_CONVERGED) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "multigrid did not reach tol %.3g in %d V-cycles (residual %.3g)", ctx->tol,
-                      ctx->itmax, m.last_res * ctx->res_scale);
+                      ctx->itmax, m.last_res * ctx->res_scale / ctx->res_unit);
         return fail(ctx, P3MAZE_ERR_NOT_CONVERGED, buf);
     }
     return P3MAZE_OK;
@@ -1130,6 +1161,7 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->zc = 8;
     ctx->fuse = 1;
     ctx->res_scale = p->method == P3MAZE_METHOD_P3M ? 4.0 * kPi / h : 1.0;
+    ctx->res_unit = p->precision == P3MAZE_MIXED ? 4.0 * kPi / h : 1.0;
     // P3M has no multiplier: every solve starts from the Verlet-predicted field
     ctx->pred = p->method == P3MAZE_METHOD_P3M ? 0 : (p->predictor == 0 ? 3 : p->predictor);
     ctx->prec = p->precision;
@@ -1278,7 +1310,8 @@ int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
     k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->evs, ctx->partial);
     k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_EVDW);
     if (ctx->prec == P3MAZE_MIXED)
-        k_dot_partial<float><<<nb, P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ctx->icur], (const float*)ctx->q, ctx->partial);
+        k_dot_partial_fix<float><<<nb, P3_THREADS, 0, s>>>(ctx->P, fx(ctx->phi[ctx->icur]), (const float*)ctx->q,
+                                                           ctx->partial);
     else
         k_dot_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ctx->icur], (const double*)ctx->q, ctx->partial);
     k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_VLR);
@@ -1397,7 +1430,21 @@ int p3maze_get_mesh(p3maze_ctx* ctx, int32_t which, double* out) {
     if (which == P3MAZE_MESH_Y && ctx->st.steps == 0)
         return fail(ctx, P3MAZE_ERR_INVALID, "no correction has been solved yet (take a step first)");
     if (!src) return fail(ctx, P3MAZE_ERR_INVALID, "unknown mesh array");
-    return copy_out(ctx, src, out, 8 * (size_t)P);
+    if (!mixed) return copy_out(ctx, src, out, 8 * (size_t)P);
+    // fixed point (x 2^40, potential units): phi relative to its first node
+    // value (the gauge constant is arbitrary), y = z h/4pi, sigma_p = s h/4pi
+    std::vector<fix_t> tmp(P);
+    int rc = copy_out(ctx, src, tmp.data(), 8 * (size_t)P);
+    if (rc) return rc;
+    const double unit = 1.0 / 1099511627776.0;
+    if (which == P3MAZE_MESH_PHI) {
+        const fix_t ref = tmp[0];
+        for (int64_t i = 0; i < P; ++i) out[i] = (double)(fix_t)(tmp[i] - ref) * unit;
+    } else {
+        const double to_charge = unit / ctx->res_unit;
+        for (int64_t i = 0; i < P; ++i) out[i] = (double)tmp[i] * to_charge;
+    }
+    return P3MAZE_OK;
 }
 
 int p3maze_get_cells(p3maze_ctx* ctx, int32_t* cell_of, int32_t* cell_start, int32_t* order) {
