@@ -375,8 +375,8 @@ def run_ours(args) -> int:
     tuning = None if args.no_tune else ctx.autotune(8)
     torch.cuda.synchronize()
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
-    ctx.set_timing(True)
     it0 = ctx.stats()["total_iters"]
+    launches0 = ctx.timing()["total_launches"]
     barrier()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")
@@ -385,8 +385,16 @@ def run_ours(args) -> int:
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
-    tm = ctx.timing()
     iters = (ctx.stats()["total_iters"] - it0) / args.steps
+    launches = ctx.timing()["total_launches"] - launches0
+    # stage breakdown: the same number of steps again with CUDA events around
+    # each stage (recorded inside the step graph; not part of the headline)
+    ctx.set_timing(True)
+    ctx.step(2)
+    ctx.set_timing(True)                    # reset the stage tallies
+    ms_staged = time_context(ctx, torch, stream, args.steps, flush)
+    tm = ctx.timing()
+    ctx.set_timing(False)
     total_ms = max_over_ranks(sum(ms), world, device="cuda")
     ms_per_step = total_ms / args.steps
     value = job_ns_per_day(ms_per_step, world, prm["dt"])
@@ -434,15 +442,19 @@ def run_ours(args) -> int:
                                        tol=prm["tol"], dt=prm["dt"], stream=stream.cuda_stream, **kw)
             cv.step(args.warmup)
             tv_tune = None if (args.no_tune or name != "fp64") else cv.autotune(8)
-            cv.set_timing(True)
             it0 = cv.stats()["total_iters"]
             msv = time_context(cv, torch, stream, args.steps, flush)
+            itv = (cv.stats()["total_iters"] - it0) / args.steps
+            cv.set_timing(True)
+            cv.step(2)
+            cv.set_timing(True)
+            time_context(cv, torch, stream, args.steps, flush)
             tv = cv.timing()
             msv_step = max_over_ranks(sum(msv), world, device="cuda") / args.steps
             variants[name] = {
                 "value": job_ns_per_day(msv_step, world, prm["dt"]),
                 "ms_per_step": msv_step,
-                "mg_iters_per_step": (cv.stats()["total_iters"] - it0) / args.steps,
+                "mg_iters_per_step": itv,
                 "stage_us": {k: 1e3 * v / args.steps for k, v in tv["ms"].items()},
                 "settings": {k: v for k, v in kw.items()},
                 "tuning": tv_tune,
@@ -480,8 +492,9 @@ def run_ours(args) -> int:
                              "(velocity rescaling), untimed"),
         "lr_step_us": sum(stage_us[k] for k in lr_stages),
         "stage_us": stage_us, "mg_iters_per_step": iters,
-        "gpu_launches": int(tm["total_launches"]),
-        "gpu_launches_per_step": tm["total_launches"] / args.steps,
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps,
+        "ms_per_step_with_stage_events": sum(ms_staged) / args.steps,
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
     }
     if not args.no_serve:

@@ -114,7 +114,9 @@ typedef struct {
     const int32_t *types;   /* host [n] species index < sr->n_types (may be NULL if no sr) */
     double alpha;           /* Ewald splitting, 1/A; sigma = 1/(sqrt(2) alpha) (Eq. 5)     */
     double r_cut;           /* real-space cutoff, A; need r_cut <= L                        */
-    int32_t mesh;           /* N points per axis, N = m 2^l with 2 <= m <= 8 and N >= 4     */
+    int32_t mesh;           /* N points per axis, N >= 4, N = m 2^l with m <= 64: the
+                               multigrid levels N, N/2, ... are halved while even and
+                               above 16, and the deepest must be <= 64                    */
     int32_t order;          /* assignment order; 4 (cubic B-spline) is the only one         */
     double tol;             /* max-norm tolerance of M y - sigma_p, e per mesh point (> 0)  */
     double dt;              /* time step, fs                                                */
@@ -128,6 +130,8 @@ typedef struct {
     const p3maze_sr_table *sr;      /* may be NULL: Coulomb only                           */
     const p3maze_topology *topology;/* may be NULL                                         */
     int32_t method;         /* P3MAZE_METHOD_MAZE (0) or P3MAZE_METHOD_P3M                  */
+    int32_t coarse_max;     /* the first level with n <= coarse_max is solved exactly
+                               (separable Hartley transforms); 0 -> 64 (mixed), 16 (FP64) */
 } p3maze_params;
 
 typedef struct {
@@ -149,8 +153,8 @@ typedef struct {
     int32_t init_iters;         /* V-cycles of the initial full solve                      */
     int32_t smooth_steps;       /* K                                                       */
     double smooth_coeff;        /* c                                                       */
-    int32_t mg_levels;          /* multigrid levels including the coarsest                 */
-    int32_t coarse_n;           /* points per axis of the coarsest level                  */
+    int32_t mg_levels;          /* multigrid levels in use, the last solved exactly        */
+    int32_t coarse_n;           /* points per axis of that coarse level                    */
     int32_t cells_per_axis;     /* cell-list grid                                          */
     double sigma;               /* Gaussian width, A                                       */
     int64_t device_bytes;       /* device memory the context allocated                     */
@@ -182,6 +186,8 @@ typedef struct {
     int32_t post_sweeps;
     int32_t diffusion_zc;       /* z planes per thread (block) of the diffusion kernel  */
     int32_t diffusion_fuse;     /* diffusion steps per launch: 1, or 4 (temporal blocking) */
+    int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
+    int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
     double ms_per_step;         /* measured with the chosen setting                    */
     double initial_ms_per_step; /* measured with the setting in use before tuning      */
     int32_t trials;             /* settings timed                                      */
@@ -317,9 +323,14 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
 
 /* Autotuner: time real MD steps under candidate settings and keep the
  * fastest -- multiplier predictor 1..3 (P3MaZe only), smoothing sweeps
- * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)}, and the diffusion
- * kernel's z planes per thread in {4, 8, 16, 32} with, in mixed mode, 1 or 4
- * diffusion steps fused per launch.  None of them changes the
+ * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)}, the diffusion kernel's
+ * z planes per thread (FP32, one step per launch, N % 4 == 0: {1, 2, 4, 8};
+ * otherwise per block: {4, 8, 16, 32}) with, in mixed mode, 1 or 4
+ * diffusion steps fused per launch, and where the short-range pair kernel
+ * is forked onto its low-priority stream (after smoothing, or right after
+ * the cell list so that it also overlaps assignment and smoothing), and the
+ * size of the exactly solved coarse level (coarse_max 16, 32 or 64).  None
+ * of them changes the
  * converged field beyond tol (they change iteration counts and speed only).
  * Every trial runs 2 warm-up steps (graph capture) and steps_per_trial timed
  * steps (CUDA events); the system advances by all of them (out->steps).

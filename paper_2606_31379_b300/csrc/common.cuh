@@ -50,6 +50,47 @@ __device__ __forceinline__ int bspline_axis(double x, double inv_h, int n, doubl
     return b < 0 ? b + n : (b >= n ? b - n : b);
 }
 
+// FP32 weights of the cubic B-spline at fraction t in [0, 1) (the same
+// polynomials as bspline4).
+__device__ __forceinline__ void bspline4f(float t, float w[4]) {
+    const float s = 1.0f - t;
+    const float t2 = t * t, t3 = t2 * t;
+    w[0] = s * s * s * (1.0f / 6.0f);
+    w[1] = (3.0f * t3 - 6.0f * t2 + 4.0f) * (1.0f / 6.0f);
+    w[2] = (-3.0f * t3 + 3.0f * t2 + 3.0f * t + 1.0f) * (1.0f / 6.0f);
+    w[3] = t3 * (1.0f / 6.0f);
+}
+
+// A particle's mesh coordinates for FP32 assignment and interpolation: base
+// node per axis (as bspline_axis), the fractions u - floor(u) rounded once
+// to FP32 (the FP64 part is done once per particle and step), and Q.
+struct __align__(32) MeshPt {
+    int bx, by, bz;
+    float q;
+    float tx, ty, tz;
+    float pad;
+};
+
+__device__ __forceinline__ int mesh_axis(double x, double inv_h, int n, float* t) {
+    double u = x * inv_h;
+    if (!(u >= 0.0 && u <= (double)n)) u = 0.0;
+    const double f = floor(u);
+    *t = (float)(u - f);
+    const int b = (int)f - 1;
+    return b < 0 ? b + n : (b >= n ? b - n : b);
+}
+
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialization attribute may be scheduled before its
+// predecessor in the stream has finished.  pdl_wait() blocks until the
+// predecessor grid has completed and its memory is visible; pdl_trigger()
+// lets the successor grid be scheduled (its blocks then wait in their own
+// pdl_wait()).  Both are no-ops for a kernel launched without the attribute.
+// Kernels of the step call pdl_wait() before touching memory a predecessor
+// writes, then pdl_trigger().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ int linear_tid() {
     return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
 }

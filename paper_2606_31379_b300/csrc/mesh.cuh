@@ -46,6 +46,34 @@ k_spread(int np, const PQ* __restrict__ xq, int n, double inv_h, T* __restrict__
     }
 }
 
+// FP32 assignment from precomputed mesh coordinates, TPP threads per
+// particle (TPP divides 16): each thread adds the 4-point x rows (b, c) =
+// (r % 4, r / 4) for r = part, part + TPP, ... of the 4x4x4 stencil.
+template <int TPP>
+__global__ void __launch_bounds__(P3_THREADS)
+k_spread_mp(int np, const MeshPt* __restrict__ mp, int n, float* __restrict__ q) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(t / TPP), part = (int)(t % TPP);
+    if (s >= np) return;
+    const MeshPt p = mp[s];
+    float wx[4], wy[4], wz[4];
+    bspline4f(p.tx, wx);
+    bspline4f(p.ty, wy);
+    bspline4f(p.tz, wz);
+    int ix[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ix[a] = wrap_idx(p.bx + a, n);
+#pragma unroll
+    for (int r = part; r < 16; r += TPP) {
+        const int b = r & 3, c = r >> 2;
+        const int iy = wrap_idx(p.by + b, n), iz = wrap_idx(p.bz + c, n);
+        const float wyz = p.q * wy[b] * wz[c];
+        float* row = q + ((int64_t)iz * n + iy) * n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) atomicAdd(row + ix[a], wyz * wx[a]);
+    }
+}
+
 // ---------------------------------------------------------------- 3D launch
 // Stencil kernels run on a (32, 8) thread block over an (x, y) tile with
 // blockIdx.z = z, so no index division is needed.  XDIV = 2 packs two x
@@ -102,71 +130,18 @@ k_diffuse(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, dou
     }
 }
 
-// One diffusion step, FP32, four x points per thread (16-byte loads), for
-// meshes with n % 4 == 0.  A warp row covers 128 consecutive x; the x-1 and
-// x+4 neighbours of a quad come from the neighbouring lanes by shuffle (the
-// row ends load them).  Each thread marches zc planes keeping z neighbours
-// in registers.  SUM as in k_diffuse.
-template <bool SUM>
-__global__ void __launch_bounds__(P3_BX * P3_BY)
-k_diffuse4(int n, int zc, const float* __restrict__ in, float* __restrict__ out, float c,
-           double* __restrict__ partial) {
-    const int lane = threadIdx.x;
-    const int q = blockIdx.x * P3_BX + lane;     // quad index along x
-    const int x = 4 * q;
-    const int y = blockIdx.y * P3_BY + threadIdx.y;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(z0 + zc, n);
-    const bool live = x < n && y < n;
-    const int nq = n >> 2;
-    // lanes outside the mesh read point (0, 0) so every access stays in bounds
-    const int yy = live ? y : 0, xx = live ? x : 0;
-    const int xl = xx == 0 ? n - 1 : xx - 1;        // x - 1 (periodic)
-    const int xr = xx + 4 == n ? 0 : xx + 4;        // x + 4 (periodic)
-    const int ym = yy == 0 ? n - 1 : yy - 1, yp = yy == n - 1 ? 0 : yy + 1;
-    const int plane = n * n;
-    double acc = 0.0;
-    const float4* in4 = reinterpret_cast<const float4*>(in);
-    auto ld4 = [&](int z, int row) { return in4[(z * plane + row * n + xx) >> 2]; };
-    float4 vm = ld4(z0 == 0 ? n - 1 : z0 - 1, yy);
-    float4 vc = ld4(z0, yy);
-    for (int z = z0; z < z1; ++z) {
-        const int zp = z == n - 1 ? 0 : z + 1;
-        const float4 vp = ld4(zp, yy);
-        const float4 a = ld4(z, ym);
-        const float4 b = ld4(z, yp);
-        // x neighbours across quads: lane-1's .w and lane+1's .x
-        float left = __shfl_up_sync(0xffffffffu, vc.w, 1);
-        float right = __shfl_down_sync(0xffffffffu, vc.x, 1);
-        if (lane == 0 || q - 1 >= nq) left = in[z * plane + yy * n + xl];
-        if (lane == P3_BX - 1 || q + 1 >= nq) right = in[z * plane + yy * n + xr];
-        float4 o;
-        o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
-        o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
-        o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
-        o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
-        if (live) {
-            reinterpret_cast<float4*>(out)[(z * plane + yy * n + x) >> 2] = o;
-            if (SUM) acc += ((double)o.x + (double)o.y) + ((double)o.z + (double)o.w);
-        }
-        vm = vc;
-        vc = vp;
-    }
-    if (SUM) {
-        acc = block_sum(acc);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
-    }
-}
-
-// k_diffuse4 with the plane count ZC fixed at compile time: every load of
-// the thread's ZC planes (its column from z0-1 to z0+ZC, the y-1 and y+1 rows
-// of its planes, the row-end x neighbours) is issued before the first
-// output is formed, so one L2 round trip covers the whole column instead of
-// one per plane.  Same arithmetic, in the same order, as k_diffuse4.
+// One explicit diffusion step in FP32 with four x-consecutive points per
+// thread (float4 loads and stores; N % 4 == 0).  The x-1 and x+4 neighbours
+// of a quad come from the neighbouring lanes by shuffle (the row ends load
+// them).  Each thread forms ZC z-consecutive planes; every load of its column
+// (planes z0-1 .. z0+ZC), of the y-1 and y+1 rows and of the row-end
+// neighbours is issued before the first output is formed, so one L2 round
+// trip covers the whole column.  SUM as in k_diffuse.
 template <int ZC, bool SUM>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
-k_diffuse4z(int n, const float* __restrict__ in, float* __restrict__ out, float c, double* __restrict__ partial) {
+k_diffuse4(int n, const float* __restrict__ in, float* __restrict__ out, float c, double* __restrict__ partial) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x;
     const int q = blockIdx.x * P3_BX + lane;
     const int x = 4 * q;
@@ -677,166 +652,171 @@ k_prolong_add(int n, const T* __restrict__ ec, T* __restrict__ ef) {
     ef[(z * n + y) * n + x] += prolong_at(ec, n >> 1, x, y, z);
 }
 
-// ---------------------------------------------------------------- small levels
-// The levels of at most 16^3 points run inside one block of 1024 threads with
-// every array in shared memory: red-black Gauss-Seidel, fused residual and
-// restriction, the exact FP64 pseudo-inverse solve on the coarsest level and
-// trilinear prolongation.  Input b (level l0, global), output e (global).
-struct BlkLevel {
-    int n, lg;  // lg = log2(n) for powers of two, else -1
-};
+// ---------------------------------------------------------------- coarse solve
+// Exact solve of M e = b on the coarsest level (n <= 64) by separable real
+// Hartley transforms.  H[k][x] = cos(2 pi k x / n) + sin(2 pi k x / n) is
+// symmetric with H H = n I, and H C H = n diag(lambda) for every symmetric
+// periodic 1D stencil C; the 7-point M is a sum of one such stencil per
+// axis, so M = H3 diag(Lambda) H3 / n^3 with H3 = Hz (x) Hy (x) Hx and
+// Lambda(k) = -4 sum_axes sin^2(pi k_axis / n).  The pseudo-inverse solve is
+//   e = H3 (D o (H3 b)),  D = 1 / (Lambda n^3), and 0 at k = 0,
+// the zero-mean solution (the mean of b is dropped).  Three launches of n
+// blocks: the x and y transforms of each z plane (k_coarse_xy), the z
+// transform, scaling and inverse z transform of each plane of constant ky
+// (k_coarse_z), and the inverse x and y transforms (k_coarse_xy again: the
+// transforms of different axes commute).  Arrays are staged in shared memory
+// padded to nP = 4 ceil(n/4) with zeros; each thread forms a 4 x 4 tile of
+// outputs (16 FMAs per 8 shared-memory loads).
+constexpr int kCoarseMax = 64;
+constexpr int kCoarseThreads = 256;
 
-__device__ __forceinline__ void dec3(int p, const BlkLevel& L, int& x, int& y, int& z) {
-    if (L.lg >= 0) {
-        x = p & (L.n - 1);
-        y = (p >> L.lg) & (L.n - 1);
-        z = p >> (2 * L.lg);
+template <typename T>
+__device__ __forceinline__ void ld4s(const T* p, T v[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 f = *reinterpret_cast<const float4*>(p);
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
     } else {
-        x = p % L.n;
-        const int q = p / L.n;
-        y = q % L.n;
-        z = q / L.n;
+        v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
     }
 }
 
 template <typename T>
-__device__ void blk_rbgs(const BlkLevel& L, T* e, const T* b, int color) {
-    const int n = L.n, half = n >> 1, m = half * n * n;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        int tx, y, z;
-        if (L.lg >= 0) {
-            tx = t & (half - 1);
-            y = (t >> (L.lg - 1)) & (n - 1);
-            z = t >> (2 * L.lg - 1);
-        } else {
-            tx = t % half;
-            const int q = t / half;
-            y = q % n;
-            z = q / n;
-        }
-        const int x = 2 * tx + ((y + z + color) & 1);
-        const int i = (z * n + y) * n + x;
-        e[i] = (nb6(e, x, y, z, n) - b[i]) * (T)(1.0 / 6.0);
+__device__ __forceinline__ void st4s(T* p, T a, T b, T c, T d) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    } else {
+        p[0] = a; p[1] = b; p[2] = c; p[3] = d;
     }
 }
 
+// Stage the n x n table H and the n x n slice src (row stride sstride) into
+// shared memory, zero-padded to nP x nP.
 template <typename T>
-__device__ void blk_resid_restrict(const BlkLevel& C, const T* e, const T* b, T* bc) {
-    const int nc = C.n, n = 2 * nc, m = nc * nc * nc;
-    const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        int X, Y, Z;
-        dec3(t, C, X, Y, Z);
-        T acc = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-            const int z = wrap_idx(2 * Z + dz, n);
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int y = wrap_idx(2 * Y + dy, n);
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int x = wrap_idx(2 * X + dx, n);
-                    const int i = (z * n + y) * n + x;
-                    acc += w1[dx + 1] * w1[dy + 1] * w1[dz + 1] * (b[i] - (nb6(e, x, y, z, n) - (T)6 * e[i]));
-                }
+__device__ __forceinline__ void coarse_stage(int n, int nP, const T* __restrict__ H, const T* __restrict__ src,
+                                             int64_t sstride, T* sH, T* sA) {
+    for (int i = threadIdx.x; i < nP * nP; i += blockDim.x) {
+        const int r = i / nP, c = i - r * nP;
+        const bool in = r < n && c < n;
+        sH[i] = in ? H[r * n + c] : (T)0;
+        sA[i] = in ? src[r * sstride + c] : (T)0;
+    }
+}
+
+// out[r][c] = sum_m L[m][r] R[m][c] over m < nP (L, R in shared memory with
+// row length nP; L symmetric use: L[m][r] = H[r][m]); tile (r0, c0) of 4 x 4.
+template <typename T>
+__device__ __forceinline__ void coarse_tile(int nP, const T* L, const T* R, int r0, int c0, T acc[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+    for (int m = 0; m < nP; ++m) {
+        T l[4], r[4];
+        ld4s(L + m * nP + r0, l);
+        ld4s(R + m * nP + c0, r);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += l[i] * r[j];
+    }
+}
+
+// y then x transform of plane z = blockIdx.x: out[z] = Hy A Hx (A = in[z]).
+// The y pass stores its result transposed (float4 per thread along its
+// rows, lanes along rows: conflict-free), so both passes read rows.
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads)
+k_coarse_xy(int n, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ H) {
+    extern __shared__ __align__(16) unsigned char coarse_smem[];
+    const int nP = (n + 3) & ~3, t4 = nP >> 2;
+    T* sH = reinterpret_cast<T*>(coarse_smem);
+    T* sA = sH + nP * nP;
+    T* sB = sA + nP * nP;
+    const int64_t plane = (int64_t)n * n;
+    const int z = blockIdx.x;
+    coarse_stage(n, nP, H, in + z * plane, n, sH, sA);
+    __syncthreads();
+    const int tile = threadIdx.x;
+    const bool act = tile < t4 * t4;
+    T acc[4][4];
+    // y pass: C[j][x] = sum_y H[y][j] A[y][x]; sB[x][j] = C[j][x]
+    if (act) {
+        const int tj = tile % t4, tx = tile / t4;
+        coarse_tile(nP, sH, sA, 4 * tj, 4 * tx, acc);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) st4s(sB + (4 * tx + c) * nP + 4 * tj, acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+    }
+    __syncthreads();
+    // x pass: out[j][k] = sum_x C[j][x] H[x][k] = sum_x sB[x][j] sH[x][k]
+    if (act) {
+        const int tj = tile / t4, tk = tile % t4;
+        coarse_tile(nP, sB, sH, 4 * tj, 4 * tk, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * tj + i;
+            if (r >= n) break;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int k = 4 * tk + c;
+                if (k < n) out[z * plane + (int64_t)r * n + k] = acc[i][c];
             }
         }
-        bc[t] = (T)4 * acc;
     }
 }
 
+// For ky = blockIdx.x: forward z transform, scaling by D, inverse z transform
+// of the slice t[z][ky][kx] (in place).
 template <typename T>
-__global__ void __launch_bounds__(1024)
-k_vcycle_block(int n0, int nlev, const T* __restrict__ b_in, T* __restrict__ e_out,
-               const double* __restrict__ g, int nu1, int nu2) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // layout: per level l: e_l, b_l (T, n_l^3); then, 16-byte aligned, the
-    // coarsest right-hand side and the pseudo-inverse kernel in FP64
-    T* e[6];
-    T* b[6];
-    BlkLevel lv[6];
-    size_t off = 0;
-    for (int l = 0, n = n0; l < nlev; ++l, n >>= 1) {
-        lv[l].n = n;
-        lv[l].lg = (n & (n - 1)) == 0 ? __ffs(n) - 1 : -1;
-        const size_t m = (size_t)n * n * n;
-        e[l] = reinterpret_cast<T*>(smem_raw + off);
-        off += m * sizeof(T);
-        b[l] = reinterpret_cast<T*>(smem_raw + off);
-        off += m * sizeof(T);
-    }
-    off = (off + 15) / 16 * 16;
-    const int nc = lv[nlev - 1].n, mc = nc * nc * nc;
-    double* bd = reinterpret_cast<double*>(smem_raw + off);
-    double* gs = bd + mc;
-    for (int i = threadIdx.x; i < mc; i += blockDim.x) gs[i] = g[i];
-    const int m0 = n0 * n0 * n0;
-    for (int i = threadIdx.x; i < m0; i += blockDim.x) b[0][i] = b_in[i];
+__global__ void __launch_bounds__(kCoarseThreads)
+k_coarse_z(int n, T* __restrict__ t, const T* __restrict__ H, const T* __restrict__ D) {
+    extern __shared__ __align__(16) unsigned char coarse_smem[];
+    const int nP = (n + 3) & ~3, t4 = nP >> 2;
+    T* sH = reinterpret_cast<T*>(coarse_smem);
+    T* sA = sH + nP * nP;
+    T* sB = sA + nP * nP;
+    const int64_t plane = (int64_t)n * n;
+    const int j = blockIdx.x;
+    coarse_stage(n, nP, H, t + (int64_t)j * n, plane, sH, sA);  // sA[z][kx]
     __syncthreads();
-    // descend
-    for (int l = 0; l < nlev - 1; ++l) {
-        const int m = lv[l].n * lv[l].n * lv[l].n;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) e[l][i] = (T)0;
-        __syncthreads();
-        for (int s = 0; s < nu1; ++s) {
-            blk_rbgs(lv[l], e[l], b[l], 0);
-            __syncthreads();
-            blk_rbgs(lv[l], e[l], b[l], 1);
-            __syncthreads();
+    const int tile = threadIdx.x, tz = tile / t4, tk = tile - tz * t4;
+    const bool act = tile < t4 * t4;
+    T acc[4][4];
+    // U[kz][kx] = sum_z H[z][kz] A[z][kx], scaled by D[kz][ky][kx]
+    if (act) {
+        coarse_tile(nP, sH, sA, 4 * tz, 4 * tk, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kz = 4 * tz + i;
+            T v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int kx = 4 * tk + c;
+                v[c] = (kz < n && kx < n) ? acc[i][c] * D[((int64_t)kz * n + j) * n + kx] : (T)0;
+            }
+            st4s(sB + kz * nP + 4 * tk, v[0], v[1], v[2], v[3]);
         }
-        blk_resid_restrict(lv[l + 1], e[l], b[l], b[l + 1]);
-        __syncthreads();
     }
-    // coarsest: exact pseudo-inverse in FP64, e_i = sum_j g[(i - j) mod n] b_j
-    for (int j = threadIdx.x; j < mc; j += blockDim.x) bd[j] = (double)b[nlev - 1][j];
     __syncthreads();
-    for (int i = threadIdx.x; i < mc; i += blockDim.x) {
-        int x, y, z;
-        dec3(i, lv[nlev - 1], x, y, z);
-        double acc = 0.0;
-        int j = 0;
-        for (int jz = 0; jz < nc; ++jz) {
-            const int dz = z >= jz ? z - jz : z - jz + nc;
-            for (int jy = 0; jy < nc; ++jy) {
-                const int dy = y >= jy ? y - jy : y - jy + nc;
-                const double* grow = gs + (dz * nc + dy) * nc;
-                for (int jx = 0; jx < nc; ++jx, ++j) {
-                    const int dx = x >= jx ? x - jx : x - jx + nc;
-                    acc += grow[dx] * bd[j];
-                }
+    // V[z][kx] = sum_kz H[kz][z] U[kz][kx]
+    if (act) {
+        coarse_tile(nP, sH, sB, 4 * tz, 4 * tk, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int z = 4 * tz + i;
+            if (z >= n) break;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int kx = 4 * tk + c;
+                if (kx < n) t[z * plane + (int64_t)j * n + kx] = acc[i][c];
             }
         }
-        e[nlev - 1][i] = (T)acc;
     }
-    __syncthreads();
-    // ascend
-    for (int l = nlev - 2; l >= 0; --l) {
-        const int n = lv[l].n, m = n * n * n;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            int x, y, z;
-            dec3(i, lv[l], x, y, z);
-            e[l][i] += prolong_at(e[l + 1], n >> 1, x, y, z);
-        }
-        __syncthreads();
-        for (int s = 0; s < nu2; ++s) {
-            blk_rbgs(lv[l], e[l], b[l], 1);
-            __syncthreads();
-            blk_rbgs(lv[l], e[l], b[l], 0);
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < m0; i += blockDim.x) e_out[i] = e[0][i];
 }
 
-// Shared memory of k_vcycle_block for levels n0, n0/2, ... (nlev of them).
-inline size_t vcycle_block_smem(int n0, int nlev, size_t tb) {
-    size_t bytes = 0;
-    int n = n0, nc = n0;
-    for (int l = 0; l < nlev; ++l) {
-        bytes += 2 * tb * (size_t)n * n * n;
-        nc = n;
-        n >>= 1;
-    }
-    bytes = (bytes + 15) / 16 * 16;
-    return bytes + 2 * 8 * (size_t)nc * nc * nc;
+// Shared memory of the coarse kernels for a level of n points per axis.
+inline size_t coarse_smem_bytes(int n, size_t tb) {
+    const size_t nP = (size_t)((n + 3) & ~3);
+    return 3 * nP * nP * tb;
 }
 
 // ---------------------------------------------------------------- interpolation
@@ -894,6 +874,91 @@ k_gather(int np, const PQ* __restrict__ xq, const int* __restrict__ order, int n
         }
     }
     const double scale = -ke * p.w * 0.5 * inv_h;
+    const int i = order[s];
+    const double f[3] = {scale * (double)gx, scale * (double)gy, scale * (double)gz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double sr = Fsr_s[3 * s + d];
+        F[3 * i + d] = sr + f[d];
+        Flr[3 * i + d] = f[d];
+        Fsr[3 * i + d] = sr;
+    }
+}
+
+// FP32 interpolation (Eq. 21) from precomputed mesh coordinates and the FP32
+// copy of phi, one thread per particle.  The central-difference sum is
+// regrouped by summation by parts, term for term over the stencil positions
+// (so it holds with periodic wrap on any mesh):
+//   sum_n W_n (phi_{n+1} - phi_{n-1}) = sum_m phi_m (W_{m-1} - W_{m+1}),
+// per axis, with the weights zero outside the 4-point support.  The x
+// gradient then needs phi on the 6x4x4 block around the stencil, y on 4x6x4
+// and z on 4x4x6: 160 distinct loads instead of 64 x 6.  Output as k_gather.
+static __global__ void __launch_bounds__(P3_THREADS)
+k_gather_mp(int np, const MeshPt* __restrict__ mp, const int* __restrict__ order, int n, double inv_h,
+            double ke, const float* __restrict__ phi, const double* __restrict__ Fsr_s,
+            double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const MeshPt p = mp[s];
+    // e: weights at stencil positions -1..4 (zero at -1 and 4); d: W_{m-1} - W_{m+1}
+    float ex[6], ey[6], ez[6], dx[6], dy[6], dz[6];
+    {
+        float w[4];
+        bspline4f(p.tx, w);
+        ex[0] = 0.0f; ex[1] = w[0]; ex[2] = w[1]; ex[3] = w[2]; ex[4] = w[3]; ex[5] = 0.0f;
+        bspline4f(p.ty, w);
+        ey[0] = 0.0f; ey[1] = w[0]; ey[2] = w[1]; ey[3] = w[2]; ey[4] = w[3]; ey[5] = 0.0f;
+        bspline4f(p.tz, w);
+        ez[0] = 0.0f; ez[1] = w[0]; ez[2] = w[1]; ez[3] = w[2]; ez[4] = w[3]; ez[5] = 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        dx[j] = (j > 0 ? ex[j - 1] : 0.0f) - (j < 5 ? ex[j + 1] : 0.0f);
+        dy[j] = (j > 0 ? ey[j - 1] : 0.0f) - (j < 5 ? ey[j + 1] : 0.0f);
+        dz[j] = (j > 0 ? ez[j - 1] : 0.0f) - (j < 5 ? ez[j + 1] : 0.0f);
+    }
+    int ix[6], iy[6], iz[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        ix[j] = wrap_idx(p.bx - 1 + j, n);
+        iy[j] = wrap_idx(p.by - 1 + j, n);
+        iz[j] = wrap_idx(p.bz - 1 + j, n);
+    }
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const bool zin = c >= 1 && c <= 4;
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            const bool yin = b >= 1 && b <= 4;
+            if (!zin && !yin) continue;
+            const float* row = phi + ((int64_t)iz[c] * n + iy[b]) * n;
+            if (zin && yin) {
+                const float wyz = ey[b] * ez[c], dyz = dy[b] * ez[c], ydz = ey[b] * dz[c];
+#pragma unroll
+                for (int a = 0; a < 6; ++a) {
+                    const float v = row[ix[a]];
+                    gx += dx[a] * wyz * v;
+                    if (a >= 1 && a <= 4) {
+                        const float xv = ex[a] * v;
+                        gy += dyz * xv;
+                        gz += ydz * xv;
+                    }
+                }
+            } else if (zin) {  // rows y = -1 and 4: y gradient only
+                const float dyz = dy[b] * ez[c];
+#pragma unroll
+                for (int a = 1; a <= 4; ++a) gy += dyz * ex[a] * row[ix[a]];
+            } else {           // planes z = -1 and 4: z gradient only
+                const float ydz = ey[b] * dz[c];
+#pragma unroll
+                for (int a = 1; a <= 4; ++a) gz += ydz * ex[a] * row[ix[a]];
+            }
+        }
+    }
+    // g = sum_m phi_m (W_{m-1} - W_{m+1}) = sum_n W_n (phi_{n+1} - phi_{n-1});
+    // F = -ke Q g / (2h)
+    const double scale = -ke * (double)p.q * 0.5 * inv_h;
     const int i = order[s];
     const double f[3] = {scale * (double)gx, scale * (double)gy, scale * (double)gz};
 #pragma unroll

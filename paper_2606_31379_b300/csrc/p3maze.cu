@@ -22,7 +22,7 @@ namespace {
 thread_local std::string g_init_error = "no error";
 
 constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
-constexpr int kBlockLevelMax = 16;  // levels with n <= 16 run in one block (shared memory)
+constexpr int kLevelMin = 16;       // levels are halved while even and larger than this
 constexpr int kMaxGraphs = 4;       // pointer phases of the phi (2) and y (4) rings
 
 // Device scalar slots.
@@ -34,6 +34,11 @@ struct Level {
     void* e = nullptr;
     void* b = nullptr;
     void* r = nullptr;
+    // levels with n <= kCoarseMax can be the coarse level: Hartley table H
+    // (n x n), scaled pseudo-inverse eigenvalues D (n^3), transform work array
+    void* H = nullptr;
+    void* D = nullptr;
+    void* t = nullptr;
 };
 
 // One captured MD step for a given pointer phase of the field rings.
@@ -48,6 +53,9 @@ struct StepGraph {
 };
 
 inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
+
+// Threads per particle of the FP32 assignment kernel.
+constexpr int kSpreadTPP = 4;
 
 // In mixed precision the 8-byte constraint arrays (phi, Psi, z history, s,
 // final residual) hold 64-bit fixed-point values (x 2^40, potential units).
@@ -78,6 +86,7 @@ struct p3maze_ctx {
     int np = 0, N = 0, nc = 0, ncell = 0, prec = 0, pred = 3, itmax = 50, nu1 = 2, nu2 = 2, K = 0;
     int nmol = 0, nlev = 0, method = 0;
     int zc = 8;                          // z planes per thread in the diffusion step (tunable)
+    int pair_fork = 0;                   // pair kernel forked after: 0 smoothing, 1 the cell list (tunable)
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
@@ -96,6 +105,7 @@ struct p3maze_ctx {
     PQ* xq = nullptr;
     PQ* xl64 = nullptr;
     float4* xl32 = nullptr;
+    MeshPt* mp = nullptr;                 // mixed mode: mesh coordinates in cell order
     double *Fs = nullptr, *ecs = nullptr, *evs = nullptr, *eb = nullptr, *ex = nullptr;
     // mesh
     void *q = nullptr, *qs = nullptr;
@@ -108,8 +118,8 @@ struct p3maze_ctx {
     double* rfin = nullptr;
     float* phi32 = nullptr;               // mixed mode: FP32 copy of phi^k for the interpolation
     std::vector<Level> lev;
-    double* gcoarse = nullptr;
-    size_t blk_smem = 0;
+    int lc = 0;                           // coarse level in use (solved exactly)
+    int cmax = 64;                        // coarse level: first with n <= cmax (tunable)
     // reductions and solver state
     double* partial = nullptr;
     double* dscal = nullptr;
@@ -235,31 +245,6 @@ int leave(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
-// Pseudo-inverse kernel of the periodic 7-point operator on an n^3 mesh:
-// g(d) = n^-3 sum_{k != 0} cos(2 pi k.d / n) / lambda(k),
-// lambda(k) = -4 sum_axes sin^2(pi k_axis / n).
-std::vector<double> coarse_green(int n) {
-    const int m = n * n * n;
-    std::vector<double> s2(n), g(m, 0.0);
-    for (int k = 0; k < n; ++k) {
-        const double s = std::sin(kPi * k / n);
-        s2[k] = s * s;
-    }
-    for (int dz = 0; dz < n; ++dz)
-        for (int dy = 0; dy < n; ++dy)
-            for (int dx = 0; dx < n; ++dx) {
-                double acc = 0.0;
-                for (int kz = 0; kz < n; ++kz)
-                    for (int ky = 0; ky < n; ++ky)
-                        for (int kx = 0; kx < n; ++kx) {
-                            if (!kx && !ky && !kz) continue;
-                            const double lam = -4.0 * (s2[kx] + s2[ky] + s2[kz]);
-                            acc += std::cos(2.0 * kPi * (double)(kx * dx + ky * dy + kz * dz) / n) / lam;
-                        }
-                g[(dz * n + dy) * n + dx] = acc / m;
-            }
-    return g;
-}
 
 // ------------------------------------------------------------------ pipeline
 int build_cells(p3maze_ctx* ctx) {
@@ -272,7 +257,8 @@ int build_cells(p3maze_ctx* ctx) {
     k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
     k_gather_sorted<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->order, ctx->r, ctx->Q, ctx->type, ctx->mol,
                                                          ctx->cell, ctx->nc, ctx->lcell, ctx->xq, ctx->xl64,
-                                                         ctx->xl32, ctx->ts, ctx->ms, ctx->cs);
+                                                         ctx->xl32, ctx->ts, ctx->ms, ctx->cs, ctx->mp, ctx->N,
+                                                         ctx->inv_h);
     CKL();
     count(ctx, P3MAZE_ST_CELLS, 5);
     stage_end(ctx, P3MAZE_ST_CELLS);
@@ -306,12 +292,35 @@ void launch_diffuse_tb(p3maze_ctx* ctx, int S, bool last, const T* src, T* dst) 
     }
 }
 
+// Planes per thread of k_diffuse4 for a tuning value zc (1, 2, 4 or 8).
+inline int diffuse4_planes(int zc) { return zc <= 1 ? 1 : zc <= 2 ? 2 : zc <= 4 ? 4 : 8; }
+
+void launch_diffuse4(int zc4, bool sum, dim3 g, cudaStream_t s, int n, const float* src, float* dst, float c,
+                     double* partial) {
+#define D4(Z)                                                                           \
+    do {                                                                                \
+        if (sum) k_diffuse4<Z, true><<<g, kB3, 0, s>>>(n, src, dst, c, partial);        \
+        else k_diffuse4<Z, false><<<g, kB3, 0, s>>>(n, src, dst, c, nullptr);           \
+    } while (0)
+    switch (zc4) {
+        case 1: D4(1); break;
+        case 2: D4(2); break;
+        case 4: D4(4); break;
+        default: D4(8); break;
+    }
+#undef D4
+}
+
 template <typename T>
 int spread_smooth(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_SPREAD);
     CK(cudaMemsetAsync(ctx->q, 0, sizeof(T) * ctx->P, s));
-    k_spread<T><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->N, ctx->inv_h, (T*)ctx->q);
+    if constexpr (sizeof(T) == 4)
+        k_spread_mp<kSpreadTPP><<<nblk((int64_t)ctx->np * kSpreadTPP), P3_THREADS, 0, s>>>(ctx->np, ctx->mp, ctx->N,
+                                                                                          (float*)ctx->q);
+    else
+        k_spread<T><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->N, ctx->inv_h, (T*)ctx->q);
     count(ctx, P3MAZE_ST_SPREAD);
     stage_end(ctx, P3MAZE_ST_SPREAD);
     stage_begin(ctx, P3MAZE_ST_SMOOTH);
@@ -338,17 +347,14 @@ int spread_smooth(p3maze_ctx* ctx) {
             k_sum_final<<<1, 1024, 0, s>>>((int)tb_blocks(ctx->N, ctx->zc), ctx->partial, ctx->dscal + S_QSUM);
             count(ctx, P3MAZE_ST_SMOOTH, launches + 1);
         } else if (ctx->N % 4 == 0) {
-            // one step per launch, four points per thread
-            const dim3 g((ctx->N / 4 + P3_BX - 1) / P3_BX, (ctx->N + P3_BY - 1) / P3_BY, (ctx->N + ctx->zc - 1) / ctx->zc);
+            // one step per launch, four points per thread, zc4 planes per thread
+            const int zc4 = diffuse4_planes(ctx->zc);
+            const dim3 g((ctx->N / 4 + P3_BX - 1) / P3_BX, (ctx->N + P3_BY - 1) / P3_BY, (ctx->N + zc4 - 1) / zc4);
             for (int k = 0; k < ctx->K; ++k) {
                 const bool last = k == ctx->K - 1;
                 T* dst = last ? (T*)ctx->qs : tmp[k & 1];
-                if (last)
-                    k_diffuse4<true><<<g, kB3, 0, s>>>(ctx->N, ctx->zc, (const float*)src, (float*)dst, (float)ctx->c,
-                                                       ctx->partial);
-                else
-                    k_diffuse4<false><<<g, kB3, 0, s>>>(ctx->N, ctx->zc, (const float*)src, (float*)dst, (float)ctx->c,
-                                                        nullptr);
+                launch_diffuse4(zc4, last, g, s, ctx->N, (const float*)src, (float*)dst, (float)ctx->c,
+                                last ? ctx->partial : nullptr);
                 src = dst;
             }
             k_sum_final<<<1, 1024, 0, s>>>((int)(g.x * g.y * g.z), ctx->partial, ctx->dscal + S_QSUM);
@@ -389,18 +395,22 @@ int spread_smooth(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
-// One V-cycle on M e_l = b_l (A6): levels with more than 16^3 points by grid
-// kernels (red-black Gauss-Seidel, fused residual + restriction, trilinear
-// prolongation), the rest inside one shared-memory block.
+// One V-cycle on M e_l = b_l: levels above the coarse level by grid kernels
+// (red-black Gauss-Seidel, fused residual + restriction, trilinear
+// prolongation); the coarse level solved exactly by separable Hartley
+// transforms (three launches).
 template <typename T>
 int vcycle(p3maze_ctx* ctx, int l) {
     cudaStream_t s = ctx->stream;
     Level& L = ctx->lev[l];
     T* e = (T*)L.e;
     T* b = (T*)L.b;
-    if (L.n <= kBlockLevelMax || l == ctx->nlev - 1) {
-        k_vcycle_block<T><<<1, 1024, ctx->blk_smem, s>>>(L.n, ctx->nlev - l, b, e, ctx->gcoarse, ctx->nu1, ctx->nu2);
-        count(ctx, P3MAZE_ST_SOLVE);
+    if (l == ctx->lc) {
+        const size_t sm = coarse_smem_bytes(L.n, sizeof(T));
+        k_coarse_xy<T><<<L.n, kCoarseThreads, sm, s>>>(L.n, b, (T*)L.t, (const T*)L.H);
+        k_coarse_z<T><<<L.n, kCoarseThreads, sm, s>>>(L.n, (T*)L.t, (const T*)L.H, (const T*)L.D);
+        k_coarse_xy<T><<<L.n, kCoarseThreads, sm, s>>>(L.n, (const T*)L.t, e, (const T*)L.H);
+        count(ctx, P3MAZE_ST_SOLVE, 3);
         CKL();
         return P3MAZE_OK;
     }
@@ -605,8 +615,8 @@ int gather_forces(p3maze_ctx* ctx) {
     CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     stage_begin(ctx, P3MAZE_ST_GATHER);
     if (mixed)
-        k_gather<float><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h, ctx->ke,
-                                                             ctx->phi32, ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
+        k_gather_mp<<<nblk(ctx->np), P3_THREADS, 0, s>>>(
+            ctx->np, ctx->mp, ctx->order, ctx->N, ctx->inv_h, ctx->ke, ctx->phi32, ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
     else
         k_gather<double><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h,
                                                               ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr,
@@ -626,10 +636,10 @@ int gather_forces(p3maze_ctx* ctx) {
 // after them so that it fills the SMs the latency-bound solve leaves idle.
 template <typename T>
 int mesh_pipeline(p3maze_ctx* ctx, int pred_order) {
-    int rc = spread_smooth<T>(ctx);
-    if (rc) return rc;
-    rc = pair_forces(ctx);
-    if (rc) return rc;
+    int rc = 0;
+    if (ctx->pair_fork == 1 && (rc = pair_forces(ctx))) return rc;
+    if ((rc = spread_smooth<T>(ctx))) return rc;
+    if (ctx->pair_fork == 0 && (rc = pair_forces(ctx))) return rc;
     return solve_field<T>(ctx, pred_order);
 }
 
@@ -828,17 +838,58 @@ int step_once(p3maze_ctx* ctx) {
     return collect_timing(ctx);
 }
 
+// Levels N, N/2, ... halved while even and larger than kLevelMin; the
+// deepest must be small enough for the exact coarse solve (<= kCoarseMax).
 int validate_mesh(int N, int* nlev, int* ncoarse) {
     if (N < 4) return 0;
     int n = N, l = 1;
-    while (n > 2 && (n % 2) == 0) {
+    while (n > kLevelMin && (n % 2) == 0) {
         n /= 2;
         ++l;
     }
-    if (n > 8) return 0;
+    if (n > kCoarseMax) return 0;
     *nlev = l;
     *ncoarse = n;
     return 1;
+}
+
+// Coarse level for a limit cmax: the first level with n <= cmax, else the deepest.
+int coarse_level(const p3maze_ctx* ctx, int cmax) {
+    for (int l = 0; l < ctx->nlev; ++l)
+        if (ctx->lev[l].n <= cmax) return l;
+    return ctx->nlev - 1;
+}
+
+void set_coarse(p3maze_ctx* ctx, int cmax) {
+    ctx->cmax = cmax;
+    ctx->lc = coarse_level(ctx, cmax);
+    ctx->st.mg_levels = ctx->lc + 1;
+    ctx->st.coarse_n = ctx->lev[ctx->lc].n;
+}
+
+// Hartley table H[k][x] = cos(2 pi k x / n) + sin(2 pi k x / n) and the
+// pseudo-inverse eigenvalues D[kz][ky][kx] = 1 / (Lambda n^3) (0 at k = 0),
+// Lambda = -4 sum_axes sin^2(pi k_axis / n), in FP64 on the host.
+void hartley_tables(int n, std::vector<double>& H, std::vector<double>& D) {
+    H.assign((size_t)n * n, 0.0);
+    D.assign((size_t)n * n * n, 0.0);
+    for (int k = 0; k < n; ++k)
+        for (int x = 0; x < n; ++x) {
+            const double a = 2.0 * kPi * (double)((int64_t)k * x % n) / n;
+            H[(size_t)k * n + x] = std::cos(a) + std::sin(a);
+        }
+    std::vector<double> s2(n);
+    for (int k = 0; k < n; ++k) {
+        const double sk = std::sin(kPi * k / n);
+        s2[k] = sk * sk;
+    }
+    const double n3 = (double)n * n * n;
+    for (int kz = 0; kz < n; ++kz)
+        for (int ky = 0; ky < n; ++ky)
+            for (int kx = 0; kx < n; ++kx) {
+                if (!kx && !ky && !kz) continue;
+                D[((size_t)kz * n + ky) * n + kx] = 1.0 / (-4.0 * (s2[kx] + s2[ky] + s2[kz]) * n3);
+            }
 }
 
 void release(p3maze_ctx* ctx) {
@@ -905,6 +956,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     ALLOC(ctx->xq, sizeof(PQ) * (size_t)n);
     ALLOC(ctx->xl64, sizeof(PQ) * (size_t)n);
     ALLOC(ctx->xl32, sizeof(float4) * (size_t)n);
+    if (mixed) ALLOC(ctx->mp, sizeof(MeshPt) * (size_t)n);
     ALLOC(ctx->Fs, 24 * (size_t)n);
     ALLOC(ctx->ecs, 8 * (size_t)n);
     ALLOC(ctx->evs, 8 * (size_t)n);
@@ -933,29 +985,37 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         ALLOC(L.e, tb * L.pts);
         ALLOC(L.b, tb * L.pts);
         if (l == 0) ALLOC(L.r, tb * L.pts);  // smoothing ping-pong buffer
+        if (nn <= kCoarseMax) {
+            ALLOC(L.H, tb * (size_t)nn * nn);
+            ALLOC(L.D, tb * L.pts);
+            ALLOC(L.t, tb * L.pts);
+        }
         nn /= 2;
     }
-    // the shared-memory V-cycle starts at the first level with n <= 16
     {
-        int l0 = 0;
-        while (l0 < ctx->nlev - 1 && ctx->lev[l0].n > kBlockLevelMax) ++l0;
-        ctx->blk_smem = vcycle_block_smem(ctx->lev[l0].n, ctx->nlev - l0, tb);
-        // The limit is an attribute of the kernel, shared by every context in
-        // the process: only ever raise it, never lower it below what another
-        // context's launches need.
-        cudaFuncAttributes fa{};
-        cudaError_t ea = mixed ? cudaFuncGetAttributes(&fa, k_vcycle_block<float>)
-                               : cudaFuncGetAttributes(&fa, k_vcycle_block<double>);
-        if (ea == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < ctx->blk_smem)
-            ea = mixed ? cudaFuncSetAttribute(k_vcycle_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)ctx->blk_smem)
-                       : cudaFuncSetAttribute(k_vcycle_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)ctx->blk_smem);
+        // The shared-memory limit is an attribute of the kernel, shared by
+        // every context in the process: only ever raise it.
+        size_t sm = 0;
+        for (const Level& L : ctx->lev)
+            if (L.H) sm = std::max(sm, coarse_smem_bytes(L.n, tb));
+        cudaError_t ea = cudaSuccess;
+        auto raise = [&](const void* fn) {
+            cudaFuncAttributes fa{};
+            cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+            if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < sm)
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) ea = e;
+        };
+        if (mixed) {
+            raise((const void*)k_coarse_xy<float>);
+            raise((const void*)k_coarse_z<float>);
+        } else {
+            raise((const void*)k_coarse_xy<double>);
+            raise((const void*)k_coarse_z<double>);
+        }
         if (ea != cudaSuccess)
-            return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory for the block V-cycle: ") + cudaGetErrorString(ea));
+            return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory for the coarse solve: ") + cudaGetErrorString(ea));
     }
-    std::vector<double> g = coarse_green(ctx->lev.back().n);
-    ALLOC(ctx->gcoarse, 8 * g.size());
     ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(ctx->N, 1)), tb_blocks(ctx->N, 1)));
     ALLOC(ctx->dscal, 8 * S_NSCAL);
     {
@@ -972,7 +1032,19 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     // host-side derived arrays
     std::vector<double> hacc(n);
     for (int i = 0; i < n; ++i) hacc[i] = 0.5 * ctx->dt * P3_ACCEL / p->masses[i];
-    CK(cudaMemcpyAsync(ctx->gcoarse, g.data(), 8 * g.size(), cudaMemcpyHostToDevice, s));
+    for (Level& L : ctx->lev) {
+        if (!L.H) continue;
+        std::vector<double> H, D;
+        hartley_tables(L.n, H, D);
+        if (mixed) {
+            std::vector<float> Hf(H.begin(), H.end()), Df(D.begin(), D.end());
+            CK(cudaMemcpy(L.H, Hf.data(), 4 * Hf.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(L.D, Df.data(), 4 * Df.size(), cudaMemcpyHostToDevice));
+        } else {
+            CK(cudaMemcpy(L.H, H.data(), 8 * H.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(L.D, D.data(), 8 * D.size(), cudaMemcpyHostToDevice));
+        }
+    }
     CK(cudaMemcpyAsync(ctx->hdt_acc, hacc.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->mass, p->masses, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->Q, p->charges, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
@@ -1025,6 +1097,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     for (int k = 0; k < 3; ++k) b += a(8 * n);           // hdt_acc mass Q
     for (int k = 0; k < 5; ++k) b += a(4 * n);           // cell order ts ms cs
     b += a(32 * n) + a(32 * n) + a(16 * n);              // xq xl64 xl32
+    if (mixed) b += a(sizeof(MeshPt) * n);               // mp
     b += a(24 * n) + a(8 * n) + a(8 * n);                // Fs ecs evs
     b += a(4 * ncell) + a(4 * ncell) + a(4 * (ncell + 1));
     if (p->types) b += a(4 * n);
@@ -1034,15 +1107,14 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     if (mixed) b += a(4 * P);                            // phi32
     for (int k = 0; k < 4; ++k) b += a(8 * P);           // y ring
     b += a(8 * P);                                       // sigma
-    int nn = N, ncoarse = N;
+    int nn = N;
     for (int l = 0; l < nlev; ++l) {
         const size_t pts = (size_t)nn * nn * nn;
         b += a(tb * pts) + a(tb * pts);
         if (l == 0) b += a(tb * pts);
-        ncoarse = nn;
+        if (nn <= kCoarseMax) b += a(tb * (size_t)nn * nn) + a(tb * pts) + a(tb * pts);  // H D t
         nn /= 2;
     }
-    b += a(8 * (size_t)ncoarse * ncoarse * ncoarse);     // coarse pseudo-inverse kernel
     b += a(8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(N, 1)), tb_blocks(N, 1)));
     b += a(8 * S_NSCAL);
     {
@@ -1085,7 +1157,8 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
         return fail(nullptr, P3MAZE_ERR_INVALID, "iteration counts must be >= 0");
     int nlev = 0, ncoarse = 0;
     if (!validate_mesh(p->mesh, &nlev, &ncoarse))
-        return fail(nullptr, P3MAZE_ERR_INVALID, "mesh must be N >= 4 with N = m 2^l, m <= 8");
+        return fail(nullptr, P3MAZE_ERR_INVALID, "mesh must be N >= 4 with N = m 2^l, m <= 64 (halving stops at 16)");
+    if (p->coarse_max < 0) return fail(nullptr, P3MAZE_ERR_INVALID, "coarse_max must be >= 0");
     double qsum = 0.0, qabs = 0.0;
     for (int i = 0; i < n; ++i) {
         if (!(p->masses[i] > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "masses must be > 0");
@@ -1158,7 +1231,8 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->tol = p->tol;
     ctx->dt = p->dt;
     ctx->method = p->method;
-    ctx->zc = 8;
+    // one diffusion step per launch; FP32 quads take 2 planes per thread
+    ctx->zc = (p->precision == P3MAZE_MIXED && p->mesh % 4 == 0) ? 2 : 8;
     ctx->fuse = 1;
     ctx->res_scale = p->method == P3MAZE_METHOD_P3M ? 4.0 * kPi / h : 1.0;
     ctx->res_unit = p->precision == P3MAZE_MIXED ? 4.0 * kPi / h : 1.0;
@@ -1187,12 +1261,12 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->v_self = -ctx->ke * q2 / (std::sqrt(2.0 * kPi) * sigma);
     ctx->st.smooth_steps = ctx->K;
     ctx->st.smooth_coeff = ctx->c;
-    ctx->st.mg_levels = nlev;
-    ctx->st.coarse_n = ncoarse;
+    (void)ncoarse;
     ctx->st.cells_per_axis = ctx->nc;
     ctx->st.sigma = sigma;
 
     int rc = setup(ctx, p, pos, vel);
+    if (!rc) set_coarse(ctx, p->coarse_max ? p->coarse_max : (p->precision == P3MAZE_MIXED ? 64 : 16));
     if (!rc) rc = initialise_field(ctx);
     if (!rc) rc = leave(ctx);
     if (!rc) {
@@ -1476,7 +1550,7 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
 namespace {
 
 struct Setting {
-    int pred, nu1, nu2, zc, fuse;
+    int pred, nu1, nu2, zc, fuse, pair_fork, cmax;
 };
 
 // Run `warm` + `steps` steps under setting `cfg`; ms per timed step.
@@ -1486,6 +1560,8 @@ int tune_trial(p3maze_ctx* ctx, const Setting& cfg, int warm, int steps, double*
     ctx->nu2 = cfg.nu2;
     ctx->zc = cfg.zc;
     ctx->fuse = cfg.fuse;
+    ctx->pair_fork = cfg.pair_fork;
+    set_coarse(ctx, cfg.cmax);
     destroy_graphs(ctx);  // the setting is recorded in the graphs
     for (int k = 0; k < warm; ++k) {
         int rc = step_once(ctx);
@@ -1523,14 +1599,15 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     const bool timing = ctx->timing;
     ctx->timing = false;
     const int warm = 2;
-    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc, ctx->fuse};
+    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc, ctx->fuse, ctx->pair_fork, ctx->cmax};
     std::vector<Setting> cand;
     const int preds[3] = {1, 2, 3};
     const int sweeps[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
     const int np = ctx->method == P3MAZE_METHOD_P3M ? 1 : 3;
     for (int a = 0; a < np; ++a)
         for (auto& sw : sweeps)
-            cand.push_back({ctx->method == P3MAZE_METHOD_P3M ? 0 : preds[a], sw[0], sw[1], start.zc, start.fuse});
+            cand.push_back({ctx->method == P3MAZE_METHOD_P3M ? 0 : preds[a], sw[0], sw[1], start.zc, start.fuse,
+                            start.pair_fork, start.cmax});
     double initial = 0.0, best = 1e300;
     Setting chosen = start;
     int trials = 0, steps = 0;
@@ -1552,12 +1629,14 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
         }
     }
     if (!rc) {
-        // diffusion kernel: steps per launch (mixed: 1 or 4) x z planes per block
+        // diffusion kernel: steps per launch (mixed: 1 or 4) x z planes per
+        // thread (one step per launch, N % 4 == 0: 1-8) or per block
         const int fuses[2] = {1, 4};
-        const int zcs[4] = {4, 8, 16, 32};
+        const int zcs_quad[4] = {1, 2, 4, 8}, zcs_other[4] = {4, 8, 16, 32};
         for (int f : fuses) {
             if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
-            for (int z : zcs) {
+            const bool quad = f == 1 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
+            for (int z : quad ? zcs_quad : zcs_other) {
                 if (z == chosen.zc && f == chosen.fuse) continue;
                 Setting c = chosen;
                 c.zc = z;
@@ -1575,12 +1654,45 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
             if (rc) break;
         }
     }
+    if (!rc) {
+        // size of the exactly solved coarse level (distinct levels only)
+        const int cms[3] = {16, 32, 64};
+        for (int cm : cms) {
+            if (coarse_level(ctx, cm) == coarse_level(ctx, chosen.cmax)) continue;
+            Setting c = chosen;
+            c.cmax = cm;
+            double ms = 0.0;
+            rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
+            trials += 1;
+            steps += warm + steps_per_trial;
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                chosen = c;
+            }
+        }
+    }
+    if (!rc) {
+        // fork point of the short-range branch
+        Setting c = chosen;
+        c.pair_fork = 1 - chosen.pair_fork;
+        double ms = 0.0;
+        rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
+        trials += 1;
+        steps += warm + steps_per_trial;
+        if (!rc && ms < best) {
+            best = ms;
+            chosen = c;
+        }
+    }
     // keep the fastest setting
     if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = chosen.pred;
     ctx->nu1 = chosen.nu1;
     ctx->nu2 = chosen.nu2;
     ctx->zc = chosen.zc;
     ctx->fuse = chosen.fuse;
+    ctx->pair_fork = chosen.pair_fork;
+    set_coarse(ctx, chosen.cmax);
     destroy_graphs(ctx);
     ctx->timing = timing;
     out->predictor = ctx->pred;
@@ -1588,6 +1700,8 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     out->post_sweeps = ctx->nu2;
     out->diffusion_zc = ctx->zc;
     out->diffusion_fuse = ctx->fuse;
+    out->pair_fork = ctx->pair_fork;
+    out->coarse_max = ctx->cmax;
     out->ms_per_step = best;
     out->initial_ms_per_step = initial;
     out->trials = trials;

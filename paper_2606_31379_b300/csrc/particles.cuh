@@ -143,14 +143,16 @@ static __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __
     }
 }
 
-// Gather particle data into cell order: xq = (x, y, z, Q) and the
-// cell-local coordinates x - c l (FP64 and FP32 copies) used by the pair kernel.
+// Gather particle data into cell order: xq = (x, y, z, Q), the cell-local
+// coordinates x - c l (FP64 and FP32 copies) used by the pair kernel, and
+// (if mp is given) the mesh coordinates of the FP32 assignment and
+// interpolation on the nm^3 mesh.
 static __global__ void k_gather_sorted(int n, const int* __restrict__ order, const double* __restrict__ r,
                                 const double* __restrict__ Q, const int* __restrict__ type,
                                 const int* __restrict__ mol, const int* __restrict__ cell, int nc,
                                 double lcell, PQ* __restrict__ xq, PQ* __restrict__ xl64,
                                 float4* __restrict__ xl32, int* __restrict__ ts, int* __restrict__ ms,
-                                int* __restrict__ cs) {
+                                int* __restrict__ cs, MeshPt* __restrict__ mp, int nm, double inv_h) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int i = order[s];
@@ -163,6 +165,15 @@ static __global__ void k_gather_sorted(int n, const int* __restrict__ order, con
     ts[s] = type ? type[i] : 0;
     ms[s] = mol ? mol[i] : -1;
     cs[s] = c;
+    if (mp) {
+        MeshPt m;
+        m.bx = mesh_axis(x, inv_h, nm, &m.tx);
+        m.by = mesh_axis(y, inv_h, nm, &m.ty);
+        m.bz = mesh_axis(z, inv_h, nm, &m.tz);
+        m.q = (float)q;
+        m.pad = 0.0f;
+        mp[s] = m;
+    }
 }
 
 // ---------------------------------------------------------------- pair forces

@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("mesh", C.c_int32), ("order", C.c_int32), ("tol", C.c_double), ("dt", C.c_double),
                 ("predictor", C.c_int32), ("precision", C.c_int32), ("max_mg_iters", C.c_int32),
                 ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32), ("coulomb_k", C.c_double),
-                ("sr", C.POINTER(SRTable)), ("topology", C.POINTER(Topology)), ("method", C.c_int32)]
+                ("sr", C.POINTER(SRTable)), ("topology", C.POINTER(Topology)), ("method", C.c_int32),
+                ("coarse_max", C.c_int32)]
 
 
 class Energies(C.Structure):
@@ -68,7 +69,8 @@ class Timing(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("predictor", C.c_int32), ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32),
-                ("diffusion_zc", C.c_int32), ("diffusion_fuse", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
+                ("diffusion_zc", C.c_int32), ("diffusion_fuse", C.c_int32),
+                ("pair_fork", C.c_int32), ("coarse_max", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
                 ("trials", C.c_int32), ("steps", C.c_int32)]
 
 
@@ -163,7 +165,7 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
                  sr_table: dict | None = None, triples=None, bonded: dict | None = None,
                  order: int = 4, predictor: int = 3, precision: str = "fp64",
                  max_mg_iters: int = 0, pre_sweeps: int = 0, post_sweeps: int = 0,
-                 coulomb_k: float = 0.0, method: str = "maze"):
+                 coulomb_k: float = 0.0, method: str = "maze", coarse_max: int = 0):
     """p3maze_params for these arguments, plus the arrays it points into
     (keep them alive while the struct is used)."""
     n = int(np.asarray(charges).shape[0])
@@ -187,6 +189,7 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
     p.max_mg_iters, p.pre_sweeps, p.post_sweeps = int(max_mg_iters), int(pre_sweeps), int(post_sweeps)
     p.coulomb_k = float(coulomb_k)
     p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M}[method]
+    p.coarse_max = int(coarse_max)
     tab = sr_table_from(sr_kind, sr_table or {})
     if tab is not None:
         keep["sr"] = tab

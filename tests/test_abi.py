@@ -64,7 +64,9 @@ def _base_kwargs(s):
 
 
 @pytest.mark.parametrize("change, needle", [
-    (dict(mesh=36), "mesh"),               # 36 = 9 * 4: coarsening stops at 9 > 8
+    (dict(mesh=65), "mesh"),               # odd and above 64, the largest exactly solved level
+    (dict(mesh=134), "mesh"),              # 134 -> 67: odd and above 64
+    (dict(coarse_max=-1), "coarse_max"),
     (dict(mesh=2), "mesh"),
     (dict(r_cut=30.0), "r_cut"),
     (dict(tol=0.0), "tol"),
