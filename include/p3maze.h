@@ -77,7 +77,8 @@ extern "C" {
 #define P3MAZE_MESH_QS     1  /* smoothed charge q^s with its mean removed                 */
 #define P3MAZE_MESH_PHI    2  /* constrained mesh potential phi^k (e/A)                    */
 #define P3MAZE_MESH_Y      3  /* converged correction y* of the last solve                 */
-#define P3MAZE_MESH_SIGMA  4  /* predicted constraint residual sigma_p of the last solve  */
+#define P3MAZE_MESH_SIGMA  4  /* predicted constraint residual sigma_p of the last solve
+                                 (after at least one step)                                  */
 
 /* Force parts readable with p3maze_get_forces (n*3 doubles, particle-major). */
 #define P3MAZE_F_TOTAL 0

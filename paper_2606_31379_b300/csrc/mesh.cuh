@@ -435,67 +435,6 @@ __device__ __forceinline__ fix_t charge_term(float qs, float mean, float u) {
     return float_to_fix(__fmul_rn(__fsub_rn(qs, mean), u));
 }
 
-// Prediction (Eq. 17) in fixed point: s = 2 Psi^k - Psi^{k-1} + (4pi/h)(q^s -
-// mean) and the correction guess z0 from the history (order 0-3, as
-// k_predict).  A non-finite q^s sets status to NONFINITE.
-static __global__ void __launch_bounds__(P3_THREADS)
-k_predict_fix(int64_t m, const fix_t* __restrict__ Psik, const fix_t* __restrict__ Psikm1,
-              const float* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, float u,
-              const fix_t* __restrict__ z1, const fix_t* __restrict__ z2, const fix_t* __restrict__ z3, int order,
-              fix_t* __restrict__ s, fix_t* __restrict__ z0, int* __restrict__ status) {
-    __shared__ float mean_s;
-    if (threadIdx.x == 0) mean_s = (float)(qsum[0] * inv_pts);
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const float q = qs[i];
-    if (!isfinite(q)) atomicCAS(status, 0, -5);
-    s[i] = 2 * Psik[i] - Psikm1[i] + charge_term(q, mean_s, u);
-    fix_t g = 0;
-    if (order == 1) g = z1[i];
-    else if (order == 2) g = 2 * z1[i] - z2[i];
-    else if (order == 3) g = 3 * (z1[i] - z2[i]) + z3[i];
-    z0[i] = g;
-}
-
-// Exact fine-level residual r = s - M z: kept in fixed point (rfin, for the
-// Psi update) and as float (input of the correction V-cycle); block maxima
-// of |r| (potential units) to bmax, as k_resid_fine.
-static __global__ void __launch_bounds__(P3_BX * P3_BY)
-k_resid_fix(int n, const fix_t* __restrict__ z, const fix_t* __restrict__ s, float* __restrict__ r,
-            fix_t* __restrict__ rfin, double* __restrict__ bmax) {
-    const int x = blockIdx.x * P3_BX + threadIdx.x;
-    const int y = blockIdx.y * P3_BY + threadIdx.y;
-    float a = 0.0f;
-    if (x < n && y < n) {
-        for (int zz = blockIdx.z; zz < n; zz += gridDim.z) {
-            const int i = (zz * n + y) * n + x;
-            const fix_t res = s[i] - (nb6(z, x, y, zz, n) - 6 * z[i]);
-            rfin[i] = res;
-            const float v = fix_to_float(res);
-            r[i] = v;
-            a = fmaxf(a, fabsf(v));
-        }
-    }
-    const float am = block_max_f(a);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        bmax[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)am;
-}
-
-// z += e, the V-cycle's float correction converted once to fixed point.  A
-// non-finite e sets status to NONFINITE.
-static __global__ void k_add_correction_fix(int64_t m, fix_t* __restrict__ z, const float* __restrict__ e,
-                                     int* __restrict__ status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const float v = e[i];
-    if (!(fabsf(v) < 8.0e6f)) {
-        atomicCAS(status, 0, -5);
-        return;
-    }
-    z[i] += float_to_fix(v);
-}
-
 // Field update in fixed point, written over the k-1 slots:
 //   phi^{k+1} = 2 phi^k - phi^{k-1} - z*
 //   Psi^{k+1} = M phi^{k+1} = r_final - (4pi/h)(q^s - mean)
@@ -544,15 +483,13 @@ struct MGState {
     double last_res;
     long long total_iters;  // summed over finished solves
     long long solves;
+    unsigned arrive;        // blocks of a fused residual kernel done (reset by the last)
+    unsigned pad;
 };
 
-static __global__ void __launch_bounds__(1024)
-k_mg_check(const double* __restrict__ bmax, int nb, double tol, int itmax, MGState* __restrict__ st,
-           cudaGraphConditionalHandle handle, int use_handle) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) a = fmax(a, bmax[i]);
-    const double res = block_max(a);
-    if (threadIdx.x != 0) return;
+// The decision of the check, by one thread, for the residual max-norm res.
+__device__ __forceinline__ void mg_decide(double res, double tol, int itmax, MGState* __restrict__ st,
+                                          cudaGraphConditionalHandle handle, int use_handle) {
     int cont = 0;
     if (!(res <= 1.0e308)) {
         if (st->status == 0) st->status = -5;
@@ -572,6 +509,141 @@ k_mg_check(const double* __restrict__ bmax, int nb, double tol, int itmax, MGSta
     }
     st->cont = cont;
     if (use_handle) cudaGraphSetConditional(handle, cont);
+}
+
+static __global__ void __launch_bounds__(1024)
+k_mg_check(const double* __restrict__ bmax, int nb, double tol, int itmax, MGState* __restrict__ st,
+           cudaGraphConditionalHandle handle, int use_handle) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a = fmax(a, bmax[i]);
+    const double res = block_max(a);
+    if (threadIdx.x == 0) mg_decide(res, tol, itmax, st, handle, use_handle);
+}
+
+// The check fused into a residual kernel: every block publishes its maximum
+// |r| (am, block-uniform) to bmax; the block that arrives last reads all of
+// them back from L2 and takes the decision of k_mg_check.
+struct CheckArgs {
+    double* bmax;
+    double tol;
+    int itmax;
+    MGState* st;
+    cudaGraphConditionalHandle handle;
+    int use_handle;
+};
+
+__device__ __forceinline__ void fused_check(float am, const CheckArgs& ck) {
+    __shared__ int last_s;
+    const int tid = linear_tid();
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (tid == 0) {
+        ck.bmax[b] = (double)am;
+        __threadfence();
+        last_s = atomicAdd(&ck.st->arrive, 1u) == (unsigned)(nb - 1);
+    }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    float a = 0.0f;
+    for (int i = tid; i < nb; i += block_threads()) a = fmaxf(a, (float)__ldcg(ck.bmax + i));
+    a = block_max_f(a);
+    if (tid == 0) {
+        ck.st->arrive = 0;
+        mg_decide((double)a, ck.tol, ck.itmax, ck.st, ck.handle, ck.use_handle);
+    }
+}
+
+// Mixed precision: prediction (Eq. 17), guess z0 and initial residual in one
+// launch, with the check fused.  Per point: s = 2 Psi^k - Psi^{k-1} +
+// (4pi/h)(q^s - mean), z0 from the history (order 0-3), r = s - M z0 with
+// z0 at the neighbours formed from their history values.  Writes z0, the
+// exact residual rfin and its float copy r32.  A non-finite q^s sets status
+// to NONFINITE.
+__device__ __forceinline__ fix_t z_guess(const fix_t* __restrict__ z1, const fix_t* __restrict__ z2,
+                                         const fix_t* __restrict__ z3, int order, int i) {
+    if (order == 1) return z1[i];
+    if (order == 2) return 2 * z1[i] - z2[i];
+    if (order == 3) return 3 * (z1[i] - z2[i]) + z3[i];
+    return 0;
+}
+
+static __global__ void __launch_bounds__(P3_BX * P3_BY)
+k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restrict__ Psikm1,
+                    const float* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, float u,
+                    const fix_t* __restrict__ z1, const fix_t* __restrict__ z2, const fix_t* __restrict__ z3,
+                    int order, fix_t* __restrict__ z0, fix_t* __restrict__ rfin, float* __restrict__ r32,
+                    CheckArgs ck) {
+    __shared__ float mean_s;
+    if (threadIdx.x == 0 && threadIdx.y == 0) mean_s = (float)(qsum[0] * inv_pts);
+    __syncthreads();
+    const int x = blockIdx.x * P3_BX + threadIdx.x;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    float a = 0.0f;
+    if (x < n && y < n) {
+        const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        for (int zz = blockIdx.z; zz < n; zz += gridDim.z) {
+            const int zm = zz == 0 ? n - 1 : zz - 1, zp = zz == n - 1 ? 0 : zz + 1;
+            const int i = (zz * n + y) * n + x;
+            const float q = qs[i];
+            if (!isfinite(q)) atomicCAS(&ck.st->status, 0, -5);
+            const fix_t s = 2 * Psik[i] - Psikm1[i] + charge_term(q, mean_s, u);
+            const fix_t zc = z_guess(z1, z2, z3, order, i);
+            fix_t nb = 0;
+            if (order > 0) {
+                const int row = (zz * n + y) * n;
+                nb = z_guess(z1, z2, z3, order, row + xm) + z_guess(z1, z2, z3, order, row + xp) +
+                     z_guess(z1, z2, z3, order, (zz * n + ym) * n + x) +
+                     z_guess(z1, z2, z3, order, (zz * n + yp) * n + x) +
+                     z_guess(z1, z2, z3, order, (zm * n + y) * n + x) +
+                     z_guess(z1, z2, z3, order, (zp * n + y) * n + x);
+            }
+            const fix_t res = s - (nb - 6 * zc);
+            z0[i] = zc;
+            rfin[i] = res;
+            const float v = fix_to_float(res);
+            r32[i] = v;
+            a = fmaxf(a, fabsf(v));
+        }
+    }
+    fused_check(block_max_f(a), ck);
+}
+
+// Mixed precision: the V-cycle's float correction e enters once as E =
+// fix(e): z += E, and the exact residual is updated without a stencil of z,
+//   r_new = s - M (z + E) = r_old - M E,
+// with E at the neighbours converted the same way; check fused.  A
+// non-finite e sets status to NONFINITE (that point is left unchanged).
+static __global__ void __launch_bounds__(P3_BX * P3_BY)
+k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fix_t* __restrict__ rfin,
+                   float* __restrict__ r32, CheckArgs ck) {
+    const int x = blockIdx.x * P3_BX + threadIdx.x;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    float a = 0.0f;
+    auto fx_of = [](float v) { return fabsf(v) < 8.0e6f ? float_to_fix(v) : (fix_t)0; };
+    if (x < n && y < n) {
+        const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        for (int zz = blockIdx.z; zz < n; zz += gridDim.z) {
+            const int zm = zz == 0 ? n - 1 : zz - 1, zp = zz == n - 1 ? 0 : zz + 1;
+            const int i = (zz * n + y) * n + x;
+            const float ec = e[i];
+            if (!(fabsf(ec) < 8.0e6f)) atomicCAS(&ck.st->status, 0, -5);
+            const fix_t E = fx_of(ec);
+            const int row = (zz * n + y) * n;
+            const fix_t nb = fx_of(e[row + xm]) + fx_of(e[row + xp]) + fx_of(e[(zz * n + ym) * n + x]) +
+                             fx_of(e[(zz * n + yp) * n + x]) + fx_of(e[(zm * n + y) * n + x]) +
+                             fx_of(e[(zp * n + y) * n + x]);
+            z[i] += E;
+            const fix_t res = rfin[i] - (nb - 6 * E);
+            rfin[i] = res;
+            const float v = fix_to_float(res);
+            r32[i] = v;
+            a = fmaxf(a, fabsf(v));
+        }
+    }
+    fused_check(block_max_f(a), ck);
 }
 
 // ---------------------------------------------------------------- multigrid
@@ -691,14 +763,27 @@ __device__ __forceinline__ void st4s(T* p, T a, T b, T c, T d) {
 
 // Stage the n x n table H and the n x n slice src (row stride sstride) into
 // shared memory, zero-padded to nP x nP.
+// Every load is issued before the first store (one memory round trip).
 template <typename T>
 __device__ __forceinline__ void coarse_stage(int n, int nP, const T* __restrict__ H, const T* __restrict__ src,
                                              int64_t sstride, T* sH, T* sA) {
-    for (int i = threadIdx.x; i < nP * nP; i += blockDim.x) {
+    constexpr int kPer = (kCoarseMax * kCoarseMax + kCoarseThreads - 1) / kCoarseThreads;
+    T h[kPer], a[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kCoarseThreads;
         const int r = i / nP, c = i - r * nP;
-        const bool in = r < n && c < n;
-        sH[i] = in ? H[r * n + c] : (T)0;
-        sA[i] = in ? src[r * sstride + c] : (T)0;
+        const bool in = i < nP * nP && r < n && c < n;
+        h[k] = in ? H[r * n + c] : (T)0;
+        a[k] = in ? src[r * sstride + c] : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kCoarseThreads;
+        if (i < nP * nP) {
+            sH[i] = h[k];
+            sA[i] = a[k];
+        }
     }
 }
 
@@ -710,6 +795,7 @@ __device__ __forceinline__ void coarse_tile(int nP, const T* L, const T* R, int 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+#pragma unroll 4
     for (int m = 0; m < nP; ++m) {
         T l[4], r[4];
         ld4s(L + m * nP + r0, l);
@@ -776,10 +862,19 @@ k_coarse_z(int n, T* __restrict__ t, const T* __restrict__ H, const T* __restric
     T* sB = sA + nP * nP;
     const int64_t plane = (int64_t)n * n;
     const int j = blockIdx.x;
-    coarse_stage(n, nP, H, t + (int64_t)j * n, plane, sH, sA);  // sA[z][kx]
-    __syncthreads();
     const int tile = threadIdx.x, tz = tile / t4, tk = tile - tz * t4;
     const bool act = tile < t4 * t4;
+    // this thread's 16 scale factors, loaded with the staging
+    T dsc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int kz = 4 * tz + i, kx = 4 * tk + c;
+            dsc[i][c] = (act && kz < n && kx < n) ? D[((int64_t)kz * n + j) * n + kx] : (T)0;
+        }
+    coarse_stage(n, nP, H, t + (int64_t)j * n, plane, sH, sA);  // sA[z][kx]
+    __syncthreads();
     T acc[4][4];
     // U[kz][kx] = sum_z H[z][kz] A[z][kx], scaled by D[kz][ky][kx]
     if (act) {
@@ -787,13 +882,8 @@ k_coarse_z(int n, T* __restrict__ t, const T* __restrict__ H, const T* __restric
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int kz = 4 * tz + i;
-            T v[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int kx = 4 * tk + c;
-                v[c] = (kz < n && kx < n) ? acc[i][c] * D[((int64_t)kz * n + j) * n + kx] : (T)0;
-            }
-            st4s(sB + kz * nP + 4 * tk, v[0], v[1], v[2], v[3]);
+            st4s(sB + kz * nP + 4 * tk, acc[i][0] * dsc[i][0], acc[i][1] * dsc[i][1], acc[i][2] * dsc[i][2],
+                 acc[i][3] * dsc[i][3]);
         }
     }
     __syncthreads();

@@ -435,56 +435,69 @@ int vcycle(p3maze_ctx* ctx, int l) {
     return P3MAZE_OK;
 }
 
+// Arguments of the check fused into the mixed-precision residual kernels.
+// P3M: max|M phi + (4pi/h) q^s| = (4pi/h) max|M y - sigma_p| for phi = phi_p - (4pi/h) y.
+CheckArgs check_args(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
+    return CheckArgs{ctx->bmax, ctx->tol * ctx->res_unit / ctx->res_scale, ctx->itmax, ctx->dmg, h, use_handle};
+}
+
+// FP64: residual of the current y, then the check kernel.
 template <typename T>
 void launch_resid_check(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
     cudaStream_t s = ctx->stream;
     const dim3 gr = resid_grid(ctx->N);
-    if (ctx->prec == P3MAZE_MIXED)
-        k_resid_fix<<<gr, kB3, 0, s>>>(ctx->N, fx(ctx->yh[0]), fx(ctx->sig), (float*)ctx->lev[0].b, fx(ctx->rfin),
-                                       ctx->bmax);
-    else
-        k_resid_fine<T><<<gr, kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin, ctx->bmax);
-    // P3M: max|M phi + (4pi/h) q^s| = (4pi/h) max|M y - sigma_p| for phi = phi_p - (4pi/h) y
-    k_mg_check<<<1, 1024, 0, s>>>(ctx->bmax, (int)(gr.x * gr.y * gr.z), ctx->tol * ctx->res_unit / ctx->res_scale,
-                                  ctx->itmax,
-                                  ctx->dmg, h, use_handle);
+    k_resid_fine<T><<<gr, kB3, 0, s>>>(ctx->N, ctx->yh[0], ctx->sig, (T*)ctx->lev[0].b, ctx->rfin, ctx->bmax);
+    const CheckArgs ck = check_args(ctx, h, use_handle);
+    k_mg_check<<<1, 1024, 0, s>>>(ck.bmax, (int)(gr.x * gr.y * gr.z), ck.tol, ck.itmax, ck.st, h, use_handle);
     count(ctx, P3MAZE_ST_SOLVE, 2);
 }
 
+// One correction iteration: V-cycle, then y += e with the new residual and
+// the check (mixed: one fused kernel; FP64: three kernels).
 template <typename T>
-int launch_iteration(p3maze_ctx* ctx) {
+int launch_iteration(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
     int rc = vcycle<T>(ctx, 0);
     if (rc) return rc;
-    if (ctx->prec == P3MAZE_MIXED)
-        k_add_correction_fix<<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, fx(ctx->yh[0]),
-                                                                           (const float*)ctx->lev[0].e,
-                                                                           &ctx->dmg->status);
-    else
+    if (ctx->prec == P3MAZE_MIXED) {
+        k_resid_update_fix<<<resid_grid(ctx->N), kB3, 0, ctx->stream>>>(ctx->N, fx(ctx->yh[0]),
+                                                                         (const float*)ctx->lev[0].e, fx(ctx->rfin),
+                                                                         (float*)ctx->lev[0].b,
+                                                                         check_args(ctx, h, use_handle));
+        count(ctx, P3MAZE_ST_SOLVE);
+    } else {
         k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0],
                                                                           (const T*)ctx->lev[0].e);
-    count(ctx, P3MAZE_ST_SOLVE);
+        count(ctx, P3MAZE_ST_SOLVE);
+        launch_resid_check<T>(ctx, h, use_handle);
+    }
     return P3MAZE_OK;
 }
 
-// Correction solve to tol (Eqs. 16, 20).  Eagerly: the host reads the check
-// kernel's decision after every residual.  While capturing a graph: a while
-// node whose body is [V-cycle, y += e, residual, check] and whose condition
-// the check kernel sets, so a step needs no host round trip.
+// Read the check's decision on the host (eager steps).
+int host_decision(p3maze_ctx* ctx, bool* cont) {
+    CK(cudaMemcpyAsync(ctx->hmg, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *cont = !ctx->hmg->status && ctx->hmg->cont;
+    return P3MAZE_OK;
+}
+
+// Correction solve to tol (Eqs. 16, 20) after the initial residual and check
+// have been launched.  Eagerly: the host reads the decision after every
+// check.  While capturing: a while node whose body is one iteration and
+// whose condition the check sets, so a step needs no host round trip.
 template <typename T>
-int solve_loop(p3maze_ctx* ctx) {
+int solve_loop(p3maze_ctx* ctx, cudaGraphConditionalHandle h) {
     cudaStream_t s = ctx->stream;
     if (!ctx->capturing) {
         for (;;) {
-            launch_resid_check<T>(ctx, 0, 0);
             CKL();
-            CK(cudaMemcpyAsync(ctx->hmg, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            if (ctx->hmg->status) break;
-            if (!ctx->hmg->cont) break;
-            int rc = launch_iteration<T>(ctx);
+            bool cont = false;
+            int rc = host_decision(ctx, &cont);
+            if (rc) return rc;
+            if (!cont) break;
+            rc = launch_iteration<T>(ctx, 0, 0);
             if (rc) return rc;
             ctx->eager_iters += 1;
-            CKL();
         }
         return P3MAZE_OK;
     }
@@ -492,11 +505,6 @@ int solve_loop(p3maze_ctx* ctx) {
     cudaGraph_t g;
     const cudaGraphNode_t* deps = nullptr;
     size_t nd = 0;
-    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
-    cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-    launch_resid_check<T>(ctx, h, 1);
-    CKL();
     CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
@@ -512,8 +520,7 @@ int solve_loop(p3maze_ctx* ctx) {
     ctx->stream = ctx->body_stream;
     ctx->in_body = true;
     ctx->body_launches = 0;
-    int brc = launch_iteration<T>(ctx);
-    launch_resid_check<T>(ctx, h, 1);
+    int brc = launch_iteration<T>(ctx, h, 1);
     ctx->in_body = false;
     ctx->stream = s;
     if (brc) {
@@ -534,13 +541,22 @@ template <typename T>
 int solve_field(p3maze_ctx* ctx, int pred_order) {
     cudaStream_t s = ctx->stream;
     const int ik = ctx->icur, ikm1 = 1 - ctx->icur;
+    const bool fixp = ctx->prec == P3MAZE_MIXED;
+    // the while node's condition handle exists before the first check
+    cudaGraphConditionalHandle h = 0;
+    if (ctx->capturing) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g;
+        CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    }
+    const int use_handle = ctx->capturing ? 1 : 0;
     stage_begin(ctx, P3MAZE_ST_PREDICT);
-    if (ctx->prec == P3MAZE_MIXED)
-        k_predict_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, fx(ctx->psi[ik]), fx(ctx->psi[ikm1]),
-                                                          (const float*)ctx->qs, ctx->dscal + S_QSUM,
-                                                          1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
-                                                          fx(ctx->yh[1]), fx(ctx->yh[2]), fx(ctx->yh[3]), pred_order,
-                                                          fx(ctx->sig), fx(ctx->yh[0]), &ctx->dmg->status);
+    if (fixp)
+        k_predict_resid_fix<<<resid_grid(ctx->N), kB3, 0, s>>>(
+            ctx->N, fx(ctx->psi[ik]), fx(ctx->psi[ikm1]), (const float*)ctx->qs, ctx->dscal + S_QSUM,
+            1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h), fx(ctx->yh[1]), fx(ctx->yh[2]), fx(ctx->yh[3]),
+            pred_order, fx(ctx->yh[0]), fx(ctx->rfin), (float*)ctx->lev[0].b, check_args(ctx, h, use_handle));
     else
         k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->psi[ik], ctx->psi[ikm1], (const T*)ctx->qs,
                                                          ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, ctx->yh[1],
@@ -549,11 +565,12 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     count(ctx, P3MAZE_ST_PREDICT, 1);
     stage_end(ctx, P3MAZE_ST_PREDICT);
     stage_begin(ctx, P3MAZE_ST_SOLVE);
-    int rc = solve_loop<T>(ctx);
+    if (!fixp) launch_resid_check<T>(ctx, h, use_handle);
+    int rc = solve_loop<T>(ctx, h);
     if (rc) return rc;
     stage_end(ctx, P3MAZE_ST_SOLVE);
     stage_begin(ctx, P3MAZE_ST_UPDATE);
-    if (ctx->prec == P3MAZE_MIXED)
+    if (fixp)
         k_update_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, fx(ctx->phi[ik]), fx(ctx->phi[ikm1]),
                                                          fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
                                                          (const float*)ctx->qs, ctx->dscal + S_QSUM,
@@ -975,7 +992,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     ALLOC(ctx->rfin, 8 * P);
     if (mixed) ALLOC(ctx->phi32, 4 * P);
     for (int k = 0; k < 4; ++k) ALLOC(ctx->yh[k], 8 * P);
-    ALLOC(ctx->sig, 8 * P);
+    if (!mixed) ALLOC(ctx->sig, 8 * P);  // mixed: the prediction is folded into the first residual
     ctx->lev.resize(ctx->nlev);
     int nn = ctx->N;
     for (int l = 0; l < ctx->nlev; ++l) {
@@ -1106,7 +1123,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     b += a(8 * P);                                       // rfin
     if (mixed) b += a(4 * P);                            // phi32
     for (int k = 0; k < 4; ++k) b += a(8 * P);           // y ring
-    b += a(8 * P);                                       // sigma
+    if (!mixed) b += a(8 * P);                           // sigma
     int nn = N;
     for (int l = 0; l < nlev; ++l) {
         const size_t pts = (size_t)nn * nn * nn;
@@ -1497,12 +1514,34 @@ int p3maze_get_mesh(p3maze_ctx* ctx, int32_t which, double* out) {
         }
         return P3MAZE_OK;
     }
+    if ((which == P3MAZE_MESH_Y || which == P3MAZE_MESH_SIGMA) && ctx->st.steps == 0)
+        return fail(ctx, P3MAZE_ERR_INVALID, "no correction has been solved yet (take a step first)");
+    if (mixed && which == P3MAZE_MESH_SIGMA) {
+        // s = r* + M z* (exact in fixed point) from the last solve's final
+        // residual and correction; sigma_p = s h/4pi
+        std::vector<fix_t> r(P), z(P);
+        int rc = copy_out(ctx, ctx->rfin, r.data(), 8 * (size_t)P);
+        if (!rc) rc = copy_out(ctx, ctx->yh[1], z.data(), 8 * (size_t)P);
+        if (rc) return rc;
+        const int n = ctx->N;
+        const double to_charge = 1.0 / (1099511627776.0 * ctx->res_unit);
+        for (int zz = 0; zz < n; ++zz)
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    auto at = [&](int a, int b, int c) {
+                        return z[((int64_t)((c + n) % n) * n + (b + n) % n) * n + (a + n) % n];
+                    };
+                    const int64_t i = ((int64_t)zz * n + y) * n + x;
+                    const fix_t mz = at(x - 1, y, zz) + at(x + 1, y, zz) + at(x, y - 1, zz) + at(x, y + 1, zz) +
+                                     at(x, y, zz - 1) + at(x, y, zz + 1) - 6 * z[i];
+                    out[i] = (double)(fix_t)(r[i] + mz) * to_charge;
+                }
+        return P3MAZE_OK;
+    }
     const double* src = which == P3MAZE_MESH_PHI   ? ctx->phi[ctx->icur]
-                      : which == P3MAZE_MESH_Y     ? (ctx->st.steps > 0 ? ctx->yh[1] : nullptr)
+                      : which == P3MAZE_MESH_Y     ? ctx->yh[1]
                       : which == P3MAZE_MESH_SIGMA ? ctx->sig
                                                    : nullptr;
-    if (which == P3MAZE_MESH_Y && ctx->st.steps == 0)
-        return fail(ctx, P3MAZE_ERR_INVALID, "no correction has been solved yet (take a step first)");
     if (!src) return fail(ctx, P3MAZE_ERR_INVALID, "unknown mesh array");
     if (!mixed) return copy_out(ctx, src, out, 8 * (size_t)P);
     // fixed point (x 2^40, potential units): phi relative to its first node

@@ -369,3 +369,19 @@ def test_three_level_hierarchy_matches_oracle(P, nacl512, precision, ftol):
         mf = O.mesh_fields(at_positions(nacl512, pos), 0.30, 64)
         margin = 1e-12 if precision == "fp64" else 1e-8
         assert constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"]) <= 1e-8 + margin
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sigma_and_correction_satisfy_eq20(P, nacl512, precision):
+    """The last solve's predicted residual sigma_p and converged correction
+    y* satisfy Eq. 20 to tol: max |sigma_p - M y*| <= tol (oracle stencil),
+    and the reported final residual agrees."""
+    tol = 1e-7
+    with _ctx(P, nacl512, precision=precision, tol=tol) as ctx:
+        with pytest.raises(P.P3MaZeError):
+            ctx.mesh("sigma")                  # no step solved yet
+        ctx.step(3)
+        sig, y = ctx.mesh("sigma"), ctx.mesh("y")
+        r = sig - O.laplacian7(y)
+        assert np.abs(r).max() <= tol * (1 + 1e-5)
+        assert abs(np.abs(r).max() - ctx.stats()["last_residual"]) <= 1e-3 * tol
