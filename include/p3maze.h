@@ -189,6 +189,8 @@ typedef struct {
     int32_t diffusion_fuse;     /* diffusion steps per launch: 1, or 4 (temporal blocking) */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
+    int32_t pair_blocks;        /* pair-kernel grid: 0 one block per home box, else that many
+                                   persistent blocks (one or two per SM)                      */
     double ms_per_step;         /* measured with the chosen setting                    */
     double initial_ms_per_step; /* measured with the setting in use before tuning      */
     int32_t trials;             /* settings timed                                      */
@@ -293,6 +295,16 @@ int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
  * a device-side while node.  enable = 0 issues every kernel individually (same
  * kernels and launch shapes), e.g. for profilers that do not list kernels of
  * conditional graph nodes.                                                    */
+/* Apply a setting (as p3maze_autotune returns it) without timing anything:
+ * predictor (1..3; ignored for P3M), pre_sweeps >= 1, post_sweeps >= 0,
+ * diffusion_zc >= 1, diffusion_fuse 1..4, pair_fork 0 or 1, coarse_max >= 1,
+ * pair_blocks >= 0; the timing fields are ignored.  Captured step graphs are
+ * dropped.  Errors: INVALID (out-of-range field, nothing changed).            */
+int p3maze_set_tuning(p3maze_ctx *ctx, const p3maze_tuning *setting);
+
+/* The setting in use (timing fields zero).                                     */
+int p3maze_get_tuning(p3maze_ctx *ctx, p3maze_tuning *out);
+
 int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
 
 /* Diffusion smoothing of a caller-owned mesh that allocates nothing.
@@ -329,8 +341,10 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
  * otherwise per block: {4, 8, 16, 32}) with, in mixed mode, 1 or 4
  * diffusion steps fused per launch, and where the short-range pair kernel
  * is forked onto its low-priority stream (after smoothing, or right after
- * the cell list so that it also overlaps assignment and smoothing), and the
- * size of the exactly solved coarse level (coarse_max 16, 32 or 64).  None
+ * the cell list so that it also overlaps assignment and smoothing) with its
+ * grid (one block per home box, or a persistent grid of one or two blocks
+ * per SM), and the size of the exactly solved coarse level (coarse_max 16,
+ * 32 or 64).  None
  * of them changes the
  * converged field beyond tol (they change iteration counts and speed only).
  * Every trial runs 2 warm-up steps (graph capture) and steps_per_trial timed

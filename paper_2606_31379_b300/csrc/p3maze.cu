@@ -87,6 +87,8 @@ struct p3maze_ctx {
     int nmol = 0, nlev = 0, method = 0;
     int zc = 8;                          // z planes per thread in the diffusion step (tunable)
     int pair_fork = 0;                   // pair kernel forked after: 0 smoothing, 1 the cell list (tunable)
+    int pair_blocks = 0;                 // pair grid: 0 one block per home box, else a persistent grid (tunable)
+    int nsm = 148;                       // SMs of the device
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
@@ -601,7 +603,8 @@ int pair_forces(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_PAIR);
     const int nbox = (ctx->nc + 1) / 2;
-    const unsigned pb = (unsigned)nbox * nbox * nbox;
+    const unsigned nboxes = (unsigned)nbox * nbox * nbox;
+    const unsigned pb = ctx->pair_blocks > 0 ? std::min(nboxes, (unsigned)ctx->pair_blocks) : nboxes;
 #define PAIR(KIND)                                                                                      \
     do {                                                                                                \
         if (mixed)                                                                                      \
@@ -939,6 +942,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     const bool mixed = p->precision == P3MAZE_MIXED;
     const size_t tb = mixed ? sizeof(float) : sizeof(double);
     CK(cudaGetDevice(&ctx->device));
+    CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     {
         // Work runs on an internal stream of the highest priority (graphs can
         // be captured on it whatever the caller passed), the short-range
@@ -1589,7 +1593,7 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
 namespace {
 
 struct Setting {
-    int pred, nu1, nu2, zc, fuse, pair_fork, cmax;
+    int pred, nu1, nu2, zc, fuse, pair_fork, cmax, pblocks;
 };
 
 // Run `warm` + `steps` steps under setting `cfg`; ms per timed step.
@@ -1600,6 +1604,7 @@ int tune_trial(p3maze_ctx* ctx, const Setting& cfg, int warm, int steps, double*
     ctx->zc = cfg.zc;
     ctx->fuse = cfg.fuse;
     ctx->pair_fork = cfg.pair_fork;
+    ctx->pair_blocks = cfg.pblocks;
     set_coarse(ctx, cfg.cmax);
     destroy_graphs(ctx);  // the setting is recorded in the graphs
     for (int k = 0; k < warm; ++k) {
@@ -1638,7 +1643,8 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     const bool timing = ctx->timing;
     ctx->timing = false;
     const int warm = 2;
-    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc, ctx->fuse, ctx->pair_fork, ctx->cmax};
+    const Setting start = {ctx->pred, ctx->nu1, ctx->nu2, ctx->zc, ctx->fuse, ctx->pair_fork, ctx->cmax,
+                           ctx->pair_blocks};
     std::vector<Setting> cand;
     const int preds[3] = {1, 2, 3};
     const int sweeps[5][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 3}};
@@ -1646,7 +1652,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     for (int a = 0; a < np; ++a)
         for (auto& sw : sweeps)
             cand.push_back({ctx->method == P3MAZE_METHOD_P3M ? 0 : preds[a], sw[0], sw[1], start.zc, start.fuse,
-                            start.pair_fork, start.cmax});
+                            start.pair_fork, start.cmax, start.pblocks});
     double initial = 0.0, best = 1e300;
     Setting chosen = start;
     int trials = 0, steps = 0;
@@ -1712,17 +1718,27 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
         }
     }
     if (!rc) {
-        // fork point of the short-range branch
-        Setting c = chosen;
-        c.pair_fork = 1 - chosen.pair_fork;
-        double ms = 0.0;
-        rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
-        trials += 1;
-        steps += warm + steps_per_trial;
-        if (!rc && ms < best) {
-            best = ms;
-            chosen = c;
-        }
+        // fork point and grid of the short-range branch: one block per home
+        // box, or a persistent grid of one or two blocks per SM that leaves
+        // room for the mesh kernels running beside it
+        const Setting base = chosen;
+        const int grids[3] = {0, ctx->nsm, 2 * ctx->nsm};
+        for (int pf = 0; pf < 2 && !rc; ++pf)
+            for (int gb : grids) {
+                if (pf == base.pair_fork && gb == base.pblocks) continue;
+                Setting c = base;
+                c.pair_fork = pf;
+                c.pblocks = gb;
+                double ms = 0.0;
+                rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
+                trials += 1;
+                steps += warm + steps_per_trial;
+                if (rc) break;
+                if (ms < best) {
+                    best = ms;
+                    chosen = c;
+                }
+            }
     }
     // keep the fastest setting
     if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = chosen.pred;
@@ -1731,6 +1747,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     ctx->zc = chosen.zc;
     ctx->fuse = chosen.fuse;
     ctx->pair_fork = chosen.pair_fork;
+    ctx->pair_blocks = chosen.pblocks;
     set_coarse(ctx, chosen.cmax);
     destroy_graphs(ctx);
     ctx->timing = timing;
@@ -1741,12 +1758,48 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     out->diffusion_fuse = ctx->fuse;
     out->pair_fork = ctx->pair_fork;
     out->coarse_max = ctx->cmax;
+    out->pair_blocks = ctx->pair_blocks;
     out->ms_per_step = best;
     out->initial_ms_per_step = initial;
     out->trials = trials;
     out->steps = steps;
     if (rc) return rc;
     return leave(ctx);
+}
+
+int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
+    if (!ctx || !t) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    if (t->predictor < 1 || t->predictor > 3 || t->pre_sweeps < 1 || t->post_sweeps < 0 || t->diffusion_zc < 1 ||
+        t->diffusion_fuse < 1 || t->diffusion_fuse > 4 || (t->pair_fork != 0 && t->pair_fork != 1) ||
+        t->coarse_max < 1 || t->pair_blocks < 0)
+        return fail(ctx, P3MAZE_ERR_INVALID, "tuning field out of range");
+    if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
+        return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = t->predictor;
+    ctx->nu1 = t->pre_sweeps;
+    ctx->nu2 = t->post_sweeps;
+    ctx->zc = t->diffusion_zc;
+    ctx->fuse = t->diffusion_fuse;
+    ctx->pair_fork = t->pair_fork;
+    ctx->pair_blocks = t->pair_blocks;
+    set_coarse(ctx, t->coarse_max);
+    destroy_graphs(ctx);
+    return P3MAZE_OK;
+}
+
+int p3maze_get_tuning(p3maze_ctx* ctx, p3maze_tuning* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    *out = p3maze_tuning{};
+    out->predictor = ctx->pred;
+    out->pre_sweeps = ctx->nu1;
+    out->post_sweeps = ctx->nu2;
+    out->diffusion_zc = ctx->zc;
+    out->diffusion_fuse = ctx->fuse;
+    out->pair_fork = ctx->pair_fork;
+    out->coarse_max = ctx->cmax;
+    out->pair_blocks = ctx->pair_blocks;
+    return P3MAZE_OK;
 }
 
 int p3maze_set_graphs(p3maze_ctx* ctx, int32_t enable) {

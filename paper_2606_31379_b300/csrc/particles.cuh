@@ -291,6 +291,12 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
     __shared__ unsigned hidx[HCAP];           // sorted index | home-cell offset bits 29..31
     __shared__ R hacc[HCAP][5];               // per home particle: force, Coulomb and non-Coulomb energy
     __shared__ int wq[NW][64];
+    // per warp: the home particle's candidates (FP32: an explicit list of
+    // chunk indices; FP64, whose staging leaves no room: kept rows' start and
+    // prefix, searched per candidate)
+    constexpr bool kList = sizeof(R) == 4;
+    __shared__ unsigned short wlist[kList ? NW : 1][kList ? CAP : 1];
+    __shared__ int wbeg[NW][32], wpre[NW][32];
     __shared__ int s_nh, s_total;
     __shared__ PairPar<R> spar[16];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -309,166 +315,233 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
         }
         spar[tid] = pp;
     }
-    const int b = blockIdx.x;
-    const int bx = b % nbox, by = (b / nbox) % nbox, bz = b / (nbox * nbox);
-    const int h0[3] = {2 * bx, 2 * by, 2 * bz};
-    int hw[3];
-    for (int d = 0; d < 3; ++d) hw[d] = min(2, nc - h0[d]);
-    const int wx = hw[0] + 4, wy = hw[1] + 4, wz = hw[2] + 4;
-    const int nreg = wx * wy * wz;
-    const R lc = (R)lcell;
-    // region cells: unwrapped u = h0 - 2 + r
-    if (tid < nreg) {
-        const int rx = tid % wx, ry = (tid / wx) % wy, rz = tid / (wx * wy);
-        int u[3] = {h0[0] - 2 + rx, h0[1] - 2 + ry, h0[2] - 2 + rz};
-        int c3[3];
-        bool shifted = false;
-        for (int d = 0; d < 3; ++d) {
-            int c = u[d] % nc;
-            if (c < 0) c += nc;
-            c3[d] = c;
-            shifted |= (c != u[d]);
+    // one home box per iteration; the grid may be smaller than the number
+    // of boxes (a persistent launch that leaves room on every SM)
+    const int nbox3 = nbox * nbox * nbox;
+    for (int b = blockIdx.x; b < nbox3; b += gridDim.x) {
+        __syncthreads();  // shared arrays of the previous box are no longer read
+        const int bx = b % nbox, by = (b / nbox) % nbox, bz = b / (nbox * nbox);
+        const int h0[3] = {2 * bx, 2 * by, 2 * bz};
+        int hw[3];
+        for (int d = 0; d < 3; ++d) hw[d] = min(2, nc - h0[d]);
+        const int wx = hw[0] + 4, wy = hw[1] + 4, wz = hw[2] + 4;
+        const int nreg = wx * wy * wz;
+        const R lc = (R)lcell;
+        // region cells: unwrapped u = h0 - 2 + r
+        if (tid < nreg) {
+            const int rx = tid % wx, ry = (tid / wx) % wy, rz = tid / (wx * wy);
+            int u[3] = {h0[0] - 2 + rx, h0[1] - 2 + ry, h0[2] - 2 + rz};
+            int c3[3];
+            bool shifted = false;
+            for (int d = 0; d < 3; ++d) {
+                int c = u[d] % nc;
+                if (c < 0) c += nc;
+                c3[d] = c;
+                shifted |= (c != u[d]);
+            }
+            const int c = (c3[2] * nc + c3[1]) * nc + c3[0];
+            rstart[tid] = start[c];
+            roff[tid + 1] = start[c + 1] - start[c];
+            rsh[tid] = shifted ? 1 : 0;
         }
-        const int c = (c3[2] * nc + c3[1]) * nc + c3[0];
-        rstart[tid] = start[c];
-        roff[tid + 1] = start[c + 1] - start[c];
-        rsh[tid] = shifted ? 1 : 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        roff[0] = 0;
-        for (int r = 0; r < nreg; ++r) roff[r + 1] += roff[r];
-        s_total = roff[nreg];
-        int nh = 0;
-        for (int rz = 2; rz < 2 + hw[2]; ++rz)
-            for (int ry = 2; ry < 2 + hw[1]; ++ry)
-                for (int rx = 2; rx < 2 + hw[0]; ++rx) {
-                    const int r = (rz * wy + ry) * wx + rx;
-                    nh += roff[r + 1] - roff[r];
-                }
-        s_nh = nh;
-    }
-    __syncthreads();
-    const int nh_all = s_nh, total = s_total;
-    const R rc2r = (R)rc2, hl2r = (R)halfL2, alr = (R)alpha, ker = (R)ke;
-    for (int hbase = 0; hbase < nh_all; hbase += HCAP) {
-        const int nh = min(HCAP, nh_all - hbase);
-        // home list of this pass: home cells in region order
+        __syncthreads();
         if (tid == 0) {
-            int k = 0;
+            roff[0] = 0;
+            for (int r = 0; r < nreg; ++r) roff[r + 1] += roff[r];
+            s_total = roff[nreg];
+            int nh = 0;
             for (int rz = 2; rz < 2 + hw[2]; ++rz)
                 for (int ry = 2; ry < 2 + hw[1]; ++ry)
                     for (int rx = 2; rx < 2 + hw[0]; ++rx) {
                         const int r = (rz * wy + ry) * wx + rx;
-                        for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t, ++k)
-                            if (k >= hbase && k < hbase + HCAP)
-                                hidx[k - hbase] = (unsigned)t | ((unsigned)(rx - 2) << 29) |
-                                                  ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
+                        nh += roff[r + 1] - roff[r];
                     }
+            s_nh = nh;
         }
         __syncthreads();
-        for (int k = tid; k < nh; k += blockDim.x) {
-            const unsigned code = hidx[k];
-            const int t = (int)(code & 0x1fffffffu);
-            const V p = xl[t];
-            V q = p;
-            q.x = (R)p.x + (R)((code >> 29) & 1u) * lc;
-            q.y = (R)p.y + (R)((code >> 30) & 1u) * lc;
-            q.z = (R)p.z + (R)((code >> 31) & 1u) * lc;
-            hpos[k] = q;
-            for (int a = 0; a < 5; ++a) hacc[k][a] = (R)0;
-        }
-        for (int c0 = 0; c0 < total; c0 += CAP) {
-            const int cn = min(CAP, total - c0);
+        const int nh_all = s_nh, total = s_total;
+        const R rc2r = (R)rc2, hl2r = (R)halfL2, alr = (R)alpha, ker = (R)ke;
+        for (int hbase = 0; hbase < nh_all; hbase += HCAP) {
+            const int nh = min(HCAP, nh_all - hbase);
+            // home list of this pass: home cells in region order
+            if (tid == 0) {
+                int k = 0;
+                for (int rz = 2; rz < 2 + hw[2]; ++rz)
+                    for (int ry = 2; ry < 2 + hw[1]; ++ry)
+                        for (int rx = 2; rx < 2 + hw[0]; ++rx) {
+                            const int r = (rz * wy + ry) * wx + rx;
+                            for (int t = rstart[r], e = rstart[r] + (roff[r + 1] - roff[r]); t < e; ++t, ++k)
+                                if (k >= hbase && k < hbase + HCAP)
+                                    hidx[k - hbase] = (unsigned)t | ((unsigned)(rx - 2) << 29) |
+                                                      ((unsigned)(ry - 2) << 30) | ((unsigned)(rz - 2) << 31);
+                        }
+            }
             __syncthreads();
-            for (int k = tid; k < cn; k += blockDim.x) {
-                const int gk = c0 + k;
-                int lo = 0, hi = nreg - 1;  // region cell holding candidate gk
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (roff[mid] <= gk) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int r = lo;
-                const int t = rstart[r] + (gk - roff[r]);
-                const int rx = r % wx, ry = (r / wx) % wy, rz = r / (wx * wy);
+            for (int k = tid; k < nh; k += blockDim.x) {
+                const unsigned code = hidx[k];
+                const int t = (int)(code & 0x1fffffffu);
                 const V p = xl[t];
                 V q = p;
-                q.x = (R)p.x + (R)(rx - 2) * lc;
-                q.y = (R)p.y + (R)(ry - 2) * lc;
-                q.z = (R)p.z + (R)(rz - 2) * lc;
-                sp[k] = q;
-                sidx[k] = rsh[r] ? -1 : t;
-                styp[k] = ts[t];
-                smol[k] = ms[t];
+                q.x = (R)p.x + (R)((code >> 29) & 1u) * lc;
+                q.y = (R)p.y + (R)((code >> 30) & 1u) * lc;
+                q.z = (R)p.z + (R)((code >> 31) & 1u) * lc;
+                hpos[k] = q;
+                for (int a = 0; a < 5; ++a) hacc[k][a] = (R)0;
             }
-            __syncthreads();
-            for (int h = warp; h < nh; h += NW) {
-                const int hs = (int)(hidx[h] & 0x1fffffffu);
-                const V pi = hpos[h];
-                const int prow = ts[hs] * tab.nt;
-                const int mi = ms[hs];
-                R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
-                int qn = 0;
-                for (int base = 0; base < cn; base += 32) {
-                    const int k = base + lane;
-                    bool hit = false;
-                    if (k < cn && sidx[k] != hs) {
-                        const V pj = sp[k];
-                        const R ddx = (R)pi.x - (R)pj.x;
-                        const R ddy = (R)pi.y - (R)pj.y;
-                        const R ddz = (R)pi.z - (R)pj.z;
-                        const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        hit = r2 < rc2r && !(mi >= 0 && smol[k] == mi && r2 < hl2r);
+            for (int c0 = 0; c0 < total; c0 += CAP) {
+                const int cn = min(CAP, total - c0);
+                __syncthreads();
+                for (int k = tid; k < cn; k += blockDim.x) {
+                    const int gk = c0 + k;
+                    int lo = 0, hi = nreg - 1;  // region cell holding candidate gk
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (roff[mid] <= gk) lo = mid;
+                        else hi = mid - 1;
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) wq[warp][qn + __popc(m & ((1u << lane) - 1u))] = k;
-                    qn += __popc(m);
+                    const int r = lo;
+                    const int t = rstart[r] + (gk - roff[r]);
+                    const int rx = r % wx, ry = (r / wx) % wy, rz = r / (wx * wy);
+                    const V p = xl[t];
+                    V q = p;
+                    q.x = (R)p.x + (R)(rx - 2) * lc;
+                    q.y = (R)p.y + (R)(ry - 2) * lc;
+                    q.z = (R)p.z + (R)(rz - 2) * lc;
+                    sp[k] = q;
+                    sidx[k] = rsh[r] ? -1 : t;
+                    styp[k] = ts[t];
+                    smol[k] = ms[t];
+                }
+                __syncthreads();
+                for (int h = warp; h < nh; h += NW) {
+                    const unsigned code = hidx[h];
+                    const int hs = (int)(code & 0x1fffffffu);
+                    const int hx = (int)((code >> 29) & 1u), hy = (int)((code >> 30) & 1u), hz = (int)((code >> 31) & 1u);
+                    const V pi = hpos[h];
+                    const int prow = ts[hs] * tab.nt;
+                    const int mi = ms[hs];
+                    R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
+                    // Candidate ranges of this home particle within the chunk:
+                    // lane l < 25 takes the cell row (dy, dz) = (l % 5 - 2, l / 5 - 2)
+                    // of its own 5x5x5 neighbourhood, drops it if its (y, z) gap
+                    // reaches r_c and otherwise keeps the contiguous run of x
+                    // cells that can come within r_c (conservatively rounded).
+                    // Cell r of the region spans [(r - 2) l, (r - 1) l) in the
+                    // coordinates of hpos and sp.
+                    int beg = 0, len = 0;
+                    if (lane < 25) {
+                        const int ry = 2 + hy + lane % 5 - 2, rz = 2 + hz + lane / 5 - 2;
+                        const R ylo = (R)(ry - 2) * lc, zlo = (R)(rz - 2) * lc;
+                        const R gy = max((R)0, max(ylo - (R)pi.y, (R)pi.y - (ylo + lc)));
+                        const R gz = max((R)0, max(zlo - (R)pi.z, (R)pi.z - (zlo + lc)));
+                        const R room = rc2r * (R)1.00001 - (gy * gy + gz * gz);
+                        if (room > (R)0) {
+                            const R sx = sqrt(room) + (R)1e-4 * lc;
+                            const int xlo = max(hx, (int)floor(((R)pi.x - sx) / lc) + 2);
+                            const int xhi = min(hx + 4, (int)floor(((R)pi.x + sx) / lc) + 2);
+                            if (xlo <= xhi) {
+                                const int r0 = (rz * wy + ry) * wx;
+                                const int a = max(roff[r0 + xlo], c0), e = min(roff[r0 + xhi + 1], c0 + cn);
+                                if (e > a) {
+                                    beg = a - c0;
+                                    len = e - a;
+                                }
+                            }
+                        }
+                    }
+                    const unsigned rm = __ballot_sync(0xffffffffu, len > 0);
+                    int incl = len;
+    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                    if constexpr (kList) {
+                        // expand the kept rows into this warp's candidate list
+                        for (int t = 0; t < len; ++t) wlist[warp][incl - len + t] = (unsigned short)(beg + t);
+                    } else if (len > 0) {
+                        const int slot = __popc(rm & ((1u << lane) - 1u));
+                        wbeg[warp][slot] = beg;
+                        wpre[warp][slot] = incl - len;
+                    }
+                    const int nrow = __popc(rm);
                     __syncwarp();
-                    if (qn >= 32) {
+                    int qn = 0;
+                    for (int base = 0; base < tot; base += 32) {
+                        const int g = base + lane;
+                        bool hit = false;
+                        int k = 0;
+                        if (g < tot) {
+                            if constexpr (kList) {
+                                k = wlist[warp][g];
+                            } else {
+                                int lo = 0, hi = nrow - 1;  // last kept row starting at or before g
+                                while (lo < hi) {
+                                    const int mid = (lo + hi + 1) >> 1;
+                                    if (wpre[warp][mid] <= g) lo = mid;
+                                    else hi = mid - 1;
+                                }
+                                k = wbeg[warp][lo] + (g - wpre[warp][lo]);
+                            }
+                            if (sidx[k] != hs) {
+                                const V pj = sp[k];
+                                const R ddx = (R)pi.x - (R)pj.x;
+                                const R ddy = (R)pi.y - (R)pj.y;
+                                const R ddz = (R)pi.z - (R)pj.z;
+                                const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                                hit = r2 < rc2r && !(mi >= 0 && smol[k] == mi && r2 < hl2r);
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, hit);
+                        if (hit) wq[warp][qn + __popc(m & ((1u << lane) - 1u))] = k;
+                        qn += __popc(m);
+                        __syncwarp();
+                        if (qn >= 32) {
+                            const int kk = wq[warp][lane];
+                            pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
+                            __syncwarp();
+                            if (lane < qn - 32) wq[warp][lane] = wq[warp][32 + lane];
+                            __syncwarp();
+                            qn -= 32;
+                        }
+                    }
+                    if (lane < qn) {
                         const int kk = wq[warp][lane];
                         pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
-                        __syncwarp();
-                        if (lane < qn - 32) wq[warp][lane] = wq[warp][32 + lane];
-                        __syncwarp();
-                        qn -= 32;
+                    }
+                    __syncwarp();
+                    // lane partials (a few pairs each) are reduced and accumulated
+                    // in the arithmetic type -- FP64 warp instructions are
+                    // expensive on this part -- and converted to FP64 once
+    #pragma unroll
+                    for (int w = 16; w > 0; w >>= 1) {
+                        fx += __shfl_xor_sync(0xffffffffu, fx, w);
+                        fy += __shfl_xor_sync(0xffffffffu, fy, w);
+                        fz += __shfl_xor_sync(0xffffffffu, fz, w);
+                        ec += __shfl_xor_sync(0xffffffffu, ec, w);
+                        ev += __shfl_xor_sync(0xffffffffu, ev, w);
+                    }
+                    if (lane == 0) {
+                        hacc[h][0] += fx;
+                        hacc[h][1] += fy;
+                        hacc[h][2] += fz;
+                        hacc[h][3] += ec;
+                        hacc[h][4] += ev;
                     }
                 }
-                if (lane < qn) {
-                    const int kk = wq[warp][lane];
-                    pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
-                }
-                __syncwarp();
-                // lane partials (a few pairs each) are reduced and accumulated
-                // in the arithmetic type -- FP64 warp instructions are
-                // expensive on this part -- and converted to FP64 once
-#pragma unroll
-                for (int w = 16; w > 0; w >>= 1) {
-                    fx += __shfl_xor_sync(0xffffffffu, fx, w);
-                    fy += __shfl_xor_sync(0xffffffffu, fy, w);
-                    fz += __shfl_xor_sync(0xffffffffu, fz, w);
-                    ec += __shfl_xor_sync(0xffffffffu, ec, w);
-                    ev += __shfl_xor_sync(0xffffffffu, ev, w);
-                }
-                if (lane == 0) {
-                    hacc[h][0] += fx;
-                    hacc[h][1] += fy;
-                    hacc[h][2] += fz;
-                    hacc[h][3] += ec;
-                    hacc[h][4] += ev;
-                }
             }
+            __syncthreads();
+            for (int k = tid; k < nh; k += blockDim.x) {
+                const int hs = (int)(hidx[k] & 0x1fffffffu);
+                Fs[3 * hs + 0] = (double)hacc[k][0];
+                Fs[3 * hs + 1] = (double)hacc[k][1];
+                Fs[3 * hs + 2] = (double)hacc[k][2];
+                ecs[hs] = 0.5 * ke * (double)hacc[k][3];
+                evs[hs] = 0.5 * (double)hacc[k][4];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int k = tid; k < nh; k += blockDim.x) {
-            const int hs = (int)(hidx[k] & 0x1fffffffu);
-            Fs[3 * hs + 0] = (double)hacc[k][0];
-            Fs[3 * hs + 1] = (double)hacc[k][1];
-            Fs[3 * hs + 2] = (double)hacc[k][2];
-            ecs[hs] = 0.5 * ke * (double)hacc[k][3];
-            evs[hs] = 0.5 * (double)hacc[k][4];
-        }
-        __syncthreads();
     }
 }
 

@@ -70,8 +70,12 @@ class Timing(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("predictor", C.c_int32), ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32),
                 ("diffusion_zc", C.c_int32), ("diffusion_fuse", C.c_int32),
-                ("pair_fork", C.c_int32), ("coarse_max", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
+                ("pair_fork", C.c_int32), ("coarse_max", C.c_int32),
+                ("pair_blocks", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
                 ("trials", C.c_int32), ("steps", C.c_int32)]
+
+
+TUNING_TIMING = ("ms_per_step", "initial_ms_per_step", "trials", "steps")
 
 
 _dp = C.POINTER(C.c_double)
@@ -83,6 +87,8 @@ _sig = {
     "p3maze_step_async": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_wait": (C.c_int, [_ctx]),
     "p3maze_step_host": (C.c_int, [_ctx, _dp, _dp, C.c_int32, _dp, _dp]),
+    "p3maze_set_tuning": (C.c_int, [_ctx, C.c_void_p]),
+    "p3maze_get_tuning": (C.c_int, [_ctx, C.c_void_p]),
     "p3maze_reinit": (C.c_int, [_ctx]),
     "p3maze_equilibrate": (C.c_int, [_ctx, C.c_int32, C.c_double]),
     "p3maze_destroy": (None, [_ctx]),
@@ -358,6 +364,22 @@ class Context:
         t = Tuning()
         self._check(lib.p3maze_autotune(self._h, int(steps_per_trial), C.byref(t)))
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def tuning(self) -> dict:
+        """The solver setting in use (the setting keys of autotune())."""
+        t = Tuning()
+        self._check(lib.p3maze_get_tuning(self._h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_ if k not in TUNING_TIMING}
+
+    def set_tuning(self, **setting):
+        """Apply solver settings (keys as tuning(); missing keys are kept)."""
+        t = Tuning()
+        self._check(lib.p3maze_get_tuning(self._h, C.byref(t)))
+        for k, v in setting.items():
+            if k not in dict(Tuning._fields_) or k in TUNING_TIMING:
+                raise KeyError(k)
+            setattr(t, k, int(v))
+        self._check(lib.p3maze_set_tuning(self._h, C.byref(t)))
 
     def set_graphs(self, enable: bool = True):
         """Replay steady-state steps as CUDA graphs (default) or launch eagerly."""

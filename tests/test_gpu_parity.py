@@ -385,3 +385,27 @@ def test_sigma_and_correction_satisfy_eq20(P, nacl512, precision):
         r = sig - O.laplacian7(y)
         assert np.abs(r).max() <= tol * (1 + 1e-5)
         assert abs(np.abs(r).max() - ctx.stats()["last_residual"]) <= 1e-3 * tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_settings_change_speed_not_results(P, nacl512, precision):
+    """A persistent pair grid (3 blocks looping over all home boxes), the
+    early fork of the pair branch and a different coarse level give the same
+    short-range forces bit for bit (each home box is computed the same way
+    whichever block takes it) and the same field to tol."""
+    with _ctx(P, nacl512, precision=precision, tol=1e-9) as a, \
+            _ctx(P, nacl512, precision=precision, tol=1e-9) as b:
+        t = b.tuning()
+        b.set_tuning(pair_blocks=3, pair_fork=1, coarse_max=16)
+        assert b.tuning() == dict(t, pair_blocks=3, pair_fork=1, coarse_max=16)
+        assert b.stats()["coarse_n"] == 16
+        b.reinit()                          # forces again at the same positions
+        np.testing.assert_array_equal(b.forces("sr"), a.forces("sr"))
+        a.step(2)
+        b.step(2)
+        ref = oracle_full(nacl512, b.positions(), 0.30, 9.0, 32)
+        assert rel_rms(b.forces(), ref["F"]) < (1e-5 if precision == "fp64" else 1e-4)
+        np.testing.assert_allclose(b.positions(), a.positions(), rtol=0,
+                                   atol=1e-9 if precision == "fp64" else 1e-7)
+        with pytest.raises(P.P3MaZeError, match="out of range"):
+            b.set_tuning(pair_fork=2)
