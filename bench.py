@@ -208,13 +208,23 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- roofline
-def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int) -> tuple[float, int]:
+def smoothing_launches(K: int, fuse: int) -> int:
+    """Diffusion launches per MD step: one per step, or two steps per launch
+    (a single step first when K is odd), or fuse > 2 steps per launch."""
+    if fuse == 2:
+        return K // 2 + K % 2
+    if fuse > 2:
+        return -(-K // fuse)
+    return K
+
+
+def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int, fuse: int = 1) -> tuple[float, int]:
     """Compulsory bytes of one launch of the stage's main kernel and the
     launches per step.  b = bytes of a bulk mesh value, P = mesh points.
-    The smoothing stage is reported per diffusion step (K of them per MD
-    step, fused S = 4 per launch in mixed mode): read P values, write P."""
+    A smoothing launch (one diffusion step, or several fused) reads the mesh
+    once and writes it once."""
     if stage == "smooth":
-        return 2.0 * P * b, K
+        return 2.0 * P * b, smoothing_launches(K, fuse)
     if stage == "spread":        # write q once, read 32 B per particle
         return P * b + 32.0 * npart, 1
     if stage == "predict":       # read phi^k, phi^{k-1}, q^s, 3 y histories; write sigma_p, y0
@@ -372,7 +382,11 @@ def run_ours(args) -> int:
     if args.no_graphs:
         ctx.set_graphs(False)
     ctx.step(args.warmup)
-    tuning = None if args.no_tune else ctx.autotune(8)
+    if args.tuning:
+        ctx.set_tuning(**json.loads(args.tuning))
+        tuning = dict(ctx.tuning(), source="--tuning")
+    else:
+        tuning = None if args.no_tune else ctx.autotune(8)
     torch.cuda.synchronize()
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
     it0 = ctx.stats()["total_iters"]
@@ -471,11 +485,13 @@ def run_ours(args) -> int:
     mesh_stages = ("smooth", "spread", "predict", "update", "gather")
     dom = max(mesh_stages, key=lambda k: stage_us[k])
     peaks = measured_peaks()
-    bytes_per_launch, launches_per_step = algorithmic_bytes(dom, b, P3, system.n, K_smooth)
+    bytes_per_launch, launches_per_step = algorithmic_bytes(dom, b, P3, system.n, K_smooth,
+                                                            (tuning or {}).get("diffusion_fuse", 1))
     launch_us = stage_us[dom] / launches_per_step
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
     fuse = (tuning or {}).get("diffusion_fuse", 1)
-    smooth_kernel = ("k_diffuse_tb (4 steps per launch; figures per diffusion step)" if fuse > 1 else
+    smooth_kernel = (f"k_diffuse_tb ({fuse} steps per launch)" if fuse > 2 else
+                     "k_diffuse4x2" if fuse == 2 else
                      "k_diffuse4" if args.precision == "mixed" else "k_diffuse")
     roofline = {"bound": "hbm", "kernel": dom if dom != "smooth" else smooth_kernel,
                 "achieved": achieved, "peak": peaks["hbm_gbs"],
@@ -584,6 +600,8 @@ def main() -> int:
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the solver-setting autotuner")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-batch measurement")
+    ap.add_argument("--tuning", type=str, default=None,
+                    help='apply this solver setting instead of autotuning, e.g. \'{"diffusion_fuse": 2}\'')
     ap.add_argument("--sweep", action="store_true",
                     help="linear-scaling sweep (4096 to 1e6 ions) and SPC/Fw 90000 atoms, one line per size")
     ap.add_argument("--sweep-max", type=int, default=None)

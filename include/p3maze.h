@@ -186,7 +186,8 @@ typedef struct {
     int32_t pre_sweeps;         /* chosen red-black Gauss-Seidel sweeps before / after  */
     int32_t post_sweeps;
     int32_t diffusion_zc;       /* z planes per thread (block) of the diffusion kernel  */
-    int32_t diffusion_fuse;     /* diffusion steps per launch: 1, or 4 (temporal blocking) */
+    int32_t diffusion_fuse;     /* diffusion steps per launch: 1; 2 (two steps as one 25-point
+                                   stencil, FP32, N % 4 == 0); 3 or 4 (temporal blocking)   */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
     int32_t pair_blocks;        /* pair-kernel grid: 0 one block per home box, else that many
@@ -209,6 +210,15 @@ typedef struct p3maze_ctx p3maze_ctx;
  * Errors: INVALID (parameters), OOM, CUDA, NOT_CONVERGED (initial solve).      */
 int p3maze_init(const p3maze_params *params, const double *pos, const double *vel,
                 void *cuda_stream, p3maze_ctx **out);
+
+/* As p3maze_init, but positions and velocities live in caller-owned device
+ * arrays d_pos/d_vel ([n][3] FP64, 8-byte aligned, on the current device):
+ * the context borrows them as its own r and v -- every step updates them in
+ * place, positions are wrapped into the box in place at init -- and never
+ * frees them; they must outlive the context.  NaN/Inf in them is reported as
+ * INVALID.  Other errors as p3maze_init.                                        */
+int p3maze_init_device(const p3maze_params *params, double *d_pos, double *d_vel, void *cuda_stream,
+                       p3maze_ctx **out);
 
 /* Advance nsteps velocity-Verlet steps (Sec. 2; supporting information Sec. 1)
  * and wait for them.  The first steps after (re)initialisation, before the
@@ -272,6 +282,20 @@ int p3maze_get_forces(p3maze_ctx *ctx, int32_t which, double *out);
  * same state, or call p3maze_reinit after an arbitrary change).  Positions
  * are wrapped into the box.                                                    */
 int p3maze_set_state(p3maze_ctx *ctx, const double *pos, const double *vel);
+
+/* Checkpoint and resume.  p3maze_save_state writes into a host buffer of
+ * p3maze_state_bytes bytes everything the next step reads -- positions,
+ * velocities, forces and their parts, per-particle energies, the assigned
+ * charge, phi^k and phi^{k-1}, (h/4pi) M phi (or M phi in fixed point), the
+ * correction history, the last residual, the step count and the solver
+ * tallies -- and p3maze_load_state restores it into a context created with
+ * the same parameters (INVALID otherwise), so that stepping continues from
+ * exactly the saved state.  (Later steps differ from an uninterrupted run
+ * only in the summation order of atomic charge assignment.)  Both wait for
+ * the context's stream.                                                        */
+int p3maze_state_bytes(p3maze_ctx *ctx, size_t *out);
+int p3maze_save_state(p3maze_ctx *ctx, void *buf, size_t bytes);
+int p3maze_load_state(p3maze_ctx *ctx, const void *buf, size_t bytes);
 
 /* Copy a mesh array (P3MAZE_MESH_*) to host, N^3 doubles.                      */
 int p3maze_get_mesh(p3maze_ctx *ctx, int32_t which, double *out);
@@ -338,7 +362,7 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
  * fastest -- multiplier predictor 1..3 (P3MaZe only), smoothing sweeps
  * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)}, the diffusion kernel's
  * z planes per thread (FP32, one step per launch, N % 4 == 0: {1, 2, 4, 8};
- * otherwise per block: {4, 8, 16, 32}) with, in mixed mode, 1 or 4
+ * otherwise per block: {4, 8, 16, 32}) with, in mixed mode, 1, 2 or 4
  * diffusion steps fused per launch, and where the short-range pair kernel
  * is forked onto its low-priority stream (after smoothing, or right after
  * the cell list so that it also overlaps assignment and smoothing) with its

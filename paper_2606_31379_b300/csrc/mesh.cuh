@@ -194,6 +194,108 @@ k_diffuse4(int n, const float* __restrict__ in, float* __restrict__ out, float c
     }
 }
 
+// Two explicit diffusion steps in one pass: (I + cM)^2 written out as one
+// 25-point stencil,
+//   (I + cM)^2 = (1 - 12c + 42c^2) I + (2c - 12c^2) S1 + c^2 S2 + 2c^2 D,
+// S1 the 6 nearest neighbours, S2 the 6 axial neighbours at distance 2, D the
+// 12 face diagonals (M^2 = 42 I - 12 S1 + S2 + 2 D for the 7-point M).  The
+// same linear operator as two launches of k_diffuse4, with one pass over
+// memory.  FP32, four x points per thread (N % 4 == 0), ZC planes per
+// thread with every load issued up front; x neighbours up to distance 2 by
+// shuffles (row ends load them).  SUM as in k_diffuse.
+template <int ZC, bool SUM>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_diffuse4x2(int n, const float* __restrict__ in, float* __restrict__ out, float a0, float a1, float a2, float a3,
+             double* __restrict__ partial) {
+    const int lane = threadIdx.x;
+    const int q = blockIdx.x * P3_BX + lane;
+    const int x = 4 * q;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int z0 = blockIdx.z * ZC;
+    const bool live = x < n && y < n;
+    const int nq = n >> 2;
+    const int yy = live ? y : 0, xx = live ? x : 0;
+    auto wr = [n](int v) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+    const int xl1 = wr(xx - 1), xl2 = wr(xx - 2), xr1 = wr(xx + 4), xr2 = wr(xx + 5);
+    const int ym1 = wr(yy - 1), yp1 = wr(yy + 1), ym2 = wr(yy - 2), yp2 = wr(yy + 2);
+    const int plane = n * n;
+    const bool lend = lane == 0 || q - 1 >= nq, rend = lane == P3_BX - 1 || q + 1 >= nq;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    auto ld4 = [&](int z, int row) { return in4[(wr(z) * plane + row * n + xx) >> 2]; };
+    auto ld1 = [&](int z, int row, int xi) { return in[wr(z) * plane + row * n + xi]; };
+    float4 col[ZC + 4], rm[ZC + 2], rp[ZC + 2], rm2[ZC], rp2[ZC];
+    float cl2[ZC], cr2[ZC], ml1[ZC], mr1[ZC], pl1[ZC], pr1[ZC], zl1[ZC + 2], zr1[ZC + 2];
+#pragma unroll
+    for (int k = 0; k < ZC + 4; ++k) col[k] = ld4(z0 - 2 + k, yy);             // (y, z0-2+k)
+#pragma unroll
+    for (int k = 0; k < ZC + 2; ++k) {
+        rm[k] = ld4(z0 - 1 + k, ym1);                                          // (y-1, z0-1+k)
+        rp[k] = ld4(z0 - 1 + k, yp1);                                          // (y+1, z0-1+k)
+        zl1[k] = lend ? ld1(z0 - 1 + k, yy, xl1) : 0.0f;                       // (x-1, y, z0-1+k)
+        zr1[k] = rend ? ld1(z0 - 1 + k, yy, xr1) : 0.0f;                       // (x+4, y, z0-1+k)
+    }
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        rm2[k] = ld4(z0 + k, ym2);
+        rp2[k] = ld4(z0 + k, yp2);
+        cl2[k] = lend ? ld1(z0 + k, yy, xl2) : 0.0f;
+        cr2[k] = rend ? ld1(z0 + k, yy, xr2) : 0.0f;
+        ml1[k] = lend ? ld1(z0 + k, ym1, xl1) : 0.0f;
+        mr1[k] = rend ? ld1(z0 + k, ym1, xr1) : 0.0f;
+        pl1[k] = lend ? ld1(z0 + k, yp1, xl1) : 0.0f;
+        pr1[k] = rend ? ld1(z0 + k, yp1, xr1) : 0.0f;
+    }
+    // x neighbours at distance 1 (and 2 for the centre row) of a row quad
+    auto xn1 = [&](const float4& v, float lend_v, float rend_v, float& l1, float& r1) {
+        l1 = __shfl_up_sync(0xffffffffu, v.w, 1);
+        r1 = __shfl_down_sync(0xffffffffu, v.x, 1);
+        if (lend) l1 = lend_v;
+        if (rend) r1 = rend_v;
+    };
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const float4 c = col[k + 2], czm = col[k + 1], czp = col[k + 3], czm2 = col[k], czp2 = col[k + 4];
+        const float4 ym = rm[k + 1], yp = rp[k + 1];
+        float cl1, cr1, yml1, ymr1, ypl1, ypr1, zml1, zmr1, zpl1, zpr1;
+        xn1(c, zl1[k + 1], zr1[k + 1], cl1, cr1);
+        float cl2v = __shfl_up_sync(0xffffffffu, c.z, 1), cr2v = __shfl_down_sync(0xffffffffu, c.y, 1);
+        if (lend) cl2v = cl2[k];
+        if (rend) cr2v = cr2[k];
+        xn1(ym, ml1[k], mr1[k], yml1, ymr1);
+        xn1(yp, pl1[k], pr1[k], ypl1, ypr1);
+        xn1(czm, zl1[k], zr1[k], zml1, zmr1);
+        xn1(czp, zl1[k + 2], zr1[k + 2], zpl1, zpr1);
+        const float C8[8] = {cl2v, cl1, c.x, c.y, c.z, c.w, cr1, cr2v};
+        const float YM[6] = {yml1, ym.x, ym.y, ym.z, ym.w, ymr1};
+        const float YP[6] = {ypl1, yp.x, yp.y, yp.z, yp.w, ypr1};
+        const float ZM[6] = {zml1, czm.x, czm.y, czm.z, czm.w, zmr1};
+        const float ZP[6] = {zpl1, czp.x, czp.y, czp.z, czp.w, zpr1};
+        const float YMZM[4] = {rm[k].x, rm[k].y, rm[k].z, rm[k].w}, YMZP[4] = {rm[k + 2].x, rm[k + 2].y, rm[k + 2].z, rm[k + 2].w};
+        const float YPZM[4] = {rp[k].x, rp[k].y, rp[k].z, rp[k].w}, YPZP[4] = {rp[k + 2].x, rp[k + 2].y, rp[k + 2].z, rp[k + 2].w};
+        const float YM2[4] = {rm2[k].x, rm2[k].y, rm2[k].z, rm2[k].w}, YP2[4] = {rp2[k].x, rp2[k].y, rp2[k].z, rp2[k].w};
+        const float ZM2[4] = {czm2.x, czm2.y, czm2.z, czm2.w}, ZP2[4] = {czp2.x, czp2.y, czp2.z, czp2.w};
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float s1 = C8[j + 1] + C8[j + 3] + YM[j + 1] + YP[j + 1] + ZM[j + 1] + ZP[j + 1];
+            const float s2 = C8[j] + C8[j + 4] + YM2[j] + YP2[j] + ZM2[j] + ZP2[j];
+            const float d = YM[j] + YM[j + 2] + YP[j] + YP[j + 2] + ZM[j] + ZM[j + 2] + ZP[j] + ZP[j + 2] +
+                            YMZM[j] + YMZP[j] + YPZM[j] + YPZP[j];
+            o[j] = a0 * C8[j + 2] + a1 * s1 + a2 * s2 + a3 * d;
+        }
+        if (live && z0 + k < n) {
+            reinterpret_cast<float4*>(out)[((z0 + k) * plane + yy * n + x) >> 2] = make_float4(o[0], o[1], o[2], o[3]);
+            if (SUM) acc += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
+        }
+    }
+    if (SUM) {
+        acc = block_sum(acc);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
 // S explicit diffusion steps fused in one launch (2.5D temporal blocking).
 // A block owns an output tile of TX x TY columns and zc planes; its
 // (TX + 2S) x (TY + 2S) threads each hold one column of the haloed tile and

@@ -313,6 +313,22 @@ void launch_diffuse4(int zc4, bool sum, dim3 g, cudaStream_t s, int n, const flo
 #undef D4
 }
 
+void launch_diffuse4x2(int zc4, bool sum, dim3 g, cudaStream_t s, int n, const float* src, float* dst,
+                       const float a[4], double* partial) {
+#define D42(Z)                                                                                            \
+    do {                                                                                                  \
+        if (sum) k_diffuse4x2<Z, true><<<g, kB3, 0, s>>>(n, src, dst, a[0], a[1], a[2], a[3], partial);   \
+        else k_diffuse4x2<Z, false><<<g, kB3, 0, s>>>(n, src, dst, a[0], a[1], a[2], a[3], nullptr);      \
+    } while (0)
+    switch (zc4) {
+        case 1: D42(1); break;
+        case 2: D42(2); break;
+        case 4: D42(4); break;
+        default: D42(8); break;
+    }
+#undef D42
+}
+
 template <typename T>
 int spread_smooth(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
@@ -334,7 +350,7 @@ int spread_smooth(p3maze_ctx* ctx) {
     } else if constexpr (sizeof(T) == 4) {
         T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
         const T* src = (const T*)ctx->q;
-        if (ctx->fuse > 1) {
+        if (ctx->fuse > 2) {
             // S = fuse steps per launch (temporal blocking), then the rest
             int done = 0, launches = 0;
             while (done < ctx->K) {
@@ -349,18 +365,30 @@ int spread_smooth(p3maze_ctx* ctx) {
             k_sum_final<<<1, 1024, 0, s>>>((int)tb_blocks(ctx->N, ctx->zc), ctx->partial, ctx->dscal + S_QSUM);
             count(ctx, P3MAZE_ST_SMOOTH, launches + 1);
         } else if (ctx->N % 4 == 0) {
-            // one step per launch, four points per thread, zc4 planes per thread
+            // four points per thread, zc4 planes per thread; fuse 2: two steps
+            // per launch as one 25-point stencil (a single step first if K is odd)
             const int zc4 = diffuse4_planes(ctx->zc);
             const dim3 g((ctx->N / 4 + P3_BX - 1) / P3_BX, (ctx->N + P3_BY - 1) / P3_BY, (ctx->N + zc4 - 1) / zc4);
-            for (int k = 0; k < ctx->K; ++k) {
-                const bool last = k == ctx->K - 1;
-                T* dst = last ? (T*)ctx->qs : tmp[k & 1];
-                launch_diffuse4(zc4, last, g, s, ctx->N, (const float*)src, (float*)dst, (float)ctx->c,
-                                last ? ctx->partial : nullptr);
+            const double c = ctx->c;
+            const float a[4] = {(float)(1.0 - 12.0 * c + 42.0 * c * c), (float)(2.0 * c - 12.0 * c * c),
+                                (float)(c * c), (float)(2.0 * c * c)};
+            int done = 0, launches = 0;
+            while (done < ctx->K) {
+                const int S = (ctx->fuse == 2 && (ctx->K - done) % 2 == 0) ? 2 : 1;
+                const bool last = done + S == ctx->K;
+                T* dst = last ? (T*)ctx->qs : tmp[launches & 1];
+                if (S == 2)
+                    launch_diffuse4x2(zc4, last, g, s, ctx->N, (const float*)src, (float*)dst, a,
+                                      last ? ctx->partial : nullptr);
+                else
+                    launch_diffuse4(zc4, last, g, s, ctx->N, (const float*)src, (float*)dst, (float)ctx->c,
+                                    last ? ctx->partial : nullptr);
                 src = dst;
+                done += S;
+                ++launches;
             }
             k_sum_final<<<1, 1024, 0, s>>>((int)(g.x * g.y * g.z), ctx->partial, ctx->dscal + S_QSUM);
-            count(ctx, P3MAZE_ST_SMOOTH, ctx->K + 1);
+            count(ctx, P3MAZE_ST_SMOOTH, launches + 1);
         } else {
             for (int k = 0; k < ctx->K; ++k) {
                 const bool last = k == ctx->K - 1;
@@ -937,7 +965,10 @@ void release(p3maze_ctx* ctx) {
     ctx->stream = nullptr;
 }
 
-int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const double* vel) {
+// pos/vel: host arrays to copy in; or d_pos/d_vel: caller-owned device
+// arrays the context borrows as its r and v (never freed by it).
+int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const double* vel, double* d_pos,
+          double* d_vel) {
     const int n = p->n_particles;
     const bool mixed = p->precision == P3MAZE_MIXED;
     const size_t tb = mixed ? sizeof(float) : sizeof(double);
@@ -960,8 +991,13 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     // particle arrays
-    ALLOC(ctx->r, 24 * (size_t)n);
-    ALLOC(ctx->v, 24 * (size_t)n);
+    if (d_pos) {
+        ctx->r = d_pos;
+        ctx->v = d_vel;
+    } else {
+        ALLOC(ctx->r, 24 * (size_t)n);
+        ALLOC(ctx->v, 24 * (size_t)n);
+    }
     ALLOC(ctx->F, 24 * (size_t)n);
     ALLOC(ctx->Fsr, 24 * (size_t)n);
     ALLOC(ctx->Flr, 24 * (size_t)n);
@@ -1070,9 +1106,11 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     CK(cudaMemcpyAsync(ctx->mass, p->masses, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->Q, p->charges, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
     if (p->types) CK(cudaMemcpyAsync(ctx->type, p->types, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->r, pos, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
-    if (vel) CK(cudaMemcpyAsync(ctx->v, vel, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
-    else CK(cudaMemsetAsync(ctx->v, 0, 24 * (size_t)n, s));
+    if (!d_pos) {
+        CK(cudaMemcpyAsync(ctx->r, pos, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
+        if (vel) CK(cudaMemcpyAsync(ctx->v, vel, 24 * (size_t)n, cudaMemcpyHostToDevice, s));
+        else CK(cudaMemsetAsync(ctx->v, 0, 24 * (size_t)n, s));
+    }
     CK(cudaMemsetAsync(ctx->Fb, 0, 24 * (size_t)n, s));
     CK(cudaMemsetAsync(ctx->dscal, 0, 8 * S_NSCAL, s));
     if (ctx->nmol) {
@@ -1088,9 +1126,14 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         CK(cudaMemcpyAsync(ctx->tri, tp->triples, 12 * (size_t)ctx->nmol, cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));  // host vectors go out of scope
     }
-    k_wrap<<<nblk(3 * (int64_t)n), P3_THREADS, 0, s>>>(n, ctx->r, ctx->L);
+    // wrap positions into the box; borrowed arrays are checked for NaN/Inf here
+    CK(cudaMemsetAsync(ctx->dmg, 0, sizeof(MGState), s));
+    k_wrap_check<<<nblk(3 * (int64_t)n), P3_THREADS, 0, s>>>(n, ctx->r, ctx->v, ctx->L, &ctx->dmg->status,
+                                                             P3MAZE_ERR_INVALID);
     CKL();
+    CK(cudaMemcpyAsync(ctx->hmg, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (ctx->hmg->status) return fail(ctx, P3MAZE_ERR_INVALID, "non-finite position or velocity");
     return P3MAZE_OK;
 }
 
@@ -1153,11 +1196,12 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
 // =============================================================== C ABI
 extern "C" {
 
-int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, void* cuda_stream,
-                p3maze_ctx** out) {
+namespace {
+int init_impl(const p3maze_params* p, const double* pos, const double* vel, double* d_pos, double* d_vel,
+              void* cuda_stream, p3maze_ctx** out) {
     if (!out) return fail(nullptr, P3MAZE_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (!p || !pos) return fail(nullptr, P3MAZE_ERR_INVALID, "params or pos is NULL");
+    if (!p || !(pos || (d_pos && d_vel))) return fail(nullptr, P3MAZE_ERR_INVALID, "params or positions NULL");
     const int n = p->n_particles;
     if (n < 1) return fail(nullptr, P3MAZE_ERR_INVALID, "n_particles must be >= 1");
     if (!p->charges || !p->masses) return fail(nullptr, P3MAZE_ERR_INVALID, "charges and masses are required");
@@ -1189,7 +1233,7 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     }
     if (std::fabs(qsum) > 1e-9 * std::max(qabs, 1e-300))
         return fail(nullptr, P3MAZE_ERR_INVALID, "system is not neutral (|sum Q| > 1e-9 sum |Q|)");
-    for (int i = 0; i < 3 * n; ++i)
+    for (int i = 0; pos && i < 3 * n; ++i)
         if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
             return fail(nullptr, P3MAZE_ERR_INVALID, "non-finite position or velocity");
     SRTable tab{};
@@ -1286,7 +1330,7 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     ctx->st.cells_per_axis = ctx->nc;
     ctx->st.sigma = sigma;
 
-    int rc = setup(ctx, p, pos, vel);
+    int rc = setup(ctx, p, pos, vel, d_pos, d_vel);
     if (!rc) set_coarse(ctx, p->coarse_max ? p->coarse_max : (p->precision == P3MAZE_MIXED ? 64 : 16));
     if (!rc) rc = initialise_field(ctx);
     if (!rc) rc = leave(ctx);
@@ -1302,6 +1346,21 @@ int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, vo
     }
     *out = ctx;
     return P3MAZE_OK;
+}
+}  // namespace
+
+int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, void* cuda_stream,
+                p3maze_ctx** out) {
+    if (!pos) return fail(nullptr, P3MAZE_ERR_INVALID, "pos is NULL");
+    return init_impl(p, pos, vel, nullptr, nullptr, cuda_stream, out);
+}
+
+int p3maze_init_device(const p3maze_params* p, double* d_pos, double* d_vel, void* cuda_stream,
+                       p3maze_ctx** out) {
+    if (!d_pos || !d_vel) return fail(nullptr, P3MAZE_ERR_INVALID, "d_pos and d_vel are required");
+    if (((uintptr_t)d_pos | (uintptr_t)d_vel) & 7)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "d_pos and d_vel must be 8-byte aligned");
+    return init_impl(p, nullptr, nullptr, d_pos, d_vel, cuda_stream, out);
 }
 
 int p3maze_step_async(p3maze_ctx* ctx, int32_t nsteps) {
@@ -1477,6 +1536,113 @@ int p3maze_get_forces(p3maze_ctx* ctx, int32_t which, double* out) {
                                                 : nullptr;
     if (!src) return fail(ctx, P3MAZE_ERR_INVALID, "unknown force part");
     return copy_out(ctx, src, out, 24 * (size_t)ctx->np);
+}
+
+// ---- checkpoint: every array the next step reads, plus the observables'
+// inputs, in a fixed order (the field and correction histories in logical
+// order, whatever the ring positions)
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t version, np, mesh, precision, method, nmol;
+    int64_t steps;
+    int32_t nhist, pad;
+    MGState mg;
+};
+
+void state_segments(p3maze_ctx* ctx, std::vector<std::pair<void*, size_t>>& seg) {
+    const size_t n3 = 24 * (size_t)ctx->np, n1 = 8 * (size_t)ctx->np, P8 = 8 * (size_t)ctx->P;
+    const size_t tb = ctx->prec == P3MAZE_MIXED ? 4 : 8;
+    seg = {{ctx->r, n3},   {ctx->v, n3},   {ctx->F, n3},   {ctx->Fsr, n3}, {ctx->Flr, n3}, {ctx->Fb, n3},
+           {ctx->ecs, n1}, {ctx->evs, n1}, {ctx->q, tb * (size_t)ctx->P},
+           {ctx->phi[ctx->icur], P8}, {ctx->phi[1 - ctx->icur], P8},
+           {ctx->psi[ctx->icur], P8}, {ctx->psi[1 - ctx->icur], P8},
+           {ctx->yh[1], P8}, {ctx->yh[2], P8}, {ctx->yh[3], P8},
+           {ctx->rfin, P8}, {ctx->dscal, 8 * (size_t)S_NSCAL}};
+    if (ctx->sig) seg.push_back({ctx->sig, P8});
+    if (ctx->phi32) seg.push_back({ctx->phi32, 4 * (size_t)ctx->P});
+    if (ctx->nmol) {
+        seg.push_back({ctx->eb, 8 * (size_t)ctx->nmol});
+        seg.push_back({ctx->ex, 8 * (size_t)ctx->nmol});
+    }
+}
+
+size_t state_size(p3maze_ctx* ctx) {
+    std::vector<std::pair<void*, size_t>> seg;
+    state_segments(ctx, seg);
+    size_t b = sizeof(StateHeader);
+    for (auto& s : seg) b += s.second;
+    return b;
+}
+}  // namespace
+
+int p3maze_state_bytes(p3maze_ctx* ctx, size_t* out) {
+    if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    *out = state_size(ctx);
+    return P3MAZE_OK;
+}
+
+int p3maze_save_state(p3maze_ctx* ctx, void* buf, size_t bytes) {
+    if (!ctx || !buf) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    if (bytes < state_size(ctx)) return fail(ctx, P3MAZE_ERR_INVALID, "buffer smaller than p3maze_state_bytes");
+    int rc = enter(ctx);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->hmg, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    StateHeader h{};
+    std::memcpy(h.magic, "P3MZSTAT", 8);
+    h.version = 1;
+    h.np = ctx->np;
+    h.mesh = ctx->N;
+    h.precision = ctx->prec;
+    h.method = ctx->method;
+    h.nmol = ctx->nmol;
+    h.steps = ctx->st.steps;
+    h.nhist = ctx->nhist;
+    h.mg = *ctx->hmg;
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    std::vector<std::pair<void*, size_t>> seg;
+    state_segments(ctx, seg);
+    for (auto& s : seg) {
+        CK(cudaMemcpyAsync(p, s.first, s.second, cudaMemcpyDeviceToHost, ctx->stream));
+        p += s.second;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return leave(ctx);
+}
+
+int p3maze_load_state(p3maze_ctx* ctx, const void* buf, size_t bytes) {
+    if (!ctx || !buf) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
+    if (bytes < state_size(ctx)) return fail(ctx, P3MAZE_ERR_INVALID, "buffer smaller than p3maze_state_bytes");
+    StateHeader h{};
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "P3MZSTAT", 8) || h.version != 1 || h.np != ctx->np || h.mesh != ctx->N ||
+        h.precision != ctx->prec || h.method != ctx->method || h.nmol != ctx->nmol)
+        return fail(ctx, P3MAZE_ERR_INVALID, "state was saved from a context with other parameters");
+    int rc = enter(ctx);
+    if (rc) return rc;
+    const unsigned char* p = static_cast<const unsigned char*>(buf) + sizeof h;
+    std::vector<std::pair<void*, size_t>> seg;
+    state_segments(ctx, seg);
+    for (auto& s : seg) {
+        CK(cudaMemcpyAsync(s.first, p, s.second, cudaMemcpyHostToDevice, ctx->stream));
+        p += s.second;
+    }
+    MGState mg = h.mg;
+    mg.it = 0;
+    mg.cont = 0;
+    mg.arrive = 0;
+    *ctx->hmg = mg;
+    CK(cudaMemcpyAsync(ctx->dmg, ctx->hmg, sizeof(MGState), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the pageable source is read before returning
+    ctx->st.steps = h.steps;
+    ctx->nhist = h.nhist;
+    ctx->st.total_iters = mg.total_iters;
+    ctx->eager_iters = mg.total_iters;  // V-cycles before the load are not graph body launches
+    ctx->graph_iters_seen = 0;
+    return leave(ctx);
 }
 
 int p3maze_set_state(p3maze_ctx* ctx, const double* pos, const double* vel) {
@@ -1676,11 +1842,12 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     if (!rc) {
         // diffusion kernel: steps per launch (mixed: 1 or 4) x z planes per
         // thread (one step per launch, N % 4 == 0: 1-8) or per block
-        const int fuses[2] = {1, 4};
+        const int fuses[3] = {1, 2, 4};
         const int zcs_quad[4] = {1, 2, 4, 8}, zcs_other[4] = {4, 8, 16, 32};
         for (int f : fuses) {
             if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
-            const bool quad = f == 1 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
+            if (f == 2 && ctx->N % 4 != 0) continue;
+            const bool quad = f <= 2 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
             for (int z : quad ? zcs_quad : zcs_other) {
                 if (z == chosen.zc && f == chosen.fuse) continue;
                 Setting c = chosen;

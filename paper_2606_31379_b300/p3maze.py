@@ -88,6 +88,10 @@ _sig = {
     "p3maze_wait": (C.c_int, [_ctx]),
     "p3maze_step_host": (C.c_int, [_ctx, _dp, _dp, C.c_int32, _dp, _dp]),
     "p3maze_set_tuning": (C.c_int, [_ctx, C.c_void_p]),
+    "p3maze_init_device": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_ctx)]),
+    "p3maze_state_bytes": (C.c_int, [_ctx, C.POINTER(C.c_size_t)]),
+    "p3maze_save_state": (C.c_int, [_ctx, C.c_void_p, C.c_size_t]),
+    "p3maze_load_state": (C.c_int, [_ctx, C.c_void_p, C.c_size_t]),
     "p3maze_get_tuning": (C.c_int, [_ctx, C.c_void_p]),
     "p3maze_reinit": (C.c_int, [_ctx]),
     "p3maze_equilibrate": (C.c_int, [_ctx, C.c_int32, C.c_double]),
@@ -238,15 +242,24 @@ class Context:
     Parameters follow p3maze_params; `stream` is a raw cudaStream_t handle
     (e.g. torch.cuda.Stream().cuda_stream) or None for the default stream."""
 
-    def __init__(self, pos, charges, masses, box: float, *, stream: int | None = None, **kw):
+    def __init__(self, pos, charges, masses, box: float, *, stream: int | None = None,
+                 device_pos: int | None = None, device_vel: int | None = None, **kw):
+        """pos: host [n][3] positions (A).  With device_pos/device_vel (device
+        addresses of caller-owned [n][3] float64 arrays, e.g. a tensor's
+        data_ptr()) the context borrows them as its positions and velocities
+        (p3maze_init_device); pos then only gives the shape."""
         self._h = _ctx()
         p, keep = build_params(pos, charges, masses, box, **kw)
         self.n = int(p.n_particles)
         self.mesh_n = int(p.mesh)
         self.box = float(box)
         vel = keep["vel"]
-        rc = lib.p3maze_init(C.byref(p), _ptr(keep["pos"]), None if vel is None else _ptr(vel),
-                             C.c_void_p(stream or 0), C.byref(self._h))
+        if device_pos is not None:
+            rc = lib.p3maze_init_device(C.byref(p), C.c_void_p(int(device_pos)), C.c_void_p(int(device_vel)),
+                                        C.c_void_p(stream or 0), C.byref(self._h))
+        else:
+            rc = lib.p3maze_init(C.byref(p), _ptr(keep["pos"]), None if vel is None else _ptr(vel),
+                                 C.c_void_p(stream or 0), C.byref(self._h))
         if rc:
             raise P3MaZeError(rc, lib.p3maze_last_error(None).decode())
         self.precision = kw.get("precision", "fp64")
@@ -364,6 +377,19 @@ class Context:
         t = Tuning()
         self._check(lib.p3maze_autotune(self._h, int(steps_per_trial), C.byref(t)))
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def save_state(self) -> np.ndarray:
+        """Checkpoint of the full stepping state (p3maze_save_state), as bytes."""
+        nb = C.c_size_t()
+        self._check(lib.p3maze_state_bytes(self._h, C.byref(nb)))
+        buf = np.empty(nb.value, np.uint8)
+        self._check(lib.p3maze_save_state(self._h, buf.ctypes.data_as(C.c_void_p), nb.value))
+        return buf
+
+    def load_state(self, buf) -> None:
+        """Resume from save_state() of a context with the same parameters."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(lib.p3maze_load_state(self._h, b.ctypes.data_as(C.c_void_p), b.nbytes))
 
     def tuning(self) -> dict:
         """The solver setting in use (the setting keys of autotune())."""

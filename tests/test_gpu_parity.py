@@ -266,7 +266,7 @@ def test_autotuner_keeps_results_within_tolerance(P, nacl512):
         assert t["predictor"] in (1, 2, 3)
         assert (t["pre_sweeps"], t["post_sweeps"]) in ((1, 1), (2, 1), (1, 2), (2, 2), (3, 3))
         # planes per thread (one step per launch, FP32 quads) or per block (4 steps per launch)
-        assert (t["diffusion_fuse"], t["diffusion_zc"]) in [(1, z) for z in (1, 2, 4, 8)] + \
+        assert (t["diffusion_fuse"], t["diffusion_zc"]) in [(f, z) for f in (1, 2) for z in (1, 2, 4, 8)] + \
             [(4, z) for z in (4, 8, 16, 32)]
         assert t["trials"] >= 16 and t["ms_per_step"] <= t["initial_ms_per_step"]
         assert ctx.stats()["steps"] == 4 + t["steps"]
@@ -409,3 +409,21 @@ def test_settings_change_speed_not_results(P, nacl512, precision):
                                    atol=1e-9 if precision == "fp64" else 1e-7)
         with pytest.raises(P.P3MaZeError, match="out of range"):
             b.set_tuning(pair_fork=2)
+
+
+@pytest.mark.parametrize("mesh, zc", [(32, 2), (24, 1), (24, 8)])
+def test_two_step_diffusion_kernel_matches_oracle(P, nacl512, mesh, zc):
+    """Two diffusion steps per launch as one 25-point stencil (mixed mode):
+    the same smoothed charge as the oracle's K single steps (K = 25 at 32^3,
+    odd, so one single step comes first; K = 14 at 24^3)."""
+    with _ctx(P, nacl512, precision="mixed", tol=1e-7, mesh=mesh) as ctx:
+        ctx.set_tuning(diffusion_fuse=2, diffusion_zc=zc)
+        ctx.reinit()
+        K = ctx.stats()["smooth_steps"]
+        assert K == (25 if mesh == 32 else 14)
+        mf = O.mesh_fields(at_positions(nacl512, ctx.positions()), 0.30, mesh)
+        qs = ctx.mesh("qs")
+        assert np.abs(qs - mf["qs"]).max() <= 1e-6 * np.abs(mf["qs"]).max()
+        ctx.step(2)
+        ref = oracle_full(nacl512, ctx.positions(), 0.30, 9.0, mesh)
+        assert rel_rms(ctx.forces(), ref["F"]) < 1e-4
