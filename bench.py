@@ -567,22 +567,44 @@ def run_sweep(args) -> int:
             eq.equilibrate(args.equilibrate, 1200.0 if system.sr_kind == "bmh" else 298.15)
             system.pos, system.vel = eq.positions(), eq.velocities()
         with P.Context.from_system(system, **kw) as ctx:
+            if args.no_graphs:
+                ctx.set_graphs(False)
             ctx.step(args.warmup)
-            tuning = ctx.autotune(4)
+            if args.tuning:
+                ctx.set_tuning(**json.loads(args.tuning))
+                tuning = dict(ctx.tuning(), source="--tuning")
+            else:
+                tuning = ctx.autotune(4)
             ctx.set_timing(True)
             it0 = ctx.stats()["total_iters"]
             ms = time_context(ctx, torch, stream, args.steps, flush)
             tm = ctx.timing()
             st = ctx.stats()
+            # the one-step diffusion kernel alone: one launch per step, 4
+            # planes per thread, pair branch forked after smoothing so that
+            # nothing runs beside it
+            ctx.set_tuning(diffusion_fuse=1, diffusion_zc=4, pair_fork=0)
+            ctx.set_timing(True)
+            ctx.step(2)
+            ctx.set_timing(True)
+            time_context(ctx, torch, stream, max(3, args.steps // 2), flush)
+            iso_us = 1e3 * ctx.timing()["ms"]["smooth"] / max(3, args.steps // 2)
         stage_us = {k: 1e3 * v / args.steps for k, v in tm["ms"].items()}
         b = 4 if args.precision == "mixed" else 8
         K = st["smooth_steps"]
-        smooth_gbs = 2.0 * mesh ** 3 * b * K / (stage_us["smooth"] * 1e-6) / 1e9
+        # algorithmic bytes: each smoothing launch reads and writes the mesh once
+        nl = smoothing_launches(K, tuning.get("diffusion_fuse", 1))
+        smooth_gbs = 2.0 * mesh ** 3 * b * nl / (stage_us["smooth"] * 1e-6) / 1e9
         ms_step = sum(ms) / args.steps
         print(json.dumps({
             "workload": name, "n_particles": system.n, "mesh": mesh, "ms_per_step": ms_step,
             "ns_per_day": ns_per_day(ms_step * 1e-3, dt), "mg_iters_per_step": (st["total_iters"] - it0) / args.steps,
-            "stage_us": stage_us, "smooth_steps": K, "smooth_algorithmic_gbs": smooth_gbs,
+            "stage_us": stage_us, "smooth_steps": K, "smooth_launches": nl,
+            "smooth_us_per_launch": stage_us["smooth"] / nl, "smooth_algorithmic_gbs": smooth_gbs,
+            "k_diffuse4_alone": {"us_per_launch": iso_us / K,
+                                 "gbs": 2.0 * mesh ** 3 * b * K / (iso_us * 1e-6) / 1e9,
+                                 "frac_of_measured_hbm": 2.0 * mesh ** 3 * b * K / (iso_us * 1e-6) / 1e9
+                                 / peaks["hbm_gbs"]},
             "smooth_frac_of_measured_hbm": smooth_gbs / peaks["hbm_gbs"], "tuning": tuning,
             "device_bytes": st["device_bytes"], "precision": args.precision,
         }), flush=True)
