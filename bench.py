@@ -236,16 +236,29 @@ def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int, fuse: int 
     return float("nan"), 1
 
 
+def kernel_source_sha(kernel: str) -> str | None:
+    """sha256 prefix of a kernel's own source text (from its name at the
+    start of a line to the end of its body) in the package's CUDA headers."""
+    import hashlib
+    import re
+
+    for f in ("mesh.cuh", "particles.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_31379_b300", "csrc", f)) as fh:
+            src = fh.read()
+        m = re.search(r"^" + re.escape(kernel) + r"\(", src, re.M)
+        if m:
+            return hashlib.sha256(src[m.start():src.index("\n}\n", m.start()) + 3].encode()).hexdigest()[:16]
+    return None
+
+
 def recorded_traffic(kernel: str, workload: str, precision: str):
     """DRAM bytes per launch from the committed ncu record, if it was taken on
-    the current kernel source (profiles/roofline_traffic.json)."""
-    import hashlib
+    the kernel's current source (profiles/roofline_traffic.json)."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)[f"{kernel}|{workload}|{precision}"]
-        with open(os.path.join(ROOT, "paper_2606_31379_b300", "csrc", "mesh.cuh"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
-        return float(rec["dram_bytes_per_launch"]) if sha == rec["mesh_cuh_sha256_16"] else None
+        ok = kernel_source_sha(kernel) == rec["kernel_source_sha256_16"]
+        return float(rec["dram_bytes_per_launch"]) if ok else None
     except Exception:
         return None
 
@@ -435,6 +448,16 @@ def run_ours(args) -> int:
            "h2d_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes),
            "d2h_bytes_per_step": int(pos_h.nbytes + vel_h.nbytes), "steps": e2e_steps}
     K_smooth = ctx.stats()["smooth_steps"]
+    # the one-step diffusion kernel alone, live in real MD steps: one launch
+    # per diffusion step and nothing beside it (pair branch forked after
+    # smoothing); CUDA events around the smoothing stage on the work stream
+    ctx.set_tuning(diffusion_fuse=1, diffusion_zc=2, pair_fork=0)
+    ctx.set_timing(True)
+    ctx.step(2)
+    ctx.set_timing(True)
+    n_alone = max(5, args.steps // 2)
+    time_context(ctx, torch, stream, n_alone, flush)
+    alone_launch_us = 1e3 * ctx.timing()["ms"]["smooth"] / n_alone / K_smooth
     ctx.close()
 
     # beside the headline: the plain FP64 path, the multiplier predictors and
@@ -512,6 +535,15 @@ def run_ours(args) -> int:
         "gpu_launches_per_step": launches / args.steps,
         "ms_per_step_with_stage_events": sum(ms_staged) / args.steps,
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
+        "roofline_alone": {
+            "kernel": "k_diffuse4 (one diffusion step per launch, 2 planes per thread, nothing beside it)",
+            "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+            "achieved": 2.0 * P3 * b / (alone_launch_us * 1e-6) / 1e9,
+            "frac": 2.0 * P3 * b / (alone_launch_us * 1e-6) / 1e9 / peaks["hbm_gbs"],
+            "launch_us": alone_launch_us, "algorithmic_bytes_per_launch": 2.0 * P3 * b,
+            "traffic": recorded_traffic("k_diffuse4", WORKLOAD, args.precision),
+            "note": "the two 8 MB FP32 meshes stay in L2 at 128^3; the HBM-bound sizes are in "
+                    "bench.py --sweep (k_diffuse4_alone)"},
     }
     if not args.no_serve:
         line["served"] = served_run(stream.cuda_stream, n_req=48, steps=200, slots=16)
