@@ -546,7 +546,7 @@ def run_ours(args) -> int:
                     "bench.py --sweep (k_diffuse4_alone)"},
     }
     if not args.no_serve:
-        line["served"] = served_run(stream.cuda_stream, n_req=48, steps=200, slots=16)
+        line["served"] = served_run(stream.cuda_stream, n_req=256, steps=200, slots=16)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system, prm)
     print(json.dumps(line))
@@ -554,9 +554,10 @@ def run_ours(args) -> int:
 
 
 def served_run(stream, n_req: int, steps: int, slots: int, rate: float = 200.0) -> dict:
-    """The served-batch workload at reduced count: Poisson arrivals, molten
-    NaCl or SPC/Fw (50/50), 216-32768 atoms log-uniform, mesh ~0.8 A, each
-    advanced `steps` steps, admitted by device memory into `slots` slots."""
+    """The served-batch workload: n_req requests with Poisson arrivals,
+    molten NaCl or SPC/Fw (50/50), 216-32768 atoms log-uniform, mesh ~0.8 A,
+    each advanced `steps` steps, admitted by device memory into `slots`
+    slots."""
     from paper_2606_31379_b300.serve import GpuBackend, Server, poisson_requests
     reqs = poisson_requests(n_req, rate=rate, seed=4, steps=steps)
     be = GpuBackend(precision="mixed", stream=stream)

@@ -366,8 +366,8 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
  * diffusion steps fused per launch, and where the short-range pair kernel
  * is forked onto its low-priority stream (after smoothing, or right after
  * the cell list so that it also overlaps assignment and smoothing) with its
- * grid (one block per home box, or a persistent grid of one or two blocks
- * per SM), and the size of the exactly solved coarse level (coarse_max 16,
+ * grid (one block per home box, or a persistent grid of one block per two
+ * SMs, one or two blocks per SM), and the size of the exactly solved coarse level (coarse_max 16,
  * 32 or 64).  None
  * of them changes the
  * converged field beyond tol (they change iteration counts and speed only).

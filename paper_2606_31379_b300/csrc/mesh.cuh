@@ -771,6 +771,35 @@ k_rbgs(int n, T* __restrict__ e, const T* __restrict__ b, int color, int first) 
     }
 }
 
+// The first red-black sweep from e = 0 in one launch: red points get -b/6,
+// black points (nb6 of the red values - b)/6, with the red values formed
+// from b on the fly in the same float operations and order as k_rbgs (each
+// product rounded on its own, as the stored values are), so the result
+// equals the two half sweeps bit for bit.
+template <typename T>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_rbgs_first(int n, T* __restrict__ e, const T* __restrict__ b) {
+    int x, y, z;
+    if (!xyz3(n, x, y, z)) return;
+    const int i = (z * n + y) * n + x;
+    const T sixth = (T)(1.0 / 6.0);
+    if (((x + y + z) & 1) == 0) {
+        e[i] = -b[i] * sixth;
+        return;
+    }
+    const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? n - 1 : z - 1, zp = z == n - 1 ? 0 : z + 1;
+    const int row = (z * n + y) * n;
+    auto red = [&](int j) {
+        if constexpr (sizeof(T) == 4) return __fmul_rn(-b[j], sixth);
+        else return __dmul_rn(-b[j], sixth);
+    };
+    const T s6 = red(row + xm) + red(row + xp) + red((z * n + ym) * n + x) + red((z * n + yp) * n + x) +
+                 red((zm * n + y) * n + x) + red((zp * n + y) * n + x);
+    e[i] = (s6 - b[i]) * sixth;
+}
+
 // Residual and full-weighting restriction fused: b_c[I] = 4 sum_d w(d)
 // (b_f - M e_f)[2I + d], w = prod of (1/4, 1/2, 1/4); the factor 4 is the
 // rediscretisation of the dimensionless M on a mesh of twice the spacing.

@@ -249,20 +249,38 @@ int leave(p3maze_ctx* ctx) {
 
 
 // ------------------------------------------------------------------ pipeline
+// Systems of at most 2048 particles (two per thread) build the cell list in
+// one block with shared-memory counts; larger ones use the multi-kernel path
+// (one SM walking 32768 particles takes about 90 us, three times longer).
+constexpr int kCellBlockMaxCells = 12288, kCellBlockMaxParticles = 2048;
+inline bool cells_in_one_block(int np, int ncell) {
+    return ncell <= kCellBlockMaxCells && np <= kCellBlockMaxParticles;
+}
+inline size_t cells_block_smem(int ncell) { return 2 * sizeof(int) * (size_t)ncell; }
+
 int build_cells(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_CELLS);
-    CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * ctx->ncell, s));
-    k_cell_count<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->cell, ctx->count);
-    k_scan_cells<<<1, 1024, 0, s>>>(ctx->ncell, ctx->count, ctx->start, ctx->fill);
-    k_cell_scatter<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->cell, ctx->start, ctx->fill, ctx->order);
-    k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
+    int launches = 1;
+    if (cells_in_one_block(ctx->np, ctx->ncell)) {
+        k_cells_block<<<1, kCellBlockThreads, cells_block_smem(ctx->ncell), s>>>(
+            ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->ncell, ctx->cell, ctx->start, ctx->order);
+        launches += 1;
+    } else {
+        CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * ctx->ncell, s));
+        k_cell_count<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->cell,
+                                                          ctx->count);
+        k_scan_cells<<<1, 1024, 0, s>>>(ctx->ncell, ctx->count, ctx->start, ctx->fill);
+        k_cell_scatter<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->cell, ctx->start, ctx->fill, ctx->order);
+        k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
+        launches += 4;
+    }
     k_gather_sorted<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->order, ctx->r, ctx->Q, ctx->type, ctx->mol,
                                                          ctx->cell, ctx->nc, ctx->lcell, ctx->xq, ctx->xl64,
                                                          ctx->xl32, ctx->ts, ctx->ms, ctx->cs, ctx->mp, ctx->N,
                                                          ctx->inv_h);
     CKL();
-    count(ctx, P3MAZE_ST_CELLS, 5);
+    count(ctx, P3MAZE_ST_CELLS, launches);
     stage_end(ctx, P3MAZE_ST_CELLS);
     return P3MAZE_OK;
 }
@@ -447,11 +465,15 @@ int vcycle(p3maze_ctx* ctx, int l) {
     Level& C = ctx->lev[l + 1];
     if (ctx->nu1 == 0) CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
     for (int it = 0; it < ctx->nu1; ++it) {
-        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 0, it == 0 ? 1 : 0);
-        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 1, 0);
+        if (it == 0) {
+            k_rbgs_first<T><<<g3(L.n), kB3, 0, s>>>(L.n, e, b);  // both colours from e = 0
+        } else {
+            k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 0, 0);
+            k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 1, 0);
+        }
     }
     k_resid_restrict<T><<<g3(C.n), kB3, 0, s>>>(C.n, e, b, (T*)C.b);
-    count(ctx, P3MAZE_ST_SOLVE, 2 * ctx->nu1 + 1);
+    count(ctx, P3MAZE_ST_SOLVE, (ctx->nu1 > 0 ? 2 * ctx->nu1 - 1 : 0) + 1);
     CKL();
     int rc = vcycle<T>(ctx, l + 1);
     if (rc) return rc;
@@ -1070,8 +1092,12 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
             raise((const void*)k_coarse_xy<double>);
             raise((const void*)k_coarse_z<double>);
         }
+        if (cells_in_one_block(ctx->np, ctx->ncell)) {
+            sm = cells_block_smem(ctx->ncell);
+            raise((const void*)k_cells_block);
+        }
         if (ea != cudaSuccess)
-            return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory for the coarse solve: ") + cudaGetErrorString(ea));
+            return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory limits: ") + cudaGetErrorString(ea));
     }
     ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(ctx->N, 1)), tb_blocks(ctx->N, 1)));
     ALLOC(ctx->dscal, 8 * S_NSCAL);
@@ -1889,7 +1915,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
         // box, or a persistent grid of one or two blocks per SM that leaves
         // room for the mesh kernels running beside it
         const Setting base = chosen;
-        const int grids[3] = {0, ctx->nsm, 2 * ctx->nsm};
+        const int grids[4] = {0, ctx->nsm / 2, ctx->nsm, 2 * ctx->nsm};
         for (int pf = 0; pf < 2 && !rc; ++pf)
             for (int gb : grids) {
                 if (pf == base.pair_fork && gb == base.pblocks) continue;

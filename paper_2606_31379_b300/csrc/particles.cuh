@@ -143,6 +143,85 @@ static __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __
     }
 }
 
+// The whole cell list of a small system in one block (kCellBlockThreads
+// threads, shared memory 2 ncell ints): cell index and counts (shared-memory
+// atomics), exclusive scan, scatter, and the in-cell sort by particle index.
+// The outputs (cell, start, order) are identical to those of k_cell_count,
+// k_scan_cells, k_cell_scatter and k_cell_sort, in one launch instead of
+// five; one SM walks the particles, so it pays only for small systems.
+constexpr int kCellBlockThreads = 1024;
+
+static __global__ void __launch_bounds__(kCellBlockThreads)
+k_cells_block(int n, const double* __restrict__ r, double inv_cell, int nc, int ncell, int* __restrict__ cell,
+              int* __restrict__ start, int* __restrict__ order) {
+    extern __shared__ int cell_smem[];
+    int* cnt = cell_smem;            // counts, then fill counters
+    int* st = cell_smem + ncell;     // exclusive prefix
+    __shared__ int wsum[kCellBlockThreads / 32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int c = tid; c < ncell; c += nt) cnt[c] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+        const int cx = min(max((int)floor(r[3 * i + 0] * inv_cell), 0), nc - 1);
+        const int cy = min(max((int)floor(r[3 * i + 1] * inv_cell), 0), nc - 1);
+        const int cz = min(max((int)floor(r[3 * i + 2] * inv_cell), 0), nc - 1);
+        const int c = (cz * nc + cy) * nc + cx;
+        cell[i] = c;
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    // exclusive scan: each thread sums a contiguous chunk, the chunk sums are
+    // scanned across the block, then each chunk is written out
+    const int chunk = (ncell + nt - 1) / nt;
+    const int beg = min(tid * chunk, ncell), end = min(beg + chunk, ncell);
+    int local = 0;
+    for (int c = beg; c < end; ++c) local += cnt[c];
+    const int lane = tid & 31, wid = tid >> 5;
+    int v = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = nt >> 5;
+        int w = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    int run = v - local + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int c = beg; c < end; ++c) {
+        st[c] = run;
+        start[c] = run;
+        run += cnt[c];
+        cnt[c] = 0;
+    }
+    if (tid == 0) start[ncell] = n;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+        const int c = cell[i];
+        order[st[c] + atomicAdd(&cnt[c], 1)] = i;
+    }
+    __syncthreads();
+    for (int c = tid; c < ncell; c += nt) {
+        const int b = st[c], e = b + cnt[c];
+        for (int j = b + 1; j < e; ++j) {
+            const int key = order[j];
+            int k = j - 1;
+            while (k >= b && order[k] > key) {
+                order[k + 1] = order[k];
+                --k;
+            }
+            order[k + 1] = key;
+        }
+    }
+}
+
 // Gather particle data into cell order: xq = (x, y, z, Q), the cell-local
 // coordinates x - c l (FP64 and FP32 copies) used by the pair kernel, and
 // (if mp is given) the mesh coordinates of the FP32 assignment and

@@ -451,3 +451,21 @@ def test_nve_total_energy_is_conserved(P, nacl512, precision):
         E, K = np.array(E), np.array(K)
         assert np.std(E) < 0.05 * np.std(K)
         assert abs(E[-1] - E[0]) < 0.10 * np.std(K)
+
+
+@pytest.mark.parametrize("n, box, mesh", [(2000, 39.7, 48), (32768, 100.9, 128)])
+def test_cell_list_both_builders_match_oracle(P, n, box, mesh):
+    """The cell list is bit-exact with the oracle's whichever way it is
+    built: in one block with shared-memory counts (2000 ions) or by the
+    multi-kernel count / scan / scatter / sort (32768 ions, above the
+    one-block limit of 2048)."""
+    s = S.nacl_melt(n, box, seed=11)
+    with P.Context.from_system(s, alpha=0.30, r_cut=9.0, mesh=mesh, tol=1e-6, dt=1.0, precision="mixed") as ctx:
+        ctx.step(2)
+        pos = ctx.positions()
+        nc, cell, start, order = ctx.cells()
+        onc, ocell, ostart, oorder = O.cell_list(pos, box, 9.0)
+        assert nc == onc
+        np.testing.assert_array_equal(cell, ocell)
+        np.testing.assert_array_equal(start, ostart)
+        np.testing.assert_array_equal(order, oorder)
