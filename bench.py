@@ -274,9 +274,13 @@ def measured_peaks() -> dict:
 
 # ----------------------------------------------------------------- CPU oracle
 def oracle_step_seconds(system, prm, n_sample: int) -> tuple[float, str]:
-    """One oracle force evaluation (full mesh part + short-range part of
-    n_sample particles scaled to all) on one host core; returns the estimated
-    seconds of a full step and a description of the sample."""
+    """One step of the oracle's plain FP64 Mass-Zero stepper on one host core:
+    assignment, smoothing, the Verlet-predicted field and its multigrid
+    correction to tol (red-black Gauss-Seidel 2+2, exact coarse level at
+    <= 64^3), interpolation, and the short-range forces of n_sample particles
+    scaled to all.  The field history is the exact field at the positions one
+    time step earlier (set up untimed).  Returns the estimated seconds of a
+    full step and a description of the sample."""
     try:
         from threadpoolctl import threadpool_limits
     except ImportError:          # numpy's FFT and array ops run on one thread anyway
@@ -284,21 +288,37 @@ def oracle_step_seconds(system, prm, n_sample: int) -> tuple[float, str]:
 
         def threadpool_limits(_n):
             return contextlib.nullcontext()
+    import copy
+
     from oracle import p3maze_oracle as O
 
     rng = np.random.default_rng(0)
     sample = rng.choice(system.n, n_sample, replace=False)
+    n, box = prm["mesh"], system.box
+    h = box / n
+    prev = copy.copy(system)
+    prev.pos = O.wrap(system.pos - prm["dt"] * system.vel, box)
+    phi_k = O.mesh_fields(prev, prm["alpha"], n)["phi"]           # history: phi^k = phi^{k-1}
+    levels = O.mg_levels(n, 64)
     with threadpool_limits(1):
         t0 = time.perf_counter()
-        mf = O.mesh_fields(system, prm["alpha"], prm["mesh"])
-        O.interpolate_lr_forces(system.pos, system.charge, system.box, prm["mesh"], mf["phi"])
+        sig = O.sigma_of_alpha(prm["alpha"])
+        K, c = O.smoothing_schedule(sig, h)
+        q = O.assign_charges(system.pos, system.charge, box, n)
+        qs = O.smooth(q, K, c)
+        qs -= qs.mean()
+        phi_p = 2.0 * phi_k - phi_k
+        sigma_p = h / (4.0 * np.pi) * O.laplacian7(phi_p) + qs
+        y, iters, _ = O.mg_correction_solve(sigma_p, np.zeros_like(sigma_p), prm["tol"], levels)
+        phi = phi_p - (4.0 * np.pi / h) * y
+        O.interpolate_lr_forces(system.pos, system.charge, box, n, phi)
         t1 = time.perf_counter()
-        O.sr_forces(system, mf["sigma"], prm["r_cut"], subset=sample)
+        O.sr_forces(system, sig, prm["r_cut"], subset=sample)
         t2 = time.perf_counter()
     est = (t1 - t0) + (t2 - t1) * system.n / n_sample
-    desc = (f"full mesh pipeline on {prm['mesh']}^3 (assignment, {mf['K']} smoothing steps, FFT solve, "
-            f"interpolation) + short-range forces of {n_sample} of {system.n} ions scaled by "
-            f"{system.n / n_sample:g}; 1 thread")
+    desc = (f"one Mass-Zero step on {n}^3 (assignment, {K} smoothing steps, prediction, {iters} multigrid "
+            f"V-cycle(s) to tol {prm['tol']:g}, interpolation) + short-range forces of {n_sample} of "
+            f"{system.n} ions scaled by {system.n / n_sample:g}; 1 thread")
     return est, desc
 
 

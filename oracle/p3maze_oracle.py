@@ -162,6 +162,113 @@ def solve_constraint_fft(qs: np.ndarray, h: float) -> np.ndarray:
     return np.fft.ifftn(phihat).real
 
 
+# ---------------------------------------------------------------- multigrid
+# The correction solve of Eq. 20 as the paper's method runs it: a multigrid
+# V-cycle iteration on M y = sigma_p until max|sigma_p - M y| <= tol.  The
+# paper does not give the smoother, transfer operators, depth or coarse solve
+# (Sec. 3.3 footnote); this follows the reading taken for the GPU path:
+# rediscretised dimensionless M on every level, red-black Gauss-Seidel (red =
+# points with x + y + z even), full-weighting restriction scaled by 4 (the
+# spacing doubles), trilinear prolongation, and the exact pseudo-inverse on
+# the coarse level.  Levels are n, n/2, ... halved while even and larger than
+# 16; the first of size <= coarse_max (else the deepest) is the coarse level.
+
+def mg_levels(n: int, coarse_max: int) -> list[int]:
+    levels = [n]
+    while levels[-1] > 16 and levels[-1] % 2 == 0:
+        levels.append(levels[-1] // 2)
+    for i, m in enumerate(levels):
+        if m <= coarse_max:
+            return levels[: i + 1]
+    return levels
+
+
+def _red_mask(n: int) -> np.ndarray:
+    i = np.arange(n)
+    return ((i[:, None, None] + i[None, :, None] + i[None, None, :]) % 2) == 0
+
+
+def gauss_seidel_half(e: np.ndarray, b: np.ndarray, mask: np.ndarray) -> np.ndarray:
+    """One red-black Gauss-Seidel half sweep on M e = b: every point of one
+    colour takes e = (sum of its six neighbours - b)/6; its neighbours all
+    have the other colour, so updating them together is Gauss-Seidel."""
+    nb = laplacian7(e) + 6.0 * e
+    return np.where(mask, (nb - b) / 6.0, e)
+
+
+def restrict_full_weighting(r: np.ndarray) -> np.ndarray:
+    """Coarse right-hand side 4 R r: R weights the fine points around 2I by the
+    tensor product of (1/4, 1/2, 1/4); the 4 rescales the dimensionless M to
+    the doubled spacing."""
+    out = r
+    for ax in range(3):
+        out = 0.25 * np.roll(out, 1, axis=ax) + 0.5 * out + 0.25 * np.roll(out, -1, axis=ax)
+    return 4.0 * out[::2, ::2, ::2]
+
+
+def prolong_trilinear(ec: np.ndarray) -> np.ndarray:
+    """Trilinear interpolation from the coarse points (fine 2I) to the fine mesh."""
+    out = ec
+    for ax in range(3):
+        shape = list(out.shape)
+        shape[ax] *= 2
+        f = np.zeros(shape)
+        even = [slice(None)] * 3
+        odd = [slice(None)] * 3
+        even[ax] = slice(0, None, 2)
+        odd[ax] = slice(1, None, 2)
+        f[tuple(even)] = out
+        f[tuple(odd)] = 0.5 * (out + np.roll(out, -1, axis=ax))
+        out = f
+    return out
+
+
+def pseudo_inverse_solve(b: np.ndarray) -> np.ndarray:
+    """e = M^+ b (the zero-mean solution; the mean of b is dropped), by FFT."""
+    lam = laplacian_eigenvalues(b.shape[0])
+    bh = np.fft.fftn(b)
+    eh = np.zeros_like(bh)
+    nz = lam != 0.0
+    eh[nz] = bh[nz] / lam[nz]
+    return np.fft.ifftn(eh).real
+
+
+def v_cycle(b: np.ndarray, levels: list[int], nu1: int = 2, nu2: int = 2, level: int = 0) -> np.ndarray:
+    """One V-cycle from e = 0 on M e = b: nu1 sweeps (red then black), the
+    coarse correction, nu2 sweeps (black then red)."""
+    if level == len(levels) - 1:
+        return pseudo_inverse_solve(b)
+    red = _red_mask(b.shape[0])
+    black = ~red
+    e = np.zeros_like(b)
+    for _ in range(nu1):
+        e = gauss_seidel_half(e, b, red)
+        e = gauss_seidel_half(e, b, black)
+    bc = restrict_full_weighting(b - laplacian7(e))
+    e = e + prolong_trilinear(v_cycle(bc, levels, nu1, nu2, level + 1))
+    for _ in range(nu2):
+        e = gauss_seidel_half(e, b, black)
+        e = gauss_seidel_half(e, b, red)
+    return e
+
+
+def mg_correction_solve(sigma: np.ndarray, y0: np.ndarray, tol: float, levels: list[int], nu1: int = 2,
+                        nu2: int = 2, itmax: int = 50):
+    """Eq. 20's correction solve: V-cycles on M e = sigma - M y, y += e, until
+    max|sigma - M y| <= tol.  Returns y, the V-cycles run and the residual
+    max-norm before and after each of them."""
+    y = np.array(y0, dtype=np.float64, copy=True)
+    r = sigma - laplacian7(y)
+    hist = [float(np.abs(r).max())]
+    it = 0
+    while hist[-1] > tol and it < itmax:
+        y = y + v_cycle(r, levels, nu1, nu2)
+        r = sigma - laplacian7(y)
+        hist.append(float(np.abs(r).max()))
+        it += 1
+    return y, it, hist
+
+
 def mesh_gradient(phi: np.ndarray, h: float) -> list[np.ndarray]:
     """Central finite-difference gradient D phi (Eq. 21's D_x, D_y, D_z)."""
     return [(np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)) / (2.0 * h) for ax in range(3)]

@@ -469,3 +469,24 @@ def test_cell_list_both_builders_match_oracle(P, n, box, mesh):
         np.testing.assert_array_equal(cell, ocell)
         np.testing.assert_array_equal(start, ostart)
         np.testing.assert_array_equal(order, oorder)
+
+
+@pytest.mark.parametrize("mesh", [32, 64])
+def test_multigrid_matches_the_oracle_iteration(P, nacl512, mesh):
+    """The FP64 GPU correction solve runs the same iteration as the oracle's
+    plain multigrid (red-black Gauss-Seidel 2+2, full weighting x4,
+    trilinear, exact coarse level at 16^3): the initial solve from phi = 0
+    needs the same number of V-cycles at each tolerance and stops at the
+    same residual (the GPU takes the max-norm on FP32-rounded values: 1e-6)."""
+    s = nacl512
+    pos = O.wrap(s.pos, s.box)
+    mf = O.mesh_fields(at_positions(s, pos), 0.30, mesh)
+    sigma = mf["qs"] - mf["qs"].mean()
+    levels = O.mg_levels(mesh, 16)
+    for tol in (1e-4, 1e-6, 1e-8, 1e-10):
+        _, it, hist = O.mg_correction_solve(sigma, np.zeros_like(sigma), tol, levels)
+        with _ctx(P, s, precision="fp64", tol=tol, mesh=mesh, coarse_max=16) as ctx:
+            st = ctx.stats()
+            assert st["mg_levels"] == len(levels) and st["coarse_n"] == levels[-1]
+            assert st["init_iters"] == it, (tol, st["init_iters"], it, hist)
+            assert st["last_residual"] == pytest.approx(hist[-1], rel=1e-6)
