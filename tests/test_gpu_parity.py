@@ -477,7 +477,9 @@ def test_multigrid_matches_the_oracle_iteration(P, nacl512, mesh):
     plain multigrid (red-black Gauss-Seidel 2+2, full weighting x4,
     trilinear, exact coarse level at 16^3): the initial solve from phi = 0
     needs the same number of V-cycles at each tolerance and stops at the
-    same residual (the GPU takes the max-norm on FP32-rounded values: 1e-6)."""
+    same residual: with phi_p = 0, phi = -(4pi/h) y and the residual
+    sigma - M y is (h/4pi) M phi + q^s, evaluated with the oracle's stencil
+    (agreement to 1e-4 relative; a different iteration changes it by O(1))."""
     s = nacl512
     pos = O.wrap(s.pos, s.box)
     mf = O.mesh_fields(at_positions(s, pos), 0.30, mesh)
@@ -489,4 +491,5 @@ def test_multigrid_matches_the_oracle_iteration(P, nacl512, mesh):
             st = ctx.stats()
             assert st["mg_levels"] == len(levels) and st["coarse_n"] == levels[-1]
             assert st["init_iters"] == it, (tol, st["init_iters"], it, hist)
-            assert st["last_residual"] == pytest.approx(hist[-1], rel=1e-6)
+            res = constraint_residual(ctx.mesh("phi"), sigma, mf["h"])
+            assert res == pytest.approx(hist[-1], rel=1e-4), (tol, res, hist[-1])
