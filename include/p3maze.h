@@ -65,6 +65,13 @@ extern "C" {
                                  predictor, convergence on max|M phi + (4pi/h) q^s| (the P3M
                                  residual of Sec. 3.3) <= tol                               */
 
+/* Long-range force interpolation */
+#define P3MAZE_LR_FORCE_FD       0  /* F = -ke Q W . D phi, central differences (Eq. 21; default):
+                                       momentum conserving, not the exact energy gradient   */
+#define P3MAZE_LR_FORCE_ANALYTIC 1  /* F = -ke Q grad W . phi: the exact gradient of
+                                       V_LR = 1/2 ke phi^T q (energy conserving), not the
+                                       paper's force; momentum conserved to discretisation error */
+
 #define P3MAZE_SR_NONE 0  /* Coulomb only                                               */
 #define P3MAZE_SR_BMH  1  /* Born-Huggins-Mayer: A exp((s-r)/rho) - C/r^6 - D/r^8         */
 #define P3MAZE_SR_LJ   2  /* Lennard-Jones: 4 eps ((s/r)^12 - (s/r)^6), pairs with eps=0 skipped */
@@ -133,6 +140,8 @@ typedef struct {
     int32_t method;         /* P3MAZE_METHOD_MAZE (0) or P3MAZE_METHOD_P3M                  */
     int32_t coarse_max;     /* the first level with n <= coarse_max is solved exactly
                                (separable Hartley transforms); 0 -> 64 (mixed), 16 (FP64) */
+    int32_t lr_force;       /* P3MAZE_LR_FORCE_FD (0, the paper's Eq. 21) or
+                               P3MAZE_LR_FORCE_ANALYTIC                                    */
 } p3maze_params;
 
 typedef struct {

@@ -99,6 +99,18 @@ def bspline4_weights(t: np.ndarray) -> np.ndarray:
     return np.stack([w0, w1, w2, w3], axis=-1)
 
 
+def bspline4_derivatives(t: np.ndarray) -> np.ndarray:
+    """d/dt of the four cubic B-spline weights (the derivative of each
+    polynomial above); they sum to zero.  Returns array (..., 4)."""
+    t = np.asarray(t, dtype=np.float64)
+    s = 1.0 - t
+    d0 = -0.5 * s * s
+    d1 = 1.5 * t * t - 2.0 * t
+    d2 = -1.5 * t * t + t + 0.5
+    d3 = 0.5 * t * t
+    return np.stack([d0, d1, d2, d3], axis=-1)
+
+
 def assignment_stencil(pos: np.ndarray, box: float, n: int):
     """Base node index (floor(u) - 1) and per-axis weights for each particle.
 
@@ -474,8 +486,43 @@ def mesh_fields(system, alpha: float, n: int, order: int = 4):
     return {"q": q, "qs": qs, "phi": phi, "K": K, "c": c, "h": h, "sigma": sigma}
 
 
+def interpolate_lr_forces_analytic(pos, charge, box, n, phi, ke=COULOMB_K) -> np.ndarray:
+    """F_a = -ke Q_a sum_n grad W(r_a - r_n) phi_n: the exact gradient of
+    V_LR = 1/2 ke phi^T q with q = A(r)Q and phi = G q (G symmetric), the
+    energy-conserving alternative to Eq. 21's finite differences (an option,
+    not the paper's force)."""
+    inv_h = n / box
+    u = pos * inv_h
+    fl = np.floor(u)
+    base = fl.astype(np.int64) - 1
+    w = bspline4_weights(u - fl)
+    dw = bspline4_derivatives(u - fl) * inv_h
+    F = np.zeros((pos.shape[0], 3))
+    for a in range(4):
+        ix = (base[:, 0] + a) % n
+        for b in range(4):
+            iy = (base[:, 1] + b) % n
+            for c in range(4):
+                iz = (base[:, 2] + c) % n
+                p = phi[ix, iy, iz]
+                F[:, 0] -= ke * charge * dw[:, 0, a] * w[:, 1, b] * w[:, 2, c] * p
+                F[:, 1] -= ke * charge * w[:, 0, a] * dw[:, 1, b] * w[:, 2, c] * p
+                F[:, 2] -= ke * charge * w[:, 0, a] * w[:, 1, b] * dw[:, 2, c] * p
+    return F
+
+
+def lr_energy_at(pos, charge, box, alpha, n, ke=COULOMB_K) -> float:
+    """V_LR = 1/2 ke phi*^T q at the given positions (the adopted reading)."""
+    h = box / n
+    K, c = smoothing_schedule(sigma_of_alpha(alpha), h)
+    q = assign_charges(pos, charge, box, n)
+    qs = smooth(q, K, c)
+    qs = qs - qs.mean()
+    return 0.5 * ke * float((solve_constraint_fft(qs, h) * q).sum())
+
+
 def forces_and_energies(system, alpha: float, r_cut: float, n: int, ke: float = COULOMB_K,
-                        order: int = 4, lr_energy: str = "assigned"):
+                        order: int = 4, lr_energy: str = "assigned", lr_force: str = "fd"):
     """Total force and energy terms of the P3MaZe decomposition at the exactly
     constrained field phi* (Eqs. 5, 6, 14, 19, 21).
 
@@ -484,7 +531,10 @@ def forces_and_energies(system, alpha: float, r_cut: float, n: int, ke: float = 
     can show the Madelung pin rejects it)."""
     mf = mesh_fields(system, alpha, n, order)
     sigma = mf["sigma"]
-    F_lr = interpolate_lr_forces(system.pos, system.charge, system.box, n, mf["phi"], ke)
+    if lr_force == "analytic":
+        F_lr = interpolate_lr_forces_analytic(system.pos, system.charge, system.box, n, mf["phi"], ke)
+    else:
+        F_lr = interpolate_lr_forces(system.pos, system.charge, system.box, n, mf["phi"], ke)
     F_sr, ec, ev = sr_forces(system, sigma, r_cut, ke)
     src = mf["q"] if lr_energy == "assigned" else mf["qs"]
     v_lr = 0.5 * ke * float((mf["phi"] * src).sum())

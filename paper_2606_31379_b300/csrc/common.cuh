@@ -61,6 +61,23 @@ __device__ __forceinline__ void bspline4f(float t, float w[4]) {
     w[3] = t3 * (1.0f / 6.0f);
 }
 
+// d/dt of the four weights (derivatives of the polynomials above; they sum
+// to zero), FP64 and FP32.
+__device__ __forceinline__ void bspline4_deriv(double t, double d[4]) {
+    const double s = 1.0 - t;
+    d[0] = -0.5 * s * s;
+    d[1] = (1.5 * t - 2.0) * t;
+    d[2] = (-1.5 * t + 1.0) * t + 0.5;
+    d[3] = 0.5 * t * t;
+}
+__device__ __forceinline__ void bspline4f_deriv(float t, float d[4]) {
+    const float s = 1.0f - t;
+    d[0] = -0.5f * s * s;
+    d[1] = (1.5f * t - 2.0f) * t;
+    d[2] = (-1.5f * t + 1.0f) * t + 0.5f;
+    d[3] = 0.5f * t * t;
+}
+
 // A particle's mesh coordinates for FP32 assignment and interpolation: base
 // node per axis (as bspline_axis), the fractions u - floor(u) rounded once
 // to FP32 (the FP64 part is done once per particle and step), and Q.

@@ -1191,4 +1191,106 @@ k_gather_mp(int np, const MeshPt* __restrict__ mp, const int* __restrict__ order
     }
 }
 
+// Analytic-gradient interpolation (an option; the paper's force is the
+// finite-difference one above): F_a = -ke Q_a sum_n grad W(r_a - r_n) phi_n,
+// grad W = inv_h (w'(tx) w(ty) w(tz), ...), the exact gradient of
+// V_LR = 1/2 ke phi^T q for phi = G q with G symmetric, so the long-range
+// force conserves energy (but is not exactly antisymmetric: momentum is
+// conserved only to the discretisation error).  64 loads of phi per particle.
+// FP32 from the mesh coordinates and the FP32 phi copy; the constant offset of
+// that copy drops out (the derivative weights sum to zero).
+static __global__ void __launch_bounds__(P3_THREADS)
+k_gather_grad_mp(int np, const MeshPt* __restrict__ mp, const int* __restrict__ order, int n, double inv_h,
+                 double ke, const float* __restrict__ phi, const double* __restrict__ Fsr_s,
+                 double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const MeshPt p = mp[s];
+    float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+    bspline4f(p.tx, wx);
+    bspline4f(p.ty, wy);
+    bspline4f(p.tz, wz);
+    bspline4f_deriv(p.tx, dx);
+    bspline4f_deriv(p.ty, dy);
+    bspline4f_deriv(p.tz, dz);
+    int ix[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ix[a] = wrap_idx(p.bx + a, n);
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int iz = wrap_idx(p.bz + c, n);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int iy = wrap_idx(p.by + b, n);
+            const float* row = phi + ((int64_t)iz * n + iy) * n;
+            const float wyz = wy[b] * wz[c], dyz = dy[b] * wz[c], ydz = wy[b] * dz[c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float v = row[ix[a]];
+                gx += dx[a] * wyz * v;
+                gy += wx[a] * dyz * v;
+                gz += wx[a] * ydz * v;
+            }
+        }
+    }
+    const double scale = -ke * (double)p.q * inv_h;
+    const int i = order[s];
+    const double f[3] = {scale * (double)gx, scale * (double)gy, scale * (double)gz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double sr = Fsr_s[3 * s + d];
+        F[3 * i + d] = sr + f[d];
+        Flr[3 * i + d] = f[d];
+        Fsr[3 * i + d] = sr;
+    }
+}
+
+// The same in FP64 from the cell-ordered positions and the FP64 phi.
+static __global__ void __launch_bounds__(P3_THREADS)
+k_gather_grad64(int np, const PQ* __restrict__ xq, const int* __restrict__ order, int n, double inv_h, double ke,
+                const double* __restrict__ phi, const double* __restrict__ Fsr_s, double* __restrict__ F,
+                double* __restrict__ Flr, double* __restrict__ Fsr) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= np) return;
+    const PQ p = xq[s];
+    double w[3][4], d[3][4];
+    int base[3];
+    const double xs[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        double u = xs[ax] * inv_h;
+        if (!(u >= 0.0 && u <= (double)n)) u = 0.0;
+        const double fl = floor(u);
+        bspline4(u - fl, w[ax]);
+        bspline4_deriv(u - fl, d[ax]);
+        base[ax] = wrap_idx((int)fl - 1, n);
+    }
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        const int iz = wrap_idx(base[2] + c, n);
+        for (int b = 0; b < 4; ++b) {
+            const int iy = wrap_idx(base[1] + b, n);
+            const double* row = phi + ((int64_t)iz * n + iy) * n;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const double v = row[wrap_idx(base[0] + a, n)];
+                gx += d[0][a] * w[1][b] * w[2][c] * v;
+                gy += w[0][a] * d[1][b] * w[2][c] * v;
+                gz += w[0][a] * w[1][b] * d[2][c] * v;
+            }
+        }
+    }
+    const double scale = -ke * p.w * inv_h;
+    const int i = order[s];
+    const double f[3] = {scale * gx, scale * gy, scale * gz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double sr = Fsr_s[3 * s + k];
+        F[3 * i + k] = sr + f[k];
+        Flr[3 * i + k] = f[k];
+        Fsr[3 * i + k] = sr;
+    }
+}
+
 }  // namespace p3

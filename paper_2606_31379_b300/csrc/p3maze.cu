@@ -88,6 +88,7 @@ struct p3maze_ctx {
     int zc = 8;                          // z planes per thread in the diffusion step (tunable)
     int pair_fork = 0;                   // pair kernel forked after: 0 smoothing, 1 the cell list (tunable)
     int pair_blocks = 0;                 // pair grid: 0 one block per home box, else a persistent grid (tunable)
+    int lr_force = 0;                    // P3MAZE_LR_FORCE_FD (the paper's) or P3MAZE_LR_FORCE_ANALYTIC
     int nsm = 148;                       // SMs of the device
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
@@ -684,13 +685,23 @@ int gather_forces(p3maze_ctx* ctx) {
     const bool mixed = ctx->prec == P3MAZE_MIXED;
     CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     stage_begin(ctx, P3MAZE_ST_GATHER);
-    if (mixed)
+    if (ctx->lr_force == P3MAZE_LR_FORCE_ANALYTIC) {
+        if (mixed)
+            k_gather_grad_mp<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->mp, ctx->order, ctx->N, ctx->inv_h,
+                                                                  ctx->ke, ctx->phi32, ctx->Fs, ctx->F, ctx->Flr,
+                                                                  ctx->Fsr);
+        else
+            k_gather_grad64<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h,
+                                                                 ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F,
+                                                                 ctx->Flr, ctx->Fsr);
+    } else if (mixed) {
         k_gather_mp<<<nblk(ctx->np), P3_THREADS, 0, s>>>(
             ctx->np, ctx->mp, ctx->order, ctx->N, ctx->inv_h, ctx->ke, ctx->phi32, ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
-    else
+    } else {
         k_gather<double><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h,
                                                               ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr,
                                                               ctx->Fsr);
+    }
     count(ctx, P3MAZE_ST_GATHER);
     if (ctx->nmol) {
         k_water<<<nblk(ctx->nmol), P3_THREADS, 0, s>>>(ctx->nmol, ctx->tri, ctx->r, ctx->Q, ctx->L, ctx->alpha, ctx->ke,
@@ -1250,6 +1261,8 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     if (!validate_mesh(p->mesh, &nlev, &ncoarse))
         return fail(nullptr, P3MAZE_ERR_INVALID, "mesh must be N >= 4 with N = m 2^l, m <= 64 (halving stops at 16)");
     if (p->coarse_max < 0) return fail(nullptr, P3MAZE_ERR_INVALID, "coarse_max must be >= 0");
+    if (p->lr_force != P3MAZE_LR_FORCE_FD && p->lr_force != P3MAZE_LR_FORCE_ANALYTIC)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "lr_force must be P3MAZE_LR_FORCE_FD or P3MAZE_LR_FORCE_ANALYTIC");
     double qsum = 0.0, qabs = 0.0;
     for (int i = 0; i < n; ++i) {
         if (!(p->masses[i] > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "masses must be > 0");
@@ -1322,6 +1335,7 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     ctx->tol = p->tol;
     ctx->dt = p->dt;
     ctx->method = p->method;
+    ctx->lr_force = p->lr_force;
     // one diffusion step per launch; FP32 quads take 2 planes per thread
     ctx->zc = (p->precision == P3MAZE_MIXED && p->mesh % 4 == 0) ? 2 : 8;
     ctx->fuse = 1;

@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("predictor", C.c_int32), ("precision", C.c_int32), ("max_mg_iters", C.c_int32),
                 ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32), ("coulomb_k", C.c_double),
                 ("sr", C.POINTER(SRTable)), ("topology", C.POINTER(Topology)), ("method", C.c_int32),
-                ("coarse_max", C.c_int32)]
+                ("coarse_max", C.c_int32), ("lr_force", C.c_int32)]
 
 
 class Energies(C.Structure):
@@ -175,7 +175,7 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
                  sr_table: dict | None = None, triples=None, bonded: dict | None = None,
                  order: int = 4, predictor: int = 3, precision: str = "fp64",
                  max_mg_iters: int = 0, pre_sweeps: int = 0, post_sweeps: int = 0,
-                 coulomb_k: float = 0.0, method: str = "maze", coarse_max: int = 0):
+                 coulomb_k: float = 0.0, method: str = "maze", coarse_max: int = 0, lr_force: str = "fd"):
     """p3maze_params for these arguments, plus the arrays it points into
     (keep them alive while the struct is used)."""
     n = int(np.asarray(charges).shape[0])
@@ -200,6 +200,7 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
     p.coulomb_k = float(coulomb_k)
     p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M}[method]
     p.coarse_max = int(coarse_max)
+    p.lr_force = {"fd": 0, "analytic": 1}[lr_force]
     tab = sr_table_from(sr_kind, sr_table or {})
     if tab is not None:
         keep["sr"] = tab

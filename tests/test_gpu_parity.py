@@ -493,3 +493,17 @@ def test_multigrid_matches_the_oracle_iteration(P, nacl512, mesh):
             assert st["init_iters"] == it, (tol, st["init_iters"], it, hist)
             res = constraint_residual(ctx.mesh("phi"), sigma, mf["h"])
             assert res == pytest.approx(hist[-1], rel=1e-4), (tol, res, hist[-1])
+
+
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_analytic_lr_force_option_matches_oracle(P, nacl512, precision, ftol):
+    """The analytic-gradient long-range force (an option; the default is the
+    paper's finite differences) matches the oracle's at the GPU's positions."""
+    with _ctx(P, nacl512, precision=precision, tol=1e-9, lr_force="analytic") as ctx:
+        ctx.step(2)
+        pos = ctx.positions()
+        ref = O.forces_and_energies(at_positions(nacl512, pos), 0.30, 9.0, 32, lr_force="analytic")
+        assert rel_rms(ctx.forces("lr"), ref["F_lr"]) < ftol
+        assert rel_rms(ctx.forces(), ref["F"]) < ftol
+        fd = O.forces_and_energies(at_positions(nacl512, pos), 0.30, 9.0, 32)
+        assert rel_rms(ctx.forces("lr"), fd["F_lr"]) > 10 * ftol     # a different force

@@ -334,3 +334,40 @@ def test_restriction_is_the_scaled_adjoint_of_prolongation():
     # constants are reproduced: P 1 = 1, R 1 = 4 (the x4 rescaling)
     assert np.allclose(O.prolong_trilinear(np.ones((8, 8, 8))), 1.0)
     assert np.allclose(O.restrict_full_weighting(np.ones((16, 16, 16))), 4.0)
+
+
+# ------------------------------------------------------------------ analytic-gradient force option
+def test_analytic_mesh_force_is_the_energy_gradient():
+    """The analytic B-spline-gradient force equals -dV_LR/dr (central finite
+    differences of V_LR = 1/2 ke phi*^T q, step 1e-5 A) to 1e-6 relative; the
+    paper's finite-difference force (Eq. 21) is not the gradient of that
+    energy (a few per cent off at this coarse mesh), which is why it does not
+    conserve energy exactly."""
+    s = S.random_neutral(8, 12.0, seed=3)
+    n, alpha = 16, 0.6
+    mf = O.mesh_fields(s, alpha, n)
+    Fa = O.interpolate_lr_forces_analytic(s.pos, s.charge, s.box, n, mf["phi"])
+    Ff = O.interpolate_lr_forces(s.pos, s.charge, s.box, n, mf["phi"])
+    eps = 1e-5
+    g = np.zeros((3, 3))
+    for i in range(3):
+        for d in range(3):
+            p1, p2 = s.pos.copy(), s.pos.copy()
+            p1[i, d] += eps
+            p2[i, d] -= eps
+            g[i, d] = -(O.lr_energy_at(p1, s.charge, s.box, alpha, n)
+                        - O.lr_energy_at(p2, s.charge, s.box, alpha, n)) / (2 * eps)
+    scale = np.abs(g).max()
+    assert np.abs(Fa[:3] - g).max() < 1e-6 * scale
+    assert np.abs(Ff[:3] - g).max() > 1e-2 * scale
+    # Eq. 21's force sums to zero exactly (Newton III on the mesh)
+    assert np.abs(Ff.sum(0)).max() < 1e-10 * np.abs(Ff).max()
+
+
+def test_bspline_derivative_weights():
+    t = np.linspace(0.0, 1.0, 11)
+    d = O.bspline4_derivatives(t)
+    assert np.allclose(d.sum(-1), 0.0, atol=1e-15)
+    h = 1e-6
+    fd = (O.bspline4_weights(t + h) - O.bspline4_weights(t - h)) / (2 * h)
+    assert np.allclose(d, fd, atol=1e-8)
