@@ -419,7 +419,7 @@ def run_ours(args) -> int:
         ctx.set_tuning(**json.loads(args.tuning))
         tuning = dict(ctx.tuning(), source="--tuning")
     else:
-        tuning = None if args.no_tune else ctx.autotune(8)
+        tuning = None if args.no_tune else ctx.autotune(12)
     torch.cuda.synchronize()
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
     it0 = ctx.stats()["total_iters"]
