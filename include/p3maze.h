@@ -377,7 +377,9 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
  * the cell list so that it also overlaps assignment and smoothing) with its
  * grid (one block per home box, or a persistent grid of one block per two
  * SMs, one or two blocks per SM), and the size of the exactly solved coarse level (coarse_max 16,
- * 32 or 64).  None
+ * 32 or 64); the diffusion candidates are timed again once the pair
+ * branch's placement changed, since the fastest kernel depends on what runs
+ * beside it.  None
  * of them changes the
  * converged field beyond tol (they change iteration counts and speed only).
  * Every trial runs 2 warm-up steps (graph capture) and steps_per_trial timed

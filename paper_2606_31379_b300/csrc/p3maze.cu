@@ -1879,17 +1879,18 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
             }
         }
     }
-    if (!rc) {
-        // diffusion kernel: steps per launch (mixed: 1 or 4) x z planes per
-        // thread (one step per launch, N % 4 == 0: 1-8) or per block
+    // diffusion kernel: steps per launch (mixed: 1, 2 or 4) x z planes per
+    // thread (one or two steps per launch, N % 4 == 0: 1-8) or per block
+    auto diffusion_pass = [&]() {
         const int fuses[3] = {1, 2, 4};
         const int zcs_quad[4] = {1, 2, 4, 8}, zcs_other[4] = {4, 8, 16, 32};
+        const Setting base = chosen;
         for (int f : fuses) {
             if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
             if (f == 2 && ctx->N % 4 != 0) continue;
             const bool quad = f <= 2 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
             for (int z : quad ? zcs_quad : zcs_other) {
-                if (z == chosen.zc && f == chosen.fuse) continue;
+                if (z == base.zc && f == base.fuse) continue;
                 Setting c = chosen;
                 c.zc = z;
                 c.fuse = f;
@@ -1897,15 +1898,15 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
                 rc = tune_trial(ctx, c, warm, steps_per_trial, &ms);
                 trials += 1;
                 steps += warm + steps_per_trial;
-                if (rc) break;
+                if (rc) return;
                 if (ms < best) {
                     best = ms;
                     chosen = c;
                 }
             }
-            if (rc) break;
         }
-    }
+    };
+    if (!rc) diffusion_pass();
     if (!rc) {
         // size of the exactly solved coarse level (distinct levels only)
         const int cms[3] = {16, 32, 64};
@@ -1947,6 +1948,9 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
                 }
             }
     }
+    // the diffusion kernel again once the pair branch is placed: which kernel
+    // is fastest depends on what runs beside it
+    if (!rc && (chosen.pair_fork != start.pair_fork || chosen.pblocks != start.pblocks)) diffusion_pass();
     // keep the fastest setting
     if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = chosen.pred;
     ctx->nu1 = chosen.nu1;
