@@ -656,20 +656,28 @@ int pair_forces(p3maze_ctx* ctx) {
     const int nbox = (ctx->nc + 1) / 2;
     const unsigned nboxes = (unsigned)nbox * nbox * nbox;
     const unsigned pb = ctx->pair_blocks > 0 ? std::min(nboxes, (unsigned)ctx->pair_blocks) : nboxes;
-#define PAIR(KIND)                                                                                      \
+#define PAIR(KIND, MOL)                                                                                 \
     do {                                                                                                \
         if (mixed)                                                                                      \
-            k_pair<KIND, float, 768><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts, ctx->ms,    \
-                ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,      \
-                ctx->Fs, ctx->ecs, ctx->evs);                                                           \
+            k_pair<KIND, float, 768, MOL><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts,        \
+                ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke,       \
+                ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
         else                                                                                            \
-            k_pair<KIND, double, 512><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts, ctx->ms,   \
-                ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke, ctx->tab,      \
-                ctx->Fs, ctx->ecs, ctx->evs);                                                           \
+            k_pair<KIND, double, 512, MOL><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts,       \
+                ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke,       \
+                ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
     } while (0)
-    if (ctx->tab.kind == 1) PAIR(1);
-    else if (ctx->tab.kind == 2) PAIR(2);
-    else PAIR(0);
+    const bool mol = ctx->nmol > 0;
+    if (ctx->tab.kind == 1) {
+        if (mol) PAIR(1, true);
+        else PAIR(1, false);
+    } else if (ctx->tab.kind == 2) {
+        if (mol) PAIR(2, true);
+        else PAIR(2, false);
+    } else {
+        if (mol) PAIR(0, true);
+        else PAIR(0, false);
+    }
 #undef PAIR
     count(ctx, P3MAZE_ST_PAIR);
     stage_end(ctx, P3MAZE_ST_PAIR);

@@ -353,7 +353,8 @@ __device__ __forceinline__ void pair_accumulate(const V& pi, const V& pj, R alph
     ev += e_v;
 }
 
-template <int KIND, typename R, int CAP>
+// MOL: the system has molecules, so intramolecular pairs are tested for.
+template <int KIND, typename R, int CAP, bool MOL>
 __global__ void __launch_bounds__(P3_THREADS)
 k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restrict__ ts,
        const int* __restrict__ ms, const int* __restrict__ start, int nc, int nbox, double lcell, double rc2,
@@ -363,9 +364,8 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
     constexpr int HCAP = 256;
     constexpr int NW = P3_THREADS / 32;
     __shared__ V sp[CAP];
-    __shared__ int sidx[CAP], styp[CAP], smol[CAP];
+    __shared__ int styp[CAP], smol[MOL ? CAP : 1];
     __shared__ int rstart[216], roff[217];
-    __shared__ signed char rsh[216];          // 1 if the region cell is a shifted image
     __shared__ V hpos[HCAP];
     __shared__ unsigned hidx[HCAP];           // sorted index | home-cell offset bits 29..31
     __shared__ R hacc[HCAP][5];               // per home particle: force, Coulomb and non-Coulomb energy
@@ -411,17 +411,14 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
             const int rx = tid % wx, ry = (tid / wx) % wy, rz = tid / (wx * wy);
             int u[3] = {h0[0] - 2 + rx, h0[1] - 2 + ry, h0[2] - 2 + rz};
             int c3[3];
-            bool shifted = false;
             for (int d = 0; d < 3; ++d) {
                 int c = u[d] % nc;
                 if (c < 0) c += nc;
                 c3[d] = c;
-                shifted |= (c != u[d]);
             }
             const int c = (c3[2] * nc + c3[1]) * nc + c3[0];
             rstart[tid] = start[c];
             roff[tid + 1] = start[c + 1] - start[c];
-            rsh[tid] = shifted ? 1 : 0;
         }
         __syncthreads();
         if (tid == 0) {
@@ -487,9 +484,8 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                     q.y = (R)p.y + (R)(ry - 2) * lc;
                     q.z = (R)p.z + (R)(rz - 2) * lc;
                     sp[k] = q;
-                    sidx[k] = rsh[r] ? -1 : t;
                     styp[k] = ts[t];
-                    smol[k] = ms[t];
+                    if (MOL) smol[k] = ms[t];
                 }
                 __syncthreads();
                 for (int h = warp; h < nh; h += NW) {
@@ -563,14 +559,16 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                                 }
                                 k = wbeg[warp][lo] + (g - wpre[warp][lo]);
                             }
-                            if (sidx[k] != hs) {
-                                const V pj = sp[k];
-                                const R ddx = (R)pi.x - (R)pj.x;
-                                const R ddy = (R)pi.y - (R)pj.y;
-                                const R ddz = (R)pi.z - (R)pj.z;
-                                const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                                hit = r2 < rc2r && !(mi >= 0 && smol[k] == mi && r2 < hl2r);
-                            }
+                            // the home particle's own staged copy is formed by
+                            // the same arithmetic as hpos, so its r2 is exactly
+                            // 0; its periodic images are at least L away
+                            const V pj = sp[k];
+                            const R ddx = (R)pi.x - (R)pj.x;
+                            const R ddy = (R)pi.y - (R)pj.y;
+                            const R ddz = (R)pi.z - (R)pj.z;
+                            const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            hit = r2 > (R)0 && r2 < rc2r;
+                            if (MOL) hit = hit && !(mi >= 0 && smol[k] == mi && r2 < hl2r);
                         }
                         const unsigned m = __ballot_sync(0xffffffffu, hit);
                         if (hit) wq[warp][qn + __popc(m & ((1u << lane) - 1u))] = k;

@@ -43,17 +43,18 @@ class Request:
 
 
 def allowed_mesh(target: float, lo: int = 16, hi: int = 128) -> int:
-    """Smallest N >= target (clamped to [lo, hi]) of the form m 2^l, m <= 8,
-    so the multigrid hierarchy coarsens to at most 8^3."""
+    """Smallest N >= target (clamped to [lo, hi]) that is a multiple of 4 (the
+    vectorised FP32 diffusion kernel) and a valid multigrid mesh: halving
+    while even and above 16 must end at 64 or below (the exact coarse solve)."""
     want = max(lo, int(math.ceil(target)))
-    n = want
+    n = want + (-want) % 4
     while n <= hi:
         m = n
-        while m > 8 and m % 2 == 0:
+        while m > 16 and m % 2 == 0:
             m //= 2
-        if m <= 8:
+        if m <= 64:
             return n
-        n += 1
+        n += 4
     return hi
 
 

@@ -69,15 +69,19 @@ def test_device_bytes_estimate_matches_allocation(P, precision):
 
 
 def test_contexts_with_different_shared_memory_needs_coexist(P):
-    """The shared-memory V-cycle kernel's limit is per process: a context with
-    a small mesh created after one with a large need must not lower it (FP64
-    28^3 needs more than 24^3)."""
+    """The coarse-solve kernels' shared-memory limit is per process: a context
+    with a small need created after one with a large need must not lower it
+    (an FP64 exact coarse solve on 48^3 stages 55 KB, above the 48 KB default;
+    24^3 needs 14 KB)."""
     big = S.nacl_melt(300, 21.1, seed=31)
     small = S.nacl_melt(216, 18.9, seed=32)
-    a = P.Context.from_system(big, alpha=0.30, r_cut=9.0, mesh=28, tol=1e-8, dt=1.0, precision="fp64")
-    b = P.Context.from_system(small, alpha=0.30, r_cut=9.0, mesh=24, tol=1e-8, dt=1.0, precision="fp64")
+    a = P.Context.from_system(big, alpha=0.30, r_cut=9.0, mesh=48, tol=1e-8, dt=1.0, precision="fp64",
+                              coarse_max=64)
+    b = P.Context.from_system(small, alpha=0.30, r_cut=9.0, mesh=24, tol=1e-8, dt=1.0, precision="fp64",
+                              coarse_max=64)
     try:
-        a.step(6)                      # graph steps of the 28^3 context after the 24^3 set-up
+        assert a.stats()["coarse_n"] == 48 and b.stats()["coarse_n"] == 24
+        a.step(6)                      # graph steps of the 48^3 context after the 24^3 set-up
         b.step(6)
         assert a.stats()["steps"] == 6 and b.stats()["steps"] == 6
     finally:

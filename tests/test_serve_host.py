@@ -82,6 +82,6 @@ def test_backfill_and_rejection():
     assert reqs[1].admitted >= reqs[0].finished - 1e-12  # waited for memory
 
 
-@pytest.mark.parametrize("target, n", [(15.2, 16), (16.0, 16), (23.6, 24), (33.0, 40), (126.0, 128), (300.0, 128)])
+@pytest.mark.parametrize("target, n", [(15.2, 16), (16.0, 16), (23.6, 24), (33.0, 36), (126.0, 128), (300.0, 128)])
 def test_allowed_mesh_sizes(target, n):
     assert allowed_mesh(target) == n
