@@ -658,49 +658,51 @@ __device__ __forceinline__ void fused_check(float am, const CheckArgs& ck) {
 
 // Mixed precision: prediction (Eq. 17), guess z0 and initial residual in one
 // launch, with the check fused.  Per point: s = 2 Psi^k - Psi^{k-1} +
-// (4pi/h)(q^s - mean), z0 from the history (order 0-3), r = s - M z0 with
-// z0 at the neighbours formed from their history values.  Writes z0, the
-// exact residual rfin and its float copy r32.  A non-finite q^s sets status
-// to NONFINITE.
+// (4pi/h)(q^s - mean), z0 from the history (order ORDER, 0-3), r = s - M z0
+// with z0 at the neighbours formed from their history values.  Writes z0,
+// the exact residual rfin and its float copy r32.  A non-finite q^s sets
+// status to NONFINITE (once per thread, after its points).
+template <int ORDER>
 __device__ __forceinline__ fix_t z_guess(const fix_t* __restrict__ z1, const fix_t* __restrict__ z2,
-                                         const fix_t* __restrict__ z3, int order, int i) {
-    if (order == 1) return z1[i];
-    if (order == 2) return 2 * z1[i] - z2[i];
-    if (order == 3) return 3 * (z1[i] - z2[i]) + z3[i];
+                                         const fix_t* __restrict__ z3, int i) {
+    if (ORDER == 1) return z1[i];
+    if (ORDER == 2) return 2 * z1[i] - z2[i];
+    if (ORDER == 3) return 3 * (z1[i] - z2[i]) + z3[i];
     return 0;
 }
 
-static __global__ void __launch_bounds__(P3_BX * P3_BY)
+template <int ORDER>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
 k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restrict__ Psikm1,
                     const float* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, float u,
                     const fix_t* __restrict__ z1, const fix_t* __restrict__ z2, const fix_t* __restrict__ z3,
-                    int order, fix_t* __restrict__ z0, fix_t* __restrict__ rfin, float* __restrict__ r32,
-                    CheckArgs ck) {
+                    fix_t* __restrict__ z0, fix_t* __restrict__ rfin, float* __restrict__ r32, CheckArgs ck) {
     __shared__ float mean_s;
     if (threadIdx.x == 0 && threadIdx.y == 0) mean_s = (float)(qsum[0] * inv_pts);
     __syncthreads();
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     float a = 0.0f;
+    bool bad = false;
     if (x < n && y < n) {
         const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
         const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+        const float mean = mean_s;
         for (int zz = blockIdx.z; zz < n; zz += gridDim.z) {
             const int zm = zz == 0 ? n - 1 : zz - 1, zp = zz == n - 1 ? 0 : zz + 1;
-            const int i = (zz * n + y) * n + x;
+            const int row = (zz * n + y) * n;
+            const int i = row + x;
             const float q = qs[i];
-            if (!isfinite(q)) atomicCAS(&ck.st->status, 0, -5);
-            const fix_t s = 2 * Psik[i] - Psikm1[i] + charge_term(q, mean_s, u);
-            const fix_t zc = z_guess(z1, z2, z3, order, i);
+            bad |= !isfinite(q);
+            const fix_t s = 2 * Psik[i] - Psikm1[i] + charge_term(q, mean, u);
+            const fix_t zc = z_guess<ORDER>(z1, z2, z3, i);
             fix_t nb = 0;
-            if (order > 0) {
-                const int row = (zz * n + y) * n;
-                nb = z_guess(z1, z2, z3, order, row + xm) + z_guess(z1, z2, z3, order, row + xp) +
-                     z_guess(z1, z2, z3, order, (zz * n + ym) * n + x) +
-                     z_guess(z1, z2, z3, order, (zz * n + yp) * n + x) +
-                     z_guess(z1, z2, z3, order, (zm * n + y) * n + x) +
-                     z_guess(z1, z2, z3, order, (zp * n + y) * n + x);
-            }
+            if (ORDER > 0)
+                nb = z_guess<ORDER>(z1, z2, z3, row + xm) + z_guess<ORDER>(z1, z2, z3, row + xp) +
+                     z_guess<ORDER>(z1, z2, z3, (zz * n + ym) * n + x) +
+                     z_guess<ORDER>(z1, z2, z3, (zz * n + yp) * n + x) +
+                     z_guess<ORDER>(z1, z2, z3, (zm * n + y) * n + x) +
+                     z_guess<ORDER>(z1, z2, z3, (zp * n + y) * n + x);
             const fix_t res = s - (nb - 6 * zc);
             z0[i] = zc;
             rfin[i] = res;
@@ -709,6 +711,7 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
             a = fmaxf(a, fabsf(v));
         }
     }
+    if (bad) atomicCAS(&ck.st->status, 0, -5);
     fused_check(block_max_f(a), ck);
 }
 
@@ -716,13 +719,15 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
 // fix(e): z += E, and the exact residual is updated without a stencil of z,
 //   r_new = s - M (z + E) = r_old - M E,
 // with E at the neighbours converted the same way; check fused.  A
-// non-finite e sets status to NONFINITE (that point is left unchanged).
+// non-finite e sets status to NONFINITE (once per thread; that point is left
+// unchanged).
 static __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fix_t* __restrict__ rfin,
                    float* __restrict__ r32, CheckArgs ck) {
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     float a = 0.0f;
+    bool bad = false;
     auto fx_of = [](float v) { return fabsf(v) < 8.0e6f ? float_to_fix(v) : (fix_t)0; };
     if (x < n && y < n) {
         const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
@@ -731,7 +736,7 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
             const int zm = zz == 0 ? n - 1 : zz - 1, zp = zz == n - 1 ? 0 : zz + 1;
             const int i = (zz * n + y) * n + x;
             const float ec = e[i];
-            if (!(fabsf(ec) < 8.0e6f)) atomicCAS(&ck.st->status, 0, -5);
+            bad |= !(fabsf(ec) < 8.0e6f);
             const fix_t E = fx_of(ec);
             const int row = (zz * n + y) * n;
             const fix_t nb = fx_of(e[row + xm]) + fx_of(e[row + xp]) + fx_of(e[(zz * n + ym) * n + x]) +
@@ -745,6 +750,7 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
             a = fmaxf(a, fabsf(v));
         }
     }
+    if (bad) atomicCAS(&ck.st->status, 0, -5);
     fused_check(block_max_f(a), ck);
 }
 

@@ -271,7 +271,7 @@ int build_cells(p3maze_ctx* ctx) {
         CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * ctx->ncell, s));
         k_cell_count<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->cell,
                                                           ctx->count);
-        k_scan_cells<<<1, 1024, 0, s>>>(ctx->ncell, ctx->count, ctx->start, ctx->fill);
+        k_scan_cells<<<1, kScanThreads, 0, s>>>(ctx->ncell, ctx->count, ctx->start, ctx->fill);
         k_cell_scatter<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->cell, ctx->start, ctx->fill, ctx->order);
         k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
         launches += 4;
@@ -605,12 +605,20 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     }
     const int use_handle = ctx->capturing ? 1 : 0;
     stage_begin(ctx, P3MAZE_ST_PREDICT);
-    if (fixp)
-        k_predict_resid_fix<<<resid_grid(ctx->N), kB3, 0, s>>>(
-            ctx->N, fx(ctx->psi[ik]), fx(ctx->psi[ikm1]), (const float*)ctx->qs, ctx->dscal + S_QSUM,
-            1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h), fx(ctx->yh[1]), fx(ctx->yh[2]), fx(ctx->yh[3]),
-            pred_order, fx(ctx->yh[0]), fx(ctx->rfin), (float*)ctx->lev[0].b, check_args(ctx, h, use_handle));
-    else
+    if (fixp) {
+#define P3_PREDICT(ORD)                                                                                           \
+    k_predict_resid_fix<ORD><<<resid_grid(ctx->N), kB3, 0, s>>>(                                                  \
+        ctx->N, fx(ctx->psi[ik]), fx(ctx->psi[ikm1]), (const float*)ctx->qs, ctx->dscal + S_QSUM,                 \
+        1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h), fx(ctx->yh[1]), fx(ctx->yh[2]), fx(ctx->yh[3]),       \
+        fx(ctx->yh[0]), fx(ctx->rfin), (float*)ctx->lev[0].b, check_args(ctx, h, use_handle))
+        switch (pred_order) {
+            case 0: P3_PREDICT(0); break;
+            case 1: P3_PREDICT(1); break;
+            case 2: P3_PREDICT(2); break;
+            default: P3_PREDICT(3); break;
+        }
+#undef P3_PREDICT
+    } else
         k_predict<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->psi[ik], ctx->psi[ikm1], (const T*)ctx->qs,
                                                          ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, ctx->yh[1],
                                                          ctx->yh[2], ctx->yh[3], pred_order, ctx->sig, ctx->yh[0]);

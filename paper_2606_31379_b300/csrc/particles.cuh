@@ -82,41 +82,78 @@ static __global__ void k_cell_count(int n, const double* __restrict__ r, double 
     atomicAdd(&count[c], 1);
 }
 
-// Exclusive scan of m counts into start[0..m] with one block of 1024 threads;
-// also clears the per-cell fill counters.
-static __global__ void __launch_bounds__(1024) k_scan_cells(int m, const int* __restrict__ count,
-                                                     int* __restrict__ start, int* __restrict__ fill) {
-    __shared__ int warp_tot[32];
-    const int tid = threadIdx.x;
-    const int chunk = (m + blockDim.x - 1) / blockDim.x;
-    const int beg = min(tid * chunk, m), end = min(beg + chunk, m);
-    int local = 0;
-    for (int j = beg; j < end; ++j) local += count[j];
-    // inclusive warp scan
-    int v = local;
-    const int lane = tid & 31, wid = tid >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int w = warp_tot[lane];
+// Exclusive scan of m counts into start[0..m] with one block; also clears the
+// per-cell fill counters.  The counts pass through shared memory in tiles of
+// kScanTile: coalesced loads, kScanPer consecutive entries summed by each
+// thread, a warp and a block scan of the thread sums, the exclusive values
+// written back into the tile and stored coalesced, and the tile total
+// carried into the next tile.  Tile index j sits at j + j/32 in shared
+// memory, so both the coalesced and the per-thread accesses are free of bank
+// conflicts.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int scan_slot(int j) { return j + (j >> 5); }
+
+static __global__ void __launch_bounds__(kScanThreads) k_scan_cells(int m, const int* __restrict__ count,
+                                                                  int* __restrict__ start, int* __restrict__ fill) {
+    __shared__ int tile[kScanTile + kScanTile / 32];
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int carry = 0;
+    for (int t0 = 0; t0 < m; t0 += kScanTile) {
+        const int len = min(kScanTile, m - t0);
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int j = k * kScanThreads + tid;
+            if (j < len) {
+                tile[scan_slot(j)] = count[t0 + j];
+                fill[t0 + j] = 0;
+            }
+        }
+        __syncthreads();
+        int v[kScanPer];
+        int local = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int j = tid * kScanPer + k;
+            v[k] = j < len ? tile[scan_slot(j)] : 0;
+            local += v[k];
+        }
+        int w = local;  // inclusive warp scan of the thread sums
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
-        warp_tot[lane] = w;  // inclusive over warps
+        if (lane == 31) warp_tot[wid] = w;
+        __syncthreads();
+        if (wid == 0) {
+            int x = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            warp_tot[lane] = x;  // inclusive over warps
+        }
+        __syncthreads();
+        int run = carry + w - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int j = tid * kScanPer + k;
+            if (j < len) tile[scan_slot(j)] = run;
+            run += v[k];
+        }
+        carry += warp_tot[kScanThreads / 32 - 1];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            const int j = k * kScanThreads + tid;
+            if (j < len) start[t0 + j] = tile[scan_slot(j)];
+        }
+        __syncthreads();  // the next tile reuses tile and warp_tot
     }
-    __syncthreads();
-    int run = v - local + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (int j = beg; j < end; ++j) {
-        start[j] = run;
-        fill[j] = 0;
-        run += count[j];
-    }
-    if (tid == blockDim.x - 1) start[m] = warp_tot[31];
+    if (tid == 0) start[m] = carry;
 }
 
 static __global__ void k_cell_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
