@@ -656,9 +656,10 @@ def run_sweep(args) -> int:
             "smooth_us_per_launch": stage_us["smooth"] / nl, "smooth_algorithmic_gbs": smooth_gbs,
             "k_diffuse4_alone": {"us_per_launch": iso_us / K,
                                  "gbs": 2.0 * mesh ** 3 * b * K / (iso_us * 1e-6) / 1e9,
-                                 "frac_of_measured_hbm": 2.0 * mesh ** 3 * b * K / (iso_us * 1e-6) / 1e9
+                                 "frac_of_hbm_peak": 2.0 * mesh ** 3 * b * K / (iso_us * 1e-6) / 1e9
                                  / peaks["hbm_gbs"]},
-            "smooth_frac_of_measured_hbm": smooth_gbs / peaks["hbm_gbs"], "tuning": tuning,
+            "smooth_frac_of_hbm_peak": smooth_gbs / peaks["hbm_gbs"],
+            "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": peaks["source"], "tuning": tuning,
             "device_bytes": st["device_bytes"], "precision": args.precision,
         }), flush=True)
     return 0

@@ -672,7 +672,7 @@ __device__ __forceinline__ fix_t z_guess(const fix_t* __restrict__ z1, const fix
 }
 
 template <int ORDER>
-__global__ void __launch_bounds__(P3_BX * P3_BY)
+__global__ void __launch_bounds__(P3_BX * P3_BY, 8)
 k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restrict__ Psikm1,
                     const float* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, float u,
                     const fix_t* __restrict__ z1, const fix_t* __restrict__ z2, const fix_t* __restrict__ z3,
@@ -719,15 +719,13 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
 // fix(e): z += E, and the exact residual is updated without a stencil of z,
 //   r_new = s - M (z + E) = r_old - M E,
 // with E at the neighbours converted the same way; check fused.  A
-// non-finite e sets status to NONFINITE (once per thread; that point is left
-// unchanged).
+// non-finite e sets status to NONFINITE (that point is left unchanged).
 static __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fix_t* __restrict__ rfin,
                    float* __restrict__ r32, CheckArgs ck) {
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     float a = 0.0f;
-    bool bad = false;
     auto fx_of = [](float v) { return fabsf(v) < 8.0e6f ? float_to_fix(v) : (fix_t)0; };
     if (x < n && y < n) {
         const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
@@ -736,7 +734,7 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
             const int zm = zz == 0 ? n - 1 : zz - 1, zp = zz == n - 1 ? 0 : zz + 1;
             const int i = (zz * n + y) * n + x;
             const float ec = e[i];
-            bad |= !(fabsf(ec) < 8.0e6f);
+            if (!(fabsf(ec) < 8.0e6f)) atomicCAS(&ck.st->status, 0, -5);
             const fix_t E = fx_of(ec);
             const int row = (zz * n + y) * n;
             const fix_t nb = fx_of(e[row + xm]) + fx_of(e[row + xp]) + fx_of(e[(zz * n + ym) * n + x]) +
@@ -750,7 +748,6 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
             a = fmaxf(a, fabsf(v));
         }
     }
-    if (bad) atomicCAS(&ck.st->status, 0, -5);
     fused_check(block_max_f(a), ck);
 }
 
