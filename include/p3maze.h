@@ -32,6 +32,12 @@
  *     context runs its kernels on two internal streams (the mesh pipeline at
  *     the highest priority, the short-range pair branch at the lowest).  A
  *     context is not thread safe; use one context per thread.
+ *   - Chained mesh kernels (the diffusion steps, the V-cycle, the fused
+ *     residual update) are launched with programmatic dependent launch, so a
+ *     grid is scheduled while its predecessor drains; each waits for its
+ *     predecessor's completion before touching memory.  The environment
+ *     variable P3MAZE_PDL=0, read when a context is created, launches them
+ *     plainly (same results bit for bit).
  */
 #ifndef P3MAZE_H
 #define P3MAZE_H

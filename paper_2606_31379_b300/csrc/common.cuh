@@ -103,8 +103,11 @@ __device__ __forceinline__ int mesh_axis(double x, double inv_h, int n, float* t
 // predecessor grid has completed and its memory is visible; pdl_trigger()
 // lets the successor grid be scheduled (its blocks then wait in their own
 // pdl_wait()).  Both are no-ops for a kernel launched without the attribute.
-// Kernels of the step call pdl_wait() before touching memory a predecessor
-// writes, then pdl_trigger().
+// Every kernel that the library launches with the attribute calls pdl_wait()
+// before its first access to memory that a predecessor reads or writes
+// (reads of constant tables may come first), then pdl_trigger(); the
+// trigger only lets the successor's blocks be scheduled, its wait still
+// holds them until this grid has completed.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

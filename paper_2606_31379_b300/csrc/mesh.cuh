@@ -207,6 +207,8 @@ template <int ZC, bool SUM>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_diffuse4x2(int n, const float* __restrict__ in, float* __restrict__ out, float a0, float a1, float a2, float a3,
              double* __restrict__ partial) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x;
     const int q = blockIdx.x * P3_BX + lane;
     const int x = 4 * q;
@@ -408,6 +410,8 @@ static __global__ void k_mv2_partial(int np, const double* __restrict__ v, const
 
 // Sum of nb partials (in a fixed order) into out[0].
 static __global__ void k_sum_final(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    pdl_wait();
+    pdl_trigger();
     double acc = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
     acc = block_sum(acc);
@@ -677,6 +681,8 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
                     const float* __restrict__ qs, const double* __restrict__ qsum, double inv_pts, float u,
                     const fix_t* __restrict__ z1, const fix_t* __restrict__ z2, const fix_t* __restrict__ z3,
                     fix_t* __restrict__ z0, fix_t* __restrict__ rfin, float* __restrict__ r32, CheckArgs ck) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float mean_s;
     if (threadIdx.x == 0 && threadIdx.y == 0) mean_s = (float)(qsum[0] * inv_pts);
     __syncthreads();
@@ -723,6 +729,8 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
 static __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fix_t* __restrict__ rfin,
                    float* __restrict__ r32, CheckArgs ck) {
+    pdl_wait();
+    pdl_trigger();
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     float a = 0.0f;
@@ -759,6 +767,8 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
 template <typename T>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_rbgs(int n, T* __restrict__ e, const T* __restrict__ b, int color, int first) {
+    pdl_wait();
+    pdl_trigger();
     const int tx = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     const int z = blockIdx.z;
@@ -782,6 +792,8 @@ k_rbgs(int n, T* __restrict__ e, const T* __restrict__ b, int color, int first) 
 template <typename T>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_rbgs_first(int n, T* __restrict__ e, const T* __restrict__ b) {
+    pdl_wait();
+    pdl_trigger();
     int x, y, z;
     if (!xyz3(n, x, y, z)) return;
     const int i = (z * n + y) * n + x;
@@ -809,6 +821,8 @@ k_rbgs_first(int n, T* __restrict__ e, const T* __restrict__ b) {
 template <typename T>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_restrict(int nc, const T* __restrict__ e, const T* __restrict__ b, T* __restrict__ bc) {
+    pdl_wait();
+    pdl_trigger();
     int X, Y, Z;
     if (!xyz3(nc, X, Y, Z)) return;
     const int n = 2 * nc;
@@ -853,6 +867,8 @@ __device__ __forceinline__ T prolong_at(const T* __restrict__ ec, int nc, int x,
 template <typename T>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_prolong_add(int n, const T* __restrict__ ec, T* __restrict__ ef) {
+    pdl_wait();
+    pdl_trigger();
     int x, y, z;
     if (!xyz3(n, x, y, z)) return;
     ef[(z * n + y) * n + x] += prolong_at(ec, n >> 1, x, y, z);
@@ -907,9 +923,15 @@ __device__ __forceinline__ void coarse_stage(int n, int nP, const T* __restrict_
     for (int k = 0; k < kPer; ++k) {
         const int i = threadIdx.x + k * kCoarseThreads;
         const int r = i / nP, c = i - r * nP;
-        const bool in = i < nP * nP && r < n && c < n;
-        h[k] = in ? H[r * n + c] : (T)0;
-        a[k] = in ? src[r * sstride + c] : (T)0;
+        h[k] = (i < nP * nP && r < n && c < n) ? H[r * n + c] : (T)0;
+    }
+    pdl_wait();  // H is constant; src is the predecessor's output
+    pdl_trigger();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kCoarseThreads;
+        const int r = i / nP, c = i - r * nP;
+        a[k] = (i < nP * nP && r < n && c < n) ? src[r * sstride + c] : (T)0;
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {

@@ -6,6 +6,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -90,6 +91,7 @@ struct p3maze_ctx {
     int pair_blocks = 0;                 // pair grid: 0 one block per home box, else a persistent grid (tunable)
     int lr_force = 0;                    // P3MAZE_LR_FORCE_FD (the paper's) or P3MAZE_LR_FORCE_ANALYTIC
     int nsm = 148;                       // SMs of the device
+    bool pdl = true;                     // diffusion launches overlap their predecessor's tail (P3MAZE_PDL=0: off)
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
@@ -316,36 +318,61 @@ void launch_diffuse_tb(p3maze_ctx* ctx, int S, bool last, const T* src, T* dst) 
 // Planes per thread of k_diffuse4 for a tuning value zc (1, 2, 4 or 8).
 inline int diffuse4_planes(int zc) { return zc <= 1 ? 1 : zc <= 2 ? 2 : zc <= 4 ? 4 : 8; }
 
-void launch_diffuse4(int zc4, bool sum, dim3 g, cudaStream_t s, int n, const float* src, float* dst, float c,
-                     double* partial) {
-#define D4(Z)                                                                           \
-    do {                                                                                \
-        if (sum) k_diffuse4<Z, true><<<g, kB3, 0, s>>>(n, src, dst, c, partial);        \
-        else k_diffuse4<Z, false><<<g, kB3, 0, s>>>(n, src, dst, c, nullptr);           \
-    } while (0)
-    switch (zc4) {
-        case 1: D4(1); break;
-        case 2: D4(2); break;
-        case 4: D4(4); break;
-        default: D4(8); break;
-    }
-#undef D4
+// Launch with programmatic stream serialisation when pdl is set: the grid may
+// be scheduled while its predecessor in the stream is still running, and
+// its blocks wait in pdl_wait() until the predecessor has completed and its
+// writes are visible.  Only kernels that call pdl_wait() before their first
+// memory access may be launched this way.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
-void launch_diffuse4x2(int zc4, bool sum, dim3 g, cudaStream_t s, int n, const float* src, float* dst,
-                       const float a[4], double* partial) {
-#define D42(Z)                                                                                            \
-    do {                                                                                                  \
-        if (sum) k_diffuse4x2<Z, true><<<g, kB3, 0, s>>>(n, src, dst, a[0], a[1], a[2], a[3], partial);   \
-        else k_diffuse4x2<Z, false><<<g, kB3, 0, s>>>(n, src, dst, a[0], a[1], a[2], a[3], nullptr);      \
-    } while (0)
+template <int Z>
+cudaError_t diffuse4_z(bool sum, bool pdl, dim3 g, cudaStream_t s, int n, const float* src, float* dst, float c,
+                       double* partial) {
+    if (sum) return launch_maybe_pdl(pdl, k_diffuse4<Z, true>, g, kB3, 0, s, n, src, dst, c, partial);
+    return launch_maybe_pdl(pdl, k_diffuse4<Z, false>, g, kB3, 0, s, n, src, dst, c, (double*)nullptr);
+}
+
+cudaError_t launch_diffuse4(int zc4, bool sum, bool pdl, dim3 g, cudaStream_t s, int n, const float* src,
+                            float* dst, float c, double* partial) {
     switch (zc4) {
-        case 1: D42(1); break;
-        case 2: D42(2); break;
-        case 4: D42(4); break;
-        default: D42(8); break;
+        case 1: return diffuse4_z<1>(sum, pdl, g, s, n, src, dst, c, partial);
+        case 2: return diffuse4_z<2>(sum, pdl, g, s, n, src, dst, c, partial);
+        case 4: return diffuse4_z<4>(sum, pdl, g, s, n, src, dst, c, partial);
+        default: return diffuse4_z<8>(sum, pdl, g, s, n, src, dst, c, partial);
     }
-#undef D42
+}
+
+template <int Z>
+cudaError_t diffuse4x2_z(bool sum, bool pdl, dim3 g, cudaStream_t s, int n, const float* src, float* dst,
+                         const float a[4], double* partial) {
+    if (sum)
+        return launch_maybe_pdl(pdl, k_diffuse4x2<Z, true>, g, kB3, 0, s, n, src, dst, a[0], a[1], a[2], a[3], partial);
+    return launch_maybe_pdl(pdl, k_diffuse4x2<Z, false>, g, kB3, 0, s, n, src, dst, a[0], a[1], a[2], a[3],
+                            (double*)nullptr);
+}
+
+cudaError_t launch_diffuse4x2(int zc4, bool sum, bool pdl, dim3 g, cudaStream_t s, int n, const float* src,
+                              float* dst, const float a[4], double* partial) {
+    switch (zc4) {
+        case 1: return diffuse4x2_z<1>(sum, pdl, g, s, n, src, dst, a, partial);
+        case 2: return diffuse4x2_z<2>(sum, pdl, g, s, n, src, dst, a, partial);
+        case 4: return diffuse4x2_z<4>(sum, pdl, g, s, n, src, dst, a, partial);
+        default: return diffuse4x2_z<8>(sum, pdl, g, s, n, src, dst, a, partial);
+    }
 }
 
 template <typename T>
@@ -396,17 +423,19 @@ int spread_smooth(p3maze_ctx* ctx) {
                 const int S = (ctx->fuse == 2 && (ctx->K - done) % 2 == 0) ? 2 : 1;
                 const bool last = done + S == ctx->K;
                 T* dst = last ? (T*)ctx->qs : tmp[launches & 1];
+                const bool pdl = ctx->pdl && launches > 0;  // overlap with the previous diffusion launch
                 if (S == 2)
-                    launch_diffuse4x2(zc4, last, g, s, ctx->N, (const float*)src, (float*)dst, a,
-                                      last ? ctx->partial : nullptr);
+                    CK(launch_diffuse4x2(zc4, last, pdl, g, s, ctx->N, (const float*)src, (float*)dst, a,
+                                         last ? ctx->partial : nullptr));
                 else
-                    launch_diffuse4(zc4, last, g, s, ctx->N, (const float*)src, (float*)dst, (float)ctx->c,
-                                    last ? ctx->partial : nullptr);
+                    CK(launch_diffuse4(zc4, last, pdl, g, s, ctx->N, (const float*)src, (float*)dst, (float)ctx->c,
+                                       last ? ctx->partial : nullptr));
                 src = dst;
                 done += S;
                 ++launches;
             }
-            k_sum_final<<<1, 1024, 0, s>>>((int)(g.x * g.y * g.z), ctx->partial, ctx->dscal + S_QSUM);
+            CK(launch_maybe_pdl(ctx->pdl, k_sum_final, dim3(1), dim3(1024), 0, s, (int)(g.x * g.y * g.z),
+                                ctx->partial, ctx->dscal + S_QSUM));
             count(ctx, P3MAZE_ST_SMOOTH, launches + 1);
         } else {
             for (int k = 0; k < ctx->K; ++k) {
@@ -449,42 +478,51 @@ int spread_smooth(p3maze_ctx* ctx) {
 // prolongation); the coarse level solved exactly by separable Hartley
 // transforms (three launches).
 template <typename T>
-int vcycle(p3maze_ctx* ctx, int l) {
+int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
     cudaStream_t s = ctx->stream;
     Level& L = ctx->lev[l];
     T* e = (T*)L.e;
     T* b = (T*)L.b;
+    // every launch but the first follows a kernel of this V-cycle and may
+    // overlap its tail (programmatic dependent launch)
+    bool pdl = ctx->pdl && pdl_first;
+    auto go = [&](auto kernel, dim3 g, dim3 blk, size_t smem, auto... args) {
+        const cudaError_t err = launch_maybe_pdl(pdl, kernel, g, blk, smem, s, args...);
+        pdl = ctx->pdl;
+        return err;
+    };
     if (l == ctx->lc) {
         const size_t sm = coarse_smem_bytes(L.n, sizeof(T));
-        k_coarse_xy<T><<<L.n, kCoarseThreads, sm, s>>>(L.n, b, (T*)L.t, (const T*)L.H);
-        k_coarse_z<T><<<L.n, kCoarseThreads, sm, s>>>(L.n, (T*)L.t, (const T*)L.H, (const T*)L.D);
-        k_coarse_xy<T><<<L.n, kCoarseThreads, sm, s>>>(L.n, (const T*)L.t, e, (const T*)L.H);
+        const dim3 gc(L.n), bc(kCoarseThreads);
+        CK(go(k_coarse_xy<T>, gc, bc, sm, L.n, (const T*)b, (T*)L.t, (const T*)L.H));
+        CK(go(k_coarse_z<T>, gc, bc, sm, L.n, (T*)L.t, (const T*)L.H, (const T*)L.D));
+        CK(go(k_coarse_xy<T>, gc, bc, sm, L.n, (const T*)L.t, e, (const T*)L.H));
         count(ctx, P3MAZE_ST_SOLVE, 3);
-        CKL();
         return P3MAZE_OK;
     }
     Level& C = ctx->lev[l + 1];
-    if (ctx->nu1 == 0) CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
+    if (ctx->nu1 == 0) {
+        CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
+        pdl = false;  // the next launch follows a memset
+    }
     for (int it = 0; it < ctx->nu1; ++it) {
         if (it == 0) {
-            k_rbgs_first<T><<<g3(L.n), kB3, 0, s>>>(L.n, e, b);  // both colours from e = 0
+            CK(go(k_rbgs_first<T>, g3(L.n), kB3, 0, L.n, e, (const T*)b));  // both colours from e = 0
         } else {
-            k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 0, 0);
-            k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 1, 0);
+            CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 0, 0));
+            CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
         }
     }
-    k_resid_restrict<T><<<g3(C.n), kB3, 0, s>>>(C.n, e, b, (T*)C.b);
+    CK(go(k_resid_restrict<T>, g3(C.n), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
     count(ctx, P3MAZE_ST_SOLVE, (ctx->nu1 > 0 ? 2 * ctx->nu1 - 1 : 0) + 1);
-    CKL();
-    int rc = vcycle<T>(ctx, l + 1);
+    int rc = vcycle<T>(ctx, l + 1, true);
     if (rc) return rc;
-    k_prolong_add<T><<<g3(L.n), kB3, 0, s>>>(L.n, (const T*)C.e, e);
+    CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
     for (int it = 0; it < ctx->nu2; ++it) {
-        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 1, 0);
-        k_rbgs<T><<<g3h(L.n), kB3, 0, s>>>(L.n, e, b, 0, 0);
+        CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
+        CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 0, 0));
     }
     count(ctx, P3MAZE_ST_SOLVE, 1 + 2 * ctx->nu2);
-    CKL();
     return P3MAZE_OK;
 }
 
@@ -509,13 +547,12 @@ void launch_resid_check(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_h
 // the check (mixed: one fused kernel; FP64: three kernels).
 template <typename T>
 int launch_iteration(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
-    int rc = vcycle<T>(ctx, 0);
+    int rc = vcycle<T>(ctx, 0, false);
     if (rc) return rc;
     if (ctx->prec == P3MAZE_MIXED) {
-        k_resid_update_fix<<<resid_grid(ctx->N), kB3, 0, ctx->stream>>>(ctx->N, fx(ctx->yh[0]),
-                                                                         (const float*)ctx->lev[0].e, fx(ctx->rfin),
-                                                                         (float*)ctx->lev[0].b,
-                                                                         check_args(ctx, h, use_handle));
+        CK(launch_maybe_pdl(ctx->pdl, k_resid_update_fix, resid_grid(ctx->N), kB3, 0, ctx->stream, ctx->N,
+                            fx(ctx->yh[0]), (const float*)ctx->lev[0].e, fx(ctx->rfin), (float*)ctx->lev[0].b,
+                            check_args(ctx, h, use_handle)));
         count(ctx, P3MAZE_ST_SOLVE);
     } else {
         k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0],
@@ -1023,6 +1060,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     const size_t tb = mixed ? sizeof(float) : sizeof(double);
     CK(cudaGetDevice(&ctx->device));
     CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (const char* v = std::getenv("P3MAZE_PDL")) ctx->pdl = std::strcmp(v, "0") != 0;
     {
         // Work runs on an internal stream of the highest priority (graphs can
         // be captured on it whatever the caller passed), the short-range
