@@ -37,7 +37,7 @@
  *     grid is scheduled while its predecessor drains; each waits for its
  *     predecessor's completion before touching memory.  The environment
  *     variable P3MAZE_PDL=0, read when a context is created, launches them
- *     plainly (same results bit for bit).
+ *     plainly (the same arithmetic).
  */
 #ifndef P3MAZE_H
 #define P3MAZE_H
