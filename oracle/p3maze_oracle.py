@@ -555,6 +555,40 @@ def forces_and_energies(system, alpha: float, r_cut: float, n: int, ke: float = 
     return out
 
 
+# ---------------------------------------------------------------------------
+# PMaZe: the whole Coulomb problem on the mesh (the comparison method, Secs. 1-2)
+# ---------------------------------------------------------------------------
+def pmaze_mesh_fields(system, n: int) -> dict:
+    """PMaZe's exactly constrained potential: the assigned charge q = A(r)Q
+    itself is the source (Sec. 2, "charge assignment and smoothing": no
+    Gaussian screening and no smoothing), its mean removed for the gauge, and
+    phi* = -(4 pi / h) M^+ q solves (h/4pi) M phi + q = 0 (Eq. 13 with q in
+    place of q^s)."""
+    h = system.box / n
+    q = assign_charges(system.pos, system.charge, system.box, n)
+    phi = solve_constraint_fft(q - q.mean(), h)
+    return {"q": q, "phi": phi, "h": h}
+
+
+def pmaze_forces_and_energies(system, r_cut: float, n: int, ke: float = COULOMB_K) -> dict:
+    """PMaZe forces at the exactly constrained field: Eq. 21 applied to the
+    full-Coulomb mesh potential gives the whole electrostatic force; pairs
+    within R_c carry only the non-Coulomb term.  v_mesh = 1/2 ke phi*^T q
+    contains the grid self-energy of every charge (Sec. 2, "electrostatic
+    energy"); the work-based energy the paper uses for PMaZe is not formed.
+    Systems with molecules are not defined here (their exclusions would need
+    the mesh pair interaction).  Only the finite-difference force of Eq. 21:
+    with the whole charge on the mesh, the exact gradient of v_mesh is
+    dominated by the gradient of the grid self-energy."""
+    if system.molecule is not None:
+        raise ValueError("PMaZe is defined here for systems without molecules")
+    mf = pmaze_mesh_fields(system, n)
+    F_mesh = interpolate_lr_forces(system.pos, system.charge, system.box, n, mf["phi"], ke)
+    F_vdw, _, ev = sr_forces(system, 1.0, r_cut, ke, coulomb=False)
+    return {"F_mesh": F_mesh, "F_vdw": F_vdw, "F": F_mesh + F_vdw, "v_vdw": float(ev.sum()),
+            "v_mesh": 0.5 * ke * float((mf["phi"] * mf["q"]).sum()), "fields": mf}
+
+
 def kinetic_energy(vel: np.ndarray, mass: np.ndarray) -> float:
     """sum 1/2 m v^2 in kcal/mol (v in A/fs, m in g/mol)."""
     return 0.5 * float((mass[:, None] * vel * vel).sum()) / ACCEL

@@ -371,3 +371,40 @@ def test_bspline_derivative_weights():
     h = 1e-6
     fd = (O.bspline4_weights(t + h) - O.bspline4_weights(t - h)) / (2 * h)
     assert np.allclose(d, fd, atol=1e-8)
+
+
+# ---------------------------------------------------------------- PMaZe
+def test_pmaze_forces_converge_to_full_coulomb_ewald():
+    """PMaZe puts the whole Coulomb problem on the mesh (Sec. 2): with no
+    screening, the Eq. 21 force of the constrained full-charge potential must
+    approach the brute-force Ewald force of the point charges as h^2, sum to
+    zero (Newton III on the mesh), and its mesh energy must exceed the Ewald
+    energy by a grid self-energy that scales as 1/h."""
+    s = S.random_neutral(8, 12.0, seed=11, dmin=1.5)
+    e_ref, F_ref = O.ewald(s.pos, s.charge, s.box, 0.5, ke=1.0)
+    ferr, self_h = [], []
+    for n in (32, 64, 128):
+        out = O.pmaze_forces_and_energies(s, 6.0, n, ke=1.0)
+        ferr.append(np.sqrt(((out["F"] - F_ref) ** 2).sum() / (F_ref ** 2).sum()))
+        assert np.abs(out["F"].sum(0)).max() < 1e-12 * np.abs(out["F"]).max()
+        self_h.append((out["v_mesh"] - e_ref) * (s.box / n))
+    assert ferr[2] < 2e-3
+    assert 3.0 < ferr[0] / ferr[1] < 5.0 and 3.0 < ferr[1] / ferr[2] < 5.0
+    assert self_h[0] > 0.0 and abs(self_h[2] - self_h[1]) < 0.01 * self_h[2]
+
+
+def test_pmaze_source_is_the_unsmoothed_assigned_charge():
+    """The PMaZe potential solves the constraint with q itself: applying
+    (h/4pi) M to it returns -(q - mean q) (Eq. 13 with q in place of q^s)."""
+    s = S.random_neutral(6, 10.0, seed=4, dmin=1.5)
+    n = 24
+    f = O.pmaze_mesh_fields(s, n)
+    q = O.assign_charges(s.pos, s.charge, s.box, n)
+    back = (f["h"] / (4.0 * np.pi)) * O.laplacian7(f["phi"])
+    assert np.abs(back + (q - q.mean())).max() < 1e-12 * np.abs(q).max()
+
+
+def test_pmaze_rejects_molecules():
+    w = S.spcfw_water(8, 6.3, seed=2)
+    with pytest.raises(ValueError):
+        O.pmaze_forces_and_energies(w, 3.0, 16)
