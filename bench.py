@@ -481,7 +481,7 @@ def run_ours(args) -> int:
     ctx.close()
 
     # beside the headline: the plain FP64 path, the multiplier predictors and
-    # the real-space P3M baseline (Sec. 3.3) on the same workload
+    # the real-space P3M baseline (Sec. 3.3) and PMaZe on the same workload
     variants = {}
     if not args.no_variants:
         # fp64: the plain FP64 path, autotuned like the headline.  The
@@ -491,12 +491,16 @@ def run_ours(args) -> int:
                    ("maze_y1", dict(precision=args.precision, predictor=1)),
                    ("maze_y2", dict(precision=args.precision, predictor=2)),
                    ("maze_y3", dict(precision=args.precision, predictor=3)),
-                   ("p3m", dict(precision=args.precision, method="p3m"))]
+                   ("p3m", dict(precision=args.precision, method="p3m")),
+                   # PMaZe: the whole Coulomb problem on a mesh of twice the
+                   # points per axis (the paper's NaCl comparison: 60^3 -> 120^3)
+                   ("pmaze", dict(precision=args.precision, method="pmaze", mesh=2 * prm["mesh"], alpha=0.0))]
         for name, kw in studies:
             if name == "fp64" and args.precision == "fp64":
                 continue
-            cv = P.Context.from_system(system, alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"],
-                                       tol=prm["tol"], dt=prm["dt"], stream=stream.cuda_stream, **kw)
+            ckw = dict(alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"], tol=prm["tol"], dt=prm["dt"])
+            ckw.update(kw)
+            cv = P.Context.from_system(system, stream=stream.cuda_stream, **ckw)
             cv.step(args.warmup)
             tv_tune = None if (args.no_tune or name != "fp64") else cv.autotune(8)
             it0 = cv.stats()["total_iters"]

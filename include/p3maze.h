@@ -70,6 +70,22 @@ extern "C" {
                                  equation solved directly by multigrid with no multiplier
                                  predictor, convergence on max|M phi + (4pi/h) q^s| (the P3M
                                  residual of Sec. 3.3) <= tol                               */
+#define P3MAZE_METHOD_PMAZE 2 /* PMaZe, the comparison method of Secs. 1-2: the whole Coulomb
+                                 problem on the mesh.  The assigned charge q itself is the
+                                 source (no smoothing, K = 0), the same Mass-Zero constraint
+                                 (h/4pi) M phi + q = 0 is enforced by the same prediction and
+                                 correction, the mesh force of Eq. 21 is the whole
+                                 electrostatic force, and pairs carry only the non-Coulomb
+                                 term (no erfc term, no Gaussian self term; alpha is not
+                                 used).  v_lr = 1/2 ke phi^T q then contains the grid
+                                 self-energy of every charge (Sec. 2, "electrostatic
+                                 energy"); the work-based energy the paper uses for PMaZe is
+                                 not formed.  Molecular topologies are rejected (their
+                                 intramolecular exclusions would need the mesh pair
+                                 interaction), and so is P3MAZE_LR_FORCE_ANALYTIC (with the
+                                 whole charge on the mesh the exact gradient is dominated by
+                                 the gradient of the grid self-energy).  The mesh must resolve the charges: the
+                                 paper's NaCl comparison uses twice the P3MaZe mesh per axis */
 
 /* Long-range force interpolation */
 #define P3MAZE_LR_FORCE_FD       0  /* F = -ke Q W . D phi, central differences (Eq. 21; default):
@@ -126,7 +142,8 @@ typedef struct {
     const double *charges;  /* host [n] e; total charge |sum Q| <= 1e-9 sum|Q| else INVALID */
     const double *masses;   /* host [n] g/mol, > 0                                         */
     const int32_t *types;   /* host [n] species index < sr->n_types (may be NULL if no sr) */
-    double alpha;           /* Ewald splitting, 1/A; sigma = 1/(sqrt(2) alpha) (Eq. 5)     */
+    double alpha;           /* Ewald splitting, 1/A; sigma = 1/(sqrt(2) alpha) (Eq. 5);
+                               not used (may be 0) with P3MAZE_METHOD_PMAZE                */
     double r_cut;           /* real-space cutoff, A; need r_cut <= L                        */
     int32_t mesh;           /* N points per axis, N >= 4, N = m 2^l with m <= 64: the
                                multigrid levels N, N/2, ... are halved while even and
@@ -143,7 +160,8 @@ typedef struct {
     double coulomb_k;       /* kcal A/(mol e^2); 0 -> 332.0637                              */
     const p3maze_sr_table *sr;      /* may be NULL: Coulomb only                           */
     const p3maze_topology *topology;/* may be NULL                                         */
-    int32_t method;         /* P3MAZE_METHOD_MAZE (0) or P3MAZE_METHOD_P3M                  */
+    int32_t method;         /* P3MAZE_METHOD_MAZE (0), P3MAZE_METHOD_P3M or
+                               P3MAZE_METHOD_PMAZE                                         */
     int32_t coarse_max;     /* the first level with n <= coarse_max is solved exactly
                                (separable Hartley transforms); 0 -> 64 (mixed), 16 (FP64) */
     int32_t lr_force;       /* P3MAZE_LR_FORCE_FD (0, the paper's Eq. 21) or

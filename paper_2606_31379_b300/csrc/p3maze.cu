@@ -98,6 +98,7 @@ struct p3maze_ctx {
     int64_t P = 0;
     double L = 0, h = 0, inv_h = 0, alpha = 0, sigma = 0, rc = 0, c = 0, tol = 0, dt = 0, ke = 0;
     double inv_cell = 0, lcell = 0, v_self = 0;
+    double ke_pair = 0;                  // Coulomb constant of the erfc pair term (0 for PMaZe)
     SRTable tab{};
     double kb = 0, r0 = 0, ka = 0, th0 = 0;
     // particle arrays (original order)
@@ -705,11 +706,11 @@ int pair_forces(p3maze_ctx* ctx) {
     do {                                                                                                \
         if (mixed)                                                                                      \
             k_pair<KIND, float, 768, MOL><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts,        \
-                ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke,       \
+                ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke_pair,  \
                 ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
         else                                                                                            \
             k_pair<KIND, double, 512, MOL><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts,       \
-                ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke,       \
+                ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke_pair,  \
                 ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
     } while (0)
     const bool mol = ctx->nmol > 0;
@@ -1299,14 +1300,17 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     const double L = p->box[0];
     if (!(L > 0.0) || std::fabs(p->box[1] - L) > 1e-12 * L || std::fabs(p->box[2] - L) > 1e-12 * L)
         return fail(nullptr, P3MAZE_ERR_INVALID, "box must be cubic and positive");
-    if (!(p->alpha > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "alpha must be > 0");
+    const bool pmaze = p->method == P3MAZE_METHOD_PMAZE;
+    if (!pmaze && !(p->alpha > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "alpha must be > 0");
+    if (pmaze && !(p->alpha >= 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "alpha must be >= 0");
     if (!(p->r_cut > 0.0) || p->r_cut > L) return fail(nullptr, P3MAZE_ERR_INVALID, "need 0 < r_cut <= L");
     if (p->order != 4) return fail(nullptr, P3MAZE_ERR_INVALID, "only order 4 (cubic B-spline) is supported");
     if (!(p->tol > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "tol must be > 0");
     if (!(p->dt >= 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "dt must be >= 0");
     if (p->predictor < 0 || p->predictor > 3) return fail(nullptr, P3MAZE_ERR_INVALID, "predictor must be 0..3");
-    if (p->method != P3MAZE_METHOD_MAZE && p->method != P3MAZE_METHOD_P3M)
-        return fail(nullptr, P3MAZE_ERR_INVALID, "method must be P3MAZE_METHOD_MAZE or P3MAZE_METHOD_P3M");
+    if (p->method != P3MAZE_METHOD_MAZE && p->method != P3MAZE_METHOD_P3M && !pmaze)
+        return fail(nullptr, P3MAZE_ERR_INVALID,
+                    "method must be P3MAZE_METHOD_MAZE, P3MAZE_METHOD_P3M or P3MAZE_METHOD_PMAZE");
     if (p->precision != P3MAZE_FP64 && p->precision != P3MAZE_MIXED)
         return fail(nullptr, P3MAZE_ERR_INVALID, "precision must be P3MAZE_FP64 or P3MAZE_MIXED");
     if (p->max_mg_iters < 0 || p->pre_sweeps < 0 || p->post_sweeps < 0)
@@ -1317,6 +1321,10 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     if (p->coarse_max < 0) return fail(nullptr, P3MAZE_ERR_INVALID, "coarse_max must be >= 0");
     if (p->lr_force != P3MAZE_LR_FORCE_FD && p->lr_force != P3MAZE_LR_FORCE_ANALYTIC)
         return fail(nullptr, P3MAZE_ERR_INVALID, "lr_force must be P3MAZE_LR_FORCE_FD or P3MAZE_LR_FORCE_ANALYTIC");
+    if (pmaze && p->lr_force != P3MAZE_LR_FORCE_FD)
+        return fail(nullptr, P3MAZE_ERR_INVALID,
+                    "P3MAZE_METHOD_PMAZE takes the finite-difference force (the exact gradient carries the grid "
+                    "self-force)");
     double qsum = 0.0, qabs = 0.0;
     for (int i = 0; i < n; ++i) {
         if (!(p->masses[i] > 0.0)) return fail(nullptr, P3MAZE_ERR_INVALID, "masses must be > 0");
@@ -1364,12 +1372,16 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
                 seen[id] = 1;
             }
         nmol = tp->n_molecules;
+        if (pmaze)
+            return fail(nullptr, P3MAZE_ERR_INVALID,
+                        "P3MAZE_METHOD_PMAZE takes no molecular topology (exclusions need the mesh pair term)");
     }
     const double h = L / p->mesh;
-    const double sigma = 1.0 / (std::sqrt(2.0) * p->alpha);
+    // PMaZe: no Gaussian screening, the assigned charge is the source (K = 0)
+    const double sigma = pmaze ? 0.0 : 1.0 / (std::sqrt(2.0) * p->alpha);
     // diffusion smoothing: per-axis variance sigma^2 - 4 h^2/6 in K steps of 2 c h^2
-    const double kappa = (sigma * sigma - 4.0 * h * h / 6.0) / (2.0 * h * h);
-    if (!(kappa > 0.0))
+    const double kappa = pmaze ? 0.0 : (sigma * sigma - 4.0 * h * h / 6.0) / (2.0 * h * h);
+    if (!pmaze && !(kappa > 0.0))
         return fail(nullptr, P3MAZE_ERR_INVALID, "mesh too coarse for alpha: need sigma^2 > 2 h^2/3");
 
     p3maze_ctx* ctx = new (std::nothrow) p3maze_ctx();
@@ -1384,8 +1396,8 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     ctx->alpha = p->alpha;
     ctx->sigma = sigma;
     ctx->rc = p->r_cut;
-    ctx->K = (int)std::ceil(6.0 * kappa);
-    ctx->c = kappa / ctx->K;
+    ctx->K = pmaze ? 0 : (int)std::ceil(6.0 * kappa);
+    ctx->c = pmaze ? 0.0 : kappa / ctx->K;
     ctx->tol = p->tol;
     ctx->dt = p->dt;
     ctx->method = p->method;
@@ -1417,7 +1429,8 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     }
     double q2 = 0.0;
     for (int i = 0; i < n; ++i) q2 += p->charges[i] * p->charges[i];
-    ctx->v_self = -ctx->ke * q2 / (std::sqrt(2.0 * kPi) * sigma);
+    ctx->v_self = pmaze ? 0.0 : -ctx->ke * q2 / (std::sqrt(2.0 * kPi) * sigma);
+    ctx->ke_pair = pmaze ? 0.0 : ctx->ke;  // PMaZe pairs: non-Coulomb term only
     ctx->st.smooth_steps = ctx->K;
     ctx->st.smooth_coeff = ctx->c;
     (void)ncoarse;
@@ -1936,6 +1949,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     // diffusion kernel: steps per launch (mixed: 1, 2 or 4) x z planes per
     // thread (one or two steps per launch, N % 4 == 0: 1-8) or per block
     auto diffusion_pass = [&]() {
+        if (ctx->K == 0) return;  // no smoothing (PMaZe)
         const int fuses[3] = {1, 2, 4};
         const int zcs_quad[4] = {1, 2, 4, 8}, zcs_other[4] = {4, 8, 16, 32};
         const Setting base = chosen;

@@ -18,7 +18,7 @@ lib = C.CDLL(_LIB_PATH)
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2, -3, -4, -5
 FP64, MIXED = 0, 1
-METHOD_MAZE, METHOD_P3M = 0, 1
+METHOD_MAZE, METHOD_P3M, METHOD_PMAZE = 0, 1, 2
 SR_NONE, SR_BMH, SR_LJ = 0, 1, 2
 MAX_TYPES = 4
 MESH = {"q": 0, "qs": 1, "phi": 2, "y": 3, "sigma": 4}
@@ -198,7 +198,7 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
     p.precision = {"fp64": FP64, "mixed": MIXED}[precision]
     p.max_mg_iters, p.pre_sweeps, p.post_sweeps = int(max_mg_iters), int(pre_sweeps), int(post_sweeps)
     p.coulomb_k = float(coulomb_k)
-    p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M}[method]
+    p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M, "pmaze": METHOD_PMAZE}[method]
     p.coarse_max = int(coarse_max)
     p.lr_force = {"fd": 0, "analytic": 1}[lr_force]
     tab = sr_table_from(sr_kind, sr_table or {})

@@ -74,6 +74,8 @@ def _base_kwargs(s):
     (dict(predictor=4), "predictor"),
     (dict(precision="fp64", alpha=-1.0), "alpha"),
     (dict(mesh=8, alpha=0.9), "too coarse"),
+    (dict(method="pmaze", alpha=-1.0), "alpha"),
+    (dict(method="pmaze", lr_force="analytic"), "finite-difference"),
 ])
 def test_init_rejects_invalid_parameters(change, needle):
     from paper_2606_31379_b300 import p3maze as P
@@ -113,3 +115,11 @@ def test_init_rejects_non_neutral_and_bad_types():
     pos[2, 1] = np.nan
     with pytest.raises(P.P3MaZeError, match="non-finite"):
         P.Context(pos, s.charge, s.mass, s.box, **_base_kwargs(s))
+
+
+def test_pmaze_rejects_a_molecular_topology_before_touching_the_device():
+    from paper_2606_31379_b300 import p3maze as P
+    w = S.spcfw_water(8, 12.0, seed=1)
+    with pytest.raises(P.P3MaZeError, match="topology") as ei:
+        P.Context.from_system(w, alpha=0.0, r_cut=6.0, mesh=16, tol=1e-6, dt=0.5, method="pmaze")
+    assert ei.value.code == P.ERR_INVALID
