@@ -531,3 +531,27 @@ def test_analytic_force_conserves_energy_where_finite_differences_do_not(P, nacl
             std[force] = (float(np.std(E)), float(np.std(K)))
     assert std["analytic"][0] < 0.005 * std["analytic"][1]
     assert std["analytic"][0] < 0.2 * std["fd"][0], std
+
+
+def test_analytic_force_meets_the_long_run_drift_target(P, nacl512):
+    """Energy drift over 50 ps of NVE (NaCl 512, FP64, analytic-gradient
+    force, cutoff 12 A, 2000 relaxation steps at 1200 K first): the linear
+    fit of the total energy, in k_BT per ns per particle, is consistent with
+    the 1e-4 target (below it within three standard errors of the fit).  The
+    paper's finite-difference force drifts about 0.2 on the same run, which
+    is why this is asserted for the energy-gradient option only."""
+    kB, T, every, nsamp = 0.0019872043, 1200.0, 100, 500
+    with _ctx(P, nacl512, precision="fp64", tol=1e-9, r_cut=12.0, lr_force="analytic") as ctx:
+        ctx.equilibrate(2000, T)
+        E = []
+        for k in range(nsamp + 1):
+            if k:
+                ctx.step(every)
+            E.append(ctx.energy()["total"])
+    E = np.array(E)
+    t = every * np.arange(E.size)                    # fs
+    slope, icpt = np.polyfit(t, E, 1)
+    se = (E - slope * t - icpt).std() / (t.std() * np.sqrt(E.size))
+    scale = 1e6 / nacl512.n / (kB * T)               # kcal/mol/fs -> k_BT/ns/particle
+    assert abs(slope) * scale - 3.0 * se * scale < 1e-4, (slope * scale, se * scale)
+    assert se * scale < 5e-4                         # the run resolves the target's scale
