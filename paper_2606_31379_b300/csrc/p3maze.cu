@@ -91,7 +91,7 @@ struct p3maze_ctx {
     int pair_blocks = 0;                 // pair grid: 0 one block per home box, else a persistent grid (tunable)
     int lr_force = 0;                    // P3MAZE_LR_FORCE_FD (the paper's) or P3MAZE_LR_FORCE_ANALYTIC
     int nsm = 148;                       // SMs of the device
-    bool pdl = true;                     // diffusion launches overlap their predecessor's tail (P3MAZE_PDL=0: off)
+    bool pdl = true;                     // chained mesh kernels overlap their predecessor's tail (P3MAZE_PDL=0: off)
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
