@@ -130,6 +130,18 @@ k_diffuse(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, dou
     }
 }
 
+// Compensated FP32 summation for the neutrality block sums: s + c carries a
+// running sum with the exact rounding error of every addition (Knuth's
+// two-sum), about 48 significant bits after the 32 additions of a thread, at
+// FP32 rates; FP64 conversions and adds run at 1/64 of that on this part.
+// The pair becomes one FP64 value per thread before the FP64 block sum.
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bv = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(v, bv)));
+    s = t;
+}
+
 // One explicit diffusion step in FP32 with four x-consecutive points per
 // thread (float4 loads and stores; N % 4 == 0).  The x-1 and x+4 neighbours
 // of a quad come from the neighbouring lanes by shuffle (the row ends load
@@ -169,7 +181,7 @@ k_diffuse4(int n, const float* __restrict__ in, float* __restrict__ out, float c
         lft[k] = lend ? in[z * plane + yy * n + xl] : 0.0f;
         rgt[k] = rend ? in[z * plane + yy * n + xr] : 0.0f;
     }
-    double acc = 0.0;
+    float acc_s = 0.0f, acc_c = 0.0f;
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
         const float4 vm = col[k], vc = col[k + 1], vp = col[k + 2], a = am[k], b = bp[k];
@@ -184,11 +196,16 @@ k_diffuse4(int n, const float* __restrict__ in, float* __restrict__ out, float c
         o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
         if (live && z0 + k < n) {
             reinterpret_cast<float4*>(out)[((z0 + k) * plane + yy * n + x) >> 2] = o;
-            if (SUM) acc += ((double)o.x + (double)o.y) + ((double)o.z + (double)o.w);
+            if (SUM) {
+                two_sum_add(acc_s, acc_c, o.x);
+                two_sum_add(acc_s, acc_c, o.y);
+                two_sum_add(acc_s, acc_c, o.z);
+                two_sum_add(acc_s, acc_c, o.w);
+            }
         }
     }
     if (SUM) {
-        acc = block_sum(acc);
+        const double acc = block_sum((double)acc_s + (double)acc_c);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
     }
@@ -254,7 +271,7 @@ k_diffuse4x2(int n, const float* __restrict__ in, float* __restrict__ out, float
         if (lend) l1 = lend_v;
         if (rend) r1 = rend_v;
     };
-    double acc = 0.0;
+    float acc_s = 0.0f, acc_c = 0.0f;
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
         const float4 c = col[k + 2], czm = col[k + 1], czp = col[k + 3], czm2 = col[k], czp2 = col[k + 4];
@@ -288,11 +305,14 @@ k_diffuse4x2(int n, const float* __restrict__ in, float* __restrict__ out, float
         }
         if (live && z0 + k < n) {
             reinterpret_cast<float4*>(out)[((z0 + k) * plane + yy * n + x) >> 2] = make_float4(o[0], o[1], o[2], o[3]);
-            if (SUM) acc += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
+            if (SUM) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) two_sum_add(acc_s, acc_c, o[j]);
+            }
         }
     }
     if (SUM) {
-        acc = block_sum(acc);
+        const double acc = block_sum((double)acc_s + (double)acc_c);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
     }
