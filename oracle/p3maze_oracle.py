@@ -45,6 +45,10 @@ Readings of the paper (each is also listed with its reason in the design notes):
   * Short range: pair terms are truncated at R_c without shifting; all
     periodic images within R_c are included (boxes with R_c <= L < 2 R_c).
 
+The comparison method PMaZe (Secs. 1-2) is here too: the assigned charge q
+itself is the source of the same constraint, Eq. 21 on that potential is the
+whole electrostatic force, and pairs keep only the non-Coulomb term.
+
 Parity pins: see tests/test_oracle_*.py (Madelung constant, brute-force Ewald,
 dense pseudo-inverse, B-spline and smoothing moments, finite-difference forces,
 Newton III).  Functions without an independent pin say so in their docstring.
