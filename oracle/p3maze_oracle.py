@@ -56,6 +56,7 @@ Newton III).  Functions without an independent pin say so in their docstring.
 from __future__ import annotations
 
 import math
+import time
 
 import numpy as np
 from scipy.special import erfc as _erfc, erf as _erf
@@ -346,14 +347,36 @@ def lj_pair(r, eps, sig):
     return e, f_over_r
 
 
+def shift_force(pair_fn, r, r_cut, *args):
+    """A pair term made continuous at the cutoff, the shifted-force form:
+    U_sf(r) = U(r) - U(r_c) + (r - r_c) F(r_c) and F_sf(r) = F(r) - F(r_c),
+    with F = -dU/dr the term's force magnitude (pair_fn returns U and F/r).
+    This is an option for energy-conservation studies; the paper leaves the
+    treatment of the cutoff open and the default truncates without a shift.
+    Returns (U_sf, F_sf / r)."""
+    e, f_over_r = pair_fn(r, *args)
+    e_c, fr_c = pair_fn(np.full_like(r, r_cut), *args)
+    f_c = fr_c * r_cut
+    return e - e_c + (r - r_cut) * f_c, f_over_r - f_c / r
+
+
 def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
-              subset: np.ndarray | None = None, coulomb: bool = True, vdw: bool = True):
+              subset: np.ndarray | None = None, coulomb: bool = True, vdw: bool = True,
+              shift: str = "none"):
     """Short-range forces and per-particle energies by explicit summation over
     every particle j and every periodic image within R_c (Eq. 19 plus the
     non-Coulomb term).  Pairs inside one molecule (nearest image) are skipped.
+    shift='force' applies the shifted-force cutoff (shift_force) to every
+    term; 'none' truncates at R_c.
 
     Returns (F (m,3), e_coul (m,), e_vdw (m,)) for the particles in `subset`
     (default all); per-particle energies carry the factor 1/2 of Eq. 5."""
+    if shift not in ("none", "force"):
+        raise ValueError(shift)
+
+    def term(fn, r, *args):
+        return shift_force(fn, r, r_cut, *args) if shift == "force" else fn(r, *args)
+
     pos, q, types, box = system.pos, system.charge, system.types, system.box
     idx = np.arange(system.n) if subset is None else np.asarray(subset)
     shifts = _image_shifts(box, r_cut)
@@ -383,14 +406,14 @@ def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
             r = np.sqrt(r2[mask])
             fr = np.zeros_like(r)
             if coulomb:
-                e, f = sr_coulomb_pair(r, q[i] * q[mask], sigma, ke)
+                e, f = term(sr_coulomb_pair, r, q[i] * q[mask], sigma, ke)
                 ec[row] += 0.5 * e.sum()
                 fr += f
             if vdw and system.sr_kind == "bmh":
                 t = system.sr_table
                 ti, tj = types[i], types[mask]
-                e, f = bmh_pair(r, t["A"][ti, tj], t["rho"][ti, tj], t["sigma"][ti, tj],
-                                t["C"][ti, tj], t["D"][ti, tj])
+                e, f = term(bmh_pair, r, t["A"][ti, tj], t["rho"][ti, tj], t["sigma"][ti, tj],
+                            t["C"][ti, tj], t["D"][ti, tj])
                 ev[row] += 0.5 * e.sum()
                 fr += f
             elif vdw and system.sr_kind == "lj":
@@ -399,10 +422,92 @@ def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
                 eps = t["eps"][ti, tj]
                 live = eps != 0.0
                 if live.any():
-                    e, f = lj_pair(r[live], eps[live], t["sigma"][ti, tj][live])
+                    e, f = term(lj_pair, r[live], eps[live], t["sigma"][ti, tj][live])
                     ev[row] += 0.5 * e.sum()
                     fr[live] += f
             F[row] += (fr[:, None] * dj).sum(0)
+    return F, ec, ev
+
+
+def sr_forces_cells(system, sigma: float, r_cut: float, ke: float = COULOMB_K, shift: str = "none"):
+    """The short-range sum of sr_forces found through the oracle's own cell
+    list instead of all pairs, O(N): cells have edge >= R_c/2, so every
+    periodic image within R_c of a particle lies in the 5 x 5 x 5 block of
+    cells around its own, each taken once with its explicit image shift (for
+    fewer than 5 cells per axis the block wraps onto other images of the same
+    cells).  Same terms, exclusions and per-particle energies as sr_forces
+    (pinned against it on small systems); used where the all-pairs loop is
+    too slow, e.g. to time the oracle's MD step."""
+    pos, q, types, box = system.pos, system.charge, system.types, system.box
+    mol = system.molecule
+    nc, cell, start, order = cell_list(pos, box, r_cut)
+    N = system.n
+    F = np.zeros((N, 3))
+    ec = np.zeros(N)
+    ev = np.zeros(N)
+
+    def term(fn, r, *args):
+        return shift_force(fn, r, r_cut, *args) if shift == "force" else fn(r, *args)
+
+    rc2 = r_cut * r_cut
+    for cz in range(nc):
+        for cy in range(nc):
+            for cx in range(nc):
+                c = (cz * nc + cy) * nc + cx
+                home = order[start[c]:start[c + 1]]
+                if home.size == 0:
+                    continue
+                js, shifts = [], []
+                for dz in range(-2, 3):
+                    for dy in range(-2, 3):
+                        for dx in range(-2, 3):
+                            u = (cx + dx, cy + dy, cz + dz)
+                            w = [ui % nc for ui in u]
+                            cc = (w[2] * nc + w[1]) * nc + w[0]
+                            j = order[start[cc]:start[cc + 1]]
+                            if j.size:
+                                js.append(j)
+                                img = np.array([(ui // nc) * box for ui in u])  # image of cell u
+                                shifts.append(np.broadcast_to(img, (j.size, 3)))
+                J = np.concatenate(js)
+                Sft = np.concatenate(shifts)
+                for i in home:
+                    d = pos[i][None, :] - (pos[J] + Sft)            # r_i - image of r_j
+                    r2 = (d * d).sum(1)
+                    mask = (r2 < rc2) & ~((J == i) & ~Sft.any(1))
+                    if mol is not None:
+                        same = mask & (mol[J] == mol[i])
+                        if same.any():
+                            d0 = pos[i][None, :] - pos[J[same]]
+                            dn = d0 - box * np.round(d0 / box)
+                            nearest = np.all(np.abs(d[same] - dn) < 1e-9 * box, axis=1)
+                            mask[np.nonzero(same)[0][nearest]] = False
+                    if not mask.any():
+                        continue
+                    Jm = J[mask]
+                    dj = d[mask]
+                    r = np.sqrt(r2[mask])
+                    fr = np.zeros_like(r)
+                    e, f = term(sr_coulomb_pair, r, q[i] * q[Jm], sigma, ke)
+                    ec[i] += 0.5 * e.sum()
+                    fr += f
+                    if system.sr_kind == "bmh":
+                        t = system.sr_table
+                        ti, tj = types[i], types[Jm]
+                        e, f = term(bmh_pair, r, t["A"][ti, tj], t["rho"][ti, tj], t["sigma"][ti, tj],
+                                    t["C"][ti, tj], t["D"][ti, tj])
+                        ev[i] += 0.5 * e.sum()
+                        fr += f
+                    elif system.sr_kind == "lj":
+                        t = system.sr_table
+                        ti, tj = types[i], types[Jm]
+                        eps = t["eps"][ti, tj]
+                        live = eps != 0.0
+                        if live.any():
+                            e, f = term(lj_pair, r[live], eps[live], t["sigma"][ti, tj][live])
+                            ev[i] += 0.5 * e.sum()
+                            fr[live] += f
+                    F[i] += (fr[:, None] * dj).sum(0)
     return F, ec, ev
 
 
@@ -526,20 +631,21 @@ def lr_energy_at(pos, charge, box, alpha, n, ke=COULOMB_K) -> float:
 
 
 def forces_and_energies(system, alpha: float, r_cut: float, n: int, ke: float = COULOMB_K,
-                        order: int = 4, lr_energy: str = "assigned", lr_force: str = "fd"):
+                        order: int = 4, lr_energy: str = "assigned", lr_force: str = "fd",
+                        sr_shift: str = "none"):
     """Total force and energy terms of the P3MaZe decomposition at the exactly
     constrained field phi* (Eqs. 5, 6, 14, 19, 21).
 
     lr_energy='assigned' uses V_LR = 1/2 phi^T q (the reading adopted here);
     'smoothed' evaluates Eq. 14 literally, 1/2 phi^T q^s (kept so that a test
-    can show the Madelung pin rejects it)."""
+    can show the Madelung pin rejects it).  sr_shift as sr_forces' shift."""
     mf = mesh_fields(system, alpha, n, order)
     sigma = mf["sigma"]
     if lr_force == "analytic":
         F_lr = interpolate_lr_forces_analytic(system.pos, system.charge, system.box, n, mf["phi"], ke)
     else:
         F_lr = interpolate_lr_forces(system.pos, system.charge, system.box, n, mf["phi"], ke)
-    F_sr, ec, ev = sr_forces(system, sigma, r_cut, ke)
+    F_sr, ec, ev = sr_forces(system, sigma, r_cut, ke, shift=sr_shift)
     src = mf["q"] if lr_energy == "assigned" else mf["qs"]
     v_lr = 0.5 * ke * float((mf["phi"] * src).sum())
     out = {
@@ -613,6 +719,71 @@ def velocity_verlet_step(system, force, dt: float, force_fn):
     out = force_fn(system)
     system.vel = system.vel + 0.5 * dt * out["F"] * acc
     return out
+
+
+def maze_md_step(system, state: dict, alpha: float, r_cut: float, n: int, dt: float, tol: float,
+                 predictor: int = 1, coarse_max: int = 64, ke: float = COULOMB_K,
+                 timings: dict | None = None) -> int:
+    """One velocity-Verlet MD step with the Mass-Zero field, the plain FP64
+    stepper (Sec. 2; SI Sec. 1 "Numerical integration"; Eqs. 16-17, 20, 21):
+      kick v += dt/2 F/m, drift r += dt v, wrap;
+      q = A(r)Q, q^s = (I + cM)^K q - mean;
+      phi_p = 2 phi^k - phi^{k-1}, sigma_p = (h/4pi) M phi_p + q^s (Eq. 17);
+      y0 from the multiplier history (order `predictor`, fewer while the
+      history is short), V-cycles on M y = sigma_p to max|M y - sigma_p| <= tol
+      (Eq. 20, the plain multigrid of mg_correction_solve);
+      phi^{k+1} = phi_p - (4pi/h) y*;
+      F = -ke Q W . D phi^{k+1} (Eq. 21) + short-range forces (cell list);
+      kick.
+    state holds 'F', 'phi' (phi^k), 'phi_prev' (phi^{k-1}) and 'y' (the
+    multiplier history, newest first); it is updated in place, and the
+    system's positions and velocities advance.  Systems without molecules.
+    If `timings` is given, the seconds spent in the short-range sum are
+    stored under 'sr'.  Returns the V-cycles of the solve."""
+    box = system.box
+    h = box / n
+    acc = ACCEL / system.mass[:, None]
+    system.vel = system.vel + 0.5 * dt * state["F"] * acc
+    system.pos = wrap(system.pos + dt * system.vel, box)
+    sigma = sigma_of_alpha(alpha)
+    K, c = smoothing_schedule(sigma, h)
+    q = assign_charges(system.pos, system.charge, box, n)
+    qs = smooth(q, K, c)
+    qs = qs - qs.mean()
+    phi_p = 2.0 * state["phi"] - state["phi_prev"]
+    sigma_p = h / (4.0 * math.pi) * laplacian7(phi_p) + qs
+    hist = state["y"]
+    order = min(predictor, len(hist))
+    if order == 0:
+        y0 = np.zeros_like(sigma_p)
+    elif order == 1:
+        y0 = hist[0]
+    elif order == 2:
+        y0 = 2.0 * hist[0] - hist[1]
+    else:
+        y0 = 3.0 * hist[0] - 3.0 * hist[1] + hist[2]
+    y, iters, _ = mg_correction_solve(sigma_p, y0, tol, mg_levels(n, coarse_max))
+    phi = phi_p - (4.0 * math.pi / h) * y
+    F_lr = interpolate_lr_forces(system.pos, system.charge, box, n, phi, ke)
+    t_sr = time.perf_counter()
+    F_sr, _, _ = sr_forces_cells(system, sigma, r_cut, ke)
+    if timings is not None:
+        timings["sr"] = time.perf_counter() - t_sr
+    state["F"] = F_lr + F_sr
+    state["phi_prev"], state["phi"] = state["phi"], phi
+    state["y"] = [y] + hist[:2]
+    system.vel = system.vel + 0.5 * dt * state["F"] * acc
+    return iters
+
+
+def maze_initial_state(system, alpha: float, r_cut: float, n: int, ke: float = COULOMB_K) -> dict:
+    """Stepper state at the start (reading A7): the exactly constrained field
+    at the initial positions as both phi^0 and phi^{-1}, an empty multiplier
+    history, and the forces there."""
+    mf = mesh_fields(system, alpha, n)
+    F = interpolate_lr_forces(system.pos, system.charge, system.box, n, mf["phi"], ke)
+    F = F + sr_forces_cells(system, mf["sigma"], r_cut, ke)[0]
+    return {"F": F, "phi": mf["phi"], "phi_prev": mf["phi"].copy(), "y": []}
 
 
 # ---------------------------------------------------------------------------

@@ -209,6 +209,100 @@ def test_sr_forces_are_minus_gradient_of_sr_energy():
     _fd_check(s, energy, F)
 
 
+def test_lj_pair_closed_form_zero_minimum_and_force():
+    """Lennard-Jones (SPC/Fw O-O term, Table S1): U(sigma) = 0, the minimum sits
+    at r = 2^(1/6) sigma with depth -eps (textbook values), and the returned
+    force is -dU/dr (central differences of the energy, step 1e-6 A)."""
+    eps, sig = 0.1554253, 3.165492
+    e0, f0 = O.lj_pair(np.array([sig]), eps, sig)
+    assert e0[0] == pytest.approx(0.0, abs=1e-15)
+    rmin = 2.0 ** (1.0 / 6.0) * sig
+    e1, f1 = O.lj_pair(np.array([rmin]), eps, sig)
+    assert e1[0] == pytest.approx(-eps, rel=1e-14)
+    assert abs(f1[0]) < 1e-12
+    r = np.linspace(2.8, 9.0, 23)
+    h = 1e-6
+    _, fr = O.lj_pair(r, eps, sig)
+    fd = -(O.lj_pair(r + h, eps, sig)[0] - O.lj_pair(r - h, eps, sig)[0]) / (2 * h)
+    np.testing.assert_allclose(fr * r, fd, rtol=1e-7, atol=1e-12)
+
+
+def test_bmh_pair_force_is_minus_derivative():
+    t = S.nacl_melt(2, 10.0, seed=0).sr_table
+    r = np.linspace(2.0, 9.0, 15)
+    h = 1e-6
+    for i, j in ((0, 0), (0, 1), (1, 1)):
+        args = (t["A"][i, j], t["rho"][i, j], t["sigma"][i, j], t["C"][i, j], t["D"][i, j])
+        _, fr = O.bmh_pair(r, *args)
+        fd = -(O.bmh_pair(r + h, *args)[0] - O.bmh_pair(r - h, *args)[0]) / (2 * h)
+        np.testing.assert_allclose(fr * r, fd, rtol=1e-7, atol=1e-10)
+
+
+def test_sr_forces_with_lj_pairs_are_minus_gradient():
+    """Two SPC/Fw molecules in a small box with their oxygens within R_c: the
+    short-range force (erfc Coulomb + O-O Lennard-Jones, intramolecular pairs
+    excluded) is minus the gradient of the short-range energy."""
+    w = S.spcfw_water(2, 8.0, seed=4)
+    o = np.nonzero(w.charge < 0)[0]
+    d = w.pos[o[0]] - w.pos[o[1]]
+    d -= w.box * np.round(d / w.box)
+    assert np.linalg.norm(d) < 6.0
+    sigma = O.sigma_of_alpha(0.30)
+    rc = 6.0
+
+    def energy(sys_):
+        _, ec, ev = O.sr_forces(sys_, sigma, rc)
+        return ec.sum() + ev.sum()
+
+    F, _, ev = O.sr_forces(w, sigma, rc)
+    assert abs(ev.sum()) > 1e-4                 # the LJ term is present
+    assert np.abs(F.sum(0)).max() < 1e-9 * np.abs(F).max()
+    _fd_check(w, energy, F, rtol=1e-6)
+
+
+def test_shifted_force_cutoff_is_continuous_and_conservative():
+    """The shifted-force option: every term and its force vanish at R_c, the
+    energy approaches zero quadratically (a wrong linear term would leave a
+    first-order step), and the summed forces are minus the gradient of the
+    summed shifted energies (BMH melt and SPC/Fw with LJ)."""
+    sigma = O.sigma_of_alpha(0.30)
+    rc = 9.0
+    t = S.nacl_melt(2, 10.0, seed=0).sr_table
+    w = S.spcfw_params()
+    cases = [(O.sr_coulomb_pair, (np.float64(-1.0), sigma, 332.0637)),
+             (O.bmh_pair, (t["A"][0, 1], t["rho"][0, 1], t["sigma"][0, 1], t["C"][0, 1], t["D"][0, 1])),
+             (O.lj_pair, (w["eps_oo"], w["sigma_oo"]))]
+    for fn, args in cases:
+        e, fr = O.shift_force(fn, np.array([rc]), rc, *args)
+        assert e[0] == 0.0 and fr[0] == 0.0
+        d = np.array([1e-2, 1e-3])
+        e, _ = O.shift_force(fn, rc - d, rc, *args)
+        scale = abs(fn(np.array([rc]), *args)[1][0]) * rc   # |F(r_c)|
+        assert np.all(np.abs(e) < 10 * scale * d)              # no first-order step ...
+        assert abs(e[1]) < 0.02 * abs(e[0]) + 1e-18           # ... it falls as d^2
+        e_plain, _ = fn(rc - d, *args)
+        assert np.any(np.abs(e_plain - e) > 0)                 # the shift is applied
+    s = S.nacl_melt(24, 11.0, seed=3, dmin=2.0)
+
+    def energy(sys_):
+        _, ec, ev = O.sr_forces(sys_, sigma, rc, shift="force")
+        return ec.sum() + ev.sum()
+
+    F, _, _ = O.sr_forces(s, sigma, rc, shift="force")
+    F0, _, _ = O.sr_forces(s, sigma, rc)
+    assert np.abs(F - F0).max() > 1e-8 * np.abs(F0).max()
+    assert np.abs(F.sum(0)).max() < 1e-9 * np.abs(F).max()
+    _fd_check(s, energy, F)
+    ww = S.spcfw_water(2, 8.0, seed=4)
+
+    def energy_w(sys_):
+        _, ec, ev = O.sr_forces(sys_, sigma, 6.0, shift="force")
+        return ec.sum() + ev.sum()
+
+    Fw, _, _ = O.sr_forces(ww, sigma, 6.0, shift="force")
+    _fd_check(ww, energy_w, Fw, rtol=1e-6)
+
+
 def test_spcfw_intramolecular_forces_are_minus_gradient():
     w = S.spcfw_water(8, 9.0, seed=2)
     sigma = O.sigma_of_alpha(0.30)
@@ -408,3 +502,56 @@ def test_pmaze_rejects_molecules():
     w = S.spcfw_water(8, 6.3, seed=2)
     with pytest.raises(ValueError):
         O.pmaze_forces_and_energies(w, 3.0, 16)
+
+
+# ---------------------------------------------------------------- O(N) forms used for timing
+@pytest.mark.parametrize("kind", ["nacl", "nacl_small_box", "water", "nacl_shift"])
+def test_cell_list_sr_sum_equals_all_pairs(kind):
+    """sr_forces_cells finds the same pairs and images as the all-pairs
+    definition sr_forces: forces and per-particle energies agree to rounding
+    (a box below 2 R_c, molecules with excluded partners, the shifted form)."""
+    sigma = O.sigma_of_alpha(0.30)
+    shift = "none"
+    if kind == "nacl":
+        s, rc = S.nacl_melt(200, 25.2, seed=2), 9.0
+    elif kind == "nacl_small_box":
+        s, rc = S.nacl_melt(40, 11.5, seed=3), 9.0          # 2 cells per axis, L < 2 R_c
+    elif kind == "water":
+        s, rc = S.spcfw_water(27, 9.4, seed=5), 6.0
+    else:
+        s, rc, shift = S.nacl_melt(120, 21.0, seed=4), 9.0, "force"
+    F, ec, ev = O.sr_forces(s, sigma, rc, shift=shift)
+    Fc, ecc, evc = O.sr_forces_cells(s, sigma, rc, shift=shift)
+    np.testing.assert_allclose(Fc, F, rtol=0, atol=1e-10 * np.abs(F).max())
+    np.testing.assert_allclose(ecc, ec, rtol=0, atol=1e-10 * np.abs(ec).max())
+    np.testing.assert_allclose(evc, ev, rtol=0, atol=1e-10 * max(np.abs(ev).max(), 1e-30))
+
+
+def test_mass_zero_stepper_tracks_the_exactly_constrained_field():
+    """maze_md_step (the plain FP64 Mass-Zero MD step) keeps the field on the
+    constraint: after every step max|(h/4pi) M phi + q^s| <= tol at the new
+    positions, and the trajectory equals velocity Verlet driven by the exact
+    (FFT-constrained) forces up to the solver tolerance's effect."""
+    s = S.nacl_melt(64, 14.0, seed=6)
+    n, alpha, rc, dt, tol = 16, 0.45, 6.5, 1.0, 1e-10
+    a = S.System(pos=O.wrap(s.pos, s.box), vel=s.vel.copy(), charge=s.charge, mass=s.mass, types=s.types,
+                 box=s.box, sr_kind=s.sr_kind, sr_table=s.sr_table)
+    b = S.System(pos=a.pos.copy(), vel=a.vel.copy(), charge=s.charge, mass=s.mass, types=s.types,
+                 box=s.box, sr_kind=s.sr_kind, sr_table=s.sr_table)
+    state = O.maze_initial_state(a, alpha, rc, n)
+
+    def exact(sys_):
+        return O.forces_and_energies(sys_, alpha, rc, n)
+
+    Fb = exact(b)["F"]
+    iters = []
+    for _ in range(5):
+        iters.append(O.maze_md_step(a, state, alpha, rc, n, dt, tol))
+        out = O.velocity_verlet_step(b, Fb, dt, exact)
+        Fb = out["F"]
+        mf = O.mesh_fields(a, alpha, n)
+        res = np.abs(mf["h"] / (4 * np.pi) * O.laplacian7(state["phi"]) + mf["qs"]).max()
+        assert res <= tol * (1 + 1e-6)
+    np.testing.assert_allclose(a.pos, b.pos, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(state["F"], Fb, rtol=0, atol=1e-6 * np.abs(Fb).max())
+    assert max(iters) >= 1
