@@ -94,6 +94,13 @@ extern "C" {
                                        V_LR = 1/2 ke phi^T q (energy conserving), not the
                                        paper's force; momentum conserved to discretisation error */
 
+/* Short-range truncation at r_cut (reading A13 leaves the cutoff unshifted) */
+#define P3MAZE_SR_TRUNCATE    0  /* pair forces and energies cut off at r_cut, unshifted (default) */
+#define P3MAZE_SR_SHIFT_FORCE 1  /* shifted force: every pair term (erfc Coulomb and non-Coulomb)
+                                    becomes U(r) - U(r_cut) + (r - r_cut) F(r_cut) with force
+                                    F(r) - F(r_cut), so energy and force are continuous at r_cut;
+                                    an option for energy-conservation studies, not the paper's */
+
 #define P3MAZE_SR_NONE 0  /* Coulomb only                                               */
 #define P3MAZE_SR_BMH  1  /* Born-Huggins-Mayer: A exp((s-r)/rho) - C/r^6 - D/r^8         */
 #define P3MAZE_SR_LJ   2  /* Lennard-Jones: 4 eps ((s/r)^12 - (s/r)^6), pairs with eps=0 skipped */
@@ -166,6 +173,7 @@ typedef struct {
                                (separable Hartley transforms); 0 -> 64 (mixed), 16 (FP64) */
     int32_t lr_force;       /* P3MAZE_LR_FORCE_FD (0, the paper's Eq. 21) or
                                P3MAZE_LR_FORCE_ANALYTIC                                    */
+    int32_t sr_shift;       /* P3MAZE_SR_TRUNCATE (0) or P3MAZE_SR_SHIFT_FORCE               */
 } p3maze_params;
 
 typedef struct {
@@ -288,6 +296,16 @@ int p3maze_step_host(p3maze_ctx *ctx, const double *pos_in, const double *vel_in
  * the same initialisation as p3maze_init (after an external state change).   */
 int p3maze_reinit(p3maze_ctx *ctx);
 
+/* Relaxation before measurements that need a settled melt (the energy-drift
+ * reading of the random d_min = 2 A starts, whose close like-charge pairs
+ * heat the system): nsteps MD steps as p3maze_step, each followed by a
+ * rescaling of all velocities on the device so that sum m v^2 equals
+ * (3n - 3) k_B temperature_K (kinetic temperature with the net momentum
+ * removed).  Not part of the paper's NVE method; it changes the state like
+ * any steps.  Waits at the end.  Errors: INVALID (nsteps < 0 or
+ * temperature_K <= 0), and as p3maze_step.                                     */
+int p3maze_equilibrate(p3maze_ctx *ctx, int32_t nsteps, double temperature_K);
+
 /* Device memory (bytes requested from cudaMalloc) that p3maze_init would
  * allocate for these parameters; host-only, no CUDA call.  For admission
  * control by memory (the allocator rounds each array up, add a margin).      */
@@ -323,8 +341,8 @@ int p3maze_set_state(p3maze_ctx *ctx, const double *pos, const double *vel);
  * correction history, the last residual, the step count and the solver
  * tallies -- and p3maze_load_state restores it into a context created with
  * the same parameters (INVALID otherwise), so that stepping continues from
- * exactly the saved state.  (Later steps differ from an uninterrupted run
- * only in the summation order of atomic charge assignment.)  Both wait for
+ * exactly the saved state: later steps repeat an uninterrupted run bit for
+ * bit (every kernel of a step is deterministic).  Both wait for
  * the context's stream.                                                        */
 int p3maze_state_bytes(p3maze_ctx *ctx, size_t *out);
 int p3maze_save_state(p3maze_ctx *ctx, void *buf, size_t bytes);
@@ -366,14 +384,14 @@ int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
 
 /* Diffusion smoothing of a caller-owned mesh that allocates nothing.
  * The paper has no counterpart: this call exists for callers that cannot
- * allocate device memory when they need the smoothing -- code recording a
- * CUDA stream capture (allocation is not allowed there), code running under a
- * fixed device-memory budget owned by a host framework, or callers that must
- * not grow their footprint after start-up.
+ * allocate device memory when they need the smoothing -- code running under a
+ * fixed device-memory budget owned by a host framework that makes every
+ * allocation itself, or long-running services that reserve their memory at
+ * start-up and must not grow their footprint afterwards.
  *   q     device, [mesh^3] FP64 input (x fastest), read only
  *   qs    device, [mesh^3] FP64 output: (I + coeff M)^steps q with its mean
  *         removed -- the same q^s the context computes (P3MAZE_MESH_QS) for
- *         steps = K, coeff = c of p3maze_get_stats; must not alias q
+ *         steps = K, coeff = c of p3maze_get_stats; must not overlap q
  *   mesh  4..64 points per axis; larger meshes are rejected (INVALID)
  *   steps >= 0; coeff in (0, 1/6] when steps > 0
  *   cuda_stream  cudaStream_t the work is queued on (NULL = legacy stream)
@@ -382,10 +400,13 @@ int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
  * loads this library until the process exits.  No cudaMalloc, cudaFree or
  * allocating library routine is called.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device
- * share the array and keep nothing from earlier calls: calls that overlap on
- * the GPU (different streams, or host threads queueing concurrently) race on
- * it and must be ordered by the caller.  Returns 0 or INVALID/CUDA; the
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process, so calls must not span a cudaDeviceReset of the
+ * device.  q and qs must not overlap each other or the scratch array
+ * (INVALID).  All calls on a device share the array and keep nothing from
+ * earlier calls: calls that overlap on the GPU (different streams, or host
+ * threads queueing concurrently) race on it and must be ordered by the
+ * caller.  Returns 0 or INVALID/CUDA; the
  * message is p3maze_last_error(NULL).  Asynchronous: outputs are ready when
  * the stream reaches this point.                                              */
 int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t steps, double coeff,

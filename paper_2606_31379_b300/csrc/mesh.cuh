@@ -20,58 +20,274 @@ __device__ __forceinline__ T nb6(const T* __restrict__ f, int x, int y, int z, i
 }
 
 // ---------------------------------------------------------------- assignment
-// q_n += Q_a W(u_a - n): cubic B-spline charge assignment (Sec. 2), one thread
-// per particle in cell order, 64 atomic adds.
+// q_n = sum_a Q_a W(u_a - n): cubic B-spline charge assignment (Sec. 2,
+// "charge assignment and smoothing"), deterministic and without atomics.
+//
+// A block owns a tile of kSpTX x kSpTY x kSpTZ mesh points and writes every
+// point of it exactly once (no memset of q, no global atomics).  A particle
+// at mesh coordinate u reaches the nodes floor(u)-1 .. floor(u)+2 per axis, so
+// the tile [o, o+e) is reached only from u in [o-2, o+e+1): the block reads
+// the cell-sorted particles of the cells covering that range (a superset:
+// cell coordinate = u nc/n) in passes of kSpCap, keeps those with a node in
+// the tile and sorts them stably by their first z node (a counting sort on
+// 19 keys).  Warp w owns the tile planes 2w and 2w+1: it walks the particles
+// whose z nodes reach those planes, in sorted order, one particle per warp
+// instruction -- lane = (x node, y node, plane) -- and adds into its own
+// planes of the shared-memory tile with plain loads and stores.  Every point
+// is owned by one warp and receives its contributions in a fixed order, so
+// the result is the same on every run, alone or in a batch.  The particles'
+// tile-local nodes are precomputed per axis (-1 outside the tile), so
+// periodic wrap needs no arithmetic in the accumulation; tiles of small
+// meshes whose z nodes can alias (e + 3 > n) are walked in full by every warp.
+constexpr int kSpTX = 32, kSpTY = 16, kSpTZ = 16;   // tile (8192 points)
+constexpr int kSpRowP = kSpTX + 4;                  // padded row: the 4 y rows of a particle in distinct banks
+constexpr int kSpPlaneP = kSpRowP * kSpTY + 16;     // padded plane: a warp's two planes in distinct banks
+constexpr int kSpThreads = 256;                     // 8 warps x 2 planes
+constexpr int kSpCap = 256;                         // candidate particles per pass (one per thread)
+constexpr int kSpRows = 128;                        // cell rows per pass (2 segments each)
+constexpr int kSpKeys = kSpTZ + 3;                  // first z node in [-3, kSpTZ - 1]
+
 template <typename T>
-__global__ void __launch_bounds__(P3_THREADS)
-k_spread(int np, const PQ* __restrict__ xq, int n, double inv_h, T* __restrict__ q) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= np) return;
-    const PQ p = xq[s];
-    double wx[4], wy[4], wz[4];
-    const int bx = bspline_axis(p.x, inv_h, n, wx);
-    const int by = bspline_axis(p.y, inv_h, n, wy);
-    const int bz = bspline_axis(p.z, inv_h, n, wz);
+struct SpEntry {
+    int loc[3];   // per axis, byte k: tile-local node of weight k (signed), -1 outside the tile
+    T w[3][4];    // weights; Q folded into the z weights
+};
+
+template <typename T>
+inline size_t spread_smem_bytes() {
+    return sizeof(T) * kSpPlaneP * kSpTZ + sizeof(SpEntry<T>) * kSpCap + sizeof(int) * 4 * kSpRows;
+}
+
+__device__ __forceinline__ int sp_loc(int packed, int k) { return (int)(signed char)(packed >> (8 * k)); }
+
+__device__ __forceinline__ int imod(int v, int m) {
+    const int r = v % m;
+    return r < 0 ? r + m : r;
+}
+
+// Exclusive scan of one int per thread over a 1-D block of kSpThreads; the
+// total is returned in *total (all threads).
+__device__ __forceinline__ int sp_block_excl_scan(int v, int* total) {
+    __shared__ int wtot[kSpThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int iz = wrap_idx(bz + c, n);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int iy = wrap_idx(by + b, n);
-            const double wyz = p.w * wy[b] * wz[c];
-            T* row = q + ((int64_t)iz * n + iy) * n;
+    for (int w = 0; w < kSpThreads / 32; ++w) {
+        const int t = wtot[w];
+        before += w < wid ? t : 0;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
+
+// Base node (wrapped) and weights of one particle: FP32 from the mesh
+// coordinates of the mixed path, FP64 from the cell-ordered positions.
+__device__ __forceinline__ void sp_particle(const MeshPt* __restrict__ src, int s, double, int, int b[3],
+                                           float w[3][4]) {
+    const MeshPt p = src[s];
+    b[0] = p.bx;
+    b[1] = p.by;
+    b[2] = p.bz;
+    bspline4f(p.tx, w[0]);
+    bspline4f(p.ty, w[1]);
+    bspline4f(p.tz, w[2]);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) atomicAdd(row + wrap_idx(bx + a, n), (T)(wyz * wx[a]));
+    for (int k = 0; k < 4; ++k) w[2][k] *= p.q;
+}
+__device__ __forceinline__ void sp_particle(const PQ* __restrict__ src, int s, double inv_h, int n, int b[3],
+                                           double w[3][4]) {
+    const PQ p = src[s];
+    b[0] = bspline_axis(p.x, inv_h, n, w[0]);
+    b[1] = bspline_axis(p.y, inv_h, n, w[1]);
+    b[2] = bspline_axis(p.z, inv_h, n, w[2]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[2][k] *= p.w;
+}
+
+// The x segments (one, or two when the cell range wraps) of candidate cell
+// row r (y, z cells) in cell order.
+__device__ __forceinline__ void sp_row(const int* __restrict__ start, int nc, const int* cl, const int* nn, int r,
+                                       int& b0, int& l0, int& b1, int& l1) {
+    const int cy = imod(cl[1] + r % nn[1], nc), cz = imod(cl[2] + r / nn[1], nc);
+    const int rb = (cz * nc + cy) * nc;
+    const int x0 = imod(cl[0], nc);
+    const int n0 = min(nn[0], nc - x0);
+    b0 = start[rb + x0];
+    l0 = start[rb + x0 + n0] - b0;
+    b1 = start[rb];
+    l1 = nn[0] > n0 ? start[rb + nn[0] - n0] - b1 : 0;
+}
+
+template <typename T, typename Src, bool VEC>
+__global__ void __launch_bounds__(kSpThreads)
+k_spread_tile(int n, int nc, const int* __restrict__ start, const Src* __restrict__ src, double inv_h,
+              T* __restrict__ q) {
+    extern __shared__ __align__(16) unsigned char sp_raw[];
+    T* acc = reinterpret_cast<T*>(sp_raw);
+    SpEntry<T>* ent = reinterpret_cast<SpEntry<T>*>(acc + kSpPlaneP * kSpTZ);
+    int* seg_beg = reinterpret_cast<int*>(ent + kSpCap);
+    int* seg_pre = seg_beg + 2 * kSpRows;
+    __shared__ int s_cl[3], s_nn[3];
+    __shared__ int whist[kSpThreads / 32][kSpKeys], wpre[kSpThreads / 32][kSpKeys], kstart[kSpKeys + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int o[3] = {(int)blockIdx.x * kSpTX, (int)blockIdx.y * kSpTY, (int)blockIdx.z * kSpTZ};
+    const int ext[3] = {min(kSpTX, n - o[0]), min(kSpTY, n - o[1]), min(kSpTZ, n - o[2])};
+    const bool alias_z = ext[2] + 3 > n;  // z nodes of one particle may reach the tile twice over the wrap
+    for (int i = tid; i < kSpPlaneP * kSpTZ; i += kSpThreads) acc[i] = (T)0;
+    if (tid < 3) {
+        const double k = (double)nc / (double)n;
+        const int od = tid == 0 ? o[0] : tid == 1 ? o[1] : o[2];  // no dynamic indexing (local memory)
+        const int ed = tid == 0 ? ext[0] : tid == 1 ? ext[1] : ext[2];
+        int lo = (int)floor((double)(od - 2) * k - 1e-9);
+        const int hi = (int)floor((double)(od + ed + 1) * k + 1e-9);
+        int cnt = hi - lo + 1;
+        if (cnt >= nc) {
+            lo = 0;
+            cnt = nc;
+        }
+        s_cl[tid] = lo;
+        s_nn[tid] = cnt;
+    }
+    pdl_wait();  // start[] and the particle copies come from the cell-list kernels
+    pdl_trigger();
+    __syncthreads();
+    const int nrows = s_nn[1] * s_nn[2];
+    // lane roles in the accumulation: x node kx, y node ky, plane of the warp
+    const int kx = lane & 3, ky = (lane >> 2) & 3, pl = 2 * warp + (lane >> 4);
+    for (int row0 = 0; row0 < nrows; row0 += kSpRows) {
+        const int nr = min(kSpRows, nrows - row0);
+        int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
+        if (tid < nr) sp_row(start, nc, s_cl, s_nn, row0 + tid, b0, l0, b1, l1);
+        int total = 0;
+        const int ex0 = sp_block_excl_scan(l0 + l1, &total);  // also orders the previous pass's reads
+        if (tid < kSpRows) {
+            seg_beg[2 * tid] = b0;
+            seg_beg[2 * tid + 1] = b1;
+            seg_pre[2 * tid] = ex0;
+            seg_pre[2 * tid + 1] = ex0 + l0;
+        }
+        for (int p0 = 0; p0 < total; p0 += kSpCap) {
+            for (int i = tid; i < (kSpThreads / 32) * kSpKeys; i += kSpThreads) (&whist[0][0])[i] = 0;
+            __syncthreads();
+            // stage 1: one candidate per thread -> tile-local nodes, weights, key
+            const int f = p0 + tid;
+            int key = -1;
+            int loc[3] = {0, 0, 0};
+            T w[3][4];
+            if (f < total) {
+                int lo = 0, hi = 2 * nr - 1;  // last segment starting at or before f
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (seg_pre[mid] <= f) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int s = seg_beg[lo] + (f - seg_pre[lo]);
+                int b[3];
+                sp_particle(src, s, inv_h, n, b, w);
+                bool hit = true;
+                int first_z = -1;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    bool any = false;
+                    unsigned packed = 0;
+#pragma unroll
+                    for (int k = 3; k >= 0; --k) {
+                        int v = b[d] + k;
+                        if (v >= n) v -= n;
+                        const int dl = v - o[d];
+                        const bool in = (unsigned)dl < (unsigned)ext[d];
+                        packed |= (unsigned)(in ? dl : 0xff) << (8 * k);
+                        any |= in;
+                        if (d == 2 && in) first_z = dl - k;  // the node of weight 0 (may lie below the tile)
+                    }
+                    loc[d] = (int)packed;
+                    hit &= any;
+                }
+                if (hit) key = alias_z ? 0 : first_z + 3;
+            }
+            // stable counting sort of this pass's hits by key
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            if (key >= 0 && rank == 0) whist[warp][key] = __popc(peers);
+            __syncthreads();
+            if (tid < kSpKeys) {
+                int run = 0;
+#pragma unroll
+                for (int ww = 0; ww < kSpThreads / 32; ++ww) {
+                    wpre[ww][tid] = run;
+                    run += whist[ww][tid];
+                }
+                whist[0][tid] = run;  // key total (whist is rebuilt next pass)
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int k = 0; k < kSpKeys; ++k) {
+                    kstart[k] = run;
+                    run += whist[0][k];
+                }
+                kstart[kSpKeys] = run;
+            }
+            __syncthreads();
+            if (key >= 0) {
+                SpEntry<T>& E = ent[kstart[key] + wpre[warp][key] + rank];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    E.loc[d] = loc[d];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) E.w[d][k] = w[d][k];
+                }
+            }
+            __syncthreads();
+            // stage 2: warp w adds the particles reaching its planes 2w, 2w+1
+            // (first z node in [2w-3, 2w+1]) in sorted order
+            const int e0 = alias_z ? 0 : kstart[2 * warp];
+            const int e1 = alias_z ? kstart[kSpKeys] : kstart[min(2 * warp + 5, kSpKeys)];
+            if (2 * warp < ext[2]) {
+                for (int e = e0; e < e1; ++e) {
+                    const SpEntry<T>& E = ent[e];
+                    const int lx = sp_loc(E.loc[0], kx), ly = sp_loc(E.loc[1], ky);
+                    const unsigned mz = __vcmpeq4((unsigned)E.loc[2], 0x01010101u * (unsigned)pl);
+                    if (lx >= 0 && ly >= 0 && mz != 0u) {
+                        const int kz = (__ffs(mz) - 1) >> 3;
+                        T* a = acc + pl * kSpPlaneP + ly * kSpRowP + lx;
+                        *a += E.w[0][kx] * E.w[1][ky] * E.w[2][kz];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // every tile point written once
+    if constexpr (VEC) {
+        // n % 4 == 0: float4 rows (the tile origin is a multiple of 32)
+        for (int i = tid; i < kSpTZ * kSpTY * (kSpTX / 4); i += kSpThreads) {
+            const int x4 = i % (kSpTX / 4), ly = (i / (kSpTX / 4)) % kSpTY, lz = i / ((kSpTX / 4) * kSpTY);
+            if (4 * x4 >= ext[0] || ly >= ext[1] || lz >= ext[2]) continue;
+            const float4 v = *reinterpret_cast<const float4*>(acc + lz * kSpPlaneP + ly * kSpRowP + 4 * x4);
+            *reinterpret_cast<float4*>(q + ((int64_t)(o[2] + lz) * n + (o[1] + ly)) * n + o[0] + 4 * x4) = v;
+        }
+    } else {
+        for (int i = tid; i < kSpTZ * kSpTY * kSpTX; i += kSpThreads) {
+            const int lx = i % kSpTX, ly = (i / kSpTX) % kSpTY, lz = i / (kSpTX * kSpTY);
+            if (lx >= ext[0] || ly >= ext[1] || lz >= ext[2]) continue;
+            q[((int64_t)(o[2] + lz) * n + (o[1] + ly)) * n + o[0] + lx] = acc[lz * kSpPlaneP + ly * kSpRowP + lx];
         }
     }
 }
 
-// FP32 assignment from precomputed mesh coordinates, TPP threads per
-// particle (TPP divides 16): each thread adds the 4-point x rows (b, c) =
-// (r % 4, r / 4) for r = part, part + TPP, ... of the 4x4x4 stencil.
-template <int TPP>
-__global__ void __launch_bounds__(P3_THREADS)
-k_spread_mp(int np, const MeshPt* __restrict__ mp, int n, float* __restrict__ q) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(t / TPP), part = (int)(t % TPP);
-    if (s >= np) return;
-    const MeshPt p = mp[s];
-    float wx[4], wy[4], wz[4];
-    bspline4f(p.tx, wx);
-    bspline4f(p.ty, wy);
-    bspline4f(p.tz, wz);
-    int ix[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) ix[a] = wrap_idx(p.bx + a, n);
-#pragma unroll
-    for (int r = part; r < 16; r += TPP) {
-        const int b = r & 3, c = r >> 2;
-        const int iy = wrap_idx(p.by + b, n), iz = wrap_idx(p.bz + c, n);
-        const float wyz = p.q * wy[b] * wz[c];
-        float* row = q + ((int64_t)iz * n + iy) * n;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) atomicAdd(row + ix[a], wyz * wx[a]);
-    }
+inline dim3 spread_grid(int n) {
+    return dim3((n + kSpTX - 1) / kSpTX, (n + kSpTY - 1) / kSpTY, (n + kSpTZ - 1) / kSpTZ);
 }
 
 // ---------------------------------------------------------------- 3D launch
@@ -438,6 +654,51 @@ static __global__ void k_sum_final(int nb, const double* __restrict__ partial, d
     if (threadIdx.x == 0) out[0] = acc;
 }
 
+// ---------------------------------------------------------------- gauge mode
+// M annihilates constants, so the correction y (z in fixed point) of a solve
+// is defined up to a constant, and so is the potential (reading A5: keep
+// mean(y) = 0).  The multiplier predictor extrapolates the history -- order
+// 3 is a triple integrator of whatever constant the V-cycles leave behind --
+// so a constant that is not removed grows with the step count until it
+// swamps the precision of phi.  Each history buffer therefore carries its
+// own sum in one extra slot, written by the field-update kernel that stores
+// it, and the predictor removes the mean of its guess: a constant shift of
+// the guess leaves every residual and every force unchanged.
+//
+// Block sums of v, reduced to *out by the block that finishes last (fixed
+// order over the partials, so the sum is the same on every run).
+__device__ __forceinline__ void sum_last_block(double v, double* __restrict__ partial, unsigned* __restrict__ arrive,
+                                               double* __restrict__ out) {
+    __shared__ int last_s;
+    const double bs = block_sum(v);
+    const int nb = gridDim.x;
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = bs;
+        __threadfence();
+        last_s = atomicAdd(arrive, 1u) == (unsigned)(nb - 1);
+    }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(partial + i);
+    a = block_sum(a);
+    if (threadIdx.x == 0) {
+        *arrive = 0u;
+        *out = a;
+    }
+}
+
+// Mean of the order-`order` guess from the sums of the history buffers
+// (slot m of each), per point.
+__device__ __forceinline__ double guess_mean(int order, const double* __restrict__ y1, const double* __restrict__ y2,
+                                             const double* __restrict__ y3, int64_t m) {
+    if (order == 1) return y1[m] / (double)m;
+    if (order == 2) return (2.0 * y1[m] - y2[m]) / (double)m;
+    if (order == 3) return (3.0 * y1[m] - 3.0 * y2[m] + y3[m]) / (double)m;
+    return 0.0;
+}
+
 // ---------------------------------------------------------------- Mass-Zero
 // psi = (h/4pi) M phi is carried from step to step (it follows from the final
 // FP64 residual: (h/4pi) M phi^{k+1} = sigma_p - M y* - q^s), so the
@@ -445,7 +706,7 @@ static __global__ void k_sum_final(int nb, const double* __restrict__ partial, d
 //   sigma_p = (h/4pi) M (2 phi^k - phi^{k-1}) + q^s - mean      (Eq. 17)
 //           = 2 psi^k - psi^{k-1} + q^s - mean(q^s)
 // and the multiplier guess y0 (Sec. 3.3): order 0 -> 0, 1 -> y^k,
-// 2 -> 2y^k - y^{k-1}, 3 -> 3y^k - 3y^{k-1} + y^{k-2}.
+// 2 -> 2y^k - y^{k-1}, 3 -> 3y^k - 3y^{k-1} + y^{k-2}, its mean removed.
 template <typename T>
 __global__ void __launch_bounds__(P3_THREADS)
 k_predict(int64_t m, const double* __restrict__ psik, const double* __restrict__ psikm1,
@@ -460,7 +721,7 @@ k_predict(int64_t m, const double* __restrict__ psik, const double* __restrict__
     if (order == 1) g = y1[i];
     else if (order == 2) g = 2.0 * y1[i] - y2[i];
     else if (order == 3) g = 3.0 * y1[i] - 3.0 * y2[i] + y3[i];
-    y0[i] = g;
+    y0[i] = g - guess_mean(order, y1, y2, y3, m);  // the gauge mode removed
 }
 
 // Fine-level FP64 residual r = sigma_p - M y (Eq. 20's argument): kept in
@@ -502,20 +763,27 @@ __global__ void k_add_correction(int64_t m, double* __restrict__ yv, const T* __
 // Field update (supporting information Sec. 1), written over the k-1 slots:
 //   phi^{k+1} = 2 phi^k - phi^{k-1} - (4pi/h) y*
 //   psi^{k+1} = (h/4pi) M phi^{k+1} = r_final - (q^s - mean)
+// Grid-stride over the points; the sum of y* goes to yv[m] (gauge mode).
 template <typename T>
-__global__ void k_update(int64_t m, const double* __restrict__ phik, double* __restrict__ phikm1,
-                         double* __restrict__ psikm1, const double* __restrict__ yv,
-                         const double* __restrict__ rfin, const T* __restrict__ qs,
-                         const double* __restrict__ qsum, double inv_pts, double coef, float* __restrict__ phi32) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const double p = 2.0 * phik[i] - phikm1[i] - coef * yv[i];
-    phikm1[i] = p;
-    psikm1[i] = rfin[i] - ((double)qs[i] - qsum[0] * inv_pts);
-    // FP32 copy for the mixed-precision interpolation, relative to one node
-    // value of phi^k so the constant mode of phi (a gauge freedom) never eats
-    // FP32 digits; the central differences are unchanged by it
-    if (phi32 != nullptr) phi32[i] = (float)(p - phik[0]);
+__global__ void __launch_bounds__(P3_THREADS)
+k_update(int64_t m, const double* __restrict__ phik, double* __restrict__ phikm1,
+         double* __restrict__ psikm1, double* __restrict__ yv,
+         const double* __restrict__ rfin, const T* __restrict__ qs,
+         const double* __restrict__ qsum, double inv_pts, double coef, float* __restrict__ phi32,
+         double* __restrict__ partial, unsigned* __restrict__ arrive) {
+    double ys = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double y = yv[i];
+        ys += y;
+        const double p = 2.0 * phik[i] - phikm1[i] - coef * y;
+        phikm1[i] = p;
+        psikm1[i] = rfin[i] - ((double)qs[i] - qsum[0] * inv_pts);
+        // FP32 copy for the mixed-precision interpolation, relative to one node
+        // value of phi^k so the constant mode of phi (a gauge freedom) never eats
+        // FP32 digits; the central differences are unchanged by it
+        if (phi32 != nullptr) phi32[i] = (float)(p - phik[0]);
+    }
+    sum_last_block(ys, partial, arrive, yv + m);
 }
 
 // ---------------------------------------------------------------- fixed point
@@ -565,10 +833,13 @@ __device__ __forceinline__ fix_t charge_term(float qs, float mean, float u) {
 //   phi^{k+1} = 2 phi^k - phi^{k-1} - z*
 //   Psi^{k+1} = M phi^{k+1} = r_final - (4pi/h)(q^s - mean)
 // and the FP32 copy of phi^{k+1} - phi^k[0] for the interpolation.
+// Grid-stride over the points; the sum of z* (as FP64, in units of the
+// fixed point) goes to slot m of z's buffer (gauge mode).
 static __global__ void __launch_bounds__(P3_THREADS)
 k_update_fix(int64_t m, const fix_t* __restrict__ phik, fix_t* __restrict__ phikm1, fix_t* __restrict__ Psikm1,
-             const fix_t* __restrict__ z, const fix_t* __restrict__ rfin, const float* __restrict__ qs,
-             const double* __restrict__ qsum, double inv_pts, float u, float* __restrict__ phi32) {
+             fix_t* __restrict__ z, const fix_t* __restrict__ rfin, const float* __restrict__ qs,
+             const double* __restrict__ qsum, double inv_pts, float u, float* __restrict__ phi32,
+             double* __restrict__ partial, unsigned* __restrict__ arrive) {
     __shared__ float mean_s;
     __shared__ fix_t ref_s;
     if (threadIdx.x == 0) {
@@ -576,12 +847,16 @@ k_update_fix(int64_t m, const fix_t* __restrict__ phik, fix_t* __restrict__ phik
         ref_s = phik[0];
     }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    const fix_t p = 2 * phik[i] - phikm1[i] - z[i];
-    phikm1[i] = p;
-    Psikm1[i] = rfin[i] - charge_term(qs[i], mean_s, u);
-    phi32[i] = fix_to_float(p - ref_s);
+    double zs = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const fix_t zi = z[i];
+        zs += (double)zi;
+        const fix_t p = 2 * phik[i] - phikm1[i] - zi;
+        phikm1[i] = p;
+        Psikm1[i] = rfin[i] - charge_term(qs[i], mean_s, u);
+        phi32[i] = fix_to_float(p - ref_s);
+    }
+    sum_last_block(zs, partial, arrive, reinterpret_cast<double*>(z + m));
 }
 
 // Partial sums of (phi_i - phi_0) b_i with phi in fixed point (energy
@@ -610,7 +885,7 @@ struct MGState {
     long long total_iters;  // summed over finished solves
     long long solves;
     unsigned arrive;        // blocks of a fused residual kernel done (reset by the last)
-    unsigned pad;
+    unsigned arrive_sum;    // blocks of a field-update kernel done (reset by the last)
 };
 
 // The decision of the check, by one thread, for the residual max-norm res.
@@ -704,8 +979,16 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
     pdl_wait();
     pdl_trigger();
     __shared__ float mean_s;
-    if (threadIdx.x == 0 && threadIdx.y == 0) mean_s = (float)(qsum[0] * inv_pts);
+    __shared__ fix_t gmean_s;  // mean of the guess (gauge mode), removed from the stored z0
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        mean_s = (float)(qsum[0] * inv_pts);
+        const int64_t m = (int64_t)n * n * n;
+        gmean_s = (fix_t)llrint(guess_mean(ORDER, reinterpret_cast<const double*>(z1),
+                                           reinterpret_cast<const double*>(z2),
+                                           reinterpret_cast<const double*>(z3), m));
+    }
     __syncthreads();
+    const fix_t gmean = gmean_s;
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     float a = 0.0f;
@@ -729,8 +1012,8 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
                      z_guess<ORDER>(z1, z2, z3, (zz * n + yp) * n + x) +
                      z_guess<ORDER>(z1, z2, z3, (zm * n + y) * n + x) +
                      z_guess<ORDER>(z1, z2, z3, (zp * n + y) * n + x);
-            const fix_t res = s - (nb - 6 * zc);
-            z0[i] = zc;
+            const fix_t res = s - (nb - 6 * zc);  // unchanged by a constant shift of the guess
+            z0[i] = zc - gmean;
             rfin[i] = res;
             const float v = fix_to_float(res);
             r32[i] = v;
@@ -864,6 +1147,241 @@ k_resid_restrict(int nc, const T* __restrict__ e, const T* __restrict__ b, T* __
         }
     }
     bc[(Z * nc + Y) * nc + X] = (T)4 * acc;
+}
+
+// The same residual and full-weighting restriction with every fine residual
+// formed once.  A block owns a tile of kRrCX x kRrCY coarse points and a run
+// of zc coarse planes; it marches the fine planes 2 Z0 - 1 .. 2 Z1 - 1 once:
+// e planes pass through a ring of three haloed tiles in shared memory, the
+// fine residual b - M e of each plane is formed once into a shared tile, and
+// each thread folds the 3 x 3 in-plane weights of its coarse columns into
+// coarse accumulators (z weights 1/4, 1/2, 1/4 as the planes go by).  Each e
+// and b value is read from memory about once (halo 1.25x and 1.1x), against
+// 27 residuals of 7 loads per coarse point in k_resid_restrict.
+constexpr int kRrCX = 32, kRrCY = 16;                        // coarse tile
+constexpr int kRrFW = 2 * kRrCX + 1, kRrFH = 2 * kRrCY + 1;  // fine residual tile
+constexpr int kRrEW = kRrFW + 2, kRrEH = kRrFH + 2;          // e tile with its halo
+constexpr int kRrThreads = 256;
+constexpr int kRrCols = kRrCX * kRrCY / kRrThreads;          // coarse columns per thread
+
+template <typename T>
+inline size_t resid_restrict_smem_bytes() {
+    return sizeof(T) * (3 * kRrEW * kRrEH + kRrFW * kRrFH);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRrThreads)
+k_resid_restrict_tile(int nc, int zc, const T* __restrict__ e, const T* __restrict__ b, T* __restrict__ bc) {
+    extern __shared__ __align__(16) unsigned char rr_raw[];
+    T* ring = reinterpret_cast<T*>(rr_raw);  // [3][kRrEH][kRrEW]
+    T* R = ring + 3 * kRrEW * kRrEH;         // [kRrFH][kRrFW]
+    pdl_wait();
+    pdl_trigger();
+    const int n = 2 * nc;
+    const int tid = threadIdx.x;
+    const int X0 = blockIdx.x * kRrCX, Y0 = blockIdx.y * kRrCY, Z0 = blockIdx.z * zc;
+    const int Z1 = min(Z0 + zc, nc);
+    auto wr = [n](int v) { return v < 0 ? v + n : (v >= n ? v - n : v); };  // v in [-n, 2n)
+    const int ex0 = 2 * X0 - 2, ey0 = 2 * Y0 - 2;  // e tile origin (fine)
+    // wrapped fine indices of the tile's columns and rows (the tile may span
+    // the periodic axis more than once on small levels)
+    __shared__ int xi[kRrEW], yi[kRrEH];
+    for (int i = tid; i < kRrEW + kRrEH; i += kRrThreads) {
+        if (i < kRrEW) xi[i] = imod(ex0 + i, n);
+        else yi[i - kRrEW] = imod(ey0 + i - kRrEW, n) * n;
+    }
+    __syncthreads();
+    auto load_e = [&](int zf, T* dst) {
+        const T* src = e + (int64_t)wr(zf) * n * n;
+        for (int i = tid; i < kRrEW * kRrEH; i += kRrThreads) {
+            const int x = i % kRrEW, y = i / kRrEW;
+            dst[i] = src[yi[y] + xi[x]];
+        }
+    };
+    const int zf0 = 2 * Z0 - 1;
+    load_e(zf0 - 1, ring);
+    load_e(zf0, ring + kRrEW * kRrEH);
+    // this thread's coarse columns
+    int cx[kRrCols], cy[kRrCols];
+#pragma unroll
+    for (int j = 0; j < kRrCols; ++j) {
+        const int c = tid + j * kRrThreads;
+        cx[j] = c % kRrCX;
+        cy[j] = c / kRrCX;
+    }
+    T acc[kRrCols];
+#pragma unroll
+    for (int j = 0; j < kRrCols; ++j) acc[j] = (T)0;
+    for (int zf = zf0; zf <= 2 * Z1 - 1; ++zf) {
+        T* elo = ring + ((zf - zf0) % 3) * kRrEW * kRrEH;      // plane zf - 1
+        T* emid = ring + ((zf - zf0 + 1) % 3) * kRrEW * kRrEH; // plane zf
+        T* ehi = ring + ((zf - zf0 + 2) % 3) * kRrEW * kRrEH;  // plane zf + 1
+        load_e(zf + 1, ehi);
+        __syncthreads();
+        const T* bp = b + (int64_t)wr(zf) * n * n;
+        for (int i = tid; i < kRrFW * kRrFH; i += kRrThreads) {
+            const int x = i % kRrFW, y = i / kRrFW;
+            const int c = (y + 1) * kRrEW + x + 1;
+            const T nb = emid[c - 1] + emid[c + 1] + emid[c - kRrEW] + emid[c + kRrEW] + elo[c] + ehi[c];
+            R[i] = bp[yi[y + 1] + xi[x + 1]] - (nb - (T)6 * emid[c]);
+        }
+        __syncthreads();
+        const bool odd = (zf & 1) != 0;  // zf = 2Z - 1 (end of Z - 1, start of Z) or zf = 2Z
+        const int Zc = odd ? (zf + 1) >> 1 : zf >> 1;
+#pragma unroll
+        for (int j = 0; j < kRrCols; ++j) {
+            const int r0 = (2 * cy[j]) * kRrFW + 2 * cx[j];  // R(2X-1, 2Y-1) relative to the tile
+            const T* rr = R + r0;
+            const T p = (T)0.25 * ((T)0.25 * rr[0] + (T)0.5 * rr[1] + (T)0.25 * rr[2]) +
+                        (T)0.5 * ((T)0.25 * rr[kRrFW] + (T)0.5 * rr[kRrFW + 1] + (T)0.25 * rr[kRrFW + 2]) +
+                        (T)0.25 * ((T)0.25 * rr[2 * kRrFW] + (T)0.5 * rr[2 * kRrFW + 1] +
+                                   (T)0.25 * rr[2 * kRrFW + 2]);
+            const int X = X0 + cx[j], Y = Y0 + cy[j];
+            if (odd) {
+                if (Zc - 1 >= Z0) {
+                    acc[j] += (T)0.25 * p;
+                    if (X < nc && Y < nc) bc[((int64_t)(Zc - 1) * nc + Y) * nc + X] = (T)4 * acc[j];
+                }
+                acc[j] = (T)0.25 * p;
+            } else {
+                acc[j] += (T)0.5 * p;
+            }
+        }
+    }
+}
+
+// Grid of k_resid_restrict_tile and its planes per block: the fewest planes
+// per block (down from 16) that still give every SM two blocks.
+inline int resid_restrict_zc(int nc, int nsm) {
+    const int tiles = ((nc + kRrCX - 1) / kRrCX) * ((nc + kRrCY - 1) / kRrCY);
+    int zc = 16;
+    while (zc > 1 && tiles * ((nc + zc - 1) / zc) < 2 * nsm) zc >>= 1;
+    return zc;
+}
+inline dim3 resid_restrict_grid(int nc, int zc) {
+    return dim3((nc + kRrCX - 1) / kRrCX, (nc + kRrCY - 1) / kRrCY, (nc + zc - 1) / zc);
+}
+
+// The first red-black sweep from e = 0 (as k_rbgs_first, bit for bit) in
+// FP32 with four x points per thread (N % 4 == 0) and ZC z planes per thread,
+// every load of the thread's b column (planes z0-1 .. z0+ZC), of the y-1 and
+// y+1 rows and of the row-end neighbours issued first; x neighbours of the
+// quad from the adjacent lanes.  Red points (x+y+z even) get -b/6, black
+// points (the six red neighbours' -b/6 summed in the order x-, x+, y-, y+,
+// z-, z+, minus b) / 6.
+template <int ZC>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_rbgs_first4(int n, float* __restrict__ e, const float* __restrict__ b) {
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x;
+    const int qd = blockIdx.x * P3_BX + lane;
+    const int x = 4 * qd;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int z0 = blockIdx.z * ZC;
+    const bool live = x < n && y < n;
+    const int nq = n >> 2;
+    const int yy = live ? y : 0, xx = live ? x : 0;
+    const int xl = xx == 0 ? n - 1 : xx - 1;
+    const int xr = xx + 4 == n ? 0 : xx + 4;
+    const int ym = yy == 0 ? n - 1 : yy - 1, yp = yy == n - 1 ? 0 : yy + 1;
+    const int plane = n * n;
+    const bool lend = lane == 0 || qd - 1 >= nq, rend = lane == P3_BX - 1 || qd + 1 >= nq;
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    auto wz = [&](int z) { return z < 0 ? z + n : (z >= n ? z - n : z); };
+    float4 col[ZC + 2], am[ZC], bp[ZC];
+    float lft[ZC], rgt[ZC];
+#pragma unroll
+    for (int k = 0; k < ZC + 2; ++k) col[k] = b4[(wz(z0 - 1 + k) * plane + yy * n + xx) >> 2];
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const int z = wz(z0 + k);
+        am[k] = b4[(z * plane + ym * n + xx) >> 2];
+        bp[k] = b4[(z * plane + yp * n + xx) >> 2];
+        lft[k] = lend ? b[z * plane + yy * n + xl] : 0.0f;
+        rgt[k] = rend ? b[z * plane + yy * n + xr] : 0.0f;
+    }
+    const float sixth = (float)(1.0 / 6.0);
+    auto red = [&](float v) { return __fmul_rn(-v, sixth); };
+#pragma unroll
+    for (int k = 0; k < ZC; ++k) {
+        const float4 vm = col[k], vc = col[k + 1], vp = col[k + 2], a = am[k], c = bp[k];
+        float left = __shfl_up_sync(0xffffffffu, vc.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, vc.x, 1);
+        if (lend) left = lft[k];
+        if (rend) right = rgt[k];
+        const int z = z0 + k;
+        const bool even0 = ((x + y + z) & 1) == 0;  // parity of the quad's first point
+        const float xs[6] = {left, vc.x, vc.y, vc.z, vc.w, right};
+        const float ys[4] = {a.x, a.y, a.z, a.w}, yq[4] = {c.x, c.y, c.z, c.w};
+        const float zs[4] = {vm.x, vm.y, vm.z, vm.w}, zq[4] = {vp.x, vp.y, vp.z, vp.w};
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool redpt = even0 == ((j & 1) == 0);
+            if (redpt) {
+                o[j] = red(xs[j + 1]);
+            } else {
+                const float s6 = red(xs[j]) + red(xs[j + 2]) + red(ys[j]) + red(yq[j]) + red(zs[j]) + red(zq[j]);
+                o[j] = (s6 - xs[j + 1]) * sixth;
+            }
+        }
+        if (live && z < n)
+            reinterpret_cast<float4*>(e)[(z * plane + yy * n + x) >> 2] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Trilinear prolongation and correction e_f += P e_c in FP32 with four x
+// points and the two z planes 2Z, 2Z+1 per thread (N % 4 == 0): the 12
+// coarse values of a quad pair are loaded once and every output is formed
+// by prolong_at's expression.
+static __global__ void __launch_bounds__(P3_BX * P3_BY)
+k_prolong_add4(int n, const float* __restrict__ ec, float* __restrict__ ef) {
+    pdl_wait();
+    pdl_trigger();
+    const int qd = blockIdx.x * P3_BX + threadIdx.x;
+    const int x = 4 * qd;
+    const int y = blockIdx.y * P3_BY + threadIdx.y;
+    const int Z = blockIdx.z;
+    const int nc = n >> 1;
+    if (x >= n || y >= n) return;
+    const int cxa = x >> 1, cxb = cxa + 1, cxc = cxa + 2 >= nc ? cxa + 2 - nc : cxa + 2;  // 2q, 2q+1, 2q+2
+    const int y0 = y >> 1, y1 = (y & 1) ? (y0 + 1 == nc ? 0 : y0 + 1) : y0;
+    const float ay = (y & 1) ? 0.5f : 1.0f, by = (y & 1) ? 0.5f : 0.0f;
+    const int Zp = Z + 1 == nc ? 0 : Z + 1;
+    float c[2][2][3];  // [z: Z, Z+1][y: y0, y1][x: 2q, 2q+1, 2q+2]
+    const int zz[2] = {Z, Zp}, yyv[2] = {y0, y1};
+#pragma unroll
+    for (int iz = 0; iz < 2; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy) {
+            const float* row = ec + (zz[iz] * nc + yyv[iy]) * nc;
+            c[iz][iy][0] = row[cxa];
+            c[iz][iy][1] = row[cxb];
+            c[iz][iy][2] = row[cxc];
+        }
+    const int plane = n * n;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int z = 2 * Z + k;
+        const float az = k ? 0.5f : 1.0f, bz = k ? 0.5f : 0.0f;
+        const int z1 = k ? 1 : 0;  // second z plane index into c (Z+1 for odd z, Z again for even)
+        float4* dst = reinterpret_cast<float4*>(ef + z * plane + y * n + x);
+        float4 v = *dst;
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i0 = j >> 1, i1 = (j & 1) ? i0 + 1 : i0;
+            const float ax = (j & 1) ? 0.5f : 1.0f, bx = (j & 1) ? 0.5f : 0.0f;
+            o[j] = az * (ay * (ax * c[0][0][i0] + bx * c[0][0][i1]) + by * (ax * c[0][1][i0] + bx * c[0][1][i1])) +
+                   bz * (ay * (ax * c[z1][0][i0] + bx * c[z1][0][i1]) + by * (ax * c[z1][1][i0] + bx * c[z1][1][i1]));
+        }
+        v.x += o[0];
+        v.y += o[1];
+        v.z += o[2];
+        v.w += o[3];
+        *dst = v;
+    }
 }
 
 // Trilinear prolongation and correction on the fine level: e_f += P e_c.

@@ -54,9 +54,9 @@ struct StepGraph {
 };
 
 inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
-
-// Threads per particle of the FP32 assignment kernel.
-constexpr int kSpreadTPP = 4;
+// Field-update grid: grid-stride, at most 1024 blocks (the partial-sum
+// buffer holds at least 1024 entries).
+inline unsigned update_blocks(int64_t m) { return std::min(nblk(m), 1024u); }
 
 // In mixed precision the 8-byte constraint arrays (phi, Psi, z history, s,
 // final residual) hold 64-bit fixed-point values (x 2^40, potential units).
@@ -90,6 +90,7 @@ struct p3maze_ctx {
     int pair_fork = 0;                   // pair kernel forked after: 0 smoothing, 1 the cell list (tunable)
     int pair_blocks = 0;                 // pair grid: 0 one block per home box, else a persistent grid (tunable)
     int lr_force = 0;                    // P3MAZE_LR_FORCE_FD (the paper's) or P3MAZE_LR_FORCE_ANALYTIC
+    int sr_shift = 0;                    // P3MAZE_SR_TRUNCATE or P3MAZE_SR_SHIFT_FORCE
     int nsm = 148;                       // SMs of the device
     bool pdl = true;                     // chained mesh kernels overlap their predecessor's tail (P3MAZE_PDL=0: off)
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
@@ -380,12 +381,21 @@ template <typename T>
 int spread_smooth(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_SPREAD);
-    CK(cudaMemsetAsync(ctx->q, 0, sizeof(T) * ctx->P, s));
-    if constexpr (sizeof(T) == 4)
-        k_spread_mp<kSpreadTPP><<<nblk((int64_t)ctx->np * kSpreadTPP), P3_THREADS, 0, s>>>(ctx->np, ctx->mp, ctx->N,
-                                                                                          (float*)ctx->q);
-    else
-        k_spread<T><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->N, ctx->inv_h, (T*)ctx->q);
+    // deterministic tiled assignment: every mesh point written once
+    if constexpr (sizeof(T) == 4) {
+        if (ctx->N % 4 == 0)
+            CK(launch_maybe_pdl(false, k_spread_tile<float, MeshPt, true>, spread_grid(ctx->N), dim3(kSpThreads),
+                                spread_smem_bytes<float>(), s, ctx->N, ctx->nc, (const int*)ctx->start,
+                                (const MeshPt*)ctx->mp, ctx->inv_h, (float*)ctx->q));
+        else
+            CK(launch_maybe_pdl(false, k_spread_tile<float, MeshPt, false>, spread_grid(ctx->N), dim3(kSpThreads),
+                                spread_smem_bytes<float>(), s, ctx->N, ctx->nc, (const int*)ctx->start,
+                                (const MeshPt*)ctx->mp, ctx->inv_h, (float*)ctx->q));
+    } else {
+        CK(launch_maybe_pdl(false, k_spread_tile<double, PQ, false>, spread_grid(ctx->N), dim3(kSpThreads),
+                            spread_smem_bytes<double>(), s, ctx->N, ctx->nc, (const int*)ctx->start,
+                            (const PQ*)ctx->xq, ctx->inv_h, (double*)ctx->q));
+    }
     count(ctx, P3MAZE_ST_SPREAD);
     stage_end(ctx, P3MAZE_ST_SPREAD);
     stage_begin(ctx, P3MAZE_ST_SMOOTH);
@@ -506,19 +516,47 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
         CK(cudaMemsetAsync(e, 0, sizeof(T) * L.pts, s));
         pdl = false;  // the next launch follows a memset
     }
+    // FP32 levels with N % 4 == 0 take the four-points-per-thread kernels
+    const bool quads = sizeof(T) == 4 && L.n % 4 == 0;
     for (int it = 0; it < ctx->nu1; ++it) {
         if (it == 0) {
-            CK(go(k_rbgs_first<T>, g3(L.n), kB3, 0, L.n, e, (const T*)b));  // both colours from e = 0
+            // both colours from e = 0
+            if constexpr (sizeof(T) == 4) {
+                if (quads) {
+                    const int zc = L.n >= 256 ? 4 : 2;
+                    const dim3 g((L.n / 4 + P3_BX - 1) / P3_BX, (L.n + P3_BY - 1) / P3_BY, (L.n + zc - 1) / zc);
+                    if (zc == 4) CK(go(k_rbgs_first4<4>, g, kB3, 0, L.n, (float*)e, (const float*)b));
+                    else CK(go(k_rbgs_first4<2>, g, kB3, 0, L.n, (float*)e, (const float*)b));
+                } else {
+                    CK(go(k_rbgs_first<T>, g3(L.n), kB3, 0, L.n, e, (const T*)b));
+                }
+            } else {
+                CK(go(k_rbgs_first<T>, g3(L.n), kB3, 0, L.n, e, (const T*)b));
+            }
         } else {
             CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 0, 0));
             CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
         }
     }
-    CK(go(k_resid_restrict<T>, g3(C.n), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
+    {
+        // residual + restriction, each fine residual formed once per block
+        const int zc = resid_restrict_zc(C.n, ctx->nsm);
+        CK(go(k_resid_restrict_tile<T>, resid_restrict_grid(C.n, zc), dim3(kRrThreads),
+              resid_restrict_smem_bytes<T>(), C.n, zc, (const T*)e, (const T*)b, (T*)C.b));
+    }
     count(ctx, P3MAZE_ST_SOLVE, (ctx->nu1 > 0 ? 2 * ctx->nu1 - 1 : 0) + 1);
     int rc = vcycle<T>(ctx, l + 1, true);
     if (rc) return rc;
-    CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
+    if constexpr (sizeof(T) == 4) {
+        if (quads) {
+            const dim3 g((L.n / 4 + P3_BX - 1) / P3_BX, (L.n + P3_BY - 1) / P3_BY, L.n / 2);
+            CK(go(k_prolong_add4, g, kB3, 0, L.n, (const float*)C.e, (float*)e));
+        } else {
+            CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
+        }
+    } else {
+        CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
+    }
     for (int it = 0; it < ctx->nu2; ++it) {
         CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
         CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 0, 0));
@@ -670,16 +708,15 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     stage_end(ctx, P3MAZE_ST_SOLVE);
     stage_begin(ctx, P3MAZE_ST_UPDATE);
     if (fixp)
-        k_update_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, fx(ctx->phi[ik]), fx(ctx->phi[ikm1]),
-                                                         fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
-                                                         (const float*)ctx->qs, ctx->dscal + S_QSUM,
-                                                         1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
-                                                         ctx->phi32);
+        k_update_fix<<<update_blocks(ctx->P), P3_THREADS, 0, s>>>(
+            ctx->P, fx(ctx->phi[ik]), fx(ctx->phi[ikm1]), fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
+            (const float*)ctx->qs, ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
+            ctx->phi32, ctx->partial, &ctx->dmg->arrive_sum);
     else
-        k_update<T><<<nblk(ctx->P), P3_THREADS, 0, s>>>(ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1],
-                                                        ctx->yh[0], ctx->rfin, (const T*)ctx->qs,
-                                                        ctx->dscal + S_QSUM, 1.0 / (double)ctx->P,
-                                                        4.0 * kPi / ctx->h, ctx->phi32);
+        k_update<T><<<update_blocks(ctx->P), P3_THREADS, 0, s>>>(
+            ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1], ctx->yh[0], ctx->rfin, (const T*)ctx->qs,
+            ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, 4.0 * kPi / ctx->h, ctx->phi32, ctx->partial,
+            &ctx->dmg->arrive_sum);
     count(ctx, P3MAZE_ST_UPDATE);
     stage_end(ctx, P3MAZE_ST_UPDATE);
     CKL();
@@ -702,18 +739,24 @@ int pair_forces(p3maze_ctx* ctx) {
     const int nbox = (ctx->nc + 1) / 2;
     const unsigned nboxes = (unsigned)nbox * nbox * nbox;
     const unsigned pb = ctx->pair_blocks > 0 ? std::min(nboxes, (unsigned)ctx->pair_blocks) : nboxes;
-#define PAIR(KIND, MOL)                                                                                 \
+#define PAIR3(KIND, MOL, SH)                                                                            \
     do {                                                                                                \
         if (mixed)                                                                                      \
-            k_pair<KIND, float, 768, MOL><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts,        \
+            k_pair<KIND, float, 768, MOL, SH><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts,    \
                 ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke_pair,  \
                 ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
         else                                                                                            \
-            k_pair<KIND, double, 512, MOL><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts,       \
+            k_pair<KIND, double, 512, MOL, SH><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts,   \
                 ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke_pair,  \
                 ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
     } while (0)
+#define PAIR(KIND, MOL)                       \
+    do {                                      \
+        if (shift) PAIR3(KIND, MOL, true);    \
+        else PAIR3(KIND, MOL, false);         \
+    } while (0)
     const bool mol = ctx->nmol > 0;
+    const bool shift = ctx->sr_shift == P3MAZE_SR_SHIFT_FORCE;
     if (ctx->tab.kind == 1) {
         if (mol) PAIR(1, true);
         else PAIR(1, false);
@@ -725,6 +768,7 @@ int pair_forces(p3maze_ctx* ctx) {
         else PAIR(0, false);
     }
 #undef PAIR
+#undef PAIR3
     count(ctx, P3MAZE_ST_PAIR);
     stage_end(ctx, P3MAZE_ST_PAIR);
     ctx->stream = main;
@@ -824,7 +868,7 @@ int initialise_field(p3maze_ctx* ctx) {
         CK(cudaMemsetAsync(ctx->phi[k], 0, mb, s));
         CK(cudaMemsetAsync(ctx->psi[k], 0, mb, s));
     }
-    for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(ctx->yh[k], 0, mb, s));
+    for (int k = 0; k < 4; ++k) CK(cudaMemsetAsync(ctx->yh[k], 0, mb + 8, s));  // with the sum slot
     CK(cudaMemsetAsync(ctx->dmg, 0, sizeof(MGState), s));
     ctx->nhist = 0;
     const bool was_timing = ctx->timing;
@@ -837,7 +881,7 @@ int initialise_field(p3maze_ctx* ctx) {
     if (rc) return rc;
     CK(cudaMemcpyAsync(ctx->phi[1 - ctx->icur], ctx->phi[ctx->icur], mb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(ctx->psi[1 - ctx->icur], ctx->psi[ctx->icur], mb, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(ctx->yh[0], 0, mb, s));
+    CK(cudaMemsetAsync(ctx->yh[0], 0, mb + 8, s));
     // the initial solve is not part of the step statistics
     CK(cudaMemsetAsync(ctx->dmg, 0, sizeof(MGState), s));
     CK(cudaStreamSynchronize(s));
@@ -1119,7 +1163,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     }
     ALLOC(ctx->rfin, 8 * P);
     if (mixed) ALLOC(ctx->phi32, 4 * P);
-    for (int k = 0; k < 4; ++k) ALLOC(ctx->yh[k], 8 * P);
+    for (int k = 0; k < 4; ++k) ALLOC(ctx->yh[k], 8 * (P + 1));  // + the buffer's sum (gauge mode)
     if (!mixed) ALLOC(ctx->sig, 8 * P);  // mixed: the prediction is folded into the first residual
     ctx->lev.resize(ctx->nlev);
     int nn = ctx->N;
@@ -1157,6 +1201,16 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         } else {
             raise((const void*)k_coarse_xy<double>);
             raise((const void*)k_coarse_z<double>);
+        }
+        sm = resid_restrict_smem_bytes<double>();
+        if (!mixed) raise((const void*)k_resid_restrict_tile<double>);
+        if (mixed) {
+            sm = spread_smem_bytes<float>();
+            raise((const void*)k_spread_tile<float, MeshPt, true>);
+            raise((const void*)k_spread_tile<float, MeshPt, false>);
+        } else {
+            sm = spread_smem_bytes<double>();
+            raise((const void*)k_spread_tile<double, PQ, false>);
         }
         if (cells_in_one_block(ctx->np, ctx->ncell)) {
             sm = cells_block_smem(ctx->ncell);
@@ -1261,7 +1315,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     for (int k = 0; k < 4; ++k) b += a(8 * P);           // phi, psi
     b += a(8 * P);                                       // rfin
     if (mixed) b += a(4 * P);                            // phi32
-    for (int k = 0; k < 4; ++k) b += a(8 * P);           // y ring
+    for (int k = 0; k < 4; ++k) b += a(8 * (P + 1));     // y ring, each with its sum
     if (!mixed) b += a(8 * P);                           // sigma
     int nn = N;
     for (int l = 0; l < nlev; ++l) {
@@ -1321,6 +1375,8 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     if (p->coarse_max < 0) return fail(nullptr, P3MAZE_ERR_INVALID, "coarse_max must be >= 0");
     if (p->lr_force != P3MAZE_LR_FORCE_FD && p->lr_force != P3MAZE_LR_FORCE_ANALYTIC)
         return fail(nullptr, P3MAZE_ERR_INVALID, "lr_force must be P3MAZE_LR_FORCE_FD or P3MAZE_LR_FORCE_ANALYTIC");
+    if (p->sr_shift != P3MAZE_SR_TRUNCATE && p->sr_shift != P3MAZE_SR_SHIFT_FORCE)
+        return fail(nullptr, P3MAZE_ERR_INVALID, "sr_shift must be P3MAZE_SR_TRUNCATE or P3MAZE_SR_SHIFT_FORCE");
     if (pmaze && p->lr_force != P3MAZE_LR_FORCE_FD)
         return fail(nullptr, P3MAZE_ERR_INVALID,
                     "P3MAZE_METHOD_PMAZE takes the finite-difference force (the exact gradient carries the grid "
@@ -1358,6 +1414,29 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     } else {
         tab.kind = 0;
         tab.nt = 1;
+    }
+    {
+        // shifted-force constants at r_cut (used only with P3MAZE_SR_SHIFT_FORCE)
+        const double rc = p->r_cut;
+        tab.rc = rc;
+        if (!pmaze) {
+            const double x = p->alpha * rc;
+            tab.cg = std::erfc(x) / rc;
+            tab.cG = std::erfc(x) / (rc * rc) + 2.0 / std::sqrt(kPi) * p->alpha * std::exp(-x * x) / rc;
+        }
+        for (int k = 0; k < tab.nt * tab.nt; ++k) {
+            if (tab.kind == P3MAZE_SR_BMH) {
+                const double A = tab.p[0][k], rho = tab.p[1][k], sg = tab.p[2][k], Cc = tab.p[3][k],
+                             Dc = tab.p[4][k];
+                const double ex = A * std::exp((sg - rc) / rho);
+                tab.urc[k] = ex - Cc / std::pow(rc, 6) - Dc / std::pow(rc, 8);
+                tab.frc[k] = ex / rho - 6.0 * Cc / std::pow(rc, 7) - 8.0 * Dc / std::pow(rc, 9);
+            } else if (tab.kind == P3MAZE_SR_LJ) {
+                const double eps = tab.p[0][k], s6 = std::pow(tab.p[1][k] / rc, 6);
+                tab.urc[k] = 4.0 * eps * (s6 * s6 - s6);
+                tab.frc[k] = 24.0 * eps * (2.0 * s6 * s6 - s6) / rc;
+            }
+        }
     }
     int nmol = 0;
     if (p->topology && p->topology->n_molecules > 0) {
@@ -1402,6 +1481,7 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     ctx->dt = p->dt;
     ctx->method = p->method;
     ctx->lr_force = p->lr_force;
+    ctx->sr_shift = p->sr_shift;
     // one diffusion step per launch; FP32 quads take 2 planes per thread
     ctx->zc = (p->precision == P3MAZE_MIXED && p->mesh % 4 == 0) ? 2 : 8;
     ctx->fuse = 1;
@@ -1664,7 +1744,7 @@ void state_segments(p3maze_ctx* ctx, std::vector<std::pair<void*, size_t>>& seg)
            {ctx->ecs, n1}, {ctx->evs, n1}, {ctx->q, tb * (size_t)ctx->P},
            {ctx->phi[ctx->icur], P8}, {ctx->phi[1 - ctx->icur], P8},
            {ctx->psi[ctx->icur], P8}, {ctx->psi[1 - ctx->icur], P8},
-           {ctx->yh[1], P8}, {ctx->yh[2], P8}, {ctx->yh[3], P8},
+           {ctx->yh[1], P8 + 8}, {ctx->yh[2], P8 + 8}, {ctx->yh[3], P8 + 8},
            {ctx->rfin, P8}, {ctx->dscal, 8 * (size_t)S_NSCAL}};
     if (ctx->sig) seg.push_back({ctx->sig, P8});
     if (ctx->phi32) seg.push_back({ctx->phi32, 4 * (size_t)ctx->P});

@@ -297,6 +297,11 @@ struct SRTable {
     int kind;      // 0 none, 1 BMH, 2 LJ
     int nt;
     double p[5][16];
+    // shifted-force cutoff (P3MAZE_SR_SHIFT_FORCE): non-Coulomb U(r_c) and
+    // F(r_c) = -U'(r_c) per species pair; erfc Coulomb g(r_c) = erfc(alpha r_c)/r_c
+    // and G(r_c) = -g'(r_c) per unit QQ
+    double urc[16], frc[16];
+    double cg, cG, rc;
 };
 
 // Math in the pair kernel's arithmetic type, with the FP32 versions named
@@ -311,6 +316,7 @@ __device__ __forceinline__ double m_rsqrt(double x) { return rsqrt(x); }
 template <typename R>
 struct PairPar {
     R a, b, c, d, e;
+    R urc, frc;  // shifted-force constants of the non-Coulomb term
 };
 
 // Per-pair screened Coulomb (Eq. 19 with alpha = 1/(sqrt2 sigma); energy
@@ -328,8 +334,16 @@ __device__ __forceinline__ float erfc_with_exp(float x, float ex) {
 }
 __device__ __forceinline__ double erfc_with_exp(double x, double) { return erfc(x); }
 
-template <int KIND, typename R>
-__device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& pp, R& ec, R& ev, R& fvdw) {
+// Shifted-force cutoff (SHIFT): each term U(r) becomes U(r) - U(r_c) + (r - r_c) F(r_c)
+// and its force F(r) - F(r_c); sc = (g(r_c), G(r_c), r_c) of the Coulomb term per unit QQ.
+template <typename R>
+struct ShiftC {
+    R cg, cG, rc;
+};
+
+template <int KIND, bool SHIFT, typename R>
+__device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& pp, const ShiftC<R>& sc, R& ec,
+                                        R& ev, R& fvdw) {
     const R ir = m_rsqrt(r2);
     const R rr = r2 * ir;
     const R ar = alpha * rr;
@@ -352,7 +366,17 @@ __device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& p
             fvdw = (R)24 * pp.a * ((R)2 * sr6 * sr6 - sr6) * ir2;
         }
     }
-    return qq * (erfcv * ir + (R)kTwoOverSqrtPi * alpha * ex) * ir2;
+    R fc = qq * (erfcv * ir + (R)kTwoOverSqrtPi * alpha * ex) * ir2;
+    if (SHIFT) {
+        const R dr = rr - sc.rc;
+        ec += qq * (dr * sc.cG - sc.cg);
+        fc -= qq * sc.cG * ir;
+        if (KIND != 0) {
+            ev += dr * pp.frc - pp.urc;
+            fvdw -= pp.frc * ir;
+        }
+    }
+    return fc;
 }
 
 // Short-range forces (Eq. 19 plus the Born-Mayer or Lennard-Jones term) on
@@ -373,15 +397,15 @@ template <typename R> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = PQ; };
 
-template <int KIND, typename R, typename V>
+template <int KIND, bool SHIFT, typename R, typename V>
 __device__ __forceinline__ void pair_accumulate(const V& pi, const V& pj, R alpha, R ke, const PairPar<R>& pp,
-                                                R& fx, R& fy, R& fz, R& ec, R& ev) {
+                                                const ShiftC<R>& sc, R& fx, R& fy, R& fz, R& ec, R& ev) {
     const R ddx = (R)pi.x - (R)pj.x;
     const R ddy = (R)pi.y - (R)pj.y;
     const R ddz = (R)pi.z - (R)pj.z;
     const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
     R e_c, e_v, f_v;
-    const R fr = pair_terms<KIND, R>(r2, (R)pi.w * (R)pj.w, alpha, pp, e_c, e_v, f_v);
+    const R fr = pair_terms<KIND, SHIFT, R>(r2, (R)pi.w * (R)pj.w, alpha, pp, sc, e_c, e_v, f_v);
     const R f = ke * fr + f_v;
     fx += f * ddx;
     fy += f * ddy;
@@ -391,7 +415,8 @@ __device__ __forceinline__ void pair_accumulate(const V& pi, const V& pj, R alph
 }
 
 // MOL: the system has molecules, so intramolecular pairs are tested for.
-template <int KIND, typename R, int CAP, bool MOL>
+// SHIFT: shifted-force cutoff (pair_terms).
+template <int KIND, typename R, int CAP, bool MOL, bool SHIFT>
 __global__ void __launch_bounds__(P3_THREADS)
 k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restrict__ ts,
        const int* __restrict__ ms, const int* __restrict__ start, int nc, int nbox, double lcell, double rc2,
@@ -429,8 +454,11 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
             pp.b = (R)(tab.p[1][tid] * tab.p[1][tid]);
             pp.c = pp.d = pp.e = (R)0;
         }
+        pp.urc = (R)tab.urc[tid];
+        pp.frc = (R)tab.frc[tid];
         spar[tid] = pp;
     }
+    const ShiftC<R> sc{(R)tab.cg, (R)tab.cG, (R)tab.rc};
     // one home box per iteration; the grid may be smaller than the number
     // of boxes (a persistent launch that leaves room on every SM)
     const int nbox3 = nbox * nbox * nbox;
@@ -613,7 +641,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                         __syncwarp();
                         if (qn >= 32) {
                             const int kk = wq[warp][lane];
-                            pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
+                            pair_accumulate<KIND, SHIFT, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], sc, fx, fy, fz, ec, ev);
                             __syncwarp();
                             if (lane < qn - 32) wq[warp][lane] = wq[warp][32 + lane];
                             __syncwarp();
@@ -622,7 +650,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                     }
                     if (lane < qn) {
                         const int kk = wq[warp][lane];
-                        pair_accumulate<KIND, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], fx, fy, fz, ec, ev);
+                        pair_accumulate<KIND, SHIFT, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], sc, fx, fy, fz, ec, ev);
                     }
                     __syncwarp();
                     // lane partials (a few pairs each) are reduced and accumulated

@@ -20,6 +20,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE = 0, -1, -2
 FP64, MIXED = 0, 1
 METHOD_MAZE, METHOD_P3M, METHOD_PMAZE = 0, 1, 2
 SR_NONE, SR_BMH, SR_LJ = 0, 1, 2
+SR_TRUNCATE, SR_SHIFT_FORCE = 0, 1
 MAX_TYPES = 4
 MESH = {"q": 0, "qs": 1, "phi": 2, "y": 3, "sigma": 4}
 FORCE = {"total": 0, "sr": 1, "lr": 2, "bond": 3}
@@ -43,7 +44,7 @@ class Params(C.Structure):
                 ("predictor", C.c_int32), ("precision", C.c_int32), ("max_mg_iters", C.c_int32),
                 ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32), ("coulomb_k", C.c_double),
                 ("sr", C.POINTER(SRTable)), ("topology", C.POINTER(Topology)), ("method", C.c_int32),
-                ("coarse_max", C.c_int32), ("lr_force", C.c_int32)]
+                ("coarse_max", C.c_int32), ("lr_force", C.c_int32), ("sr_shift", C.c_int32)]
 
 
 class Energies(C.Structure):
@@ -175,7 +176,8 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
                  sr_table: dict | None = None, triples=None, bonded: dict | None = None,
                  order: int = 4, predictor: int = 3, precision: str = "fp64",
                  max_mg_iters: int = 0, pre_sweeps: int = 0, post_sweeps: int = 0,
-                 coulomb_k: float = 0.0, method: str = "maze", coarse_max: int = 0, lr_force: str = "fd"):
+                 coulomb_k: float = 0.0, method: str = "maze", coarse_max: int = 0, lr_force: str = "fd",
+                 sr_shift: str = "none"):
     """p3maze_params for these arguments, plus the arrays it points into
     (keep them alive while the struct is used)."""
     n = int(np.asarray(charges).shape[0])
@@ -201,6 +203,7 @@ def build_params(pos, charges, masses, box: float, *, alpha: float, r_cut: float
     p.method = {"maze": METHOD_MAZE, "p3m": METHOD_P3M, "pmaze": METHOD_PMAZE}[method]
     p.coarse_max = int(coarse_max)
     p.lr_force = {"fd": 0, "analytic": 1}[lr_force]
+    p.sr_shift = {"none": SR_TRUNCATE, "force": SR_SHIFT_FORCE}[sr_shift]
     tab = sr_table_from(sr_kind, sr_table or {})
     if tab is not None:
         keep["sr"] = tab

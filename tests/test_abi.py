@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI (no GPU needed, no compute call made).
 
-* the shared library loads and exports every function include/p3maze.h declares;
+* the shared library loads and exports every function include/p3maze.h declares,
+  and exports no p3maze_* function that the header does not declare;
 * the ctypes structures have the C layout (sizes and offsets from gcc);
 * p3maze_init rejects invalid parameters before it touches the device.
 """
@@ -32,6 +33,8 @@ def test_library_exports_every_declared_function():
     out = subprocess.run(["nm", "-D", "--defined-only", P._LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r" T (p3maze_\w+)", out))
     assert set(names) <= exported
+    # and nothing is exported that the header does not declare
+    assert exported <= set(names), sorted(exported - set(names))
 
 
 def test_ctypes_layout_matches_c(tmp_path):

@@ -4,7 +4,6 @@ import numpy as np
 import pytest
 
 from paper_2606_31379_b300 import synth as S
-from tests.parity_helpers import rel_rms
 
 pytestmark = pytest.mark.gpu
 
@@ -27,9 +26,12 @@ def _ctx(P, system, precision, **kw):
     return P.Context.from_system(system, alpha=0.30, tol=1e-9, precision=precision, **kw)
 
 
-@pytest.mark.parametrize("precision, tol, mode", [("fp64", 1e-9, "shared"), ("mixed", 1e-5, "shared"),
-                                                 ("fp64", 1e-9, "per_member")])
-def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, tol, mode):
+@pytest.mark.parametrize("precision, mode", [("fp64", "shared"), ("mixed", "shared"), ("fp64", "per_member"),
+                                             ("mixed", "per_member")])
+def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, mode):
+    """A member of a batch follows the same trajectory as the same system
+    stepped alone, bit for bit: every kernel is deterministic and a member's
+    kernels read only its own arrays."""
     total = 12
     alone = []
     for system, kw in _systems():
@@ -46,8 +48,8 @@ def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, tol, mode)
         batch.wait()
         for c, (pos, F, steps) in zip(ctxs, alone):
             assert c.stats()["steps"] == steps == total
-            np.testing.assert_allclose(c.positions(), pos, rtol=0, atol=1e-9 if precision == "fp64" else 1e-7)
-            assert rel_rms(c.forces(), F) < tol
+            np.testing.assert_array_equal(c.positions(), pos)
+            np.testing.assert_array_equal(c.forces(), F)
         # membership change: drop one, keep stepping, it can still step alone
         batch.remove(ctxs[1])
         batch.step(2)

@@ -217,18 +217,85 @@ def test_nacl_32k_128_sampled_parity(P, precision, ftol):
         assert constraint_residual(ctx.mesh("phi"), mf["qs"], mf["h"]) <= prm["tol"] + margin
 
 
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_nacl_32k_long_run_sampled_parity(P, precision, ftol):
+    """The 32768-ion, 128^3 workload over 300 MD steps: every 100 steps the
+    GPU's total force on 48 sampled ions, the mesh force on all of them and
+    the smoothed charge are compared with the oracle at the GPU's own
+    positions (the per-step comparison of the full-size workload, sampled in
+    time and in particles)."""
+    s, prm = S.make_workload("nacl_32k")
+    sample = np.random.default_rng(1).choice(s.n, 48, replace=False)
+    with P.Context.from_system(s, alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"],
+                               tol=1e-8, dt=prm["dt"], precision=precision) as ctx:
+        for _ in range(3):
+            ctx.step(100)
+            pos = ctx.positions()
+            F_ref, mf, F_lr = oracle_sampled(s, pos, prm["alpha"], prm["r_cut"], prm["mesh"], sample)
+            tolq = 1e-12 if precision == "fp64" else 1e-6
+            assert np.abs(ctx.mesh("qs") - mf["qs"]).max() <= tolq * np.abs(mf["qs"]).max()
+            assert rel_rms(ctx.forces("lr"), F_lr) < ftol
+            assert rel_rms(ctx.forces()[sample], F_ref) < ftol
+        assert ctx.stats()["steps"] == 300
+
+
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_spcfw_90k_128_sampled_parity(P, precision, ftol):
+    """Flexible SPC/Fw water, 30 000 molecules (90 000 atoms), L = 96.4 A,
+    128^3 mesh, dt 0.5 fs: after two steps the total force (mesh, erfc +
+    O-O Lennard-Jones pairs, bonded terms and the intramolecular exclusion)
+    on 48 sampled atoms and the mesh force on all atoms match the oracle at
+    the GPU's positions."""
+    s, prm = S.make_workload("spcfw_30k")
+    sample = np.random.default_rng(2).choice(s.n, 48, replace=False)
+    with P.Context.from_system(s, alpha=prm["alpha"], r_cut=prm["r_cut"], mesh=prm["mesh"],
+                               tol=1e-8, dt=prm["dt"], precision=precision) as ctx:
+        ctx.step(2)
+        pos = ctx.positions()
+        F_ref, mf, F_lr = oracle_sampled(s, pos, prm["alpha"], prm["r_cut"], prm["mesh"], sample)
+        tolq = 1e-12 if precision == "fp64" else 1e-6
+        assert np.abs(ctx.mesh("qs") - mf["qs"]).max() <= tolq * np.abs(mf["qs"]).max()
+        assert rel_rms(ctx.forces("lr"), F_lr) < ftol
+        assert rel_rms(ctx.forces()[sample], F_ref) < ftol
+
+
+@pytest.mark.parametrize("precision, ftol", [("fp64", 1e-5), ("mixed", 1e-4)])
+def test_shifted_force_cutoff_matches_oracle(P, nacl512, precision, ftol):
+    """The shifted-force cutoff option: forces and the pair energies match
+    the oracle's shifted sums (BMH melt; SPC/Fw with Lennard-Jones)."""
+    with _ctx(P, nacl512, precision=precision, sr_shift="force") as ctx:
+        ctx.step(2)
+        pos = ctx.positions()
+        ref = O.forces_and_energies(at_positions(nacl512, pos), 0.30, 9.0, 32, sr_shift="force")
+        plain = O.forces_and_energies(at_positions(nacl512, pos), 0.30, 9.0, 32)
+        assert rel_rms(ctx.forces("sr"), ref["F_sr"]) < ftol
+        assert rel_rms(ctx.forces(), ref["F"]) < ftol
+        assert rel_rms(ctx.forces("sr"), plain["F_sr"]) > 10 * ftol * (precision == "fp64")
+        e = ctx.energy()
+        etol = 1e-9 if precision == "fp64" else 1e-5
+        assert e["v_sr"] == pytest.approx(ref["v_sr"], rel=etol)
+        assert e["v_vdw"] == pytest.approx(ref["v_vdw"], rel=etol)
+    w = S.spcfw_water(64, 12.42, seed=3)
+    with P.Context.from_system(w, alpha=0.30, r_cut=6.0, mesh=16, tol=1e-9, dt=0.5, precision=precision,
+                               sr_shift="force") as ctx:
+        ctx.step(2)
+        pos = ctx.positions()
+        ref = O.forces_and_energies(at_positions(w, pos), 0.30, 6.0, 16, sr_shift="force")
+        assert rel_rms(ctx.forces(), ref["F"]) < ftol
+        assert ctx.energy()["v_vdw"] == pytest.approx(ref["v_vdw"], rel=1e-9 if precision == "fp64" else 1e-5)
+
+
 def test_async_steps_match_blocking_steps(P, nacl512):
     """p3maze_step_async + p3maze_wait run the same kernels as p3maze_step.
-    Charge assignment adds with FP32 atomics, so summation order (and the
-    last bits) differs between runs: forces by ~1e-7 relative, which moves
-    positions by ~1e-7 x |a| t^2 / 2 ~ 4e-9 A after 6 fs at the random
-    start's accelerations (|a| ~ 2e-3 A/fs^2); bound 1e-7 A."""
+    Every kernel of a step is deterministic (the charge assignment adds each
+    mesh point's contributions in a fixed order, with no atomics), so the two
+    trajectories agree bit for bit."""
     with _ctx(P, nacl512, precision="mixed", tol=1e-8) as a, _ctx(P, nacl512, precision="mixed", tol=1e-8) as b:
         a.step(6)
         b.step_async(6)
         b.wait()
-        np.testing.assert_allclose(b.positions(), a.positions(), rtol=0, atol=1e-7)
-        assert rel_rms(b.forces(), a.forces()) < 1e-5
+        np.testing.assert_array_equal(b.positions(), a.positions())
+        np.testing.assert_array_equal(b.forces(), a.forces())
         assert b.stats()["steps"] == a.stats()["steps"] == 6
 
 
