@@ -2,12 +2,15 @@
 
 Requests -- "advance this system by N MD steps" -- arrive over time.  The
 server admits them as batch slots and device memory free up (the memory a
-system needs comes from p3maze_device_bytes), keeps every admitted system's
-particles, meshes and multigrid hierarchy resident, advances all resident
-systems together (one batch step per iteration: each member replays its
-captured step graph on its own stream, so their kernels overlap on the
-device), and retires each system when its steps are done.  Requests that
-arrive while others are running join at the next iteration.
+system needs comes from p3maze_device_bytes), prepares each admitted system
+on an admission thread (its seeded configuration, its context, the initial
+constraint solve and its first steps) while the resident systems keep
+stepping, keeps every admitted system's particles, meshes and multigrid
+hierarchy resident, advances all resident systems together (one batch step
+per iteration: each member replays its captured step graph on its own
+stream, so their kernels overlap on the device), and retires each system
+when its steps are done.  Requests that arrive while others are running
+join at a step boundary once prepared.
 
 The GPU work sits behind a small backend interface so that the admission and
 bookkeeping logic can be exercised on the CPU with a fake backend.
@@ -37,9 +40,10 @@ class Request:
     arrival: float           # seconds after the start of the run
     admitted: float | None = None
     finished: float | None = None
-    status: str = "queued"   # queued, running, done, failed, rejected
+    status: str = "queued"   # queued, starting, running, done, failed, rejected
     step_latencies: list = field(default_factory=list)
     result: dict = field(default_factory=dict)
+    admit_host_s: float = 0.0  # host time of the preparation (system, context, first steps)
 
 
 def allowed_mesh(target: float, lo: int = 16, hi: int = 128) -> int:
@@ -91,28 +95,79 @@ def poisson_requests(n: int, rate: float, seed: int, lo: int = 216, hi: int = 32
 
 # ----------------------------------------------------------------- backends
 class GpuBackend:
-    """Resident contexts in a per-member batch on the current CUDA device."""
+    """Resident contexts in a per-member batch on the current CUDA device.
 
-    def __init__(self, precision: str = "mixed", stream: int | None = None):
+    Admission work runs on a host thread of its own: the request's seeded
+    system is generated, its context created (device allocation, the initial
+    constraint solve) and advanced by its first steps (the ones that fill the
+    multiplier history and test convergence on the host), all on the
+    admission stream, while the stepping thread keeps advancing the batch.
+    A prepared context joins the batch at the next step boundary.  One
+    admission thread: contexts are created one at a time (a context is used
+    by one thread at a time -- the admission thread until it hands it over).
+    """
+
+    WARMUP_STEPS = 3                        # fills the predictor history of any order
+
+    def __init__(self, precision: str = "mixed", stream: int | None = None, admit_stream: int | None = None):
+        import queue
+        import threading
+
         from . import p3maze as P
 
         self.P = P
         self.precision = precision
         self.stream = stream
+        self.admit_stream = admit_stream
         self.batch = P.Batch(stream=stream, mode="per_member")
         self.clock = time.perf_counter
         self.steps = {}                     # host-side step count per member
+        self._todo = queue.Queue()
+        self._ready = queue.Queue()
+        self._worker = threading.Thread(target=self._admit_loop, name="p3maze-admission", daemon=True)
+        self._worker.start()
 
     def estimate(self, req: Request) -> int:
         system, prm = request_system(req)
         return self.P.device_bytes(system, precision=self.precision, **prm)
 
-    def open(self, req: Request):
-        system, prm = request_system(req)
-        ctx = self.P.Context.from_system(system, precision=self.precision, stream=self.stream, **prm)
-        self.batch.add(ctx)                 # the first steps run on their own
+    def _admit_loop(self):
+        while True:
+            req = self._todo.get()
+            if req is None:
+                return
+            t0 = time.perf_counter()
+            try:
+                system, prm = request_system(req)
+                ctx = self.P.Context.from_system(system, precision=self.precision, stream=self.admit_stream, **prm)
+                ctx.step(self.WARMUP_STEPS)
+                self._ready.put((req, ctx, time.perf_counter() - t0, None))
+            except Exception as e:          # reported to the stepping thread
+                self._ready.put((req, None, time.perf_counter() - t0, e))
+
+    def submit(self, req: Request):
+        """Queue a request's preparation on the admission thread."""
+        self._todo.put(req)
+
+    def poll(self, block: bool = False) -> list:
+        """Prepared requests: (request, handle or None, admission host seconds,
+        error or None).  block: wait for at least one."""
+        import queue
+
+        out = []
+        try:
+            out.append(self._ready.get(block=block))
+            while True:
+                out.append(self._ready.get_nowait())
+        except queue.Empty:
+            pass
+        return out
+
+    def attach(self, ctx):
+        """Join a prepared context to the batch (its history is full, so no
+        steps run here)."""
+        self.batch.add(ctx)
         self.steps[ctx] = ctx.stats()["steps"]
-        return ctx
 
     def steps_done(self, handle) -> int:
         return self.steps[handle]
@@ -151,11 +206,21 @@ class GpuBackend:
             time.sleep(dt)
 
     def shutdown(self):
+        self._todo.put(None)
+        self._worker.join()
+        for req, ctx, _, _ in self.poll():
+            if ctx is not None:
+                ctx.close()
         self.batch.close()
 
 
 # ----------------------------------------------------------------- server
 class Server:
+    """Continuous batching: the stepping loop reserves a slot and the
+    request's device memory, hands the request to the backend's admission
+    worker, keeps stepping the resident systems, and attaches each prepared
+    system at the next step boundary."""
+
     def __init__(self, backend, budget_bytes: int, max_slots: int, margin: float = 1.05,
                  margin_bytes: int = 4 << 20):
         self.backend = backend
@@ -174,16 +239,33 @@ class Server:
         be = self.backend
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: list[Request] = []
+        starting: dict[int, int] = {}       # rid -> bytes reserved, preparation in flight
         active: dict[int, tuple] = {}       # rid -> (request, handle, bytes)
         t0 = be.clock()
         need = {}
-        while pending or queue or active:
+
+        def attach(ready):
+            for req, handle, host_s, err in ready:
+                nbytes = starting.pop(req.rid)
+                req.admit_host_s = host_s
+                if err is not None or handle is None:
+                    req.status = "failed"
+                    req.finished = be.clock() - t0
+                    self.used -= nbytes
+                    continue
+                be.attach(handle)
+                req.admitted = be.clock() - t0
+                req.status = "running"
+                active[req.rid] = (req, handle, nbytes)
+
+        while pending or queue or active or starting:
             now = be.clock() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.pop(0))
+            attach(be.poll())
             # admission: FIFO, later arrivals may pass a head that does not fit
             for req in list(queue):
-                if len(active) >= self.max_slots:
+                if len(active) + len(starting) >= self.max_slots:
                     break
                 if req.rid not in need:
                     need[req.rid] = self._need(req)
@@ -194,18 +276,22 @@ class Server:
                 if self.used + need[req.rid] > self.budget:
                     continue
                 queue.remove(req)
-                handle = be.open(req)
-                req.admitted = be.clock() - t0
-                req.status = "running"
-                active[req.rid] = (req, handle, need[req.rid])
+                req.status = "starting"
+                starting[req.rid] = need[req.rid]
                 self.used += need[req.rid]
+                be.submit(req)
             self.peak_used = max(self.peak_used, self.used)
-            self.peak_slots = max(self.peak_slots, len(active))
             if not active:
+                if starting:
+                    attach(be.poll(block=True))
+                    continue
                 if pending:
                     be.sleep_until(t0 + pending[0].arrival)
                     continue
+                if queue:
+                    continue
                 break
+            self.peak_slots = max(self.peak_slots, len(active))
             t_step = be.clock()
             failed = be.step()
             lat = be.clock() - t_step
@@ -234,6 +320,7 @@ class Server:
         lat = np.concatenate([np.asarray(r.step_latencies) for r in done]) if done else np.zeros(1)
         rl = np.asarray([r.finished - r.arrival for r in done]) if done else np.zeros(1)
         qw = np.asarray([r.admitted - r.arrival for r in done]) if done else np.zeros(1)
+        ah = np.asarray([getattr(r, "admit_host_s", 0.0) for r in done]) if done else np.zeros(1)
         return {
             "requests": len(requests), "done": len(done),
             "failed": sum(r.status == "failed" for r in requests),
@@ -247,5 +334,7 @@ class Server:
             "request_latency_s_p99": float(np.percentile(rl, 99)),
             "queue_wait_s_p50": float(np.percentile(qw, 50)),
             "queue_wait_s_p99": float(np.percentile(qw, 99)),
+            "admission_host_s_p50": float(np.percentile(ah, 50)),
+            "admission_host_s_p99": float(np.percentile(ah, 99)),
             "peak_bytes": self.peak_used, "peak_slots": self.peak_slots,
         }
