@@ -1,14 +1,15 @@
 // Diffusion smoothing of a caller-owned mesh that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// smoothing: code that is recording a CUDA stream capture (allocation calls
-// are not allowed in a capture), code that runs under a fixed device-memory
-// budget handed out by a host framework that owns every allocation, or
-// callers that must not grow the process's footprint after start-up.  This
-// entry point serves them: the caller passes the input and output meshes, and
-// the only scratch (a ping-pong mesh and the block partial sums of the
-// neutrality mean) lives in one file-scope device array below, reserved on
-// every GPU that loads this library until the process exits.
+// smoothing: code that runs under a fixed device-memory budget handed out by
+// a host framework that owns every allocation (a cudaMalloc behind its back
+// would break its accounting, or fail once the budget is taken), and
+// long-running services that reserve their device memory at start-up and
+// must not grow the process's footprint afterwards.  This entry point serves
+// them: the caller passes the input and output meshes, and the only scratch
+// (a ping-pong mesh and the block partial sums of the neutrality mean) lives
+// in one file-scope device array below, reserved on every GPU that loads this
+// library until the process exits.
 #include "p3maze.h"
 
 #include <cuda_runtime.h>
@@ -38,6 +39,12 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMesh + kNoAllo
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kMaxDevices] = {};
 
+// [a, a + an) and [b, b + bn) share a byte.
+bool overlap(const void* a, size_t an, const void* b, size_t bn) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bn && y < x + an;
+}
+
 int na_fail(int code, const char* msg) {
     p3_set_global_error(msg);  // read back with p3maze_last_error(NULL)
     return code;
@@ -51,7 +58,9 @@ __global__ void k_sub_mean(int64_t m, double* __restrict__ x, const double* __re
 
 // Device address of the scratch array for the current device.  The array's
 // name in host code is only a host-side stand-in, so the address is looked up
-// with cudaGetSymbolAddress once per device, with that device current.
+// with cudaGetSymbolAddress once per device, with that device current, and
+// kept for the life of the process (a cudaDeviceReset in between would leave
+// it stale: calls must not span a reset of the device).
 int scratch_for_current_device(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -73,15 +82,18 @@ int scratch_for_current_device(double** out) {
 extern "C" int p3maze_smooth_noalloc(const double* q, double* qs, int32_t mesh, int32_t steps, double coeff,
                                      void* cuda_stream) {
     if (!q || !qs) return na_fail(P3MAZE_ERR_INVALID, "q and qs must be device pointers");
-    if (q == qs) return na_fail(P3MAZE_ERR_INVALID, "q and qs must not alias");
     if (mesh < 4 || mesh > kNoAllocMaxMesh)
         return na_fail(P3MAZE_ERR_INVALID, "mesh must be 4..64 points per axis (fixed scratch of 2 MiB)");
+    const size_t bytes = sizeof(double) * (size_t)mesh * mesh * mesh;
+    if (overlap(q, bytes, qs, bytes)) return na_fail(P3MAZE_ERR_INVALID, "q and qs must not overlap");
     if (steps < 0) return na_fail(P3MAZE_ERR_INVALID, "steps must be >= 0");
     if (!(coeff > 0.0 && coeff <= 1.0 / 6.0) && steps > 0)
         return na_fail(P3MAZE_ERR_INVALID, "coeff must lie in (0, 1/6]");
     double* scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
+    if (overlap(q, bytes, scratch, sizeof(g_noalloc_scratch)) || overlap(qs, bytes, scratch, sizeof(g_noalloc_scratch)))
+        return na_fail(P3MAZE_ERR_INVALID, "q and qs must not overlap the library's scratch array");
     double* tmp = scratch;
     double* partial = scratch + kNoAllocMesh;
     double* total = partial + kNoAllocPartials;

@@ -1,9 +1,9 @@
 """The allocation-free smoothing entry point, p3maze_smooth_noalloc.
 
 It serves callers that cannot allocate device memory when they need the
-smoothing (code recording a CUDA stream capture, or code under a device-memory
-budget owned by a host framework): its only scratch is a fixed device array in
-the library.  Its output must equal the smoothed charge q^s that the regular
+smoothing (code under a device-memory budget owned by a host framework that
+makes every allocation itself, or services that reserve their memory at
+start-up): its only scratch is a fixed device array in the library.  Its output must equal the smoothed charge q^s that the regular
 context path computes (p3maze_get_mesh, P3MAZE_MESH_QS), within the FP64 mesh
 tolerance of the parity tests, on two calls in a row that share the scratch.
 This file sorts last so that a run stopping at the first failure has already
@@ -56,3 +56,7 @@ def test_smooth_noalloc_rejects_meshes_beyond_its_scratch():
     assert ei.value.code == P.ERR_INVALID and "64" in str(ei.value)
     with pytest.raises(P.P3MaZeError):
         P.smooth_noalloc(buf.data_ptr(), buf.data_ptr(), 8, 1, 0.1, None)
+    # partly overlapping input and output (4^3 doubles each, 8 doubles apart)
+    big = torch.zeros(2 * 64, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.P3MaZeError, match="overlap"):
+        P.smooth_noalloc(big.data_ptr(), big[8:].data_ptr(), 4, 1, 0.1, None)
