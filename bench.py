@@ -64,13 +64,18 @@ def job_ns_per_day(ms_per_step_max: float, world: int, dt_fs: float) -> float:
     return world * ns_per_day(ms_per_step_max * 1e-3, dt_fs)
 
 
-def workload_config(prm, precision):
+def workload_config(prm):
+    """The workload both arms run (identical in the GPU and the oracle line;
+    how each arm computes it is under "settings" and "dtype")."""
     return {
         "workload": "molten NaCl, 32768 ions, L=100.9 A, 128^3 mesh, alpha 0.30/A, r_cut 9 A, "
                     "order-4 B-spline, tol 1e-6, dt 1 fs, NVE",
         "n_particles": 32768, "mesh": prm["mesh"], "tol": prm["tol"], "dt_fs": prm["dt"],
-        "precision": precision, "l2": "flushed (256 MiB write) before every timed step",
+        "l2": "flushed (256 MiB write) before every timed GPU step (inputs of the CPU oracle exceed no cache "
+              "it could reuse across steps)",
         "parallelism": "replicas (one independent system per GPU, no collective)",
+        "parameters": "Fumi-Tosi BMH table written from memory, not verified against the 1964 source "
+                      "(parity does not depend on it: both arms read the same table)",
     }
 
 
@@ -273,14 +278,28 @@ def measured_peaks() -> dict:
 
 
 # ----------------------------------------------------------------- CPU oracle
-def oracle_step_seconds(system, prm, n_sample: int) -> tuple[float, str]:
-    """One step of the oracle's plain FP64 Mass-Zero stepper on one host core:
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def oracle_md_steps(system, prm, steps: int, budget_s: float, warmup: int = 0) -> dict:
+    """Whole MD steps of the oracle's plain FP64 Mass-Zero stepper
+    (oracle.maze_md_step) on one host core, unextrapolated: kick and drift,
     assignment, smoothing, the Verlet-predicted field and its multigrid
     correction to tol (red-black Gauss-Seidel 2+2, exact coarse level at
-    <= 64^3), interpolation, and the short-range forces of n_sample particles
-    scaled to all.  The field history is the exact field at the positions one
-    time step earlier (set up untimed).  Returns the estimated seconds of a
-    full step and a description of the sample."""
+    <= 64^3), field update, interpolation, short-range forces through the
+    oracle's cell list, kick.  The start (exact field and forces at the
+    initial positions) is set up untimed.  Steps are timed until `steps` are
+    done or `budget_s` of timed work is spent (at least one); the steps
+    actually timed are reported."""
     try:
         from threadpoolctl import threadpool_limits
     except ImportError:          # numpy's FFT and array ops run on one thread anyway
@@ -292,47 +311,42 @@ def oracle_step_seconds(system, prm, n_sample: int) -> tuple[float, str]:
 
     from oracle import p3maze_oracle as O
 
-    rng = np.random.default_rng(0)
-    sample = rng.choice(system.n, n_sample, replace=False)
-    n, box = prm["mesh"], system.box
-    h = box / n
-    prev = copy.copy(system)
-    prev.pos = O.wrap(system.pos - prm["dt"] * system.vel, box)
-    phi_k = O.mesh_fields(prev, prm["alpha"], n)["phi"]           # history: phi^k = phi^{k-1}
-    levels = O.mg_levels(n, 64)
+    sysm = copy.deepcopy(system)
+    n, dt = prm["mesh"], prm["dt"]
+    args = (prm["alpha"], prm["r_cut"], n, dt, prm["tol"])
     with threadpool_limits(1):
         t0 = time.perf_counter()
-        sig = O.sigma_of_alpha(prm["alpha"])
-        K, c = O.smoothing_schedule(sig, h)
-        q = O.assign_charges(system.pos, system.charge, box, n)
-        qs = O.smooth(q, K, c)
-        qs -= qs.mean()
-        phi_p = 2.0 * phi_k - phi_k
-        sigma_p = h / (4.0 * np.pi) * O.laplacian7(phi_p) + qs
-        y, iters, _ = O.mg_correction_solve(sigma_p, np.zeros_like(sigma_p), prm["tol"], levels)
-        phi = phi_p - (4.0 * np.pi / h) * y
-        O.interpolate_lr_forces(system.pos, system.charge, box, n, phi)
-        t1 = time.perf_counter()
-        O.sr_forces(system, sig, prm["r_cut"], subset=sample)
-        t2 = time.perf_counter()
-    est = (t1 - t0) + (t2 - t1) * system.n / n_sample
-    desc = (f"one Mass-Zero step on {n}^3 (assignment, {K} smoothing steps, prediction, {iters} multigrid "
-            f"V-cycle(s) to tol {prm['tol']:g}, interpolation) + short-range forces of {n_sample} of "
-            f"{system.n} ions scaled by {system.n / n_sample:g}; 1 thread")
-    return est, desc
+        state = O.maze_initial_state(sysm, prm["alpha"], prm["r_cut"], n)
+        setup_s = time.perf_counter() - t0
+        for _ in range(warmup):
+            O.maze_md_step(sysm, state, *args)
+        sec, sr, iters = [], [], []
+        while len(sec) < max(1, steps):
+            tim = {}
+            t = time.perf_counter()
+            iters.append(O.maze_md_step(sysm, state, *args, timings=tim))
+            sec.append(time.perf_counter() - t)
+            sr.append(tim["sr"])
+            if sum(sec) >= budget_s:
+                break
+    mean = sum(sec) / len(sec)
+    mesh = mean - sum(sr) / len(sr)
+    sigma = O.sigma_of_alpha(prm["alpha"])
+    K, _ = O.smoothing_schedule(sigma, system.box / n)
+    desc = (f"{len(sec)} whole MD step(s) of the FP64 oracle's Mass-Zero stepper on {system.n} ions, {n}^3 "
+            f"({K} smoothing steps, {sum(iters) / len(iters):g} multigrid V-cycles per step to tol "
+            f"{prm['tol']:g}, cell-list short-range forces); 1 thread; untimed set-up {setup_s:.1f} s")
+    return {"sec_per_step": mean, "mesh_sec_per_step": mesh, "sr_sec_per_step": sum(sr) / len(sr),
+            "steps_timed": len(sec), "warmup_run": warmup, "vcycles_per_step": sum(iters) / len(iters),
+            "setup_s": setup_s, "sample": desc}
 
 
-def cpu_baseline(system, prm, budget_s: float = 12.0) -> dict:
-    times, desc = [], ""
-    t_start = time.perf_counter()
-    while time.perf_counter() - t_start < budget_s or not times:
-        est, desc = oracle_step_seconds(system, prm, 64)
-        times.append(est)
-        if len(times) >= 5:
-            break
-    sec = statistics.median(times)
-    return {"value": ns_per_day(sec, prm["dt"]), "unit": "ns/day", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} estimated steps: {desc}", "sec_per_step": sec}
+def cpu_baseline(system, prm, budget_s: float = 15.0) -> dict:
+    r = oracle_md_steps(system, prm, 1, budget_s)
+    return {"value": ns_per_day(r["sec_per_step"], prm["dt"]), "unit": "ns/day", "cores": 1, "kind": "oracle",
+            "sample": r["sample"], "sec_per_step": r["sec_per_step"],
+            "mesh_sec_per_step": r["mesh_sec_per_step"], "sr_sec_per_step": r["sr_sec_per_step"],
+            "cpu_model": cpu_model(), "cores_available": os.cpu_count()}
 
 
 def run_reference(args) -> int:
@@ -341,25 +355,57 @@ def run_reference(args) -> int:
         return 0
     from paper_2606_31379_b300 import synth as S
     system, prm = S.make_workload(WORKLOAD)
-    for _ in range(args.warmup):
-        oracle_step_seconds(system, prm, 64)
-    times, desc = [], ""
-    for _ in range(args.steps):
-        est, desc = oracle_step_seconds(system, prm, 64)
-        times.append(est)
-    sec = sum(times) / len(times)
+    # the oracle has no warm-up effects (no JIT, caches or clocks to settle):
+    # at most one untimed step, and whole steps timed within a bounded budget
+    r = oracle_md_steps(system, prm, args.steps, budget_s=args.reference_budget, warmup=min(args.warmup, 1))
+    sec = r["sec_per_step"]
     value = ns_per_day(sec, prm["dt"])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "steps": r["steps_timed"], "warmup": r["warmup_run"], "steps_requested": args.steps,
+        "warmup_requested": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA,
-        "config": workload_config(prm, "fp64 (CPU oracle)"),
-        "cpu_baseline": {"value": value, "unit": "ns/day", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: {desc}"},
+        "config": workload_config(prm),
+        "settings": {"precision": "fp64 (CPU oracle)", "start": "seeded random configuration (no equilibration)"},
+        "cpu_baseline": {"value": value, "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": r["sample"],
+                         "mesh_sec_per_step": r["mesh_sec_per_step"], "sr_sec_per_step": r["sr_sec_per_step"],
+                         "cpu_model": cpu_model(), "cores_available": os.cpu_count()},
         "e2e": {"value": value, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+# ----------------------------------------------------------------- accuracy
+def accuracy_vs_oracle(ctx, system, prm, n_sample: int = 64) -> dict:
+    """Errors of a context's observables against the FP64 oracle at the
+    context's own current positions: the mesh force of every particle and the
+    total force of a seeded sample (relative RMS), and each energy term of
+    Eqs. 5, 6 and 14 plus the non-Coulomb term (relative error)."""
+    import copy
+
+    from oracle import p3maze_oracle as O
+
+    s = copy.copy(system)
+    s.pos = ctx.positions()
+    sample = np.random.default_rng(7).choice(s.n, n_sample, replace=False)
+    mf = O.mesh_fields(s, prm["alpha"], prm["mesh"])
+    F_lr = O.interpolate_lr_forces(s.pos, s.charge, s.box, prm["mesh"], mf["phi"])
+    F_sr_s, _, _ = O.sr_forces(s, mf["sigma"], prm["r_cut"], subset=sample)
+    _, ec, ev = O.sr_forces_cells(s, mf["sigma"], prm["r_cut"])
+    ref = {"v_lr": 0.5 * O.COULOMB_K * float((mf["phi"] * mf["q"]).sum()), "v_sr": float(ec.sum()),
+           "v_vdw": float(ev.sum()), "v_self": O.self_energy(s.charge, mf["sigma"])}
+
+    def rel_rms(a, b):
+        return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+    e = ctx.energy()
+    return {"force_lr_rel_rms": rel_rms(ctx.forces("lr"), F_lr),
+            "force_rel_rms_sampled": rel_rms(ctx.forces()[sample], F_lr[sample] + F_sr_s),
+            "energy_rel_err": {k: abs(e[k] - v) / abs(v) for k, v in ref.items()},
+            "sample": f"{n_sample} particles (seeded) for the total force; mesh force and energies over all "
+                      f"{s.n}; oracle field by the FFT solve, short-range energy through the oracle's cell list",
+            "bars": {"force_rel_rms": "1e-5 (FP64) / 1e-4 (mixed)"}}
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -478,6 +524,7 @@ def run_ours(args) -> int:
     n_alone = max(5, args.steps // 2)
     time_context(ctx, torch, stream, n_alone, flush)
     alone_launch_us = 1e3 * ctx.timing()["ms"]["smooth"] / n_alone / K_smooth
+    accuracy = None if (args.no_accuracy or rank != 0) else accuracy_vs_oracle(ctx, system, prm)
     ctx.close()
 
     # beside the headline: the plain FP64 path, the multiplier predictors and
@@ -512,12 +559,17 @@ def run_ours(args) -> int:
             time_context(cv, torch, stream, args.steps, flush)
             tv = cv.timing()
             msv_step = max_over_ranks(sum(msv), world, device="cuda") / args.steps
+            if name == "fp64" and not args.no_accuracy and rank == 0:
+                acc_v = accuracy_vs_oracle(cv, system, prm)
+            else:
+                acc_v = None
             variants[name] = {
                 "value": job_ns_per_day(msv_step, world, prm["dt"]),
                 "ms_per_step": msv_step,
                 "mg_iters_per_step": itv,
                 "stage_us": {k: 1e3 * v / args.steps for k, v in tv["ms"].items()},
                 "settings": {k: v for k, v in kw.items()},
+                "accuracy_vs_oracle": acc_v,
                 "tuning": tv_tune,
             }
             cv.close()
@@ -550,15 +602,17 @@ def run_ours(args) -> int:
         "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": DATA,
-        "config": dict(workload_config(prm, args.precision), graphs=not args.no_graphs, tuning=tuning,
-                       start=f"seeded random configuration equilibrated {args.equilibrate} steps at 1200 K "
-                             "(velocity rescaling), untimed"),
+        "config": workload_config(prm),
+        "settings": {"precision": args.precision, "graphs": not args.no_graphs, "tuning": tuning,
+                     "start": f"seeded random configuration equilibrated {args.equilibrate} steps at 1200 K "
+                              "(velocity rescaling), untimed"},
         "lr_step_us": sum(stage_us[k] for k in lr_stages),
         "stage_us": stage_us, "mg_iters_per_step": iters,
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
         "ms_per_step_with_stage_events": sum(ms_staged) / args.steps,
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
+        "accuracy_vs_oracle": accuracy,
         "roofline_alone": {
             "kernel": "k_diffuse4 (one diffusion step per launch, 2 planes per thread, nothing beside it)",
             "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
@@ -677,7 +731,10 @@ def main() -> int:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-budget", type=float, default=120.0,
+                    help="seconds of timed oracle work in --impl reference (whole steps, at least one)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle check of the timed states")
     ap.add_argument("--no-tune", action="store_true", help="skip the solver-setting autotuner")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-batch measurement")
     ap.add_argument("--tuning", type=str, default=None,
