@@ -228,7 +228,11 @@ typedef struct {
     int32_t post_sweeps;
     int32_t diffusion_zc;       /* z planes per thread (block) of the diffusion kernel  */
     int32_t diffusion_fuse;     /* diffusion steps per launch: 1; 2 (two steps as one 25-point
-                                   stencil, FP32, N % 4 == 0); 3 or 4 (temporal blocking)   */
+                                   stencil, FP32, N % 4 == 0); 3 or 4 (temporal blocking);
+                                   5: all K steps in one launch, the mesh resident in the
+                                   shared memory of a 16-CTA thread-block cluster (FP32,
+                                   16 <= N <= 64, N % 4 == 0; the default there when the
+                                   device runs such clusters)                                */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
     int32_t pair_blocks;        /* pair-kernel grid: 0 one block per home box, else that many
@@ -372,7 +376,7 @@ int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
  * conditional graph nodes.                                                    */
 /* Apply a setting (as p3maze_autotune returns it) without timing anything:
  * predictor (1..3; ignored for P3M), pre_sweeps >= 1, post_sweeps >= 0,
- * diffusion_zc >= 1, diffusion_fuse 1..4, pair_fork 0 or 1, coarse_max >= 1,
+ * diffusion_zc >= 1, diffusion_fuse 1..5, pair_fork 0 or 1, coarse_max >= 1,
  * pair_blocks >= 0; the timing fields are ignored.  Captured step graphs are
  * dropped.  Errors: INVALID (out-of-range field, nothing changed).            */
 int p3maze_set_tuning(p3maze_ctx *ctx, const p3maze_tuning *setting);
@@ -466,9 +470,15 @@ int p3maze_batch_size(const p3maze_batch *batch);
 
 /* P3MAZE_BATCH_SHARED_GRAPH (default): one graph launch per batch step, the
  * graph recorded again after every membership change.  P3MAZE_BATCH_PER_MEMBER:
- * each member replays its own cached step graph on its own stream (forked
- * from and joined to the batch stream) -- one launch per member, no
- * re-recording when members come and go; used by the serving loop.             */
+ * each member replays its own cached step graphs on its own stream (forked
+ * from and joined to the batch stream), with no re-recording when members
+ * come and go; used by the serving loop.  There the members whose smoothing
+ * runs as a cluster launch (diffusion_fuse 5) are smoothed together: every
+ * member's step head (kick/drift, cell list, assignment), then ONE launch
+ * with one 16-CTA cluster per such member doing all their diffusion steps,
+ * then the step tails (solve, interpolation, kick); the results are those of
+ * each member stepped alone, bit for bit.  The batch allocates a small
+ * device table of those members (its only device allocation).               */
 #define P3MAZE_BATCH_SHARED_GRAPH 0
 #define P3MAZE_BATCH_PER_MEMBER   1
 int p3maze_batch_set_mode(p3maze_batch *batch, int32_t mode);

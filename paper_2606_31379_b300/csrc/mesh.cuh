@@ -4,6 +4,8 @@
 // index (iz*N + iy)*N + ix.  T is the bulk mesh type (double or float).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace p3 {
@@ -427,6 +429,109 @@ k_diffuse4(int n, const float* __restrict__ in, float* __restrict__ out, float c
     }
 }
 
+// All K diffusion steps of small FP32 meshes in one launch, the mesh resident
+// in the distributed shared memory of a thread-block cluster.  One cluster of
+// kClCTAs CTAs per mesh (16 <= n <= 64, n % 4 == 0); CTA r owns the z planes
+// [r n / kClCTAs, (r+1) n / kClCTAs) in two shared-memory buffers.  A step
+// reads the planes of the current buffer -- the slab's first and last planes'
+// outer neighbours from the adjacent CTAs' shared memory (periodic over the
+// cluster) -- and writes the next buffer; one cluster barrier separates the
+// steps, so every CTA reads only planes the whole cluster has finished.  The
+// per-point arithmetic is k_diffuse4's (same operands, same order).  The
+// first step reads q from memory, the last writes q^s and the compensated
+// FP32 sums of its outputs; rank 0 adds the CTAs' FP64 sums in rank order
+// into the mesh's neutrality sum.  The launch covers every mesh of a table
+// (one cluster each), so many systems' smoothing is one launch.
+constexpr int kClCTAs = 16;        // cluster size (non-portable; opted in per kernel)
+constexpr int kClThreads = 512;
+constexpr int kClMinN = 16, kClMaxN = 64;
+
+struct ClusterMesh {
+    const float* q;    // assigned charge, n^3
+    float* qs;         // smoothed charge, n^3
+    double* qsum;      // FP64 sum of qs (neutrality mean)
+    int n, K;
+    float c;
+    int pad;
+};
+
+inline int cluster_planes(int n) { return (n + kClCTAs - 1) / kClCTAs; }
+inline size_t cluster_smem_bytes(int nmax) {
+    return 2 * sizeof(float) * (size_t)cluster_planes(nmax) * nmax * nmax + 16;
+}
+inline bool cluster_mesh_ok(int n) { return n >= kClMinN && n <= kClMaxN && n % 4 == 0; }
+
+static __global__ void __launch_bounds__(kClThreads)
+k_diffuse_cluster(const ClusterMesh* __restrict__ tab) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    __shared__ double psum;
+    const int member = blockIdx.x / kClCTAs;
+    const int rank = (int)cluster.block_rank();
+    pdl_wait();  // q comes from the assignment kernel
+    pdl_trigger();
+    const ClusterMesh M = tab[member];
+    const int n = M.n, nq = n >> 2, plane = n * n, plane4 = plane >> 2;
+    const int z0 = rank * n / kClCTAs, z1 = (rank + 1) * n / kClCTAs, p = z1 - z0;
+    const int pmax = (n + kClCTAs - 1) / kClCTAs;
+    float* const buf0 = reinterpret_cast<float*>(cl_raw);
+    float* const buf1 = buf0 + (size_t)pmax * plane;
+    const int lo = (rank + kClCTAs - 1) % kClCTAs, hi = (rank + 1) % kClCTAs;
+    const int p_lo = (lo + 1) * n / kClCTAs - lo * n / kClCTAs;  // planes of the CTA below
+    const float4* q4 = reinterpret_cast<const float4*>(M.q) + (size_t)z0 * plane4;
+    float4* a4 = reinterpret_cast<float4*>(buf0);
+    for (int i = threadIdx.x; i < p * plane4; i += kClThreads) a4[i] = q4[i];
+    cluster.sync();
+    const float c = M.c;
+    float acc_s = 0.0f, acc_c = 0.0f;
+    for (int st = 0; st < M.K; ++st) {
+        const float* A = (st & 1) ? buf1 : buf0;
+        float* B = (st & 1) ? buf0 : buf1;
+        const float* Alo = cluster.map_shared_rank(const_cast<float*>(A), lo) + (size_t)(p_lo - 1) * plane;
+        const float* Ahi = cluster.map_shared_rank(const_cast<float*>(A), hi);
+        const bool last = st == M.K - 1;
+        for (int i = threadIdx.x; i < p * plane4; i += kClThreads) {
+            const int zl = i / plane4, r = i - zl * plane4, y = r / nq, qx = r - y * nq, x = 4 * qx;
+            const float* Ap = A + (size_t)zl * plane;
+            const float4 vc = reinterpret_cast<const float4*>(Ap)[r];
+            const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
+            const float4 a = reinterpret_cast<const float4*>(Ap + ym * n)[qx];
+            const float4 b = reinterpret_cast<const float4*>(Ap + yp * n)[qx];
+            const float* Zm = zl > 0 ? Ap - plane : Alo;
+            const float* Zp = zl < p - 1 ? Ap + plane : Ahi;
+            const float4 vm = *reinterpret_cast<const float4*>(Zm + y * n + x);
+            const float4 vp = *reinterpret_cast<const float4*>(Zp + y * n + x);
+            const float left = Ap[y * n + (x == 0 ? n - 1 : x - 1)];
+            const float right = Ap[y * n + (x + 4 == n ? 0 : x + 4)];
+            float4 o;
+            o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
+            o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
+            o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
+            o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
+            if (last) {
+                reinterpret_cast<float4*>(M.qs)[(size_t)z0 * plane4 + i] = o;
+                two_sum_add(acc_s, acc_c, o.x);
+                two_sum_add(acc_s, acc_c, o.y);
+                two_sum_add(acc_s, acc_c, o.z);
+                two_sum_add(acc_s, acc_c, o.w);
+            } else {
+                reinterpret_cast<float4*>(B)[i] = o;
+            }
+        }
+        cluster.sync();  // B complete everywhere before anyone reads it; A free
+    }
+    const double bs = block_sum((double)acc_s + (double)acc_c);
+    if (threadIdx.x == 0) psum = bs;
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int r = 0; r < kClCTAs; ++r) tot += *cluster.map_shared_rank(&psum, r);
+        M.qsum[0] = tot;
+    }
+    cluster.sync();  // the other CTAs' psum stays alive until rank 0 has read it
+}
+
 // Two explicit diffusion steps in one pass: (I + cM)^2 written out as one
 // 25-point stencil,
 //   (I + cM)^2 = (1 - 12c + 42c^2) I + (2c - 12c^2) S1 + c^2 S2 + 2c^2 D,
@@ -661,9 +766,14 @@ static __global__ void k_sum_final(int nb, const double* __restrict__ partial, d
 // 3 is a triple integrator of whatever constant the V-cycles leave behind --
 // so a constant that is not removed grows with the step count until it
 // swamps the precision of phi.  Each history buffer therefore carries its
-// own sum in one extra slot, written by the field-update kernel that stores
-// it, and the predictor removes the mean of its guess: a constant shift of
-// the guess leaves every residual and every force unchanged.
+// own sum in one extra slot, and the predictor removes the mean of its
+// guess: a constant shift of the guess leaves every residual and every force
+// unchanged.  FP64: the field-update kernel measures the sum of y* (its
+// rounding does not propagate, the next step measures again).  Mixed: the
+// sum of z in fixed point is kept exactly in 64-bit integers -- the
+// prediction records the guess's exact remainder after removing an integer
+// mean, each residual update adds its increments' exact sum -- so the
+// recorded sums equal the buffers' sums bit for bit.
 //
 // Block sums of v, reduced to *out by the block that finishes last (fixed
 // order over the partials, so the sum is the same on every run).
@@ -833,13 +943,12 @@ __device__ __forceinline__ fix_t charge_term(float qs, float mean, float u) {
 //   phi^{k+1} = 2 phi^k - phi^{k-1} - z*
 //   Psi^{k+1} = M phi^{k+1} = r_final - (4pi/h)(q^s - mean)
 // and the FP32 copy of phi^{k+1} - phi^k[0] for the interpolation.
-// Grid-stride over the points; the sum of z* (as FP64, in units of the
-// fixed point) goes to slot m of z's buffer (gauge mode).
+// (The sum of z*, slot m of z's buffer, is kept by the prediction and the
+// residual updates: see k_predict_resid_fix and k_resid_update_fix.)
 static __global__ void __launch_bounds__(P3_THREADS)
 k_update_fix(int64_t m, const fix_t* __restrict__ phik, fix_t* __restrict__ phikm1, fix_t* __restrict__ Psikm1,
-             fix_t* __restrict__ z, const fix_t* __restrict__ rfin, const float* __restrict__ qs,
-             const double* __restrict__ qsum, double inv_pts, float u, float* __restrict__ phi32,
-             double* __restrict__ partial, unsigned* __restrict__ arrive) {
+             const fix_t* __restrict__ z, const fix_t* __restrict__ rfin, const float* __restrict__ qs,
+             const double* __restrict__ qsum, double inv_pts, float u, float* __restrict__ phi32) {
     __shared__ float mean_s;
     __shared__ fix_t ref_s;
     if (threadIdx.x == 0) {
@@ -847,16 +956,12 @@ k_update_fix(int64_t m, const fix_t* __restrict__ phik, fix_t* __restrict__ phik
         ref_s = phik[0];
     }
     __syncthreads();
-    double zs = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const fix_t zi = z[i];
-        zs += (double)zi;
-        const fix_t p = 2 * phik[i] - phikm1[i] - zi;
-        phikm1[i] = p;
-        Psikm1[i] = rfin[i] - charge_term(qs[i], mean_s, u);
-        phi32[i] = fix_to_float(p - ref_s);
-    }
-    sum_last_block(zs, partial, arrive, reinterpret_cast<double*>(z + m));
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const fix_t p = 2 * phik[i] - phikm1[i] - z[i];
+    phikm1[i] = p;
+    Psikm1[i] = rfin[i] - charge_term(qs[i], mean_s, u);
+    phi32[i] = fix_to_float(p - ref_s);
 }
 
 // Partial sums of (phi_i - phi_0) b_i with phi in fixed point (energy
@@ -931,15 +1036,37 @@ struct CheckArgs {
     MGState* st;
     cudaGraphConditionalHandle handle;
     int use_handle;
+    long long* bsum;     // optional: exact block sums of the increments (gauge mode) ...
+    long long* sum_out;  // ... added into *sum_out by the last block
 };
 
-__device__ __forceinline__ void fused_check(float am, const CheckArgs& ck) {
+// Block-wide sum of a 64-bit integer (all threads get the result).
+__device__ __forceinline__ long long block_sum_ll(long long v) {
+    __shared__ long long shl[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int tid = linear_tid(), lane = tid & 31, wid = tid >> 5;
+    __syncthreads();
+    if (lane == 0) shl[wid] = v;
+    __syncthreads();
+    const int nw = (block_threads() + 31) >> 5;
+    v = (tid < nw) ? shl[tid] : 0ll;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tid == 0) shl[0] = v;
+    __syncthreads();
+    v = shl[0];
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ void fused_check(float am, const CheckArgs& ck, long long bs = 0) {
     __shared__ int last_s;
     const int tid = linear_tid();
     const int nb = gridDim.x * gridDim.y * gridDim.z;
     const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (tid == 0) {
         ck.bmax[b] = (double)am;
+        if (ck.sum_out) ck.bsum[b] = bs;
         __threadfence();
         last_s = atomicAdd(&ck.st->arrive, 1u) == (unsigned)(nb - 1);
     }
@@ -947,10 +1074,16 @@ __device__ __forceinline__ void fused_check(float am, const CheckArgs& ck) {
     if (!last_s) return;
     __threadfence();
     float a = 0.0f;
-    for (int i = tid; i < nb; i += block_threads()) a = fmaxf(a, (float)__ldcg(ck.bmax + i));
+    long long sacc = 0;
+    for (int i = tid; i < nb; i += block_threads()) {
+        a = fmaxf(a, (float)__ldcg(ck.bmax + i));
+        if (ck.sum_out) sacc += __ldcg(ck.bsum + i);
+    }
     a = block_max_f(a);
+    if (ck.sum_out) sacc = block_sum_ll(sacc);
     if (tid == 0) {
         ck.st->arrive = 0;
+        if (ck.sum_out) *ck.sum_out += sacc;
         mg_decide((double)a, ck.tol, ck.itmax, ck.st, ck.handle, ck.use_handle);
     }
 }
@@ -983,9 +1116,16 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         mean_s = (float)(qsum[0] * inv_pts);
         const int64_t m = (int64_t)n * n * n;
-        gmean_s = (fix_t)llrint(guess_mean(ORDER, reinterpret_cast<const double*>(z1),
-                                           reinterpret_cast<const double*>(z2),
-                                           reinterpret_cast<const double*>(z3), m));
+        // exact sums in fixed point: the guess's sum is the same combination
+        // of the history sums (slot m of each buffer); an integer mean is
+        // removed and the exact remainder recorded (the V-cycles' increments
+        // are added by the residual updates), so the recorded sums never
+        // drift from the buffers' true sums
+        const fix_t sg = ORDER == 1 ? z1[m] : ORDER == 2 ? 2 * z1[m] - z2[m]
+                                                         : ORDER == 3 ? 3 * (z1[m] - z2[m]) + z3[m] : (fix_t)0;
+        const fix_t gm = sg / (fix_t)m;
+        gmean_s = gm;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) z0[m] = sg - (fix_t)m * gm;
     }
     __syncthreads();
     const fix_t gmean = gmean_s;
@@ -1037,6 +1177,7 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
     const int x = blockIdx.x * P3_BX + threadIdx.x;
     const int y = blockIdx.y * P3_BY + threadIdx.y;
     float a = 0.0f;
+    long long es = 0;  // exact sum of the increments (gauge-mode bookkeeping of z's sum)
     auto fx_of = [](float v) { return fabsf(v) < 8.0e6f ? float_to_fix(v) : (fix_t)0; };
     if (x < n && y < n) {
         const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
@@ -1052,6 +1193,7 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
                              fx_of(e[(zz * n + yp) * n + x]) + fx_of(e[(zm * n + y) * n + x]) +
                              fx_of(e[(zp * n + y) * n + x]);
             z[i] += E;
+            es += E;
             const fix_t res = rfin[i] - (nb - 6 * E);
             rfin[i] = res;
             const float v = fix_to_float(res);
@@ -1059,7 +1201,8 @@ k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fi
             a = fmaxf(a, fabsf(v));
         }
     }
-    fused_check(block_max_f(a), ck);
+    const float am = block_max_f(a);
+    fused_check(am, ck, ck.sum_out ? block_sum_ll(es) : 0ll);
 }
 
 // ---------------------------------------------------------------- multigrid

@@ -25,6 +25,7 @@ thread_local std::string g_init_error = "no error";
 constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
 constexpr int kLevelMin = 16;       // levels are halved while even and larger than this
 constexpr int kMaxGraphs = 4;       // pointer phases of the phi (2) and y (4) rings
+constexpr int kMaxStepGraphs = 2 * kMaxGraphs + 1;  // whole steps, tails (per phase) and one head
 
 // Device scalar slots.
 enum { S_QSUM = 0, S_ESR, S_EVDW, S_VLR, S_MV2, S_EBOND, S_EXCL, S_NSCAL };
@@ -43,8 +44,11 @@ struct Level {
 };
 
 // One captured MD step for a given pointer phase of the field rings.
+enum { PART_ALL = 0, PART_HEAD = 1, PART_TAIL = 2 };  // what a step graph records
+
 struct StepGraph {
     bool valid = false;
+    int part = PART_ALL;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     int icur = 0;
@@ -54,9 +58,6 @@ struct StepGraph {
 };
 
 inline unsigned nblk(int64_t m) { return (unsigned)((m + P3_THREADS - 1) / P3_THREADS); }
-// Field-update grid: grid-stride, at most 1024 blocks (the partial-sum
-// buffer holds at least 1024 entries).
-inline unsigned update_blocks(int64_t m) { return std::min(nblk(m), 1024u); }
 
 // In mixed precision the 8-byte constraint arrays (phi, Psi, z history, s,
 // final residual) hold 64-bit fixed-point values (x 2^40, potential units).
@@ -93,7 +94,10 @@ struct p3maze_ctx {
     int sr_shift = 0;                    // P3MAZE_SR_TRUNCATE or P3MAZE_SR_SHIFT_FORCE
     int nsm = 148;                       // SMs of the device
     bool pdl = true;                     // chained mesh kernels overlap their predecessor's tail (P3MAZE_PDL=0: off)
-    int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 or 4 (tunable)
+    int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 to 4, or 5: all in one
+                                         // cluster launch (16 <= N <= 64) (tunable)
+    ClusterMesh* cltab = nullptr;        // this mesh's entry for the cluster smoothing kernel
+    bool cluster_ok = false;             // the device runs 16-CTA clusters of the smoothing kernel
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
     int64_t P = 0;
@@ -139,7 +143,7 @@ struct p3maze_ctx {
     bool use_graphs = true;
     bool capturing = false;
     bool in_body = false;
-    StepGraph graphs[kMaxGraphs];
+    StepGraph graphs[kMaxStepGraphs];
     int64_t body_launches = 0;       // kernels per V-cycle iteration of the while body
     int64_t eager_iters = 0;         // V-cycles launched outside graphs since the last reset
     int64_t graph_iters_seen = 0;    // graph V-cycles already folded into the launch count
@@ -294,6 +298,11 @@ int build_cells(p3maze_ctx* ctx) {
 constexpr int kTbX = 32, kTbY = 16;
 inline dim3 tb_grid(int n, int zc) { return dim3((n + kTbX - 1) / kTbX, (n + kTbY - 1) / kTbY, (n + zc - 1) / zc); }
 inline unsigned tb_blocks(int n, int zc) { const dim3 g = tb_grid(n, zc); return g.x * g.y * g.z; }
+// Entries of the partial-sum buffer.
+inline unsigned partial_slots(int n) { return std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(n, 1)), tb_blocks(n, 1)); }
+// FP64 field update: grid-stride over at most 1024 blocks (their sums are
+// added by the last block; more blocks would queue on its arrival counter).
+inline unsigned update_blocks(int n) { return std::min(nblk((int64_t)n * n * n), 1024u); }
 
 template <typename T, int S>
 void launch_tb_s(p3maze_ctx* ctx, bool last, const T* src, T* dst) {
@@ -341,6 +350,55 @@ cudaError_t launch_maybe_pdl(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size
     return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
+// All diffusion steps of `members` meshes (table on the device, N <= nmax)
+// in one launch, one 16-CTA cluster per mesh.
+cudaError_t launch_cluster_smoothing(const ClusterMesh* tab, int members, int nmax, cudaStream_t s, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClCTAs * members);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = cluster_smem_bytes(nmax);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClCTAs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, k_diffuse_cluster, tab);
+}
+
+// Whether the device co-schedules 16-CTA clusters of the smoothing kernel
+// with the shared memory of an n = kClMaxN mesh (asked once per process).
+bool cluster_smoothing_supported() {
+    static int cached = -1;
+    if (cached >= 0) return cached == 1;
+    const size_t smem = cluster_smem_bytes(kClMaxN);
+    cudaError_t e = cudaFuncSetAttribute(k_diffuse_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_diffuse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nclusters = 0;
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kClCTAs);
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kClCTAs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&nclusters, k_diffuse_cluster, &cfg);
+    }
+    if (e != cudaSuccess) cudaGetLastError();  // not available: the per-step kernels are used
+    cached = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
+    return cached == 1;
+}
+
 template <int Z>
 cudaError_t diffuse4_z(bool sum, bool pdl, dim3 g, cudaStream_t s, int n, const float* src, float* dst, float c,
                        double* partial) {
@@ -378,7 +436,7 @@ cudaError_t launch_diffuse4x2(int zc4, bool sum, bool pdl, dim3 g, cudaStream_t 
 }
 
 template <typename T>
-int spread_smooth(p3maze_ctx* ctx) {
+int spread_assign(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_SPREAD);
     // deterministic tiled assignment: every mesh point written once
@@ -398,6 +456,14 @@ int spread_smooth(p3maze_ctx* ctx) {
     }
     count(ctx, P3MAZE_ST_SPREAD);
     stage_end(ctx, P3MAZE_ST_SPREAD);
+    CKL();
+    return P3MAZE_OK;
+}
+
+// K diffusion steps q -> q^s and the neutrality sum (Sec. 2; reading A2).
+template <typename T>
+int smooth(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_SMOOTH);
     if (ctx->K == 0) {
         CK(cudaMemcpyAsync(ctx->qs, ctx->q, sizeof(T) * ctx->P, cudaMemcpyDeviceToDevice, s));
@@ -407,7 +473,11 @@ int spread_smooth(p3maze_ctx* ctx) {
     } else if constexpr (sizeof(T) == 4) {
         T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
         const T* src = (const T*)ctx->q;
-        if (ctx->fuse > 2) {
+        if (ctx->fuse == 5) {
+            // every step in one launch, the mesh resident in a cluster's shared memory
+            CK(launch_cluster_smoothing(ctx->cltab, 1, ctx->N, s, false));
+            count(ctx, P3MAZE_ST_SMOOTH, 1);
+        } else if (ctx->fuse > 2) {
             // S = fuse steps per launch (temporal blocking), then the rest
             int done = 0, launches = 0;
             while (done < ctx->K) {
@@ -482,6 +552,12 @@ int spread_smooth(p3maze_ctx* ctx) {
     CKL();
     stage_end(ctx, P3MAZE_ST_SMOOTH);
     return P3MAZE_OK;
+}
+
+template <typename T>
+int spread_smooth(p3maze_ctx* ctx) {
+    int rc = spread_assign<T>(ctx);
+    return rc ? rc : smooth<T>(ctx);
 }
 
 // One V-cycle on M e_l = b_l: levels above the coarse level by grid kernels
@@ -567,8 +643,9 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
 
 // Arguments of the check fused into the mixed-precision residual kernels.
 // P3M: max|M phi + (4pi/h) q^s| = (4pi/h) max|M y - sigma_p| for phi = phi_p - (4pi/h) y.
-CheckArgs check_args(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle) {
-    return CheckArgs{ctx->bmax, ctx->tol * ctx->res_unit / ctx->res_scale, ctx->itmax, ctx->dmg, h, use_handle};
+CheckArgs check_args(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_handle, double* sum_out = nullptr) {
+    return CheckArgs{ctx->bmax, ctx->tol * ctx->res_unit / ctx->res_scale, ctx->itmax, ctx->dmg, h, use_handle,
+                     reinterpret_cast<long long*>(ctx->partial), reinterpret_cast<long long*>(sum_out)};
 }
 
 // FP64: residual of the current y, then the check kernel.
@@ -589,9 +666,10 @@ int launch_iteration(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_hand
     int rc = vcycle<T>(ctx, 0, false);
     if (rc) return rc;
     if (ctx->prec == P3MAZE_MIXED) {
+        // the increments' sum goes to slot P of the correction (gauge mode)
         CK(launch_maybe_pdl(ctx->pdl, k_resid_update_fix, resid_grid(ctx->N), kB3, 0, ctx->stream, ctx->N,
                             fx(ctx->yh[0]), (const float*)ctx->lev[0].e, fx(ctx->rfin), (float*)ctx->lev[0].b,
-                            check_args(ctx, h, use_handle)));
+                            check_args(ctx, h, use_handle, ctx->yh[0] + ctx->P)));
         count(ctx, P3MAZE_ST_SOLVE);
     } else {
         k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0],
@@ -708,12 +786,12 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     stage_end(ctx, P3MAZE_ST_SOLVE);
     stage_begin(ctx, P3MAZE_ST_UPDATE);
     if (fixp)
-        k_update_fix<<<update_blocks(ctx->P), P3_THREADS, 0, s>>>(
+        k_update_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(
             ctx->P, fx(ctx->phi[ik]), fx(ctx->phi[ikm1]), fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
             (const float*)ctx->qs, ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
-            ctx->phi32, ctx->partial, &ctx->dmg->arrive_sum);
+            ctx->phi32);
     else
-        k_update<T><<<update_blocks(ctx->P), P3_THREADS, 0, s>>>(
+        k_update<T><<<update_blocks(ctx->N), P3_THREADS, 0, s>>>(
             ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1], ctx->yh[0], ctx->rfin, (const T*)ctx->qs,
             ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, 4.0 * kPi / ctx->h, ctx->phi32, ctx->partial,
             &ctx->dmg->arrive_sum);
@@ -915,6 +993,40 @@ int step_body(p3maze_ctx* ctx, int order) {
     return P3MAZE_OK;
 }
 
+// A mixed-precision step split at the smoothing, for batches whose members'
+// smoothing runs as one cluster launch over all of them: the head is the
+// kick/drift, the cell list and the assignment (no pointer-phase dependence);
+// the tail forks the short-range branch and runs the solve, interpolation,
+// kick and pointer rotation.  head + cluster smoothing + tail = step_body.
+int step_head(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    stage_begin(ctx, P3MAZE_ST_INTEGRATE);
+    k_kick_drift<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->F, ctx->hdt_acc, ctx->dt, ctx->L);
+    count(ctx, P3MAZE_ST_INTEGRATE);
+    stage_end(ctx, P3MAZE_ST_INTEGRATE);
+    CKL();
+    int rc = build_cells(ctx);
+    return rc ? rc : spread_assign<float>(ctx);
+}
+
+int step_tail(p3maze_ctx* ctx, int order) {
+    int rc = pair_forces(ctx);
+    if (!rc) rc = solve_field<float>(ctx, order);
+    if (!rc) rc = gather_forces(ctx);
+    if (rc) return rc;
+    cudaStream_t s = ctx->stream;
+    k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
+    count(ctx, P3MAZE_ST_GATHER);
+    stage_end(ctx, P3MAZE_ST_GATHER);
+    CKL();
+    double* oldest = ctx->yh[3];
+    ctx->yh[3] = ctx->yh[2];
+    ctx->yh[2] = ctx->yh[1];
+    ctx->yh[1] = ctx->yh[0];
+    ctx->yh[0] = oldest;
+    return P3MAZE_OK;
+}
+
 void destroy_graphs(p3maze_ctx* ctx) {
     for (StepGraph& G : ctx->graphs) {
         if (G.x) cudaGraphExecDestroy(G.x);
@@ -925,7 +1037,7 @@ void destroy_graphs(p3maze_ctx* ctx) {
 
 // Record one steady-state step (full predictor history) for the current
 // pointer phase.  The pointer state is restored afterwards.
-int capture_graph(p3maze_ctx* ctx, StepGraph& G) {
+int capture_graph(p3maze_ctx* ctx, StepGraph& G, int part) {
     cudaStream_t s = ctx->stream;
     int64_t saved[P3MAZE_NSTAGES];
     bool saved_pending[P3MAZE_NSTAGES];
@@ -940,7 +1052,7 @@ int capture_graph(p3maze_ctx* ctx, StepGraph& G) {
     std::memcpy(yh, ctx->yh, sizeof yh);
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     ctx->capturing = true;
-    int rc = step_body(ctx, ctx->pred);
+    int rc = part == PART_HEAD ? step_head(ctx) : part == PART_TAIL ? step_tail(ctx, ctx->pred) : step_body(ctx, ctx->pred);
     ctx->capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -967,15 +1079,20 @@ int capture_graph(p3maze_ctx* ctx, StepGraph& G) {
     }
     G.g = g;
     G.icur = icur;
+    G.part = part;
     std::memcpy(G.yh, yh, sizeof yh);
     G.valid = true;
     return P3MAZE_OK;
 }
 
-int step_graph(p3maze_ctx* ctx) {
+// Replay (recording it first if needed) the graph of a whole step or of a
+// step's head or tail for the current pointer phase (the head has none).
+int step_graph(p3maze_ctx* ctx, int part = PART_ALL) {
     StepGraph* G = nullptr;
     for (StepGraph& sg : ctx->graphs)
-        if (sg.valid && sg.icur == ctx->icur && std::memcmp(sg.yh, ctx->yh, sizeof sg.yh) == 0) G = &sg;
+        if (sg.valid && sg.part == part &&
+            (part == PART_HEAD || (sg.icur == ctx->icur && std::memcmp(sg.yh, ctx->yh, sizeof sg.yh) == 0)))
+            G = &sg;
     if (!G) {
         for (StepGraph& sg : ctx->graphs)
             if (!sg.valid) {
@@ -986,7 +1103,7 @@ int step_graph(p3maze_ctx* ctx) {
             destroy_graphs(ctx);
             G = &ctx->graphs[0];
         }
-        int rc = capture_graph(ctx, *G);
+        int rc = capture_graph(ctx, *G, part);
         if (rc) return rc;
     }
     CK(cudaGraphLaunch(G->x, ctx->stream));
@@ -994,6 +1111,7 @@ int step_graph(p3maze_ctx* ctx) {
         ctx->launches[st] += G->launches[st];
         if (G->timed[st]) ctx->pending[st] = true;
     }
+    if (part == PART_HEAD) return P3MAZE_OK;
     // pointer rotation identical to step_body
     ctx->icur = 1 - ctx->icur;
     double* oldest = ctx->yh[3];
@@ -1219,8 +1337,18 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         if (ea != cudaSuccess)
             return fail(ctx, P3MAZE_ERR_CUDA, std::string("shared memory limits: ") + cudaGetErrorString(ea));
     }
-    ALLOC(ctx->partial, 8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(ctx->N, 1)), tb_blocks(ctx->N, 1)));
+    ALLOC(ctx->partial, 8 * (size_t)partial_slots(ctx->N));
     ALLOC(ctx->dscal, 8 * S_NSCAL);
+    if (mixed && ctx->K > 0 && cluster_mesh_ok(ctx->N)) {
+        // smoothing of the whole mesh in one cluster launch (mode 5) when the
+        // device co-schedules the clusters; the table entry exists either way
+        ALLOC(ctx->cltab, sizeof(ClusterMesh));
+        const ClusterMesh cm{(const float*)ctx->q, (float*)ctx->qs, ctx->dscal + S_QSUM, ctx->N, ctx->K,
+                             (float)ctx->c, 0};
+        CK(cudaMemcpy(ctx->cltab, &cm, sizeof cm, cudaMemcpyHostToDevice));
+        ctx->cluster_ok = cluster_smoothing_supported();
+        if (ctx->cluster_ok) ctx->fuse = 5;
+    }
     {
         const dim3 gr = resid_grid(ctx->N);
         ALLOC(ctx->bmax, 8 * (size_t)gr.x * gr.y * gr.z);
@@ -1325,8 +1453,9 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
         if (nn <= kCoarseMax) b += a(tb * (size_t)nn * nn) + a(tb * pts) + a(tb * pts);  // H D t
         nn /= 2;
     }
-    b += a(8 * (size_t)std::max<unsigned>(std::max<unsigned>(1024, gz_blocks(N, 1)), tb_blocks(N, 1)));
+    b += a(8 * (size_t)partial_slots(N));
     b += a(8 * S_NSCAL);
+    if (mixed && p->method != P3MAZE_METHOD_PMAZE && cluster_mesh_ok(N)) b += a(sizeof(ClusterMesh));
     {
         const dim3 gr = resid_grid(N);
         b += a(8 * (size_t)gr.x * gr.y * gr.z);
@@ -2030,14 +2159,19 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     // thread (one or two steps per launch, N % 4 == 0: 1-8) or per block
     auto diffusion_pass = [&]() {
         if (ctx->K == 0) return;  // no smoothing (PMaZe)
-        const int fuses[3] = {1, 2, 4};
+        const int fuses[4] = {1, 2, 4, 5};
         const int zcs_quad[4] = {1, 2, 4, 8}, zcs_other[4] = {4, 8, 16, 32};
         const Setting base = chosen;
         for (int f : fuses) {
             if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
             if (f == 2 && ctx->N % 4 != 0) continue;
+            if (f == 5 && !ctx->cluster_ok) continue;
             const bool quad = f <= 2 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
-            for (int z : quad ? zcs_quad : zcs_other) {
+            // the cluster kernel has no z planes per thread: one trial
+            std::vector<int> zcs = f == 5 ? std::vector<int>{base.zc}
+                                          : quad ? std::vector<int>(zcs_quad, zcs_quad + 4)
+                                                 : std::vector<int>(zcs_other, zcs_other + 4);
+            for (int z : zcs) {
                 if (z == base.zc && f == base.fuse) continue;
                 Setting c = chosen;
                 c.zc = z;
@@ -2129,11 +2263,14 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
 int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (!ctx || !t) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
     if (t->predictor < 1 || t->predictor > 3 || t->pre_sweeps < 1 || t->post_sweeps < 0 || t->diffusion_zc < 1 ||
-        t->diffusion_fuse < 1 || t->diffusion_fuse > 4 || (t->pair_fork != 0 && t->pair_fork != 1) ||
+        t->diffusion_fuse < 1 || t->diffusion_fuse > 5 || (t->pair_fork != 0 && t->pair_fork != 1) ||
         t->coarse_max < 1 || t->pair_blocks < 0)
         return fail(ctx, P3MAZE_ERR_INVALID, "tuning field out of range");
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
+    if (t->diffusion_fuse == 5 && !ctx->cluster_ok)
+        return fail(ctx, P3MAZE_ERR_INVALID,
+                    "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs 16-CTA clusters");
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = t->predictor;
     ctx->nu1 = t->pre_sweeps;
@@ -2200,6 +2337,13 @@ struct p3maze_batch {
     };
     Phase phases[kMaxGraphs];
     int mode = 0;                       // P3MAZE_BATCH_SHARED_GRAPH or P3MAZE_BATCH_PER_MEMBER
+    // per-member mode: the members smoothed by one cluster launch (mode 5)
+    ClusterMesh* cltab = nullptr;       // device table, cl_cap entries
+    int cl_cap = 0;
+    bool cl_dirty = true;               // membership changed: rebuild the table
+    std::vector<ClusterMesh> cl_host;
+    std::vector<char> cl_member;        // per member: smoothed by the batch's cluster launch
+    int cl_nmax = 0;
     std::string err = "no error";
 };
 
@@ -2334,6 +2478,7 @@ int p3maze_batch_add(p3maze_batch* b, p3maze_ctx* ctx) {
     BCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     b->members.push_back(ctx);
     b->ev_done.push_back(ev);
+    b->cl_dirty = true;
     batch_drop_graphs(b);
     return P3MAZE_OK;
 }
@@ -2346,6 +2491,7 @@ int p3maze_batch_remove(p3maze_batch* b, p3maze_ctx* ctx) {
             cudaEventDestroy(b->ev_done[i]);
             b->members.erase(b->members.begin() + (long)i);
             b->ev_done.erase(b->ev_done.begin() + (long)i);
+            b->cl_dirty = true;
             batch_drop_graphs(b);
             return P3MAZE_OK;
         }
@@ -2358,6 +2504,73 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
     if (b->members.empty() || nsteps == 0) return P3MAZE_OK;
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    if (b->mode == P3MAZE_BATCH_PER_MEMBER && !b->cl_dirty) {
+        // a member's smoothing mode may have been changed (p3maze_set_tuning)
+        for (size_t i = 0; i < b->members.size(); ++i)
+            if ((b->members[i]->fuse == 5) != (b->cl_member[i] != 0)) b->cl_dirty = true;
+    }
+    if (b->mode == P3MAZE_BATCH_PER_MEMBER && b->cl_dirty) {
+        // members whose smoothing is a cluster launch (mode 5) share one
+        b->cl_host.clear();
+        b->cl_member.assign(b->members.size(), 0);
+        b->cl_nmax = 0;
+        for (size_t i = 0; i < b->members.size(); ++i) {
+            p3maze_ctx* m = b->members[i];
+            if (m->fuse != 5) continue;
+            b->cl_member[i] = 1;
+            b->cl_host.push_back(ClusterMesh{(const float*)m->q, (float*)m->qs, m->dscal + S_QSUM, m->N, m->K,
+                                             (float)m->c, 0});
+            b->cl_nmax = std::max(b->cl_nmax, m->N);
+        }
+        if ((int)b->cl_host.size() > b->cl_cap) {
+            BCK(cudaStreamSynchronize(b->origin));
+            if (b->cltab) cudaFree(b->cltab);
+            b->cltab = nullptr;
+            b->cl_cap = 0;
+            const int cap = std::max<int>(16, (int)b->cl_host.size() * 2);
+            BCK(cudaMalloc(&b->cltab, sizeof(ClusterMesh) * cap));
+            b->cl_cap = cap;
+        }
+        if (!b->cl_host.empty())
+            BCK(cudaMemcpyAsync(b->cltab, b->cl_host.data(), sizeof(ClusterMesh) * b->cl_host.size(),
+                                cudaMemcpyHostToDevice, b->origin));
+        b->cl_dirty = false;
+    }
+    if (b->mode == P3MAZE_BATCH_PER_MEMBER && !b->cl_host.empty()) {
+        // heads of every member's step on their own streams; the smoothing of
+        // the cluster members as one launch on the batch stream; then the
+        // tails (members not smoothed there take whole steps in the first fork)
+        for (int k = 0; k < nsteps; ++k) {
+            BCK(cudaEventRecord(b->ev_fork, b->origin));
+            for (size_t i = 0; i < b->members.size(); ++i) {
+                p3maze_ctx* m = b->members[i];
+                BCK(cudaStreamWaitEvent(m->stream, b->ev_fork, 0));
+                int rc = b->cl_member[i] ? step_graph(m, PART_HEAD) : step_once(m);
+                if (rc) return bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
+                BCK(cudaEventRecord(b->ev_done[i], m->stream));
+                BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
+            }
+            BCK(launch_cluster_smoothing(b->cltab, (int)b->cl_host.size(), b->cl_nmax, b->origin, false));
+            BCK(cudaEventRecord(b->ev_fork, b->origin));
+            for (size_t i = 0; i < b->members.size(); ++i) {
+                if (!b->cl_member[i]) continue;
+                p3maze_ctx* m = b->members[i];
+                BCK(cudaStreamWaitEvent(m->stream, b->ev_fork, 0));
+                int rc = step_graph(m, PART_TAIL);
+                if (!rc) {
+                    m->nhist = std::min(m->nhist + 1, 3);
+                    m->st.steps += 1;
+                    rc = collect_timing(m);
+                }
+                if (rc) return bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
+                BCK(cudaEventRecord(b->ev_done[i], m->stream));
+                BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
+            }
+        }
+        BCK(cudaEventRecord(b->ev_out, b->origin));
+        BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+        return P3MAZE_OK;
+    }
     if (b->mode == P3MAZE_BATCH_PER_MEMBER) {
         // each member replays its own cached step graph on its own stream,
         // forked from and joined to the batch stream
@@ -2427,6 +2640,7 @@ int p3maze_batch_set_mode(p3maze_batch* b, int32_t mode) {
         return bfail(b, P3MAZE_ERR_INVALID, "unknown batch mode");
     BCK(cudaStreamSynchronize(b->origin));
     b->mode = mode;
+    b->cl_dirty = true;
     return P3MAZE_OK;
 }
 
@@ -2439,6 +2653,7 @@ void p3maze_batch_destroy(p3maze_batch* b) {
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->cltab) cudaFree(b->cltab);
     delete b;
 }
 

@@ -230,7 +230,8 @@ class Server:
         self.margin_bytes = margin_bytes
         self.used = 0
         self.peak_used = 0
-        self.peak_slots = 0
+        self.peak_slots = 0                 # slots taken: resident systems and systems being prepared
+        self.peak_resident = 0              # systems stepping together on the device
 
     def _need(self, req: Request) -> int:
         return int(self.backend.estimate(req) * self.margin) + self.margin_bytes
@@ -281,6 +282,7 @@ class Server:
                 self.used += need[req.rid]
                 be.submit(req)
             self.peak_used = max(self.peak_used, self.used)
+            self.peak_slots = max(self.peak_slots, len(active) + len(starting))
             if not active:
                 if starting:
                     attach(be.poll(block=True))
@@ -291,7 +293,7 @@ class Server:
                 if queue:
                     continue
                 break
-            self.peak_slots = max(self.peak_slots, len(active))
+            self.peak_resident = max(self.peak_resident, len(active))
             t_step = be.clock()
             failed = be.step()
             lat = be.clock() - t_step
@@ -336,5 +338,5 @@ class Server:
             "queue_wait_s_p99": float(np.percentile(qw, 99)),
             "admission_host_s_p50": float(np.percentile(ah, 50)),
             "admission_host_s_p99": float(np.percentile(ah, 99)),
-            "peak_bytes": self.peak_used, "peak_slots": self.peak_slots,
+            "peak_bytes": self.peak_used, "peak_slots": self.peak_slots, "peak_resident": self.peak_resident,
         }

@@ -74,7 +74,7 @@ def test_every_request_finishes_with_exact_steps_within_budget_and_slots():
         assert r.result["steps"] == 50
         assert len(r.step_latencies) == 50 - 3
         assert r.admitted >= r.arrival - 1e-12 and r.finished > r.admitted
-    assert srv.peak_used <= 12_000_000 and srv.peak_slots <= 6
+    assert srv.peak_used <= 12_000_000 and srv.peak_slots <= 6 and srv.peak_resident <= 6
     assert m["step_latency_ms_p50"] <= m["step_latency_ms_p99"]
     assert m["steps_per_s"] > 0 and m["atom_steps_per_s"] > 0
     # systems overlap: at some point several were resident
