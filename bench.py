@@ -625,27 +625,33 @@ def run_ours(args) -> int:
     }
     if not args.no_serve:
         line["served"] = served_run(stream.cuda_stream, n_req=256, steps=200, slots=16)
+        # the same stream of requests with every member launching its own
+        # diffusion kernels (no shared cluster smoothing), for comparison
+        line["served_per_step_smoothing"] = served_run(stream.cuda_stream, n_req=256, steps=200, slots=16,
+                                                       smoothing="per_step")
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system, prm)
     print(json.dumps(line))
     return 0
 
 
-def served_run(stream, n_req: int, steps: int, slots: int, rate: float = 200.0) -> dict:
+def served_run(stream, n_req: int, steps: int, slots: int, rate: float = 200.0, smoothing: str = "default") -> dict:
     """The served-batch workload: n_req requests with Poisson arrivals,
     molten NaCl or SPC/Fw (50/50), 216-32768 atoms log-uniform, mesh ~0.8 A,
     each advanced `steps` steps, admitted by device memory into `slots`
-    slots."""
+    slots.  smoothing="default": members of at most 64^3 are smoothed by one
+    cluster launch per batch step; "per_step": every member launches its own
+    diffusion kernels (the comparison)."""
     from paper_2606_31379_b300.serve import GpuBackend, Server, poisson_requests
     reqs = poisson_requests(n_req, rate=rate, seed=4, steps=steps)
-    be = GpuBackend(precision="mixed", stream=stream)
+    be = GpuBackend(precision="mixed", stream=stream, smoothing=smoothing)
     try:
         m = Server(be, budget_bytes=60 << 30, max_slots=slots).run(reqs)
     finally:
         be.shutdown()
     m["config"] = {"requests": n_req, "arrival_rate_per_s": rate, "steps_per_request": steps, "slots": slots,
                    "sizes": "216-32768 atoms log-uniform, molten NaCl / SPC/Fw 50:50, mesh ~0.8 A",
-                   "precision": "mixed", "start": "seeded random configurations"}
+                   "precision": "mixed", "start": "seeded random configurations", "smoothing": smoothing}
     return m
 
 

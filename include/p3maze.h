@@ -230,13 +230,19 @@ typedef struct {
     int32_t diffusion_fuse;     /* diffusion steps per launch: 1; 2 (two steps as one 25-point
                                    stencil, FP32, N % 4 == 0); 3 or 4 (temporal blocking);
                                    5: all K steps in one launch, the mesh resident in the
-                                   shared memory of a 16-CTA thread-block cluster (FP32,
+                                   shared memory of a thread-block cluster (FP32,
                                    16 <= N <= 64, N % 4 == 0; the default there when the
                                    device runs such clusters)                                */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
     int32_t pair_blocks;        /* pair-kernel grid: 0 one block per home box, else that many
                                    persistent blocks (one or two per SM)                      */
+    int32_t cluster_ctas;       /* mode 5: CTAs per cluster, 1, 2, 4, 8 or 16, at least the
+                                   fewest whose two slab buffers (2 x 4 ceil(N/ctas) N^2 bytes)
+                                   fit 200 KiB of shared memory; 0 = automatic: 16 for a
+                                   context stepped alone, and in a per-member batch the
+                                   largest that keeps the batch's launch within one CTA
+                                   per SM.  Ignored by the other modes.                      */
     double ms_per_step;         /* measured with the chosen setting                    */
     double initial_ms_per_step; /* measured with the setting in use before tuning      */
     int32_t trials;             /* settings timed                                      */

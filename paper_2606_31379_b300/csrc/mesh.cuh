@@ -430,21 +430,25 @@ k_diffuse4(int n, const float* __restrict__ in, float* __restrict__ out, float c
 }
 
 // All K diffusion steps of small FP32 meshes in one launch, the mesh resident
-// in the distributed shared memory of a thread-block cluster.  One cluster of
-// kClCTAs CTAs per mesh (16 <= n <= 64, n % 4 == 0); CTA r owns the z planes
-// [r n / kClCTAs, (r+1) n / kClCTAs) in two shared-memory buffers.  A step
+// in the (distributed) shared memory of a thread-block cluster.  One cluster
+// of cs CTAs per mesh (16 <= n <= 64, n % 4 == 0; cs = cluster_size_for(n),
+// the fewest CTAs, 1 to 16, whose slabs fit the shared-memory budget); CTA r
+// owns the z planes [r n / cs, (r+1) n / cs) in two shared-memory buffers.  A step
 // reads the planes of the current buffer -- the slab's first and last planes'
 // outer neighbours from the adjacent CTAs' shared memory (periodic over the
 // cluster) -- and writes the next buffer; one cluster barrier separates the
 // steps, so every CTA reads only planes the whole cluster has finished.  The
 // per-point arithmetic is k_diffuse4's (same operands, same order).  The
-// first step reads q from memory, the last writes q^s and the compensated
-// FP32 sums of its outputs; rank 0 adds the CTAs' FP64 sums in rank order
-// into the mesh's neutrality sum.  The launch covers every mesh of a table
-// (one cluster each), so many systems' smoothing is one launch.
-constexpr int kClCTAs = 16;        // cluster size (non-portable; opted in per kernel)
+// first step reads q from memory, the last writes q^s to memory and to the
+// slab.  The neutrality sum is formed per plane (one warp, lanes striding the
+// plane with compensated FP32 sums, a fixed butterfly in FP64) and rank 0
+// adds the planes in z order, so it does not depend on the cluster size.  The
+// launch covers every mesh of a table (one cluster each), so many systems'
+// smoothing is one launch.
+constexpr int kClMaxCTAs = 16;               // largest cluster (non-portable; opted in per kernel)
 constexpr int kClThreads = 512;
 constexpr int kClMinN = 16, kClMaxN = 64;
+constexpr size_t kClSmemBudget = 200 * 1024;  // both slab buffers of one CTA
 
 struct ClusterMesh {
     const float* q;    // assigned charge, n^3
@@ -455,36 +459,47 @@ struct ClusterMesh {
     int pad;
 };
 
-inline int cluster_planes(int n) { return (n + kClCTAs - 1) / kClCTAs; }
-inline size_t cluster_smem_bytes(int nmax) {
-    return 2 * sizeof(float) * (size_t)cluster_planes(nmax) * nmax * nmax + 16;
+inline int cluster_planes(int n, int cs) { return (n + cs - 1) / cs; }
+inline size_t cluster_smem_bytes(int nmax, int cs) {
+    return 2 * sizeof(float) * (size_t)cluster_planes(nmax, cs) * nmax * nmax + 16;
 }
 inline bool cluster_mesh_ok(int n) { return n >= kClMinN && n <= kClMaxN && n % 4 == 0; }
+// CTAs per mesh (a power of two) when `members` meshes share one launch on a
+// device of nsm SMs: at least the fewest whose double-buffered slabs fit the
+// budget, and then doubled while the launch still has at most one CTA per SM
+// (more CTAs per mesh shorten each step; a single mesh gets the largest
+// cluster).
+inline int cluster_size_for(int n, int members = 1, int nsm = 148) {
+    int cs = 1;
+    while (cs < kClMaxCTAs && cluster_smem_bytes(n, cs) > kClSmemBudget + 16) cs *= 2;
+    while (cs < kClMaxCTAs && 2 * cs * members <= nsm) cs *= 2;
+    return cs;
+}
 
 static __global__ void __launch_bounds__(kClThreads)
 k_diffuse_cluster(const ClusterMesh* __restrict__ tab) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char cl_raw[];
-    __shared__ double psum;
-    const int member = blockIdx.x / kClCTAs;
+    __shared__ double psum[kClMaxN];  // per local plane
+    const int cs = (int)cluster.num_blocks();
+    const int member = blockIdx.x / cs;
     const int rank = (int)cluster.block_rank();
     pdl_wait();  // q comes from the assignment kernel
     pdl_trigger();
     const ClusterMesh M = tab[member];
     const int n = M.n, nq = n >> 2, plane = n * n, plane4 = plane >> 2;
-    const int z0 = rank * n / kClCTAs, z1 = (rank + 1) * n / kClCTAs, p = z1 - z0;
-    const int pmax = (n + kClCTAs - 1) / kClCTAs;
+    const int z0 = rank * n / cs, z1 = (rank + 1) * n / cs, p = z1 - z0;
+    const int pmax = (n + cs - 1) / cs;
     float* const buf0 = reinterpret_cast<float*>(cl_raw);
     float* const buf1 = buf0 + (size_t)pmax * plane;
-    const int lo = (rank + kClCTAs - 1) % kClCTAs, hi = (rank + 1) % kClCTAs;
-    const int p_lo = (lo + 1) * n / kClCTAs - lo * n / kClCTAs;  // planes of the CTA below
+    const int lo = (rank + cs - 1) % cs, hi = (rank + 1) % cs;  // itself when cs = 1
+    const int p_lo = (lo + 1) * n / cs - lo * n / cs;           // planes of the CTA below
     const float4* q4 = reinterpret_cast<const float4*>(M.q) + (size_t)z0 * plane4;
     float4* a4 = reinterpret_cast<float4*>(buf0);
     for (int i = threadIdx.x; i < p * plane4; i += kClThreads) a4[i] = q4[i];
     cluster.sync();
     const float c = M.c;
-    float acc_s = 0.0f, acc_c = 0.0f;
     for (int st = 0; st < M.K; ++st) {
         const float* A = (st & 1) ? buf1 : buf0;
         float* B = (st & 1) ? buf0 : buf1;
@@ -509,24 +524,34 @@ k_diffuse_cluster(const ClusterMesh* __restrict__ tab) {
             o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
             o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
             o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
-            if (last) {
-                reinterpret_cast<float4*>(M.qs)[(size_t)z0 * plane4 + i] = o;
-                two_sum_add(acc_s, acc_c, o.x);
-                two_sum_add(acc_s, acc_c, o.y);
-                two_sum_add(acc_s, acc_c, o.z);
-                two_sum_add(acc_s, acc_c, o.w);
-            } else {
-                reinterpret_cast<float4*>(B)[i] = o;
-            }
+            if (last) reinterpret_cast<float4*>(M.qs)[(size_t)z0 * plane4 + i] = o;
+            reinterpret_cast<float4*>(B)[i] = o;
         }
         cluster.sync();  // B complete everywhere before anyone reads it; A free
     }
-    const double bs = block_sum((double)acc_s + (double)acc_c);
-    if (threadIdx.x == 0) psum = bs;
+    // the last step's output is in buffer K & 1 (K >= 1; K = 0 leaves q itself)
+    const float* Q = M.K == 0 ? buf0 : ((M.K & 1) ? buf1 : buf0);
+    if (M.K == 0) {
+        for (int i = threadIdx.x; i < p * plane4; i += kClThreads)
+            reinterpret_cast<float4*>(M.qs)[(size_t)z0 * plane4 + i] = a4[i];
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int zl = warp; zl < p; zl += kClThreads / 32) {
+        const float* Qp = Q + (size_t)zl * plane;
+        float s = 0.0f, e = 0.0f;
+        for (int j = lane; j < plane; j += 32) two_sum_add(s, e, Qp[j]);
+        double v = (double)s + (double)e;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) psum[zl] = v;
+    }
     cluster.sync();
     if (rank == 0 && threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int r = 0; r < kClCTAs; ++r) tot += *cluster.map_shared_rank(&psum, r);
+        double tot = 0.0;  // planes in z order: r ascending, then its planes
+        for (int r = 0; r < cs; ++r) {
+            const double* ps = cluster.map_shared_rank(psum, r);
+            const int pr = (r + 1) * n / cs - r * n / cs;
+            for (int zl = 0; zl < pr; ++zl) tot += ps[zl];
+        }
         M.qsum[0] = tot;
     }
     cluster.sync();  // the other CTAs' psum stays alive until rank 0 has read it
@@ -1169,7 +1194,7 @@ k_predict_resid_fix(int n, const fix_t* __restrict__ Psik, const fix_t* __restri
 //   r_new = s - M (z + E) = r_old - M E,
 // with E at the neighbours converted the same way; check fused.  A
 // non-finite e sets status to NONFINITE (that point is left unchanged).
-static __global__ void __launch_bounds__(P3_BX * P3_BY)
+static __global__ void __launch_bounds__(P3_BX * P3_BY, 8)  // 32 registers: the 1024 blocks of 128^3 in one wave
 k_resid_update_fix(int n, fix_t* __restrict__ z, const float* __restrict__ e, fix_t* __restrict__ rfin,
                    float* __restrict__ r32, CheckArgs ck) {
     pdl_wait();
@@ -1290,119 +1315,6 @@ k_resid_restrict(int nc, const T* __restrict__ e, const T* __restrict__ b, T* __
         }
     }
     bc[(Z * nc + Y) * nc + X] = (T)4 * acc;
-}
-
-// The same residual and full-weighting restriction with every fine residual
-// formed once.  A block owns a tile of kRrCX x kRrCY coarse points and a run
-// of zc coarse planes; it marches the fine planes 2 Z0 - 1 .. 2 Z1 - 1 once:
-// e planes pass through a ring of three haloed tiles in shared memory, the
-// fine residual b - M e of each plane is formed once into a shared tile, and
-// each thread folds the 3 x 3 in-plane weights of its coarse columns into
-// coarse accumulators (z weights 1/4, 1/2, 1/4 as the planes go by).  Each e
-// and b value is read from memory about once (halo 1.25x and 1.1x), against
-// 27 residuals of 7 loads per coarse point in k_resid_restrict.
-constexpr int kRrCX = 32, kRrCY = 16;                        // coarse tile
-constexpr int kRrFW = 2 * kRrCX + 1, kRrFH = 2 * kRrCY + 1;  // fine residual tile
-constexpr int kRrEW = kRrFW + 2, kRrEH = kRrFH + 2;          // e tile with its halo
-constexpr int kRrThreads = 256;
-constexpr int kRrCols = kRrCX * kRrCY / kRrThreads;          // coarse columns per thread
-
-template <typename T>
-inline size_t resid_restrict_smem_bytes() {
-    return sizeof(T) * (3 * kRrEW * kRrEH + kRrFW * kRrFH);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kRrThreads)
-k_resid_restrict_tile(int nc, int zc, const T* __restrict__ e, const T* __restrict__ b, T* __restrict__ bc) {
-    extern __shared__ __align__(16) unsigned char rr_raw[];
-    T* ring = reinterpret_cast<T*>(rr_raw);  // [3][kRrEH][kRrEW]
-    T* R = ring + 3 * kRrEW * kRrEH;         // [kRrFH][kRrFW]
-    pdl_wait();
-    pdl_trigger();
-    const int n = 2 * nc;
-    const int tid = threadIdx.x;
-    const int X0 = blockIdx.x * kRrCX, Y0 = blockIdx.y * kRrCY, Z0 = blockIdx.z * zc;
-    const int Z1 = min(Z0 + zc, nc);
-    auto wr = [n](int v) { return v < 0 ? v + n : (v >= n ? v - n : v); };  // v in [-n, 2n)
-    const int ex0 = 2 * X0 - 2, ey0 = 2 * Y0 - 2;  // e tile origin (fine)
-    // wrapped fine indices of the tile's columns and rows (the tile may span
-    // the periodic axis more than once on small levels)
-    __shared__ int xi[kRrEW], yi[kRrEH];
-    for (int i = tid; i < kRrEW + kRrEH; i += kRrThreads) {
-        if (i < kRrEW) xi[i] = imod(ex0 + i, n);
-        else yi[i - kRrEW] = imod(ey0 + i - kRrEW, n) * n;
-    }
-    __syncthreads();
-    auto load_e = [&](int zf, T* dst) {
-        const T* src = e + (int64_t)wr(zf) * n * n;
-        for (int i = tid; i < kRrEW * kRrEH; i += kRrThreads) {
-            const int x = i % kRrEW, y = i / kRrEW;
-            dst[i] = src[yi[y] + xi[x]];
-        }
-    };
-    const int zf0 = 2 * Z0 - 1;
-    load_e(zf0 - 1, ring);
-    load_e(zf0, ring + kRrEW * kRrEH);
-    // this thread's coarse columns
-    int cx[kRrCols], cy[kRrCols];
-#pragma unroll
-    for (int j = 0; j < kRrCols; ++j) {
-        const int c = tid + j * kRrThreads;
-        cx[j] = c % kRrCX;
-        cy[j] = c / kRrCX;
-    }
-    T acc[kRrCols];
-#pragma unroll
-    for (int j = 0; j < kRrCols; ++j) acc[j] = (T)0;
-    for (int zf = zf0; zf <= 2 * Z1 - 1; ++zf) {
-        T* elo = ring + ((zf - zf0) % 3) * kRrEW * kRrEH;      // plane zf - 1
-        T* emid = ring + ((zf - zf0 + 1) % 3) * kRrEW * kRrEH; // plane zf
-        T* ehi = ring + ((zf - zf0 + 2) % 3) * kRrEW * kRrEH;  // plane zf + 1
-        load_e(zf + 1, ehi);
-        __syncthreads();
-        const T* bp = b + (int64_t)wr(zf) * n * n;
-        for (int i = tid; i < kRrFW * kRrFH; i += kRrThreads) {
-            const int x = i % kRrFW, y = i / kRrFW;
-            const int c = (y + 1) * kRrEW + x + 1;
-            const T nb = emid[c - 1] + emid[c + 1] + emid[c - kRrEW] + emid[c + kRrEW] + elo[c] + ehi[c];
-            R[i] = bp[yi[y + 1] + xi[x + 1]] - (nb - (T)6 * emid[c]);
-        }
-        __syncthreads();
-        const bool odd = (zf & 1) != 0;  // zf = 2Z - 1 (end of Z - 1, start of Z) or zf = 2Z
-        const int Zc = odd ? (zf + 1) >> 1 : zf >> 1;
-#pragma unroll
-        for (int j = 0; j < kRrCols; ++j) {
-            const int r0 = (2 * cy[j]) * kRrFW + 2 * cx[j];  // R(2X-1, 2Y-1) relative to the tile
-            const T* rr = R + r0;
-            const T p = (T)0.25 * ((T)0.25 * rr[0] + (T)0.5 * rr[1] + (T)0.25 * rr[2]) +
-                        (T)0.5 * ((T)0.25 * rr[kRrFW] + (T)0.5 * rr[kRrFW + 1] + (T)0.25 * rr[kRrFW + 2]) +
-                        (T)0.25 * ((T)0.25 * rr[2 * kRrFW] + (T)0.5 * rr[2 * kRrFW + 1] +
-                                   (T)0.25 * rr[2 * kRrFW + 2]);
-            const int X = X0 + cx[j], Y = Y0 + cy[j];
-            if (odd) {
-                if (Zc - 1 >= Z0) {
-                    acc[j] += (T)0.25 * p;
-                    if (X < nc && Y < nc) bc[((int64_t)(Zc - 1) * nc + Y) * nc + X] = (T)4 * acc[j];
-                }
-                acc[j] = (T)0.25 * p;
-            } else {
-                acc[j] += (T)0.5 * p;
-            }
-        }
-    }
-}
-
-// Grid of k_resid_restrict_tile and its planes per block: the fewest planes
-// per block (down from 16) that still give every SM two blocks.
-inline int resid_restrict_zc(int nc, int nsm) {
-    const int tiles = ((nc + kRrCX - 1) / kRrCX) * ((nc + kRrCY - 1) / kRrCY);
-    int zc = 16;
-    while (zc > 1 && tiles * ((nc + zc - 1) / zc) < 2 * nsm) zc >>= 1;
-    return zc;
-}
-inline dim3 resid_restrict_grid(int nc, int zc) {
-    return dim3((nc + kRrCX - 1) / kRrCX, (nc + kRrCY - 1) / kRrCY, (nc + zc - 1) / zc);
 }
 
 // The first red-black sweep from e = 0 (as k_rbgs_first, bit for bit) in

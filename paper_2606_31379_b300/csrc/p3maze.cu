@@ -97,7 +97,8 @@ struct p3maze_ctx {
     int fuse = 1;                        // mixed mode: diffusion steps per launch, 1 to 4, or 5: all in one
                                          // cluster launch (16 <= N <= 64) (tunable)
     ClusterMesh* cltab = nullptr;        // this mesh's entry for the cluster smoothing kernel
-    bool cluster_ok = false;             // the device runs 16-CTA clusters of the smoothing kernel
+    bool cluster_ok = false;             // the device runs this mesh's clusters of the smoothing kernel
+    int cl_ctas = 0;                     // CTAs per cluster of mode 5 (0: automatic)
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
     int64_t P = 0;
@@ -350,17 +351,18 @@ cudaError_t launch_maybe_pdl(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size
     return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
-// All diffusion steps of `members` meshes (table on the device, N <= nmax)
-// in one launch, one 16-CTA cluster per mesh.
-cudaError_t launch_cluster_smoothing(const ClusterMesh* tab, int members, int nmax, cudaStream_t s, bool pdl) {
+// All diffusion steps of `members` meshes (table on the device, N <= nmax,
+// all with cluster size cs) in one launch, one cluster of cs CTAs per mesh.
+cudaError_t launch_cluster_smoothing(const ClusterMesh* tab, int members, int cs, int nmax, cudaStream_t s,
+                                     bool pdl) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kClCTAs * members);
+    cfg.gridDim = dim3(cs * members);
     cfg.blockDim = dim3(kClThreads);
-    cfg.dynamicSmemBytes = cluster_smem_bytes(nmax);
+    cfg.dynamicSmemBytes = cluster_smem_bytes(nmax, cs);
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClCTAs;
+    attr[0].val.clusterDim.x = cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -370,24 +372,26 @@ cudaError_t launch_cluster_smoothing(const ClusterMesh* tab, int members, int nm
     return cudaLaunchKernelEx(&cfg, k_diffuse_cluster, tab);
 }
 
-// Whether the device co-schedules 16-CTA clusters of the smoothing kernel
-// with the shared memory of an n = kClMaxN mesh (asked once per process).
-bool cluster_smoothing_supported() {
-    static int cached = -1;
-    if (cached >= 0) return cached == 1;
-    const size_t smem = cluster_smem_bytes(kClMaxN);
+// Whether the device co-schedules clusters of cs CTAs of the smoothing
+// kernel with its largest shared-memory need (asked once per size and
+// process).
+bool cluster_smoothing_supported(int cs) {
+    static int cached[kClMaxCTAs + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    if (cs < 1 || cs > kClMaxCTAs) return false;
+    if (cached[cs] >= 0) return cached[cs] == 1;
+    const size_t smem = kClSmemBudget + 16;
     cudaError_t e = cudaFuncSetAttribute(k_diffuse_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_diffuse_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nclusters = 0;
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(kClCTAs);
+        cfg.gridDim = dim3(cs);
         cfg.blockDim = dim3(kClThreads);
         cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kClCTAs;
+        attr[0].val.clusterDim.x = cs;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
@@ -395,8 +399,8 @@ bool cluster_smoothing_supported() {
         e = cudaOccupancyMaxActiveClusters(&nclusters, k_diffuse_cluster, &cfg);
     }
     if (e != cudaSuccess) cudaGetLastError();  // not available: the per-step kernels are used
-    cached = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
-    return cached == 1;
+    cached[cs] = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
+    return cached[cs] == 1;
 }
 
 template <int Z>
@@ -475,7 +479,8 @@ int smooth(p3maze_ctx* ctx) {
         const T* src = (const T*)ctx->q;
         if (ctx->fuse == 5) {
             // every step in one launch, the mesh resident in a cluster's shared memory
-            CK(launch_cluster_smoothing(ctx->cltab, 1, ctx->N, s, false));
+            const int cs = ctx->cl_ctas ? ctx->cl_ctas : cluster_size_for(ctx->N, 1, ctx->nsm);
+            CK(launch_cluster_smoothing(ctx->cltab, 1, cs, ctx->N, s, false));
             count(ctx, P3MAZE_ST_SMOOTH, 1);
         } else if (ctx->fuse > 2) {
             // S = fuse steps per launch (temporal blocking), then the rest
@@ -614,12 +619,7 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
             CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
         }
     }
-    {
-        // residual + restriction, each fine residual formed once per block
-        const int zc = resid_restrict_zc(C.n, ctx->nsm);
-        CK(go(k_resid_restrict_tile<T>, resid_restrict_grid(C.n, zc), dim3(kRrThreads),
-              resid_restrict_smem_bytes<T>(), C.n, zc, (const T*)e, (const T*)b, (T*)C.b));
-    }
+    CK(go(k_resid_restrict<T>, g3(C.n), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
     count(ctx, P3MAZE_ST_SOLVE, (ctx->nu1 > 0 ? 2 * ctx->nu1 - 1 : 0) + 1);
     int rc = vcycle<T>(ctx, l + 1, true);
     if (rc) return rc;
@@ -1320,8 +1320,6 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
             raise((const void*)k_coarse_xy<double>);
             raise((const void*)k_coarse_z<double>);
         }
-        sm = resid_restrict_smem_bytes<double>();
-        if (!mixed) raise((const void*)k_resid_restrict_tile<double>);
         if (mixed) {
             sm = spread_smem_bytes<float>();
             raise((const void*)k_spread_tile<float, MeshPt, true>);
@@ -1346,7 +1344,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         const ClusterMesh cm{(const float*)ctx->q, (float*)ctx->qs, ctx->dscal + S_QSUM, ctx->N, ctx->K,
                              (float)ctx->c, 0};
         CK(cudaMemcpy(ctx->cltab, &cm, sizeof cm, cudaMemcpyHostToDevice));
-        ctx->cluster_ok = cluster_smoothing_supported();
+        ctx->cluster_ok = cluster_smoothing_supported(cluster_size_for(ctx->N, 1, ctx->nsm));
         if (ctx->cluster_ok) ctx->fuse = 5;
     }
     {
@@ -2252,6 +2250,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     out->pair_fork = ctx->pair_fork;
     out->coarse_max = ctx->cmax;
     out->pair_blocks = ctx->pair_blocks;
+    out->cluster_ctas = ctx->cl_ctas;
     out->ms_per_step = best;
     out->initial_ms_per_step = initial;
     out->trials = trials;
@@ -2264,13 +2263,18 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (!ctx || !t) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
     if (t->predictor < 1 || t->predictor > 3 || t->pre_sweeps < 1 || t->post_sweeps < 0 || t->diffusion_zc < 1 ||
         t->diffusion_fuse < 1 || t->diffusion_fuse > 5 || (t->pair_fork != 0 && t->pair_fork != 1) ||
-        t->coarse_max < 1 || t->pair_blocks < 0)
+        t->coarse_max < 1 || t->pair_blocks < 0 || t->cluster_ctas < 0 || t->cluster_ctas > kClMaxCTAs ||
+        (t->cluster_ctas & (t->cluster_ctas - 1)) != 0)
         return fail(ctx, P3MAZE_ERR_INVALID, "tuning field out of range");
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
     if (t->diffusion_fuse == 5 && !ctx->cluster_ok)
         return fail(ctx, P3MAZE_ERR_INVALID,
-                    "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs 16-CTA clusters");
+                    "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs such clusters");
+    if (t->diffusion_fuse == 5 && t->cluster_ctas &&
+        (cluster_smem_bytes(ctx->N, t->cluster_ctas) > kClSmemBudget + 16 ||
+         !cluster_smoothing_supported(t->cluster_ctas)))
+        return fail(ctx, P3MAZE_ERR_INVALID, "cluster_ctas too small for this mesh or not run by the device");
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = t->predictor;
     ctx->nu1 = t->pre_sweeps;
@@ -2279,6 +2283,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     ctx->fuse = t->diffusion_fuse;
     ctx->pair_fork = t->pair_fork;
     ctx->pair_blocks = t->pair_blocks;
+    ctx->cl_ctas = t->cluster_ctas;
     set_coarse(ctx, t->coarse_max);
     destroy_graphs(ctx);
     return P3MAZE_OK;
@@ -2295,6 +2300,7 @@ int p3maze_get_tuning(p3maze_ctx* ctx, p3maze_tuning* out) {
     out->pair_fork = ctx->pair_fork;
     out->coarse_max = ctx->cmax;
     out->pair_blocks = ctx->pair_blocks;
+    out->cluster_ctas = ctx->cl_ctas;
     return P3MAZE_OK;
 }
 
@@ -2322,6 +2328,10 @@ int p3maze_get_timing(p3maze_ctx* ctx, p3maze_timing* out) {
 // ------------------------------------------------------------------ batches
 }  // extern "C"
 
+// A member's entry in the batch's cluster table: 0 when its smoothing is not
+// a cluster launch, else 1 + its requested cluster size (0 = automatic).
+static char cl_tag(const p3maze_ctx* m) { return m->fuse == 5 ? (char)(1 + m->cl_ctas) : 0; }
+
 struct p3maze_batch {
     cudaStream_t origin = nullptr;      // capture and launch stream
     cudaStream_t user = nullptr;        // caller's stream (fenced on entry and exit)
@@ -2342,8 +2352,11 @@ struct p3maze_batch {
     int cl_cap = 0;
     bool cl_dirty = true;               // membership changed: rebuild the table
     std::vector<ClusterMesh> cl_host;
-    std::vector<char> cl_member;        // per member: smoothed by the batch's cluster launch
-    int cl_nmax = 0;
+    std::vector<char> cl_member;        // per member: cl_tag when the table was built (0: not in it)
+    struct ClGroup {
+        int cs, first, count, nmax;     // cluster size; table entries [first, first + count)
+    };
+    std::vector<ClGroup> cl_groups;     // one launch per cluster size
     std::string err = "no error";
 };
 
@@ -2507,20 +2520,39 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
     if (b->mode == P3MAZE_BATCH_PER_MEMBER && !b->cl_dirty) {
         // a member's smoothing mode may have been changed (p3maze_set_tuning)
         for (size_t i = 0; i < b->members.size(); ++i)
-            if ((b->members[i]->fuse == 5) != (b->cl_member[i] != 0)) b->cl_dirty = true;
+            if (cl_tag(b->members[i]) != b->cl_member[i]) b->cl_dirty = true;
     }
     if (b->mode == P3MAZE_BATCH_PER_MEMBER && b->cl_dirty) {
         // members whose smoothing is a cluster launch (mode 5) share one
+        // launch per cluster size; the size per mesh shrinks as the batch
+        // grows (cluster_size_for), down to the smallest whose slabs fit
         b->cl_host.clear();
+        b->cl_groups.clear();
         b->cl_member.assign(b->members.size(), 0);
-        b->cl_nmax = 0;
+        int ncl = 0, nsm = 148;
+        for (p3maze_ctx* m : b->members) {
+            ncl += m->fuse == 5;
+            nsm = m->nsm;
+        }
+        std::vector<std::pair<int, int>> order;  // (cluster size, member)
         for (size_t i = 0; i < b->members.size(); ++i) {
             p3maze_ctx* m = b->members[i];
             if (m->fuse != 5) continue;
-            b->cl_member[i] = 1;
+            b->cl_member[i] = cl_tag(m);
+            int cs = m->cl_ctas ? m->cl_ctas : cluster_size_for(m->N, ncl, nsm);
+            if (!cluster_smoothing_supported(cs)) cs = cluster_size_for(m->N, 1, nsm);  // its own, checked at init
+            order.emplace_back(cs, (int)i);
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+        for (const auto& [cs, i] : order) {
+            p3maze_ctx* m = b->members[i];
+            if (b->cl_groups.empty() || b->cl_groups.back().cs != cs)
+                b->cl_groups.push_back(p3maze_batch::ClGroup{cs, (int)b->cl_host.size(), 0, 0});
+            b->cl_groups.back().count += 1;
+            b->cl_groups.back().nmax = std::max(b->cl_groups.back().nmax, m->N);
             b->cl_host.push_back(ClusterMesh{(const float*)m->q, (float*)m->qs, m->dscal + S_QSUM, m->N, m->K,
                                              (float)m->c, 0});
-            b->cl_nmax = std::max(b->cl_nmax, m->N);
         }
         if ((int)b->cl_host.size() > b->cl_cap) {
             BCK(cudaStreamSynchronize(b->origin));
@@ -2550,7 +2582,8 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
                 BCK(cudaEventRecord(b->ev_done[i], m->stream));
                 BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
             }
-            BCK(launch_cluster_smoothing(b->cltab, (int)b->cl_host.size(), b->cl_nmax, b->origin, false));
+            for (const p3maze_batch::ClGroup& g : b->cl_groups)
+                BCK(launch_cluster_smoothing(b->cltab + g.first, g.count, g.cs, g.nmax, b->origin, false));
             BCK(cudaEventRecord(b->ev_fork, b->origin));
             for (size_t i = 0; i < b->members.size(); ++i) {
                 if (!b->cl_member[i]) continue;

@@ -109,7 +109,12 @@ class GpuBackend:
 
     WARMUP_STEPS = 3                        # fills the predictor history of any order
 
-    def __init__(self, precision: str = "mixed", stream: int | None = None, admit_stream: int | None = None):
+    def __init__(self, precision: str = "mixed", stream: int | None = None, admit_stream: int | None = None,
+                 smoothing: str = "default"):
+        """smoothing: "default" keeps each context's own choice (meshes of at
+        most 64^3 smooth in one cluster launch, shared by the whole batch);
+        "per_step" forces one diffusion kernel launch per two steps (the
+        25-point kernel), for comparison."""
         import queue
         import threading
 
@@ -122,6 +127,7 @@ class GpuBackend:
         self.batch = P.Batch(stream=stream, mode="per_member")
         self.clock = time.perf_counter
         self.steps = {}                     # host-side step count per member
+        self.smoothing = smoothing
         self._todo = queue.Queue()
         self._ready = queue.Queue()
         self._worker = threading.Thread(target=self._admit_loop, name="p3maze-admission", daemon=True)
@@ -140,6 +146,8 @@ class GpuBackend:
             try:
                 system, prm = request_system(req)
                 ctx = self.P.Context.from_system(system, precision=self.precision, stream=self.admit_stream, **prm)
+                if self.smoothing == "per_step" and ctx.tuning()["diffusion_fuse"] == 5:
+                    ctx.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
                 ctx.step(self.WARMUP_STEPS)
                 self._ready.put((req, ctx, time.perf_counter() - t0, None))
             except Exception as e:          # reported to the stepping thread

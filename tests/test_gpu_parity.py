@@ -288,7 +288,8 @@ def test_shifted_force_cutoff_matches_oracle(P, nacl512, precision, ftol):
 @pytest.mark.parametrize("mesh", [16, 20, 32, 48, 64])
 def test_cluster_smoothing_matches_oracle(P, mesh):
     """All K diffusion steps in one cluster launch (FP32, the mesh in the
-    distributed shared memory of 16 CTAs; smoothing mode 5): q^s matches the
+    distributed shared memory of 16 CTAs, the size a context stepped alone
+    takes; smoothing mode 5): q^s matches the
     oracle's (I + cM)^K q to the mixed bar and the one-step-per-launch path
     to FP32 rounding, for meshes with one to four planes per CTA, and the
     neutrality mean it forms gives the same constrained field."""
@@ -298,7 +299,7 @@ def test_cluster_smoothing_matches_oracle(P, mesh):
     kw = dict(alpha=0.30, r_cut=r_cut, mesh=mesh, tol=1e-8, dt=1.0, precision="mixed")
     with P.Context.from_system(s, **kw) as a, P.Context.from_system(s, **kw) as b:
         if a.tuning()["diffusion_fuse"] != 5:
-            pytest.skip("the device does not run 16-CTA clusters of the smoothing kernel")
+            pytest.skip("the device does not run clusters of the smoothing kernel")
         b.set_tuning(diffusion_fuse=1)
         a.step(2)
         b.step(2)
@@ -315,6 +316,49 @@ def test_cluster_smoothing_matches_oracle(P, mesh):
         b.step(1)
         assert a.timing()["launches"]["smooth"] == 1                     # all K steps, one launch
         assert b.timing()["launches"]["smooth"] == a.stats()["smooth_steps"] + 1
+
+
+def _min_cluster_ctas(mesh):
+    cs = 1
+    while cs < 16 and 2 * 4 * -(-mesh // cs) * mesh * mesh > 200 * 1024:
+        cs *= 2
+    return cs
+
+
+@pytest.mark.parametrize("mesh", [16, 28, 32, 44, 60])
+def test_cluster_smoothing_is_the_same_for_every_cluster_size(P, mesh):
+    """Mode 5 with 1 to 16 CTAs per cluster: each CTA smooths its own slab of
+    planes with the same per-point arithmetic, so from the same positions
+    every cluster size gives the same q^s bit for bit, in one launch; sizes
+    whose slabs do not fit the shared memory are rejected."""
+    box = 0.8 * mesh
+    s = S.nacl_melt(2 * int(round(0.031899 * box ** 3 / 2)), box, seed=60 + mesh)
+    kw = dict(alpha=0.30, r_cut=min(9.0, box), mesh=mesh, tol=1e-8, dt=1.0, precision="mixed")
+    lo = _min_cluster_ctas(mesh)
+    with P.Context.from_system(s, **kw) as a:
+        if a.tuning()["diffusion_fuse"] != 5:
+            pytest.skip("the device does not run clusters of the smoothing kernel")
+        if lo > 1:
+            with pytest.raises(P.P3MaZeError, match="cluster_ctas"):
+                a.set_tuning(cluster_ctas=lo // 2)
+        with pytest.raises(P.P3MaZeError, match="out of range"):
+            a.set_tuning(cluster_ctas=3)
+        state = a.save_state()
+        ref = None
+        for cs in [c for c in (1, 2, 4, 8, 16) if c >= lo]:
+            a.load_state(state)
+            a.set_tuning(cluster_ctas=cs)
+            assert a.tuning()["cluster_ctas"] == cs
+            a.set_timing(True)
+            a.step(1)
+            assert a.timing()["launches"]["smooth"] == 1
+            qs = a.mesh("qs")
+            if ref is None:
+                ref = qs
+                mf = O.mesh_fields(at_positions(s, a.positions()), 0.30, mesh)
+                assert np.abs(qs - mf["qs"]).max() <= 1e-6 * np.abs(mf["qs"]).max()
+            else:
+                np.testing.assert_array_equal(qs, ref)
 
 
 def test_async_steps_match_blocking_steps(P, nacl512):
