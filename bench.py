@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -629,10 +630,121 @@ def run_ours(args) -> int:
         # diffusion kernels (no shared cluster smoothing), for comparison
         line["served_per_step_smoothing"] = served_run(stream.cuda_stream, n_req=256, steps=200, slots=16,
                                                        smoothing="per_step")
+    if not args.no_serve:
+        line["batch_small"] = batch_small_run(stream, peaks)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(system, prm)
     print(json.dumps(line))
     return 0
+
+
+def small_batch_bytes(mesh: int, n_atoms: int, iters: float) -> float:
+    """Algorithmic bytes of one mixed-precision MD step of a member: each
+    mesh array read or written once per pass that needs it, FP32 meshes 4 B
+    and fixed-point meshes 8 B per point, particles 4 B per coordinate.  Per
+    mesh point: assignment output 4, smoothing in + out 8, prediction and
+    residual 64, per V-cycle about 100 (sweeps 8 + 24, restriction and
+    prolongation 8.5 each, residual update 44, coarser levels 1/7 more),
+    field update 56, interpolation input 4.  Per particle: kick/drift 120,
+    cell list 32, assignment 32, pair forces 32, interpolation 104."""
+    P3 = float(mesh) ** 3
+    return P3 * (4 + 8 + 64 + 100.0 * iters + 56 + 4) + n_atoms * (120 + 32 + 32 + 32 + 104)
+
+
+def batch_small_run(stream, peaks, members: int = 32, steps: int = 60, warmup: int = 6) -> dict:
+    """Many small systems (16^3-64^3 meshes) advanced as one batch: system-
+    steps/s of six batch configurations -- one graph for the whole batch or
+    each member's own cached graphs, each with the smoothing of every member
+    in one cluster launch per cluster size (cluster_fused), each member's
+    smoothing in its own cluster launch (cluster_own), or each member's own
+    per-step diffusion launches (per_step).  The same seeded members in every
+    configuration."""
+    import torch
+    from paper_2606_31379_b300 import p3maze as P
+    from paper_2606_31379_b300.serve import Request, request_system
+
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i in range(members):
+        kind = "nacl" if i % 2 == 0 else "water"
+        atoms = int(round(math.exp(rng.uniform(math.log(216), math.log(4096)))))
+        reqs.append(Request(rid=i, kind=kind, n_atoms=atoms, seed=2000 + i, steps=steps, arrival=0.0))
+    systems = [request_system(r) for r in reqs]
+    out = {"config": {"members": members, "steps": steps, "warmup": warmup,
+                      "sizes": "216-4096 atoms log-uniform, molten NaCl / SPC/Fw alternating, mesh ~0.8 A",
+                      "meshes": sorted({p["mesh"] for _, p in systems}), "precision": "mixed"}}
+    ref_F = None
+    for mode in ("shared", "per_member"):
+        for smoothing in ("cluster_fused", "cluster_own", "per_step"):
+            ctxs = []
+            batch = P.Batch(stream=stream.cuda_stream, mode=mode, fused_smoothing=smoothing == "cluster_fused")
+            try:
+                n_atoms = 0
+                for system, prm in systems:
+                    c = P.Context.from_system(system, precision="mixed", **prm)
+                    if smoothing == "per_step" and c.tuning()["diffusion_fuse"] == 5:
+                        c.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                    ctxs.append(c)
+                    n_atoms += system.n
+                for c in ctxs:
+                    batch.add(c)
+                with torch.cuda.stream(stream):
+                    batch.step(warmup)
+                    batch.wait()
+                    it0 = [c.stats()["total_iters"] for c in ctxs]
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    batch.step(steps)
+                    e1.record(stream)
+                    batch.wait()
+                    torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) * 1e-3
+                iters = [(c.stats()["total_iters"] - i0) / steps for c, i0 in zip(ctxs, it0)]
+                algo = sum(small_batch_bytes(p["mesh"], s.n, it) for (s, p), it in zip(systems, iters)) * steps
+                F = np.concatenate([c.forces() for c in ctxs])
+                rec = {"system_steps_per_s": members * steps / sec, "ms_per_batch_step": 1e3 * sec / steps,
+                       "atom_steps_per_s": n_atoms * steps / sec,
+                       "mg_iters_per_step": float(np.mean(iters)),
+                       "algorithmic_GBps": algo / sec / 1e9,
+                       "hbm_frac": algo / sec / 1e9 / peaks["hbm_gbs"]}
+                if ref_F is None:
+                    ref_F = F
+                else:  # all four advance the same members the same number of steps
+                    rec["force_rel_rms_vs_first"] = float(np.sqrt(np.mean((F - ref_F) ** 2) / np.mean(ref_F ** 2)))
+                out[f"{mode}_{smoothing}"] = rec
+            finally:
+                batch.close()
+                for c in ctxs:
+                    c.close()
+    # one context alone: the whole smoothing in one cluster launch or per-step launches
+    alone = {}
+    for atoms in (512, 1728, 4096):
+        system, prm = request_system(Request(rid=0, kind="nacl", n_atoms=atoms, seed=77, steps=0, arrival=0.0))
+        rec = {"mesh": prm["mesh"]}
+        for smoothing in ("cluster", "per_step"):
+            with P.Context.from_system(system, precision="mixed", stream=stream.cuda_stream, **prm) as c:
+                if c.tuning()["diffusion_fuse"] != 5:
+                    break
+                if smoothing == "per_step":
+                    c.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                c.step(warmup)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c.step(steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                c.set_timing(True)
+                c.step(steps)
+                rec[smoothing] = {"ms_per_step": e0.elapsed_time(e1) / steps,
+                                  "smooth_us_per_step": 1e3 * c.timing()["ms"]["smooth"] / steps}
+        alone[f"nacl_{atoms}"] = rec
+    out["alone"] = alone
+    out["note"] = ("hbm_frac: algorithmic bytes of every member's step (small_batch_bytes) over the batch "
+                   "time, of measured HBM bandwidth; meshes this small stay in L2, so the steps are bound by "
+                   "launch latency and the fraction measures how well the batch fills the GPU")
+    return out
 
 
 def served_run(stream, n_req: int, steps: int, slots: int, rate: float = 200.0, smoothing: str = "default") -> dict:

@@ -478,16 +478,28 @@ int p3maze_batch_size(const p3maze_batch *batch);
  * graph recorded again after every membership change.  P3MAZE_BATCH_PER_MEMBER:
  * each member replays its own cached step graphs on its own stream (forked
  * from and joined to the batch stream), with no re-recording when members
- * come and go; used by the serving loop.  There the members whose smoothing
- * runs as a cluster launch (diffusion_fuse 5) are smoothed together: every
- * member's step head (kick/drift, cell list, assignment), then ONE launch
- * with one 16-CTA cluster per such member doing all their diffusion steps,
- * then the step tails (solve, interpolation, kick); the results are those of
- * each member stepped alone, bit for bit.  The batch allocates a small
- * device table of those members (its only device allocation).               */
+ * come and go; used by the serving loop.  The members whose smoothing runs
+ * as a cluster launch (diffusion_fuse 5) can be smoothed together
+ * (p3maze_batch_set_fused_smoothing): every member's step head (kick/drift, cell list, assignment),
+ * then ONE launch per cluster size with one cluster per such member doing
+ * all their diffusion steps, then the step tails (solve, interpolation,
+ * kick); the results are those of each member stepped alone, bit for bit.
+ * The batch allocates a small device table of those members (its only
+ * device allocation).  A member's setting changed while it is in the batch
+ * (p3maze_set_tuning, p3maze_autotune, p3maze_set_timing, p3maze_set_graphs)
+ * is picked up at the next batch step.                                      */
 #define P3MAZE_BATCH_SHARED_GRAPH 0
 #define P3MAZE_BATCH_PER_MEMBER   1
 int p3maze_batch_set_mode(p3maze_batch *batch, int32_t mode);
+
+/* enable = 1: the members whose smoothing is a cluster launch are smoothed
+ * together, as described above; 0: each member's cluster launch stays inside
+ * its own step (no split of the step, no join across members); -1 (default):
+ * together in P3MAZE_BATCH_PER_MEMBER, each in its own step in
+ * P3MAZE_BATCH_SHARED_GRAPH (where the join costs more than the launches it
+ * saves).  Results are the same bit for bit either way.
+ * Errors: INVALID (NULL).                                                    */
+int p3maze_batch_set_fused_smoothing(p3maze_batch *batch, int32_t enable);
 void p3maze_batch_destroy(p3maze_batch *batch);
 const char *p3maze_batch_last_error(const p3maze_batch *batch);
 

@@ -500,32 +500,44 @@ k_diffuse_cluster(const ClusterMesh* __restrict__ tab) {
     for (int i = threadIdx.x; i < p * plane4; i += kClThreads) a4[i] = q4[i];
     cluster.sync();
     const float c = M.c;
+    // work items: an x-quad column (qx, y) over a run of L consecutive local
+    // planes, marched in z with the lower and centre planes in registers;
+    // L is chosen so the items cover the block about once
+    const int ncol = plane4;
+    const int L = max(1, min(p, (p * ncol + kClThreads - 1) / kClThreads));
+    const int nrun = (p + L - 1) / L;
     for (int st = 0; st < M.K; ++st) {
         const float* A = (st & 1) ? buf1 : buf0;
         float* B = (st & 1) ? buf0 : buf1;
         const float* Alo = cluster.map_shared_rank(const_cast<float*>(A), lo) + (size_t)(p_lo - 1) * plane;
         const float* Ahi = cluster.map_shared_rank(const_cast<float*>(A), hi);
         const bool last = st == M.K - 1;
-        for (int i = threadIdx.x; i < p * plane4; i += kClThreads) {
-            const int zl = i / plane4, r = i - zl * plane4, y = r / nq, qx = r - y * nq, x = 4 * qx;
-            const float* Ap = A + (size_t)zl * plane;
-            const float4 vc = reinterpret_cast<const float4*>(Ap)[r];
+        for (int it = threadIdx.x; it < ncol * nrun; it += kClThreads) {
+            const int run = it / ncol, col = it - run * ncol, y = col / nq, qx = col - y * nq, x = 4 * qx;
+            const int za = run * L, zb = min(p, za + L);
             const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
-            const float4 a = reinterpret_cast<const float4*>(Ap + ym * n)[qx];
-            const float4 b = reinterpret_cast<const float4*>(Ap + yp * n)[qx];
-            const float* Zm = zl > 0 ? Ap - plane : Alo;
-            const float* Zp = zl < p - 1 ? Ap + plane : Ahi;
-            const float4 vm = *reinterpret_cast<const float4*>(Zm + y * n + x);
-            const float4 vp = *reinterpret_cast<const float4*>(Zp + y * n + x);
-            const float left = Ap[y * n + (x == 0 ? n - 1 : x - 1)];
-            const float right = Ap[y * n + (x + 4 == n ? 0 : x + 4)];
-            float4 o;
-            o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
-            o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
-            o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
-            o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
-            if (last) reinterpret_cast<float4*>(M.qs)[(size_t)z0 * plane4 + i] = o;
-            reinterpret_cast<float4*>(B)[i] = o;
+            const int xl = x == 0 ? n - 1 : x - 1, xr = x + 4 == n ? 0 : x + 4;
+            const int off = y * n + x;
+            float4 vm = *reinterpret_cast<const float4*>((za > 0 ? A + (size_t)(za - 1) * plane : Alo) + off);
+            float4 vc = *reinterpret_cast<const float4*>(A + (size_t)za * plane + off);
+            for (int zl = za; zl < zb; ++zl) {
+                const float* Ap = A + (size_t)zl * plane;
+                const float4 vp = *reinterpret_cast<const float4*>((zl < p - 1 ? Ap + plane : Ahi) + off);
+                const float4 a = *reinterpret_cast<const float4*>(Ap + ym * n + x);
+                const float4 b = *reinterpret_cast<const float4*>(Ap + yp * n + x);
+                const float left = Ap[y * n + xl];
+                const float right = Ap[y * n + xr];
+                float4 o;
+                o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
+                o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
+                o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
+                o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
+                const size_t io = (size_t)zl * plane4 + col;
+                if (last) reinterpret_cast<float4*>(M.qs)[(size_t)z0 * plane4 + io] = o;
+                reinterpret_cast<float4*>(B)[io] = o;
+                vm = vc;
+                vc = vp;
+            }
         }
         cluster.sync();  // B complete everywhere before anyone reads it; A free
     }

@@ -99,6 +99,7 @@ struct p3maze_ctx {
     ClusterMesh* cltab = nullptr;        // this mesh's entry for the cluster smoothing kernel
     bool cluster_ok = false;             // the device runs this mesh's clusters of the smoothing kernel
     int cl_ctas = 0;                     // CTAs per cluster of mode 5 (0: automatic)
+    int64_t settings_gen = 0;            // bumped whenever a setting recorded in graphs changes
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
     int64_t P = 0;
@@ -2059,7 +2060,10 @@ int p3maze_set_timing(p3maze_ctx* ctx, int32_t enable) {
         for (int st = 0; st < P3MAZE_NSTAGES; ++st)
             for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ctx->ev[st][k]));
     CK(cudaStreamSynchronize(ctx->stream));
-    if ((enable != 0) != ctx->timing) destroy_graphs(ctx);  // event-record nodes differ
+    if ((enable != 0) != ctx->timing) {  // event-record nodes differ
+        destroy_graphs(ctx);
+        ctx->settings_gen += 1;
+    }
     ctx->timing = enable != 0;
     for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
         ctx->stage_ms[st] = 0.0;
@@ -2087,6 +2091,7 @@ int tune_trial(p3maze_ctx* ctx, const Setting& cfg, int warm, int steps, double*
     ctx->pair_blocks = cfg.pblocks;
     set_coarse(ctx, cfg.cmax);
     destroy_graphs(ctx);  // the setting is recorded in the graphs
+    ctx->settings_gen += 1;
     for (int k = 0; k < warm; ++k) {
         int rc = step_once(ctx);
         if (rc) return rc;
@@ -2241,6 +2246,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     ctx->pair_blocks = chosen.pblocks;
     set_coarse(ctx, chosen.cmax);
     destroy_graphs(ctx);
+    ctx->settings_gen += 1;
     ctx->timing = timing;
     out->predictor = ctx->pred;
     out->pre_sweeps = ctx->nu1;
@@ -2286,6 +2292,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     ctx->cl_ctas = t->cluster_ctas;
     set_coarse(ctx, t->coarse_max);
     destroy_graphs(ctx);
+    ctx->settings_gen += 1;
     return P3MAZE_OK;
 }
 
@@ -2307,7 +2314,10 @@ int p3maze_get_tuning(p3maze_ctx* ctx, p3maze_tuning* out) {
 int p3maze_set_graphs(p3maze_ctx* ctx, int32_t enable) {
     if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
     CK(cudaStreamSynchronize(ctx->stream));
-    if (!enable) destroy_graphs(ctx);
+    if (!enable) {
+        destroy_graphs(ctx);
+        ctx->settings_gen += 1;
+    }
     ctx->use_graphs = enable != 0;
     return P3MAZE_OK;
 }
@@ -2328,9 +2338,6 @@ int p3maze_get_timing(p3maze_ctx* ctx, p3maze_timing* out) {
 // ------------------------------------------------------------------ batches
 }  // extern "C"
 
-// A member's entry in the batch's cluster table: 0 when its smoothing is not
-// a cluster launch, else 1 + its requested cluster size (0 = automatic).
-static char cl_tag(const p3maze_ctx* m) { return m->fuse == 5 ? (char)(1 + m->cl_ctas) : 0; }
 
 struct p3maze_batch {
     cudaStream_t origin = nullptr;      // capture and launch stream
@@ -2344,15 +2351,19 @@ struct p3maze_batch {
         cudaGraphExec_t x = nullptr;
         std::vector<int> icur;
         std::vector<std::array<double*, 4>> yh;
+        std::vector<std::array<int64_t, P3MAZE_NSTAGES>> launches;  // per member and step
     };
     Phase phases[kMaxGraphs];
     int mode = 0;                       // P3MAZE_BATCH_SHARED_GRAPH or P3MAZE_BATCH_PER_MEMBER
-    // per-member mode: the members smoothed by one cluster launch (mode 5)
+    // the members smoothed by the batch's cluster launches (mode 5)
     ClusterMesh* cltab = nullptr;       // device table, cl_cap entries
     int cl_cap = 0;
-    bool cl_dirty = true;               // membership changed: rebuild the table
+    bool cl_dirty = true;               // membership or a member's setting changed: rebuild
+    int fuse_smoothing = -1;            // smooth the mode-5 members together: 1 yes, 0 each in its own
+                                        // step, -1 by mode (yes for per-member, no for the shared graph)
     std::vector<ClusterMesh> cl_host;
-    std::vector<char> cl_member;        // per member: cl_tag when the table was built (0: not in it)
+    std::vector<char> cl_member;        // per member: in the table
+    std::vector<int64_t> gen_seen;      // per member: settings_gen when the table was built
     struct ClGroup {
         int cs, first, count, nmax;     // cluster size; table entries [first, first + count)
     };
@@ -2394,13 +2405,43 @@ bool phase_matches(const p3maze_batch::Phase& ph, const std::vector<p3maze_ctx*>
 }
 
 // One graph holding one MD step of every member, each member's step a branch
-// from a common fork (with its own device-side multigrid while node).
+// from a common fork (with its own device-side multigrid while node).  The
+// members smoothed by the batch's cluster launches (mode 5) branch twice:
+// their heads (kick/drift, cell list, assignment) join the batch stream, the
+// cluster launches smooth all their meshes, and their tails fork again.
 int batch_capture(p3maze_batch* b, p3maze_batch::Phase& ph) {
+    struct Saved {
+        int icur;
+        std::array<double*, 4> yh;
+        bool timing;
+        int64_t launches[P3MAZE_NSTAGES];
+    };
+    std::vector<Saved> sv(b->members.size());
+    std::vector<char> held(b->members.size(), 0);  // state saved, not yet restored
     BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
     int rc = e == cudaSuccess ? P3MAZE_OK : bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
     ph.icur.clear();
     ph.yh.clear();
+    ph.launches.assign(b->members.size(), {});
+    auto restore = [&](size_t i) {
+        p3maze_ctx* m = b->members[i];
+        held[i] = 0;
+        m->capturing = false;
+        m->timing = sv[i].timing;
+        for (int st = 0; st < P3MAZE_NSTAGES; ++st) {
+            ph.launches[i][st] = m->launches[st] - sv[i].launches[st];
+            m->launches[st] = sv[i].launches[st];
+        }
+        m->icur = sv[i].icur;
+        for (int k = 0; k < 4; ++k) m->yh[k] = sv[i].yh[k];
+    };
+    auto join = [&](size_t i) {
+        cudaError_t je = cudaEventRecord(b->ev_done[i], b->members[i]->stream);
+        if (je == cudaSuccess) je = cudaStreamWaitEvent(b->origin, b->ev_done[i], 0);
+        return je == cudaSuccess ? P3MAZE_OK : bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(je));
+    };
+    bool any_split = false;
     for (size_t i = 0; i < b->members.size() && !rc; ++i) {
         p3maze_ctx* m = b->members[i];
         e = cudaStreamWaitEvent(m->stream, b->ev_fork, 0);
@@ -2408,30 +2449,61 @@ int batch_capture(p3maze_batch* b, p3maze_batch::Phase& ph) {
             rc = bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
             break;
         }
-        const int icur = m->icur;
-        std::array<double*, 4> yh;
-        for (int k = 0; k < 4; ++k) yh[k] = m->yh[k];
-        ph.icur.push_back(icur);
-        ph.yh.push_back(yh);
-        const bool timing = m->timing;
-        int64_t saved[P3MAZE_NSTAGES];
-        for (int st = 0; st < P3MAZE_NSTAGES; ++st) saved[st] = m->launches[st];
+        Saved& s = sv[i];
+        s.icur = m->icur;
+        for (int k = 0; k < 4; ++k) s.yh[k] = m->yh[k];
+        s.timing = m->timing;
+        for (int st = 0; st < P3MAZE_NSTAGES; ++st) s.launches[st] = m->launches[st];
+        held[i] = 1;
+        ph.icur.push_back(s.icur);
+        ph.yh.push_back(s.yh);
         m->timing = false;
         m->capturing = true;
-        rc = step_body(m, m->pred);
-        m->capturing = false;
-        m->timing = timing;
-        for (int st = 0; st < P3MAZE_NSTAGES; ++st) m->launches[st] = saved[st];
-        m->icur = icur;
-        for (int k = 0; k < 4; ++k) m->yh[k] = yh[k];
+        const bool split = b->cl_member[i] != 0;
+        any_split |= split;
+        rc = split ? step_head(m) : step_body(m, m->pred);
+        if (!split || rc) restore(i);
         if (rc) {
             rc = bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
             break;
         }
-        e = cudaEventRecord(b->ev_done[i], m->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev_done[i], 0);
-        if (e != cudaSuccess) rc = bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
+        m->capturing = false;
+        if (split) rc = join(i);  // whole steps join at the end: the cluster launch waits for heads only
     }
+    if (!rc && any_split) {
+        for (const p3maze_batch::ClGroup& g : b->cl_groups) {
+            e = launch_cluster_smoothing(b->cltab + g.first, g.count, g.cs, g.nmax, b->origin, false);
+            if (e != cudaSuccess) {
+                rc = bfail(b, P3MAZE_ERR_CUDA, std::string("cluster smoothing: ") + cudaGetErrorString(e));
+                break;
+            }
+        }
+        if (!rc) {
+            e = cudaEventRecord(b->ev_fork, b->origin);
+            if (e != cudaSuccess) rc = bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
+        }
+        for (size_t i = 0; i < b->members.size() && !rc; ++i) {
+            if (!b->cl_member[i]) continue;
+            p3maze_ctx* m = b->members[i];
+            e = cudaStreamWaitEvent(m->stream, b->ev_fork, 0);
+            if (e != cudaSuccess) {
+                rc = bfail(b, P3MAZE_ERR_CUDA, cudaGetErrorString(e));
+                break;
+            }
+            m->capturing = true;
+            rc = step_tail(m, m->pred);
+            restore(i);
+            if (rc) {
+                rc = bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
+                break;
+            }
+            rc = join(i);
+        }
+    }
+    for (size_t i = 0; i < b->members.size() && !rc; ++i)
+        if (!b->cl_member[i]) rc = join(i);
+    for (size_t i = 0; i < b->members.size(); ++i)  // after a failure: members left between head and tail
+        if (held[i]) restore(i);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->origin, &g);
     if (rc || e != cudaSuccess) {
@@ -2517,18 +2589,22 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
     if (b->members.empty() || nsteps == 0) return P3MAZE_OK;
     BCK(cudaEventRecord(b->ev_in, b->user));
     BCK(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
-    if (b->mode == P3MAZE_BATCH_PER_MEMBER && !b->cl_dirty) {
-        // a member's smoothing mode may have been changed (p3maze_set_tuning)
+    if (!b->cl_dirty) {
+        // a member's setting may have changed since (p3maze_set_tuning, p3maze_autotune, timing)
         for (size_t i = 0; i < b->members.size(); ++i)
-            if (cl_tag(b->members[i]) != b->cl_member[i]) b->cl_dirty = true;
+            if (b->members[i]->settings_gen != b->gen_seen[i]) b->cl_dirty = true;
     }
-    if (b->mode == P3MAZE_BATCH_PER_MEMBER && b->cl_dirty) {
+    if (b->cl_dirty) {
         // members whose smoothing is a cluster launch (mode 5) share one
         // launch per cluster size; the size per mesh shrinks as the batch
-        // grows (cluster_size_for), down to the smallest whose slabs fit
+        // grows (cluster_size_for), down to the smallest whose slabs fit.
+        // The shared graphs record the table and the members' settings.
+        batch_drop_graphs(b);
         b->cl_host.clear();
         b->cl_groups.clear();
         b->cl_member.assign(b->members.size(), 0);
+        b->gen_seen.resize(b->members.size());
+        for (size_t i = 0; i < b->members.size(); ++i) b->gen_seen[i] = b->members[i]->settings_gen;
         int ncl = 0, nsm = 148;
         for (p3maze_ctx* m : b->members) {
             ncl += m->fuse == 5;
@@ -2537,8 +2613,9 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
         std::vector<std::pair<int, int>> order;  // (cluster size, member)
         for (size_t i = 0; i < b->members.size(); ++i) {
             p3maze_ctx* m = b->members[i];
-            if (m->fuse != 5) continue;
-            b->cl_member[i] = cl_tag(m);
+            const bool fused = b->fuse_smoothing < 0 ? b->mode == P3MAZE_BATCH_PER_MEMBER : b->fuse_smoothing != 0;
+            if (m->fuse != 5 || !fused) continue;
+            b->cl_member[i] = 1;
             int cs = m->cl_ctas ? m->cl_ctas : cluster_size_for(m->N, ncl, nsm);
             if (!cluster_smoothing_supported(cs)) cs = cluster_size_for(m->N, 1, nsm);  // its own, checked at init
             order.emplace_back(cs, (int)i);
@@ -2570,8 +2647,10 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
     }
     if (b->mode == P3MAZE_BATCH_PER_MEMBER && !b->cl_host.empty()) {
         // heads of every member's step on their own streams; the smoothing of
-        // the cluster members as one launch on the batch stream; then the
-        // tails (members not smoothed there take whole steps in the first fork)
+        // the cluster members as one launch per cluster size on the batch
+        // stream; then the tails.  Members not smoothed there take whole
+        // steps from the first fork and join at the end, so the cluster
+        // launch waits for the heads only.
         for (int k = 0; k < nsteps; ++k) {
             BCK(cudaEventRecord(b->ev_fork, b->origin));
             for (size_t i = 0; i < b->members.size(); ++i) {
@@ -2580,7 +2659,7 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
                 int rc = b->cl_member[i] ? step_graph(m, PART_HEAD) : step_once(m);
                 if (rc) return bfail(b, rc, std::string("member ") + std::to_string(i) + ": " + m->err);
                 BCK(cudaEventRecord(b->ev_done[i], m->stream));
-                BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
+                if (b->cl_member[i]) BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
             }
             for (const p3maze_batch::ClGroup& g : b->cl_groups)
                 BCK(launch_cluster_smoothing(b->cltab + g.first, g.count, g.cs, g.nmax, b->origin, false));
@@ -2599,6 +2678,8 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
                 BCK(cudaEventRecord(b->ev_done[i], m->stream));
                 BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
             }
+            for (size_t i = 0; i < b->members.size(); ++i)
+                if (!b->cl_member[i]) BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
         }
         BCK(cudaEventRecord(b->ev_out, b->origin));
         BCK(cudaStreamWaitEvent(b->user, b->ev_out, 0));
@@ -2640,7 +2721,9 @@ int p3maze_batch_step(p3maze_batch* b, int32_t nsteps) {
             if (rc) return rc;
         }
         BCK(cudaGraphLaunch(ph->x, b->origin));
-        for (p3maze_ctx* m : b->members) {
+        for (size_t i = 0; i < b->members.size(); ++i) {
+            p3maze_ctx* m = b->members[i];
+            for (int st = 0; st < P3MAZE_NSTAGES; ++st) m->launches[st] += ph->launches[i][st];
             m->icur = 1 - m->icur;
             double* oldest = m->yh[3];
             m->yh[3] = m->yh[2];
@@ -2666,6 +2749,14 @@ int p3maze_batch_wait(p3maze_batch* b) {
 }
 
 int p3maze_batch_size(const p3maze_batch* b) { return b ? (int)b->members.size() : 0; }
+
+int p3maze_batch_set_fused_smoothing(p3maze_batch* b, int32_t enable) {
+    if (!b) return bfail(nullptr, P3MAZE_ERR_INVALID, "batch is NULL");
+    BCK(cudaStreamSynchronize(b->origin));
+    b->fuse_smoothing = enable < 0 ? -1 : enable != 0;
+    b->cl_dirty = true;
+    return P3MAZE_OK;
+}
 
 int p3maze_batch_set_mode(p3maze_batch* b, int32_t mode) {
     if (!b) return bfail(nullptr, P3MAZE_ERR_INVALID, "batch is NULL");

@@ -119,6 +119,7 @@ _sig = {
     "p3maze_batch_wait": (C.c_int, [C.c_void_p]),
     "p3maze_batch_size": (C.c_int, [C.c_void_p]),
     "p3maze_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int32]),
+    "p3maze_batch_set_fused_smoothing": (C.c_int, [C.c_void_p, C.c_int32]),
     "p3maze_batch_destroy": (None, [C.c_void_p]),
     "p3maze_batch_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -446,7 +447,7 @@ class Batch:
 
     SHARED_GRAPH, PER_MEMBER = 0, 1
 
-    def __init__(self, stream: int | None = None, mode: str = "shared"):
+    def __init__(self, stream: int | None = None, mode: str = "shared", fused_smoothing: bool | None = None):
         self._h = C.c_void_p()
         rc = lib.p3maze_batch_create(C.c_void_p(stream or 0), C.byref(self._h))
         if rc:
@@ -454,6 +455,14 @@ class Batch:
         self.members: list[Context] = []
         if mode != "shared":
             self._check(lib.p3maze_batch_set_mode(self._h, {"per_member": self.PER_MEMBER}[mode]))
+        if fused_smoothing is not None:
+            self.set_fused_smoothing(fused_smoothing)
+
+    def set_fused_smoothing(self, enable: bool | None):
+        """Smooth the members whose smoothing is a cluster launch together
+        (one launch per cluster size), each inside its own step, or (None)
+        as the mode prefers: together per member, apart in the shared graph."""
+        self._check(lib.p3maze_batch_set_fused_smoothing(self._h, -1 if enable is None else 1 if enable else 0))
 
     def _check(self, rc: int):
         if rc:

@@ -62,6 +62,84 @@ def test_each_result_is_the_same_alone_and_in_the_batch(P, precision, mode):
             c.close()
 
 
+@pytest.mark.parametrize("mode, fused", [("shared", True), ("shared", False), ("per_member", True),
+                                         ("per_member", False)])
+def test_many_small_members_with_smaller_clusters_match_alone(P, mode, fused):
+    """Twelve members of 16^3-24^3 meshes plus one 48^3 member smoothed per
+    step: with the smoothing fused across members the batch smooths the
+    small ones with 8-CTA clusters (at most one CTA per SM over the launch)
+    where each alone uses 16; the neutrality sum is formed per plane in z
+    order, so the trajectories are still those of each member alone, bit for
+    bit, fused or not."""
+    boxes = [12.8 + 3.2 * (i % 3) for i in range(12)]       # meshes 16, 20, 24 at 0.8 A
+    systems = [(S.nacl_melt(2 * int(round(0.031899 * b ** 3 / 2)), b, seed=70 + i),
+                dict(mesh=int(round(b / 0.8)), r_cut=6.0, dt=1.0)) for i, b in enumerate(boxes)]
+    systems.append((S.nacl_melt(300, 21.1, seed=31), dict(mesh=48, r_cut=9.0, dt=1.0)))
+    per_step = {len(systems) - 1}
+    total = 9
+
+    def make(i):
+        system, kw = systems[i]
+        c = _ctx(P, system, "mixed", **kw)
+        if i in per_step:
+            c.set_tuning(diffusion_fuse=2, diffusion_zc=2)
+        return c
+
+    alone = []
+    for i in range(len(systems)):
+        with make(i) as c:
+            if i == 0 and c.tuning()["diffusion_fuse"] != 5:
+                pytest.skip("the device does not run clusters of the smoothing kernel")
+            c.step(total)
+            alone.append(c.positions())
+    ctxs = [make(i) for i in range(len(systems))]
+    batch = P.Batch(mode=mode, fused_smoothing=fused)
+    try:
+        for c in ctxs:
+            batch.add(c)
+        batch.step(total - 3)
+        batch.wait()
+        for c, pos in zip(ctxs, alone):
+            np.testing.assert_array_equal(c.positions(), pos)
+    finally:
+        batch.close()
+        for c in ctxs:
+            c.close()
+
+
+@pytest.mark.parametrize("mode", ["shared", "per_member"])
+def test_a_setting_changed_inside_the_batch_takes_effect(P, mode):
+    """A member's smoothing mode changed while it is in the batch applies
+    from the next batch step on: the trajectory equals the member stepped
+    alone with the same change at the same step."""
+    system, kw = _systems()[0]
+    switch = dict(diffusion_fuse=2, diffusion_zc=2)
+    with _ctx(P, system, "mixed", **kw) as c:
+        if c.tuning()["diffusion_fuse"] != 5:
+            pytest.skip("the device does not run clusters of the smoothing kernel")
+        c.step(6)
+        c.set_tuning(**switch)
+        c.step(4)
+        ref = c.positions()
+    others = [_ctx(P, s, "mixed", **k) for s, k in _systems()[1:]]
+    ctx = _ctx(P, system, "mixed", **kw)
+    batch = P.Batch(mode=mode)
+    try:
+        for c in [ctx] + others:
+            batch.add(c)
+        batch.step(3)
+        ctx.set_tuning(**switch)
+        ctx.set_timing(True)
+        batch.step(4)
+        batch.wait()
+        np.testing.assert_array_equal(ctx.positions(), ref)
+        assert ctx.timing()["launches"]["smooth"] > 4          # per-step launches again
+    finally:
+        batch.close()
+        for c in [ctx] + others:
+            c.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_device_bytes_estimate_matches_allocation(P, precision):
     for system, kw in _systems():
