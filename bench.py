@@ -11,8 +11,10 @@ One step = one velocity-Verlet MD step through the whole path: kick/drift,
 cell list, charge assignment, 25 diffusion smoothing steps, Mass-Zero
 prediction and multigrid correction solve to tol, field update, erfc +
 Born-Mayer pair forces, force interpolation, kick.  Inputs are resident on
-the device when the timed region starts; L2 is flushed (256 MiB written)
-before every timed step, outside the step's events.
+the device when the timed region starts.  The timed steps run back to back,
+as in an MD run; each step reads and writes about 160 MB of mesh state, more
+than the 126 MB L2.  The same number of steps with the L2 overwritten
+(256 MiB) before each, outside the step's events, is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
@@ -72,8 +74,10 @@ def workload_config(prm):
         "workload": "molten NaCl, 32768 ions, L=100.9 A, 128^3 mesh, alpha 0.30/A, r_cut 9 A, "
                     "order-4 B-spline, tol 1e-6, dt 1 fs, NVE",
         "n_particles": 32768, "mesh": prm["mesh"], "tol": prm["tol"], "dt_fs": prm["dt"],
-        "l2": "flushed (256 MiB write) before every timed GPU step (inputs of the CPU oracle exceed no cache "
-              "it could reuse across steps)",
+        "l2": "inputs larger than L2: the timed GPU steps run back to back, as in an MD run, and each step "
+              "reads and writes about 160 MB of mesh state (phi and psi at two times, two multiplier-history "
+              "buffers and the residual as 64-bit fixed point, five FP32 meshes at 128^3), more than the "
+              "126 MB L2; the same steps with a 256 MiB L2 overwrite before each are ms_per_step_l2_flushed",
         "parallelism": "replicas (one independent system per GPU, no collective)",
         "parameters": "Fumi-Tosi BMH table written from memory, not verified against the 1964 source "
                       "(parity does not depend on it: both arms read the same table)",
@@ -410,8 +414,19 @@ def accuracy_vs_oracle(ctx, system, prm, n_sample: int = 64) -> dict:
 
 
 # ----------------------------------------------------------------- GPU arm
-def time_context(ctx, torch, stream, steps: int, flush):
-    """K timed steps; returns per-step ms list (CUDA events on ctx's stream)."""
+def time_context(ctx, torch, stream, steps: int, flush=None):
+    """K timed steps (CUDA events on ctx's stream); returns per-step ms.
+    flush=None: the K steps back to back, one event pair around them (the
+    per-step list is their mean K times); else the L2 is overwritten with
+    `flush` before every step and each step is timed alone."""
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            ctx.step(steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) / steps] * steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(stream):
         for k in range(steps):
@@ -475,18 +490,20 @@ def run_ours(args) -> int:
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")
     with ClockSampler(gpu_id) as clk:
-        ms = time_context(ctx, torch, stream, args.steps, flush)
+        ms = time_context(ctx, torch, stream, args.steps)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     iters = (ctx.stats()["total_iters"] - it0) / args.steps
     launches = ctx.timing()["total_launches"] - launches0
+    # the same number of steps with the L2 overwritten before each one
+    ms_flushed = time_context(ctx, torch, stream, args.steps, flush)
     # stage breakdown: the same number of steps again with CUDA events around
     # each stage (recorded inside the step graph; not part of the headline)
     ctx.set_timing(True)
     ctx.step(2)
     ctx.set_timing(True)                    # reset the stage tallies
-    ms_staged = time_context(ctx, torch, stream, args.steps, flush)
+    ms_staged = time_context(ctx, torch, stream, args.steps)
     tm = ctx.timing()
     ctx.set_timing(False)
     total_ms = max_over_ranks(sum(ms), world, device="cuda")
@@ -552,12 +569,12 @@ def run_ours(args) -> int:
             cv.step(args.warmup)
             tv_tune = None if (args.no_tune or name != "fp64") else cv.autotune(8)
             it0 = cv.stats()["total_iters"]
-            msv = time_context(cv, torch, stream, args.steps, flush)
+            msv = time_context(cv, torch, stream, args.steps)
             itv = (cv.stats()["total_iters"] - it0) / args.steps
             cv.set_timing(True)
             cv.step(2)
             cv.set_timing(True)
-            time_context(cv, torch, stream, args.steps, flush)
+            time_context(cv, torch, stream, args.steps)
             tv = cv.timing()
             msv_step = max_over_ranks(sum(msv), world, device="cuda") / args.steps
             if name == "fp64" and not args.no_accuracy and rank == 0:
@@ -612,6 +629,7 @@ def run_ours(args) -> int:
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,
         "ms_per_step_with_stage_events": sum(ms_staged) / args.steps,
+        "ms_per_step_l2_flushed": max_over_ranks(sum(ms_flushed), world, device="cuda") / args.steps,
         "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
         "accuracy_vs_oracle": accuracy,
         "roofline_alone": {

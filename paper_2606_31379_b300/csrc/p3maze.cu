@@ -620,7 +620,10 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
             CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
         }
     }
-    CK(go(k_resid_restrict<T>, g3(C.n), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
+    if (C.n >= 64)
+        CK(go(k_resid_restrict_z<T, 4>, gz(C.n, 4), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
+    else
+        CK(go(k_resid_restrict_z<T, 2>, gz(C.n, 2), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
     count(ctx, P3MAZE_ST_SOLVE, (ctx->nu1 > 0 ? 2 * ctx->nu1 - 1 : 0) + 1);
     int rc = vcycle<T>(ctx, l + 1, true);
     if (rc) return rc;
