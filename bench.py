@@ -786,7 +786,7 @@ def served_run(stream, n_req: int, steps: int, slots: int, rate: float = 200.0, 
 
 
 SWEEP = [("nacl_4k", 4096, 50.45, 64), ("nacl_32k", 32768, 100.9, 128), ("nacl_262k", 262144, 201.8, 256),
-         ("nacl_1m", 1000000, 315.4, 384)]
+         ("nacl_580k", 580000, 263.0, 320), ("nacl_1m", 1000000, 315.4, 384)]
 
 
 def run_sweep(args) -> int:

@@ -756,6 +756,132 @@ k_diffuse_tb(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, 
     }
 }
 
+// S explicit diffusion steps per pass over memory in FP32 quads (N % 4 ==
+// 0), 2.5D temporal blocking with asynchronous copies.  A block of 512
+// threads holds a haloed tile of 64 x 32 columns (16 quads x 32 rows; one
+// quad of halo on each x side, S rows on each y side) and streams z from
+// z0 - S to z0 + zc + S.  The input planes of the tile arrive through a ring
+// of kTqRing shared-memory planes filled by cp.async 16-byte copies issued
+// kTqAhead planes ahead (no registers held by loads in flight).  When input
+// plane z_in is resident, level t (t steps applied) is formed at plane
+// z_in - t: level 1 from the ring, level t > 1 from the thread's register
+// window of level t - 1 (z neighbours) and that level's plane published in
+// shared memory one z step earlier (y neighbours, double buffered); x
+// neighbours of a quad come from the adjacent lanes.  Values outside the
+// region where level t is exact (t points in from the haloed tile's edge)
+// are formed but never reach an output.  The per-point arithmetic is
+// k_diffuse4's (same operands, same order), so S launches of k_diffuse4 and
+// one of this kernel give the same bits.  SUM as in k_diffuse4.
+constexpr int kTq = 16, kTh = 32, kTqThreads = kTq * kTh;  // quads per row, rows, threads
+constexpr int kTqAhead = 5, kTqRing = kTqAhead + 3;        // planes in flight; ring planes
+constexpr int kTqTX = 4 * kTq - 8;                         // output columns per tile (56)
+template <int S>
+constexpr int tq_tile_y() { return kTh - 2 * S; }
+template <int S>
+constexpr size_t tq_smem_bytes() {
+    return sizeof(float4) * kTq * kTh * (kTqRing + 2 * (S - 1));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One diffusion step of a quad (k_diffuse4's expression); the x neighbours
+// outside the quad come from the lanes on either side.
+__device__ __forceinline__ float4 diffuse_quad(float4 vc, float4 vm, float4 vp, float4 a, float4 b, float c) {
+    const float left = __shfl_up_sync(0xffffffffu, vc.w, 1);
+    const float right = __shfl_down_sync(0xffffffffu, vc.x, 1);
+    float4 o;
+    o.x = vc.x + c * (left + vc.y + a.x + b.x + vm.x + vp.x - 6.0f * vc.x);
+    o.y = vc.y + c * (vc.x + vc.z + a.y + b.y + vm.y + vp.y - 6.0f * vc.y);
+    o.z = vc.z + c * (vc.y + vc.w + a.z + b.z + vm.z + vp.z - 6.0f * vc.z);
+    o.w = vc.w + c * (vc.z + right + a.w + b.w + vm.w + vp.w - 6.0f * vc.w);
+    return o;
+}
+
+template <int S, bool SUM>
+__global__ void __launch_bounds__(kTqThreads, 2)
+k_diffuse_tq(int n, int zc, const float* __restrict__ in, float* __restrict__ out, float c,
+             double* __restrict__ partial) {
+    constexpr int TY = tq_tile_y<S>();
+    constexpr int PL = kTq * kTh;  // float4 per plane
+    extern __shared__ __align__(16) unsigned char tq_raw[];
+    float4* ring = reinterpret_cast<float4*>(tq_raw);  // [kTqRing][kTh][kTq]
+    float4* lvl = ring + kTqRing * PL;                 // [S-1][2][kTh][kTq]
+    const int tid = threadIdx.x, q = tid & (kTq - 1), r = tid / kTq;
+    const int x0 = blockIdx.x * kTqTX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zc, zend = min(z0 + zc, n);
+    const size_t plane = (size_t)n * n;
+    int gx = (x0 - 4 + 4 * q) % n, gy = (y0 - S + r) % n;  // the quad this thread copies
+    gx = gx < 0 ? gx + n : gx;
+    gy = gy < 0 ? gy + n : gy;
+    const size_t colq = (size_t)gy * n + gx;
+    const int zstart = z0 - S, nsteps = (zend - z0) + 2 * S;
+    pdl_wait();  // `in` comes from the previous launch
+    pdl_trigger();
+    auto issue = [&](int st) {  // input plane zstart + st into ring slot st % kTqRing
+        if (st < nsteps) {
+            int z = (zstart + st) % n;
+            z = z < 0 ? z + n : z;
+            cp_async16(ring + (st % kTqRing) * PL + r * kTq + q, in + (size_t)z * plane + colq);
+        }
+        cp_async_commit();  // one group per plane, empty past the end
+    };
+#pragma unroll
+    for (int d = 0; d < kTqAhead; ++d) issue(d);
+    const int rm = r == 0 ? 0 : r - 1, rp = r == kTh - 1 ? r : r + 1;  // clamped: edge rows are halo
+    const bool writer = q >= 1 && q < kTq - 1 && r >= S && r < kTh - S && x0 + 4 * (q - 1) < n && y0 + r - S < n;
+    const size_t ocol = (size_t)(y0 + r - S) * n + x0 + 4 * (q - 1);
+    float4 win[S > 1 ? S - 1 : 1][3];
+#pragma unroll
+    for (int t = 0; t < (S > 1 ? S - 1 : 1); ++t) win[t][0] = win[t][1] = win[t][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc_s = 0.0f, acc_c = 0.0f;
+    for (int st = 0; st < nsteps; ++st) {
+        cp_async_wait<kTqAhead - 1>();  // this thread's copy of plane st has landed
+        __syncthreads();                // everyone's, and the previous step's reads are done
+        issue(st + kTqAhead);           // into the slot of plane st - 3, no longer read
+        const int cur = st & 1, prv = cur ^ 1;
+        // level 1 at input plane st - 1 (ring slots of st - 2, st - 1, st)
+        const float4* Pm = ring + ((st + 2 * kTqRing - 2) % kTqRing) * PL;
+        const float4* Pc = ring + ((st + kTqRing - 1) % kTqRing) * PL;
+        const float4* Pp = ring + (st % kTqRing) * PL;
+        float4 o = diffuse_quad(Pc[r * kTq + q], Pm[r * kTq + q], Pp[r * kTq + q], Pc[rm * kTq + q],
+                                Pc[rp * kTq + q], c);
+#pragma unroll
+        for (int t = 2; t <= S; ++t) {
+            // publish level t - 1 (formed at plane st - (t - 1)) and form level t from it
+            win[t - 2][0] = win[t - 2][1];
+            win[t - 2][1] = win[t - 2][2];
+            win[t - 2][2] = o;
+            lvl[((t - 2) * 2 + cur) * PL + r * kTq + q] = o;
+            const float4* L = lvl + ((t - 2) * 2 + prv) * PL;
+            o = diffuse_quad(win[t - 2][1], win[t - 2][0], win[t - 2][2], L[rm * kTq + q], L[rp * kTq + q], c);
+        }
+        // o is level S at plane st - S (input numbering), output plane zstart + st - S
+        const int zo = zstart + st - S;
+        if (writer && zo >= z0 && zo < zend) {
+            reinterpret_cast<float4*>(out + (size_t)zo * plane + ocol)[0] = o;
+            if (SUM) {
+                two_sum_add(acc_s, acc_c, o.x);
+                two_sum_add(acc_s, acc_c, o.y);
+                two_sum_add(acc_s, acc_c, o.z);
+                two_sum_add(acc_s, acc_c, o.w);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if (SUM) {
+        const double acc = block_sum((double)acc_s + (double)acc_c);
+        if (tid == 0) partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- reductions
 template <typename T>
 __global__ void k_sum_partial(int64_t m, const T* __restrict__ x, double* __restrict__ partial) {
@@ -1331,16 +1457,32 @@ k_resid_restrict(int nc, const T* __restrict__ e, const T* __restrict__ b, T* __
 
 // The same residual and full weighting, marched in z: a thread owns the
 // coarse column (X, Y) for ZC coarse planes.  It keeps the 3x3 fine points
-// around (2X, 2Y) of three consecutive fine planes in registers, loads per
-// fine plane the next plane's 3x3 block, the 12 in-plane points around the
-// block and the 3x3 of b, forms the nine fine residuals of the plane once
-// (the operand order of nb6) and their x-y weighted sum R(z); then
+// around (2X, 2Y) of three consecutive fine planes in registers, with the
+// left and right neighbours (x = 2X-2, 2X+2) of the centre plane's rows.
+// Per fine plane it loads the next plane's rows as the pairs (2X-2, 2X-1),
+// (2X, 2X+1) and the point 2X+2, the rows 2Y-2 and 2Y+2 of the centre plane
+// and the 3x3 of b as pairs (n is even, so every pair is aligned), forms the
+// nine fine residuals of the plane once (the operand order of nb6) and their
+// x-y weighted sum R(z); then
 //   bc(X, Y, Z) = 4 (R(2Z-1) / 4 + R(2Z) / 2 + R(2Z+1) / 4).
 // The weights are powers of two; only the summation order differs from
-// k_resid_restrict.  About 9 loads per fine point instead of 27.
+// k_resid_restrict.  19 loads per fine plane per thread instead of 27 per
+// fine point.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
 template <typename T, int ZC>
 __global__ void __launch_bounds__(P3_BX * P3_BY)
 k_resid_restrict_z(int nc, const T* __restrict__ e, const T* __restrict__ b, T* __restrict__ bc) {
+    using V2 = typename Vec2<T>::type;
     pdl_wait();
     pdl_trigger();
     const int X = blockIdx.x * P3_BX + threadIdx.x, Y = blockIdx.y * P3_BY + threadIdx.y;
@@ -1348,52 +1490,68 @@ k_resid_restrict_z(int nc, const T* __restrict__ e, const T* __restrict__ b, T* 
     const int n = 2 * nc;
     const int Z0 = blockIdx.z * ZC, Z1 = min(Z0 + ZC, nc);
     const int cx = 2 * X, cy = 2 * Y;
-    const int xs[3] = {cx == 0 ? n - 1 : cx - 1, cx, cx + 1};
+    const int xa = cx == 0 ? n - 2 : cx - 2;              // pair (2X-2, 2X-1), wrapped as a pair
+    const int xr = cx + 2 >= n ? cx + 2 - n : cx + 2;
     const int ys[3] = {cy == 0 ? n - 1 : cy - 1, cy, cy + 1};
-    const int xl = cx < 2 ? cx - 2 + n : cx - 2, xr = cx + 2 >= n ? cx + 2 - n : cx + 2;
     const int yd = cy < 2 ? cy - 2 + n : cy - 2, yu = cy + 2 >= n ? cy + 2 - n : cy + 2;
     const size_t plane = (size_t)n * n;
     const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
-    T em[3][3], ec[3][3], ep[3][3];
-    auto load_block = [&](int z, T (&v)[3][3]) {
+    T em[3][3], ec[3][3], ep[3][3];  // fine planes z-1, z, z+1: [row][x - 2X + 1]
+    T lc[3], rc[3], lp[3], rp[3];    // x = 2X-2 and 2X+2 of the rows of planes z and z+1
+    auto load_rows = [&](int z, T (&v)[3][3], T (&l)[3], T (&r)[3]) {
         const T* p = e + (size_t)z * plane;
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) v[j][i] = p[ys[j] * n + xs[i]];
+        for (int j = 0; j < 3; ++j) {
+            const V2 a = *reinterpret_cast<const V2*>(p + ys[j] * n + xa);
+            const V2 m = *reinterpret_cast<const V2*>(p + ys[j] * n + cx);
+            l[j] = a.x;
+            v[j][0] = a.y;
+            v[j][1] = m.x;
+            v[j][2] = m.y;
+            r[j] = p[ys[j] * n + xr];
+        }
     };
     auto wrapz = [&](int z) { return z < 0 ? z + n : (z >= n ? z - n : z); };
     int f = 2 * Z0 - 1;  // first fine plane
-    load_block(wrapz(f - 1), em);
-    load_block(wrapz(f), ec);
+    {
+        T l[3], r[3];
+        load_rows(wrapz(f - 1), em, l, r);
+    }
+    load_rows(wrapz(f), ec, lc, rc);
     T r_lo = 0, r_mid = 0;  // R of the fine planes 2Z-1 and 2Z
     for (int k = 0; k <= 2 * (Z1 - Z0); ++k, ++f) {
         const int zf = wrapz(f);
-        load_block(wrapz(f + 1), ep);
+        load_rows(wrapz(f + 1), ep, lp, rp);
         const T* pe = e + (size_t)zf * plane;
         const T* pb = b + (size_t)zf * plane;
-        T rl[3], rr[3], rd[3], ru[3], bb[3][3];
+        T rd[3], ru[3], bb[3][3];
+        {
+            const V2 da = *reinterpret_cast<const V2*>(pe + yd * n + xa);
+            const V2 dm = *reinterpret_cast<const V2*>(pe + yd * n + cx);
+            const V2 ua = *reinterpret_cast<const V2*>(pe + yu * n + xa);
+            const V2 um = *reinterpret_cast<const V2*>(pe + yu * n + cx);
+            rd[0] = da.y;
+            rd[1] = dm.x;
+            rd[2] = dm.y;
+            ru[0] = ua.y;
+            ru[1] = um.x;
+            ru[2] = um.y;
+        }
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            rl[j] = pe[ys[j] * n + xl];
-            rr[j] = pe[ys[j] * n + xr];
+            const V2 a = *reinterpret_cast<const V2*>(pb + ys[j] * n + xa);
+            const V2 m = *reinterpret_cast<const V2*>(pb + ys[j] * n + cx);
+            bb[j][0] = a.y;
+            bb[j][1] = m.x;
+            bb[j][2] = m.y;
         }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            rd[i] = pe[yd * n + xs[i]];
-            ru[i] = pe[yu * n + xs[i]];
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) bb[j][i] = pb[ys[j] * n + xs[i]];
         T R = 0;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const T xm = i == 0 ? rl[j] : ec[j][i - 1];
-                const T xp = i == 2 ? rr[j] : ec[j][i + 1];
+                const T xm = i == 0 ? lc[j] : ec[j][i - 1];
+                const T xp = i == 2 ? rc[j] : ec[j][i + 1];
                 const T ym = j == 0 ? rd[i] : ec[j - 1][i];
                 const T yp = j == 2 ? ru[i] : ec[j + 1][i];
                 const T nb = xm + xp + ym + yp + em[j][i] + ep[j][i];
@@ -1410,12 +1568,15 @@ k_resid_restrict_z(int nc, const T* __restrict__ e, const T* __restrict__ b, T* 
             r_lo = R;  // and opens coarse plane Z + 1
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < 3; ++j) {
+            lc[j] = lp[j];
+            rc[j] = rp[j];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 em[j][i] = ec[j][i];
                 ec[j][i] = ep[j][i];
             }
+        }
     }
 }
 

@@ -352,6 +352,36 @@ cudaError_t launch_maybe_pdl(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size
     return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
+// FP32 quads (N % 4 == 0): the asynchronous-copy temporal blocking, a
+// 56 x (32 - 2S) output tile per block.
+template <int S>
+dim3 tq_grid(int n, int zc) {
+    return dim3((n + kTqTX - 1) / kTqTX, (n + tq_tile_y<S>() - 1) / tq_tile_y<S>(), (n + zc - 1) / zc);
+}
+inline unsigned tq_blocks(int n, int zc, int S) {
+    const dim3 g = S == 1 ? tq_grid<1>(n, zc) : S == 2 ? tq_grid<2>(n, zc) : S == 3 ? tq_grid<3>(n, zc)
+                                                                                   : tq_grid<4>(n, zc);
+    return g.x * g.y * g.z;
+}
+template <int S>
+cudaError_t launch_tq_s(p3maze_ctx* ctx, bool last, bool pdl, const float* src, float* dst) {
+    const dim3 g = tq_grid<S>(ctx->N, ctx->zc);
+    if (last)
+        return launch_maybe_pdl(pdl, k_diffuse_tq<S, true>, g, dim3(kTqThreads), tq_smem_bytes<S>(), ctx->stream,
+                                ctx->N, ctx->zc, src, dst, (float)ctx->c, ctx->partial);
+    return launch_maybe_pdl(pdl, k_diffuse_tq<S, false>, g, dim3(kTqThreads), tq_smem_bytes<S>(), ctx->stream,
+                            ctx->N, ctx->zc, src, dst, (float)ctx->c, (double*)nullptr);
+}
+cudaError_t launch_diffuse_tq(p3maze_ctx* ctx, int S, bool last, bool pdl, const float* src, float* dst) {
+    switch (S) {
+        case 1: return launch_tq_s<1>(ctx, last, pdl, src, dst);
+        case 2: return launch_tq_s<2>(ctx, last, pdl, src, dst);
+        case 3: return launch_tq_s<3>(ctx, last, pdl, src, dst);
+        default: return launch_tq_s<4>(ctx, last, pdl, src, dst);
+    }
+}
+
+
 // All diffusion steps of `members` meshes (table on the device, N <= nmax,
 // all with cluster size cs) in one launch, one cluster of cs CTAs per mesh.
 cudaError_t launch_cluster_smoothing(const ClusterMesh* tab, int members, int cs, int nmax, cudaStream_t s,
@@ -484,18 +514,25 @@ int smooth(p3maze_ctx* ctx) {
             CK(launch_cluster_smoothing(ctx->cltab, 1, cs, ctx->N, s, false));
             count(ctx, P3MAZE_ST_SMOOTH, 1);
         } else if (ctx->fuse > 2) {
-            // S = fuse steps per launch (temporal blocking), then the rest
-            int done = 0, launches = 0;
+            // S = fuse steps per launch (temporal blocking), the remainder first
+            const bool quads = ctx->N % 4 == 0;
+            int done = 0, launches = 0, last_S = 1;
             while (done < ctx->K) {
-                const int S = std::min(ctx->fuse, ctx->K - done);
+                const int rem = (ctx->K - done) % ctx->fuse;
+                const int S = (done == 0 && rem) ? rem : std::min(ctx->fuse, ctx->K - done);
                 const bool last = done + S == ctx->K;
                 T* dst = last ? (T*)ctx->qs : tmp[launches & 1];
-                launch_diffuse_tb<T>(ctx, S, last, src, dst);
+                if (quads)
+                    CK(launch_diffuse_tq(ctx, S, last, ctx->pdl && launches > 0, (const float*)src, (float*)dst));
+                else
+                    launch_diffuse_tb<T>(ctx, S, last, src, dst);
                 src = dst;
                 done += S;
+                last_S = S;
                 ++launches;
             }
-            k_sum_final<<<1, 1024, 0, s>>>((int)tb_blocks(ctx->N, ctx->zc), ctx->partial, ctx->dscal + S_QSUM);
+            const int nb = quads ? (int)tq_blocks(ctx->N, ctx->zc, last_S) : (int)tb_blocks(ctx->N, ctx->zc);
+            k_sum_final<<<1, 1024, 0, s>>>(nb, ctx->partial, ctx->dscal + S_QSUM);
             count(ctx, P3MAZE_ST_SMOOTH, launches + 1);
         } else if (ctx->N % 4 == 0) {
             // four points per thread, zc4 planes per thread; fuse 2: two steps
@@ -1328,6 +1365,18 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
             sm = spread_smem_bytes<float>();
             raise((const void*)k_spread_tile<float, MeshPt, true>);
             raise((const void*)k_spread_tile<float, MeshPt, false>);
+            sm = tq_smem_bytes<1>();
+            raise((const void*)k_diffuse_tq<1, true>);
+            raise((const void*)k_diffuse_tq<1, false>);
+            sm = tq_smem_bytes<2>();
+            raise((const void*)k_diffuse_tq<2, true>);
+            raise((const void*)k_diffuse_tq<2, false>);
+            sm = tq_smem_bytes<3>();
+            raise((const void*)k_diffuse_tq<3, true>);
+            raise((const void*)k_diffuse_tq<3, false>);
+            sm = tq_smem_bytes<4>();
+            raise((const void*)k_diffuse_tq<4, true>);
+            raise((const void*)k_diffuse_tq<4, false>);
         } else {
             sm = spread_smem_bytes<double>();
             raise((const void*)k_spread_tile<double, PQ, false>);

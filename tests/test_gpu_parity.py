@@ -573,6 +573,34 @@ def test_two_step_diffusion_kernel_matches_oracle(P, nacl512, mesh, zc):
         assert rel_rms(ctx.forces(), ref["F"]) < 1e-4
 
 
+@pytest.mark.parametrize("mesh, fuse, zc", [(32, 4, 8), (32, 3, 16), (24, 4, 4), (20, 4, 32), (16, 3, 4),
+                                           (64, 4, 16), (18, 4, 8)])
+def test_temporal_blocking_matches_single_steps(P, nacl512, mesh, fuse, zc):
+    """S = fuse diffusion steps per pass over memory (mixed mode; the
+    remainder of K first): the FP32 quad kernel applies k_diffuse4's
+    arithmetic step by step inside a haloed tile, so q^s equals the
+    one-step-per-launch path up to the neutrality mean (formed over other
+    blocks), and the oracle's K steps to the mixed bar.  Meshes below the
+    64-point tile width wrap the halo around the mesh; 18 is not a multiple
+    of 4 and takes the scalar kernel."""
+    with _ctx(P, nacl512, precision="mixed", tol=1e-7, mesh=mesh) as a, \
+            _ctx(P, nacl512, precision="mixed", tol=1e-7, mesh=mesh) as b:
+        a.set_tuning(diffusion_fuse=fuse, diffusion_zc=zc)
+        b.set_tuning(diffusion_fuse=1, diffusion_zc=2)
+        a.reinit()
+        b.reinit()
+        K = a.stats()["smooth_steps"]
+        qa, qb = a.mesh("qs"), b.mesh("qs")
+        assert np.abs(qa - qb).max() <= 1e-12 * np.abs(qb).max()
+        mf = O.mesh_fields(at_positions(nacl512, a.positions()), 0.30, mesh)
+        assert np.abs(qa - mf["qs"]).max() <= 1e-6 * np.abs(mf["qs"]).max()
+        a.set_timing(True)
+        a.step(1)
+        assert a.timing()["launches"]["smooth"] == -(-K // fuse) + 1
+        ref = oracle_full(nacl512, a.positions(), 0.30, 9.0, mesh)
+        assert rel_rms(a.forces(), ref["F"]) < 1e-4
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_nve_total_energy_is_conserved(P, nacl512, precision):
     """NVE after relaxation (1000 velocity-rescaled steps at 1200 K): over
