@@ -226,9 +226,12 @@ typedef struct {
     int32_t predictor;          /* chosen multiplier predictor (0 for P3M)              */
     int32_t pre_sweeps;         /* chosen red-black Gauss-Seidel sweeps before / after  */
     int32_t post_sweeps;
-    int32_t diffusion_zc;       /* z planes per thread (block) of the diffusion kernel  */
+    int32_t diffusion_zc;       /* z planes per thread (modes 1, 2) or per block (3, 4) of the
+                                   diffusion kernel                                        */
     int32_t diffusion_fuse;     /* diffusion steps per launch: 1; 2 (two steps as one 25-point
-                                   stencil, FP32, N % 4 == 0); 3 or 4 (temporal blocking);
+                                   stencil, FP32, N % 4 == 0); 3 or 4 (temporal blocking in
+                                   shared memory, the input planes copied asynchronously;
+                                   FP32 quads when N % 4 == 0);
                                    5: all K steps in one launch, the mesh resident in the
                                    shared memory of a thread-block cluster (FP32,
                                    16 <= N <= 64, N % 4 == 0; the default there when the

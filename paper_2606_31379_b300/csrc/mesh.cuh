@@ -757,24 +757,27 @@ k_diffuse_tb(int n, int zc, const T* __restrict__ in, T* __restrict__ out, T c, 
 }
 
 // S explicit diffusion steps per pass over memory in FP32 quads (N % 4 ==
-// 0), 2.5D temporal blocking with asynchronous copies.  A block of 512
+// 0), 2.5D temporal blocking with asynchronous copies.  A block of 256
 // threads holds a haloed tile of 64 x 32 columns (16 quads x 32 rows; one
-// quad of halo on each x side, S rows on each y side) and streams z from
-// z0 - S to z0 + zc + S.  The input planes of the tile arrive through a ring
-// of kTqRing shared-memory planes filled by cp.async 16-byte copies issued
+// quad of halo on each x side, S rows on each y side); thread (q, p) owns the
+// quad q of rows 2p and 2p+1.  The block streams z from z0 - S to
+// z0 + zc + S.  The input planes of the tile arrive through a ring of
+// kTqRing shared-memory planes filled by cp.async 16-byte copies issued
 // kTqAhead planes ahead (no registers held by loads in flight).  When input
 // plane z_in is resident, level t (t steps applied) is formed at plane
-// z_in - t: level 1 from the ring, level t > 1 from the thread's register
-// window of level t - 1 (z neighbours) and that level's plane published in
-// shared memory one z step earlier (y neighbours, double buffered); x
-// neighbours of a quad come from the adjacent lanes.  Values outside the
+// z_in - t: each thread keeps, for both of its rows, a register window of
+// three consecutive planes of the input and of every level below S (the z
+// neighbours); the y neighbour between its two rows is in registers, the
+// outer two come from the plane published in shared memory one z step
+// earlier (the input ring for level 1; double-buffered level planes above);
+// x neighbours of a quad come from the adjacent lanes.  Values outside the
 // region where level t is exact (t points in from the haloed tile's edge)
 // are formed but never reach an output.  The per-point arithmetic is
 // k_diffuse4's (same operands, same order), so S launches of k_diffuse4 and
 // one of this kernel give the same bits.  SUM as in k_diffuse4.
-constexpr int kTq = 16, kTh = 32, kTqThreads = kTq * kTh;  // quads per row, rows, threads
-constexpr int kTqAhead = 5, kTqRing = kTqAhead + 3;        // planes in flight; ring planes
-constexpr int kTqTX = 4 * kTq - 8;                         // output columns per tile (56)
+constexpr int kTq = 16, kTh = 32, kTqThreads = kTq * kTh / 2;  // quads per row, rows, threads
+constexpr int kTqAhead = 5, kTqRing = kTqAhead + 3;            // planes in flight; ring planes
+constexpr int kTqTX = 4 * kTq - 8;                             // output columns per tile (56)
 template <int S>
 constexpr int tq_tile_y() { return kTh - 2 * S; }
 template <int S>
@@ -811,17 +814,19 @@ k_diffuse_tq(int n, int zc, const float* __restrict__ in, float* __restrict__ ou
              double* __restrict__ partial) {
     constexpr int TY = tq_tile_y<S>();
     constexpr int PL = kTq * kTh;  // float4 per plane
+    constexpr int NW = S > 1 ? S - 1 : 1;
     extern __shared__ __align__(16) unsigned char tq_raw[];
     float4* ring = reinterpret_cast<float4*>(tq_raw);  // [kTqRing][kTh][kTq]
     float4* lvl = ring + kTqRing * PL;                 // [S-1][2][kTh][kTq]
-    const int tid = threadIdx.x, q = tid & (kTq - 1), r = tid / kTq;
+    const int tid = threadIdx.x, q = tid & (kTq - 1), r0 = 2 * (tid / kTq), r1 = r0 + 1;
     const int x0 = blockIdx.x * kTqTX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zc, zend = min(z0 + zc, n);
     const size_t plane = (size_t)n * n;
-    int gx = (x0 - 4 + 4 * q) % n, gy = (y0 - S + r) % n;  // the quad this thread copies
+    int gx = (x0 - 4 + 4 * q) % n, gy0 = (y0 - S + r0) % n, gy1 = (y0 - S + r1) % n;  // the quads this thread copies
     gx = gx < 0 ? gx + n : gx;
-    gy = gy < 0 ? gy + n : gy;
-    const size_t colq = (size_t)gy * n + gx;
+    gy0 = gy0 < 0 ? gy0 + n : gy0;
+    gy1 = gy1 < 0 ? gy1 + n : gy1;
+    const size_t col0 = (size_t)gy0 * n + gx, col1 = (size_t)gy1 * n + gx;
     const int zstart = z0 - S, nsteps = (zend - z0) + 2 * S;
     pdl_wait();  // `in` comes from the previous launch
     pdl_trigger();
@@ -829,49 +834,82 @@ k_diffuse_tq(int n, int zc, const float* __restrict__ in, float* __restrict__ ou
         if (st < nsteps) {
             int z = (zstart + st) % n;
             z = z < 0 ? z + n : z;
-            cp_async16(ring + (st % kTqRing) * PL + r * kTq + q, in + (size_t)z * plane + colq);
+            float4* d = ring + (st % kTqRing) * PL + q;
+            cp_async16(d + r0 * kTq, in + (size_t)z * plane + col0);
+            cp_async16(d + r1 * kTq, in + (size_t)z * plane + col1);
         }
         cp_async_commit();  // one group per plane, empty past the end
     };
 #pragma unroll
     for (int d = 0; d < kTqAhead; ++d) issue(d);
-    const int rm = r == 0 ? 0 : r - 1, rp = r == kTh - 1 ? r : r + 1;  // clamped: edge rows are halo
-    const bool writer = q >= 1 && q < kTq - 1 && r >= S && r < kTh - S && x0 + 4 * (q - 1) < n && y0 + r - S < n;
-    const size_t ocol = (size_t)(y0 + r - S) * n + x0 + 4 * (q - 1);
-    float4 win[S > 1 ? S - 1 : 1][3];
+    const int ra = r0 == 0 ? 0 : r0 - 1, rb = r1 == kTh - 1 ? r1 : r1 + 1;  // outer y neighbours (edge rows are halo)
+    const bool wq = q >= 1 && q < kTq - 1 && x0 + 4 * (q - 1) < n;
+    const bool w0 = wq && r0 >= S && r0 < kTh - S && y0 + r0 - S < n;
+    const bool w1 = wq && r1 >= S && r1 < kTh - S && y0 + r1 - S < n;
+    const size_t oc0 = (size_t)(y0 + r0 - S) * n + x0 + 4 * (q - 1), oc1 = oc0 + n;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 i0[3] = {z4, z4, z4}, i1[3] = {z4, z4, z4};  // input window, rows r0 and r1
+    float4 w[NW][2][3];                                 // level windows
 #pragma unroll
-    for (int t = 0; t < (S > 1 ? S - 1 : 1); ++t) win[t][0] = win[t][1] = win[t][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 0; t < NW; ++t)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) w[t][0][k] = w[t][1][k] = z4;
     float acc_s = 0.0f, acc_c = 0.0f;
     for (int st = 0; st < nsteps; ++st) {
-        cp_async_wait<kTqAhead - 1>();  // this thread's copy of plane st has landed
+        cp_async_wait<kTqAhead - 1>();  // this thread's copies of plane st have landed
         __syncthreads();                // everyone's, and the previous step's reads are done
         issue(st + kTqAhead);           // into the slot of plane st - 3, no longer read
         const int cur = st & 1, prv = cur ^ 1;
-        // level 1 at input plane st - 1 (ring slots of st - 2, st - 1, st)
-        const float4* Pm = ring + ((st + 2 * kTqRing - 2) % kTqRing) * PL;
-        const float4* Pc = ring + ((st + kTqRing - 1) % kTqRing) * PL;
-        const float4* Pp = ring + (st % kTqRing) * PL;
-        float4 o = diffuse_quad(Pc[r * kTq + q], Pm[r * kTq + q], Pp[r * kTq + q], Pc[rm * kTq + q],
-                                Pc[rp * kTq + q], c);
+        const float4* Pn = ring + (st % kTqRing) * PL;                   // plane st
+        const float4* Pc = ring + ((st + kTqRing - 1) % kTqRing) * PL;  // plane st - 1
+        i0[0] = i0[1];
+        i0[1] = i0[2];
+        i0[2] = Pn[r0 * kTq + q];
+        i1[0] = i1[1];
+        i1[1] = i1[2];
+        i1[2] = Pn[r1 * kTq + q];
+        // level 1 at input plane st - 1
+        float4 o0 = diffuse_quad(i0[1], i0[0], i0[2], Pc[ra * kTq + q], i1[1], c);
+        float4 o1 = diffuse_quad(i1[1], i1[0], i1[2], i0[1], Pc[rb * kTq + q], c);
 #pragma unroll
         for (int t = 2; t <= S; ++t) {
             // publish level t - 1 (formed at plane st - (t - 1)) and form level t from it
-            win[t - 2][0] = win[t - 2][1];
-            win[t - 2][1] = win[t - 2][2];
-            win[t - 2][2] = o;
-            lvl[((t - 2) * 2 + cur) * PL + r * kTq + q] = o;
+            float4* W0 = w[t - 2][0];
+            float4* W1 = w[t - 2][1];
+            W0[0] = W0[1];
+            W0[1] = W0[2];
+            W0[2] = o0;
+            W1[0] = W1[1];
+            W1[1] = W1[2];
+            W1[2] = o1;
+            float4* Lc = lvl + ((t - 2) * 2 + cur) * PL;
+            Lc[r0 * kTq + q] = o0;
+            Lc[r1 * kTq + q] = o1;
             const float4* L = lvl + ((t - 2) * 2 + prv) * PL;
-            o = diffuse_quad(win[t - 2][1], win[t - 2][0], win[t - 2][2], L[rm * kTq + q], L[rp * kTq + q], c);
+            o0 = diffuse_quad(W0[1], W0[0], W0[2], L[ra * kTq + q], W1[1], c);
+            o1 = diffuse_quad(W1[1], W1[0], W1[2], W0[1], L[rb * kTq + q], c);
         }
-        // o is level S at plane st - S (input numbering), output plane zstart + st - S
+        // o0, o1: level S at plane st - S (input numbering), output plane zstart + st - S
         const int zo = zstart + st - S;
-        if (writer && zo >= z0 && zo < zend) {
-            reinterpret_cast<float4*>(out + (size_t)zo * plane + ocol)[0] = o;
-            if (SUM) {
-                two_sum_add(acc_s, acc_c, o.x);
-                two_sum_add(acc_s, acc_c, o.y);
-                two_sum_add(acc_s, acc_c, o.z);
-                two_sum_add(acc_s, acc_c, o.w);
+        if (zo >= z0 && zo < zend) {
+            float* op = out + (size_t)zo * plane;
+            if (w0) {
+                *reinterpret_cast<float4*>(op + oc0) = o0;
+                if (SUM) {
+                    two_sum_add(acc_s, acc_c, o0.x);
+                    two_sum_add(acc_s, acc_c, o0.y);
+                    two_sum_add(acc_s, acc_c, o0.z);
+                    two_sum_add(acc_s, acc_c, o0.w);
+                }
+            }
+            if (w1) {
+                *reinterpret_cast<float4*>(op + oc1) = o1;
+                if (SUM) {
+                    two_sum_add(acc_s, acc_c, o1.x);
+                    two_sum_add(acc_s, acc_c, o1.y);
+                    two_sum_add(acc_s, acc_c, o1.z);
+                    two_sum_add(acc_s, acc_c, o1.w);
+                }
             }
         }
     }

@@ -2210,12 +2210,13 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
             }
         }
     }
-    // diffusion kernel: steps per launch (mixed: 1, 2 or 4) x z planes per
-    // thread (one or two steps per launch, N % 4 == 0: 1-8) or per block
+    // diffusion kernel: steps per launch (mixed: 1 to 4, or all in a
+    // cluster) x z planes per thread (one or two steps per launch, N % 4 ==
+    // 0: 1-8) or per block (temporal blocking: 8-64 in quads, else 4-32)
     auto diffusion_pass = [&]() {
         if (ctx->K == 0) return;  // no smoothing (PMaZe)
-        const int fuses[4] = {1, 2, 4, 5};
-        const int zcs_quad[4] = {1, 2, 4, 8}, zcs_other[4] = {4, 8, 16, 32};
+        const int fuses[5] = {1, 2, 3, 4, 5};
+        const int zcs_quad[4] = {1, 2, 4, 8}, zcs_tq[4] = {8, 16, 32, 64}, zcs_other[4] = {4, 8, 16, 32};
         const Setting base = chosen;
         for (int f : fuses) {
             if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
@@ -2223,9 +2224,11 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
             if (f == 5 && !ctx->cluster_ok) continue;
             const bool quad = f <= 2 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
             // the cluster kernel has no z planes per thread: one trial
+            const bool tq = f >= 3 && f <= 4 && ctx->N % 4 == 0;
             std::vector<int> zcs = f == 5 ? std::vector<int>{base.zc}
-                                          : quad ? std::vector<int>(zcs_quad, zcs_quad + 4)
-                                                 : std::vector<int>(zcs_other, zcs_other + 4);
+                                   : quad ? std::vector<int>(zcs_quad, zcs_quad + 4)
+                                   : tq   ? std::vector<int>(zcs_tq, zcs_tq + 4)
+                                          : std::vector<int>(zcs_other, zcs_other + 4);
             for (int z : zcs) {
                 if (z == base.zc && f == base.fuse) continue;
                 Setting c = chosen;

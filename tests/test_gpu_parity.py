@@ -408,10 +408,10 @@ def test_autotuner_keeps_results_within_tolerance(P, nacl512):
         t = ctx.autotune(3)
         assert t["predictor"] in (1, 2, 3)
         assert (t["pre_sweeps"], t["post_sweeps"]) in ((1, 1), (2, 1), (1, 2), (2, 2), (3, 3))
-        # planes per thread (one step per launch, FP32 quads) or per block (4 steps per launch),
-        # or every step in one cluster launch (the planes-per-thread setting is then unused)
+        # planes per thread (one or two steps per launch, FP32 quads) or per block (3 or 4 steps
+        # per launch), or every step in one cluster launch (the planes setting is then unused)
         assert (t["diffusion_fuse"], t["diffusion_zc"]) in [(f, z) for f in (1, 2) for z in (1, 2, 4, 8)] + \
-            [(4, z) for z in (4, 8, 16, 32)] or t["diffusion_fuse"] == 5
+            [(f, z) for f in (3, 4) for z in (8, 16, 32, 64)] or t["diffusion_fuse"] == 5
         assert t["trials"] >= 16 and t["ms_per_step"] <= t["initial_ms_per_step"]
         assert ctx.stats()["steps"] == 4 + t["steps"]
         ctx.step(2)
