@@ -855,6 +855,7 @@ k_diffuse_tq(int n, int zc, const float* __restrict__ in, float* __restrict__ ou
 #pragma unroll
         for (int k = 0; k < 3; ++k) w[t][0][k] = w[t][1][k] = z4;
     float acc_s = 0.0f, acc_c = 0.0f;
+#pragma unroll 3  // the three-plane windows rotate by renaming
     for (int st = 0; st < nsteps; ++st) {
         cp_async_wait<kTqAhead - 1>();  // this thread's copies of plane st have landed
         __syncthreads();                // everyone's, and the previous step's reads are done

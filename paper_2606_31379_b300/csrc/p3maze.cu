@@ -657,7 +657,7 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
             CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
         }
     }
-    if (C.n >= 64)
+    if (C.n >= 128)
         CK(go(k_resid_restrict_z<T, 4>, gz(C.n, 4), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
     else
         CK(go(k_resid_restrict_z<T, 2>, gz(C.n, 2), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
