@@ -246,6 +246,10 @@ typedef struct {
                                    context stepped alone, and in a per-member batch the
                                    largest that keeps the batch's launch within one CTA
                                    per SM.  Ignored by the other modes.                      */
+    int32_t sweep_fuse;         /* 1 (default): on FP32 levels with N % 4 == 0 the red-black
+                                   sweeps after the first run in pairs of one-launch,
+                                   out-of-place full sweeps; 0: two in-place half sweeps per
+                                   sweep.  The same bits either way.                           */
     double ms_per_step;         /* measured with the chosen setting                    */
     double initial_ms_per_step; /* measured with the setting in use before tuning      */
     int32_t trials;             /* settings timed                                      */
@@ -386,7 +390,8 @@ int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
 /* Apply a setting (as p3maze_autotune returns it) without timing anything:
  * predictor (1..3; ignored for P3M), pre_sweeps >= 1, post_sweeps >= 0,
  * diffusion_zc >= 1, diffusion_fuse 1..5, pair_fork 0 or 1, coarse_max >= 1,
- * pair_blocks >= 0; the timing fields are ignored.  Captured step graphs are
+ * pair_blocks >= 0, cluster_ctas 0 or a power of two up to 16, sweep_fuse 0 or
+ * 1; the timing fields are ignored.  Captured step graphs are
  * dropped.  Errors: INVALID (out-of-range field, nothing changed).            */
 int p3maze_set_tuning(p3maze_ctx *ctx, const p3maze_tuning *setting);
 
@@ -412,10 +417,9 @@ int p3maze_set_graphs(p3maze_ctx *ctx, int32_t enable);
  * ping-pong mesh and the block sums of the mean), present on every GPU that
  * loads this library until the process exits.  No cudaMalloc, cudaFree or
  * allocating library routine is called.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  The address is kept for
- * the life of the process, so calls must not span a cudaDeviceReset of the
- * device.  q and qs must not overlap each other or the scratch array
+ * the array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it for the life of the process, so calls must not span a
+ * cudaDeviceReset of the device.  q and qs must not overlap each other or the scratch array
  * (INVALID).  All calls on a device share the array and keep nothing from
  * earlier calls: calls that overlap on the GPU (different streams, or host
  * threads queueing concurrently) race on it and must be ordered by the

@@ -1688,6 +1688,131 @@ k_rbgs_first4(int n, float* __restrict__ e, const float* __restrict__ b) {
     }
 }
 
+// One full red-black Gauss-Seidel sweep in one launch (FP32 quads, N % 4 ==
+// 0), out of place: colour PA first from the old values in ein, then the
+// other colour from the new ones, every point written to eout -- the two
+// in-place launches of k_rbgs (PA, then 1 - PA) bit for bit, each point
+// formed by the same expression (nb6's operand order, minus b, times 1/6).
+// In place it would race: a block reads old second-colour values that its
+// neighbours overwrite.  A thread owns a quad of row y and marches ZC planes
+// in z; it keeps
+// the old rows y-1, y, y+1 of the planes around the current one and the new
+// first-colour values of its row at planes z-1, z, z+1 in registers, and
+// forms the new first-colour values of rows y-1 and y+1 at plane z itself
+// (their old rows y-2 and y+2 loaded), so no value crosses threads but by
+// shuffle.  x neighbours come from the adjacent lanes; a warp is one row of
+// 32 quads of which lanes 1..30 are written (lanes 0 and 31 are halo, their
+// outer points never reach a written value).
+template <int PA, int ZC>
+__global__ void __launch_bounds__(P3_BX * P3_BY)
+k_rbgs_pair4(int n, const float* __restrict__ e, float* __restrict__ eout, const float* __restrict__ b) {
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x;
+    const int nq = n >> 2;
+    int qd = (int)blockIdx.x * (P3_BX - 2) + lane - 1;  // quad of this lane (wrapped for loads)
+    const bool writer = lane >= 1 && lane <= P3_BX - 2 && qd >= 0 && qd < nq;
+    qd = ((qd % nq) + nq) % nq;
+    const int x = 4 * qd;
+    const int y = (int)blockIdx.y * P3_BY + threadIdx.y;
+    const bool live = y < n;
+    const int yy = live ? y : 0;
+    auto wr = [&](int v) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+    const int ym = wr(yy - 1), yp = wr(yy + 1), ymm = wr(yy - 2), ypp = wr(yy + 2);
+    const size_t plane = (size_t)n * n;
+    auto ld = [&](const float* a, int row, int z) {
+        return *reinterpret_cast<const float4*>(a + (size_t)wr(z) * plane + (size_t)row * n + x);
+    };
+    const float sixth = (float)(1.0 / 6.0);
+    // the first colour at the points of quad c (row parity par = (row + z) & 1); the
+    // other points keep their old values
+    auto first = [&](float4 c, float4 am, float4 ap, float4 zm, float4 zp, float4 bb, int par) {
+        const float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+        const float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+        const float xs[6] = {left, c.x, c.y, c.z, c.w, right};
+        const float ya[4] = {am.x, am.y, am.z, am.w}, yb[4] = {ap.x, ap.y, ap.z, ap.w};
+        const float za[4] = {zm.x, zm.y, zm.z, zm.w}, zb[4] = {zp.x, zp.y, zp.z, zp.w};
+        const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (((par + j) & 1) == PA) {
+                const float s = xs[j] + xs[j + 2] + ya[j] + yb[j] + za[j] + zb[j];
+                o[j] = (s - bv[j]) * sixth;
+            } else {
+                o[j] = xs[j + 1];
+            }
+        }
+        return make_float4(o[0], o[1], o[2], o[3]);
+    };
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, n);
+    // windows: old row y at planes z-1 .. z+2, old rows y-1 and y+1 at z-1 .. z+1,
+    // b row y at z, z+1, new first colour of row y at z-1 .. z+1
+    float4 r0[4], rm[3], rp[3], bq[2], na[3];
+    r0[0] = ld(e, yy, z0 - 2);  // (used only to form na[0])
+    r0[1] = ld(e, yy, z0 - 1);
+    r0[2] = ld(e, yy, z0);
+    r0[3] = ld(e, yy, z0 + 1);
+    rm[0] = ld(e, ym, z0 - 1);
+    rm[1] = ld(e, ym, z0);
+    rp[0] = ld(e, yp, z0 - 1);
+    rp[1] = ld(e, yp, z0);
+    bq[0] = ld(b, yy, z0 - 1);
+    bq[1] = ld(b, yy, z0);
+    na[0] = first(r0[1], rm[0], rp[0], r0[0], r0[2], bq[0], (yy + z0 - 1) & 1);
+    na[1] = first(r0[2], rm[1], rp[1], r0[1], r0[3], bq[1], (yy + z0) & 1);
+    // shift to the loop's indexing: r0 = planes z-1 .. z+1 (+ z+2 loaded in the loop)
+    r0[0] = r0[1];
+    r0[1] = r0[2];
+    r0[2] = r0[3];
+    bq[0] = bq[1];
+    for (int z = z0; z < z1; ++z) {
+        r0[3] = ld(e, yy, z + 2);
+        rm[2] = ld(e, ym, z + 1);
+        rp[2] = ld(e, yp, z + 1);
+        const float4 rmm = ld(e, ymm, z), rpp = ld(e, ypp, z);
+        bq[1] = ld(b, yy, z + 1);
+        const float4 bm = ld(b, ym, z), bp = ld(b, yp, z);
+        na[2] = first(r0[2], rm[2], rp[2], r0[1], r0[3], bq[1], (yy + z + 1) & 1);
+        const float4 nam = first(rm[1], rmm, r0[1], rm[0], rm[2], bm, (yy + 1 + z) & 1);
+        const float4 nap = first(rp[1], r0[1], rpp, rp[0], rp[2], bp, (yy + 1 + z) & 1);
+        // the second colour at row y, plane z from the new first-colour values
+        {
+            const float4 c = na[1];
+            const float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+            const float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+            const float xs[6] = {left, c.x, c.y, c.z, c.w, right};
+            const float ya[4] = {nam.x, nam.y, nam.z, nam.w}, yb[4] = {nap.x, nap.y, nap.z, nap.w};
+            const float za[4] = {na[0].x, na[0].y, na[0].z, na[0].w}, zb[4] = {na[2].x, na[2].y, na[2].z, na[2].w};
+            const float bv[4] = {bq[0].x, bq[0].y, bq[0].z, bq[0].w};
+            const int par = (yy + z) & 1;
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (((par + j) & 1) != PA) {
+                    const float s = xs[j] + xs[j + 2] + ya[j] + yb[j] + za[j] + zb[j];
+                    o[j] = (s - bv[j]) * sixth;
+                } else {
+                    o[j] = xs[j + 1];
+                }
+            }
+            if (writer && live)
+                *reinterpret_cast<float4*>(eout + (size_t)z * plane + (size_t)yy * n + x) =
+                    make_float4(o[0], o[1], o[2], o[3]);
+        }
+        r0[0] = r0[1];
+        r0[1] = r0[2];
+        r0[2] = r0[3];
+        rm[0] = rm[1];
+        rm[1] = rm[2];
+        rp[0] = rp[1];
+        rp[1] = rp[2];
+        bq[0] = bq[1];
+        na[0] = na[1];
+        na[1] = na[2];
+    }
+}
+
 // Trilinear prolongation and correction e_f += P e_c in FP32 with four x
 // points and the two z planes 2Z, 2Z+1 per thread (N % 4 == 0): the 12
 // coarse values of a quad pair are loaded once and every output is formed

@@ -41,6 +41,10 @@ struct Level {
     void* H = nullptr;
     void* D = nullptr;
     void* t = nullptr;
+    // FP32 levels with N % 4 == 0 that sweep: the other buffer of the
+    // out-of-place full sweeps (level 0: the smoothing ping-pong buffer, free
+    // during the solve)
+    void* e2 = nullptr;
 };
 
 // One captured MD step for a given pointer phase of the field rings.
@@ -99,6 +103,7 @@ struct p3maze_ctx {
     ClusterMesh* cltab = nullptr;        // this mesh's entry for the cluster smoothing kernel
     bool cluster_ok = false;             // the device runs this mesh's clusters of the smoothing kernel
     int cl_ctas = 0;                     // CTAs per cluster of mode 5 (0: automatic)
+    int sweep_fuse = 1;                  // FP32 quad levels: a full red-black sweep per launch
     int64_t settings_gen = 0;            // bumped whenever a setting recorded in graphs changes
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
@@ -637,6 +642,41 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
     }
     // FP32 levels with N % 4 == 0 take the four-points-per-thread kernels
     const bool quads = sizeof(T) == 4 && L.n % 4 == 0;
+    int launches = 0;
+    // `count` full red-black sweeps, colour pa first.  FP32 quad levels run
+    // them in pairs of out-of-place full sweeps (e -> e2 -> e) so that the
+    // result lands in e; an odd one first as the two in-place half sweeps.
+    auto sweeps = [&](int count, int pa) -> int {
+        const bool pairs = quads && ctx->sweep_fuse && L.e2;
+        int done = 0;
+        if (!pairs || (count & 1)) {
+            const int halves = pairs ? 1 : count;
+            for (int k = 0; k < halves; ++k) {
+                CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, pa, 0));
+                CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1 - pa, 0));
+                launches += 2;
+            }
+            done = halves;
+        }
+        if constexpr (sizeof(T) == 4) {
+            const int zc = L.n >= 128 ? 4 : 2;
+            const dim3 g((L.n / 4 + P3_BX - 3) / (P3_BX - 2), (L.n + P3_BY - 1) / P3_BY, (L.n + zc - 1) / zc);
+            float* const e1 = (float*)e;
+            float* const e2 = (float*)L.e2;
+            for (; done < count; done += 2) {
+                for (int h = 0; h < 2; ++h) {
+                    const float* src = h ? e2 : e1;
+                    float* dst = h ? e1 : e2;
+                    if (pa == 0 && zc == 4) CK(go(k_rbgs_pair4<0, 4>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                    else if (pa == 0) CK(go(k_rbgs_pair4<0, 2>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                    else if (zc == 4) CK(go(k_rbgs_pair4<1, 4>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                    else CK(go(k_rbgs_pair4<1, 2>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                    launches += 1;
+                }
+            }
+        }
+        return P3MAZE_OK;
+    };
     for (int it = 0; it < ctx->nu1; ++it) {
         if (it == 0) {
             // both colours from e = 0
@@ -652,16 +692,20 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
             } else {
                 CK(go(k_rbgs_first<T>, g3(L.n), kB3, 0, L.n, e, (const T*)b));
             }
+            launches += 1;
         } else {
-            CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 0, 0));
-            CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
+            // the remaining pre-sweeps at once
+            int rc = sweeps(ctx->nu1 - 1, 0);
+            if (rc) return rc;
+            break;
         }
     }
     if (C.n >= 128)
         CK(go(k_resid_restrict_z<T, 4>, gz(C.n, 4), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
     else
         CK(go(k_resid_restrict_z<T, 2>, gz(C.n, 2), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
-    count(ctx, P3MAZE_ST_SOLVE, (ctx->nu1 > 0 ? 2 * ctx->nu1 - 1 : 0) + 1);
+    count(ctx, P3MAZE_ST_SOLVE, launches + 1);
+    launches = 0;
     int rc = vcycle<T>(ctx, l + 1, true);
     if (rc) return rc;
     if constexpr (sizeof(T) == 4) {
@@ -674,11 +718,9 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
     } else {
         CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
     }
-    for (int it = 0; it < ctx->nu2; ++it) {
-        CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1, 0));
-        CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 0, 0));
-    }
-    count(ctx, P3MAZE_ST_SOLVE, 1 + 2 * ctx->nu2);
+    rc = sweeps(ctx->nu2, 1);
+    if (rc) return rc;
+    count(ctx, P3MAZE_ST_SOLVE, 1 + launches);
     return P3MAZE_OK;
 }
 
@@ -1333,6 +1375,10 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         ALLOC(L.e, tb * L.pts);
         ALLOC(L.b, tb * L.pts);
         if (l == 0) ALLOC(L.r, tb * L.pts);  // smoothing ping-pong buffer
+        if (mixed && nn % 4 == 0) {
+            if (l == 0) L.e2 = L.r;
+            else if (l + 1 < ctx->nlev) ALLOC(L.e2, tb * L.pts);  // the deepest level never sweeps
+        }
         if (nn <= kCoarseMax) {
             ALLOC(L.H, tb * (size_t)nn * nn);
             ALLOC(L.D, tb * L.pts);
@@ -1501,6 +1547,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
         const size_t pts = (size_t)nn * nn * nn;
         b += a(tb * pts) + a(tb * pts);
         if (l == 0) b += a(tb * pts);
+        if (mixed && nn % 4 == 0 && l > 0 && l + 1 < nlev) b += a(tb * pts);  // e2
         if (nn <= kCoarseMax) b += a(tb * (size_t)nn * nn) + a(tb * pts) + a(tb * pts);  // H D t
         nn /= 2;
     }
@@ -2312,6 +2359,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     out->coarse_max = ctx->cmax;
     out->pair_blocks = ctx->pair_blocks;
     out->cluster_ctas = ctx->cl_ctas;
+    out->sweep_fuse = ctx->sweep_fuse;
     out->ms_per_step = best;
     out->initial_ms_per_step = initial;
     out->trials = trials;
@@ -2325,7 +2373,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (t->predictor < 1 || t->predictor > 3 || t->pre_sweeps < 1 || t->post_sweeps < 0 || t->diffusion_zc < 1 ||
         t->diffusion_fuse < 1 || t->diffusion_fuse > 5 || (t->pair_fork != 0 && t->pair_fork != 1) ||
         t->coarse_max < 1 || t->pair_blocks < 0 || t->cluster_ctas < 0 || t->cluster_ctas > kClMaxCTAs ||
-        (t->cluster_ctas & (t->cluster_ctas - 1)) != 0)
+        (t->cluster_ctas & (t->cluster_ctas - 1)) != 0 || (t->sweep_fuse != 0 && t->sweep_fuse != 1))
         return fail(ctx, P3MAZE_ERR_INVALID, "tuning field out of range");
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
@@ -2345,6 +2393,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     ctx->pair_fork = t->pair_fork;
     ctx->pair_blocks = t->pair_blocks;
     ctx->cl_ctas = t->cluster_ctas;
+    ctx->sweep_fuse = t->sweep_fuse;
     set_coarse(ctx, t->coarse_max);
     destroy_graphs(ctx);
     ctx->settings_gen += 1;
@@ -2363,6 +2412,7 @@ int p3maze_get_tuning(p3maze_ctx* ctx, p3maze_tuning* out) {
     out->coarse_max = ctx->cmax;
     out->pair_blocks = ctx->pair_blocks;
     out->cluster_ctas = ctx->cl_ctas;
+    out->sweep_fuse = ctx->sweep_fuse;
     return P3MAZE_OK;
 }
 

@@ -72,7 +72,8 @@ class Tuning(C.Structure):
     _fields_ = [("predictor", C.c_int32), ("pre_sweeps", C.c_int32), ("post_sweeps", C.c_int32),
                 ("diffusion_zc", C.c_int32), ("diffusion_fuse", C.c_int32),
                 ("pair_fork", C.c_int32), ("coarse_max", C.c_int32),
-                ("pair_blocks", C.c_int32), ("cluster_ctas", C.c_int32), ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
+                ("pair_blocks", C.c_int32), ("cluster_ctas", C.c_int32), ("sweep_fuse", C.c_int32),
+                ("ms_per_step", C.c_double), ("initial_ms_per_step", C.c_double),
                 ("trials", C.c_int32), ("steps", C.c_int32)]
 
 

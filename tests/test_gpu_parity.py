@@ -573,6 +573,32 @@ def test_two_step_diffusion_kernel_matches_oracle(P, nacl512, mesh, zc):
         assert rel_rms(ctx.forces(), ref["F"]) < 1e-4
 
 
+@pytest.mark.parametrize("mesh, coarse, pre, post", [(32, 16, 1, 2), (32, 16, 2, 1), (64, 16, 3, 3),
+                                                    (64, 16, 2, 2), (48, 16, 1, 3), (40, 64, 2, 2)])
+def test_fused_red_black_sweeps_equal_half_sweeps(P, nacl512, mesh, coarse, pre, post):
+    """Mixed mode: red-black sweeps after the first as one-launch out-of-place
+    full sweeps in pairs (an odd one as two in-place half sweeps) give the same
+    bits as two half-sweep launches per sweep, on every level of a 2- or
+    3-level hierarchy (48^3: levels 48, 24; 40^3: its own exact coarse level,
+    no sweeps at all)."""
+    kw = dict(precision="mixed", tol=1e-8, mesh=mesh)
+    with _ctx(P, nacl512, **kw) as a, _ctx(P, nacl512, **kw) as b:
+        for c, f in ((a, 1), (b, 0)):
+            c.set_tuning(coarse_max=coarse, pre_sweeps=pre, post_sweeps=post, sweep_fuse=f)
+            assert c.tuning()["sweep_fuse"] == f
+            c.reinit()
+            c.step(4)
+        np.testing.assert_array_equal(a.mesh("phi"), b.mesh("phi"))
+        np.testing.assert_array_equal(a.forces(), b.forces())
+        np.testing.assert_array_equal(a.positions(), b.positions())
+        assert a.stats()["total_iters"] == b.stats()["total_iters"]
+        ref = oracle_full(nacl512, a.positions(), 0.30, 9.0, mesh)
+        assert rel_rms(a.forces(), ref["F"]) < 1e-4
+    with _ctx(P, nacl512, **kw) as c:
+        with pytest.raises(P.P3MaZeError, match="out of range"):
+            c.set_tuning(sweep_fuse=2)
+
+
 @pytest.mark.parametrize("mesh, fuse, zc", [(32, 4, 8), (32, 3, 16), (24, 4, 4), (20, 4, 32), (16, 3, 4),
                                            (64, 4, 16), (18, 4, 8)])
 def test_temporal_blocking_matches_single_steps(P, nacl512, mesh, fuse, zc):
