@@ -481,7 +481,7 @@ def run_ours(args) -> int:
         ctx.set_tuning(**json.loads(args.tuning))
         tuning = dict(ctx.tuning(), source="--tuning")
     else:
-        tuning = None if args.no_tune else ctx.autotune(12)
+        tuning = None if args.no_tune else ctx.autotune(40)
     # the warm-up steps again with the final setting: a setting change drops
     # the step graphs, and these steps record them (one per pointer phase of
     # the field and correction rings) outside the timed region
@@ -827,7 +827,7 @@ def run_sweep(args) -> int:
                 ctx.set_tuning(**json.loads(args.tuning))
                 tuning = dict(ctx.tuning(), source="--tuning")
             else:
-                tuning = ctx.autotune(4)
+                tuning = ctx.autotune(12)
             ctx.step(max(args.warmup, 4))  # record the step graphs of the final setting untimed
             ctx.set_timing(True)
             it0 = ctx.stats()["total_iters"]

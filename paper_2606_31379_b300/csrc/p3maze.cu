@@ -43,8 +43,10 @@ struct Level {
     void* t = nullptr;
     // FP32 levels with N % 4 == 0 that sweep: the other buffer of the
     // out-of-place full sweeps (level 0: the smoothing ping-pong buffer, free
-    // during the solve)
+    // during the solve), and the buffer (e or e2) that holds the level's
+    // correction when its V-cycle ends (set when the V-cycle is launched)
     void* e2 = nullptr;
+    void* fin = nullptr;
 };
 
 // One captured MD step for a given pointer phase of the field rings.
@@ -633,6 +635,7 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
         CK(go(k_coarse_z<T>, gc, bc, sm, L.n, (T*)L.t, (const T*)L.H, (const T*)L.D));
         CK(go(k_coarse_xy<T>, gc, bc, sm, L.n, (const T*)L.t, e, (const T*)L.H));
         count(ctx, P3MAZE_ST_SOLVE, 3);
+        L.fin = e;
         return P3MAZE_OK;
     }
     Level& C = ctx->lev[l + 1];
@@ -643,36 +646,30 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
     // FP32 levels with N % 4 == 0 take the four-points-per-thread kernels
     const bool quads = sizeof(T) == 4 && L.n % 4 == 0;
     int launches = 0;
-    // `count` full red-black sweeps, colour pa first.  FP32 quad levels run
-    // them in pairs of out-of-place full sweeps (e -> e2 -> e) so that the
-    // result lands in e; an odd one first as the two in-place half sweeps.
+    // cur: the buffer holding the level's correction.  `count` full red-black
+    // sweeps, colour pa first: on FP32 quad levels one out-of-place launch per
+    // sweep (cur -> the other buffer), else two in-place half sweeps.
+    T* cur = e;
     auto sweeps = [&](int count, int pa) -> int {
         const bool pairs = quads && ctx->sweep_fuse && L.e2;
-        int done = 0;
-        if (!pairs || (count & 1)) {
-            const int halves = pairs ? 1 : count;
-            for (int k = 0; k < halves; ++k) {
-                CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, pa, 0));
-                CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, e, (const T*)b, 1 - pa, 0));
+        for (int k = 0; k < count; ++k) {
+            if (!pairs) {
+                CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, cur, (const T*)b, pa, 0));
+                CK(go(k_rbgs<T>, g3h(L.n), kB3, 0, L.n, cur, (const T*)b, 1 - pa, 0));
                 launches += 2;
+                continue;
             }
-            done = halves;
-        }
-        if constexpr (sizeof(T) == 4) {
-            const int zc = L.n >= 128 ? 4 : 2;
-            const dim3 g((L.n / 4 + P3_BX - 3) / (P3_BX - 2), (L.n + P3_BY - 1) / P3_BY, (L.n + zc - 1) / zc);
-            float* const e1 = (float*)e;
-            float* const e2 = (float*)L.e2;
-            for (; done < count; done += 2) {
-                for (int h = 0; h < 2; ++h) {
-                    const float* src = h ? e2 : e1;
-                    float* dst = h ? e1 : e2;
-                    if (pa == 0 && zc == 4) CK(go(k_rbgs_pair4<0, 4>, g, kB3, 0, L.n, src, dst, (const float*)b));
-                    else if (pa == 0) CK(go(k_rbgs_pair4<0, 2>, g, kB3, 0, L.n, src, dst, (const float*)b));
-                    else if (zc == 4) CK(go(k_rbgs_pair4<1, 4>, g, kB3, 0, L.n, src, dst, (const float*)b));
-                    else CK(go(k_rbgs_pair4<1, 2>, g, kB3, 0, L.n, src, dst, (const float*)b));
-                    launches += 1;
-                }
+            if constexpr (sizeof(T) == 4) {
+                const int zc = L.n >= 128 ? 4 : 2;
+                const dim3 g((L.n / 4 + P3_BX - 3) / (P3_BX - 2), (L.n + P3_BY - 1) / P3_BY, (L.n + zc - 1) / zc);
+                const float* src = (const float*)cur;
+                float* dst = (float*)(cur == e ? (T*)L.e2 : e);
+                if (pa == 0 && zc == 4) CK(go(k_rbgs_pair4<0, 4>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                else if (pa == 0) CK(go(k_rbgs_pair4<0, 2>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                else if (zc == 4) CK(go(k_rbgs_pair4<1, 4>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                else CK(go(k_rbgs_pair4<1, 2>, g, kB3, 0, L.n, src, dst, (const float*)b));
+                cur = (T*)dst;
+                launches += 1;
             }
         }
         return P3MAZE_OK;
@@ -701,26 +698,28 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
         }
     }
     if (C.n >= 128)
-        CK(go(k_resid_restrict_z<T, 4>, gz(C.n, 4), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
+        CK(go(k_resid_restrict_z<T, 4>, gz(C.n, 4), kB3, 0, C.n, (const T*)cur, (const T*)b, (T*)C.b));
     else
-        CK(go(k_resid_restrict_z<T, 2>, gz(C.n, 2), kB3, 0, C.n, (const T*)e, (const T*)b, (T*)C.b));
+        CK(go(k_resid_restrict_z<T, 2>, gz(C.n, 2), kB3, 0, C.n, (const T*)cur, (const T*)b, (T*)C.b));
     count(ctx, P3MAZE_ST_SOLVE, launches + 1);
     launches = 0;
     int rc = vcycle<T>(ctx, l + 1, true);
     if (rc) return rc;
+    const T* ec = (const T*)C.fin;  // the coarse correction, wherever its V-cycle left it
     if constexpr (sizeof(T) == 4) {
         if (quads) {
             const dim3 g((L.n / 4 + P3_BX - 1) / P3_BX, (L.n + P3_BY - 1) / P3_BY, L.n / 2);
-            CK(go(k_prolong_add4, g, kB3, 0, L.n, (const float*)C.e, (float*)e));
+            CK(go(k_prolong_add4, g, kB3, 0, L.n, (const float*)ec, (float*)cur));
         } else {
-            CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
+            CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, ec, cur));
         }
     } else {
-        CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, (const T*)C.e, e));
+        CK(go(k_prolong_add<T>, g3(L.n), kB3, 0, L.n, ec, cur));
     }
     rc = sweeps(ctx->nu2, 1);
     if (rc) return rc;
     count(ctx, P3MAZE_ST_SOLVE, 1 + launches);
+    L.fin = cur;
     return P3MAZE_OK;
 }
 
@@ -751,12 +750,12 @@ int launch_iteration(p3maze_ctx* ctx, cudaGraphConditionalHandle h, int use_hand
     if (ctx->prec == P3MAZE_MIXED) {
         // the increments' sum goes to slot P of the correction (gauge mode)
         CK(launch_maybe_pdl(ctx->pdl, k_resid_update_fix, resid_grid(ctx->N), kB3, 0, ctx->stream, ctx->N,
-                            fx(ctx->yh[0]), (const float*)ctx->lev[0].e, fx(ctx->rfin), (float*)ctx->lev[0].b,
+                            fx(ctx->yh[0]), (const float*)ctx->lev[0].fin, fx(ctx->rfin), (float*)ctx->lev[0].b,
                             check_args(ctx, h, use_handle, ctx->yh[0] + ctx->P)));
         count(ctx, P3MAZE_ST_SOLVE);
     } else {
         k_add_correction<T><<<nblk(ctx->P), P3_THREADS, 0, ctx->stream>>>(ctx->P, ctx->yh[0],
-                                                                          (const T*)ctx->lev[0].e);
+                                                                          (const T*)ctx->lev[0].fin);
         count(ctx, P3MAZE_ST_SOLVE);
         launch_resid_check<T>(ctx, h, use_handle);
     }

@@ -577,10 +577,10 @@ def test_two_step_diffusion_kernel_matches_oracle(P, nacl512, mesh, zc):
                                                     (64, 16, 2, 2), (48, 16, 1, 3), (40, 64, 2, 2)])
 def test_fused_red_black_sweeps_equal_half_sweeps(P, nacl512, mesh, coarse, pre, post):
     """Mixed mode: red-black sweeps after the first as one-launch out-of-place
-    full sweeps in pairs (an odd one as two in-place half sweeps) give the same
-    bits as two half-sweep launches per sweep, on every level of a 2- or
-    3-level hierarchy (48^3: levels 48, 24; 40^3: its own exact coarse level,
-    no sweeps at all)."""
+    full sweeps (the correction alternating between two buffers, odd and even
+    counts) give the same bits as two in-place half-sweep launches per sweep,
+    on every level of a 2- or 3-level hierarchy (48^3: levels 48, 24; 40^3:
+    its own exact coarse level, no sweeps at all)."""
     kw = dict(precision="mixed", tol=1e-8, mesh=mesh)
     with _ctx(P, nacl512, **kw) as a, _ctx(P, nacl512, **kw) as b:
         for c, f in ((a, 1), (b, 0)):
