@@ -246,10 +246,12 @@ typedef struct {
                                    context stepped alone, and in a per-member batch the
                                    largest that keeps the batch's launch within one CTA
                                    per SM.  Ignored by the other modes.                      */
-    int32_t sweep_fuse;         /* 1 (default): on FP32 levels with N % 4 == 0 every red-black
-                                   sweep after the first is one out-of-place launch (the
-                                   correction alternates between two buffers); 0: two
-                                   in-place half sweeps per sweep.  The same bits either way. */
+    int32_t sweep_fuse;         /* 1 (default): on FP32 levels of at most 64^3 with N % 4 == 0
+                                   every red-black sweep after the first is one out-of-place
+                                   launch (the correction alternates between two buffers;
+                                   larger levels, where it is slower, keep the half sweeps);
+                                   0: two in-place half sweeps per sweep everywhere.  The
+                                   same bits either way.                                     */
     double ms_per_step;         /* measured with the chosen setting                    */
     double initial_ms_per_step; /* measured with the setting in use before tuning      */
     int32_t trials;             /* settings timed                                      */
