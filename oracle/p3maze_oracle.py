@@ -362,7 +362,7 @@ def shift_force(pair_fn, r, r_cut, *args):
 
 def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
               subset: np.ndarray | None = None, coulomb: bool = True, vdw: bool = True,
-              shift: str = "none"):
+              shift: str = "none", virial: bool = False):
     """Short-range forces and per-particle energies by explicit summation over
     every particle j and every periodic image within R_c (Eq. 19 plus the
     non-Coulomb term).  Pairs inside one molecule (nearest image) are skipped.
@@ -370,7 +370,10 @@ def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
     term; 'none' truncates at R_c.
 
     Returns (F (m,3), e_coul (m,), e_vdw (m,)) for the particles in `subset`
-    (default all); per-particle energies carry the factor 1/2 of Eq. 5."""
+    (default all); per-particle energies carry the factor 1/2 of Eq. 5.  With
+    virial=True also w (m,): half of sum_j r_ij . F_ij over the particle's
+    pairs (r_ij = r_i - r_j, F_ij the pair force on i), so that w.sum() is the
+    short-range pair virial sum_{i<j} r_ij . F_ij."""
     if shift not in ("none", "force"):
         raise ValueError(shift)
 
@@ -384,6 +387,7 @@ def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
     F = np.zeros((idx.size, 3))
     ec = np.zeros(idx.size)
     ev = np.zeros(idx.size)
+    w = np.zeros(idx.size)
     for row, i in enumerate(idx):
         d0 = pos[i][None, :] - pos                      # r_i - r_j
         for s in shifts:
@@ -426,6 +430,9 @@ def sr_forces(system, sigma: float, r_cut: float, ke: float = COULOMB_K,
                     ev[row] += 0.5 * e.sum()
                     fr[live] += f
             F[row] += (fr[:, None] * dj).sum(0)
+            w[row] += 0.5 * (fr * r * r).sum()              # r_ij . F_ij = (F/r) r^2
+    if virial:
+        return F, ec, ev, w
     return F, ec, ev
 
 
@@ -645,12 +652,13 @@ def forces_and_energies(system, alpha: float, r_cut: float, n: int, ke: float = 
         F_lr = interpolate_lr_forces_analytic(system.pos, system.charge, system.box, n, mf["phi"], ke)
     else:
         F_lr = interpolate_lr_forces(system.pos, system.charge, system.box, n, mf["phi"], ke)
-    F_sr, ec, ev = sr_forces(system, sigma, r_cut, ke, shift=sr_shift)
+    F_sr, ec, ev, w = sr_forces(system, sigma, r_cut, ke, shift=sr_shift, virial=True)
     src = mf["q"] if lr_energy == "assigned" else mf["qs"]
     v_lr = 0.5 * ke * float((mf["phi"] * src).sum())
     out = {
         "F_lr": F_lr, "F_sr": F_sr, "F": F_lr + F_sr,
         "v_sr": float(ec.sum()), "v_vdw": float(ev.sum()), "v_lr": v_lr,
+        "w_sr": float(w.sum()),
         "v_self": self_energy(system.charge, sigma, ke),
         "fields": mf,
     }

@@ -209,6 +209,43 @@ def test_sr_forces_are_minus_gradient_of_sr_energy():
     _fd_check(s, energy, F)
 
 
+def test_sr_virial_is_the_scaling_derivative_of_the_sr_energy():
+    """The short-range pair virial W = sum_{i<j} r_ij . F_ij.  For one pair it
+    is -r dU/dr, with dU/dr by a central difference of the pair energy.  For
+    a melt with the shifted-force cutoff (energy and force continuous at R_c)
+    it is -dV/dlambda at lambda = 1, every position and the box scaled by
+    lambda.  A wrong sign, a lost factor 1/2 (the double count) or a missing
+    term fails both."""
+    import dataclasses
+    sigma = O.sigma_of_alpha(0.30)
+    rc = 9.0
+    pair = S.nacl_melt(2, 30.0, seed=0)
+    r0 = 3.1
+
+    def u(r):
+        sys_ = dataclasses.replace(pair, pos=np.array([[5.0, 5.0, 5.0], [5.0 + r, 5.0, 5.0]]))
+        _, ec, ev = O.sr_forces(sys_, sigma, rc)
+        return ec.sum() + ev.sum()
+
+    one = dataclasses.replace(pair, pos=np.array([[5.0, 5.0, 5.0], [5.0 + r0, 5.0, 5.0]]))
+    _, _, _, w = O.sr_forces(one, sigma, rc, virial=True)
+    dudr = (u(r0 + 1e-5) - u(r0 - 1e-5)) / 2e-5
+    assert w.sum() == pytest.approx(-r0 * dudr, rel=1e-7)
+    assert w[0] == pytest.approx(w[1], rel=1e-12)           # each particle carries half
+    m = S.nacl_melt(24, 11.0, seed=3, dmin=2.0)
+
+    def v(lam):
+        sys_ = dataclasses.replace(m, pos=m.pos * lam, box=m.box * lam)
+        _, ec, ev = O.sr_forces(sys_, sigma, rc, shift="force")
+        return ec.sum() + ev.sum()
+
+    _, _, _, w = O.sr_forces(m, sigma, rc, shift="force", virial=True)
+    dv = (v(1.0 + 1e-6) - v(1.0 - 1e-6)) / 2e-6
+    assert w.sum() == pytest.approx(-dv, rel=1e-6)
+    ref = O.forces_and_energies(m, 0.30, rc, 16, sr_shift="force")
+    assert ref["w_sr"] == pytest.approx(w.sum(), rel=1e-12)
+
+
 def test_lj_pair_closed_form_zero_minimum_and_force():
     """Lennard-Jones (SPC/Fw O-O term, Table S1): U(sigma) = 0, the minimum sits
     at r = 2^(1/6) sigma with depth -eps (textbook values), and the returned
