@@ -185,6 +185,8 @@ typedef struct {
     double v_bond;      /* bonds + angles                                                  */
     double kinetic;
     double total;
+    double w_sr;        /* short-range pair virial sum_{i<j} r_ij . F_ij of the erfc and
+                           non-Coulomb pair terms (kcal/mol; not part of total)          */
 } p3maze_energies;
 
 typedef struct {

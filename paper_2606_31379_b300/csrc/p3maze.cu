@@ -28,7 +28,7 @@ constexpr int kMaxGraphs = 4;       // pointer phases of the phi (2) and y (4) r
 constexpr int kMaxStepGraphs = 2 * kMaxGraphs + 1;  // whole steps, tails (per phase) and one head
 
 // Device scalar slots.
-enum { S_QSUM = 0, S_ESR, S_EVDW, S_VLR, S_MV2, S_EBOND, S_EXCL, S_NSCAL };
+enum { S_QSUM = 0, S_ESR, S_EVDW, S_VLR, S_MV2, S_EBOND, S_EXCL, S_WSR, S_NSCAL };
 
 struct Level {
     int n = 0;
@@ -129,7 +129,7 @@ struct p3maze_ctx {
     PQ* xl64 = nullptr;
     float4* xl32 = nullptr;
     MeshPt* mp = nullptr;                 // mixed mode: mesh coordinates in cell order
-    double *Fs = nullptr, *ecs = nullptr, *evs = nullptr, *eb = nullptr, *ex = nullptr;
+    double *Fs = nullptr, *ecs = nullptr, *evs = nullptr, *wsr = nullptr, *eb = nullptr, *ex = nullptr;
     // mesh
     void *q = nullptr, *qs = nullptr;
     double* phi[2] = {nullptr, nullptr};
@@ -911,11 +911,11 @@ int pair_forces(p3maze_ctx* ctx) {
         if (mixed)                                                                                      \
             k_pair<KIND, float, 768, MOL, SH><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl32, ctx->ts,    \
                 ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke_pair,  \
-                ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
+                ctx->tab, ctx->Fs, ctx->ecs, ctx->evs, ctx->wsr);                                       \
         else                                                                                            \
             k_pair<KIND, double, 512, MOL, SH><<<pb, P3_THREADS, 0, s>>>(ctx->np, ctx->xl64, ctx->ts,   \
                 ctx->ms, ctx->start, ctx->nc, nbox, ctx->lcell, rc2, halfL2, ctx->alpha, ctx->ke_pair,  \
-                ctx->tab, ctx->Fs, ctx->ecs, ctx->evs);                                                 \
+                ctx->tab, ctx->Fs, ctx->ecs, ctx->evs, ctx->wsr);                                       \
     } while (0)
 #define PAIR(KIND, MOL)                       \
     do {                                      \
@@ -1356,6 +1356,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     ALLOC(ctx->Fs, 24 * (size_t)n);
     ALLOC(ctx->ecs, 8 * (size_t)n);
     ALLOC(ctx->evs, 8 * (size_t)n);
+    ALLOC(ctx->wsr, 8 * (size_t)n);
     ALLOC(ctx->count, 4 * (size_t)ctx->ncell);
     ALLOC(ctx->fill, 4 * (size_t)ctx->ncell);
     ALLOC(ctx->start, 4 * ((size_t)ctx->ncell + 1));
@@ -1539,7 +1540,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     for (int k = 0; k < 5; ++k) b += a(4 * n);           // cell order ts ms cs
     b += a(32 * n) + a(32 * n) + a(16 * n);              // xq xl64 xl32
     if (mixed) b += a(sizeof(MeshPt) * n);               // mp
-    b += a(24 * n) + a(8 * n) + a(8 * n);                // Fs ecs evs
+    b += a(24 * n) + a(8 * n) + a(8 * n) + a(8 * n);     // Fs ecs evs wsr
     b += a(4 * ncell) + a(4 * ncell) + a(4 * (ncell + 1));
     if (p->types) b += a(4 * n);
     b += a(tb * P) + a(tb * P);                          // q qs
@@ -1883,6 +1884,8 @@ int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
     k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_ESR);
     k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->evs, ctx->partial);
     k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_EVDW);
+    k_sum_partial<double><<<nb, P3_THREADS, 0, s>>>(ctx->np, ctx->wsr, ctx->partial);
+    k_sum_final<<<1, P3_THREADS, 0, s>>>(nb, ctx->partial, ctx->dscal + S_WSR);
     if (ctx->prec == P3MAZE_MIXED)
         k_dot_partial_fix<float><<<nb, P3_THREADS, 0, s>>>(ctx->P, fx(ctx->phi[ctx->icur]), (const float*)ctx->q,
                                                            ctx->partial);
@@ -1909,6 +1912,7 @@ int p3maze_energy(p3maze_ctx* ctx, p3maze_energies* out) {
     out->v_excl = ctx->nmol ? h[S_EXCL] : 0.0;
     out->kinetic = 0.5 * h[S_MV2] / P3_ACCEL;
     out->total = out->v_sr + out->v_lr + out->v_self + out->v_excl + out->v_vdw + out->v_bond + out->kinetic;
+    out->w_sr = h[S_WSR];
     return P3MAZE_OK;
 }
 
@@ -1974,7 +1978,7 @@ void state_segments(p3maze_ctx* ctx, std::vector<std::pair<void*, size_t>>& seg)
     const size_t n3 = 24 * (size_t)ctx->np, n1 = 8 * (size_t)ctx->np, P8 = 8 * (size_t)ctx->P;
     const size_t tb = ctx->prec == P3MAZE_MIXED ? 4 : 8;
     seg = {{ctx->r, n3},   {ctx->v, n3},   {ctx->F, n3},   {ctx->Fsr, n3}, {ctx->Flr, n3}, {ctx->Fb, n3},
-           {ctx->ecs, n1}, {ctx->evs, n1}, {ctx->q, tb * (size_t)ctx->P},
+           {ctx->ecs, n1}, {ctx->evs, n1}, {ctx->wsr, n1}, {ctx->q, tb * (size_t)ctx->P},
            {ctx->phi[ctx->icur], P8}, {ctx->phi[1 - ctx->icur], P8},
            {ctx->psi[ctx->icur], P8}, {ctx->psi[1 - ctx->icur], P8},
            {ctx->yh[1], P8 + 8}, {ctx->yh[2], P8 + 8}, {ctx->yh[3], P8 + 8},
@@ -2011,7 +2015,7 @@ int p3maze_save_state(p3maze_ctx* ctx, void* buf, size_t bytes) {
     CK(cudaStreamSynchronize(ctx->stream));
     StateHeader h{};
     std::memcpy(h.magic, "P3MZSTAT", 8);
-    h.version = 1;
+    h.version = 2;
     h.np = ctx->np;
     h.mesh = ctx->N;
     h.precision = ctx->prec;
@@ -2038,7 +2042,7 @@ int p3maze_load_state(p3maze_ctx* ctx, const void* buf, size_t bytes) {
     if (bytes < state_size(ctx)) return fail(ctx, P3MAZE_ERR_INVALID, "buffer smaller than p3maze_state_bytes");
     StateHeader h{};
     std::memcpy(&h, buf, sizeof h);
-    if (std::memcmp(h.magic, "P3MZSTAT", 8) || h.version != 1 || h.np != ctx->np || h.mesh != ctx->N ||
+    if (std::memcmp(h.magic, "P3MZSTAT", 8) || h.version != 2 || h.np != ctx->np || h.mesh != ctx->N ||
         h.precision != ctx->prec || h.method != ctx->method || h.nmol != ctx->nmol)
         return fail(ctx, P3MAZE_ERR_INVALID, "state was saved from a context with other parameters");
     int rc = enter(ctx);

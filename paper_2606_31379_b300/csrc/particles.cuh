@@ -389,7 +389,8 @@ __device__ __forceinline__ R pair_terms(R r2, R qq, R alpha, const PairPar<R>& p
 // time and compacts those inside the cutoff into a per-warp queue
 // (__ballot_sync), so the pair functions run with every lane on a real pair.
 // Pairs within one molecule closer than L/2 (the nearest image) are excluded.
-// Each particle's force and half of its pair energies are accumulated in the
+// Each particle's force and half of its pair energies and of its pair virial
+// (sum of r_ij . F_ij) are accumulated in the
 // arithmetic type in shared memory (FP32 sums of FP32 pair terms in mixed
 // mode) and written as FP64; no global atomics.  Regions larger than the staging
 // buffer are processed in chunks, home lists longer than 256 in passes.
@@ -399,7 +400,7 @@ template <> struct Vec4<double> { using type = PQ; };
 
 template <int KIND, bool SHIFT, typename R, typename V>
 __device__ __forceinline__ void pair_accumulate(const V& pi, const V& pj, R alpha, R ke, const PairPar<R>& pp,
-                                                const ShiftC<R>& sc, R& fx, R& fy, R& fz, R& ec, R& ev) {
+                                                const ShiftC<R>& sc, R& fx, R& fy, R& fz, R& ec, R& ev, R& w) {
     const R ddx = (R)pi.x - (R)pj.x;
     const R ddy = (R)pi.y - (R)pj.y;
     const R ddz = (R)pi.z - (R)pj.z;
@@ -412,6 +413,7 @@ __device__ __forceinline__ void pair_accumulate(const V& pi, const V& pj, R alph
     fz += f * ddz;
     ec += e_c;
     ev += e_v;
+    w += f * r2;  // r_ij . F_ij
 }
 
 // MOL: the system has molecules, so intramolecular pairs are tested for.
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(P3_THREADS)
 k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restrict__ ts,
        const int* __restrict__ ms, const int* __restrict__ start, int nc, int nbox, double lcell, double rc2,
        double halfL2, double alpha, double ke, SRTable tab, double* __restrict__ Fs,
-       double* __restrict__ ecs, double* __restrict__ evs) {
+       double* __restrict__ ecs, double* __restrict__ evs, double* __restrict__ wsr) {
     using V = typename Vec4<R>::type;
     constexpr int HCAP = 256;
     constexpr int NW = P3_THREADS / 32;
@@ -430,7 +432,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
     __shared__ int rstart[216], roff[217];
     __shared__ V hpos[HCAP];
     __shared__ unsigned hidx[HCAP];           // sorted index | home-cell offset bits 29..31
-    __shared__ R hacc[HCAP][5];               // per home particle: force, Coulomb and non-Coulomb energy
+    __shared__ R hacc[HCAP][6];               // per home particle: force, Coulomb and non-Coulomb energy, virial
     __shared__ int wq[NW][64];
     // per warp: the home particle's candidates (FP32: an explicit list of
     // chunk indices; FP64, whose staging leaves no room: kept rows' start and
@@ -527,7 +529,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                 q.y = (R)p.y + (R)((code >> 30) & 1u) * lc;
                 q.z = (R)p.z + (R)((code >> 31) & 1u) * lc;
                 hpos[k] = q;
-                for (int a = 0; a < 5; ++a) hacc[k][a] = (R)0;
+                for (int a = 0; a < 6; ++a) hacc[k][a] = (R)0;
             }
             for (int c0 = 0; c0 < total; c0 += CAP) {
                 const int cn = min(CAP, total - c0);
@@ -560,7 +562,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                     const V pi = hpos[h];
                     const int prow = ts[hs] * tab.nt;
                     const int mi = ms[hs];
-                    R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0;
+                    R fx = 0, fy = 0, fz = 0, ec = 0, ev = 0, wv = 0;
                     // Candidate ranges of this home particle within the chunk:
                     // lane l < 25 takes the cell row (dy, dz) = (l % 5 - 2, l / 5 - 2)
                     // of its own 5x5x5 neighbourhood, drops it if its (y, z) gap
@@ -641,7 +643,8 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                         __syncwarp();
                         if (qn >= 32) {
                             const int kk = wq[warp][lane];
-                            pair_accumulate<KIND, SHIFT, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], sc, fx, fy, fz, ec, ev);
+                            pair_accumulate<KIND, SHIFT, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], sc, fx, fy, fz, ec, ev,
+                                                               wv);
                             __syncwarp();
                             if (lane < qn - 32) wq[warp][lane] = wq[warp][32 + lane];
                             __syncwarp();
@@ -650,7 +653,8 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                     }
                     if (lane < qn) {
                         const int kk = wq[warp][lane];
-                        pair_accumulate<KIND, SHIFT, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], sc, fx, fy, fz, ec, ev);
+                        pair_accumulate<KIND, SHIFT, R, V>(pi, sp[kk], alr, ker, spar[prow + styp[kk]], sc, fx, fy, fz, ec, ev,
+                                                               wv);
                     }
                     __syncwarp();
                     // lane partials (a few pairs each) are reduced and accumulated
@@ -663,6 +667,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                         fz += __shfl_xor_sync(0xffffffffu, fz, w);
                         ec += __shfl_xor_sync(0xffffffffu, ec, w);
                         ev += __shfl_xor_sync(0xffffffffu, ev, w);
+                        wv += __shfl_xor_sync(0xffffffffu, wv, w);
                     }
                     if (lane == 0) {
                         hacc[h][0] += fx;
@@ -670,6 +675,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                         hacc[h][2] += fz;
                         hacc[h][3] += ec;
                         hacc[h][4] += ev;
+                        hacc[h][5] += wv;
                     }
                 }
             }
@@ -681,6 +687,7 @@ k_pair(int n, const typename Vec4<R>::type* __restrict__ xl, const int* __restri
                 Fs[3 * hs + 2] = (double)hacc[k][2];
                 ecs[hs] = 0.5 * ke * (double)hacc[k][3];
                 evs[hs] = 0.5 * (double)hacc[k][4];
+                wsr[hs] = 0.5 * (double)hacc[k][5];
             }
             __syncthreads();
         }

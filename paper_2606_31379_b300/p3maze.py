@@ -49,7 +49,7 @@ class Params(C.Structure):
 
 class Energies(C.Structure):
     _fields_ = [(k, C.c_double) for k in
-                ("v_sr", "v_lr", "v_self", "v_excl", "v_vdw", "v_bond", "kinetic", "total")]
+                ("v_sr", "v_lr", "v_self", "v_excl", "v_vdw", "v_bond", "kinetic", "total", "w_sr")]
 
 
 class Stats(C.Structure):

@@ -74,7 +74,7 @@ def test_init_forces_and_energies_match_oracle(P, nacl512, precision, ftol):
         np.testing.assert_allclose(ctx.forces("sr") + ctx.forces("lr"), F, rtol=0, atol=1e-9 * np.abs(F).max())
         e = ctx.energy()
         etol = 1e-9 if precision == "fp64" else 1e-5
-        for k in ("v_sr", "v_self", "v_vdw"):
+        for k in ("v_sr", "v_self", "v_vdw", "w_sr"):  # w_sr: the short-range pair virial
             assert e[k] == pytest.approx(ref[k], rel=etol, abs=1e-9), k
         # V_LR = 1/2 phi^T q is first order in the field error: a residual of
         # tol = 1e-10 against |q^s| ~ 1e-3 allows ~1e-7 relative
@@ -275,6 +275,7 @@ def test_shifted_force_cutoff_matches_oracle(P, nacl512, precision, ftol):
         etol = 1e-9 if precision == "fp64" else 1e-5
         assert e["v_sr"] == pytest.approx(ref["v_sr"], rel=etol)
         assert e["v_vdw"] == pytest.approx(ref["v_vdw"], rel=etol)
+        assert e["w_sr"] == pytest.approx(ref["w_sr"], rel=etol)
     w = S.spcfw_water(64, 12.42, seed=3)
     with P.Context.from_system(w, alpha=0.30, r_cut=6.0, mesh=16, tol=1e-9, dt=0.5, precision=precision,
                                sr_shift="force") as ctx:
@@ -282,7 +283,9 @@ def test_shifted_force_cutoff_matches_oracle(P, nacl512, precision, ftol):
         pos = ctx.positions()
         ref = O.forces_and_energies(at_positions(w, pos), 0.30, 6.0, 16, sr_shift="force")
         assert rel_rms(ctx.forces(), ref["F"]) < ftol
-        assert ctx.energy()["v_vdw"] == pytest.approx(ref["v_vdw"], rel=1e-9 if precision == "fp64" else 1e-5)
+        ew = ctx.energy()
+        for k in ("v_vdw", "w_sr"):
+            assert ew[k] == pytest.approx(ref[k], rel=1e-9 if precision == "fp64" else 1e-5), k
 
 
 @pytest.mark.parametrize("mesh", [16, 20, 32, 48, 64])
