@@ -300,6 +300,25 @@ int p3maze_step_async(p3maze_ctx *ctx, int32_t nsteps);
 /* Wait for queued steps and report a recorded solver failure.                  */
 int p3maze_wait(p3maze_ctx *ctx);
 
+/* Rollback of failed steps (SURVEY-style recovery; off by default).
+ * enable = 1: the context keeps a device copy of its state (the segments of
+ * p3maze_save_state and the solver state; p3maze_state_bytes of extra device
+ * memory, not part of p3maze_device_bytes), taken by the first p3maze_step,
+ * p3maze_step_async or p3maze_step_host after the last wait.  When the steps
+ * of that call (or of the p3maze_step_async calls up to the p3maze_wait) end
+ * in NOT_CONVERGED, NONFINITE or INVALID (non-finite state copied in), the
+ * copy is put back before the error is returned: positions, velocities,
+ * forces, fields, multiplier history and step count are those before the
+ * failed steps, and the context can step again (e.g. after
+ * p3maze_set_solver).  p3maze_equilibrate and batch steps are not covered.
+ * enable = 0 frees the copy.  Errors: INVALID (NULL), OOM.                    */
+int p3maze_set_rollback(p3maze_ctx *ctx, int32_t enable);
+
+/* Change the constraint tolerance (e per mesh point, as params.tol) and the
+ * V-cycle limit of every later solve; recorded step graphs are dropped.
+ * Errors: INVALID (tol <= 0 or non-finite, max_mg_iters < 1).                 */
+int p3maze_set_solver(p3maze_ctx *ctx, double tol, int32_t max_mg_iters);
+
 /* One host round trip in one call, for drivers that keep the state on the
  * host: copy pos_in/vel_in (host [n][3], A and A/fs; either may be NULL to
  * keep the device copy) in as the continuing state (as p3maze_set_state:

@@ -109,6 +109,14 @@ struct p3maze_ctx {
     bool cluster_ok = false;             // the device runs this mesh's clusters of the smoothing kernel
     int cl_ctas = 0;                     // CTAs per cluster of mode 5 (0: automatic)
     int sweep_fuse = 1;                  // FP32 quad levels: a full red-black sweep per launch
+    // rollback (p3maze_set_rollback): a device copy of the state taken at the
+    // first step call after the last wait, restored when that call's steps fail
+    bool rollback = false;
+    void* snap = nullptr;
+    size_t snap_bytes = 0;
+    bool snap_taken = false;
+    int64_t snap_steps = 0;
+    int snap_nhist = 0;
     int64_t settings_gen = 0;            // bumped whenever a setting recorded in graphs changes
     double res_scale = 1.0;              // residual in the method's units: 1 (MaZe) or 4pi/h (P3M)
     double res_unit = 1.0;               // device residual per charge unit: 1 (FP64) or 4pi/h (mixed, fixed point)
@@ -1280,6 +1288,8 @@ void hartley_tables(int n, std::vector<double>& H, std::vector<double>& D) {
 
 void release(p3maze_ctx* ctx) {
     destroy_graphs(ctx);
+    if (ctx->snap) cudaFree(ctx->snap);
+    ctx->snap = nullptr;
     for (int st = 0; st < P3MAZE_NSTAGES; ++st)
         for (int k = 0; k < 2; ++k)
             if (ctx->ev[st][k]) cudaEventDestroy(ctx->ev[st][k]);
@@ -1768,6 +1778,101 @@ int init_impl(const p3maze_params* p, const double* pos, const double* vel, doub
     *out = ctx;
     return P3MAZE_OK;
 }
+
+struct StateHeader {
+    char magic[8];
+    int32_t version, np, mesh, precision, method, nmol;
+    int64_t steps;
+    int32_t nhist, pad;
+    MGState mg;
+};
+
+void state_segments(p3maze_ctx* ctx, std::vector<std::pair<void*, size_t>>& seg) {
+    const size_t n3 = 24 * (size_t)ctx->np, n1 = 8 * (size_t)ctx->np, P8 = 8 * (size_t)ctx->P;
+    const size_t tb = ctx->prec == P3MAZE_MIXED ? 4 : 8;
+    seg = {{ctx->r, n3},   {ctx->v, n3},   {ctx->F, n3},   {ctx->Fsr, n3}, {ctx->Flr, n3}, {ctx->Fb, n3},
+           {ctx->ecs, n1}, {ctx->evs, n1}, {ctx->wsr, n1}, {ctx->q, tb * (size_t)ctx->P},
+           {ctx->phi[ctx->icur], P8}, {ctx->phi[1 - ctx->icur], P8},
+           {ctx->psi[ctx->icur], P8}, {ctx->psi[1 - ctx->icur], P8},
+           {ctx->yh[1], P8 + 8}, {ctx->yh[2], P8 + 8}, {ctx->yh[3], P8 + 8},
+           {ctx->rfin, P8}, {ctx->dscal, 8 * (size_t)S_NSCAL}};
+    if (ctx->sig) seg.push_back({ctx->sig, P8});
+    if (ctx->phi32) seg.push_back({ctx->phi32, 4 * (size_t)ctx->P});
+    if (ctx->nmol) {
+        seg.push_back({ctx->eb, 8 * (size_t)ctx->nmol});
+        seg.push_back({ctx->ex, 8 * (size_t)ctx->nmol});
+    }
+}
+
+size_t state_size(p3maze_ctx* ctx) {
+    std::vector<std::pair<void*, size_t>> seg;
+    state_segments(ctx, seg);
+    size_t b = sizeof(StateHeader);
+    for (auto& s : seg) b += s.second;
+    return b;
+}
+
+// Device copy of the state (the checkpoint's segments and the solver state),
+// queued on the work stream; taken once until the next wait.
+int take_snapshot(p3maze_ctx* ctx) {
+    if (!ctx->rollback || ctx->snap_taken || !ctx->snap) return P3MAZE_OK;
+    std::vector<std::pair<void*, size_t>> seg;
+    state_segments(ctx, seg);
+    unsigned char* p = static_cast<unsigned char*>(ctx->snap);
+    for (auto& s : seg) {
+        CK(cudaMemcpyAsync(p, s.first, s.second, cudaMemcpyDeviceToDevice, ctx->stream));
+        p += s.second;
+    }
+    CK(cudaMemcpyAsync(p, ctx->dmg, sizeof(MGState), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->snap_steps = ctx->st.steps;
+    ctx->snap_nhist = ctx->nhist;
+    ctx->snap_taken = true;
+    return P3MAZE_OK;
+}
+
+// Put the snapshot back (the segments by their roles at the current pointer
+// phase, as p3maze_load_state does) and wait for it.
+int restore_snapshot(p3maze_ctx* ctx) {
+    std::vector<std::pair<void*, size_t>> seg;
+    state_segments(ctx, seg);
+    const unsigned char* p = static_cast<const unsigned char*>(ctx->snap);
+    for (auto& s : seg) {
+        CK(cudaMemcpyAsync(s.first, p, s.second, cudaMemcpyDeviceToDevice, ctx->stream));
+        p += s.second;
+    }
+    CK(cudaMemcpyAsync(ctx->hmg, p, sizeof(MGState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    MGState mg = *ctx->hmg;
+    mg.it = 0;
+    mg.cont = 0;
+    mg.arrive = 0;
+    mg.arrive_sum = 0;
+    *ctx->hmg = mg;
+    CK(cudaMemcpyAsync(ctx->dmg, ctx->hmg, sizeof(MGState), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->st.steps = ctx->snap_steps;
+    ctx->nhist = ctx->snap_nhist;
+    ctx->st.total_iters = mg.total_iters;
+    ctx->eager_iters = mg.total_iters;  // as after p3maze_load_state
+    ctx->graph_iters_seen = 0;
+    return P3MAZE_OK;
+}
+
+// The solver state of the queued steps; with rollback on, a failed call's
+// steps are undone.
+int finish_steps(p3maze_ctx* ctx) {
+    const int rc = read_solver_state(ctx);
+    const bool undo = rc && ctx->rollback && ctx->snap_taken &&
+                      (rc == P3MAZE_ERR_NOT_CONVERGED || rc == P3MAZE_ERR_NONFINITE || rc == P3MAZE_ERR_INVALID);
+    if (undo) {
+        const std::string msg = ctx->err;
+        const int rrc = restore_snapshot(ctx);
+        if (rrc) return rrc;
+        ctx->err = msg + " (state rolled back to before the failed steps)";
+    }
+    ctx->snap_taken = false;
+    return rc;
+}
 }  // namespace
 
 int p3maze_init(const p3maze_params* p, const double* pos, const double* vel, void* cuda_stream,
@@ -1789,6 +1894,8 @@ int p3maze_step_async(p3maze_ctx* ctx, int32_t nsteps) {
     if (nsteps < 0) return fail(ctx, P3MAZE_ERR_INVALID, "nsteps must be >= 0");
     int rc = enter(ctx);
     if (rc) return rc;
+    rc = take_snapshot(ctx);
+    if (rc) return rc;
     for (int k = 0; k < nsteps; ++k) {
         rc = step_once(ctx);
         if (rc) return rc;
@@ -1798,13 +1905,50 @@ int p3maze_step_async(p3maze_ctx* ctx, int32_t nsteps) {
 
 int p3maze_wait(p3maze_ctx* ctx) {
     if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
-    return read_solver_state(ctx);
+    return finish_steps(ctx);
 }
 
 int p3maze_step(p3maze_ctx* ctx, int32_t nsteps) {
     int rc = p3maze_step_async(ctx, nsteps);
     if (rc) return rc;
-    return read_solver_state(ctx);
+    return finish_steps(ctx);
+}
+
+int p3maze_set_rollback(p3maze_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->snap_taken = false;
+    if (!enable) {
+        if (ctx->snap) cudaFree(ctx->snap);
+        ctx->snap = nullptr;
+        ctx->snap_bytes = 0;
+        ctx->rollback = false;
+        return P3MAZE_OK;
+    }
+    if (!ctx->snap) {
+        const size_t bytes = state_size(ctx) - sizeof(StateHeader) + sizeof(MGState);
+        cudaError_t e = cudaMalloc(&ctx->snap, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->snap = nullptr;
+            return fail(ctx, P3MAZE_ERR_OOM, std::string("rollback copy: ") + cudaGetErrorString(e));
+        }
+        ctx->snap_bytes = bytes;
+    }
+    ctx->rollback = true;
+    return P3MAZE_OK;
+}
+
+int p3maze_set_solver(p3maze_ctx* ctx, double tol, int32_t max_mg_iters) {
+    if (!ctx) return fail(nullptr, P3MAZE_ERR_INVALID, "ctx is NULL");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(ctx, P3MAZE_ERR_INVALID, "tol must be > 0");
+    if (max_mg_iters < 1) return fail(ctx, P3MAZE_ERR_INVALID, "max_mg_iters must be >= 1");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tol = tol;
+    ctx->itmax = max_mg_iters;
+    destroy_graphs(ctx);  // the tolerance and the limit are recorded in the graphs
+    ctx->settings_gen += 1;
+    return P3MAZE_OK;
 }
 
 int p3maze_step_host(p3maze_ctx* ctx, const double* pos_in, const double* vel_in, int32_t nsteps, double* pos_out,
@@ -1814,6 +1958,8 @@ int p3maze_step_host(p3maze_ctx* ctx, const double* pos_in, const double* vel_in
     cudaStream_t s = ctx->stream;
     const size_t bytes = 24 * (size_t)ctx->np;
     int rc = enter(ctx);
+    if (rc) return rc;
+    rc = take_snapshot(ctx);
     if (rc) return rc;
     if (pos_in) CK(cudaMemcpyAsync(ctx->r, pos_in, bytes, cudaMemcpyHostToDevice, s));
     if (vel_in) CK(cudaMemcpyAsync(ctx->v, vel_in, bytes, cudaMemcpyHostToDevice, s));
@@ -1830,7 +1976,7 @@ int p3maze_step_host(p3maze_ctx* ctx, const double* pos_in, const double* vel_in
     if (vel_out) CK(cudaMemcpyAsync(vel_out, ctx->v, bytes, cudaMemcpyDeviceToHost, s));
     rc = leave(ctx);
     if (rc) return rc;
-    return read_solver_state(ctx);
+    return finish_steps(ctx);
 }
 
 int p3maze_equilibrate(p3maze_ctx* ctx, int32_t nsteps, double temperature_K) {
@@ -1965,40 +2111,6 @@ int p3maze_get_forces(p3maze_ctx* ctx, int32_t which, double* out) {
 // ---- checkpoint: every array the next step reads, plus the observables'
 // inputs, in a fixed order (the field and correction histories in logical
 // order, whatever the ring positions)
-namespace {
-struct StateHeader {
-    char magic[8];
-    int32_t version, np, mesh, precision, method, nmol;
-    int64_t steps;
-    int32_t nhist, pad;
-    MGState mg;
-};
-
-void state_segments(p3maze_ctx* ctx, std::vector<std::pair<void*, size_t>>& seg) {
-    const size_t n3 = 24 * (size_t)ctx->np, n1 = 8 * (size_t)ctx->np, P8 = 8 * (size_t)ctx->P;
-    const size_t tb = ctx->prec == P3MAZE_MIXED ? 4 : 8;
-    seg = {{ctx->r, n3},   {ctx->v, n3},   {ctx->F, n3},   {ctx->Fsr, n3}, {ctx->Flr, n3}, {ctx->Fb, n3},
-           {ctx->ecs, n1}, {ctx->evs, n1}, {ctx->wsr, n1}, {ctx->q, tb * (size_t)ctx->P},
-           {ctx->phi[ctx->icur], P8}, {ctx->phi[1 - ctx->icur], P8},
-           {ctx->psi[ctx->icur], P8}, {ctx->psi[1 - ctx->icur], P8},
-           {ctx->yh[1], P8 + 8}, {ctx->yh[2], P8 + 8}, {ctx->yh[3], P8 + 8},
-           {ctx->rfin, P8}, {ctx->dscal, 8 * (size_t)S_NSCAL}};
-    if (ctx->sig) seg.push_back({ctx->sig, P8});
-    if (ctx->phi32) seg.push_back({ctx->phi32, 4 * (size_t)ctx->P});
-    if (ctx->nmol) {
-        seg.push_back({ctx->eb, 8 * (size_t)ctx->nmol});
-        seg.push_back({ctx->ex, 8 * (size_t)ctx->nmol});
-    }
-}
-
-size_t state_size(p3maze_ctx* ctx) {
-    std::vector<std::pair<void*, size_t>> seg;
-    state_segments(ctx, seg);
-    size_t b = sizeof(StateHeader);
-    for (auto& s : seg) b += s.second;
-    return b;
-}
-}  // namespace
 
 int p3maze_state_bytes(p3maze_ctx* ctx, size_t* out) {
     if (!ctx || !out) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");

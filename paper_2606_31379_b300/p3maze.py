@@ -88,6 +88,8 @@ _sig = {
     "p3maze_step": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_step_async": (C.c_int, [_ctx, C.c_int32]),
     "p3maze_wait": (C.c_int, [_ctx]),
+    "p3maze_set_rollback": (C.c_int, [_ctx, C.c_int32]),
+    "p3maze_set_solver": (C.c_int, [_ctx, C.c_double, C.c_int32]),
     "p3maze_step_host": (C.c_int, [_ctx, _dp, _dp, C.c_int32, _dp, _dp]),
     "p3maze_set_tuning": (C.c_int, [_ctx, C.c_void_p]),
     "p3maze_init_device": (C.c_int, [C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_ctx)]),
@@ -312,6 +314,15 @@ class Context:
     def wait(self):
         """Wait for queued steps; raises on a recorded solver failure."""
         self._check(lib.p3maze_wait(self._h))
+
+    def set_rollback(self, enable: bool = True):
+        """Keep a device copy of the state so that steps ending in a solver
+        failure are undone before the error is raised."""
+        self._check(lib.p3maze_set_rollback(self._h, 1 if enable else 0))
+
+    def set_solver(self, tol: float, max_mg_iters: int):
+        """Constraint tolerance and V-cycle limit of later solves."""
+        self._check(lib.p3maze_set_solver(self._h, float(tol), int(max_mg_iters)))
 
     def equilibrate(self, nsteps: int, temperature: float):
         """nsteps MD steps with velocity rescaling to temperature (K) after each."""

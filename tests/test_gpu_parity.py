@@ -161,6 +161,49 @@ def test_non_convergence_is_reported(P, nacl512):
     assert "did not reach" in str(ei.value)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_failed_steps_roll_back_and_the_run_continues(P, nacl512, precision):
+    """With rollback on, steps that end in NOT_CONVERGED (a tolerance no
+    V-cycle budget reaches) are undone: positions, velocities, step count and
+    the later trajectory equal those of a context that never failed, bit for
+    bit.  Without rollback the failed steps stay applied."""
+    kw = dict(precision=precision, tol=1e-8)
+    with _ctx(P, nacl512, **kw) as a, _ctx(P, nacl512, **kw) as b, _ctx(P, nacl512, **kw) as c:
+        for x in (a, b, c):
+            x.step(5)
+        a.set_rollback(True)
+        r0, v0 = a.positions(), a.velocities()
+        msgs = []
+        for x in (a, c):
+            x.set_solver(1e-16, 2)
+            with pytest.raises(P.P3MaZeError) as ei:
+                x.step(3)
+            assert ei.value.code == P.ERR_NOT_CONVERGED
+            msgs.append(str(ei.value))
+            x.set_solver(1e-8, 50)
+        assert "rolled back" in msgs[0] and "rolled back" not in msgs[1]
+        np.testing.assert_array_equal(a.positions(), r0)
+        np.testing.assert_array_equal(a.velocities(), v0)
+        assert a.stats()["steps"] == 5 and c.stats()["steps"] == 8
+        assert np.abs(c.positions() - r0).max() > 0          # no rollback: the steps stay
+        # the same with queued steps, reported by wait()
+        a.set_solver(1e-16, 2)
+        a.step_async(2)
+        a.step_async(1)
+        with pytest.raises(P.P3MaZeError):
+            a.wait()
+        a.set_solver(1e-8, 50)
+        np.testing.assert_array_equal(a.positions(), r0)
+        a.step(6)
+        b.step(6)
+        np.testing.assert_array_equal(a.positions(), b.positions())
+        np.testing.assert_array_equal(a.forces(), b.forces())
+        assert a.stats()["steps"] == b.stats()["steps"] == 11
+        with pytest.raises(P.P3MaZeError):
+            a.set_solver(0.0, 10)
+        a.set_rollback(False)
+
+
 def test_momentum_conservation_on_gpu(P, nacl512):
     with _ctx(P, nacl512, tol=1e-11) as ctx:
         F = ctx.forces()
