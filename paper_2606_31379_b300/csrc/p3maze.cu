@@ -93,6 +93,11 @@ struct p3maze_ctx {
     cudaStream_t body_stream = nullptr;  // capture of the while-node body
     cudaStream_t pair_stream = nullptr;  // short-range forces, concurrent with the mesh pipeline
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // positions are final once the drift of a step has run: recorded there (a
+    // node of the step graphs) so that p3maze_step_host copies them out on
+    // copy_stream while the step's forces are formed
+    cudaEvent_t ev_drift = nullptr, ev_copied = nullptr;
+    cudaStream_t copy_stream = nullptr;
     // parameters
     int np = 0, N = 0, nc = 0, ncell = 0, prec = 0, pred = 3, itmax = 50, nu1 = 2, nu2 = 2, K = 0;
     int nmol = 0, nlev = 0, method = 0;
@@ -187,11 +192,15 @@ int fail(p3maze_ctx* c, int code, const std::string& msg) {
     return code;
 }
 
+// A failed runtime call also leaves the thread's last error set: it is
+// cleared, so that a later launch check does not report it again.
 #define CK(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError();                                                               \
             return fail(ctx, P3MAZE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                     \
     } while (0)
 
 #define CKL()                                                                                 \
@@ -1075,6 +1084,9 @@ int step_body(p3maze_ctx* ctx, int order) {
     count(ctx, P3MAZE_ST_INTEGRATE);
     stage_end(ctx, P3MAZE_ST_INTEGRATE);
     CKL();
+    // an event node of the step graph when capturing (an external record)
+    CK(ctx->capturing ? cudaEventRecordWithFlags(ctx->ev_drift, s, cudaEventRecordExternal)
+                      : cudaEventRecord(ctx->ev_drift, s));
     int rc = field_and_forces(ctx, order);
     if (rc) return rc;
     k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
@@ -1102,6 +1114,9 @@ int step_head(p3maze_ctx* ctx) {
     count(ctx, P3MAZE_ST_INTEGRATE);
     stage_end(ctx, P3MAZE_ST_INTEGRATE);
     CKL();
+    // an event node of the step graph when capturing (an external record)
+    CK(ctx->capturing ? cudaEventRecordWithFlags(ctx->ev_drift, s, cudaEventRecordExternal)
+                      : cudaEventRecord(ctx->ev_drift, s));
     int rc = build_cells(ctx);
     return rc ? rc : spread_assign<float>(ctx);
 }
@@ -1303,8 +1318,12 @@ void release(p3maze_ctx* ctx) {
     if (ctx->pair_stream) cudaStreamDestroy(ctx->pair_stream);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_drift) cudaEventDestroy(ctx->ev_drift);
+    if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     ctx->pair_stream = nullptr;
-    ctx->ev_fork = ctx->ev_join = nullptr;
+    ctx->copy_stream = nullptr;
+    ctx->ev_fork = ctx->ev_join = ctx->ev_drift = ctx->ev_copied = nullptr;
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -1339,6 +1358,9 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     CK(cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_drift, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
     // particle arrays
     if (d_pos) {
         ctx->r = d_pos;
@@ -1972,7 +1994,15 @@ int p3maze_step_host(p3maze_ctx* ctx, const double* pos_in, const double* vel_in
         rc = step_once(ctx);
         if (rc) return rc;
     }
-    if (pos_out) CK(cudaMemcpyAsync(pos_out, ctx->r, bytes, cudaMemcpyDeviceToHost, s));
+    if (pos_out && nsteps > 0) {
+        // the last step's positions, copied while its forces are formed
+        CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_drift, 0));
+        CK(cudaMemcpyAsync(pos_out, ctx->r, bytes, cudaMemcpyDeviceToHost, ctx->copy_stream));
+        CK(cudaEventRecord(ctx->ev_copied, ctx->copy_stream));
+        CK(cudaStreamWaitEvent(s, ctx->ev_copied, 0));
+    } else if (pos_out) {
+        CK(cudaMemcpyAsync(pos_out, ctx->r, bytes, cudaMemcpyDeviceToHost, s));
+    }
     if (vel_out) CK(cudaMemcpyAsync(vel_out, ctx->v, bytes, cudaMemcpyDeviceToHost, s));
     rc = leave(ctx);
     if (rc) return rc;
@@ -2609,8 +2639,10 @@ int bfail(p3maze_batch* b, int code, const std::string& msg) {
 #define BCK(call)                                                                              \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
+        if (e_ != cudaSuccess) {                                                               \
+            cudaGetLastError();                                                                \
             return bfail(b, P3MAZE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                      \
     } while (0)
 
 void batch_drop_graphs(p3maze_batch* b) {

@@ -501,10 +501,13 @@ def test_time_reversibility(P, nacl512, precision, xtol):
     assert np.abs(v2 + v0).max() < xtol          # A/fs: an error built up over >= 1 fs
 
 
-def test_step_host_matches_separate_calls(P, nacl512):
-    """p3maze_step_host (copy in, steps, copy out, one wait) gives the same
-    state as set_state + step + get on a twin context."""
-    with _ctx(P, nacl512, precision="fp64", tol=1e-10) as a, _ctx(P, nacl512, precision="fp64", tol=1e-10) as b:
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_host_matches_separate_calls(P, nacl512, precision):
+    """p3maze_step_host (copy in, steps, copy out -- the positions while the
+    last step's forces are formed -- one wait) gives the same state as
+    set_state + step + get on a twin context, bit for bit."""
+    with _ctx(P, nacl512, precision=precision, tol=1e-10) as a, \
+            _ctx(P, nacl512, precision=precision, tol=1e-10) as b:
         a.step(3)
         b.step(3)
         x, v = a.positions(), a.velocities()
@@ -513,12 +516,18 @@ def test_step_host_matches_separate_calls(P, nacl512):
         a.step(2)
         xo, vo = np.empty_like(x), np.empty_like(v)
         b.step_host(x, v, 2, xo, vo)
-        np.testing.assert_allclose(xo, a.positions(), rtol=0, atol=1e-9)
-        np.testing.assert_allclose(vo, a.velocities(), rtol=0, atol=1e-9)
+        np.testing.assert_array_equal(xo, a.positions())
+        np.testing.assert_array_equal(vo, a.velocities())
         # NULL inputs keep the device state; NULL outputs skip the copies
         b.step_host(None, None, 1, None, None)
         a.step(1)
-        np.testing.assert_allclose(b.positions(), a.positions(), rtol=0, atol=1e-9)
+        np.testing.assert_array_equal(b.positions(), a.positions())
+        # many steps in one call (graph replays), the copy-out after the last
+        for k in range(3):
+            b.step_host(None, None, 4, xo, vo)
+            a.step(4)
+            np.testing.assert_array_equal(xo, a.positions())
+            np.testing.assert_array_equal(vo, a.velocities())
 
 
 def test_step_host_flags_nonfinite_input(P, nacl512):
