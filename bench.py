@@ -677,11 +677,12 @@ def small_batch_bytes(mesh: int, n_atoms: int, iters: float) -> float:
 
 def batch_small_run(stream, peaks, members: int = 32, steps: int = 60, warmup: int = 6) -> dict:
     """Many small systems (16^3-64^3 meshes) advanced as one batch: system-
-    steps/s of six batch configurations -- one graph for the whole batch or
+    steps/s of eight batch configurations -- one graph for the whole batch or
     each member's own cached graphs, each with the smoothing of every member
     in one cluster launch per cluster size (cluster_fused), each member's
-    smoothing in its own cluster launch (cluster_own), or each member's own
-    per-step diffusion launches (per_step).  The same seeded members in every
+    smoothing in its own cluster launch (cluster_own), each member's own
+    per-step diffusion launches (per_step), or each member's smoothing in the
+    Hartley basis (spectral).  The same seeded members in every
     configuration."""
     import torch
     from paper_2606_31379_b300 import p3maze as P
@@ -699,15 +700,18 @@ def batch_small_run(stream, peaks, members: int = 32, steps: int = 60, warmup: i
                       "meshes": sorted({p["mesh"] for _, p in systems}), "precision": "mixed"}}
     ref_F = None
     for mode in ("shared", "per_member"):
-        for smoothing in ("cluster_fused", "cluster_own", "per_step"):
+        for smoothing in ("cluster_fused", "cluster_own", "per_step", "spectral"):
             ctxs = []
             batch = P.Batch(stream=stream.cuda_stream, mode=mode, fused_smoothing=smoothing == "cluster_fused")
             try:
                 n_atoms = 0
                 for system, prm in systems:
                     c = P.Context.from_system(system, precision="mixed", **prm)
-                    if smoothing == "per_step" and c.tuning()["diffusion_fuse"] == 5:
-                        c.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                    if prm["mesh"] <= 64:  # every member here; the default is the spectral mode
+                        if smoothing == "per_step":
+                            c.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                        elif smoothing.startswith("cluster"):
+                            c.set_tuning(diffusion_fuse=5)
                     ctxs.append(c)
                     n_atoms += system.n
                 for c in ctxs:
@@ -746,12 +750,12 @@ def batch_small_run(stream, peaks, members: int = 32, steps: int = 60, warmup: i
     for atoms in (512, 1728, 4096):
         system, prm = request_system(Request(rid=0, kind="nacl", n_atoms=atoms, seed=77, steps=0, arrival=0.0))
         rec = {"mesh": prm["mesh"]}
-        for smoothing in ("cluster", "per_step"):
+        for smoothing in ("cluster", "per_step", "spectral"):
             with P.Context.from_system(system, precision="mixed", stream=stream.cuda_stream, **prm) as c:
-                if c.tuning()["diffusion_fuse"] != 5:
-                    break
                 if smoothing == "per_step":
                     c.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                elif smoothing == "cluster":
+                    c.set_tuning(diffusion_fuse=5)
                 c.step(warmup)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -236,8 +236,11 @@ typedef struct {
                                    FP32 quads when N % 4 == 0);
                                    5: all K steps in one launch, the mesh resident in the
                                    shared memory of a thread-block cluster (FP32,
-                                   16 <= N <= 64, N % 4 == 0; the default there when the
-                                   device runs such clusters)                                */
+                                   16 <= N <= 64, N % 4 == 0); 6: all K steps at once in
+                                   the Hartley basis, where (I + cM)^K is the diagonal
+                                   (1 + c lambda_k)^K -- the same operator, rounded
+                                   differently (FP32, N <= 64; three transform launches;
+                                   the default there)                                       */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
     int32_t pair_blocks;        /* pair-kernel grid: 0 one block per home box, else that many
@@ -412,7 +415,7 @@ int p3maze_get_timing(p3maze_ctx *ctx, p3maze_timing *out);
  * conditional graph nodes.                                                    */
 /* Apply a setting (as p3maze_autotune returns it) without timing anything:
  * predictor (1..3; ignored for P3M), pre_sweeps >= 1, post_sweeps >= 0,
- * diffusion_zc >= 1, diffusion_fuse 1..5, pair_fork 0 or 1, coarse_max >= 1,
+ * diffusion_zc >= 1, diffusion_fuse 1..6, pair_fork 0 or 1, coarse_max >= 1,
  * pair_blocks >= 0, cluster_ctas 0 or a power of two up to 16, sweep_fuse 0 or
  * 1; the timing fields are ignored.  Captured step graphs are
  * dropped.  Errors: INVALID (out-of-range field, nothing changed).            */

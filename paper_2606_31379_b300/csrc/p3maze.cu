@@ -113,6 +113,7 @@ struct p3maze_ctx {
     ClusterMesh* cltab = nullptr;        // this mesh's entry for the cluster smoothing kernel
     bool cluster_ok = false;             // the device runs this mesh's clusters of the smoothing kernel
     int cl_ctas = 0;                     // CTAs per cluster of mode 5 (0: automatic)
+    void* Ssm = nullptr;                 // mode 6: (1 + c lambda_k)^K / N^3 in the Hartley basis (FP32, N <= 64)
     int sweep_fuse = 1;                  // FP32 quad levels: a full red-black sweep per launch
     // rollback (p3maze_set_rollback): a device copy of the state taken at the
     // first step call after the last wait, restored when that call's steps fail
@@ -535,7 +536,19 @@ int smooth(p3maze_ctx* ctx) {
     } else if constexpr (sizeof(T) == 4) {
         T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
         const T* src = (const T*)ctx->q;
-        if (ctx->fuse == 5) {
+        if (ctx->fuse == 6) {
+            // all K steps at once in the Hartley basis (N <= 64): forward
+            // transform, scale by (1 + c lambda_k)^K / N^3, inverse transform
+            const Level& L0 = ctx->lev[0];
+            const size_t sm = coarse_smem_bytes(ctx->N, sizeof(float));
+            const dim3 gc(ctx->N), bc(kCoarseThreads);
+            k_coarse_xy<float><<<gc, bc, sm, s>>>(ctx->N, (const float*)ctx->q, (float*)L0.t, (const float*)L0.H);
+            k_coarse_z<float><<<gc, bc, sm, s>>>(ctx->N, (float*)L0.t, (const float*)L0.H, (const float*)ctx->Ssm);
+            k_coarse_xy<float><<<gc, bc, sm, s>>>(ctx->N, (const float*)L0.t, (float*)ctx->qs, (const float*)L0.H);
+            k_sum_partial<float><<<kReduceBlocks, P3_THREADS, 0, s>>>(ctx->P, (const float*)ctx->qs, ctx->partial);
+            k_sum_final<<<1, P3_THREADS, 0, s>>>(kReduceBlocks, ctx->partial, ctx->dscal + S_QSUM);
+            count(ctx, P3MAZE_ST_SMOOTH, 5);
+        } else if (ctx->fuse == 5) {
             // every step in one launch, the mesh resident in a cluster's shared memory
             const int cs = ctx->cl_ctas ? ctx->cl_ctas : cluster_size_for(ctx->N, 1, ctx->nsm);
             CK(launch_cluster_smoothing(ctx->cltab, 1, cs, ctx->N, s, false));
@@ -1512,6 +1525,27 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
             CK(cudaMemcpy(L.D, D.data(), 8 * D.size(), cudaMemcpyHostToDevice));
         }
     }
+    if (mixed && ctx->K > 0 && ctx->lev[0].H) {
+        // the smoothing operator (I + cM)^K is diagonal in the Hartley basis:
+        // eigenvalue (1 + c lambda_k)^K, lambda_k = -4 sum_axes sin^2(pi k_axis / N)
+        const int N = ctx->N;
+        std::vector<double> s2(N);
+        for (int k = 0; k < N; ++k) {
+            const double sk = std::sin(kPi * k / N);
+            s2[k] = sk * sk;
+        }
+        std::vector<float> S((size_t)N * N * N);
+        const double inv_n3 = 1.0 / ((double)N * N * N);
+        for (int kz = 0; kz < N; ++kz)
+            for (int ky = 0; ky < N; ++ky)
+                for (int kx = 0; kx < N; ++kx) {
+                    const double g = 1.0 - 4.0 * ctx->c * (s2[kx] + s2[ky] + s2[kz]);
+                    S[((size_t)kz * N + ky) * N + kx] = (float)(std::pow(g, ctx->K) * inv_n3);
+                }
+        ALLOC(ctx->Ssm, 4 * S.size());
+        CK(cudaMemcpy(ctx->Ssm, S.data(), 4 * S.size(), cudaMemcpyHostToDevice));
+        ctx->fuse = 6;  // the default for such meshes: fastest alone and in a batch graph
+    }
     CK(cudaMemcpyAsync(ctx->hdt_acc, hacc.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->mass, p->masses, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->Q, p->charges, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
@@ -1593,6 +1627,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     b += a(8 * (size_t)partial_slots(N));
     b += a(8 * S_NSCAL);
     if (mixed && p->method != P3MAZE_METHOD_PMAZE && cluster_mesh_ok(N)) b += a(sizeof(ClusterMesh));
+    if (mixed && p->method != P3MAZE_METHOD_PMAZE && N <= kCoarseMax) b += a(4 * P);  // spectral smoothing table
     {
         const dim3 gr = resid_grid(N);
         b += a(8 * (size_t)gr.x * gr.y * gr.z);
@@ -2414,17 +2449,18 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     // 0: 1-8) or per block (temporal blocking: 8-64 in quads, else 4-32)
     auto diffusion_pass = [&]() {
         if (ctx->K == 0) return;  // no smoothing (PMaZe)
-        const int fuses[5] = {1, 2, 3, 4, 5};
+        const int fuses[6] = {1, 2, 3, 4, 5, 6};
         const int zcs_quad[4] = {1, 2, 4, 8}, zcs_tq[4] = {8, 16, 32, 64}, zcs_other[4] = {4, 8, 16, 32};
         const Setting base = chosen;
         for (int f : fuses) {
             if (f > 1 && ctx->prec != P3MAZE_MIXED) continue;
             if (f == 2 && ctx->N % 4 != 0) continue;
             if (f == 5 && !ctx->cluster_ok) continue;
+            if (f == 6 && !ctx->Ssm) continue;
             const bool quad = f <= 2 && ctx->prec == P3MAZE_MIXED && ctx->N % 4 == 0;
             // the cluster kernel has no z planes per thread: one trial
             const bool tq = f >= 3 && f <= 4 && ctx->N % 4 == 0;
-            std::vector<int> zcs = f == 5 ? std::vector<int>{base.zc}
+            std::vector<int> zcs = f >= 5 ? std::vector<int>{base.zc}
                                    : quad ? std::vector<int>(zcs_quad, zcs_quad + 4)
                                    : tq   ? std::vector<int>(zcs_tq, zcs_tq + 4)
                                           : std::vector<int>(zcs_other, zcs_other + 4);
@@ -2523,12 +2559,14 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
 int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (!ctx || !t) return fail(ctx, P3MAZE_ERR_INVALID, "NULL argument");
     if (t->predictor < 1 || t->predictor > 3 || t->pre_sweeps < 1 || t->post_sweeps < 0 || t->diffusion_zc < 1 ||
-        t->diffusion_fuse < 1 || t->diffusion_fuse > 5 || (t->pair_fork != 0 && t->pair_fork != 1) ||
+        t->diffusion_fuse < 1 || t->diffusion_fuse > 6 || (t->pair_fork != 0 && t->pair_fork != 1) ||
         t->coarse_max < 1 || t->pair_blocks < 0 || t->cluster_ctas < 0 || t->cluster_ctas > kClMaxCTAs ||
         (t->cluster_ctas & (t->cluster_ctas - 1)) != 0 || (t->sweep_fuse != 0 && t->sweep_fuse != 1))
         return fail(ctx, P3MAZE_ERR_INVALID, "tuning field out of range");
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
+    if (t->diffusion_fuse == 6 && !ctx->Ssm)
+        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64");
     if (t->diffusion_fuse == 5 && !ctx->cluster_ok)
         return fail(ctx, P3MAZE_ERR_INVALID,
                     "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs such clusters");

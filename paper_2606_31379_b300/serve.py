@@ -111,8 +111,9 @@ class GpuBackend:
 
     def __init__(self, precision: str = "mixed", stream: int | None = None, admit_stream: int | None = None,
                  smoothing: str = "default"):
-        """smoothing: "default" keeps each context's own choice (meshes of at
-        most 64^3 smooth in one cluster launch, shared by the whole batch);
+        """smoothing: "default" smooths meshes of at most 64^3 in cluster
+        launches, fused across the batch's members (between separately
+        launched member graphs this beats each member's own smoothing);
         "per_step" forces one diffusion kernel launch per two steps (the
         25-point kernel), for comparison."""
         import queue
@@ -146,8 +147,15 @@ class GpuBackend:
             try:
                 system, prm = request_system(req)
                 ctx = self.P.Context.from_system(system, precision=self.precision, stream=self.admit_stream, **prm)
-                if self.smoothing == "per_step" and ctx.tuning()["diffusion_fuse"] == 5:
-                    ctx.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                if ctx.tuning()["diffusion_fuse"] >= 5:  # a mesh of at most 64^3
+                    if self.smoothing == "per_step":
+                        ctx.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
+                    else:
+                        # the cluster launch, fused across the batch's members
+                        try:
+                            ctx.set_tuning(diffusion_fuse=5)
+                        except self.P.P3MaZeError:
+                            pass                # no such clusters: keep the context's default
                 ctx.step(self.WARMUP_STEPS)
                 self._ready.put((req, ctx, time.perf_counter() - t0, None))
             except Exception as e:          # reported to the stepping thread

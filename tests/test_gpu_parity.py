@@ -344,8 +344,7 @@ def test_cluster_smoothing_matches_oracle(P, mesh):
     r_cut = min(9.0, box)
     kw = dict(alpha=0.30, r_cut=r_cut, mesh=mesh, tol=1e-8, dt=1.0, precision="mixed")
     with P.Context.from_system(s, **kw) as a, P.Context.from_system(s, **kw) as b:
-        if a.tuning()["diffusion_fuse"] != 5:
-            pytest.skip("the device does not run clusters of the smoothing kernel")
+        _use_cluster(P, a)
         b.set_tuning(diffusion_fuse=1)
         a.step(2)
         b.step(2)
@@ -362,6 +361,43 @@ def test_cluster_smoothing_matches_oracle(P, mesh):
         b.step(1)
         assert a.timing()["launches"]["smooth"] == 1                     # all K steps, one launch
         assert b.timing()["launches"]["smooth"] == a.stats()["smooth_steps"] + 1
+
+
+@pytest.mark.parametrize("mesh", [16, 24, 32, 48, 60, 64])
+def test_spectral_smoothing_matches_oracle(P, mesh):
+    """Smoothing mode 6: (I + cM)^K applied as its diagonal (1 + c lambda_k)^K
+    between FP32 Hartley transforms matches the oracle's K explicit steps.
+    Bar: each of the six FP32 transform passes sums N products of magnitude
+    up to sqrt2 |x|, so q^s carries about 6 sqrt(N) 2^-24 sqrt2 of the largest
+    intermediate, below 5e-6 of max |q^s| for N <= 64; the forces then match
+    the oracle to the mixed bar."""
+    box = 0.8 * mesh
+    s = S.nacl_melt(2 * int(round(0.031899 * box ** 3 / 2)), box, seed=90 + mesh)
+    kw = dict(alpha=0.30, r_cut=min(9.0, box), mesh=mesh, tol=1e-8, dt=1.0, precision="mixed")
+    with P.Context.from_system(s, **kw) as a:
+        a.set_tuning(diffusion_fuse=6)
+        a.reinit()
+        mf = O.mesh_fields(at_positions(s, a.positions()), 0.30, mesh)
+        qa = a.mesh("qs")
+        assert np.abs(qa - mf["qs"]).max() <= 5e-6 * np.abs(mf["qs"]).max()
+        a.set_timing(True)
+        a.step(2)
+        assert a.timing()["launches"]["smooth"] == 2 * 5
+        ref = oracle_full(s, a.positions(), 0.30, min(9.0, box), mesh)
+        assert rel_rms(a.forces(), ref["F"]) < 1e-4
+    w = S.nacl_melt(300, 21.1, seed=31)
+    with P.Context.from_system(w, alpha=0.30, r_cut=9.0, mesh=80, tol=1e-8, dt=1.0, precision="mixed") as c:
+        with pytest.raises(P.P3MaZeError, match="spectral"):
+            c.set_tuning(diffusion_fuse=6)
+
+
+def _use_cluster(P, c):
+    """Select the cluster smoothing (mode 5; meshes of at most 64^3 default to
+    the spectral mode); skip where the device runs no such clusters."""
+    try:
+        c.set_tuning(diffusion_fuse=5)
+    except P.P3MaZeError:
+        pytest.skip("the device does not run clusters of the smoothing kernel")
 
 
 def _min_cluster_ctas(mesh):
@@ -382,8 +418,7 @@ def test_cluster_smoothing_is_the_same_for_every_cluster_size(P, mesh):
     kw = dict(alpha=0.30, r_cut=min(9.0, box), mesh=mesh, tol=1e-8, dt=1.0, precision="mixed")
     lo = _min_cluster_ctas(mesh)
     with P.Context.from_system(s, **kw) as a:
-        if a.tuning()["diffusion_fuse"] != 5:
-            pytest.skip("the device does not run clusters of the smoothing kernel")
+        _use_cluster(P, a)
         if lo > 1:
             with pytest.raises(P.P3MaZeError, match="cluster_ctas"):
                 a.set_tuning(cluster_ctas=lo // 2)
@@ -455,9 +490,10 @@ def test_autotuner_keeps_results_within_tolerance(P, nacl512):
         assert t["predictor"] in (1, 2, 3)
         assert (t["pre_sweeps"], t["post_sweeps"]) in ((1, 1), (2, 1), (1, 2), (2, 2), (3, 3))
         # planes per thread (one or two steps per launch, FP32 quads) or per block (3 or 4 steps
-        # per launch), or every step in one cluster launch (the planes setting is then unused)
+        # per launch), or every step in one cluster launch or in the Hartley basis (the planes
+        # setting is then unused)
         assert (t["diffusion_fuse"], t["diffusion_zc"]) in [(f, z) for f in (1, 2) for z in (1, 2, 4, 8)] + \
-            [(f, z) for f in (3, 4) for z in (8, 16, 32, 64)] or t["diffusion_fuse"] == 5
+            [(f, z) for f in (3, 4) for z in (8, 16, 32, 64)] or t["diffusion_fuse"] in (5, 6)
         assert t["trials"] >= 16 and t["ms_per_step"] <= t["initial_ms_per_step"]
         assert ctx.stats()["steps"] == 4 + t["steps"]
         ctx.step(2)
