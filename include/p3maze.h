@@ -239,7 +239,8 @@ typedef struct {
                                    16 <= N <= 64, N % 4 == 0); 6: all K steps at once in
                                    the Hartley basis, where (I + cM)^K is the diagonal
                                    (1 + c lambda_k)^K -- the same operator, rounded
-                                   differently (FP32, N <= 64; three transform launches;
+                                   differently (FP32, N <= 64 or N = 128; three transform
+                                   launches, each 1D transform by FFT for N = 32, 64, 128;
                                    the default there)                                       */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */

@@ -2085,6 +2085,275 @@ inline size_t coarse_smem_bytes(int n, size_t tb) {
     return 3 * nP * nP * tb;
 }
 
+// ---------------------------------------------------------------- spectral smoothing by FFT
+// (I + cM)^K q for meshes of n = 32, 64 or 128 points per axis (powers of two
+// whose n x n plane fits in shared memory).  The operator is the separable
+// Hartley diagonalisation of the coarse solve, q^s = H3 (S o (H3 q)) with
+// S(k) = (1 + c lambda_k)^K / n^3, but each 1D Hartley transform takes
+// O(n log n) operations: two real lines a, b packed as z = a + ib go through
+// one complex FFT Z, and with A = (Z[k] + conj Z[n-k]) / 2 (the DFT of a),
+// B = (Z[k] - conj Z[n-k]) / 2i (that of b), the Hartley coefficients
+// Re A - Im A and Re B - Im B are
+//   Ha[k] = (Re Z[k] - Im Z[k] + Re Z[n-k] + Im Z[n-k]) / 2,
+//   Hb[k] = (Re Z[k] + Im Z[k] - Re Z[n-k] + Im Z[n-k]) / 2.
+// One warp transforms one pair of lines: lane l holds points l + 32 j
+// (j < n / 32) in registers; the radix-2 decimation-in-frequency stages of
+// half-size 32 and more run inside the lane, those of half-size 16 .. 1
+// across lanes by shuffles.  The result, in bit-reversed order, goes through
+// shared memory for the split.  Twiddles exp(-2 pi i k / n), k < n / 2, are
+// FP64 values rounded once to FP32; each lane keeps the ones it uses in
+// registers.  Three launches of n blocks: x and y transforms of each z plane
+// (k_fht_xy), z transform, scaling and z transform again of each plane of
+// constant ky (k_fht_z), and k_fht_xy once more, which also writes the
+// compensated sum of each output plane.
+//
+// Shared-memory layout of an n x n plane: element (r, c) at
+// r n + (c ^ (r mod 32)).  Rows stay 16-byte aligned (the XOR keeps each
+// group of four within its 16 bytes), and a warp reading 32 consecutive
+// elements of a row or of a column touches 32 distinct banks.  Inside a
+// line, the bit-reversed FFT output of point p sits at p ^ (p / 32), which
+// keeps the split's reads at reversed indices conflict-free as well.
+constexpr int kFhtMaxN = 128;
+
+template <int R>
+__host__ __device__ constexpr int fht_threads() { return R == 1 ? 512 : 1024; }
+
+template <int R>
+__device__ __forceinline__ int fht_at(int r, int c) { return r * (32 * R) + (c ^ (r & 31)); }
+
+// element p of line `line`: a row (COL false) or a column (COL true)
+template <int R, bool COL>
+__device__ __forceinline__ int fht_line(int line, int p) { return COL ? fht_at<R>(p, line) : fht_at<R>(line, p); }
+
+// g[e] = f[e ^ x]: the order of a row's four elements inside their 16 bytes
+__device__ __forceinline__ float4 fht_perm4(float4 f, int x) {
+    if (x & 1) f = make_float4(f.y, f.x, f.w, f.z);
+    if (x & 2) f = make_float4(f.z, f.w, f.x, f.y);
+    return f;
+}
+
+__device__ __forceinline__ float2 fht_cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+
+// The twiddles of one lane: stage of half-size 32 M (M = R/2 .. 1), register
+// pair (j, j + M), j mod 2M = j' < M: in[M - 1 + j'] = W_{64M}^(lane + 32 j');
+// cross-lane stage of half-size m = 16 >> s (s < 4): x[s] = W_{2m}^(lane mod m)
+// on the lane with bit m set, 1 on its partner (half-size 1 needs none).
+template <int R>
+struct FhtTw {
+    float2 in[R > 1 ? R - 1 : 1];
+    float2 x[4];
+};
+
+template <int R>
+__device__ __forceinline__ void fht_twiddles(FhtTw<R>& t, const float2* __restrict__ tw, int lane) {
+    constexpr int n = 32 * R;
+#pragma unroll
+    for (int M = R / 2; M >= 1; M >>= 1)
+#pragma unroll
+        for (int j = 0; j < M; ++j) t.in[M - 1 + j] = tw[(lane + 32 * j) * (n / (64 * M))];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int m = 16 >> s;
+        t.x[s] = (lane & m) ? tw[(lane & (m - 1)) * (n / (2 * m))] : make_float2(1.f, 0.f);
+    }
+}
+
+// In-place radix-2 DIF FFT of n = 32 R points held as v[j] = z[lane + 32 j];
+// on return v[j] holds Z[rev(lane + 32 j)] (log2 n-bit reversal).
+template <int R>
+__device__ __forceinline__ void warp_fft_dif(float2 (&v)[R], const FhtTw<R>& t, int lane) {
+#pragma unroll
+    for (int M = R / 2; M >= 1; M >>= 1)
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if ((j & M) == 0) {
+                const float2 a = v[j], b = v[j + M];
+                v[j] = make_float2(a.x + b.x, a.y + b.y);
+                v[j + M] = fht_cmul(make_float2(a.x - b.x, a.y - b.y), t.in[M - 1 + (j & (2 * M - 1))]);
+            }
+    // lane pairs (l, l ^ m): the lane with bit m set holds z[i + m] and forms
+    // (z[i] - z[i + m]) W_{2m}^(i mod 2m), its partner z[i] + z[i + m]
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int m = 16 >> s;
+        const float sg = (lane & m) ? -1.f : 1.f;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const float ox = __shfl_xor_sync(0xffffffffu, v[j].x, m);
+            const float oy = __shfl_xor_sync(0xffffffffu, v[j].y, m);
+            const float2 d = make_float2(fmaf(sg, v[j].x, ox), fmaf(sg, v[j].y, oy));
+            v[j] = s < 4 ? fht_cmul(d, t.x[s]) : d;
+        }
+    }
+}
+
+// Hartley transforms, in place, of lines la and lb of the plane s (rows, or
+// columns with COL).  All 32 lanes of a warp call it.
+template <int R, bool COL>
+__device__ __forceinline__ void warp_fht2(float* s, int la, int lb, const FhtTw<R>& t, int lane) {
+    constexpr int n = 32 * R;
+    constexpr int L = R == 1 ? 5 : R == 2 ? 6 : 7;
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        v[j] = make_float2(s[fht_line<R, COL>(la, p)], s[fht_line<R, COL>(lb, p)]);
+    }
+    warp_fft_dif<R>(v, t, lane);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int q = (lane + 32 * j) ^ j;  // point p at p ^ (p / 32)
+        s[fht_line<R, COL>(la, q)] = v[j].x;
+        s[fht_line<R, COL>(lb, q)] = v[j].y;
+    }
+    __syncwarp();
+    float ha[R], hb[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int k = lane + 32 * j;
+        const int rk = (int)(__brev((unsigned)k) >> (32 - L));
+        const int rn = (int)(__brev((unsigned)((n - k) & (n - 1))) >> (32 - L));
+        const int qk = rk ^ (rk >> 5), qn = rn ^ (rn >> 5);
+        const float zr = s[fht_line<R, COL>(la, qk)], zi = s[fht_line<R, COL>(lb, qk)];
+        const float wr = s[fht_line<R, COL>(la, qn)], wi = s[fht_line<R, COL>(lb, qn)];
+        ha[j] = 0.5f * ((zr - zi) + (wr + wi));
+        hb[j] = 0.5f * ((zr + zi) + (wi - wr));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int p = lane + 32 * j;
+        s[fht_line<R, COL>(la, p)] = ha[j];
+        s[fht_line<R, COL>(lb, p)] = hb[j];
+    }
+    __syncwarp();
+}
+
+// x and y transforms of z plane blockIdx.x: out[z] = Hy in[z] Hx.  With
+// partial != nullptr, partial[blockIdx.x] gets the compensated sum of the
+// output plane.
+template <int R>
+__global__ void __launch_bounds__(fht_threads<R>())
+k_fht_xy(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
+         double* __restrict__ partial) {
+    constexpr int n = 32 * R, T = fht_threads<R>(), Q = n * n / 4;
+    extern __shared__ __align__(16) unsigned char fht_smem[];
+    float* s = reinterpret_cast<float*>(fht_smem);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    FhtTw<R> t;
+    fht_twiddles<R>(t, tw, lane);  // constant: before the wait
+    const int64_t base = (int64_t)blockIdx.x * n * n / 4;
+    pdl_wait();
+    pdl_trigger();
+    const float4* src = reinterpret_cast<const float4*>(in) + base;
+    float4 f[(Q + T - 1) / T];
+#pragma unroll
+    for (int k = 0; k < (Q + T - 1) / T; ++k)
+        if (tid + k * T < Q) f[k] = src[tid + k * T];
+#pragma unroll
+    for (int k = 0; k < (Q + T - 1) / T; ++k) {
+        const int i = tid + k * T, r = 4 * i / n, c = 4 * i % n;
+        if (i < Q) *reinterpret_cast<float4*>(s + r * n + (c ^ (r & 28))) = fht_perm4(f[k], r & 3);
+    }
+    __syncthreads();
+    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, false>(s, 2 * p, 2 * p + 1, t, lane);
+    __syncthreads();
+    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, true>(s, 2 * p, 2 * p + 1, t, lane);
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(out) + base;
+    float acc_s = 0.f, acc_c = 0.f;
+#pragma unroll
+    for (int k = 0; k < (Q + T - 1) / T; ++k) {
+        const int i = tid + k * T, r = 4 * i / n, c = 4 * i % n;
+        if (i < Q) {
+            const float4 o = fht_perm4(*reinterpret_cast<const float4*>(s + r * n + (c ^ (r & 28))), r & 3);
+            dst[i] = o;
+            if (partial) {
+                two_sum_add(acc_s, acc_c, o.x);
+                two_sum_add(acc_s, acc_c, o.y);
+                two_sum_add(acc_s, acc_c, o.z);
+                two_sum_add(acc_s, acc_c, o.w);
+            }
+        }
+    }
+    if (partial) {
+        const double acc = block_sum((double)acc_s + (double)acc_c);
+        if (tid == 0) partial[blockIdx.x] = acc;
+    }
+}
+
+// For ky = blockIdx.x: z transform of the slice t[z][ky][x] (rows z,
+// columns x in shared memory), scaling by S (laid out like t; its slice
+// copied asynchronously into a second shared plane while the transform
+// runs, each 16-byte group at its position in the swizzled layout, in
+// natural order), and the z transform again, in place.
+template <int R>
+__global__ void __launch_bounds__(fht_threads<R>())
+k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __restrict__ S) {
+    constexpr int n = 32 * R, T = fht_threads<R>(), Q = n * n / 4, PER = (Q + T - 1) / T;
+    extern __shared__ __align__(16) unsigned char fht_smem[];
+    float* s = reinterpret_cast<float*>(fht_smem);
+    float* ss = s + n * n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t ky = blockIdx.x;
+    FhtTw<R> t;
+    fht_twiddles<R>(t, tw, lane);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {  // S is constant: before the wait
+        const int i = tid + k * T, z = 4 * i / n, x = 4 * i % n;
+        if (i < Q) cp_async16(ss + z * n + (x ^ (z & 28)), S + ((int64_t)z * n + ky) * n + x);
+    }
+    cp_async_commit();
+    pdl_wait();
+    pdl_trigger();
+    float4 f[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * T, z = 4 * i / n, x = 4 * i % n;
+        if (i < Q) f[k] = *reinterpret_cast<const float4*>(tz + ((int64_t)z * n + ky) * n + x);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * T, z = 4 * i / n, x = 4 * i % n;
+        if (i < Q) *reinterpret_cast<float4*>(s + z * n + (x ^ (z & 28))) = fht_perm4(f[k], z & 3);
+    }
+    __syncthreads();
+    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, true>(s, 2 * p, 2 * p + 1, t, lane);
+    cp_async_wait<0>();
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * T, z = 4 * i / n, x = 4 * i % n;
+        if (i < Q) {
+            const int o = z * n + (x ^ (z & 28));
+            const float4 g = *reinterpret_cast<const float4*>(s + o);
+            const float4 w = fht_perm4(*reinterpret_cast<const float4*>(ss + o), z & 3);
+            *reinterpret_cast<float4*>(s + o) = make_float4(g.x * w.x, g.y * w.y, g.z * w.z, g.w * w.w);
+        }
+    }
+    __syncthreads();
+    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, true>(s, 2 * p, 2 * p + 1, t, lane);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * T, z = 4 * i / n, x = 4 * i % n;
+        if (i < Q)
+            *reinterpret_cast<float4*>(tz + ((int64_t)z * n + ky) * n + x) =
+                fht_perm4(*reinterpret_cast<const float4*>(s + z * n + (x ^ (z & 28))), z & 3);
+    }
+}
+
+// Shared memory of the FFT smoothing kernels at n points per axis: the
+// plane, and for k_fht_z the slice of S.
+inline size_t fht_smem_bytes(int n) { return (size_t)n * n * sizeof(float); }
+inline size_t fht_z_smem_bytes(int n) { return 2 * fht_smem_bytes(n); }
+
+// Meshes the FFT smoothing handles.
+inline bool fht_supported(int n) { return n == 32 || n == 64 || n == kFhtMaxN; }
+
 // ---------------------------------------------------------------- interpolation
 // F_a = -ke Q_a sum_n W(r_a - r_n) (D phi)_n with central differences
 // (Eq. 21), one thread per particle in cell order; writes the total force

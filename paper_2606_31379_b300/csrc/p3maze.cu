@@ -113,7 +113,9 @@ struct p3maze_ctx {
     ClusterMesh* cltab = nullptr;        // this mesh's entry for the cluster smoothing kernel
     bool cluster_ok = false;             // the device runs this mesh's clusters of the smoothing kernel
     int cl_ctas = 0;                     // CTAs per cluster of mode 5 (0: automatic)
-    void* Ssm = nullptr;                 // mode 6: (1 + c lambda_k)^K / N^3 in the Hartley basis (FP32, N <= 64)
+    void* Ssm = nullptr;                 // mode 6: (1 + c lambda_k)^K / N^3 in the Hartley basis (FP32, N <= 64
+                                         // or N = 128)
+    void* fht_tw = nullptr;              // mode 6 by FFT (N = 32, 64, 128): exp(-2 pi i k / N), k < N / 2
     int sweep_fuse = 1;                  // FP32 quad levels: a full red-black sweep per launch
     // rollback (p3maze_set_rollback): a device copy of the state taken at the
     // first step call after the last wait, restored when that call's steps fail
@@ -409,6 +411,33 @@ cudaError_t launch_diffuse_tq(p3maze_ctx* ctx, int S, bool last, bool pdl, const
     }
 }
 
+// Spectral smoothing by FFT (N = 32, 64, 128): the x-y transforms of q into
+// the smoothing ping-pong mesh, the z transforms and scaling in place, the
+// x-y transforms into q^s with per-plane sums, and the neutrality sum.
+template <int R>
+cudaError_t launch_fht_r(p3maze_ctx* ctx) {
+    cudaStream_t s = ctx->stream;
+    const dim3 g(32 * R), b(fht_threads<R>());
+    const size_t sm = fht_smem_bytes(32 * R);
+    float* t = (float*)ctx->lev[0].e;
+    const float2* tw = (const float2*)ctx->fht_tw;
+    cudaError_t e = launch_maybe_pdl(ctx->pdl, k_fht_xy<R>, g, b, sm, s, (const float*)ctx->q, t, tw, (double*)nullptr);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(ctx->pdl, k_fht_z<R>, g, b, fht_z_smem_bytes(32 * R), s, t, tw, (const float*)ctx->Ssm);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(ctx->pdl, k_fht_xy<R>, g, b, sm, s, (const float*)t, (float*)ctx->qs, tw, ctx->partial);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(ctx->pdl, k_sum_final, dim3(1), dim3(1024), 0, s, 32 * R, (const double*)ctx->partial,
+                             ctx->dscal + S_QSUM);
+    return e;
+}
+cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
+    switch (ctx->N) {
+        case 32: return launch_fht_r<1>(ctx);
+        case 64: return launch_fht_r<2>(ctx);
+        default: return launch_fht_r<4>(ctx);
+    }
+}
 
 // All diffusion steps of `members` meshes (table on the device, N <= nmax,
 // all with cluster size cs) in one launch, one cluster of cs CTAs per mesh.
@@ -536,7 +565,11 @@ int smooth(p3maze_ctx* ctx) {
     } else if constexpr (sizeof(T) == 4) {
         T* tmp[2] = {(T*)ctx->lev[0].e, (T*)ctx->lev[0].r};
         const T* src = (const T*)ctx->q;
-        if (ctx->fuse == 6) {
+        if (ctx->fuse == 6 && ctx->fht_tw) {
+            // all K steps at once in the Hartley basis, each 1D transform by FFT
+            CK(launch_fht_smoothing(ctx));
+            count(ctx, P3MAZE_ST_SMOOTH, 4);
+        } else if (ctx->fuse == 6) {
             // all K steps at once in the Hartley basis (N <= 64): forward
             // transform, scale by (1 + c lambda_k)^K / N^3, inverse transform
             const Level& L0 = ctx->lev[0];
@@ -1525,7 +1558,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
             CK(cudaMemcpy(L.D, D.data(), 8 * D.size(), cudaMemcpyHostToDevice));
         }
     }
-    if (mixed && ctx->K > 0 && ctx->lev[0].H) {
+    if (mixed && ctx->K > 0 && (ctx->lev[0].H || fht_supported(ctx->N))) {
         // the smoothing operator (I + cM)^K is diagonal in the Hartley basis:
         // eigenvalue (1 + c lambda_k)^K, lambda_k = -4 sum_axes sin^2(pi k_axis / N)
         const int N = ctx->N;
@@ -1544,6 +1577,25 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
                 }
         ALLOC(ctx->Ssm, 4 * S.size());
         CK(cudaMemcpy(ctx->Ssm, S.data(), 4 * S.size(), cudaMemcpyHostToDevice));
+        if (fht_supported(N)) {
+            std::vector<float2> tw(N / 2);
+            for (int k = 0; k < N / 2; ++k)
+                tw[k] = make_float2((float)std::cos(2.0 * kPi * k / N), (float)-std::sin(2.0 * kPi * k / N));
+            ALLOC(ctx->fht_tw, sizeof(float2) * tw.size());
+            CK(cudaMemcpy(ctx->fht_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+            // the shared-memory limit of a kernel is shared by every context: only ever raise it
+            auto raise = [&](const void* fn, size_t sm) {
+                cudaFuncAttributes fa{};
+                cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+                if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < sm)
+                    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                return e;
+            };
+            if (N == 128) {
+                CK(raise((const void*)k_fht_xy<4>, fht_smem_bytes(N)));
+                CK(raise((const void*)k_fht_z<4>, fht_z_smem_bytes(N)));
+            }
+        }
         ctx->fuse = 6;  // the default for such meshes: fastest alone and in a batch graph
     }
     CK(cudaMemcpyAsync(ctx->hdt_acc, hacc.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
@@ -1627,7 +1679,10 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     b += a(8 * (size_t)partial_slots(N));
     b += a(8 * S_NSCAL);
     if (mixed && p->method != P3MAZE_METHOD_PMAZE && cluster_mesh_ok(N)) b += a(sizeof(ClusterMesh));
-    if (mixed && p->method != P3MAZE_METHOD_PMAZE && N <= kCoarseMax) b += a(4 * P);  // spectral smoothing table
+    if (mixed && p->method != P3MAZE_METHOD_PMAZE && (N <= kCoarseMax || fht_supported(N))) {
+        b += a(4 * P);  // spectral smoothing table
+        if (fht_supported(N)) b += a(sizeof(float2) * (size_t)(N / 2));  // its FFT twiddles
+    }
     {
         const dim3 gr = resid_grid(N);
         b += a(8 * (size_t)gr.x * gr.y * gr.z);
@@ -2566,7 +2621,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
     if (t->diffusion_fuse == 6 && !ctx->Ssm)
-        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64");
+        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64 or N = 128");
     if (t->diffusion_fuse == 5 && !ctx->cluster_ok)
         return fail(ctx, P3MAZE_ERR_INVALID,
                     "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs such clusters");

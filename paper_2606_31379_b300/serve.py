@@ -147,7 +147,7 @@ class GpuBackend:
             try:
                 system, prm = request_system(req)
                 ctx = self.P.Context.from_system(system, precision=self.precision, stream=self.admit_stream, **prm)
-                if ctx.tuning()["diffusion_fuse"] >= 5:  # a mesh of at most 64^3
+                if ctx.tuning()["diffusion_fuse"] >= 5:  # spectral default: meshes of at most 64^3, or 128^3
                     if self.smoothing == "per_step":
                         ctx.set_tuning(diffusion_fuse=2 if prm["mesh"] % 4 == 0 else 1, diffusion_zc=2)
                     else:
@@ -155,7 +155,7 @@ class GpuBackend:
                         try:
                             ctx.set_tuning(diffusion_fuse=5)
                         except self.P.P3MaZeError:
-                            pass                # no such clusters: keep the context's default
+                            pass                # no such clusters (or a 128^3 mesh): keep the default
                 ctx.step(self.WARMUP_STEPS)
                 self._ready.put((req, ctx, time.perf_counter() - t0, None))
             except Exception as e:          # reported to the stepping thread
