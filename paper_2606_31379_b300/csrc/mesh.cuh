@@ -2099,20 +2099,26 @@ inline size_t coarse_smem_bytes(int n, size_t tb) {
 // One warp transforms one pair of lines: lane l holds points l + 32 j
 // (j < n / 32) in registers; the radix-2 decimation-in-frequency stages of
 // half-size 32 and more run inside the lane, those of half-size 16 .. 1
-// across lanes by shuffles.  The result, in bit-reversed order, goes through
-// shared memory for the split.  Twiddles exp(-2 pi i k / n), k < n / 2, are
-// FP64 values rounded once to FP32; each lane keeps the ones it uses in
-// registers.  Three launches of n blocks: x and y transforms of each z plane
-// (k_fht_xy), z transform, scaling and z transform again of each plane of
-// constant ky (k_fht_z), and k_fht_xy once more, which also writes the
-// compensated sum of each output plane.
+// across lanes by shuffles.  The forward transforms (decimation in
+// frequency) leave the coefficients in bit-reversed order, the inverse ones
+// (decimation in time) take them so and return natural order: the scaling
+// table is stored bit-reversed in all three indices, and nothing is ever
+// reordered.  The split's partner Z[n - k] is in another lane and comes by
+// one shuffle per register.  The kernels form 2 Ha and 2 Hb (the halving
+// is left to the scaling table, which carries 1/64 for the six transforms).
+// Twiddles exp(-2 pi i k / n), k < n / 2, are FP64 values rounded once to
+// FP32; each lane keeps the ones it uses in registers.  Three launches of n
+// blocks: forward x and y transforms of each z plane (k_fht_xy), forward z
+// transform, scaling and inverse z transform of each plane of constant ky
+// (k_fht_z), and the inverse x and y transforms (k_fht_xy), which also
+// write the compensated sum of each output plane.
 //
 // Shared-memory layout of an n x n plane: element (r, c) at
-// r n + (c ^ (r mod 32)).  Rows stay 16-byte aligned (the XOR keeps each
-// group of four within its 16 bytes), and a warp reading 32 consecutive
-// elements of a row or of a column touches 32 distinct banks.  Inside a
-// line, the bit-reversed FFT output of point p sits at p ^ (p / 32), which
-// keeps the split's reads at reversed indices conflict-free as well.
+// r n + (c ^ (r mod 32)) (k_fht_xy's row pass reads its rows straight from
+// global memory and writes them so).  Rows stay 16-byte
+// aligned (the XOR keeps each group of four within its 16 bytes), and a warp
+// reading or writing 32 consecutive elements of a row or of a column touches
+// 32 distinct banks.
 constexpr int kFhtMaxN = 128;
 
 template <int R>
@@ -2189,93 +2195,184 @@ __device__ __forceinline__ void warp_fft_dif(float2 (&v)[R], const FhtTw<R>& t, 
     }
 }
 
-// Hartley transforms, in place, of lines la and lb of the plane s (rows, or
-// columns with COL).  All 32 lanes of a warp call it.
-template <int R, bool COL>
-__device__ __forceinline__ void warp_fht2(float* s, int la, int lb, const FhtTw<R>& t, int lane) {
-    constexpr int n = 32 * R;
-    constexpr int L = R == 1 ? 5 : R == 2 ? 6 : 7;
-    float2 v[R];
+// In-place radix-2 DIT FFT: v[j] holds X[rev(lane + 32 j)] on entry and
+// Y[lane + 32 j] = sum_k X[k] W_n^(k (lane + 32 j)) on return.  The stages
+// of the DIF transform in reverse order, each twiddle applied to the upper
+// input before its butterfly.
+template <int R>
+__device__ __forceinline__ void warp_fft_dit(float2 (&v)[R], const FhtTw<R>& t, int lane) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int p = lane + 32 * j;
-        v[j] = make_float2(s[fht_line<R, COL>(la, p)], s[fht_line<R, COL>(lb, p)]);
-    }
-    warp_fft_dif<R>(v, t, lane);
-    __syncwarp();
+    for (int s = 4; s >= 0; --s) {
+        const int m = 16 >> s;
+        const float sg = (lane & m) ? -1.f : 1.f;
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int q = (lane + 32 * j) ^ j;  // point p at p ^ (p / 32)
-        s[fht_line<R, COL>(la, q)] = v[j].x;
-        s[fht_line<R, COL>(lb, q)] = v[j].y;
+        for (int j = 0; j < R; ++j) {
+            const float2 u = s < 4 ? fht_cmul(v[j], t.x[s]) : v[j];
+            const float ox = __shfl_xor_sync(0xffffffffu, u.x, m);
+            const float oy = __shfl_xor_sync(0xffffffffu, u.y, m);
+            v[j] = make_float2(fmaf(sg, u.x, ox), fmaf(sg, u.y, oy));
+        }
     }
-    __syncwarp();
-    float ha[R], hb[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int k = lane + 32 * j;
-        const int rk = (int)(__brev((unsigned)k) >> (32 - L));
-        const int rn = (int)(__brev((unsigned)((n - k) & (n - 1))) >> (32 - L));
-        const int qk = rk ^ (rk >> 5), qn = rn ^ (rn >> 5);
-        const float zr = s[fht_line<R, COL>(la, qk)], zi = s[fht_line<R, COL>(lb, qk)];
-        const float wr = s[fht_line<R, COL>(la, qn)], wi = s[fht_line<R, COL>(lb, qn)];
-        ha[j] = 0.5f * ((zr - zi) + (wr + wi));
-        hb[j] = 0.5f * ((zr + zi) + (wi - wr));
-    }
-    __syncwarp();
+    for (int M = 1; M <= R / 2; M <<= 1)
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int p = lane + 32 * j;
-        s[fht_line<R, COL>(la, p)] = ha[j];
-        s[fht_line<R, COL>(lb, p)] = hb[j];
-    }
-    __syncwarp();
+        for (int j = 0; j < R; ++j)
+            if ((j & M) == 0) {
+                const float2 a = v[j], b = fht_cmul(v[j + M], t.in[M - 1 + (j & (2 * M - 1))]);
+                v[j] = make_float2(a.x + b.x, a.y + b.y);
+                v[j + M] = make_float2(a.x - b.x, a.y - b.y);
+            }
 }
 
-// x and y transforms of z plane blockIdx.x: out[z] = Hy in[z] Hx.  With
-// partial != nullptr, partial[blockIdx.x] gets the compensated sum of the
-// output plane.
-template <int R>
+// Shared-memory word at byte offset off of the kernel's dynamic shared memory.
+__device__ __forceinline__ float& fht_s(unsigned off) {
+    extern __shared__ __align__(16) unsigned char fht_smem[];
+    return *reinterpret_cast<float*>(fht_smem + off);
+}
+
+// Highest set bit of x > 0 (as a value); 0 for x = 0.
+__host__ __device__ constexpr int fht_hibit(int x) {
+    int h = x ? 1 : 0;
+    while (h && h <= x / 2) h <<= 1;
+    return h;
+}
+
+// Hartley transforms, times 2, of two lines held as v[j] = (a, b) at point
+// lane + 32 j; on return v[j] = (2 Ha, 2 Hb) at position lane + 32 j.
+// Forward (INV false): points in natural order, coefficients in
+// bit-reversed order (DIF).  Inverse: points in bit-reversed order,
+// coefficients in natural order (DIT).  The split pairs each Z[k] with
+// Z[n - k], which another lane holds:
+//  - DIF output, position p = l + 32 j (Z[rev p]): Z[n - rev p] sits at
+//    p ^ (hibit(p) - 1), i.e. lane l ^ (hibit(l) - 1) for j = 0, else lane
+//    l ^ 31 and register j ^ (hibit(j) - 1);
+//  - DIT output, position m = l + 32 j: n - m is lane 32 - l, register
+//    R - 1 - j for l > 0, and register (R - j) mod R of lane 0 itself.
+// All 32 lanes of a warp call it.
+template <int R, bool INV>
+__device__ __forceinline__ void fht_pair(float2 (&v)[R], const FhtTw<R>& t, int lane) {
+    float2 w[R];
+    if constexpr (INV) {
+        warp_fft_dit<R>(v, t, lane);
+        const int src = (32 - lane) & 31;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            w[j].x = __shfl_sync(0xffffffffu, v[R - 1 - j].x, src);
+            w[j].y = __shfl_sync(0xffffffffu, v[R - 1 - j].y, src);
+            if (lane == 0) w[j] = v[(R - j) % R];
+        }
+    } else {
+        warp_fft_dif<R>(v, t, lane);
+        const int src0 = lane ? lane ^ ((1 << (31 - __clz(lane))) - 1) : 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int jp = j ? j ^ (fht_hibit(j) - 1) : 0;
+            const int src = j ? lane ^ 31 : src0;
+            w[j].x = __shfl_sync(0xffffffffu, v[jp].x, src);
+            w[j].y = __shfl_sync(0xffffffffu, v[jp].y, src);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        v[j] = make_float2((v[j].x - v[j].y) + (w[j].x + w[j].y), (v[j].x + v[j].y) + (w[j].y - w[j].x));
+}
+
+// The same for two lines in shared memory: point lane + 32 j of line a read
+// at byte ia + j JS, its coefficient written at oa + j JS (likewise for b).
+template <int R, bool INV, unsigned JS>
+__device__ __forceinline__ void warp_fht2(unsigned ia, unsigned ib, unsigned oa, unsigned ob, const FhtTw<R>& t,
+                                          int lane) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = make_float2(fht_s(ia + j * JS), fht_s(ib + j * JS));
+    fht_pair<R, INV>(v, t, lane);
+    __syncwarp();  // every lane has read its points before any writes in place
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        fht_s(oa + j * JS) = v[j].x;
+        fht_s(ob + j * JS) = v[j].y;
+    }
+}
+
+// Row pass: each warp's row pairs of the plane at src read straight from
+// global memory (all of them before the first transform), transformed, and
+// written swizzled into the plane at shared byte 0.
+template <int R, bool INV>
+__device__ __forceinline__ void fht_rows(const float* __restrict__ src, const FhtTw<R>& t, int warp, int lane) {
+    constexpr int n = 32 * R, W = fht_threads<R>() / 32, NT = n / 2 / W;
+    static_assert(NT * W == n / 2, "row pairs per warp");
+    float2 v[NT][R];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        const int r = 2 * (warp + i * W);
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            v[i][j] = make_float2(src[r * n + lane + 32 * j], src[(r + 1) * n + lane + 32 * j]);
+    }
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        const int r = 2 * (warp + i * W);
+        fht_pair<R, INV>(v[i], t, lane);
+        const unsigned oa = 4u * (unsigned)(r * n + (lane ^ (r & 31)));
+        const unsigned ob = 4u * (unsigned)((r + 1) * n + (lane ^ ((r + 1) & 31)));
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            fht_s(oa + 128u * j) = v[i][j].x;
+            fht_s(ob + 128u * j) = v[i][j].y;
+        }
+    }
+}
+
+// Column pass over the swizzled plane at byte 0, in place.
+template <int R, bool INV>
+__device__ __forceinline__ void fht_cols(const FhtTw<R>& t, int warp, int lane) {
+    constexpr int n = 32 * R, W = fht_threads<R>() / 32;
+    for (int p = warp; p < n / 2; p += W) {
+        const int c = 2 * p;
+        const unsigned a = 4u * (unsigned)(lane * n + (c ^ lane)), b = 4u * (unsigned)(lane * n + ((c + 1) ^ lane));
+        warp_fht2<R, INV, 128u * n>(a, b, a, b, t, lane);
+    }
+}
+
+// Shared memory of the FFT smoothing kernels at n points per axis: the
+// plane, and for k_fht_z the slice of S.
+inline size_t fht_smem_bytes(int n) { return (size_t)n * n * sizeof(float); }
+inline size_t fht_z_smem_bytes(int n) { return 2 * fht_smem_bytes(n); }
+
+// x and y transforms of z plane blockIdx.x: out[z] = 4 Hy in[z] Hx, forward
+// (natural order in, bit-reversed in x and y out) or inverse (the reverse).
+// With partial != nullptr, partial[blockIdx.x] gets the compensated sum of
+// the output plane.
+template <int R, bool INV>
 __global__ void __launch_bounds__(fht_threads<R>())
 k_fht_xy(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
          double* __restrict__ partial) {
-    constexpr int n = 32 * R, T = fht_threads<R>(), Q = n * n / 4;
+    constexpr int n = 32 * R, T = fht_threads<R>(), Q = n * n / 4, PER = (Q + T - 1) / T;
     extern __shared__ __align__(16) unsigned char fht_smem[];
     float* s = reinterpret_cast<float*>(fht_smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     FhtTw<R> t;
     fht_twiddles<R>(t, tw, lane);  // constant: before the wait
-    const int64_t base = (int64_t)blockIdx.x * n * n / 4;
+    const int64_t base = (int64_t)blockIdx.x * Q;
     pdl_wait();
     pdl_trigger();
-    const float4* src = reinterpret_cast<const float4*>(in) + base;
-    float4 f[(Q + T - 1) / T];
-#pragma unroll
-    for (int k = 0; k < (Q + T - 1) / T; ++k)
-        if (tid + k * T < Q) f[k] = src[tid + k * T];
-#pragma unroll
-    for (int k = 0; k < (Q + T - 1) / T; ++k) {
-        const int i = tid + k * T, r = 4 * i / n, c = 4 * i % n;
-        if (i < Q) *reinterpret_cast<float4*>(s + r * n + (c ^ (r & 28))) = fht_perm4(f[k], r & 3);
-    }
+    fht_rows<R, INV>(in + base * 4, t, warp, lane);
     __syncthreads();
-    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, false>(s, 2 * p, 2 * p + 1, t, lane);
-    __syncthreads();
-    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, true>(s, 2 * p, 2 * p + 1, t, lane);
+    fht_cols<R, INV>(t, warp, lane);
     __syncthreads();
     float4* dst = reinterpret_cast<float4*>(out) + base;
     float acc_s = 0.f, acc_c = 0.f;
 #pragma unroll
-    for (int k = 0; k < (Q + T - 1) / T; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const int i = tid + k * T, r = 4 * i / n, c = 4 * i % n;
         if (i < Q) {
-            const float4 o = fht_perm4(*reinterpret_cast<const float4*>(s + r * n + (c ^ (r & 28))), r & 3);
-            dst[i] = o;
+            const float4 v = fht_perm4(*reinterpret_cast<const float4*>(s + r * n + (c ^ (r & 28))), r & 3);
+            dst[i] = v;
             if (partial) {
-                two_sum_add(acc_s, acc_c, o.x);
-                two_sum_add(acc_s, acc_c, o.y);
-                two_sum_add(acc_s, acc_c, o.z);
-                two_sum_add(acc_s, acc_c, o.w);
+                two_sum_add(acc_s, acc_c, v.x);
+                two_sum_add(acc_s, acc_c, v.y);
+                two_sum_add(acc_s, acc_c, v.z);
+                two_sum_add(acc_s, acc_c, v.w);
             }
         }
     }
@@ -2285,11 +2382,12 @@ k_fht_xy(const float* __restrict__ in, float* __restrict__ out, const float2* __
     }
 }
 
-// For ky = blockIdx.x: z transform of the slice t[z][ky][x] (rows z,
-// columns x in shared memory), scaling by S (laid out like t; its slice
-// copied asynchronously into a second shared plane while the transform
-// runs, each 16-byte group at its position in the swizzled layout, in
-// natural order), and the z transform again, in place.
+// For ky = blockIdx.x: forward z transform of the slice t[z][ky][x] (rows
+// z, columns x of a swizzled plane in shared memory), scaling by S (laid
+// out like t, bit-reversed in all three indices; its slice copied
+// asynchronously into a second shared plane while the transform runs, each
+// 16-byte group at its swizzled position, in natural order), and the
+// inverse z transform, in place.
 template <int R>
 __global__ void __launch_bounds__(fht_threads<R>())
 k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __restrict__ S) {
@@ -2321,21 +2419,21 @@ k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __re
         if (i < Q) *reinterpret_cast<float4*>(s + z * n + (x ^ (z & 28))) = fht_perm4(f[k], z & 3);
     }
     __syncthreads();
-    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, true>(s, 2 * p, 2 * p + 1, t, lane);
+    fht_cols<R, false>(t, warp, lane);
     cp_async_wait<0>();
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int i = tid + k * T, z = 4 * i / n, x = 4 * i % n;
         if (i < Q) {
-            const int o = z * n + (x ^ (z & 28));
-            const float4 g = *reinterpret_cast<const float4*>(s + o);
-            const float4 w = fht_perm4(*reinterpret_cast<const float4*>(ss + o), z & 3);
-            *reinterpret_cast<float4*>(s + o) = make_float4(g.x * w.x, g.y * w.y, g.z * w.z, g.w * w.w);
+            const int e = z * n + (x ^ (z & 28));
+            const float4 g = *reinterpret_cast<const float4*>(s + e);
+            const float4 w = fht_perm4(*reinterpret_cast<const float4*>(ss + e), z & 3);
+            *reinterpret_cast<float4*>(s + e) = make_float4(g.x * w.x, g.y * w.y, g.z * w.z, g.w * w.w);
         }
     }
     __syncthreads();
-    for (int p = warp; p < n / 2; p += T / 32) warp_fht2<R, true>(s, 2 * p, 2 * p + 1, t, lane);
+    fht_cols<R, true>(t, warp, lane);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
@@ -2345,11 +2443,6 @@ k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __re
                 fht_perm4(*reinterpret_cast<const float4*>(s + z * n + (x ^ (z & 28))), z & 3);
     }
 }
-
-// Shared memory of the FFT smoothing kernels at n points per axis: the
-// plane, and for k_fht_z the slice of S.
-inline size_t fht_smem_bytes(int n) { return (size_t)n * n * sizeof(float); }
-inline size_t fht_z_smem_bytes(int n) { return 2 * fht_smem_bytes(n); }
 
 // Meshes the FFT smoothing handles.
 inline bool fht_supported(int n) { return n == 32 || n == 64 || n == kFhtMaxN; }

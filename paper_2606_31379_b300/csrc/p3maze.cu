@@ -41,6 +41,9 @@ struct Level {
     void* H = nullptr;
     void* D = nullptr;
     void* t = nullptr;
+    // mixed precision, n = 32 or 64: the coarse solve by FFT (D stored
+    // bit-reversed and scaled for those kernels), twiddles exp(-2 pi i k / n)
+    void* tw = nullptr;
     // FP32 levels with N % 4 == 0 that sweep: the other buffer of the
     // out-of-place full sweeps (level 0: the smoothing ping-pong buffer, free
     // during the solve), and the buffer (e or e2) that holds the level's
@@ -411,32 +414,92 @@ cudaError_t launch_diffuse_tq(p3maze_ctx* ctx, int S, bool last, bool pdl, const
     }
 }
 
-// Spectral smoothing by FFT (N = 32, 64, 128): the x-y transforms of q into
-// the smoothing ping-pong mesh, the z transforms and scaling in place, the
-// x-y transforms into q^s with per-plane sums, and the neutrality sum.
+// y = H3 (table o (H3 x)) by FFT (n = 32, 64, 128; the table bit-reversed
+// and scaled for the kernels): the x-y transforms of x into tmp, the z
+// transforms and scaling in place, the x-y transforms into y (with per-plane
+// sums when partial is given).  pdl_first: the first launch may overlap its
+// predecessor.
 template <int R>
-cudaError_t launch_fht_r(p3maze_ctx* ctx) {
-    cudaStream_t s = ctx->stream;
+cudaError_t launch_fht_r(bool pdl_first, bool pdl, cudaStream_t s, const float* x, float* tmp, float* y,
+                         const float2* tw, const float* table, double* partial) {
     const dim3 g(32 * R), b(fht_threads<R>());
     const size_t sm = fht_smem_bytes(32 * R);
-    float* t = (float*)ctx->lev[0].e;
-    const float2* tw = (const float2*)ctx->fht_tw;
-    cudaError_t e = launch_maybe_pdl(ctx->pdl, k_fht_xy<R>, g, b, sm, s, (const float*)ctx->q, t, tw, (double*)nullptr);
-    if (e == cudaSuccess)
-        e = launch_maybe_pdl(ctx->pdl, k_fht_z<R>, g, b, fht_z_smem_bytes(32 * R), s, t, tw, (const float*)ctx->Ssm);
-    if (e == cudaSuccess)
-        e = launch_maybe_pdl(ctx->pdl, k_fht_xy<R>, g, b, sm, s, (const float*)t, (float*)ctx->qs, tw, ctx->partial);
-    if (e == cudaSuccess)
-        e = launch_maybe_pdl(ctx->pdl, k_sum_final, dim3(1), dim3(1024), 0, s, 32 * R, (const double*)ctx->partial,
-                             ctx->dscal + S_QSUM);
+    cudaError_t e = launch_maybe_pdl(pdl_first, k_fht_xy<R, false>, g, b, sm, s, x, tmp, tw, (double*)nullptr);
+    if (e == cudaSuccess) e = launch_maybe_pdl(pdl, k_fht_z<R>, g, b, fht_z_smem_bytes(32 * R), s, tmp, tw, table);
+    if (e == cudaSuccess) e = launch_maybe_pdl(pdl, k_fht_xy<R, true>, g, b, sm, s, (const float*)tmp, y, tw, partial);
     return e;
 }
-cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
-    switch (ctx->N) {
-        case 32: return launch_fht_r<1>(ctx);
-        case 64: return launch_fht_r<2>(ctx);
-        default: return launch_fht_r<4>(ctx);
+cudaError_t launch_fht(int n, bool pdl_first, bool pdl, cudaStream_t s, const float* x, float* tmp, float* y,
+                       const float2* tw, const float* table, double* partial) {
+    switch (n) {
+        case 32: return launch_fht_r<1>(pdl_first, pdl, s, x, tmp, y, tw, table, partial);
+        case 64: return launch_fht_r<2>(pdl_first, pdl, s, x, tmp, y, tw, table, partial);
+        default: return launch_fht_r<4>(pdl_first, pdl, s, x, tmp, y, tw, table, partial);
     }
+}
+
+// Spectral smoothing by FFT: q into q^s through the smoothing ping-pong
+// mesh, and the neutrality sum of the per-plane sums.
+cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
+    cudaError_t e = launch_fht(ctx->N, ctx->pdl, ctx->pdl, ctx->stream, (const float*)ctx->q, (float*)ctx->lev[0].e,
+                               (float*)ctx->qs, (const float2*)ctx->fht_tw, (const float*)ctx->Ssm, ctx->partial);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(ctx->pdl, k_sum_final, dim3(1), dim3(1024), 0, ctx->stream, ctx->N,
+                             (const double*)ctx->partial, ctx->dscal + S_QSUM);
+    return e;
+}
+
+// Bit-reversed position of each index 0..n-1 (n a power of two).
+std::vector<int> fht_positions(int n) {
+    int bits = 0;
+    while ((1 << bits) < n) ++bits;
+    std::vector<int> pos(n);
+    for (int k = 0; k < n; ++k) {
+        int r = 0;
+        for (int b = 0; b < bits; ++b) r |= ((k >> b) & 1) << (bits - 1 - b);
+        pos[k] = r;
+    }
+    return pos;
+}
+
+// Twiddles exp(-2 pi i k / n), k < n / 2, from FP64.
+std::vector<float2> fht_twiddle_table(int n) {
+    std::vector<float2> tw(n / 2);
+    for (int k = 0; k < n / 2; ++k)
+        tw[k] = make_float2((float)std::cos(2.0 * kPi * k / n), (float)-std::sin(2.0 * kPi * k / n));
+    return tw;
+}
+
+// Raise the shared-memory limit of the FFT kernels for n points per axis.
+// The limit is an attribute of the kernel, shared by every context in the
+// process: only ever raise it.
+cudaError_t fht_raise_smem(int n) {
+    auto raise = [](const void* fn, size_t sm) {
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+        if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < sm)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        return e;
+    };
+    const size_t sxy = fht_smem_bytes(n), sz = fht_z_smem_bytes(n);
+    const void* k[3];
+    if (n == 32) {
+        k[0] = (const void*)k_fht_xy<1, false>;
+        k[1] = (const void*)k_fht_xy<1, true>;
+        k[2] = (const void*)k_fht_z<1>;
+    } else if (n == 64) {
+        k[0] = (const void*)k_fht_xy<2, false>;
+        k[1] = (const void*)k_fht_xy<2, true>;
+        k[2] = (const void*)k_fht_z<2>;
+    } else {
+        k[0] = (const void*)k_fht_xy<4, false>;
+        k[1] = (const void*)k_fht_xy<4, true>;
+        k[2] = (const void*)k_fht_z<4>;
+    }
+    cudaError_t e = raise(k[0], sxy);
+    if (e == cudaSuccess) e = raise(k[1], sxy);
+    if (e == cudaSuccess) e = raise(k[2], sz);
+    return e;
 }
 
 // All diffusion steps of `members` meshes (table on the device, N <= nmax,
@@ -694,6 +757,13 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
         pdl = ctx->pdl;
         return err;
     };
+    if (l == ctx->lc && L.tw) {
+        CK(launch_fht(L.n, pdl, ctx->pdl, s, (const float*)b, (float*)L.t, (float*)e, (const float2*)L.tw,
+                      (const float*)L.D, nullptr));
+        count(ctx, P3MAZE_ST_SOLVE, 3);
+        L.fin = e;
+        return P3MAZE_OK;
+    }
     if (l == ctx->lc) {
         const size_t sm = coarse_smem_bytes(L.n, sizeof(T));
         const dim3 gc(L.n), bc(kCoarseThreads);
@@ -1549,7 +1619,23 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         if (!L.H) continue;
         std::vector<double> H, D;
         hartley_tables(L.n, H, D);
-        if (mixed) {
+        if (mixed && fht_supported(L.n)) {
+            // the FFT kernels: D bit-reversed in all three indices, 2^-6 for
+            // their six doubled transforms
+            const int n = L.n;
+            const std::vector<int> pos = fht_positions(n);
+            std::vector<float> Df(D.size());
+            for (int kz = 0; kz < n; ++kz)
+                for (int ky = 0; ky < n; ++ky)
+                    for (int kx = 0; kx < n; ++kx)
+                        Df[((size_t)pos[kz] * n + pos[ky]) * n + pos[kx]] =
+                            (float)(D[((size_t)kz * n + ky) * n + kx] / 64.0);
+            CK(cudaMemcpy(L.D, Df.data(), 4 * Df.size(), cudaMemcpyHostToDevice));
+            const std::vector<float2> tw = fht_twiddle_table(n);
+            ALLOC(L.tw, sizeof(float2) * tw.size());
+            CK(cudaMemcpy(L.tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+            CK(fht_raise_smem(n));
+        } else if (mixed) {
             std::vector<float> Hf(H.begin(), H.end()), Df(D.begin(), D.end());
             CK(cudaMemcpy(L.H, Hf.data(), 4 * Hf.size(), cudaMemcpyHostToDevice));
             CK(cudaMemcpy(L.D, Df.data(), 4 * Df.size(), cudaMemcpyHostToDevice));
@@ -1569,32 +1655,27 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         }
         std::vector<float> S((size_t)N * N * N);
         const double inv_n3 = 1.0 / ((double)N * N * N);
+        // the FFT kernels form twice each Hartley transform (2^-6 for the six)
+        // and keep the coefficients in bit-reversed order
+        const bool fft = fht_supported(N);
+        const double fht_scale = fft ? 1.0 / 64.0 : 1.0;
+        std::vector<int> pos = fht_positions(N);
+        if (!fft)
+            for (int k = 0; k < N; ++k) pos[k] = k;
         for (int kz = 0; kz < N; ++kz)
             for (int ky = 0; ky < N; ++ky)
                 for (int kx = 0; kx < N; ++kx) {
                     const double g = 1.0 - 4.0 * ctx->c * (s2[kx] + s2[ky] + s2[kz]);
-                    S[((size_t)kz * N + ky) * N + kx] = (float)(std::pow(g, ctx->K) * inv_n3);
+                    S[((size_t)pos[kz] * N + pos[ky]) * N + pos[kx]] =
+                        (float)(std::pow(g, ctx->K) * inv_n3 * fht_scale);
                 }
         ALLOC(ctx->Ssm, 4 * S.size());
         CK(cudaMemcpy(ctx->Ssm, S.data(), 4 * S.size(), cudaMemcpyHostToDevice));
-        if (fht_supported(N)) {
-            std::vector<float2> tw(N / 2);
-            for (int k = 0; k < N / 2; ++k)
-                tw[k] = make_float2((float)std::cos(2.0 * kPi * k / N), (float)-std::sin(2.0 * kPi * k / N));
+        if (fft) {
+            const std::vector<float2> tw = fht_twiddle_table(N);
             ALLOC(ctx->fht_tw, sizeof(float2) * tw.size());
             CK(cudaMemcpy(ctx->fht_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
-            // the shared-memory limit of a kernel is shared by every context: only ever raise it
-            auto raise = [&](const void* fn, size_t sm) {
-                cudaFuncAttributes fa{};
-                cudaError_t e = cudaFuncGetAttributes(&fa, fn);
-                if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < sm)
-                    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                return e;
-            };
-            if (N == 128) {
-                CK(raise((const void*)k_fht_xy<4>, fht_smem_bytes(N)));
-                CK(raise((const void*)k_fht_z<4>, fht_z_smem_bytes(N)));
-            }
+            CK(fht_raise_smem(N));
         }
         ctx->fuse = 6;  // the default for such meshes: fastest alone and in a batch graph
     }
@@ -1674,6 +1755,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
         if (l == 0) b += a(tb * pts);
         if (mixed && nn % 4 == 0 && l > 0 && l + 1 < nlev) b += a(tb * pts);  // e2
         if (nn <= kCoarseMax) b += a(tb * (size_t)nn * nn) + a(tb * pts) + a(tb * pts);  // H D t
+        if (mixed && nn <= kCoarseMax && fht_supported(nn)) b += a(sizeof(float2) * (size_t)(nn / 2));  // tw
         nn /= 2;
     }
     b += a(8 * (size_t)partial_slots(N));
