@@ -1153,6 +1153,8 @@ k_update_fix(int64_t m, const fix_t* __restrict__ phik, fix_t* __restrict__ phik
              const double* __restrict__ qsum, double inv_pts, float u, float* __restrict__ phi32) {
     __shared__ float mean_s;
     __shared__ fix_t ref_s;
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0) {
         mean_s = (float)(qsum[0] * inv_pts);
         ref_s = phik[0];
@@ -2458,6 +2460,8 @@ __global__ void __launch_bounds__(P3_THREADS)
 k_gather(int np, const PQ* __restrict__ xq, const int* __restrict__ order, int n, double inv_h,
          double ke, const R* __restrict__ phi, const double* __restrict__ Fsr_s,
          double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr) {
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
     const PQ p = xq[s];
@@ -2525,6 +2529,8 @@ static __global__ void __launch_bounds__(P3_THREADS)
 k_gather_mp(int np, const MeshPt* __restrict__ mp, const int* __restrict__ order, int n, double inv_h,
             double ke, const float* __restrict__ phi, const double* __restrict__ Fsr_s,
             double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr) {
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= np) return;
     const MeshPt p = mp[s];

@@ -293,6 +293,27 @@ int leave(p3maze_ctx* ctx) {
 
 
 // ------------------------------------------------------------------ pipeline
+// Launch with programmatic stream serialisation when pdl is set: the grid may
+// be scheduled while its predecessor in the stream is still running, and
+// its blocks wait in pdl_wait() until the predecessor has completed and its
+// writes are visible.  Only kernels that call pdl_wait() before their first
+// memory access may be launched this way.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Systems of at most 2048 particles (two per thread) build the cell list in
 // one block with shared-memory counts; larger ones use the multi-kernel path
 // (one SM walking 32768 particles takes about 90 us, three times longer).
@@ -306,23 +327,28 @@ int build_cells(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_CELLS);
     int launches = 1;
+    // every launch may overlap its predecessor's tail (programmatic dependent
+    // launch); the per-cell counts are zero on entry (cleared at setup and by
+    // k_cell_sort once the scan has used them)
+    const bool pdl = ctx->pdl;
     if (cells_in_one_block(ctx->np, ctx->ncell)) {
-        k_cells_block<<<1, kCellBlockThreads, cells_block_smem(ctx->ncell), s>>>(
-            ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->ncell, ctx->cell, ctx->start, ctx->order);
+        CK(launch_maybe_pdl(pdl, k_cells_block, dim3(1), dim3(kCellBlockThreads), cells_block_smem(ctx->ncell), s,
+                            ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->ncell, ctx->cell, ctx->start, ctx->order));
         launches += 1;
     } else {
-        CK(cudaMemsetAsync(ctx->count, 0, sizeof(int) * ctx->ncell, s));
-        k_cell_count<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->cell,
-                                                          ctx->count);
-        k_scan_cells<<<1, kScanThreads, 0, s>>>(ctx->ncell, ctx->count, ctx->start, ctx->fill);
-        k_cell_scatter<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->cell, ctx->start, ctx->fill, ctx->order);
-        k_cell_sort<<<nblk(ctx->ncell), P3_THREADS, 0, s>>>(ctx->ncell, ctx->start, ctx->order);
+        CK(launch_maybe_pdl(pdl, k_cell_count, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->r,
+                            ctx->inv_cell, ctx->nc, ctx->cell, ctx->count));
+        CK(launch_maybe_pdl(pdl, k_scan_cells, dim3(1), dim3(kScanThreads), 0, s, ctx->ncell, ctx->count, ctx->start,
+                            ctx->fill));
+        CK(launch_maybe_pdl(pdl, k_cell_scatter, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->cell,
+                            ctx->start, ctx->fill, ctx->order));
+        CK(launch_maybe_pdl(pdl, k_cell_sort, dim3(nblk(ctx->ncell)), dim3(P3_THREADS), 0, s, ctx->ncell, ctx->start,
+                            ctx->order, ctx->count));
         launches += 4;
     }
-    k_gather_sorted<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->order, ctx->r, ctx->Q, ctx->type, ctx->mol,
-                                                         ctx->cell, ctx->nc, ctx->lcell, ctx->xq, ctx->xl64,
-                                                         ctx->xl32, ctx->ts, ctx->ms, ctx->cs, ctx->mp, ctx->N,
-                                                         ctx->inv_h);
+    CK(launch_maybe_pdl(pdl, k_gather_sorted, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->order,
+                        ctx->r, ctx->Q, ctx->type, ctx->mol, ctx->cell, ctx->nc, ctx->lcell, ctx->xq, ctx->xl64,
+                        ctx->xl32, ctx->ts, ctx->ms, ctx->cs, ctx->mp, ctx->N, ctx->inv_h));
     CKL();
     count(ctx, P3MAZE_ST_CELLS, launches);
     stage_end(ctx, P3MAZE_ST_CELLS);
@@ -364,26 +390,6 @@ void launch_diffuse_tb(p3maze_ctx* ctx, int S, bool last, const T* src, T* dst) 
 // Planes per thread of k_diffuse4 for a tuning value zc (1, 2, 4 or 8).
 inline int diffuse4_planes(int zc) { return zc <= 1 ? 1 : zc <= 2 ? 2 : zc <= 4 ? 4 : 8; }
 
-// Launch with programmatic stream serialisation when pdl is set: the grid may
-// be scheduled while its predecessor in the stream is still running, and
-// its blocks wait in pdl_wait() until the predecessor has completed and its
-// writes are visible.  Only kernels that call pdl_wait() before their first
-// memory access may be launched this way.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_maybe_pdl(bool pdl, void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
-                             Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = g;
-    cfg.blockDim = b;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
-}
 
 // FP32 quads (N % 4 == 0): the asynchronous-copy temporal blocking, a
 // 56 x (32 - 2S) output tile per block.
@@ -597,15 +603,15 @@ int spread_assign(p3maze_ctx* ctx) {
     // deterministic tiled assignment: every mesh point written once
     if constexpr (sizeof(T) == 4) {
         if (ctx->N % 4 == 0)
-            CK(launch_maybe_pdl(false, k_spread_tile<float, MeshPt, true>, spread_grid(ctx->N), dim3(kSpThreads),
+            CK(launch_maybe_pdl(ctx->pdl, k_spread_tile<float, MeshPt, true>, spread_grid(ctx->N), dim3(kSpThreads),
                                 spread_smem_bytes<float>(), s, ctx->N, ctx->nc, (const int*)ctx->start,
                                 (const MeshPt*)ctx->mp, ctx->inv_h, (float*)ctx->q));
         else
-            CK(launch_maybe_pdl(false, k_spread_tile<float, MeshPt, false>, spread_grid(ctx->N), dim3(kSpThreads),
+            CK(launch_maybe_pdl(ctx->pdl, k_spread_tile<float, MeshPt, false>, spread_grid(ctx->N), dim3(kSpThreads),
                                 spread_smem_bytes<float>(), s, ctx->N, ctx->nc, (const int*)ctx->start,
                                 (const MeshPt*)ctx->mp, ctx->inv_h, (float*)ctx->q));
     } else {
-        CK(launch_maybe_pdl(false, k_spread_tile<double, PQ, false>, spread_grid(ctx->N), dim3(kSpThreads),
+        CK(launch_maybe_pdl(ctx->pdl, k_spread_tile<double, PQ, false>, spread_grid(ctx->N), dim3(kSpThreads),
                             spread_smem_bytes<double>(), s, ctx->N, ctx->nc, (const int*)ctx->start,
                             (const PQ*)ctx->xq, ctx->inv_h, (double*)ctx->q));
     }
@@ -983,10 +989,11 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     stage_begin(ctx, P3MAZE_ST_PREDICT);
     if (fixp) {
 #define P3_PREDICT(ORD)                                                                                           \
-    k_predict_resid_fix<ORD><<<resid_grid(ctx->N), kB3, 0, s>>>(                                                  \
-        ctx->N, fx(ctx->psi[ik]), fx(ctx->psi[ikm1]), (const float*)ctx->qs, ctx->dscal + S_QSUM,                 \
-        1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h), fx(ctx->yh[1]), fx(ctx->yh[2]), fx(ctx->yh[3]),       \
-        fx(ctx->yh[0]), fx(ctx->rfin), (float*)ctx->lev[0].b, check_args(ctx, h, use_handle))
+    CK(launch_maybe_pdl(ctx->pdl, k_predict_resid_fix<ORD>, resid_grid(ctx->N), kB3, 0, s, ctx->N,                \
+                        fx(ctx->psi[ik]), fx(ctx->psi[ikm1]), (const float*)ctx->qs, ctx->dscal + S_QSUM,         \
+                        1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h), fx(ctx->yh[1]), fx(ctx->yh[2]),       \
+                        fx(ctx->yh[3]), fx(ctx->yh[0]), fx(ctx->rfin), (float*)ctx->lev[0].b,                    \
+                        check_args(ctx, h, use_handle)))
         switch (pred_order) {
             case 0: P3_PREDICT(0); break;
             case 1: P3_PREDICT(1); break;
@@ -1008,10 +1015,10 @@ int solve_field(p3maze_ctx* ctx, int pred_order) {
     stage_end(ctx, P3MAZE_ST_SOLVE);
     stage_begin(ctx, P3MAZE_ST_UPDATE);
     if (fixp)
-        k_update_fix<<<nblk(ctx->P), P3_THREADS, 0, s>>>(
-            ctx->P, fx(ctx->phi[ik]), fx(ctx->phi[ikm1]), fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
-            (const float*)ctx->qs, ctx->dscal + S_QSUM, 1.0 / (double)ctx->P, (float)(4.0 * kPi / ctx->h),
-            ctx->phi32);
+        CK(launch_maybe_pdl(ctx->pdl, k_update_fix, dim3(nblk(ctx->P)), dim3(P3_THREADS), 0, s, ctx->P,
+                            fx(ctx->phi[ik]), fx(ctx->phi[ikm1]), fx(ctx->psi[ikm1]), fx(ctx->yh[0]), fx(ctx->rfin),
+                            (const float*)ctx->qs, ctx->dscal + S_QSUM, 1.0 / (double)ctx->P,
+                            (float)(4.0 * kPi / ctx->h), ctx->phi32));
     else
         k_update<T><<<update_blocks(ctx->N), P3_THREADS, 0, s>>>(
             ctx->P, ctx->phi[ik], ctx->phi[ikm1], ctx->psi[ikm1], ctx->yh[0], ctx->rfin, (const T*)ctx->qs,
@@ -1033,6 +1040,12 @@ int pair_forces(p3maze_ctx* ctx) {
     cudaStream_t main = ctx->stream;
     CK(cudaEventRecord(ctx->ev_fork, main));
     CK(cudaStreamWaitEvent(ctx->pair_stream, ctx->ev_fork, 0));
+    // the positions of this step are final (drift done): p3maze_step_host's
+    // copy-out may start.  Recorded here, beside the fork's own event node,
+    // so that no chain of dependent launches is cut by one more node (an
+    // external record when capturing: an event node of the step graph)
+    CK(ctx->capturing ? cudaEventRecordWithFlags(ctx->ev_drift, main, cudaEventRecordExternal)
+                      : cudaEventRecord(ctx->ev_drift, main));
     ctx->stream = ctx->pair_stream;
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_PAIR);
@@ -1093,12 +1106,13 @@ int gather_forces(p3maze_ctx* ctx) {
                                                                  ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F,
                                                                  ctx->Flr, ctx->Fsr);
     } else if (mixed) {
-        k_gather_mp<<<nblk(ctx->np), P3_THREADS, 0, s>>>(
-            ctx->np, ctx->mp, ctx->order, ctx->N, ctx->inv_h, ctx->ke, ctx->phi32, ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr);
+        CK(launch_maybe_pdl(ctx->pdl, k_gather_mp, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->mp,
+                            ctx->order, ctx->N, ctx->inv_h, ctx->ke, (const float*)ctx->phi32, (const double*)ctx->Fs,
+                            ctx->F, ctx->Flr, ctx->Fsr));
     } else {
-        k_gather<double><<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->xq, ctx->order, ctx->N, ctx->inv_h,
-                                                              ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F, ctx->Flr,
-                                                              ctx->Fsr);
+        CK(launch_maybe_pdl(ctx->pdl, k_gather<double>, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np,
+                            (const PQ*)ctx->xq, (const int*)ctx->order, ctx->N, ctx->inv_h, ctx->ke,
+                            (const double*)ctx->phi[ctx->icur], (const double*)ctx->Fs, ctx->F, ctx->Flr, ctx->Fsr));
     }
     count(ctx, P3MAZE_ST_GATHER);
     if (ctx->nmol) {
@@ -1200,12 +1214,10 @@ int step_body(p3maze_ctx* ctx, int order) {
     count(ctx, P3MAZE_ST_INTEGRATE);
     stage_end(ctx, P3MAZE_ST_INTEGRATE);
     CKL();
-    // an event node of the step graph when capturing (an external record)
-    CK(ctx->capturing ? cudaEventRecordWithFlags(ctx->ev_drift, s, cudaEventRecordExternal)
-                      : cudaEventRecord(ctx->ev_drift, s));
     int rc = field_and_forces(ctx, order);
     if (rc) return rc;
-    k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
+    CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
+                        (const double*)ctx->F, (const double*)ctx->hdt_acc));
     count(ctx, P3MAZE_ST_GATHER);
     stage_end(ctx, P3MAZE_ST_GATHER);
     CKL();
@@ -1230,9 +1242,6 @@ int step_head(p3maze_ctx* ctx) {
     count(ctx, P3MAZE_ST_INTEGRATE);
     stage_end(ctx, P3MAZE_ST_INTEGRATE);
     CKL();
-    // an event node of the step graph when capturing (an external record)
-    CK(ctx->capturing ? cudaEventRecordWithFlags(ctx->ev_drift, s, cudaEventRecordExternal)
-                      : cudaEventRecord(ctx->ev_drift, s));
     int rc = build_cells(ctx);
     return rc ? rc : spread_assign<float>(ctx);
 }
@@ -1243,7 +1252,8 @@ int step_tail(p3maze_ctx* ctx, int order) {
     if (!rc) rc = gather_forces(ctx);
     if (rc) return rc;
     cudaStream_t s = ctx->stream;
-    k_kick<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->v, ctx->F, ctx->hdt_acc);
+    CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
+                        (const double*)ctx->F, (const double*)ctx->hdt_acc));
     count(ctx, P3MAZE_ST_GATHER);
     stage_end(ctx, P3MAZE_ST_GATHER);
     CKL();
@@ -1506,6 +1516,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     ALLOC(ctx->evs, 8 * (size_t)n);
     ALLOC(ctx->wsr, 8 * (size_t)n);
     ALLOC(ctx->count, 4 * (size_t)ctx->ncell);
+    CK(cudaMemset(ctx->count, 0, 4 * (size_t)ctx->ncell));  // k_cell_sort keeps it zero between builds
     ALLOC(ctx->fill, 4 * (size_t)ctx->ncell);
     ALLOC(ctx->start, 4 * ((size_t)ctx->ncell + 1));
     if (p->types) ALLOC(ctx->type, 4 * (size_t)n);

@@ -10,6 +10,8 @@ namespace p3 {
 // v += (dt/2) F / m.  hdt_acc[i] = 0.5 dt ACCEL / m_i.
 static __global__ void k_kick(int n, double* __restrict__ v, const double* __restrict__ F,
                        const double* __restrict__ hdt_acc) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double a = hdt_acc[i];
@@ -70,6 +72,8 @@ static __global__ void k_wrap_check(int n, double* __restrict__ r, const double*
 // and per-cell counts.
 static __global__ void k_cell_count(int n, const double* __restrict__ r, double inv_cell, int nc,
                              int* __restrict__ cell, int* __restrict__ count) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     // clamped on both sides so that a non-finite position cannot index out of
@@ -100,6 +104,8 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_cells(int m, const
                                                                   int* __restrict__ start, int* __restrict__ fill) {
     __shared__ int tile[kScanTile + kScanTile / 32];
     __shared__ int warp_tot[kScanThreads / 32];
+    pdl_wait();
+    pdl_trigger();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int carry = 0;
     for (int t0 = 0; t0 < m; t0 += kScanTile) {
@@ -158,16 +164,23 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_cells(int m, const
 
 static __global__ void k_cell_scatter(int n, const int* __restrict__ cell, const int* __restrict__ start,
                                int* __restrict__ fill, int* __restrict__ order) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = cell[i];
     order[start[c] + atomicAdd(&fill[c], 1)] = i;
 }
 
-// Sort each cell's members by particle index so the order is deterministic.
-static __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __restrict__ order) {
+// Sort each cell's members by particle index so the order is deterministic,
+// and clear the cell's count for the next build (the scan has consumed it).
+static __global__ void k_cell_sort(int m, const int* __restrict__ start, int* __restrict__ order,
+                                   int* __restrict__ count) {
+    pdl_wait();
+    pdl_trigger();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m) return;
+    count[c] = 0;
     const int b = start[c], e = start[c + 1];
     for (int j = b + 1; j < e; ++j) {
         const int key = order[j];
@@ -195,6 +208,8 @@ k_cells_block(int n, const double* __restrict__ r, double inv_cell, int nc, int 
     int* cnt = cell_smem;            // counts, then fill counters
     int* st = cell_smem + ncell;     // exclusive prefix
     __shared__ int wsum[kCellBlockThreads / 32];
+    pdl_wait();
+    pdl_trigger();
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int c = tid; c < ncell; c += nt) cnt[c] = 0;
     __syncthreads();
@@ -269,6 +284,8 @@ static __global__ void k_gather_sorted(int n, const int* __restrict__ order, con
                                 double lcell, PQ* __restrict__ xq, PQ* __restrict__ xl64,
                                 float4* __restrict__ xl32, int* __restrict__ ts, int* __restrict__ ms,
                                 int* __restrict__ cs, MeshPt* __restrict__ mp, int nm, double inv_h) {
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int i = order[s];
