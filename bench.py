@@ -220,15 +220,43 @@ class ClockSampler:
 # ----------------------------------------------------------------- roofline
 def smoothing_launches(K: int, fuse: int) -> int:
     """Diffusion launches per MD step: one per step, or two steps per launch
-    (a single step first when K is odd), or fuse > 2 steps per launch."""
+    (a single step first when K is odd), or fuse = 3, 4 steps per launch;
+    all steps in one cluster launch (5) or three transform launches (6)."""
     if fuse == 2:
         return K // 2 + K % 2
+    if fuse == 5:
+        return 1
+    if fuse == 6:
+        return 3
     if fuse > 2:
         return -(-K // fuse)
     return K
 
 
-def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int, fuse: int = 1) -> tuple[float, int]:
+def fft_smoothing_flops(n: int) -> float:
+    """Algorithmic FP32 operations of one spectral smoothing by FFT on an n^3
+    mesh: six passes of n^2 / 2 complex radix-2 FFTs of length n (5 n log2 n
+    each, the textbook count), the split of each into two Hartley lines
+    (3 per output point), and the scaling (1 per point)."""
+    lg = math.log2(n)
+    return 6.0 * (2.5 * n ** 3 * lg + 3.0 * n ** 3) + n ** 3
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 148) -> float:
+    """FP32 peak from unit counts: 128 FP32 lanes per SM (four sub-partitions
+    of 32), one FMA (2 operations) per lane per clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# kernel of each mesh stage (mixed precision / FP64)
+STAGE_KERNEL = {"spread": ("k_spread_tile", "k_spread_tile"),
+                "predict": ("k_predict_resid_fix", "k_predict"),
+                "update": ("k_update_fix", "k_update"),
+                "gather": ("k_gather_mp", "k_gather")}
+
+
+def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int, fuse: int = 1,
+                      order: int = 3) -> tuple[float, int]:
     """Compulsory bytes of one launch of the stage's main kernel and the
     launches per step.  b = bytes of a bulk mesh value, P = mesh points.
     A smoothing launch (one diffusion step, or several fused) reads the mesh
@@ -237,8 +265,9 @@ def algorithmic_bytes(stage: str, b: int, P: int, npart: int, K: int, fuse: int 
         return 2.0 * P * b, smoothing_launches(K, fuse)
     if stage == "spread":        # write q once, read 32 B per particle
         return P * b + 32.0 * npart, 1
-    if stage == "predict":       # read phi^k, phi^{k-1}, q^s, 3 y histories; write sigma_p, y0
-        return P * (8 + 8 + b + 24 + 16), 1
+    if stage == "predict":       # read Psi^k, Psi^{k-1}, q^s and `order` multiplier histories (8 B each);
+        # write the residual and the guess y0 (8 B each), in mixed mode also the FP32 residual copy
+        return P * (8 + 8 + b + 8 * order + 16 + (4 if b == 4 else 0)), 1
     if stage == "update":        # read phi^k, phi^{k-1}, y; write phi^{k+1}
         return P * 32.0, 1
     if stage == "gather":        # read phi once, 32 B per particle in, 3 x 24 B out
@@ -495,6 +524,9 @@ def run_ours(args) -> int:
     torch.cuda.nvtx.range_push("timed")
     with ClockSampler(gpu_id) as clk:
         ms = time_context(ctx, torch, stream, args.steps)
+    clocks = clk.summary()
+    fuse_used = ctx.tuning()["diffusion_fuse"]
+    pred_used = ctx.tuning()["predictor"]
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
@@ -608,20 +640,38 @@ def run_ours(args) -> int:
     mesh_stages = ("smooth", "spread", "predict", "update", "gather")
     dom = max(mesh_stages, key=lambda k: stage_us[k])
     peaks = measured_peaks()
-    bytes_per_launch, launches_per_step = algorithmic_bytes(dom, b, P3, system.n, K_smooth,
-                                                            (tuning or {}).get("diffusion_fuse", 1))
-    launch_us = stage_us[dom] / launches_per_step
-    achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
-    fuse = (tuning or {}).get("diffusion_fuse", 1)
-    smooth_kernel = (f"k_diffuse_tb ({fuse} steps per launch)" if fuse > 2 else
-                     "k_diffuse4x2" if fuse == 2 else
-                     "k_diffuse4" if args.precision == "mixed" else "k_diffuse")
-    roofline = {"bound": "hbm", "kernel": dom if dom != "smooth" else smooth_kernel,
-                "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": recorded_traffic(smooth_kernel if dom == "smooth" else dom, WORKLOAD, args.precision),
-                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
-                "launch_us": launch_us}
+    fuse = fuse_used
+    if dom == "smooth" and fuse == 6:
+        # spectral smoothing by FFT: FP32 arithmetic on L2-resident planes,
+        # bound by instruction issue and shared-memory/shuffle traffic, not
+        # HBM: reported against the FP32 peak from unit counts and the clock
+        # sampled during the timed steps
+        sm_mhz = clocks.get("sm_mhz") or 2032.0
+        flops = fft_smoothing_flops(prm["mesh"])
+        launch_us = stage_us["smooth"] / 3.0
+        achieved = flops / 3.0 / (launch_us * 1e-6) / 1e12
+        peak = fp32_peak_tflops(sm_mhz)
+        roofline = {"bound": "alu", "kernel": "k_fht_xy / k_fht_z (spectral smoothing by FFT, three launches)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": recorded_traffic("k_fht_xy", WORKLOAD, args.precision),
+                    "peak_source": f"FP32 units: 148 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz",
+                    "algorithmic_flops_per_launch": flops / 3.0, "launch_us": launch_us}
+    else:
+        bytes_per_launch, launches_per_step = algorithmic_bytes(dom, b, P3, system.n, K_smooth, fuse,
+                                                                pred_used)
+        launch_us = stage_us[dom] / launches_per_step
+        achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
+        if dom == "smooth":
+            kernel = (f"k_diffuse_tq ({fuse} steps per launch)" if fuse in (3, 4) else
+                      "k_diffuse_cluster" if fuse == 5 else "k_diffuse4x2" if fuse == 2 else
+                      "k_diffuse4" if args.precision == "mixed" else "k_diffuse")
+        else:
+            kernel = STAGE_KERNEL[dom][0 if args.precision == "mixed" else 1]
+        roofline = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": recorded_traffic(kernel, WORKLOAD, args.precision),
+                    "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
+                    "launch_us": launch_us}
     line = {
         "metric": METRIC, "value": value, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -636,7 +686,7 @@ def run_ours(args) -> int:
         "gpu_launches_per_step": launches / args.steps,
         "ms_per_step_with_stage_events": sum(ms_staged) / args.steps,
         "ms_per_step_l2_flushed": max_over_ranks(sum(ms_flushed), world, device="cuda") / args.steps,
-        "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "variants": variants,
+        "roofline": roofline, "clocks": clocks, "e2e": e2e, "variants": variants,
         "accuracy_vs_oracle": accuracy,
         "roofline_alone": {
             "kernel": "k_diffuse4 (one diffusion step per launch, 2 planes per thread, nothing beside it)",
