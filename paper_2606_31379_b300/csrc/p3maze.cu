@@ -237,6 +237,15 @@ int dalloc(p3maze_ctx* ctx, P** p, size_t bytes) {
         if (rc_) return rc_;                               \
     } while (0)
 
+// Host array -> device array on the context's stream, complete on return (the
+// source may be a temporary).  A plain cudaMemcpy runs on the legacy default
+// stream, which the context's non-blocking streams are not ordered after.
+#define UPLOAD(dst, src, bytes)                                                                  \
+    do {                                                                                         \
+        CK(cudaMemcpyAsync((dst), (src), (size_t)(bytes), cudaMemcpyHostToDevice, ctx->stream)); \
+        CK(cudaStreamSynchronize(ctx->stream));                                                  \
+    } while (0)
+
 // Count `k` kernel launches of stage `st` (into the while-body tally while
 // capturing the body).
 inline void count(p3maze_ctx* ctx, int st, int k = 1) {
@@ -1516,7 +1525,10 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
     ALLOC(ctx->evs, 8 * (size_t)n);
     ALLOC(ctx->wsr, 8 * (size_t)n);
     ALLOC(ctx->count, 4 * (size_t)ctx->ncell);
-    CK(cudaMemset(ctx->count, 0, 4 * (size_t)ctx->ncell));  // k_cell_sort keeps it zero between builds
+    // zero before the first build (on the context's stream: the legacy default
+    // stream of a plain cudaMemset is not ordered with it); k_cell_sort keeps
+    // it zero between builds
+    CK(cudaMemsetAsync(ctx->count, 0, 4 * (size_t)ctx->ncell, ctx->stream));
     ALLOC(ctx->fill, 4 * (size_t)ctx->ncell);
     ALLOC(ctx->start, 4 * ((size_t)ctx->ncell + 1));
     if (p->types) ALLOC(ctx->type, 4 * (size_t)n);
@@ -1608,7 +1620,7 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
         ALLOC(ctx->cltab, sizeof(ClusterMesh));
         const ClusterMesh cm{(const float*)ctx->q, (float*)ctx->qs, ctx->dscal + S_QSUM, ctx->N, ctx->K,
                              (float)ctx->c, 0};
-        CK(cudaMemcpy(ctx->cltab, &cm, sizeof cm, cudaMemcpyHostToDevice));
+        UPLOAD(ctx->cltab, &cm, sizeof cm);
         ctx->cluster_ok = cluster_smoothing_supported(cluster_size_for(ctx->N, 1, ctx->nsm));
         if (ctx->cluster_ok) ctx->fuse = 5;
     }
@@ -1641,18 +1653,18 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
                     for (int kx = 0; kx < n; ++kx)
                         Df[((size_t)pos[kz] * n + pos[ky]) * n + pos[kx]] =
                             (float)(D[((size_t)kz * n + ky) * n + kx] / 64.0);
-            CK(cudaMemcpy(L.D, Df.data(), 4 * Df.size(), cudaMemcpyHostToDevice));
+            UPLOAD(L.D, Df.data(), 4 * Df.size());
             const std::vector<float2> tw = fht_twiddle_table(n);
             ALLOC(L.tw, sizeof(float2) * tw.size());
-            CK(cudaMemcpy(L.tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+            UPLOAD(L.tw, tw.data(), sizeof(float2) * tw.size());
             CK(fht_raise_smem(n));
         } else if (mixed) {
             std::vector<float> Hf(H.begin(), H.end()), Df(D.begin(), D.end());
-            CK(cudaMemcpy(L.H, Hf.data(), 4 * Hf.size(), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(L.D, Df.data(), 4 * Df.size(), cudaMemcpyHostToDevice));
+            UPLOAD(L.H, Hf.data(), 4 * Hf.size());
+            UPLOAD(L.D, Df.data(), 4 * Df.size());
         } else {
-            CK(cudaMemcpy(L.H, H.data(), 8 * H.size(), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(L.D, D.data(), 8 * D.size(), cudaMemcpyHostToDevice));
+            UPLOAD(L.H, H.data(), 8 * H.size());
+            UPLOAD(L.D, D.data(), 8 * D.size());
         }
     }
     if (mixed && ctx->K > 0 && (ctx->lev[0].H || fht_supported(ctx->N))) {
@@ -1681,11 +1693,11 @@ int setup(p3maze_ctx* ctx, const p3maze_params* p, const double* pos, const doub
                         (float)(std::pow(g, ctx->K) * inv_n3 * fht_scale);
                 }
         ALLOC(ctx->Ssm, 4 * S.size());
-        CK(cudaMemcpy(ctx->Ssm, S.data(), 4 * S.size(), cudaMemcpyHostToDevice));
+        UPLOAD(ctx->Ssm, S.data(), 4 * S.size());
         if (fft) {
             const std::vector<float2> tw = fht_twiddle_table(N);
             ALLOC(ctx->fht_tw, sizeof(float2) * tw.size());
-            CK(cudaMemcpy(ctx->fht_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+            UPLOAD(ctx->fht_tw, tw.data(), sizeof(float2) * tw.size());
             CK(fht_raise_smem(N));
         }
         ctx->fuse = 6;  // the default for such meshes: fastest alone and in a batch graph
