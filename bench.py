@@ -439,7 +439,10 @@ def accuracy_vs_oracle(ctx, system, prm, n_sample: int = 64) -> dict:
             "energy_rel_err": {k: abs(e[k] - v) / abs(v) for k, v in ref.items()},
             "sample": f"{n_sample} particles (seeded) for the total force; mesh force and energies over all "
                       f"{s.n}; oracle field by the FFT solve, short-range energy through the oracle's cell list",
-            "bars": {"force_rel_rms": "1e-5 (FP64) / 1e-4 (mixed)"}}
+            "bars": {"note": "the parity tests' bars, 1e-5 (FP64) / 1e-4 (mixed) relative RMS on forces, hold "
+                             "with the constraint solved to tol 1e-8..1e-9; here the field is solved to the "
+                             "workload's tol (max|r| <= 1e-6), whose own error, set by tol and the solver "
+                             "setting, dominates the mesh force"}}
 
 
 # ----------------------------------------------------------------- GPU arm
@@ -542,6 +545,9 @@ def run_ours(args) -> int:
     ms_staged = time_context(ctx, torch, stream, args.steps)
     tm = ctx.timing()
     ctx.set_timing(False)
+    # accuracy of the state the timed setting produced (before the
+    # end-to-end and one-kernel measurements below change anything)
+    accuracy = None if (args.no_accuracy or rank != 0) else accuracy_vs_oracle(ctx, system, prm)
     total_ms = max_over_ranks(sum(ms), world, device="cuda")
     ms_per_step = total_ms / args.steps
     value = job_ns_per_day(ms_per_step, world, prm["dt"])
@@ -578,7 +584,6 @@ def run_ours(args) -> int:
     n_alone = max(5, args.steps // 2)
     time_context(ctx, torch, stream, n_alone, flush)
     alone_launch_us = 1e3 * ctx.timing()["ms"]["smooth"] / n_alone / K_smooth
-    accuracy = None if (args.no_accuracy or rank != 0) else accuracy_vs_oracle(ctx, system, prm)
     ctx.close()
 
     # beside the headline: the plain FP64 path, the multiplier predictors and
