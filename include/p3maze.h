@@ -258,8 +258,9 @@ typedef struct {
                                    larger levels, where it is slower, keep the half sweeps);
                                    0: two in-place half sweeps per sweep everywhere.  The
                                    same bits either way.                                     */
-    double ms_per_step;         /* measured with the chosen setting                    */
-    double initial_ms_per_step; /* measured with the setting in use before tuning      */
+    double ms_per_step;         /* measured with the chosen setting (confirmation round) */
+    double initial_ms_per_step; /* measured with the setting in use before tuning (the
+                                   same round)                                          */
     int32_t trials;             /* settings timed                                      */
     int32_t steps;              /* MD steps advanced while tuning                      */
 } p3maze_tuning;
@@ -457,23 +458,26 @@ int p3maze_smooth_noalloc(const double *q, double *qs, int32_t mesh, int32_t ste
                           void *cuda_stream);
 
 /* Autotuner: time real MD steps under candidate settings and keep the
- * fastest -- multiplier predictor 1..3 (P3MaZe only), smoothing sweeps
- * (pre, post) in {(1,1), (2,1), (1,2), (2,2), (3,3)}, the diffusion kernel's
- * z planes per thread (FP32, one step per launch, N % 4 == 0: {1, 2, 4, 8};
- * otherwise per block: {4, 8, 16, 32}) with, in mixed mode, 1, 2 or 4
- * diffusion steps fused per launch, and where the short-range pair kernel
- * is forked onto its low-priority stream (after smoothing, or right after
- * the cell list so that it also overlaps assignment and smoothing) with its
- * grid (one block per home box, or a persistent grid of one block per two
- * SMs, one or two blocks per SM), and the size of the exactly solved coarse level (coarse_max 16,
- * 32 or 64); the diffusion candidates are timed again once the pair
- * branch's placement changed, since the fastest kernel depends on what runs
- * beside it.  None
- * of them changes the
- * converged field beyond tol (they change iteration counts and speed only).
- * Every trial runs 2 warm-up steps (graph capture) and steps_per_trial timed
- * steps (CUDA events); the system advances by all of them (out->steps).
- * Errors as p3maze_step.                                                      */
+ * fastest, in greedy passes:
+ *  - multiplier predictor 1..3 (P3MaZe only) x smoothing sweeps (pre, post)
+ *    in {(1,1), (2,1), (1,2), (2,2), (3,3)};
+ *  - the smoothing kernel (diffusion_fuse 1..6 where the mesh and precision
+ *    allow it) with its z planes per thread or block;
+ *  - the size of the exactly solved coarse level (coarse_max 16, 32, 64);
+ *  - where the short-range pair kernel is forked onto its low-priority
+ *    stream (after smoothing, or right after the cell list) and its grid
+ *    (one block per home box, or a persistent grid of one block per two
+ *    SMs, one or two blocks per SM); the smoothing candidates are timed
+ *    again if that placement changed, since the fastest kernel depends on
+ *    what runs beside it;
+ *  - a confirmation round: the starting setting and the three fastest other
+ *    settings timed again with 2 x steps_per_trial steps each, in two rounds
+ *    of opposite order; the fastest of these is kept, and out->ms_per_step
+ *    and out->initial_ms_per_step are these re-measurements.
+ * None of the settings changes the converged field beyond tol (they change
+ * iteration counts and speed only).  Every trial runs 2 warm-up steps (graph
+ * capture) and its timed steps (CUDA events); the system advances by all of
+ * them (out->steps).  Errors as p3maze_step.                                  */
 int p3maze_autotune(p3maze_ctx *ctx, int32_t steps_per_trial, p3maze_tuning *out);
 
 /* ---- batches: many systems advanced by shared launches ---------------------- */

@@ -2524,6 +2524,10 @@ namespace {
 
 struct Setting {
     int pred, nu1, nu2, zc, fuse, pair_fork, cmax, pblocks;
+    bool operator==(const Setting& o) const {
+        return pred == o.pred && nu1 == o.nu1 && nu2 == o.nu2 && zc == o.zc && fuse == o.fuse &&
+               pair_fork == o.pair_fork && cmax == o.cmax && pblocks == o.pblocks;
+    }
 };
 
 // Run `warm` + `steps` steps under setting `cfg`; ms per timed step.
@@ -2587,7 +2591,9 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     double initial = 0.0, best = 1e300;
     Setting chosen = start;
     int trials = 0, steps = 0;
+    std::vector<std::pair<double, Setting>> log;  // every trial's time
     rc = tune_trial(ctx, start, warm, steps_per_trial, &initial);
+    log.push_back({initial, start});
     trials += 1;
     steps += warm + steps_per_trial;
     if (!rc) {
@@ -2598,6 +2604,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
             trials += 1;
             steps += warm + steps_per_trial;
             if (rc) break;
+            log.push_back({ms, c});
             if (ms < best) {
                 best = ms;
                 chosen = c;
@@ -2634,6 +2641,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
                 trials += 1;
                 steps += warm + steps_per_trial;
                 if (rc) return;
+                log.push_back({ms, c});
                 if (ms < best) {
                     best = ms;
                     chosen = c;
@@ -2654,6 +2662,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
             trials += 1;
             steps += warm + steps_per_trial;
             if (rc) break;
+            log.push_back({ms, c});
             if (ms < best) {
                 best = ms;
                 chosen = c;
@@ -2677,6 +2686,7 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
                 trials += 1;
                 steps += warm + steps_per_trial;
                 if (rc) break;
+                log.push_back({ms, c});
                 if (ms < best) {
                     best = ms;
                     chosen = c;
@@ -2686,6 +2696,43 @@ int p3maze_autotune(p3maze_ctx* ctx, int32_t steps_per_trial, p3maze_tuning* out
     // the diffusion kernel again once the pair branch is placed: which kernel
     // is fastest depends on what runs beside it
     if (!rc && (chosen.pair_fork != start.pair_fork || chosen.pblocks != start.pblocks)) diffusion_pass();
+    // confirmation: the starting setting and the three fastest other
+    // settings timed again, twice as long, in two rounds of opposite order.
+    // Single short trials are noisy and the state drifts while tuning, so a
+    // close call is otherwise decided by chance (measured: at 10^6 ions the
+    // greedy passes kept a persistent pair grid 6 % slower than the
+    // per-box grid).  The reported times are these re-measurements.
+    if (!rc && log.size() > 1) {
+        std::stable_sort(log.begin(), log.end(),
+                         [](const std::pair<double, Setting>& a, const std::pair<double, Setting>& b) {
+                             return a.first < b.first;
+                         });
+        std::vector<Setting> top{start};
+        for (const auto& e : log) {
+            if (top.size() == 4) break;
+            bool seen = false;
+            for (const Setting& t : top) seen = seen || t == e.second;
+            if (!seen) top.push_back(e.second);
+        }
+        std::vector<double> sum(top.size(), 0.0);
+        for (int round = 0; round < 2 && !rc; ++round)
+            for (size_t k = 0; k < top.size() && !rc; ++k) {
+                const size_t i = round == 0 ? k : top.size() - 1 - k;
+                double ms = 0.0;
+                rc = tune_trial(ctx, top[i], warm, 2 * steps_per_trial, &ms);
+                trials += 1;
+                steps += warm + 2 * steps_per_trial;
+                sum[i] += ms;
+            }
+        if (!rc) {
+            size_t bi = 0;
+            for (size_t i = 1; i < top.size(); ++i)
+                if (sum[i] < sum[bi]) bi = i;
+            chosen = top[bi];
+            best = 0.5 * sum[bi];
+            initial = 0.5 * sum[0];
+        }
+    }
     // keep the fastest setting
     if (ctx->method != P3MAZE_METHOD_P3M) ctx->pred = chosen.pred;
     ctx->nu1 = chosen.nu1;
