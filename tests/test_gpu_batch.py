@@ -176,3 +176,30 @@ def test_contexts_with_different_shared_memory_needs_coexist(P):
     finally:
         a.close()
         b.close()
+
+
+def test_setup_is_ordered_on_the_context_stream(P):
+    """A context created while the legacy default stream is busy starts from
+    the same state as one created on an idle device: its setup copies and the
+    clearing of the per-cell counts run on the context's own stream.  (A plain
+    cudaMemset or pageable cudaMemcpy runs on the legacy default stream, which
+    the context's non-blocking streams are not ordered after: the first cell
+    list could be built from counts not yet cleared.)  4096 ions, so the cell
+    list takes the multi-kernel builder with its count array."""
+    import torch
+
+    s = S.nacl_melt(4096, 50.45, seed=23)
+    kw = dict(alpha=0.30, r_cut=9.0, mesh=64, tol=1e-8, dt=1.0, precision="mixed")
+    with P.Context.from_system(s, **kw) as a:
+        a.step(3)
+        ref = a.forces()
+    torch.cuda.synchronize()
+    x = torch.randn(4096, 4096, device="cuda")
+    for _ in range(40):                     # some tens of ms queued on the legacy default stream
+        x = x @ x
+        x = x / x.norm()
+    with P.Context.from_system(s, **kw) as b:
+        b.step(3)
+        got = b.forces()
+    torch.cuda.synchronize()
+    assert np.array_equal(got, ref)
