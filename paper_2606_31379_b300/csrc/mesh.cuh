@@ -2446,8 +2446,132 @@ k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __re
     }
 }
 
-// Meshes the FFT smoothing handles.
-inline bool fht_supported(int n) { return n == 32 || n == 64 || n == kFhtMaxN; }
+
+// ---------------------------------------------------------------- FFT smoothing, n = 256
+// A 256 x 256 plane does not fit in shared memory, so the transforms run as
+// five passes over global memory: forward x (row pairs straight from global
+// memory, k_fht_rows), forward y (k_fht_cols), forward z + scaling + inverse
+// z (k_fht_cols, MODE 1), inverse y, inverse x with per-block sums.  The
+// line-pair transform is fht_pair, as above.
+constexpr int kFhtBigN = 256;
+constexpr int kFhtRowWarps = 8;     // row pairs per block of k_fht_rows
+constexpr int kFhtColThreads = 512; // 16 warps: one column pair each of a 32-column tile
+
+// x transforms of row pairs: warp w of block b takes rows 2 (8 b + w) and
+// 2 (8 b + w) + 1 of the n^3 array (all z and y), reads them from `in` and
+// writes their coefficients to `out` at the same positions.  With partial,
+// partial[blockIdx.x] gets the compensated sum of the block's output.
+template <int R, bool INV>
+__global__ void __launch_bounds__(32 * kFhtRowWarps)
+k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
+           double* __restrict__ partial) {
+    constexpr int n = 32 * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    FhtTw<R> t;
+    fht_twiddles<R>(t, tw, lane);  // constant: before the wait
+    pdl_wait();
+    pdl_trigger();
+    const int64_t r = 2 * ((int64_t)blockIdx.x * kFhtRowWarps + warp);
+    const float* a = in + r * n;
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = make_float2(a[lane + 32 * j], a[n + lane + 32 * j]);
+    fht_pair<R, INV>(v, t, lane);
+    float* o = out + r * n;
+    float acc_s = 0.f, acc_c = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        o[lane + 32 * j] = v[j].x;
+        o[n + lane + 32 * j] = v[j].y;
+        if (partial) {
+            two_sum_add(acc_s, acc_c, v[j].x);
+            two_sum_add(acc_s, acc_c, v[j].y);
+        }
+    }
+    if (partial) {
+        const double acc = block_sum((double)acc_s + (double)acc_c);
+        if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    }
+}
+
+// Transforms along an axis of element stride ls (y: n, z: n^2) for the 32
+// consecutive x of tile blockIdx.x, at offset blockIdx.y * os of the other
+// axis (y lines: z planes, os = n^2; z lines: y rows, os = n).  The n x 32
+// tile sits in shared memory with element (p, c) at 32 p + (c ^ (p mod 32))
+// (16-byte groups kept together, so rows load as float4 and both rows and
+// columns are free of bank conflicts); one warp per column pair.  MODE 0: a
+// forward (INV false) or inverse transform, in place.  MODE 1: forward,
+// scaling by S (laid out like the data; its tile copied in by cp.async
+// meanwhile), inverse.
+template <int R, int MODE, bool INV>
+__global__ void __launch_bounds__(kFhtColThreads)
+k_fht_cols(float* __restrict__ d, int64_t ls, int64_t os, const float2* __restrict__ tw,
+           const float* __restrict__ S) {
+    constexpr int n = 32 * R, Q = n * 32 / 4, PER = Q / kFhtColThreads;
+    static_assert(PER * kFhtColThreads == Q, "float4 groups per thread");
+    extern __shared__ __align__(16) unsigned char fht_smem[];
+    float* s = reinterpret_cast<float*>(fht_smem);
+    float* ss = s + n * 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.y * os + (int64_t)blockIdx.x * 32;
+    FhtTw<R> t;
+    fht_twiddles<R>(t, tw, lane);
+    if constexpr (MODE == 1) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {  // S is constant: before the wait
+            const int i = tid + k * kFhtColThreads, p = i >> 3, c = (i & 7) * 4;
+            cp_async16(ss + 32 * p + (c ^ (p & 28)), S + base + p * ls + c);
+        }
+        cp_async_commit();
+    }
+    pdl_wait();
+    pdl_trigger();
+    float4 f[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * kFhtColThreads, p = i >> 3, c = (i & 7) * 4;
+        f[k] = *reinterpret_cast<const float4*>(d + base + p * ls + c);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * kFhtColThreads, p = i >> 3, c = (i & 7) * 4;
+        *reinterpret_cast<float4*>(s + 32 * p + (c ^ (p & 28))) = fht_perm4(f[k], p & 3);
+    }
+    __syncthreads();
+    const int c0 = 2 * warp;  // this warp's column pair
+    const unsigned a = 4u * (unsigned)(32 * lane + (c0 ^ lane)), b = 4u * (unsigned)(32 * lane + ((c0 + 1) ^ lane));
+    constexpr unsigned JS = 4u * 32u * 32u;
+    if constexpr (MODE == 0) {
+        warp_fht2<R, INV, JS>(a, b, a, b, t, lane);
+    } else {
+        warp_fht2<R, false, JS>(a, b, a, b, t, lane);
+        cp_async_wait<0>();
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * kFhtColThreads, p = i >> 3, c = (i & 7) * 4;
+            const int e = 32 * p + (c ^ (p & 28));
+            const float4 g = *reinterpret_cast<const float4*>(s + e);
+            const float4 w = fht_perm4(*reinterpret_cast<const float4*>(ss + e), p & 3);
+            *reinterpret_cast<float4*>(s + e) = make_float4(g.x * w.x, g.y * w.y, g.z * w.z, g.w * w.w);
+        }
+        __syncthreads();
+        warp_fht2<R, true, JS>(a, b, a, b, t, lane);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * kFhtColThreads, p = i >> 3, c = (i & 7) * 4;
+        *reinterpret_cast<float4*>(d + base + p * ls + c) =
+            fht_perm4(*reinterpret_cast<const float4*>(s + 32 * p + (c ^ (p & 28))), p & 3);
+    }
+}
+
+// Shared memory of k_fht_cols: the tile, and in MODE 1 the tile of S.
+inline size_t fht_cols_smem_bytes(int n, int mode) { return (size_t)(mode ? 2 : 1) * n * 32 * sizeof(float); }
+
+// Meshes the FFT smoothing handles: a plane per block up to 128, five passes at 256.
+inline bool fht_supported(int n) { return n == 32 || n == 64 || n == kFhtMaxN || n == kFhtBigN; }
 
 // ---------------------------------------------------------------- interpolation
 // F_a = -ke Q_a sum_n W(r_a - r_n) (D phi)_n with central differences

@@ -453,9 +453,40 @@ cudaError_t launch_fht(int n, bool pdl_first, bool pdl, cudaStream_t s, const fl
     }
 }
 
+// n = 256: forward x (q into the ping-pong mesh t), forward y, forward z +
+// scaling + inverse z, inverse y (all in place in t), inverse x (t into q^s,
+// with per-block sums); five launches.
+cudaError_t launch_fht_big(p3maze_ctx* ctx) {
+    constexpr int R = kFhtBigN / 32;
+    const int64_t n = ctx->N;
+    const bool pdl = ctx->pdl;
+    cudaStream_t s = ctx->stream;
+    float* t = (float*)ctx->lev[0].e;
+    const float2* tw = (const float2*)ctx->fht_tw;
+    const dim3 gr((unsigned)(n * n / 2 / kFhtRowWarps)), br(32 * kFhtRowWarps);
+    const dim3 gc((unsigned)(n / 32), (unsigned)n), bc(kFhtColThreads);
+    const size_t s0 = fht_cols_smem_bytes((int)n, 0), s1 = fht_cols_smem_bytes((int)n, 1);
+    cudaError_t e = launch_maybe_pdl(pdl, k_fht_rows<R, false>, gr, br, 0, s, (const float*)ctx->q, t, tw,
+                                     (double*)nullptr);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(pdl, k_fht_cols<R, 0, false>, gc, bc, s0, s, t, n, n * n, tw, (const float*)nullptr);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(pdl, k_fht_cols<R, 1, false>, gc, bc, s1, s, t, n * n, n, tw, (const float*)ctx->Ssm);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(pdl, k_fht_cols<R, 0, true>, gc, bc, s0, s, t, n, n * n, tw, (const float*)nullptr);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(pdl, k_fht_rows<R, true>, gr, br, 0, s, (const float*)t, (float*)ctx->qs, tw,
+                             ctx->partial);
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(pdl, k_sum_final, dim3(1), dim3(1024), 0, s, (int)gr.x, (const double*)ctx->partial,
+                             ctx->dscal + S_QSUM);
+    return e;
+}
+
 // Spectral smoothing by FFT: q into q^s through the smoothing ping-pong
-// mesh, and the neutrality sum of the per-plane sums.
+// mesh, and the neutrality sum of the per-plane (or per-block) sums.
 cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
+    if (ctx->N == kFhtBigN) return launch_fht_big(ctx);
     cudaError_t e = launch_fht(ctx->N, ctx->pdl, ctx->pdl, ctx->stream, (const float*)ctx->q, (float*)ctx->lev[0].e,
                                (float*)ctx->qs, (const float2*)ctx->fht_tw, (const float*)ctx->Ssm, ctx->partial);
     if (e == cudaSuccess)
@@ -463,6 +494,7 @@ cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
                              (const double*)ctx->partial, ctx->dscal + S_QSUM);
     return e;
 }
+inline int fht_smoothing_launches(int n) { return n == kFhtBigN ? 6 : 4; }
 
 // Bit-reversed position of each index 0..n-1 (n a power of two).
 std::vector<int> fht_positions(int n) {
@@ -496,6 +528,13 @@ cudaError_t fht_raise_smem(int n) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         return e;
     };
+    if (n == kFhtBigN) {
+        constexpr int R = kFhtBigN / 32;
+        cudaError_t e = raise((const void*)k_fht_cols<R, 0, false>, fht_cols_smem_bytes(n, 0));
+        if (e == cudaSuccess) e = raise((const void*)k_fht_cols<R, 0, true>, fht_cols_smem_bytes(n, 0));
+        if (e == cudaSuccess) e = raise((const void*)k_fht_cols<R, 1, false>, fht_cols_smem_bytes(n, 1));
+        return e;
+    }
     const size_t sxy = fht_smem_bytes(n), sz = fht_z_smem_bytes(n);
     const void* k[3];
     if (n == 32) {
@@ -646,7 +685,7 @@ int smooth(p3maze_ctx* ctx) {
         if (ctx->fuse == 6 && ctx->fht_tw) {
             // all K steps at once in the Hartley basis, each 1D transform by FFT
             CK(launch_fht_smoothing(ctx));
-            count(ctx, P3MAZE_ST_SMOOTH, 4);
+            count(ctx, P3MAZE_ST_SMOOTH, fht_smoothing_launches(ctx->N));
         } else if (ctx->fuse == 6) {
             // all K steps at once in the Hartley basis (N <= 64): forward
             // transform, scale by (1 + c lambda_k)^K / N^3, inverse transform
@@ -2773,7 +2812,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
     if (t->diffusion_fuse == 6 && !ctx->Ssm)
-        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64 or N = 128");
+        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64, 128 or 256");
     if (t->diffusion_fuse == 5 && !ctx->cluster_ok)
         return fail(ctx, P3MAZE_ERR_INVALID,
                     "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs such clusters");
