@@ -2344,11 +2344,12 @@ inline size_t fht_z_smem_bytes(int n) { return 2 * fht_smem_bytes(n); }
 // x and y transforms of z plane blockIdx.x: out[z] = 4 Hy in[z] Hx, forward
 // (natural order in, bit-reversed in x and y out) or inverse (the reverse).
 // With partial != nullptr, partial[blockIdx.x] gets the compensated sum of
-// the output plane.
+// the output plane and the last block to finish writes their sum (fixed
+// order) to *sum_out.
 template <int R, bool INV>
 __global__ void __launch_bounds__(fht_threads<R>())
 k_fht_xy(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
-         double* __restrict__ partial) {
+         double* __restrict__ partial, unsigned* __restrict__ arrive, double* __restrict__ sum_out) {
     constexpr int n = 32 * R, T = fht_threads<R>(), Q = n * n / 4, PER = (Q + T - 1) / T;
     extern __shared__ __align__(16) unsigned char fht_smem[];
     float* s = reinterpret_cast<float*>(fht_smem);
@@ -2378,10 +2379,7 @@ k_fht_xy(const float* __restrict__ in, float* __restrict__ out, const float2* __
             }
         }
     }
-    if (partial) {
-        const double acc = block_sum((double)acc_s + (double)acc_c);
-        if (tid == 0) partial[blockIdx.x] = acc;
-    }
+    if (partial) sum_last_block((double)acc_s + (double)acc_c, partial, arrive, sum_out);
 }
 
 // For ky = blockIdx.x: forward z transform of the slice t[z][ky][x] (rows
@@ -2460,11 +2458,12 @@ constexpr int kFhtColThreads = 512; // 16 warps: one column pair each of a 32-co
 // x transforms of row pairs: warp w of block b takes rows 2 (8 b + w) and
 // 2 (8 b + w) + 1 of the n^3 array (all z and y), reads them from `in` and
 // writes their coefficients to `out` at the same positions.  With partial,
-// partial[blockIdx.x] gets the compensated sum of the block's output.
+// partial[blockIdx.x] gets the compensated sum of the block's output and the
+// last block to finish writes their sum (fixed order) to *sum_out.
 template <int R, bool INV>
 __global__ void __launch_bounds__(32 * kFhtRowWarps)
 k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
-           double* __restrict__ partial) {
+           double* __restrict__ partial, unsigned* __restrict__ arrive, double* __restrict__ sum_out) {
     constexpr int n = 32 * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     FhtTw<R> t;
@@ -2488,10 +2487,7 @@ k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* 
             two_sum_add(acc_s, acc_c, v[j].y);
         }
     }
-    if (partial) {
-        const double acc = block_sum((double)acc_s + (double)acc_c);
-        if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-    }
+    if (partial) sum_last_block((double)acc_s + (double)acc_c, partial, arrive, sum_out);
 }
 
 // Transforms along an axis of element stride ls (y: n, z: n^2) for the 32

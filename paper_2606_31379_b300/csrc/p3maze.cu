@@ -431,31 +431,44 @@ cudaError_t launch_diffuse_tq(p3maze_ctx* ctx, int S, bool last, bool pdl, const
 
 // y = H3 (table o (H3 x)) by FFT (n = 32, 64, 128; the table bit-reversed
 // and scaled for the kernels): the x-y transforms of x into tmp, the z
-// transforms and scaling in place, the x-y transforms into y (with per-plane
-// sums when partial is given).  pdl_first: the first launch may overlap its
-// predecessor.
+// transforms and scaling in place (n = 64, 128: tiles of 32 x columns over
+// all SMs; n = 32: one block per ky slice), the x-y transforms into y.  With
+// partial given, the last launch also forms the sum of y into *sum_out
+// (arrive: its block counter, zero between uses).  pdl_first: the first
+// launch may overlap its predecessor.
 template <int R>
 cudaError_t launch_fht_r(bool pdl_first, bool pdl, cudaStream_t s, const float* x, float* tmp, float* y,
-                         const float2* tw, const float* table, double* partial) {
-    const dim3 g(32 * R), b(fht_threads<R>());
-    const size_t sm = fht_smem_bytes(32 * R);
-    cudaError_t e = launch_maybe_pdl(pdl_first, k_fht_xy<R, false>, g, b, sm, s, x, tmp, tw, (double*)nullptr);
-    if (e == cudaSuccess) e = launch_maybe_pdl(pdl, k_fht_z<R>, g, b, fht_z_smem_bytes(32 * R), s, tmp, tw, table);
-    if (e == cudaSuccess) e = launch_maybe_pdl(pdl, k_fht_xy<R, true>, g, b, sm, s, (const float*)tmp, y, tw, partial);
+                         const float2* tw, const float* table, double* partial, unsigned* arrive,
+                         double* sum_out) {
+    constexpr int n = 32 * R;
+    const dim3 g(n), b(fht_threads<R>());
+    const size_t sm = fht_smem_bytes(n);
+    cudaError_t e = launch_maybe_pdl(pdl_first, k_fht_xy<R, false>, g, b, sm, s, x, tmp, tw, (double*)nullptr,
+                                     (unsigned*)nullptr, (double*)nullptr);
+    if (e == cudaSuccess) {
+        if constexpr (R >= 2)
+            e = launch_maybe_pdl(pdl, k_fht_cols<R, 1, false>, dim3(n / 32, n), dim3(kFhtColThreads),
+                                 fht_cols_smem_bytes(n, 1), s, tmp, (int64_t)n * n, (int64_t)n, tw, table);
+        else
+            e = launch_maybe_pdl(pdl, k_fht_z<R>, g, b, fht_z_smem_bytes(n), s, tmp, tw, table);
+    }
+    if (e == cudaSuccess)
+        e = launch_maybe_pdl(pdl, k_fht_xy<R, true>, g, b, sm, s, (const float*)tmp, y, tw, partial, arrive, sum_out);
     return e;
 }
 cudaError_t launch_fht(int n, bool pdl_first, bool pdl, cudaStream_t s, const float* x, float* tmp, float* y,
-                       const float2* tw, const float* table, double* partial) {
+                       const float2* tw, const float* table, double* partial, unsigned* arrive, double* sum_out) {
     switch (n) {
-        case 32: return launch_fht_r<1>(pdl_first, pdl, s, x, tmp, y, tw, table, partial);
-        case 64: return launch_fht_r<2>(pdl_first, pdl, s, x, tmp, y, tw, table, partial);
-        default: return launch_fht_r<4>(pdl_first, pdl, s, x, tmp, y, tw, table, partial);
+        case 32: return launch_fht_r<1>(pdl_first, pdl, s, x, tmp, y, tw, table, partial, arrive, sum_out);
+        case 64: return launch_fht_r<2>(pdl_first, pdl, s, x, tmp, y, tw, table, partial, arrive, sum_out);
+        default: return launch_fht_r<4>(pdl_first, pdl, s, x, tmp, y, tw, table, partial, arrive, sum_out);
     }
 }
 
 // n = 256: forward x (q into the ping-pong mesh t), forward y, forward z +
 // scaling + inverse z, inverse y (all in place in t), inverse x (t into q^s,
-// with per-block sums); five launches.
+// with the neutrality sum by its last block); five launches.  The block
+// counter is the FP64 field update's (never in the same context: mixed only).
 cudaError_t launch_fht_big(p3maze_ctx* ctx) {
     constexpr int R = kFhtBigN / 32;
     const int64_t n = ctx->N;
@@ -467,7 +480,7 @@ cudaError_t launch_fht_big(p3maze_ctx* ctx) {
     const dim3 gc((unsigned)(n / 32), (unsigned)n), bc(kFhtColThreads);
     const size_t s0 = fht_cols_smem_bytes((int)n, 0), s1 = fht_cols_smem_bytes((int)n, 1);
     cudaError_t e = launch_maybe_pdl(pdl, k_fht_rows<R, false>, gr, br, 0, s, (const float*)ctx->q, t, tw,
-                                     (double*)nullptr);
+                                     (double*)nullptr, (unsigned*)nullptr, (double*)nullptr);
     if (e == cudaSuccess)
         e = launch_maybe_pdl(pdl, k_fht_cols<R, 0, false>, gc, bc, s0, s, t, n, n * n, tw, (const float*)nullptr);
     if (e == cudaSuccess)
@@ -476,25 +489,21 @@ cudaError_t launch_fht_big(p3maze_ctx* ctx) {
         e = launch_maybe_pdl(pdl, k_fht_cols<R, 0, true>, gc, bc, s0, s, t, n, n * n, tw, (const float*)nullptr);
     if (e == cudaSuccess)
         e = launch_maybe_pdl(pdl, k_fht_rows<R, true>, gr, br, 0, s, (const float*)t, (float*)ctx->qs, tw,
-                             ctx->partial);
-    if (e == cudaSuccess)
-        e = launch_maybe_pdl(pdl, k_sum_final, dim3(1), dim3(1024), 0, s, (int)gr.x, (const double*)ctx->partial,
-                             ctx->dscal + S_QSUM);
+                             ctx->partial, &ctx->dmg->arrive_sum, ctx->dscal + S_QSUM);
     return e;
 }
 
 // Spectral smoothing by FFT: q into q^s through the smoothing ping-pong
-// mesh, and the neutrality sum of the per-plane (or per-block) sums.
+// mesh; the last launch's last block forms the neutrality sum from the
+// per-plane (or per-block) sums.  The block counter is the FP64 field
+// update's (mixed only, so never used by both in one context).
 cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
     if (ctx->N == kFhtBigN) return launch_fht_big(ctx);
-    cudaError_t e = launch_fht(ctx->N, ctx->pdl, ctx->pdl, ctx->stream, (const float*)ctx->q, (float*)ctx->lev[0].e,
-                               (float*)ctx->qs, (const float2*)ctx->fht_tw, (const float*)ctx->Ssm, ctx->partial);
-    if (e == cudaSuccess)
-        e = launch_maybe_pdl(ctx->pdl, k_sum_final, dim3(1), dim3(1024), 0, ctx->stream, ctx->N,
-                             (const double*)ctx->partial, ctx->dscal + S_QSUM);
-    return e;
+    return launch_fht(ctx->N, ctx->pdl, ctx->pdl, ctx->stream, (const float*)ctx->q, (float*)ctx->lev[0].e,
+                      (float*)ctx->qs, (const float2*)ctx->fht_tw, (const float*)ctx->Ssm, ctx->partial,
+                      &ctx->dmg->arrive_sum, ctx->dscal + S_QSUM);
 }
-inline int fht_smoothing_launches(int n) { return n == kFhtBigN ? 6 : 4; }
+inline int fht_smoothing_launches(int n) { return n == kFhtBigN ? 5 : 3; }
 
 // Bit-reversed position of each index 0..n-1 (n a power of two).
 std::vector<int> fht_positions(int n) {
@@ -535,8 +544,9 @@ cudaError_t fht_raise_smem(int n) {
         if (e == cudaSuccess) e = raise((const void*)k_fht_cols<R, 1, false>, fht_cols_smem_bytes(n, 1));
         return e;
     }
-    const size_t sxy = fht_smem_bytes(n), sz = fht_z_smem_bytes(n);
+    const size_t sxy = fht_smem_bytes(n), sz = fht_z_smem_bytes(n), sc = fht_cols_smem_bytes(n, 1);
     const void* k[3];
+    size_t szk = sz;
     if (n == 32) {
         k[0] = (const void*)k_fht_xy<1, false>;
         k[1] = (const void*)k_fht_xy<1, true>;
@@ -544,15 +554,17 @@ cudaError_t fht_raise_smem(int n) {
     } else if (n == 64) {
         k[0] = (const void*)k_fht_xy<2, false>;
         k[1] = (const void*)k_fht_xy<2, true>;
-        k[2] = (const void*)k_fht_z<2>;
+        k[2] = (const void*)k_fht_cols<2, 1, false>;
+        szk = sc;
     } else {
         k[0] = (const void*)k_fht_xy<4, false>;
         k[1] = (const void*)k_fht_xy<4, true>;
-        k[2] = (const void*)k_fht_z<4>;
+        k[2] = (const void*)k_fht_cols<4, 1, false>;
+        szk = sc;
     }
     cudaError_t e = raise(k[0], sxy);
     if (e == cudaSuccess) e = raise(k[1], sxy);
-    if (e == cudaSuccess) e = raise(k[2], sz);
+    if (e == cudaSuccess) e = raise(k[2], szk);
     return e;
 }
 
@@ -813,7 +825,7 @@ int vcycle(p3maze_ctx* ctx, int l, bool pdl_first) {
     };
     if (l == ctx->lc && L.tw) {
         CK(launch_fht(L.n, pdl, ctx->pdl, s, (const float*)b, (float*)L.t, (float*)e, (const float2*)L.tw,
-                      (const float*)L.D, nullptr));
+                      (const float*)L.D, nullptr, nullptr, nullptr));
         count(ctx, P3MAZE_ST_SOLVE, 3);
         L.fin = e;
         return P3MAZE_OK;
