@@ -2455,36 +2455,47 @@ constexpr int kFhtBigN = 256;
 constexpr int kFhtRowWarps = 8;     // row pairs per block of k_fht_rows
 constexpr int kFhtColThreads = 512; // 16 warps: one column pair each of a 32-column tile
 
-// x transforms of row pairs: warp w of block b takes rows 2 (8 b + w) and
-// 2 (8 b + w) + 1 of the n^3 array (all z and y), reads them from `in` and
-// writes their coefficients to `out` at the same positions.  With partial,
-// partial[blockIdx.x] gets the compensated sum of the block's output and the
-// last block to finish writes their sum (fixed order) to *sum_out.
+// x transforms of row pairs: warp w of block b takes the kFhtRowPairs row
+// pairs starting at rows 2 (kFhtRowPairs (8 b + w) + i), i < kFhtRowPairs,
+// of the n^3 array (all z and y), reads them from `in` (all loads first)
+// and writes their coefficients to `out` at the same positions.  The pairs
+// of a warp are independent chains, so their latencies overlap.  With
+// partial, partial[blockIdx.x] gets the compensated sum of the block's
+// output and the last block to finish writes their sum (fixed order) to
+// *sum_out.
+constexpr int kFhtRowPairs = 2;
 template <int R, bool INV>
 __global__ void __launch_bounds__(32 * kFhtRowWarps)
 k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
            double* __restrict__ partial, unsigned* __restrict__ arrive, double* __restrict__ sum_out) {
-    constexpr int n = 32 * R;
+    constexpr int n = 32 * R, NP = kFhtRowPairs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     FhtTw<R> t;
     fht_twiddles<R>(t, tw, lane);  // constant: before the wait
     pdl_wait();
     pdl_trigger();
-    const int64_t r = 2 * ((int64_t)blockIdx.x * kFhtRowWarps + warp);
-    const float* a = in + r * n;
-    float2 v[R];
+    const int64_t r0 = 2 * NP * ((int64_t)blockIdx.x * kFhtRowWarps + warp);
+    float2 v[NP][R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = make_float2(a[lane + 32 * j], a[n + lane + 32 * j]);
-    fht_pair<R, INV>(v, t, lane);
-    float* o = out + r * n;
+    for (int i = 0; i < NP; ++i) {
+        const float* a = in + (r0 + 2 * i) * n;
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[i][j] = make_float2(a[lane + 32 * j], a[n + lane + 32 * j]);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) fht_pair<R, INV>(v[i], t, lane);
     float acc_s = 0.f, acc_c = 0.f;
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        o[lane + 32 * j] = v[j].x;
-        o[n + lane + 32 * j] = v[j].y;
-        if (partial) {
-            two_sum_add(acc_s, acc_c, v[j].x);
-            two_sum_add(acc_s, acc_c, v[j].y);
+    for (int i = 0; i < NP; ++i) {
+        float* o = out + (r0 + 2 * i) * n;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            o[lane + 32 * j] = v[i][j].x;
+            o[n + lane + 32 * j] = v[i][j].y;
+            if (partial) {
+                two_sum_add(acc_s, acc_c, v[i][j].x);
+                two_sum_add(acc_s, acc_c, v[i][j].y);
+            }
         }
     }
     if (partial) sum_last_block((double)acc_s + (double)acc_c, partial, arrive, sum_out);

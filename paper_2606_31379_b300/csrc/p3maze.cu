@@ -476,7 +476,7 @@ cudaError_t launch_fht_big(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     float* t = (float*)ctx->lev[0].e;
     const float2* tw = (const float2*)ctx->fht_tw;
-    const dim3 gr((unsigned)(n * n / 2 / kFhtRowWarps)), br(32 * kFhtRowWarps);
+    const dim3 gr((unsigned)(n * n / 2 / kFhtRowPairs / kFhtRowWarps)), br(32 * kFhtRowWarps);
     const dim3 gc((unsigned)(n / 32), (unsigned)n), bc(kFhtColThreads);
     const size_t s0 = fht_cols_smem_bytes((int)n, 0), s1 = fht_cols_smem_bytes((int)n, 1);
     cudaError_t e = launch_maybe_pdl(pdl, k_fht_rows<R, false>, gr, br, 0, s, (const float*)ctx->q, t, tw,
