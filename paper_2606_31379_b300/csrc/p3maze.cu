@@ -469,9 +469,9 @@ cudaError_t launch_fht(int n, bool pdl_first, bool pdl, cudaStream_t s, const fl
 // scaling + inverse z, inverse y (all in place in t), inverse x (t into q^s,
 // with the neutrality sum by its last block); five launches.  The block
 // counter is the FP64 field update's (never in the same context: mixed only).
-cudaError_t launch_fht_big(p3maze_ctx* ctx) {
-    constexpr int R = kFhtBigN / 32;
-    const int64_t n = ctx->N;
+template <int R>
+cudaError_t launch_fht_passes(p3maze_ctx* ctx) {
+    const int64_t n = 32 * R;
     const bool pdl = ctx->pdl;
     cudaStream_t s = ctx->stream;
     float* t = (float*)ctx->lev[0].e;
@@ -498,7 +498,7 @@ cudaError_t launch_fht_big(p3maze_ctx* ctx) {
 // per-plane (or per-block) sums.  The block counter is the FP64 field
 // update's (mixed only, so never used by both in one context).
 cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
-    if (ctx->N == kFhtBigN) return launch_fht_big(ctx);
+    if (ctx->N == kFhtBigN) return launch_fht_passes<kFhtBigN / 32>(ctx);
     return launch_fht(ctx->N, ctx->pdl, ctx->pdl, ctx->stream, (const float*)ctx->q, (float*)ctx->lev[0].e,
                       (float*)ctx->qs, (const float2*)ctx->fht_tw, (const float*)ctx->Ssm, ctx->partial,
                       &ctx->dmg->arrive_sum, ctx->dscal + S_QSUM);
