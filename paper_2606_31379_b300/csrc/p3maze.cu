@@ -332,32 +332,37 @@ inline bool cells_in_one_block(int np, int ncell) {
 }
 inline size_t cells_block_smem(int ncell) { return 2 * sizeof(int) * (size_t)ncell; }
 
-int build_cells(p3maze_ctx* ctx) {
+int build_cells(p3maze_ctx* ctx, bool counted) {
     cudaStream_t s = ctx->stream;
     stage_begin(ctx, P3MAZE_ST_CELLS);
-    int launches = 1;
+    int launches = 0;
     // every launch may overlap its predecessor's tail (programmatic dependent
     // launch); the per-cell counts are zero on entry (cleared at setup and by
-    // k_cell_sort once the scan has used them)
+    // k_cell_sort once the scan has used them), or already formed by the
+    // drift (counted)
     const bool pdl = ctx->pdl;
     if (cells_in_one_block(ctx->np, ctx->ncell)) {
         CK(launch_maybe_pdl(pdl, k_cells_block, dim3(1), dim3(kCellBlockThreads), cells_block_smem(ctx->ncell), s,
                             ctx->np, ctx->r, ctx->inv_cell, ctx->nc, ctx->ncell, ctx->cell, ctx->start, ctx->order));
         launches += 1;
     } else {
-        CK(launch_maybe_pdl(pdl, k_cell_count, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->r,
-                            ctx->inv_cell, ctx->nc, ctx->cell, ctx->count));
+        if (!counted) {
+            CK(launch_maybe_pdl(pdl, k_cell_count, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->r,
+                                ctx->inv_cell, ctx->nc, ctx->cell, ctx->count));
+            launches += 1;
+        }
         CK(launch_maybe_pdl(pdl, k_scan_cells, dim3(1), dim3(kScanThreads), 0, s, ctx->ncell, ctx->count, ctx->start,
                             ctx->fill));
         CK(launch_maybe_pdl(pdl, k_cell_scatter, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->cell,
                             ctx->start, ctx->fill, ctx->order));
         CK(launch_maybe_pdl(pdl, k_cell_sort, dim3(nblk(ctx->ncell)), dim3(P3_THREADS), 0, s, ctx->ncell, ctx->start,
                             ctx->order, ctx->count));
-        launches += 4;
+        launches += 3;
     }
     CK(launch_maybe_pdl(pdl, k_gather_sorted, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->order,
                         ctx->r, ctx->Q, ctx->type, ctx->mol, ctx->cell, ctx->nc, ctx->lcell, ctx->xq, ctx->xl64,
                         ctx->xl32, ctx->ts, ctx->ms, ctx->cs, ctx->mp, ctx->N, ctx->inv_h));
+    launches += 1;
     CKL();
     count(ctx, P3MAZE_ST_CELLS, launches);
     stage_end(ctx, P3MAZE_ST_CELLS);
@@ -1198,8 +1203,8 @@ int mesh_pipeline(p3maze_ctx* ctx, int pred_order) {
 
 // Cell list, mesh pipeline and forces at the current positions.  The gather
 // stage stays open: the caller closes it (after the final half kick).
-int field_and_forces(p3maze_ctx* ctx, int pred_order) {
-    int rc = build_cells(ctx);
+int field_and_forces(p3maze_ctx* ctx, int pred_order, bool counted) {
+    int rc = build_cells(ctx, counted);
     if (rc) return rc;
     rc = ctx->prec == P3MAZE_MIXED ? mesh_pipeline<float>(ctx, pred_order)
                                    : mesh_pipeline<double>(ctx, pred_order);
@@ -1247,7 +1252,7 @@ int initialise_field(p3maze_ctx* ctx) {
     ctx->nhist = 0;
     const bool was_timing = ctx->timing;
     ctx->timing = false;
-    int rc = field_and_forces(ctx, 0);
+    int rc = field_and_forces(ctx, 0, false);
     ctx->timing = was_timing;
     if (rc) return rc;
     rc = read_solver_state(ctx);
@@ -1265,16 +1270,34 @@ int initialise_field(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
+// Half kick and drift.  On the multi-kernel cell-list path the same launch
+// also forms each particle's cell and the per-cell counts (*counted: the
+// cell-list build then skips its count kernel).
+int kick_drift(p3maze_ctx* ctx, bool* counted) {
+    cudaStream_t s = ctx->stream;
+    stage_begin(ctx, P3MAZE_ST_INTEGRATE);
+    *counted = !cells_in_one_block(ctx->np, ctx->ncell);
+    if (*counted)
+        CK(launch_maybe_pdl(ctx->pdl, k_kick_drift_count, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np,
+                            ctx->r, ctx->v, (const double*)ctx->F, (const double*)ctx->hdt_acc, ctx->dt, ctx->L,
+                            ctx->inv_cell, ctx->nc, ctx->cell, ctx->count));
+    else
+        k_kick_drift<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->F, ctx->hdt_acc, ctx->dt,
+                                                          ctx->L);
+    count(ctx, P3MAZE_ST_INTEGRATE);
+    stage_end(ctx, P3MAZE_ST_INTEGRATE);
+    CKL();
+    return P3MAZE_OK;
+}
+
 // The launches of one MD step (eager, or recorded into a graph): kick/drift,
 // field and forces, closing kick.
 int step_body(p3maze_ctx* ctx, int order) {
     cudaStream_t s = ctx->stream;
-    stage_begin(ctx, P3MAZE_ST_INTEGRATE);
-    k_kick_drift<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->F, ctx->hdt_acc, ctx->dt, ctx->L);
-    count(ctx, P3MAZE_ST_INTEGRATE);
-    stage_end(ctx, P3MAZE_ST_INTEGRATE);
-    CKL();
-    int rc = field_and_forces(ctx, order);
+    bool counted = false;
+    int rc = kick_drift(ctx, &counted);
+    if (rc) return rc;
+    rc = field_and_forces(ctx, order, counted);
     if (rc) return rc;
     CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
                         (const double*)ctx->F, (const double*)ctx->hdt_acc));
@@ -1297,12 +1320,10 @@ int step_body(p3maze_ctx* ctx, int order) {
 // kick and pointer rotation.  head + cluster smoothing + tail = step_body.
 int step_head(p3maze_ctx* ctx) {
     cudaStream_t s = ctx->stream;
-    stage_begin(ctx, P3MAZE_ST_INTEGRATE);
-    k_kick_drift<<<nblk(ctx->np), P3_THREADS, 0, s>>>(ctx->np, ctx->r, ctx->v, ctx->F, ctx->hdt_acc, ctx->dt, ctx->L);
-    count(ctx, P3MAZE_ST_INTEGRATE);
-    stage_end(ctx, P3MAZE_ST_INTEGRATE);
-    CKL();
-    int rc = build_cells(ctx);
+    bool counted = false;
+    int rc = kick_drift(ctx, &counted);
+    if (rc) return rc;
+    rc = build_cells(ctx, counted);
     return rc ? rc : spread_assign<float>(ctx);
 }
 
