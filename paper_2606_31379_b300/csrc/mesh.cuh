@@ -2659,7 +2659,8 @@ k_gather(int np, const PQ* __restrict__ xq, const int* __restrict__ order, int n
 static __global__ void __launch_bounds__(P3_THREADS)
 k_gather_mp(int np, const MeshPt* __restrict__ mp, const int* __restrict__ order, int n, double inv_h,
             double ke, const float* __restrict__ phi, const double* __restrict__ Fsr_s,
-            double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr) {
+            double* __restrict__ F, double* __restrict__ Flr, double* __restrict__ Fsr,
+            const double* __restrict__ hdt_acc, double* __restrict__ v) {
     pdl_wait();
     pdl_trigger();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2729,9 +2730,13 @@ k_gather_mp(int np, const MeshPt* __restrict__ mp, const int* __restrict__ order
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double sr = Fsr_s[3 * s + d];
-        F[3 * i + d] = sr + f[d];
+        const double Ft = sr + f[d];
+        F[3 * i + d] = Ft;
         Flr[3 * i + d] = f[d];
         Fsr[3 * i + d] = sr;
+        // the closing half kick of the step (k_kick's arithmetic), when no
+        // other term is added to F after this kernel
+        if (v != nullptr) v[3 * i + d] += hdt_acc[i] * Ft;
     }
 }
 

@@ -1155,10 +1155,14 @@ int pair_forces(p3maze_ctx* ctx) {
     return P3MAZE_OK;
 }
 
-// Join the pair branch, then interpolate the mesh force and add the bonded terms.
-int gather_forces(p3maze_ctx* ctx) {
+// Join the pair branch, then interpolate the mesh force and add the bonded
+// terms.  kick: the step's closing half kick follows; the mixed
+// finite-difference interpolation does it itself when nothing else is added
+// to F (no molecules), and *kicked says so.
+int gather_forces(p3maze_ctx* ctx, bool kick, bool* kicked) {
     cudaStream_t s = ctx->stream;
     const bool mixed = ctx->prec == P3MAZE_MIXED;
+    *kicked = false;
     CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     stage_begin(ctx, P3MAZE_ST_GATHER);
     if (ctx->lr_force == P3MAZE_LR_FORCE_ANALYTIC) {
@@ -1171,9 +1175,11 @@ int gather_forces(p3maze_ctx* ctx) {
                                                                  ctx->ke, ctx->phi[ctx->icur], ctx->Fs, ctx->F,
                                                                  ctx->Flr, ctx->Fsr);
     } else if (mixed) {
+        *kicked = kick && ctx->nmol == 0;
         CK(launch_maybe_pdl(ctx->pdl, k_gather_mp, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->mp,
                             ctx->order, ctx->N, ctx->inv_h, ctx->ke, (const float*)ctx->phi32, (const double*)ctx->Fs,
-                            ctx->F, ctx->Flr, ctx->Fsr));
+                            ctx->F, ctx->Flr, ctx->Fsr, *kicked ? (const double*)ctx->hdt_acc : (const double*)nullptr,
+                            *kicked ? ctx->v : (double*)nullptr));
     } else {
         CK(launch_maybe_pdl(ctx->pdl, k_gather<double>, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np,
                             (const PQ*)ctx->xq, (const int*)ctx->order, ctx->N, ctx->inv_h, ctx->ke,
@@ -1202,14 +1208,15 @@ int mesh_pipeline(p3maze_ctx* ctx, int pred_order) {
 }
 
 // Cell list, mesh pipeline and forces at the current positions.  The gather
-// stage stays open: the caller closes it (after the final half kick).
-int field_and_forces(p3maze_ctx* ctx, int pred_order, bool counted) {
+// stage stays open: the caller closes it (after the final half kick, which
+// the interpolation may have done: *kicked).
+int field_and_forces(p3maze_ctx* ctx, int pred_order, bool counted, bool kick, bool* kicked) {
     int rc = build_cells(ctx, counted);
     if (rc) return rc;
     rc = ctx->prec == P3MAZE_MIXED ? mesh_pipeline<float>(ctx, pred_order)
                                    : mesh_pipeline<double>(ctx, pred_order);
     if (rc) return rc;
-    return gather_forces(ctx);
+    return gather_forces(ctx, kick, kicked);
 }
 
 // Copy the solver state to the host and turn a recorded failure into an error.
@@ -1252,7 +1259,8 @@ int initialise_field(p3maze_ctx* ctx) {
     ctx->nhist = 0;
     const bool was_timing = ctx->timing;
     ctx->timing = false;
-    int rc = field_and_forces(ctx, 0, false);
+    bool kicked = false;
+    int rc = field_and_forces(ctx, 0, false, false, &kicked);
     ctx->timing = was_timing;
     if (rc) return rc;
     rc = read_solver_state(ctx);
@@ -1297,11 +1305,14 @@ int step_body(p3maze_ctx* ctx, int order) {
     bool counted = false;
     int rc = kick_drift(ctx, &counted);
     if (rc) return rc;
-    rc = field_and_forces(ctx, order, counted);
+    bool kicked = false;
+    rc = field_and_forces(ctx, order, counted, true, &kicked);
     if (rc) return rc;
-    CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
-                        (const double*)ctx->F, (const double*)ctx->hdt_acc));
-    count(ctx, P3MAZE_ST_GATHER);
+    if (!kicked) {
+        CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
+                            (const double*)ctx->F, (const double*)ctx->hdt_acc));
+        count(ctx, P3MAZE_ST_GATHER);
+    }
     stage_end(ctx, P3MAZE_ST_GATHER);
     CKL();
     // the converged correction becomes y^{k+1}; the oldest history buffer is reused
@@ -1319,7 +1330,6 @@ int step_body(p3maze_ctx* ctx, int order) {
 // the tail forks the short-range branch and runs the solve, interpolation,
 // kick and pointer rotation.  head + cluster smoothing + tail = step_body.
 int step_head(p3maze_ctx* ctx) {
-    cudaStream_t s = ctx->stream;
     bool counted = false;
     int rc = kick_drift(ctx, &counted);
     if (rc) return rc;
@@ -1330,12 +1340,15 @@ int step_head(p3maze_ctx* ctx) {
 int step_tail(p3maze_ctx* ctx, int order) {
     int rc = pair_forces(ctx);
     if (!rc) rc = solve_field<float>(ctx, order);
-    if (!rc) rc = gather_forces(ctx);
+    bool kicked = false;
+    if (!rc) rc = gather_forces(ctx, true, &kicked);
     if (rc) return rc;
     cudaStream_t s = ctx->stream;
-    CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
-                        (const double*)ctx->F, (const double*)ctx->hdt_acc));
-    count(ctx, P3MAZE_ST_GATHER);
+    if (!kicked) {
+        CK(launch_maybe_pdl(ctx->pdl, k_kick, dim3(nblk(ctx->np)), dim3(P3_THREADS), 0, s, ctx->np, ctx->v,
+                            (const double*)ctx->F, (const double*)ctx->hdt_acc));
+        count(ctx, P3MAZE_ST_GATHER);
+    }
     stage_end(ctx, P3MAZE_ST_GATHER);
     CKL();
     double* oldest = ctx->yh[3];
