@@ -2144,86 +2144,189 @@ __device__ __forceinline__ float2 fht_cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
 
-// The twiddles of one lane: stage of half-size 32 M (M = R/2 .. 1), register
-// pair (j, j + M), j mod 2M = j' < M: in[M - 1 + j'] = W_{64M}^(lane + 32 j');
-// cross-lane stage of half-size m = 16 >> s (s < 4): x[s] = W_{2m}^(lane mod m)
-// on the lane with bit m set, 1 on its partner (half-size 1 needs none).
+// Line length n = 32 R with R = Q R2: Q = 3 or 5 for a mixed-radix length
+// (192, 320, 384), else 1; R2 a power of two.  The radix-2 part transforms
+// m = 32 R2 points.
+template <int R>
+struct FhtShape {
+    static constexpr int Q = R % 3 == 0 ? 3 : R % 5 == 0 ? 5 : 1;
+    static constexpr int R2 = R / Q;
+};
+
+// The twiddles of one lane.  Radix-2 part (m points): stage of half-size
+// 32 M (M = R2/2 .. 1), register pair (j, j + M), j mod 2M = j' < M:
+// in[M - 1 + j'] = W_{64M}^(lane + 32 j'); cross-lane stage of half-size
+// h = 16 >> s (s < 4): x[s] = W_{2h}^(lane mod h) on the lane with bit h set,
+// 1 on its partner (half-size 1 needs none).  Radix-Q step: rq[j1 (Q-1) +
+// k - 1] = W_n^((lane + 32 j1) k), om[j] = exp(-2 pi i j / Q).  The table tw
+// holds W_n^t, t < n/2, then (Q > 1) the Q roots of unity.
 template <int R>
 struct FhtTw {
-    float2 in[R > 1 ? R - 1 : 1];
+    static constexpr int Q = FhtShape<R>::Q, R2 = FhtShape<R>::R2;
+    float2 in[R2 > 1 ? R2 - 1 : 1];
     float2 x[4];
+    float2 rq[Q > 1 ? R2 * (Q - 1) : 1];
+    float2 om[Q > 1 ? Q : 1];
 };
 
 template <int R>
 __device__ __forceinline__ void fht_twiddles(FhtTw<R>& t, const float2* __restrict__ tw, int lane) {
-    constexpr int n = 32 * R;
+    constexpr int n = 32 * R, Q = FhtShape<R>::Q, R2 = FhtShape<R>::R2, m = 32 * R2;
+    // W_m^k = W_n^(Q k)
 #pragma unroll
-    for (int M = R / 2; M >= 1; M >>= 1)
+    for (int M = R2 / 2; M >= 1; M >>= 1)
 #pragma unroll
-        for (int j = 0; j < M; ++j) t.in[M - 1 + j] = tw[(lane + 32 * j) * (n / (64 * M))];
+        for (int j = 0; j < M; ++j) t.in[M - 1 + j] = tw[Q * (lane + 32 * j) * (m / (64 * M))];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-        const int m = 16 >> s;
-        t.x[s] = (lane & m) ? tw[(lane & (m - 1)) * (n / (2 * m))] : make_float2(1.f, 0.f);
+        const int h = 16 >> s;
+        t.x[s] = (lane & h) ? tw[Q * (lane & (h - 1)) * (m / (2 * h))] : make_float2(1.f, 0.f);
+    }
+    if constexpr (Q > 1) {
+#pragma unroll
+        for (int j1 = 0; j1 < R2; ++j1)
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                const int e = (lane + 32 * j1) * k;  // < n; W_n^(e) = -W_n^(e - n/2) past n/2
+                const float2 w = tw[e < n / 2 ? e : e - n / 2];
+                t.rq[j1 * (Q - 1) + k - 1] = e < n / 2 ? w : make_float2(-w.x, -w.y);
+            }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) t.om[j] = tw[n / 2 + j];
     }
 }
 
-// In-place radix-2 DIF FFT of n = 32 R points held as v[j] = z[lane + 32 j];
-// on return v[j] holds Z[rev(lane + 32 j)] (log2 n-bit reversal).
-template <int R>
-__device__ __forceinline__ void warp_fft_dif(float2 (&v)[R], const FhtTw<R>& t, int lane) {
+// In-place radix-2 DIF FFT of m = 32 R2 points held as v[j] = z[lane + 32 j];
+// on return v[j] holds Z[rev(lane + 32 j)] (log2 m-bit reversal).
+template <int R2>
+__device__ __forceinline__ void warp_fft_dif_p2(float2 (&v)[R2], const float2* tin, const float2* tx, int lane) {
 #pragma unroll
-    for (int M = R / 2; M >= 1; M >>= 1)
+    for (int M = R2 / 2; M >= 1; M >>= 1)
 #pragma unroll
-        for (int j = 0; j < R; ++j)
+        for (int j = 0; j < R2; ++j)
             if ((j & M) == 0) {
                 const float2 a = v[j], b = v[j + M];
                 v[j] = make_float2(a.x + b.x, a.y + b.y);
-                v[j + M] = fht_cmul(make_float2(a.x - b.x, a.y - b.y), t.in[M - 1 + (j & (2 * M - 1))]);
+                v[j + M] = fht_cmul(make_float2(a.x - b.x, a.y - b.y), tin[M - 1 + (j & (2 * M - 1))]);
             }
-    // lane pairs (l, l ^ m): the lane with bit m set holds z[i + m] and forms
-    // (z[i] - z[i + m]) W_{2m}^(i mod 2m), its partner z[i] + z[i + m]
+    // lane pairs (l, l ^ h): the lane with bit h set holds z[i + h] and forms
+    // (z[i] - z[i + h]) W_{2h}^(i mod 2h), its partner z[i] + z[i + h]
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
-        const int m = 16 >> s;
-        const float sg = (lane & m) ? -1.f : 1.f;
+        const int h = 16 >> s;
+        const float sg = (lane & h) ? -1.f : 1.f;
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const float ox = __shfl_xor_sync(0xffffffffu, v[j].x, m);
-            const float oy = __shfl_xor_sync(0xffffffffu, v[j].y, m);
+        for (int j = 0; j < R2; ++j) {
+            const float ox = __shfl_xor_sync(0xffffffffu, v[j].x, h);
+            const float oy = __shfl_xor_sync(0xffffffffu, v[j].y, h);
             const float2 d = make_float2(fmaf(sg, v[j].x, ox), fmaf(sg, v[j].y, oy));
-            v[j] = s < 4 ? fht_cmul(d, t.x[s]) : d;
+            v[j] = s < 4 ? fht_cmul(d, tx[s]) : d;
         }
     }
 }
 
 // In-place radix-2 DIT FFT: v[j] holds X[rev(lane + 32 j)] on entry and
-// Y[lane + 32 j] = sum_k X[k] W_n^(k (lane + 32 j)) on return.  The stages
+// Y[lane + 32 j] = sum_k X[k] W_m^(k (lane + 32 j)) on return.  The stages
 // of the DIF transform in reverse order, each twiddle applied to the upper
 // input before its butterfly.
-template <int R>
-__device__ __forceinline__ void warp_fft_dit(float2 (&v)[R], const FhtTw<R>& t, int lane) {
+template <int R2>
+__device__ __forceinline__ void warp_fft_dit_p2(float2 (&v)[R2], const float2* tin, const float2* tx, int lane) {
 #pragma unroll
     for (int s = 4; s >= 0; --s) {
-        const int m = 16 >> s;
-        const float sg = (lane & m) ? -1.f : 1.f;
+        const int h = 16 >> s;
+        const float sg = (lane & h) ? -1.f : 1.f;
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const float2 u = s < 4 ? fht_cmul(v[j], t.x[s]) : v[j];
-            const float ox = __shfl_xor_sync(0xffffffffu, u.x, m);
-            const float oy = __shfl_xor_sync(0xffffffffu, u.y, m);
+        for (int j = 0; j < R2; ++j) {
+            const float2 u = s < 4 ? fht_cmul(v[j], tx[s]) : v[j];
+            const float ox = __shfl_xor_sync(0xffffffffu, u.x, h);
+            const float oy = __shfl_xor_sync(0xffffffffu, u.y, h);
             v[j] = make_float2(fmaf(sg, u.x, ox), fmaf(sg, u.y, oy));
         }
     }
 #pragma unroll
-    for (int M = 1; M <= R / 2; M <<= 1)
+    for (int M = 1; M <= R2 / 2; M <<= 1)
 #pragma unroll
-        for (int j = 0; j < R; ++j)
+        for (int j = 0; j < R2; ++j)
             if ((j & M) == 0) {
-                const float2 a = v[j], b = fht_cmul(v[j + M], t.in[M - 1 + (j & (2 * M - 1))]);
+                const float2 a = v[j], b = fht_cmul(v[j + M], tin[M - 1 + (j & (2 * M - 1))]);
                 v[j] = make_float2(a.x + b.x, a.y + b.y);
                 v[j + M] = make_float2(a.x - b.x, a.y - b.y);
             }
+}
+
+__device__ __forceinline__ float2 fht_cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// DIF FFT of n = 32 R points held as v[j] = z[lane + 32 j].  Q = 1: radix 2,
+// position p holds Z[rev(p)].  Q > 1: first the radix-Q step across the
+// registers j1 + R2 j2 (points q + m j2, q = lane + 32 j1): Y_k[q] =
+// W_n^(q k) sum_j2 z[q + m j2] W_Q^(j2 k) into register j1 + R2 k, then the
+// m-point radix-2 transform of each Y_k; position q' + m k (q' = lane +
+// 32 j1) holds Z[k + Q rev_m(q')].
+template <int R>
+__device__ __forceinline__ void warp_fft_dif(float2 (&v)[R], const FhtTw<R>& t, int lane) {
+    constexpr int Q = FhtShape<R>::Q, R2 = FhtShape<R>::R2;
+    if constexpr (Q == 1) {
+        warp_fft_dif_p2<R>(v, t.in, t.x, lane);
+    } else {
+#pragma unroll
+        for (int j1 = 0; j1 < R2; ++j1) {
+            float2 xs[Q];
+#pragma unroll
+            for (int j2 = 0; j2 < Q; ++j2) xs[j2] = v[j1 + R2 * j2];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                float2 y = xs[0];
+#pragma unroll
+                for (int j2 = 1; j2 < Q; ++j2) y = fht_cadd(y, fht_cmul(xs[j2], t.om[(j2 * k) % Q]));
+                v[j1 + R2 * k] = k ? fht_cmul(y, t.rq[j1 * (Q - 1) + k - 1]) : y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            float2 g[R2];
+#pragma unroll
+            for (int j1 = 0; j1 < R2; ++j1) g[j1] = v[j1 + R2 * k];
+            warp_fft_dif_p2<R2>(g, t.in, t.x, lane);
+#pragma unroll
+            for (int j1 = 0; j1 < R2; ++j1) v[j1 + R2 * k] = g[j1];
+        }
+    }
+}
+
+// DIT FFT: v holds X in warp_fft_dif's output order on entry and
+// Y[lane + 32 j] = sum_f X[f] W_n^(f (lane + 32 j)) on return.  Q > 1: the
+// m-point radix-2 transform of each group k, then per q the twiddle
+// W_n^(q k) and the radix-Q step across the groups.
+template <int R>
+__device__ __forceinline__ void warp_fft_dit(float2 (&v)[R], const FhtTw<R>& t, int lane) {
+    constexpr int Q = FhtShape<R>::Q, R2 = FhtShape<R>::R2;
+    if constexpr (Q == 1) {
+        warp_fft_dit_p2<R>(v, t.in, t.x, lane);
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            float2 g[R2];
+#pragma unroll
+            for (int j1 = 0; j1 < R2; ++j1) g[j1] = v[j1 + R2 * k];
+            warp_fft_dit_p2<R2>(g, t.in, t.x, lane);
+#pragma unroll
+            for (int j1 = 0; j1 < R2; ++j1) v[j1 + R2 * k] = g[j1];
+        }
+#pragma unroll
+        for (int j1 = 0; j1 < R2; ++j1) {
+            float2 gs[Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                gs[k] = k ? fht_cmul(v[j1 + R2 * k], t.rq[j1 * (Q - 1) + k - 1]) : v[j1 + R2 * k];
+#pragma unroll
+            for (int j2 = 0; j2 < Q; ++j2) {
+                float2 y = gs[0];
+#pragma unroll
+                for (int k = 1; k < Q; ++k) y = fht_cadd(y, fht_cmul(gs[k], t.om[(k * j2) % Q]));
+                v[j1 + R2 * j2] = y;
+            }
+        }
+    }
 }
 
 // Shared-memory word at byte offset off of the kernel's dynamic shared memory.
@@ -2242,12 +2345,15 @@ __host__ __device__ constexpr int fht_hibit(int x) {
 // Hartley transforms, times 2, of two lines held as v[j] = (a, b) at point
 // lane + 32 j; on return v[j] = (2 Ha, 2 Hb) at position lane + 32 j.
 // Forward (INV false): points in natural order, coefficients in
-// bit-reversed order (DIF).  Inverse: points in bit-reversed order,
-// coefficients in natural order (DIT).  The split pairs each Z[k] with
-// Z[n - k], which another lane holds:
-//  - DIF output, position p = l + 32 j (Z[rev p]): Z[n - rev p] sits at
-//    p ^ (hibit(p) - 1), i.e. lane l ^ (hibit(l) - 1) for j = 0, else lane
-//    l ^ 31 and register j ^ (hibit(j) - 1);
+// warp_fft_dif's order.  Inverse: points in that order, coefficients in
+// natural order (DIT).  The split pairs each Z[f] with Z[n - f], which
+// another lane holds:
+//  - DIF output, position p = l + 32 j1 + m k (register j = j1 + R2 k, Z[f]
+//    with f = k + Q rev_m(l + 32 j1)): for k = 0 the partner is the radix-2
+//    one, p ^ (hibit(p) - 1), i.e. lane l ^ (hibit(l) - 1) for j1 = 0, else
+//    lane l ^ 31 and register j1 ^ (hibit(j1) - 1); for k > 0 it is
+//    f' = (Q - k) + Q (m - 1 - rev_m(l + 32 j1)): lane l ^ 31, register
+//    (j1 ^ (R2 - 1)) + R2 (Q - k);
 //  - DIT output, position m = l + 32 j: n - m is lane 32 - l, register
 //    R - 1 - j for l > 0, and register (R - j) mod R of lane 0 itself.
 // All 32 lanes of a warp call it.
@@ -2265,11 +2371,13 @@ __device__ __forceinline__ void fht_pair(float2 (&v)[R], const FhtTw<R>& t, int 
         }
     } else {
         warp_fft_dif<R>(v, t, lane);
+        constexpr int Q = FhtShape<R>::Q, R2 = FhtShape<R>::R2;
         const int src0 = lane ? lane ^ ((1 << (31 - __clz(lane))) - 1) : 0;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            const int jp = j ? j ^ (fht_hibit(j) - 1) : 0;
-            const int src = j ? lane ^ 31 : src0;
+            const int j1 = j % R2, k = j / R2;
+            const int jp = k ? (j1 ^ (R2 - 1)) + R2 * (Q - k) : j1 ? j1 ^ (fht_hibit(j1) - 1) : 0;
+            const int src = (k || j1) ? lane ^ 31 : src0;
             w[j].x = __shfl_sync(0xffffffffu, v[jp].x, src);
             w[j].y = __shfl_sync(0xffffffffu, v[jp].y, src);
         }
@@ -2445,9 +2553,9 @@ k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __re
 }
 
 
-// ---------------------------------------------------------------- FFT smoothing, n = 256
-// A 256 x 256 plane does not fit in shared memory, so the transforms run as
-// five passes over global memory: forward x (row pairs straight from global
+// ---------------------------------------------------------------- FFT smoothing, n >= 192
+// A plane of 192 points or more does not fit in shared memory, so the
+// transforms run as five passes over global memory: forward x (row pairs straight from global
 // memory, k_fht_rows), forward y (k_fht_cols), forward z + scaling + inverse
 // z (k_fht_cols, MODE 1), inverse y, inverse x with per-block sums.  The
 // line-pair transform is fht_pair, as above.
@@ -2511,7 +2619,7 @@ k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* 
 // scaling by S (laid out like the data; its tile copied in by cp.async
 // meanwhile), inverse.
 template <int R, int MODE, bool INV>
-__global__ void __launch_bounds__(kFhtColThreads, 2)  // two blocks per SM: at most 64 registers
+__global__ void __launch_bounds__(kFhtColThreads, R <= 8 ? 2 : 1)  // two blocks per SM up to 256 points
 k_fht_cols(float* __restrict__ d, int64_t ls, int64_t os, const float2* __restrict__ tw,
            const float* __restrict__ S) {
     constexpr int n = 32 * R, Q = n * 32 / 4, PER = Q / kFhtColThreads;
@@ -2577,8 +2685,13 @@ k_fht_cols(float* __restrict__ d, int64_t ls, int64_t os, const float2* __restri
 // Shared memory of k_fht_cols: the tile, and in MODE 1 the tile of S.
 inline size_t fht_cols_smem_bytes(int n, int mode) { return (size_t)(mode ? 2 : 1) * n * 32 * sizeof(float); }
 
-// Meshes the FFT smoothing handles: a plane per block up to 128, five passes at 256.
-inline bool fht_supported(int n) { return n == 32 || n == 64 || n == kFhtMaxN || n == kFhtBigN; }
+// Meshes the FFT smoothing handles: a plane per block up to 128, five
+// passes over global memory at 192, 256, 320 and 384 (192 = 3 x 64, 320 =
+// 5 x 64, 384 = 3 x 128 by the mixed-radix transform).
+inline bool fht_passes(int n) { return n == 192 || n == kFhtBigN || n == 320 || n == 384; }
+inline bool fht_supported(int n) { return n == 32 || n == 64 || n == kFhtMaxN || fht_passes(n); }
+// Radix-3/5 factor of a supported length (1 for powers of two).
+inline int fht_q(int n) { return n % 3 == 0 ? 3 : n % 5 == 0 ? 5 : 1; }
 
 // ---------------------------------------------------------------- interpolation
 // F_a = -ke Q_a sum_n W(r_a - r_n) (D phi)_n with central differences

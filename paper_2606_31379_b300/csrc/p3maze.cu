@@ -503,33 +503,49 @@ cudaError_t launch_fht_passes(p3maze_ctx* ctx) {
 // per-plane (or per-block) sums.  The block counter is the FP64 field
 // update's (mixed only, so never used by both in one context).
 cudaError_t launch_fht_smoothing(p3maze_ctx* ctx) {
-    if (ctx->N == kFhtBigN) return launch_fht_passes<kFhtBigN / 32>(ctx);
+    switch (ctx->N) {
+        case 192: return launch_fht_passes<6>(ctx);
+        case 256: return launch_fht_passes<8>(ctx);
+        case 320: return launch_fht_passes<10>(ctx);
+        case 384: return launch_fht_passes<12>(ctx);
+        default: break;
+    }
     return launch_fht(ctx->N, ctx->pdl, ctx->pdl, ctx->stream, (const float*)ctx->q, (float*)ctx->lev[0].e,
                       (float*)ctx->qs, (const float2*)ctx->fht_tw, (const float*)ctx->Ssm, ctx->partial,
                       &ctx->dmg->arrive_sum, ctx->dscal + S_QSUM);
 }
-inline int fht_smoothing_launches(int n) { return n == kFhtBigN ? 5 : 3; }
+inline int fht_smoothing_launches(int n) { return fht_passes(n) ? 5 : 3; }
 
-// Bit-reversed position of each index 0..n-1 (n a power of two).
+// Position of each frequency 0..n-1 in the forward transforms' output:
+// n = Q m (m a power of two), frequency f = k + Q r at rev_m(r) + m k
+// (Q = 1: plain bit reversal).
 std::vector<int> fht_positions(int n) {
+    const int Q = fht_q(n), m = n / Q;
     int bits = 0;
-    while ((1 << bits) < n) ++bits;
+    while ((1 << bits) < m) ++bits;
     std::vector<int> pos(n);
-    for (int k = 0; k < n; ++k) {
+    for (int f = 0; f < n; ++f) {
+        const int k = f % Q, r0 = f / Q;
         int r = 0;
-        for (int b = 0; b < bits; ++b) r |= ((k >> b) & 1) << (bits - 1 - b);
-        pos[k] = r;
+        for (int b = 0; b < bits; ++b) r |= ((r0 >> b) & 1) << (bits - 1 - b);
+        pos[f] = r + m * k;
     }
     return pos;
 }
 
-// Twiddles exp(-2 pi i k / n), k < n / 2, from FP64.
+// Twiddles exp(-2 pi i k / n), k < n / 2, then for a mixed-radix length the
+// Q roots exp(-2 pi i j / Q); from FP64.
 std::vector<float2> fht_twiddle_table(int n) {
-    std::vector<float2> tw(n / 2);
+    const int Q = fht_q(n);
+    std::vector<float2> tw(n / 2 + (Q > 1 ? Q : 0));
     for (int k = 0; k < n / 2; ++k)
         tw[k] = make_float2((float)std::cos(2.0 * kPi * k / n), (float)-std::sin(2.0 * kPi * k / n));
+    if (Q > 1)
+        for (int j = 0; j < Q; ++j)
+            tw[n / 2 + j] = make_float2((float)std::cos(2.0 * kPi * j / Q), (float)-std::sin(2.0 * kPi * j / Q));
     return tw;
 }
+inline size_t fht_twiddle_count(int n) { return (size_t)(n / 2 + (fht_q(n) > 1 ? fht_q(n) : 0)); }
 
 // Raise the shared-memory limit of the FFT kernels for n points per axis.
 // The limit is an attribute of the kernel, shared by every context in the
@@ -542,11 +558,17 @@ cudaError_t fht_raise_smem(int n) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         return e;
     };
-    if (n == kFhtBigN) {
-        constexpr int R = kFhtBigN / 32;
-        cudaError_t e = raise((const void*)k_fht_cols<R, 0, false>, fht_cols_smem_bytes(n, 0));
-        if (e == cudaSuccess) e = raise((const void*)k_fht_cols<R, 0, true>, fht_cols_smem_bytes(n, 0));
-        if (e == cudaSuccess) e = raise((const void*)k_fht_cols<R, 1, false>, fht_cols_smem_bytes(n, 1));
+    if (fht_passes(n)) {
+        const void* k0[4] = {(const void*)k_fht_cols<6, 0, false>, (const void*)k_fht_cols<8, 0, false>,
+                             (const void*)k_fht_cols<10, 0, false>, (const void*)k_fht_cols<12, 0, false>};
+        const void* k0i[4] = {(const void*)k_fht_cols<6, 0, true>, (const void*)k_fht_cols<8, 0, true>,
+                              (const void*)k_fht_cols<10, 0, true>, (const void*)k_fht_cols<12, 0, true>};
+        const void* k1[4] = {(const void*)k_fht_cols<6, 1, false>, (const void*)k_fht_cols<8, 1, false>,
+                             (const void*)k_fht_cols<10, 1, false>, (const void*)k_fht_cols<12, 1, false>};
+        const int i = n == 192 ? 0 : n == 256 ? 1 : n == 320 ? 2 : 3;
+        cudaError_t e = raise(k0[i], fht_cols_smem_bytes(n, 0));
+        if (e == cudaSuccess) e = raise(k0i[i], fht_cols_smem_bytes(n, 0));
+        if (e == cudaSuccess) e = raise(k1[i], fht_cols_smem_bytes(n, 1));
         return e;
     }
     const size_t sxy = fht_smem_bytes(n), sz = fht_z_smem_bytes(n), sc = fht_cols_smem_bytes(n, 1);
@@ -1871,7 +1893,7 @@ size_t planned_bytes(const p3maze_params* p, int nlev) {
     if (mixed && p->method != P3MAZE_METHOD_PMAZE && cluster_mesh_ok(N)) b += a(sizeof(ClusterMesh));
     if (mixed && p->method != P3MAZE_METHOD_PMAZE && (N <= kCoarseMax || fht_supported(N))) {
         b += a(4 * P);  // spectral smoothing table
-        if (fht_supported(N)) b += a(sizeof(float2) * (size_t)(N / 2));  // its FFT twiddles
+        if (fht_supported(N)) b += a(sizeof(float2) * fht_twiddle_count(N));  // its FFT twiddles
     }
     {
         const dim3 gr = resid_grid(N);

@@ -363,14 +363,15 @@ def test_cluster_smoothing_matches_oracle(P, mesh):
         assert b.timing()["launches"]["smooth"] == a.stats()["smooth_steps"] + 1
 
 
-@pytest.mark.parametrize("mesh", [16, 24, 32, 48, 60, 64, 128, 256])
+@pytest.mark.parametrize("mesh", [16, 24, 32, 48, 60, 64, 128, 192, 256, 320])
 def test_spectral_smoothing_matches_oracle(P, mesh):
     """Smoothing mode 6: (I + cM)^K applied as its diagonal (1 + c lambda_k)^K
     between FP32 Hartley transforms matches the oracle's K explicit steps.
     N = 32, 64, 128 take each 1D transform by FFT (three transform launches,
-    the last forming the neutrality sum), N = 256 by five FFT passes over
-    global memory, the other sizes by dense transforms (three launches, a sum
-    over blocks and the final sum).
+    the last forming the neutrality sum), N = 192, 256, 320 by five FFT
+    passes over global memory (192 = 3 x 64 and 320 = 5 x 64 with a radix-3
+    or radix-5 step), the other sizes by dense transforms (three launches, a
+    sum over blocks and the final sum).
     Bar: a dense pass sums N products of magnitude up to sqrt2 |x|, so q^s
     carries about 6 sqrt(N) 2^-24 sqrt2 of the largest intermediate, below
     5e-6 of max |q^s| for N <= 64; an FFT pass rounds log2 N times per point,
@@ -386,7 +387,7 @@ def test_spectral_smoothing_matches_oracle(P, mesh):
         assert np.abs(qa - mf["qs"]).max() <= 5e-6 * np.abs(mf["qs"]).max()
         a.set_timing(True)
         a.step(2)
-        assert a.timing()["launches"]["smooth"] == 2 * {32: 3, 64: 3, 128: 3, 256: 5}.get(mesh, 5)
+        assert a.timing()["launches"]["smooth"] == 2 * {32: 3, 64: 3, 128: 3}.get(mesh, 5)
         if mesh <= 64:
             ref = oracle_full(s, a.positions(), 0.30, min(9.0, box), mesh)
             assert rel_rms(a.forces(), ref["F"]) < 1e-4
@@ -400,6 +401,22 @@ def test_spectral_smoothing_matches_oracle(P, mesh):
     with P.Context.from_system(w, alpha=0.30, r_cut=9.0, mesh=80, tol=1e-8, dt=1.0, precision="mixed") as c:
         with pytest.raises(P.P3MaZeError, match="spectral"):
             c.set_tuning(diffusion_fuse=6)
+
+
+def test_spectral_smoothing_384(P):
+    """384 = 3 x 128, the mixed-radix FFT with four registers per lane in its
+    radix-2 part: q^s of the five-pass spectral smoothing against the
+    oracle's K explicit diffusion steps applied to the GPU's own assigned
+    charge (a dilute melt: the smoothing does not depend on the density).
+    Bar as for the other FFT sizes."""
+    box = 0.8 * 384
+    s = S.nacl_melt(20000, box, seed=77)
+    with P.Context.from_system(s, alpha=0.30, r_cut=9.0, mesh=384, tol=1e-6, dt=1.0, precision="mixed") as a:
+        a.set_tuning(diffusion_fuse=6)
+        a.reinit()
+        st = a.stats()
+        ref = O.smooth(a.mesh("q").astype(np.float64), st["smooth_steps"], st["smooth_coeff"])
+        assert np.abs(a.mesh("qs") - ref).max() <= 5e-6 * np.abs(ref).max()
 
 
 def _use_cluster(P, c):
