@@ -2559,7 +2559,7 @@ k_fht_z(float* __restrict__ tz, const float2* __restrict__ tw, const float* __re
 // memory, k_fht_rows), forward y (k_fht_cols), forward z + scaling + inverse
 // z (k_fht_cols, MODE 1), inverse y, inverse x with per-block sums.  The
 // line-pair transform is fht_pair, as above.
-constexpr int kFhtBigN = 256;
+constexpr int kFhtBigN = 256;      // the largest power of two the passes serve
 constexpr int kFhtRowWarps = 8;     // row pairs per block of k_fht_rows
 constexpr int kFhtColThreads = 512; // 16 warps: one column pair each of a 32-column tile
 

@@ -470,10 +470,11 @@ cudaError_t launch_fht(int n, bool pdl_first, bool pdl, cudaStream_t s, const fl
     }
 }
 
-// n = 256: forward x (q into the ping-pong mesh t), forward y, forward z +
-// scaling + inverse z, inverse y (all in place in t), inverse x (t into q^s,
-// with the neutrality sum by its last block); five launches.  The block
-// counter is the FP64 field update's (never in the same context: mixed only).
+// n = 32 R >= 192 (192, 256, 320, 384): forward x (q into the ping-pong
+// mesh t), forward y, forward z + scaling + inverse z, inverse y (all in
+// place in t), inverse x (t into q^s, with the neutrality sum by its last
+// block); five launches.  The block counter is the FP64 field update's
+// (never in the same context: mixed only).
 template <int R>
 cudaError_t launch_fht_passes(p3maze_ctx* ctx) {
     const int64_t n = 32 * R;
