@@ -1127,6 +1127,8 @@ __device__ __forceinline__ float fix_to_float(fix_t v) {
 // 2^8) split exactly into 2^32 hi + lo.  Which integer is chosen does not
 // matter for exactness: the same integer enters phi and Psi.  Finite inputs
 // of magnitude below 2^23 only (the callers flag non-finite values).
+// (Measured and not kept: one direct float-to-int64 conversion, which gives
+// the same integers, took the residual update at 128^3 from 28.5 to 39 us.)
 __device__ __forceinline__ fix_t float_to_fix(float e) {
     const float f = e * kFixOne;
     if (fabsf(f) < 2147483648.0f) return (fix_t)__float2int_rn(f);
