@@ -239,10 +239,12 @@ typedef struct {
                                    16 <= N <= 64, N % 4 == 0); 6: all K steps at once in
                                    the Hartley basis, where (I + cM)^K is the diagonal
                                    (1 + c lambda_k)^K -- the same operator, rounded
-                                   differently (FP32, N <= 64, 128 or 256; each 1D
-                                   transform by FFT for N = 32, 64, 128 (three launches)
-                                   and 256 (five passes over global memory), dense
-                                   transforms otherwise; the default at those sizes)      */
+                                   differently (FP32, N <= 64 or N in {128, 192, 256,
+                                   320, 384}; each 1D transform by FFT for N = 32, 64,
+                                   128 (three launches) and 192, 256, 320, 384 (five
+                                   passes over global memory; radix 3 or 5 times a power
+                                   of two at 192, 320, 384), dense transforms otherwise;
+                                   the default at those sizes)                             */
     int32_t pair_fork;          /* short-range forces start after: 0 smoothing, 1 the cell list */
     int32_t coarse_max;         /* chosen coarse-level limit (16, 32 or 64)                */
     int32_t pair_blocks;        /* pair-kernel grid: 0 one block per home box, else that many

@@ -2881,7 +2881,7 @@ int p3maze_set_tuning(p3maze_ctx* ctx, const p3maze_tuning* t) {
     if (t->diffusion_fuse > 1 && ctx->prec != P3MAZE_MIXED)
         return fail(ctx, P3MAZE_ERR_INVALID, "fused diffusion steps need mixed precision");
     if (t->diffusion_fuse == 6 && !ctx->Ssm)
-        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64, 128 or 256");
+        return fail(ctx, P3MAZE_ERR_INVALID, "spectral smoothing needs mixed precision and N <= 64 or N in {128, 192, 256, 320, 384}");
     if (t->diffusion_fuse == 5 && !ctx->cluster_ok)
         return fail(ctx, P3MAZE_ERR_INVALID,
                     "cluster smoothing needs 16 <= N <= 64, N % 4 == 0 and a device that runs such clusters");
