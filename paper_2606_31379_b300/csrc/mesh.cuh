@@ -2621,7 +2621,7 @@ k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* 
 // scaling by S (laid out like the data; its tile copied in by cp.async
 // meanwhile), inverse.
 template <int R, int MODE, bool INV>
-__global__ void __launch_bounds__(kFhtColThreads, R <= 8 ? 2 : 1)  // two blocks per SM up to 256 points
+__global__ void __launch_bounds__(kFhtColThreads, 2)  // two blocks per SM (at most 64 registers)
 k_fht_cols(float* __restrict__ d, int64_t ls, int64_t os, const float2* __restrict__ tw,
            const float* __restrict__ S) {
     constexpr int n = 32 * R, Q = n * 32 / 4, PER = Q / kFhtColThreads;
