@@ -2575,7 +2575,7 @@ constexpr int kFhtColThreads = 512; // 16 warps: one column pair each of a 32-co
 // *sum_out.
 constexpr int kFhtRowPairs = 2;
 template <int R, bool INV>
-__global__ void __launch_bounds__(32 * kFhtRowWarps)
+__global__ void __launch_bounds__(32 * kFhtRowWarps, 4)  // four blocks per SM (at most 64 registers)
 k_fht_rows(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
            double* __restrict__ partial, unsigned* __restrict__ arrive, double* __restrict__ sum_out) {
     constexpr int n = 32 * R, NP = kFhtRowPairs;
