@@ -170,7 +170,9 @@ typedef struct {
     int32_t method;         /* P3MAZE_METHOD_MAZE (0), P3MAZE_METHOD_P3M or
                                P3MAZE_METHOD_PMAZE                                         */
     int32_t coarse_max;     /* the first level with n <= coarse_max is solved exactly
-                               (separable Hartley transforms); 0 -> 64 (mixed), 16 (FP64) */
+                               (separable Hartley transforms: by FFT in mixed precision
+                               at n = 32 and 64, dense otherwise); 0 -> 64 (mixed),
+                               16 (FP64)                                                   */
     int32_t lr_force;       /* P3MAZE_LR_FORCE_FD (0, the paper's Eq. 21) or
                                P3MAZE_LR_FORCE_ANALYTIC                                    */
     int32_t sr_shift;       /* P3MAZE_SR_TRUNCATE (0) or P3MAZE_SR_SHIFT_FORCE               */
